@@ -1,0 +1,308 @@
+"""Benchmark: exact order-4 higher-order motif census on a face-to-face-shaped hypergraph.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one pass of the whole exact path over the resident hyperedge list:
+device ingest (normalise, deduplicate, hash sets, CSR; hm_build) and the
+order-4 census (work spaces + every candidate family; hm_count_exact). The
+metric is connected 4-node sets counted per second (the histogram total over
+the step time). Inputs are synthetic (the paper's datasets are not
+available): 330 nodes, 20,000 distinct hyperedges of sizes 2-5, power-law
+node activity. L2 is flushed (256 MiB write) before every timed step.
+
+Under torchrun each rank counts its own replica (weak scaling); rank 0 prints
+one JSON line with the max time over ranks. `--impl reference` times the
+CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "order-4 census: connected 4-node sets counted per second"
+UNIT = "sets/s"
+WORKLOAD = "f2f-330"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(h, order: int, budget_s: float = 15.0):
+    """The oracle (plain ESU + fill-in) on a bounded sample of ESU roots."""
+    import oracle
+    threads = os.cpu_count() or 1
+    g = oracle.Graph.from_hypergraph(h, 4)
+    roots, t_used, sets = 0, 0.0, 0
+    step = max(threads, 8)
+    while t_used < budget_s and roots < h.num_nodes:
+        hi = min(h.num_nodes, roots + step)
+        t0 = time.perf_counter()
+        hist, _ = g.census(order, threads=threads, roots=(roots, hi))
+        t_used += time.perf_counter() - t0
+        sets += int(hist.sum())
+        roots = hi
+        step *= 2
+    return {"value": sets / t_used, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{WORKLOAD} order-{order}: ESU roots [0, {roots}) of {h.num_nodes} "
+                      f"({sets} connected sets in {t_used:.1f} s)"}
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    from paper_2209_10241_gb300 import synth
+    h = synth.workload(WORKLOAD)
+    times = []
+    per_step_budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(h, args.order, budget_s=per_step_budget)
+        if i >= args.warmup:
+            times.append(cb["value"])
+    value = statistics.median(times)
+    cb["value"] = value
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "order": args.order, "nodes": 330,
+                   "hyperedges": 20000},
+        "cpu_baseline": cb,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--order", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2209_10241_gb300 import binding as hm
+    from paper_2209_10241_gb300 import synth
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    hm.load()
+    h = synth.workload(WORKLOAD)
+    mem = torch.from_numpy(h.members).cuda()
+    off = torch.from_numpy(h.offsets).cuda()
+    n = h.num_nodes
+    ncls = hm.num_classes(args.order)
+    hist = torch.empty(ncls, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        g = hm.build(mem, off, n, args.order)
+        hm.count_exact(g, args.order, out=hist)
+        return g
+
+    for _ in range(args.warmup):
+        g = step()
+    totals = hm.work_totals(g, args.order)
+    g.free()
+    torch.cuda.synchronize()
+    sets_per_step = int(hist.sum().item())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # device-resident timed region
+    hm.trace_read()
+    hm.trace_enable(True)
+    launches0 = hm.launch_count()
+    total_ms = 0.0
+    with Clocks(local) as clk:
+        barrier()
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g = step()
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            g.free()
+        barrier()
+    hm.trace_enable(False)
+    launches = hm.launch_count() - launches0
+    trace = hm.trace_read()
+    assert int(hist.sum().item()) == sets_per_step
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = sets_per_step * args.steps * world / (total_ms / 1e3)
+
+    # end-to-end through the C ABI with host buffers
+    hmem = torch.from_numpy(h.members).pin_memory()
+    hoff = torch.from_numpy(h.offsets).pin_memory()
+    hout = torch.empty(ncls, dtype=torch.int64).pin_memory()
+    for _ in range(2):
+        hm.count_exact_host(hmem, hoff, n, args.order, out=hout)
+    barrier()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hm.count_exact_host(hmem, hoff, n, args.order, out=hout)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    assert int(hout.sum().item()) == sets_per_step
+    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_ms = float(t.item())
+    e2e_value = sets_per_step * args.steps * world / (e2e_ms / 1e3)
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # dominant kernel from the trace (events on the launching stream)
+    per = {}
+    for name, ms in trace:
+        c = per.setdefault(name, [0, 0.0])
+        c[0] += 1
+        c[1] += ms
+    dom = max(per, key=lambda k: per[k][1])
+    launches, dom_ms = per[dom][0], per[dom][1]
+    avg_s = dom_ms / launches / 1e3
+    peaks, src = _peaks()
+    gens = totals[dom]
+    bytes_per_gen = {"census_P": 256, "census_S": 256, "census_TX": 288, "census_Q": 320,
+                     "census_W": 64, "census_T3": 96}[dom]
+    achieved = gens * bytes_per_gen / avg_s / 1e9
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "order": args.order, "nodes": n,
+                   "hyperedges": h.num_hyperedges, "l2": "flushed (256 MiB write) before each step",
+                   "parallelism": f"replicas x{world}"},
+        "sets_per_step": sets_per_step,
+        "candidates_per_step": totals,
+        "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4),
+                        "share": round(v[1] / sum(x[1] for x in per.values()), 4)}
+                    for k, v in sorted(per.items(), key=lambda kv: -kv[1][1])},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": src},
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(h.members.nbytes + h.offsets.nbytes),
+                "d2h_bytes_per_step": ncls * 8},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(h, args.order)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

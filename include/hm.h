@@ -1,0 +1,200 @@
+/*
+ * hm.h -- C ABI of the GB300 higher-order motif library.
+ *
+ * Implements the counting step of "Exact and sampling methods for mining
+ * higher-order motifs in large hypergraphs" (Lotito, Musciotto, Battiston,
+ * Montresor): given a hypergraph H and an order k in {3, 4}, the frequency of
+ * every higher-order motif of order k (problem statement, Sec. 3), exactly
+ * (Sec. 4) or by stratified hyperedge sampling (Alg. 4, Sec. 5), plus the
+ * counting of randomised null-model hypergraphs (Sec. 6.3).
+ *
+ * Conventions for every entry point
+ *   - Pointers named d_* are CUDA device pointers; h_* are host pointers.
+ *     The caller owns them; the library keeps no reference after the call's
+ *     stream work completes.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Work is enqueued on it; entry points documented as
+ *     "synchronous" also wait for it.
+ *   - Node ids are int32 in [0, num_nodes). Counts are uint64.
+ *   - Every entry point returns an hm_status; on failure hm_last_error()
+ *     returns a message for the calling thread. No entry point aborts the
+ *     process.
+ *
+ * Motif classes. A k-node pattern is encoded as a mask over the subsets of
+ * its k positions with 2..k members, ordered by size, then lexicographically:
+ *   k=3: bit 0 {0,1}, bit 1 {0,2}, bit 2 {1,2}, bit 3 {0,1,2};
+ *   k=4: bits 0-5 {01,02,03,12,13,23}, bits 6-9 {012,013,023,123},
+ *        bit 10 {0123}.
+ * The canonical mask of a pattern is the minimum over its k! relabelings
+ * (isomorphism, Def. 3). Class ids number the connected canonical masks in
+ * ascending order: 6 classes for k=3, 171 for k=4.
+ */
+#ifndef HM_H_
+#define HM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hm_graph hm_graph;
+typedef int hm_status;
+
+enum {
+  HM_OK = 0,
+  HM_EINVAL = 1,       /* bad argument or input (message says which)            */
+  HM_ENOMEM = 2,       /* a device or host allocation failed                      */
+  HM_ECUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
+  HM_ETABLEFULL = 4,   /* a hash insertion exceeded its probe bound               */
+  HM_ETIMEOUT = 5,     /* a bounded device-side wait gave up                      */
+  HM_EUNSUPPORTED = 6  /* valid request this graph was not built for              */
+};
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* hm_last_error(void);
+
+/* Library version string. */
+const char* hm_version(void);
+
+/* Number of motif classes of order k (6 for k=3, 171 for k=4), -1 otherwise. */
+int hm_num_classes(int order);
+
+/*
+ * Class metadata (Sec. 4.3 isomorphism classes; Alg. 4 needs maxcard and
+ * countmax). For class `cls` of order `order`: its canonical mask, the size of
+ * its largest hyperedge (maxcard) and how many hyperedges of that size it has
+ * (countmax). Any output pointer may be NULL. HM_EINVAL on a bad order/cls.
+ */
+hm_status hm_class_info(int order, int cls, uint32_t* canonical_mask, int32_t* maxcard,
+                        int32_t* countmax);
+
+/*
+ * Class id of a labelled mask of order k (any labelling), or -1 when the
+ * pattern is not connected. HM_EINVAL on a bad order or mask.
+ */
+hm_status hm_class_of_mask(int order, uint32_t mask, int32_t* cls);
+
+/*
+ * Build the device representation of a hypergraph (Def. 1, Sec. 3, with the
+ * hash of every hyperedge used for fill-in, Sec. 4.3).
+ *   d_members  int32[d_offsets[num_hyperedges]]: members, hyperedge by hyperedge
+ *   d_offsets  int64[num_hyperedges + 1]: hyperedge j is
+ *              d_members[d_offsets[j] .. d_offsets[j+1]), offsets[0] == 0,
+ *              non-decreasing (the host reads the last entry)
+ *   num_nodes  node ids must lie in [0, num_nodes), 1 <= num_nodes < 2^31
+ *   max_order  3 or 4: the largest order this graph will be counted at
+ * Normalisation, not errors: repeated members collapse, hyperedges with fewer
+ * than two distinct members are dropped, duplicate hyperedges collapse (E is a
+ * set). Hyperedges with more than max_order distinct members cannot lie in a
+ * max_order-node set (Def. 2), so they are only counted (hm_graph_info).
+ * Synchronous on `stream`. Errors: HM_EINVAL (bad sizes, a member outside
+ * [0, num_nodes), offsets not monotone), HM_ENOMEM, HM_ECUDA. On success *out
+ * owns device memory until hm_free.
+ */
+hm_status hm_build(const int32_t* d_members, const int64_t* d_offsets, int64_t num_hyperedges,
+                   int32_t num_nodes, int max_order, void* stream, hm_graph** out);
+
+/*
+ * Sizes of a built graph. counts (host, 8 entries):
+ *   counts[0] = num_nodes, counts[1] = input hyperedges,
+ *   counts[s] for s = 2..max_order = distinct hyperedges of size s (|E_s|),
+ *   counts[max_order+1] = input hyperedges with more than max_order distinct
+ *   members (not deduplicated), remaining entries 0.
+ */
+hm_status hm_graph_info(const hm_graph* g, int64_t* counts);
+
+/*
+ * Copy E_s (distinct hyperedges of size s, ascending lexicographic order of
+ * their sorted members; the order the sampler indexes) to d_out, an int32
+ * device buffer of s * |E_s| entries. Enqueued on `stream`.
+ */
+hm_status hm_graph_edges(const hm_graph* g, int s, int32_t* d_out, void* stream);
+
+/*
+ * Exact census (problem statement, Sec. 3; exact algorithms, Sec. 4.2):
+ * d_hist[c] = number of `order`-node sets V' whose induced sub-hypergraph
+ * H[V'] (Def. 2) is connected and of class c.
+ *   d_hist  uint64[hm_num_classes(order)], device, overwritten.
+ * Enqueued on `stream` (the first call per order also builds and caches
+ * per-graph work spaces, which synchronises). HM_EINVAL if order is not 3 or
+ * 4, HM_EUNSUPPORTED if order > the graph's max_order.
+ */
+hm_status hm_count_exact(hm_graph* g, int order, uint64_t* d_hist, void* stream);
+
+/*
+ * Stratified hyperedge-sampling estimator (Alg. 4, Sec. 5; budgets as in
+ * Appendix A).
+ *   samples_per_size  host uint64[order+1]; entry s (2..order) is S_s, the
+ *                     number of draws (with replacement) from E_s. NULL: split
+ *                     total_samples as S_2 = floor(S/6), S_4 = floor(S/3),
+ *                     S_3 = S - S_2 - S_4 for order 4 (S_3 = 3 S_2, S_4 = 2 S_2,
+ *                     Appendix A), and S_2 = floor(S/4), S_3 = S - S_2 for
+ *                     order 3.
+ *   seed              Philox4x32-10 key; draw t of stratum s uses counter
+ *                     (t lo, t hi, s, 0x53414D50) and the 64-bit value
+ *                     (r0 << 32) | r1; the index is mulhi64(value, |E_s|)
+ *                     (uniform) or the inverse CDF of d_q at
+ *                     mulhi64(value, Q_s) (weighted).
+ *   d_q               NULL for uniform draws, else uint32 weights (each >= 1) of
+ *                     E_2, E_3, ..., E_order concatenated (device); each counted
+ *                     set is then weighted by floor(2^63 / q_e).
+ *   d_est             double[ncls] (device): the corrected estimate of class c,
+ *                     (n_c * |E_m|) / (S_m * countmax_c) uniform, or
+ *                     (A_c * 2^-63 * Q_m) / (S_m * countmax_c) weighted,
+ *                     with m = maxcard(c), evaluated in IEEE double in this order.
+ *   d_raw             uint64[2 * ncls] (device) or NULL: (raw[2c], raw[2c+1]) =
+ *                     low and high words of the integer accumulator of class c
+ *                     (the plain count n_c for uniform draws).
+ * Enqueued on `stream`. HM_EINVAL on a bad order, or when a stratum with
+ * |E_s| > 0 gets S_s == 0 (its classes could not be estimated); an empty
+ * stratum contributes an exact 0. HM_EUNSUPPORTED if order > max_order.
+ */
+hm_status hm_count_sampled(hm_graph* g, int order, const uint64_t* samples_per_size,
+                           uint64_t total_samples, uint64_t seed, const uint32_t* d_q,
+                           double* d_est, uint64_t* d_raw, void* stream);
+
+/*
+ * Candidate counts of the exact census (the index spaces hm_count_exact
+ * walks), written to host `totals`: order 3 -> {T3, W}: 3-hyperedges and
+ * pair-neighbour pairs sum_v C(d2(v), 2); order 4 -> {Q, TX, S, P}:
+ * 4-hyperedges, sum over 3-hyperedges e of sum_{x in e} (d2(x) + t3(x)),
+ * sum_v C(d2(v), 3), sum over pairs (u,v) of (d2(u)-1)(d2(v)-1); d2 = pair
+ * degree, t3 = number of 3-hyperedges through the node. Synchronous.
+ */
+hm_status hm_work_totals(hm_graph* g, int order, uint64_t* totals, void* stream);
+
+/*
+ * End-to-end exact census from HOST buffers: copies the hyperedge list to the
+ * device, builds the graph with max_order = order, counts (as hm_count_exact)
+ * and copies the histogram back, all on `stream`; synchronous. Device memory
+ * is taken and released inside the call.
+ *   h_members, h_offsets  host arrays laid out as for hm_build
+ *   h_hist                host uint64[hm_num_classes(order)], overwritten
+ * Errors as hm_build and hm_count_exact.
+ */
+hm_status hm_count_exact_host(const int32_t* h_members, const int64_t* h_offsets,
+                              int64_t num_hyperedges, int32_t num_nodes, int order,
+                              uint64_t* h_hist, void* stream);
+
+/*
+ * Kernel timing trace (no counterpart in the paper; instrumentation). While
+ * enabled, every census kernel launch is bracketed by CUDA events recorded on
+ * its launching stream. hm_trace_read waits for the recorded events, writes
+ * up to max_entries (name, milliseconds) pairs -- names as NUL-terminated
+ * strings in rows of name_len bytes of `names` (may be NULL), times in `ms`
+ * (may be NULL) -- sets *count, and clears the trace.
+ */
+hm_status hm_trace_enable(int on);
+/* Number of kernels the library has launched in this process (instrumentation). */
+uint64_t hm_launch_count(void);
+hm_status hm_trace_read(int max_entries, char* names, int name_len, float* ms, int* count);
+
+/* Release a graph and its device memory. NULL is allowed. */
+void hm_free(hm_graph* g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HM_H_ */

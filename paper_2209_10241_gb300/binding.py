@@ -1,0 +1,212 @@
+"""Thin ctypes binding of libhm.so (argument marshalling only).
+
+Every computation runs in the CUDA library; this module passes torch device
+pointers and the current CUDA stream to the C ABI declared in include/hm.h.
+If the library is missing, loading fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhm.so")
+_lib = None
+
+HM_OK = 0
+_STATUS = {1: "HM_EINVAL", 2: "HM_ENOMEM", 3: "HM_ECUDA", 4: "HM_ETABLEFULL",
+           5: "HM_ETIMEOUT", 6: "HM_EUNSUPPORTED"}
+
+
+class HMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_vp = ctypes.c_void_p
+_SIGS = {
+    "hm_last_error": (ctypes.c_char_p, []),
+    "hm_version": (ctypes.c_char_p, []),
+    "hm_num_classes": (ctypes.c_int, [ctypes.c_int]),
+    "hm_class_info": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
+    "hm_class_of_mask": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32, _vp]),
+    "hm_build": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int, _vp,
+                                ctypes.POINTER(_vp)]),
+    "hm_graph_info": (ctypes.c_int, [_vp, _vp]),
+    "hm_graph_edges": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "hm_count_exact": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "hm_count_sampled": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_uint64, ctypes.c_uint64,
+                                        _vp, _vp, _vp, _vp]),
+    "hm_count_exact_host": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int,
+                                           _vp, _vp]),
+    "hm_work_totals": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "hm_trace_enable": (ctypes.c_int, [ctypes.c_int]),
+    "hm_launch_count": (ctypes.c_uint64, []),
+    "hm_trace_read": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]),
+    "hm_free": (None, [_vp]),
+}
+# declared in include/hm.h; checked by the ABI test
+EXPORTS = tuple(_SIGS)
+
+
+def load(path: str = LIB_PATH):
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
+                               "`python -m paper_2209_10241_gb300.build` (no CPU fallback exists)")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            if hasattr(L, name):
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != HM_OK:
+        raise HMError(status, load().hm_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def num_classes(order: int) -> int:
+    return int(load().hm_num_classes(order))
+
+
+def class_info(order: int, cls: int):
+    m, a, b = ctypes.c_uint32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().hm_class_info(order, cls, ctypes.byref(m), ctypes.byref(a), ctypes.byref(b)))
+    return m.value, a.value, b.value
+
+
+def class_of_mask(order: int, mask: int) -> int:
+    c = ctypes.c_int32()
+    _check(load().hm_class_of_mask(order, mask, ctypes.byref(c)))
+    return c.value
+
+
+class Graph:
+    """A hypergraph built on the current CUDA device (hm_build)."""
+
+    def __init__(self, handle, kmax: int):
+        self._h = handle
+        self.kmax = kmax
+        counts = (ctypes.c_int64 * 8)()
+        _check(load().hm_graph_info(self._h, counts))
+        self.counts = list(counts)
+        self.num_nodes = self.counts[0]
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.hm_free(self._h)
+            self._h = None
+
+    def free(self):
+        self.__del__()
+
+    def count(self, s: int) -> int:
+        return int(self.counts[s])
+
+    def edges(self, s: int, stream=None) -> torch.Tensor:
+        out = torch.empty((self.count(s), s), dtype=torch.int32, device="cuda")
+        _check(load().hm_graph_edges(self._h, s, _dptr(out), _stream(stream)))
+        return out
+
+
+def build(members: torch.Tensor, offsets: torch.Tensor, num_nodes: int, max_order: int = 4,
+          stream=None) -> Graph:
+    """hm_build on device tensors (int32 members, int64 offsets)."""
+    assert members.is_cuda and offsets.is_cuda
+    members = members.contiguous().to(torch.int32)
+    offsets = offsets.contiguous().to(torch.int64)
+    h = ctypes.c_void_p()
+    _check(load().hm_build(_dptr(members), _dptr(offsets), offsets.numel() - 1, int(num_nodes),
+                           int(max_order), _stream(stream), ctypes.byref(h)))
+    return Graph(h, max_order)
+
+
+def count_exact(g: Graph, order: int, out: torch.Tensor = None, stream=None) -> torch.Tensor:
+    """hm_count_exact; returns an int64 device tensor holding the uint64 counts."""
+    if out is None:
+        out = torch.empty(max(1, num_classes(order)), dtype=torch.int64, device="cuda")
+    _check(load().hm_count_exact(g._h, order, _dptr(out), _stream(stream)))
+    return out
+
+
+def count_sampled(g: Graph, order: int, samples=None, total: int = 0, seed: int = 0,
+                  q: torch.Tensor = None, stream=None):
+    """hm_count_sampled; returns (estimates float64, raw int64[2*ncls]) device tensors."""
+    nc = max(1, num_classes(order))
+    est = torch.empty(nc, dtype=torch.float64, device="cuda")
+    raw = torch.empty(2 * nc, dtype=torch.int64, device="cuda")
+    sp = None
+    if samples is not None:
+        arr = (ctypes.c_uint64 * 5)()
+        for s in range(2, min(order, 4) + 1):
+            arr[s] = int(samples[s])
+        sp = arr
+    _check(load().hm_count_sampled(g._h, order, sp, int(total), int(seed) & (2**64 - 1),
+                                   _dptr(q), _dptr(est), _dptr(raw), _stream(stream)))
+    return est, raw
+
+
+def from_host(h, max_order: int = 4, device="cuda") -> Graph:
+    """Copy a synth.Hypergraph to the device and build it."""
+    mem = torch.from_numpy(h.members).to(device)
+    off = torch.from_numpy(h.offsets).to(device)
+    return build(mem, off, h.num_nodes, max_order)
+
+
+def count_exact_host(members, offsets, num_nodes: int, order: int, out=None, stream=None):
+    """hm_count_exact_host on host (ideally pinned) tensors; returns a host int64 tensor."""
+    assert not members.is_cuda and not offsets.is_cuda
+    if out is None:
+        out = torch.empty(num_classes(order), dtype=torch.int64)
+    _check(load().hm_count_exact_host(_dptr(members), _dptr(offsets), offsets.numel() - 1,
+                                      int(num_nodes), int(order), _dptr(out), _stream(stream)))
+    return out
+
+
+def trace_enable(on: bool = True):
+    _check(load().hm_trace_enable(1 if on else 0))
+
+
+def trace_read(max_entries: int = 4096):
+    """[(kernel name, ms)] recorded since the last read."""
+    name_len = 32
+    names = ctypes.create_string_buffer(max_entries * name_len)
+    ms = (ctypes.c_float * max_entries)()
+    cnt = ctypes.c_int()
+    _check(load().hm_trace_read(max_entries, names, name_len, ms, ctypes.byref(cnt)))
+    raw = names.raw
+    return [(raw[i * name_len:(i + 1) * name_len].split(b"\0")[0].decode(), float(ms[i]))
+            for i in range(cnt.value)]
+
+
+FAMILIES = {3: ("census_T3", "census_W"), 4: ("census_Q", "census_TX", "census_S", "census_P")}
+
+
+def work_totals(g: Graph, order: int, stream=None) -> dict:
+    """Candidates per family of the exact census {kernel name: count}."""
+    arr = (ctypes.c_uint64 * 4)()
+    _check(load().hm_work_totals(g._h, order, arr, _stream(stream)))
+    return {name: int(arr[i]) for i, name in enumerate(FAMILIES[order])}
+
+
+def launch_count() -> int:
+    """Kernels launched by libhm.so so far in this process."""
+    return int(load().hm_launch_count())

@@ -1,0 +1,510 @@
+// Graph ingest on the device: normalisation of hyperedges into sets (Def. 1),
+// deduplication (E is a set), the per-size hyperedge hash sets that make the
+// fill-in of Sec. 4.3 a constant number of probes, and the CSR neighbourhoods
+// the candidate generators walk.
+#include <cstdlib>
+#include <mutex>
+
+#include "hm_internal.cuh"
+
+namespace hm {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+
+constexpr int T256 = 256;
+
+unsigned grid1d(int64_t n, int threads = T256) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 152 * 64) b = 152 * 64;
+  return (unsigned)b;
+}
+
+int bits_for(int64_t maxval) {
+  int b = 1;
+  while (b < 62 && (1ll << b) <= maxval) ++b;
+  return b;
+}
+
+enum { ERR_RANGE = 1, ERR_OFFSETS = 2, ERR_TABLE = 4 };
+
+// One thread per input hyperedge: the set of its members (sorted, repeats
+// collapsed) as long as it has at most kmax distinct members. WRITE=false
+// only counts per size; WRITE=true emits the packed sort key of each kept
+// hyperedge (members concatenated with b bits each, most significant first).
+template <bool WRITE>
+__global__ void k_normalize(const int32_t* __restrict__ mem, const int64_t* __restrict__ off,
+                            int64_t m, int32_t n, int kmax, int b,
+                            unsigned long long* __restrict__ cnt, int* __restrict__ err,
+                            uint64_t* __restrict__ c2, uint64_t* __restrict__ c3hi,
+                            uint64_t* __restrict__ c3lo, uint64_t* __restrict__ c4hi,
+                            uint64_t* __restrict__ c4lo) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s0 = off[j], s1 = off[j + 1];
+    if (s1 < s0 || s0 < 0) {
+      atomicOr(err, ERR_OFFSETS);
+      continue;
+    }
+    int32_t v[5] = {0, 0, 0, 0, 0};
+    int cntd = 0;
+    bool big = false, bad = false;
+    for (int64_t p = s0; p < s1; ++p) {
+      const int32_t x = mem[p];
+      if (x < 0 || x >= n) {
+        bad = true;
+        continue;
+      }
+      if (big) continue;
+      bool present = false;
+      int pos = 0;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        present |= (i < cntd && v[i] == x);
+        pos += (i < cntd && v[i] < x) ? 1 : 0;
+      }
+      if (present) continue;
+#pragma unroll
+      for (int i = 4; i > 0; --i)
+        if (i > pos && i <= cntd) v[i] = v[i - 1];
+#pragma unroll
+      for (int i = 0; i < 5; ++i)
+        if (i == pos) v[i] = x;
+      ++cntd;
+      if (cntd > kmax) big = true;
+    }
+    if (bad) {
+      atomicOr(err, ERR_RANGE);
+      continue;
+    }
+    if (big) {
+      if (!WRITE) atomicAdd(&cnt[kmax + 1], 1ull);
+      continue;
+    }
+    if (cntd < 2) continue;
+    const unsigned long long slot = atomicAdd(&cnt[cntd], 1ull);
+    if (WRITE) {
+      unsigned __int128 key = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (i < cntd) key = (key << b) | (uint32_t)v[i];
+      if (cntd == 2) {
+        c2[slot] = (uint64_t)key;
+      } else if (cntd == 3) {
+        c3lo[slot] = (uint64_t)key;
+        c3hi[slot] = (uint64_t)(key >> 64);
+      } else {
+        c4lo[slot] = (uint64_t)key;
+        c4hi[slot] = (uint64_t)(key >> 64);
+      }
+    }
+  }
+}
+
+__global__ void k_unpack2(const uint64_t* __restrict__ c, int64_t m, int b, uint64_t* __restrict__ e2) {
+  const uint64_t mask = (1ull << b) - 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t k = c[i];
+    e2[i] = ((k >> b) << 32) | (k & mask);
+  }
+}
+
+__global__ void k_unpack34(const uint64_t* __restrict__ hi, const uint64_t* __restrict__ lo,
+                           int64_t m, int s, int b, int4* __restrict__ e) {
+  const uint64_t mask = (1ull << b) - 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    unsigned __int128 key = ((unsigned __int128)hi[i] << 64) | lo[i];
+    int32_t v[4] = {-1, -1, -1, -1};
+    for (int j = s - 1; j >= 0; --j) {
+      v[j] = (int32_t)((uint64_t)key & mask);
+      key >>= b;
+    }
+    e[i] = make_int4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+__global__ void k_insert2(const uint64_t* __restrict__ e2, int64_t m, uint64_t* table,
+                          uint64_t mask, int* err) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t key = e2[i];
+    uint64_t slot = hash_pair(key) & mask;
+    bool done = false;
+    for (uint64_t it = 0; it <= mask; ++it) {
+      unsigned long long old =
+          atomicCAS((unsigned long long*)(table + slot), (unsigned long long)EMPTY64,
+                    (unsigned long long)key);
+      if (old == EMPTY64) {
+        done = true;
+        break;
+      }
+      slot = (slot + 1) & mask;
+    }
+    if (!done) atomicOr(err, ERR_TABLE);
+  }
+}
+
+// Keys are distinct, so a slot is claimed by a CAS on its first 8 bytes and
+// the second half is then stored plainly; probes run in later kernels.
+__global__ void k_insert4(const int4* __restrict__ e, int64_t m, int4* table, uint64_t mask,
+                          int* err) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int4 k = e[i];
+    uint64_t slot = hash_tuple(k.x, k.y, k.z, k.w) & mask;
+    const unsigned long long first = (uint64_t)(uint32_t)k.x | ((uint64_t)(uint32_t)k.y << 32);
+    const unsigned long long second = (uint64_t)(uint32_t)k.z | ((uint64_t)(uint32_t)k.w << 32);
+    bool done = false;
+    for (uint64_t it = 0; it <= mask; ++it) {
+      unsigned long long* w = (unsigned long long*)(table + slot);
+      if (atomicCAS(w, (unsigned long long)EMPTY64, first) == EMPTY64) {
+        w[1] = second;
+        done = true;
+        break;
+      }
+      slot = (slot + 1) & mask;
+    }
+    if (!done) atomicOr(err, ERR_TABLE);
+  }
+}
+
+__global__ void k_directed_pairs(const uint64_t* __restrict__ e2, int64_t m, int b,
+                                 uint64_t* __restrict__ keys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t u = e2[i] >> 32, v = e2[i] & 0xFFFFFFFFull;
+    keys[2 * i] = (u << b) | v;
+    keys[2 * i + 1] = (v << b) | u;
+  }
+}
+
+__global__ void k_low_bits(const uint64_t* __restrict__ keys, int64_t m, int b,
+                           int32_t* __restrict__ out) {
+  const uint64_t mask = (1ull << b) - 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int32_t)(keys[i] & mask);
+}
+
+__global__ void k_triple_incidence(const int4* __restrict__ e3, int64_t m, int tb,
+                                   uint64_t* __restrict__ keys) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int4 e = e3[t];
+    keys[3 * t] = ((uint64_t)e.x << tb) | (uint64_t)t;
+    keys[3 * t + 1] = ((uint64_t)e.y << tb) | (uint64_t)t;
+    keys[3 * t + 2] = ((uint64_t)e.z << tb) | (uint64_t)t;
+  }
+}
+
+__device__ int32_t find_pos(const int32_t* __restrict__ a, int64_t lo, int64_t hi, int32_t x) {
+  int64_t l = lo, h = hi;
+  while (l < h) {
+    int64_t mid = (l + h) >> 1;
+    if (a[mid] < x)
+      l = mid + 1;
+    else
+      h = mid;
+  }
+  return (int32_t)(l - lo);
+}
+
+__global__ void k_pairpos(const uint64_t* __restrict__ e2, int64_t m, const int64_t* __restrict__ off2,
+                          const int32_t* __restrict__ adj2, int2* __restrict__ pos) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int32_t u = (int32_t)(e2[p] >> 32), v = (int32_t)(e2[p] & 0xFFFFFFFFull);
+    pos[p] = make_int2(find_pos(adj2, off2[u], off2[u + 1], v),
+                       find_pos(adj2, off2[v], off2[v + 1], u));
+  }
+}
+
+__global__ void k_bitmap(const uint64_t* __restrict__ e2, int64_t m, int32_t bw,
+                         uint32_t* __restrict__ bits) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int32_t u = (int32_t)(e2[p] >> 32), v = (int32_t)(e2[p] & 0xFFFFFFFFull);
+    atomicOr(bits + (size_t)u * bw + (v >> 5), 1u << (v & 31));
+    atomicOr(bits + (size_t)v * bw + (u >> 5), 1u << (u & 31));
+  }
+}
+
+__global__ void k_max_degree(const int64_t* __restrict__ off, int32_t n, int* out) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    atomicMax(out, (int)(off[v + 1] - off[v]));
+}
+
+__global__ void k_edges_out(const uint64_t* __restrict__ e2, const int4* __restrict__ e34,
+                            int64_t m, int s, int32_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (s == 2) {
+      out[2 * i] = (int32_t)(e2[i] >> 32);
+      out[2 * i + 1] = (int32_t)(e2[i] & 0xFFFFFFFFull);
+    } else {
+      int4 e = e34[i];
+      out[s * i] = e.x;
+      out[s * i + 1] = e.y;
+      out[s * i + 2] = e.z;
+      if (s == 4) out[s * i + 3] = e.w;
+    }
+  }
+}
+
+uint64_t table_capacity(int64_t m) {
+  uint64_t c = 16;
+  while (c < (uint64_t)(2 * m)) c <<= 1;
+  return c;
+}
+
+bool use_bitmap(int64_t n) {
+  const char* env = std::getenv("HM_PAIR_BITMAP");
+  if (env && env[0] == '0') return false;
+  const int64_t bytes = n * ((n + 31) / 32) * 4;
+  if (env && env[0] == '1') return bytes <= (1ll << 31);
+  return bytes <= (32ll << 20);
+}
+
+template <class T>
+T* keep(hm_graph* g, T* p) {
+  if (p) g->owned.push_back((void*)p);
+  return p;
+}
+
+}  // namespace
+
+void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets, int64_t m,
+                 int32_t n, int kmax, cudaStream_t s) {
+  g->n = n;
+  g->kmax = kmax;
+  g->m_in = m;
+  HM_CUDA(cudaGetDevice(&g->device));
+  const int b = bits_for((int64_t)n - 1);
+  g->bits = b;
+
+  DBuf<unsigned long long> cnt(8, s), cnt2(8, s);
+  DBuf<int> err(1, s);
+  HM_CUDA(cudaMemsetAsync(cnt.p, 0, 8 * sizeof(unsigned long long), s));
+  HM_CUDA(cudaMemsetAsync(cnt2.p, 0, 8 * sizeof(unsigned long long), s));
+  HM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+  if (m > 0) {
+    k_normalize<false><<<grid1d(m), T256, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt.p,
+                                                  err.p, nullptr, nullptr, nullptr, nullptr,
+                                                  nullptr);
+    HM_KCHECK();
+  }
+  unsigned long long hc[8];
+  int herr = 0;
+  HM_CUDA(cudaMemcpyAsync(hc, cnt.p, sizeof hc, cudaMemcpyDeviceToHost, s));
+  HM_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof herr, cudaMemcpyDeviceToHost, s));
+  HM_CUDA(cudaStreamSynchronize(s));
+  HM_CHECK(!(herr & ERR_OFFSETS), HM_EINVAL, "offsets are negative or not non-decreasing");
+  HM_CHECK(!(herr & ERR_RANGE), HM_EINVAL, "a member lies outside [0, num_nodes)");
+  g->counts[0] = n;
+  g->counts[1] = m;
+  g->counts[kmax + 1] = (int64_t)hc[kmax + 1];
+
+  DBuf<uint64_t> c2(hc[2], s), c3hi(kmax >= 3 ? hc[3] : 0, s), c3lo(kmax >= 3 ? hc[3] : 0, s),
+      c4hi(kmax >= 4 ? hc[4] : 0, s), c4lo(kmax >= 4 ? hc[4] : 0, s);
+  if (m > 0) {
+    k_normalize<true><<<grid1d(m), T256, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt2.p,
+                                                 err.p, c2.p, c3hi.p, c3lo.p, c4hi.p, c4lo.p);
+    HM_KCHECK();
+  }
+  // sort + unique per size: the ascending order of E_s
+  radix_sort_u64(c2.p, nullptr, (int64_t)hc[2], 2 * b, s);
+  const int64_t m2 = unique_sorted(nullptr, c2.p, (int64_t)hc[2], s);
+  int64_t m3 = 0, m4 = 0;
+  if (kmax >= 3) {
+    int bits3 = 3 * b;
+    radix_sort_u128(c3hi.p, c3lo.p, (int64_t)hc[3], bits3 > 64 ? bits3 - 64 : 0,
+                    bits3 > 64 ? 64 : bits3, s);
+    m3 = unique_sorted(c3hi.p, c3lo.p, (int64_t)hc[3], s);
+  }
+  if (kmax >= 4) {
+    int bits4 = 4 * b;
+    radix_sort_u128(c4hi.p, c4lo.p, (int64_t)hc[4], bits4 > 64 ? bits4 - 64 : 0,
+                    bits4 > 64 ? 64 : bits4, s);
+    m4 = unique_sorted(c4hi.p, c4lo.p, (int64_t)hc[4], s);
+  }
+  g->counts[2] = m2;
+  if (kmax >= 3) g->counts[3] = m3;
+  if (kmax >= 4) g->counts[4] = m4;
+
+  g->e2 = keep(g, dalloc<uint64_t>(m2));
+  if (m2) {
+    k_unpack2<<<grid1d(m2), T256, 0, s>>>(c2.p, m2, b, g->e2);
+    HM_KCHECK();
+  }
+  if (m3) {
+    g->e3 = keep(g, dalloc<int4>(m3));
+    k_unpack34<<<grid1d(m3), T256, 0, s>>>(c3hi.p, c3lo.p, m3, 3, b, g->e3);
+    HM_KCHECK();
+  }
+  if (m4) {
+    g->e4 = keep(g, dalloc<int4>(m4));
+    k_unpack34<<<grid1d(m4), T256, 0, s>>>(c4hi.p, c4lo.p, m4, 4, b, g->e4);
+    HM_KCHECK();
+  }
+  HM_CUDA(cudaGetLastError());
+  c2.release();
+  c3hi.release();
+  c3lo.release();
+  c4hi.release();
+  c4lo.release();
+
+  // hash sets (load <= 0.5)
+  {
+    uint64_t cap = table_capacity(m2);
+    g->h2 = keep(g, dalloc<uint64_t>(cap));
+    g->h2_mask = cap - 1;
+    HM_CUDA(cudaMemsetAsync(g->h2, 0xFF, cap * sizeof(uint64_t), s));
+    if (m2) {
+      k_insert2<<<grid1d(m2), T256, 0, s>>>(g->e2, m2, g->h2, g->h2_mask, err.p);
+      HM_KCHECK();
+    }
+  }
+  if (m3) {
+    uint64_t cap = table_capacity(m3);
+    g->h3 = keep(g, dalloc<int4>(cap));
+    g->h3_mask = cap - 1;
+    HM_CUDA(cudaMemsetAsync(g->h3, 0xFF, cap * sizeof(int4), s));
+    k_insert4<<<grid1d(m3), T256, 0, s>>>(g->e3, m3, g->h3, g->h3_mask, err.p);
+    HM_KCHECK();
+  }
+  if (m4) {
+    uint64_t cap = table_capacity(m4);
+    g->h4 = keep(g, dalloc<int4>(cap));
+    g->h4_mask = cap - 1;
+    HM_CUDA(cudaMemsetAsync(g->h4, 0xFF, cap * sizeof(int4), s));
+    k_insert4<<<grid1d(m4), T256, 0, s>>>(g->e4, m4, g->h4, g->h4_mask, err.p);
+    HM_KCHECK();
+  }
+  HM_CUDA(cudaGetLastError());
+
+  // CSR of pair neighbours, sorted
+  g->off2 = keep(g, dalloc<int64_t>((size_t)n + 1));
+  g->adj2 = keep(g, dalloc<int32_t>(2 * m2));
+  {
+    DBuf<uint64_t> keys(2 * m2, s);
+    if (m2) {
+      k_directed_pairs<<<grid1d(m2), T256, 0, s>>>(g->e2, m2, b, keys.p);
+      HM_KCHECK();
+      radix_sort_u64(keys.p, nullptr, 2 * m2, 2 * b, s);
+      k_low_bits<<<grid1d(2 * m2), T256, 0, s>>>(keys.p, 2 * m2, b, g->adj2);
+      HM_KCHECK();
+    }
+    csr_offsets(keys.p, 2 * m2, b, n, g->off2, s);
+  }
+  // CSR of triple incidence, ascending triple index
+  g->off3 = keep(g, dalloc<int64_t>((size_t)n + 1));
+  if (m3) {
+    g->inc3 = keep(g, dalloc<int32_t>(3 * m3));
+    const int tb = bits_for(m3);
+    DBuf<uint64_t> keys(3 * m3, s);
+    k_triple_incidence<<<grid1d(m3), T256, 0, s>>>(g->e3, m3, tb, keys.p);
+    HM_KCHECK();
+    radix_sort_u64(keys.p, nullptr, 3 * m3, b + tb, s);
+    k_low_bits<<<grid1d(3 * m3), T256, 0, s>>>(keys.p, 3 * m3, tb, g->inc3);
+    HM_KCHECK();
+    csr_offsets(keys.p, 3 * m3, tb, n, g->off3, s);
+  } else {
+    HM_CUDA(cudaMemsetAsync(g->off3, 0, ((size_t)n + 1) * sizeof(int64_t), s));
+  }
+  if (m2) {
+    g->pairpos = keep(g, dalloc<int2>(m2));
+    k_pairpos<<<grid1d(m2), T256, 0, s>>>(g->e2, m2, g->off2, g->adj2, g->pairpos);
+    HM_KCHECK();
+  }
+  if (use_bitmap(n)) {
+    g->bwords = (n + 31) / 32;
+    size_t words = (size_t)n * g->bwords;
+    g->bits2 = keep(g, dalloc<uint32_t>(words));
+    HM_CUDA(cudaMemsetAsync(g->bits2, 0, words * sizeof(uint32_t), s));
+    if (m2) {
+      k_bitmap<<<grid1d(m2), T256, 0, s>>>(g->e2, m2, g->bwords, g->bits2);
+      HM_KCHECK();
+    }
+  }
+  {
+    DBuf<int> mx(1, s);
+    HM_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(int), s));
+    k_max_degree<<<grid1d(n), T256, 0, s>>>(g->off2, n, mx.p);
+    HM_KCHECK();
+    HM_CUDA(cudaMemcpyAsync(&g->max_d2, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  }
+  HM_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof herr, cudaMemcpyDeviceToHost, s));
+  HM_CUDA(cudaStreamSynchronize(s));
+  HM_CHECK(!(herr & ERR_TABLE), HM_ETABLEFULL, "hash insertion exceeded its probe bound");
+}
+
+void free_graph(hm_graph* g) {
+  if (!g) return;
+  for (void* p : g->owned) cudaFree(p);
+  for (auto* sp : {&g->W, &g->S, &g->P, &g->TX})
+    if (sp->ws) cudaFree(sp->ws);
+  delete g;
+}
+
+}  // namespace hm
+
+extern "C" {
+
+const char* hm_last_error(void) { return hm::g_last_error.c_str(); }
+
+const char* hm_version(void) { return "hm 0.1 (sm_103a)"; }
+
+hm_status hm_build(const int32_t* d_members, const int64_t* d_offsets, int64_t num_hyperedges,
+                   int32_t num_nodes, int max_order, void* stream, hm_graph** out) {
+  hm_graph* g = nullptr;
+  hm_status st = hm::guarded([&] {
+    HM_CHECK(out != nullptr, HM_EINVAL, "out is NULL");
+    *out = nullptr;
+    HM_CHECK(max_order == 3 || max_order == 4, HM_EINVAL, "max_order must be 3 or 4");
+    HM_CHECK(num_nodes >= 1, HM_EINVAL, "num_nodes must be >= 1");
+    HM_CHECK(num_hyperedges >= 0 && num_hyperedges < (1ll << 31), HM_EINVAL,
+             "num_hyperedges must be in [0, 2^31)");
+    HM_CHECK(num_hyperedges == 0 || (d_members && d_offsets), HM_EINVAL,
+             "members/offsets are NULL");
+    g = new hm_graph;
+    hm::build_graph(g, d_members, d_offsets, num_hyperedges, num_nodes, max_order,
+                    (cudaStream_t)stream);
+    *out = g;
+  });
+  if (st != HM_OK && g) {
+    std::string msg = hm_last_error();
+    hm::free_graph(g);
+    hm::set_last_error(msg);
+  }
+  return st;
+}
+
+hm_status hm_graph_info(const hm_graph* g, int64_t* counts) {
+  return hm::guarded([&] {
+    HM_CHECK(g && counts, HM_EINVAL, "NULL argument");
+    for (int i = 0; i < 8; ++i) counts[i] = g->counts[i];
+  });
+}
+
+hm_status hm_graph_edges(const hm_graph* g, int s, int32_t* d_out, void* stream) {
+  return hm::guarded([&] {
+    HM_CHECK(g, HM_EINVAL, "NULL graph");
+    HM_CHECK(s >= 2 && s <= g->kmax, HM_EINVAL, "size must be in [2, max_order]");
+    int64_t m = g->counts[s];
+    if (m == 0) return;
+    HM_CHECK(d_out, HM_EINVAL, "NULL output");
+    cudaStream_t st = (cudaStream_t)stream;
+    hm::k_edges_out<<<hm::grid1d(m), 256, 0, st>>>(g->e2, s == 3 ? g->e3 : g->e4, m, s, d_out);
+    HM_KCHECK();
+  });
+}
+
+void hm_free(hm_graph* g) { hm::free_graph(g); }
+
+}  // extern "C"

@@ -1,0 +1,315 @@
+// Exact census of higher-order motifs of order 3 and 4 (problem statement,
+// Sec. 3; efficient exact algorithms, Sec. 4.2, Alg. 2 and Alg. 3).
+//
+// Alg. 2/3 enumerate candidate node sets from the hyperedges (largest size
+// first) and drop repeats with a global "visited" set. Here every connected
+// k-node set is generated by exactly one (anchor, item) pair of one family,
+// decided by a local canonical-generation rule, so no visited set is needed
+// and all families run as flat data-parallel index spaces:
+//
+//   k = 3  T3  anchor: a 3-hyperedge; the set is the hyperedge (Alg. 2 loop 1)
+//          W   anchor: node v, items: pairs x < y of pair-neighbours of v; the
+//              set {v,x,y} with no 3-hyperedge (Alg. 2 loop 2); kept when v
+//              is the smallest node of induced pair-degree 2
+//   k = 4  Q   anchor: a 4-hyperedge (Alg. 3 loop 1)
+//          TX  anchor: a 3-hyperedge e; items: hyperedges h of size 2 or 3
+//              through a member x of e adding one node d (Alg. 3 loop 2); kept
+//              when the set has no 4-hyperedge, e is its smallest 3-hyperedge,
+//              h its smallest hyperedge containing d and x = min(h ∩ e)
+//          S   anchor: node v, items: triples of pair-neighbours of v; sets
+//              with pairs only (Alg. 3 loop 3) holding a node of induced
+//              degree 3; kept when v is the smallest such node
+//          P   anchor: pair (u,v), items: x in N2(u), y in N2(v); pairs-only
+//              sets whose induced degrees are all <= 2 (paths and 4-cycles);
+//              kept when (u,v) is the smallest pair whose ends have degree 2
+// Hyperedge order for "smallest": size, then the sorted member tuple.
+//
+// Each candidate's induced sub-hypergraph is filled in by probing its
+// subsets of size 2..k (Sec. 4.3) and classified by one lookup of the
+// labelled mask in the class table; counts are aggregated per warp
+// (__match_any_sync) into shared-memory bins and flushed once per block.
+#include <cmath>
+
+#include "families.cuh"
+
+namespace hm {
+namespace {
+
+using namespace fam;
+
+template <class F>
+__global__ void __launch_bounds__(CENSUS_THREADS)
+    k_census(const DevGraph g, const F fam, const uint64_t* __restrict__ ws, int64_t A,
+             uint64_t total, const uint8_t* __restrict__ lut_g, int nmask, int ncls,
+             unsigned long long* __restrict__ hist) {
+  __shared__ unsigned long long bins[176];
+  __shared__ uint8_t lut[2048];
+  for (int i = threadIdx.x; i < nmask; i += blockDim.x) lut[i] = lut_g[i];
+  for (int i = threadIdx.x; i < ncls; i += blockDim.x) bins[i] = 0;
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  const uint64_t nchunks = (total + CHUNK - 1) / CHUNK;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t cb = warp * 32; cb < nchunks; cb += nwarps * 32) {
+    const uint64_t g0 = (cb + lane) * CHUNK;
+    const uint64_t g1 = min(g0 + CHUNK, total);
+    typename F::State st;
+    int64_t a = 0;
+    uint64_t r = 0, wa = 0;
+    if (!F::kDirect && g0 < total) {
+      a = anchor_of(ws, A, g0);
+      r = g0 - ws[a];
+      wa = ws[a + 1] - ws[a];
+      fam.begin(g, a, r, st);
+    }
+    for (int it = 0; it < CHUNK; ++it) {
+      const uint64_t gi = g0 + it;
+      int cls = -1;
+      if (gi < g1) {
+        uint32_t mask = 0;
+        bool ok;
+        if (F::kDirect) {
+          ok = fam.item(g, (int64_t)gi, st, mask);
+        } else {
+          if (r == wa) {
+            do {
+              ++a;
+            } while (ws[a + 1] == ws[a]);
+            r = 0;
+            wa = ws[a + 1] - ws[a];
+            fam.begin(g, a, 0, st);
+          }
+          ok = fam.item(g, a, st, mask);
+          ++r;
+          fam.next(st);
+        }
+        if (ok) {
+          const uint8_t c = lut[mask];
+          cls = c == 0xFF ? -1 : (int)c;
+        }
+      }
+      const unsigned peers = __match_any_sync(0xffffffffu, cls);
+      if (cls >= 0 && lane == __ffs(peers) - 1)
+        atomicAdd(&bins[cls], (unsigned long long)__popc(peers));
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < ncls; i += blockDim.x)
+    if (bins[i]) atomicAdd(&hist[i], bins[i]);
+}
+
+// ---------------------------------------------------------------- work spaces
+__global__ void k_ws_nodes(const int64_t* __restrict__ off2, int32_t n, int choose,
+                           uint64_t* __restrict__ w) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t d = (uint64_t)(off2[v + 1] - off2[v]);
+    w[v] = choose == 2 ? choose2(d) : choose3(d);
+  }
+}
+
+__global__ void k_ws_pairs(const uint64_t* __restrict__ e2, int64_t m, const int64_t* __restrict__ off2,
+                           uint64_t* __restrict__ w) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = (int32_t)(e2[p] >> 32), v = (int32_t)(e2[p] & 0xFFFFFFFFull);
+    const uint64_t du = (uint64_t)(off2[u + 1] - off2[u]), dv = (uint64_t)(off2[v + 1] - off2[v]);
+    w[p] = (du - 1) * (dv - 1);
+  }
+}
+
+__global__ void k_ws_triples(const int4* __restrict__ e3, int64_t m, const int64_t* __restrict__ off2,
+                             const int64_t* __restrict__ off3, uint64_t* __restrict__ w) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int4 e = e3[t];
+    uint64_t s = 0;
+    const int32_t xs[3] = {e.x, e.y, e.z};
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      s += (uint64_t)(off2[xs[j] + 1] - off2[xs[j]]) + (uint64_t)(off3[xs[j] + 1] - off3[xs[j]]);
+    w[t] = s;
+  }
+}
+
+unsigned grid1d(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > 152 * 64) b = 152 * 64;
+  return (unsigned)b;
+}
+
+void ensure_space(hm_graph* g, hm_graph::Space& sp, char fam, cudaStream_t s) {
+  if (sp.ready) return;
+  int64_t A = 0;
+  if (fam == 'W' || fam == 'S') A = g->n;
+  if (fam == 'P') A = g->counts[2];
+  if (fam == 'X') A = g->kmax >= 3 ? g->counts[3] : 0;
+  DBuf<uint64_t> w(A, s);
+  uint64_t* ws = dalloc<uint64_t>((size_t)A + 1);
+  try {
+    if (A > 0) {
+      if (fam == 'W') {
+        k_ws_nodes<<<grid1d(A), 256, 0, s>>>(g->off2, g->n, 2, w.p);
+        HM_KCHECK();
+      }
+      if (fam == 'S') {
+        k_ws_nodes<<<grid1d(A), 256, 0, s>>>(g->off2, g->n, 3, w.p);
+        HM_KCHECK();
+      }
+      if (fam == 'P') {
+        k_ws_pairs<<<grid1d(A), 256, 0, s>>>(g->e2, A, g->off2, w.p);
+        HM_KCHECK();
+      }
+      if (fam == 'X') {
+        k_ws_triples<<<grid1d(A), 256, 0, s>>>(g->e3, A, g->off2, g->off3, w.p);
+        HM_KCHECK();
+      }
+    }
+    scan_exclusive_u64(w.p, ws, A, s);
+    HM_CUDA(cudaMemcpyAsync(&sp.total, ws + A, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    cudaFree(ws);
+    throw;
+  }
+  sp.ws = ws;
+  sp.anchors = A;
+  sp.ready = true;
+}
+
+int census_blocks(const void* kernel, uint64_t total) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    HM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  int per_sm = 0;
+  HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, CENSUS_THREADS, 0));
+  if (per_sm < 1) per_sm = 1;
+  const uint64_t chunks = (total + CHUNK - 1) / CHUNK;
+  const uint64_t need = (chunks + CENSUS_THREADS - 1) / CENSUS_THREADS;
+  uint64_t blocks = (uint64_t)sms * per_sm;
+  if (need < blocks) blocks = need;
+  return (int)(blocks < 1 ? 1 : blocks);
+}
+
+template <class F>
+void launch_family(const hm_graph* g, const F& fam, const hm_graph::Space* sp, uint64_t total,
+                   int order, unsigned long long* hist, cudaStream_t s) {
+  if (total == 0) return;
+  const ClassTables& T = class_tables(order);
+  const uint8_t* lut = device_lut(order);
+  const int blocks = census_blocks((const void*)k_census<F>, total);
+  cudaEvent_t ev = nullptr;
+  const bool tr = trace_on();
+  if (tr) trace_begin(s, &ev);
+  k_census<F><<<blocks, CENSUS_THREADS, 0, s>>>(g->view(), fam, sp ? sp->ws : nullptr,
+                                               sp ? sp->anchors : 0, total, lut,
+                                               (int)T.lut.size(), T.ncls, hist);
+  HM_KCHECK();
+  if (tr) trace_end(F::kName, s, ev);
+}
+
+}  // namespace
+
+// Work spaces and launches of the census of one order; shared with the
+// null-model batch.
+void prepare_census(hm_graph* g, int order, cudaStream_t s) {
+  if (order == 3) {
+    ensure_space(g, g->W, 'W', s);
+  } else {
+    HM_CHECK(g->max_d2 < (1 << 21), HM_EUNSUPPORTED,
+             "a node has 2^21 or more pair neighbours; order-4 star space overflows");
+    ensure_space(g, g->S, 'S', s);
+    ensure_space(g, g->P, 'P', s);
+    ensure_space(g, g->TX, 'X', s);
+  }
+}
+
+void launch_census(const hm_graph* g, int order, unsigned long long* hist, cudaStream_t s) {
+  if (order == 3) {
+    launch_family(g, FamT3{}, nullptr, (uint64_t)g->counts[3], 3, hist, s);
+    launch_family(g, FamW{}, &g->W, g->W.total, 3, hist, s);
+  } else {
+    launch_family(g, FamQ{}, nullptr, (uint64_t)g->counts[4], 4, hist, s);
+    launch_family(g, FamTX{}, &g->TX, g->TX.total, 4, hist, s);
+    launch_family(g, FamS{}, &g->S, g->S.total, 4, hist, s);
+    launch_family(g, FamP{}, &g->P, g->P.total, 4, hist, s);
+  }
+}
+
+}  // namespace hm
+
+extern "C" hm_status hm_count_exact(hm_graph* g, int order, uint64_t* d_hist, void* stream) {
+  return hm::guarded([&] {
+    HM_CHECK(g != nullptr, HM_EINVAL, "NULL graph");
+    HM_CHECK(order == 3 || order == 4, HM_EINVAL, "order must be 3 or 4");
+    HM_CHECK(order <= g->kmax, HM_EUNSUPPORTED, "order exceeds the graph's max_order");
+    HM_CHECK(d_hist != nullptr, HM_EINVAL, "NULL histogram");
+    int dev = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    HM_CHECK(dev == g->device, HM_EINVAL, "graph was built on another device");
+    cudaStream_t s = (cudaStream_t)stream;
+    hm::prepare_census(g, order, s);
+    HM_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(uint64_t) * hm::class_tables(order).ncls, s));
+    hm::launch_census(g, order, (unsigned long long*)d_hist, s);
+  });
+}
+
+extern "C" hm_status hm_count_exact_host(const int32_t* h_members, const int64_t* h_offsets,
+                                         int64_t num_hyperedges, int32_t num_nodes, int order,
+                                         uint64_t* h_hist, void* stream) {
+  hm_graph* g = nullptr;
+  hm_status st = hm::guarded([&] {
+    HM_CHECK(order == 3 || order == 4, HM_EINVAL, "order must be 3 or 4");
+    HM_CHECK(h_offsets && h_hist, HM_EINVAL, "NULL argument");
+    HM_CHECK(num_hyperedges >= 0 && num_hyperedges < (1ll << 31), HM_EINVAL,
+             "num_hyperedges must be in [0, 2^31)");
+    HM_CHECK(num_nodes >= 1, HM_EINVAL, "num_nodes must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t total = h_offsets[num_hyperedges];
+    HM_CHECK(total >= 0 && (total == 0 || h_members), HM_EINVAL, "bad members/offsets");
+    hm::DBuf<int32_t> mem(total, s);
+    hm::DBuf<int64_t> off(num_hyperedges + 1, s);
+    hm::DBuf<unsigned long long> hist(hm::class_tables(order).ncls, s);
+    if (total)
+      HM_CUDA(cudaMemcpyAsync(mem.p, h_members, total * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    HM_CUDA(cudaMemcpyAsync(off.p, h_offsets, (num_hyperedges + 1) * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, s));
+    g = new hm_graph;
+    hm::build_graph(g, mem.p, off.p, num_hyperedges, num_nodes, order, s);
+    hm::prepare_census(g, order, s);
+    HM_CUDA(cudaMemsetAsync(hist.p, 0, hist.n * sizeof(unsigned long long), s));
+    hm::launch_census(g, order, hist.p, s);
+    HM_CUDA(cudaMemcpyAsync(h_hist, hist.p, hist.n * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+  });
+  if (g) {
+    std::string msg = hm_last_error();
+    hm::free_graph(g);
+    hm::set_last_error(msg);
+  }
+  return st;
+}
+
+extern "C" hm_status hm_work_totals(hm_graph* g, int order, uint64_t* totals, void* stream) {
+  return hm::guarded([&] {
+    HM_CHECK(g && totals, HM_EINVAL, "NULL argument");
+    HM_CHECK(order == 3 || order == 4, HM_EINVAL, "order must be 3 or 4");
+    HM_CHECK(order <= g->kmax, HM_EUNSUPPORTED, "order exceeds the graph's max_order");
+    hm::prepare_census(g, order, (cudaStream_t)stream);
+    if (order == 3) {
+      totals[0] = (uint64_t)g->counts[3];
+      totals[1] = g->W.total;
+    } else {
+      totals[0] = (uint64_t)g->counts[4];
+      totals[1] = g->TX.total;
+      totals[2] = g->S.total;
+      totals[3] = g->P.total;
+    }
+  });
+}

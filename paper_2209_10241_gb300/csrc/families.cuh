@@ -1,0 +1,324 @@
+// Candidate families of the exact census and the per-sample enumeration of
+// the sampling estimator: index-space decoding and the canonical-generation
+// rules, shared by census.cu and sampler.cu. See census.cu for the rules.
+#pragma once
+
+#include "hm_internal.cuh"
+
+namespace hm {
+namespace fam {
+
+constexpr int CENSUS_THREADS = 256;
+constexpr int CHUNK = 32;  // consecutive items per lane
+
+__host__ __device__ __forceinline__ uint64_t choose2(uint64_t x) { return x * (x - 1) / 2; }
+__host__ __device__ __forceinline__ uint64_t choose3(uint64_t x) {
+  return x < 3 ? 0 : x * (x - 1) / 2 * (x - 2) / 3;
+}
+
+// r = C(j,2) + i with 0 <= i < j
+__device__ __forceinline__ void unrank2(uint64_t r, uint32_t& i, uint32_t& j) {
+  uint64_t jj = (uint64_t)((1.0 + sqrt(1.0 + 8.0 * (double)r)) * 0.5);
+  if (jj < 1) jj = 1;
+  while (choose2(jj) > r) --jj;
+  while (choose2(jj + 1) <= r) ++jj;
+  j = (uint32_t)jj;
+  i = (uint32_t)(r - choose2(jj));
+}
+
+// r = C(l,3) + C(j,2) + i with 0 <= i < j < l
+__device__ __forceinline__ void unrank3(uint64_t r, uint32_t& i, uint32_t& j, uint32_t& l) {
+  uint64_t ll = (uint64_t)cbrt(6.0 * (double)r) + 1;
+  if (ll < 2) ll = 2;
+  while (choose3(ll) > r) --ll;
+  while (choose3(ll + 1) <= r) ++ll;
+  l = (uint32_t)ll;
+  unrank2(r - choose3(ll), i, j);
+}
+
+// sorted member tuple of a 3-hyperedge, comparable
+struct Tri {
+  uint64_t hi;
+  uint32_t lo;
+};
+__device__ __forceinline__ Tri make_tri(int32_t a, int32_t b, int32_t c) {
+  sort3(a, b, c);
+  return Tri{((uint64_t)(uint32_t)a << 32) | (uint32_t)b, (uint32_t)c};
+}
+__device__ __forceinline__ bool tri_less(const Tri& x, const Tri& y) {
+  return x.hi < y.hi || (x.hi == y.hi && x.lo < y.lo);
+}
+__device__ __forceinline__ bool tri_eq(const Tri& x, const Tri& y) {
+  return x.hi == y.hi && x.lo == y.lo;
+}
+
+// ---------------------------------------------------------------- families
+// Direct families: one candidate per anchor. With `map` set (sampling), the
+// anchor is a sample and map[anchor] the sampled hyperedge.
+struct FamT3 {
+  static constexpr const char* kName = "census_T3";
+  static constexpr bool kDirect = true;
+  const int64_t* map = nullptr;
+  struct State {};
+  __device__ void begin(const DevGraph&, int64_t, uint64_t, State&) const {}
+  __device__ void next(State&) const {}
+  __device__ bool item(const DevGraph& g, int64_t t, State&, uint32_t& mask) const {
+    const int4 e = g.e3[map ? map[t] : t];
+    mask = (has_pair(g, e.x, e.y) ? 1u : 0u) | (has_pair(g, e.x, e.z) ? 2u : 0u) |
+           (has_pair(g, e.y, e.z) ? 4u : 0u) | 8u;
+    return true;
+  }
+};
+
+struct FamQ {
+  static constexpr const char* kName = "census_Q";
+  static constexpr bool kDirect = true;
+  const int64_t* map = nullptr;
+  struct State {};
+  __device__ void begin(const DevGraph&, int64_t, uint64_t, State&) const {}
+  __device__ void next(State&) const {}
+  __device__ bool item(const DevGraph& g, int64_t q, State&, uint32_t& mask) const {
+    const int4 e = g.e4[map ? map[q] : q];
+    const int32_t a = e.x, b = e.y, c = e.z, d = e.w;
+    mask = (has_pair(g, a, b) ? 1u : 0u) | (has_pair(g, a, c) ? 2u : 0u) |
+           (has_pair(g, a, d) ? 4u : 0u) | (has_pair(g, b, c) ? 8u : 0u) |
+           (has_pair(g, b, d) ? 16u : 0u) | (has_pair(g, c, d) ? 32u : 0u) |
+           (has_triple(g, a, b, c) ? 64u : 0u) | (has_triple(g, a, b, d) ? 128u : 0u) |
+           (has_triple(g, a, c, d) ? 256u : 0u) | (has_triple(g, b, c, d) ? 512u : 0u) | 1024u;
+    return true;
+  }
+};
+
+struct FamW {
+  static constexpr const char* kName = "census_W";
+  static constexpr bool kDirect = false;
+  struct State {
+    uint32_t i, j;
+    int64_t o;
+  };
+  __device__ void begin(const DevGraph& g, int64_t v, uint64_t r, State& s) const {
+    s.o = g.off2[v];
+    unrank2(r, s.i, s.j);
+  }
+  __device__ void next(State& s) const {
+    if (++s.i == s.j) {
+      s.i = 0;
+      ++s.j;
+    }
+  }
+  __device__ bool item(const DevGraph& g, int64_t a, State& s, uint32_t& mask) const {
+    const int32_t v = (int32_t)a;
+    const int32_t x = g.adj2[s.o + s.i], y = g.adj2[s.o + s.j];
+    const bool xy = has_pair(g, x, y);
+    if (xy && (x < v || y < v)) return false;  // a triangle is kept at its smallest node
+    if (has_triple(g, v, x, y)) return false;  // counted with its 3-hyperedge
+    mask = 3u | (xy ? 4u : 0u);                // positions v=0, x=1, y=2
+    return true;
+  }
+};
+
+struct FamS {
+  static constexpr const char* kName = "census_S";
+  static constexpr bool kDirect = false;
+  struct State {
+    uint32_t i, j, l;
+    int64_t o;
+  };
+  __device__ void begin(const DevGraph& g, int64_t v, uint64_t r, State& s) const {
+    s.o = g.off2[v];
+    unrank3(r, s.i, s.j, s.l);
+  }
+  __device__ void next(State& s) const {
+    if (++s.i == s.j) {
+      s.i = 0;
+      if (++s.j == s.l) {
+        s.j = 1;
+        ++s.l;
+      }
+    }
+  }
+  __device__ bool item(const DevGraph& g, int64_t a, State& s, uint32_t& mask) const {
+    const int32_t v = (int32_t)a;
+    const int32_t x = g.adj2[s.o + s.i], y = g.adj2[s.o + s.j], z = g.adj2[s.o + s.l];
+    const bool xy = has_pair(g, x, y), xz = has_pair(g, x, z), yz = has_pair(g, y, z);
+    // v has induced degree 3; it must be the smallest node of degree 3
+    if ((xy && xz && x < v) || (xy && yz && y < v) || (xz && yz && z < v)) return false;
+    if (has_triple(g, v, x, y) || has_triple(g, v, x, z) || has_triple(g, v, y, z) ||
+        has_triple(g, x, y, z) || has_quad(g, v, x, y, z))
+      return false;  // not a pairs-only set: counted by Q or TX
+    mask = 7u | (xy ? 8u : 0u) | (xz ? 16u : 0u) | (yz ? 32u : 0u);  // v=0,x=1,y=2,z=3
+    return true;
+  }
+};
+
+struct FamP {
+  static constexpr const char* kName = "census_P";
+  static constexpr bool kDirect = false;
+  struct State {
+    int32_t u, v;
+    int64_t ou, ov;
+    uint32_t pu, pv, dv1, i2, j2;
+  };
+  __device__ void begin(const DevGraph& g, int64_t p, uint64_t r, State& s) const {
+    const uint64_t uv = g.e2[p];
+    s.u = (int32_t)(uv >> 32);
+    s.v = (int32_t)(uv & 0xFFFFFFFFull);
+    s.ou = g.off2[s.u];
+    s.ov = g.off2[s.v];
+    s.dv1 = (uint32_t)(g.off2[s.v + 1] - s.ov - 1);
+    const int2 pp = g.pairpos[p];
+    s.pu = (uint32_t)pp.x;
+    s.pv = (uint32_t)pp.y;
+    s.i2 = (uint32_t)(r / s.dv1);
+    s.j2 = (uint32_t)(r % s.dv1);
+  }
+  __device__ void next(State& s) const {
+    if (++s.j2 == s.dv1) {
+      s.j2 = 0;
+      ++s.i2;
+    }
+  }
+  __device__ bool item(const DevGraph& g, int64_t, State& s, uint32_t& mask) const {
+    const int32_t u = s.u, v = s.v;
+    const int32_t x = g.adj2[s.ou + s.i2 + (s.i2 >= s.pu ? 1 : 0)];  // N2(u) \ {v}
+    const int32_t y = g.adj2[s.ov + s.j2 + (s.j2 >= s.pv ? 1 : 0)];  // N2(v) \ {u}
+    if (x == y) return false;
+    if (has_pair(g, u, y) || has_pair(g, v, x)) return false;  // a degree-3 node: family S
+    const bool xy = has_pair(g, x, y);
+    if (xy) {  // 4-cycle: kept at its smallest pair
+      const uint64_t kuv = pair_key(u, v);
+      if (pair_key(u, x) < kuv || pair_key(v, y) < kuv || pair_key(x, y) < kuv) return false;
+    }
+    if (has_triple(g, u, v, x) || has_triple(g, u, v, y) || has_triple(g, u, x, y) ||
+        has_triple(g, v, x, y) || has_quad(g, u, v, x, y))
+      return false;
+    mask = 1u | 2u | 16u | (xy ? 32u : 0u);  // u=0, v=1, x=2, y=3: pairs 01, 02, 13 (+23)
+    return true;
+  }
+};
+
+// kCensus: the anchor is a 3-hyperedge and a set is kept only at its smallest
+// 3-hyperedge. Otherwise (sampling, Alg. 4) the anchor is a sample whose
+// 3-hyperedge is map[anchor] and every set through it whose largest hyperedges
+// have 3 members is kept.
+template <bool kCensus>
+struct FamTXT {
+  static constexpr const char* kName = kCensus ? "census_TX" : "sample_TX";
+  static constexpr bool kDirect = false;
+  const int64_t* map = nullptr;
+  struct State {
+    int32_t x[3];
+    int32_t d2[3];
+    uint64_t w[3];
+    uint64_t r;
+    int64_t t;
+  };
+  __device__ void begin(const DevGraph& g, int64_t anchor, uint64_t r, State& s) const {
+    const int64_t t = kCensus ? anchor : map[anchor];
+    s.t = t;
+    const int4 e = g.e3[t];
+    s.x[0] = e.x;
+    s.x[1] = e.y;
+    s.x[2] = e.z;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int32_t n = s.x[j];
+      s.d2[j] = (int32_t)(g.off2[n + 1] - g.off2[n]);
+      s.w[j] = (uint64_t)s.d2[j] + (uint64_t)(g.off3[n + 1] - g.off3[n]);
+    }
+    s.r = r;
+  }
+  __device__ void next(State& s) const { ++s.r; }
+  __device__ bool item(const DevGraph& g, int64_t, State& s, uint32_t& mask) const {
+    const int64_t t = s.t;
+    uint64_t r = s.r;
+    int which = 0;
+    if (r >= s.w[0]) {
+      r -= s.w[0];
+      which = 1;
+      if (r >= s.w[1]) {
+        r -= s.w[1];
+        which = 2;
+      }
+    }
+    const int32_t a = s.x[0], b = s.x[1], c = s.x[2];
+    const int32_t x = s.x[which];
+    int32_t d;
+    bool hpair;
+    Tri htri{0, 0};
+    if (r < (uint64_t)s.d2[which]) {
+      d = g.adj2[g.off2[x] + r];
+      if (d == a || d == b || d == c) return false;
+      hpair = true;
+    } else {
+      const int32_t th = g.inc3[g.off3[x] + (int64_t)(r - s.d2[which])];
+      if (th == t) return false;
+      const int4 h = g.e3[th];
+      const int32_t hm[3] = {h.x, h.y, h.z};
+      int outside = 0;
+      int32_t o = -1, inmin = 0x7FFFFFFF;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        if (hm[j] == a || hm[j] == b || hm[j] == c) {
+          inmin = min(inmin, hm[j]);
+        } else {
+          ++outside;
+          o = hm[j];
+        }
+      }
+      if (outside != 1 || x != inmin) return false;
+      d = o;
+      hpair = false;
+      htri = make_tri(h.x, h.y, h.z);
+    }
+    // h must be the smallest hyperedge of the set containing d
+    const bool ad = has_pair(g, a, d), bd = has_pair(g, b, d), cd = has_pair(g, c, d);
+    if (ad || bd || cd) {
+      if (!hpair) return false;
+      uint64_t mn = ~0ull;
+      if (ad) mn = min(mn, pair_key(a, d));
+      if (bd) mn = min(mn, pair_key(b, d));
+      if (cd) mn = min(mn, pair_key(c, d));
+      if (pair_key(x, d) != mn) return false;
+    }
+    const bool abd = has_triple(g, a, b, d), acd = has_triple(g, a, c, d),
+               bcd = has_triple(g, b, c, d);
+    const Tri e = make_tri(a, b, c);
+    const Tri tabd = make_tri(a, b, d), tacd = make_tri(a, c, d), tbcd = make_tri(b, c, d);
+    // census: e must be the smallest 3-hyperedge of the set
+    if (kCensus &&
+        ((abd && tri_less(tabd, e)) || (acd && tri_less(tacd, e)) || (bcd && tri_less(tbcd, e))))
+      return false;
+    if (!hpair) {
+      Tri mn{~0ull, 0xFFFFFFFFu};
+      if (abd && tri_less(tabd, mn)) mn = tabd;
+      if (acd && tri_less(tacd, mn)) mn = tacd;
+      if (bcd && tri_less(tbcd, mn)) mn = tbcd;
+      if (!tri_eq(htri, mn)) return false;
+    }
+    if (has_quad(g, a, b, c, d)) return false;  // holds a 4-hyperedge (family Q)
+    const bool ab = has_pair(g, a, b), ac = has_pair(g, a, c), bc = has_pair(g, b, c);
+    mask = (ab ? 1u : 0u) | (ac ? 2u : 0u) | (ad ? 4u : 0u) | (bc ? 8u : 0u) |
+           (bd ? 16u : 0u) | (cd ? 32u : 0u) | 64u | (abd ? 128u : 0u) | (acd ? 256u : 0u) |
+           (bcd ? 512u : 0u);  // a=0, b=1, c=2, d=3
+    return true;
+  }
+};
+using FamTX = FamTXT<true>;
+
+__device__ __forceinline__ int64_t anchor_of(const uint64_t* __restrict__ ws, int64_t A,
+                                             uint64_t g0) {
+  // last a with ws[a] <= g0 (ws non-decreasing, ws[0] = 0)
+  int64_t lo = 0, hi = A;  // answer in [0, A)
+  while (hi - lo > 1) {
+    int64_t mid = (lo + hi) >> 1;
+    if (ws[mid] <= g0)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+}  // namespace fam
+}  // namespace hm

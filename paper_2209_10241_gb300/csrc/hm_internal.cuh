@@ -1,0 +1,329 @@
+// Internal definitions of the CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "hm.h"
+
+namespace hm {
+
+// ------------------------------------------------------------------ errors
+struct Error : std::runtime_error {
+  hm_status code;
+  Error(hm_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void set_last_error(const std::string& msg);
+
+#define HM_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      throw ::hm::Error(e_ == cudaErrorMemoryAllocation ? HM_ENOMEM : HM_ECUDA,         \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));            \
+  } while (0)
+
+// Kernels launched by the library (all devices, all threads).
+uint64_t launch_count_add(uint64_t n);
+
+// check a kernel launch and count it
+#define HM_KCHECK()                                   \
+  do {                                                \
+    ::hm::launch_count_add(1);                        \
+    HM_CUDA(cudaGetLastError());                      \
+  } while (0)
+
+#define HM_CHECK(cond, code, msg)                       \
+  do {                                                  \
+    if (!(cond)) throw ::hm::Error((code), (msg));      \
+  } while (0)
+
+// Run an entry point body, converting exceptions into a status code.
+template <class F>
+hm_status guarded(F&& f) {
+  try {
+    f();
+    set_last_error("");
+    return HM_OK;
+  } catch (const Error& e) {
+    set_last_error(e.what());
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    return HM_ENOMEM;
+  } catch (const std::exception& e) {
+    set_last_error(e.what());
+    return HM_ECUDA;
+  }
+}
+
+// Stream-ordered device buffer (freed on the stream it was allocated on).
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaStream_t s = nullptr;
+  DBuf() = default;
+  DBuf(size_t count, cudaStream_t st) { alloc(count, st); }
+  void alloc(size_t count, cudaStream_t st) {
+    release();
+    s = st;
+    n = count;
+    if (count) HM_CUDA(cudaMallocAsync((void**)&p, count * sizeof(T), st));
+  }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    n = 0;
+  }
+  T* release_ownership() {
+    T* q = p;
+    p = nullptr;
+    n = 0;
+    return q;
+  }
+  ~DBuf() { release(); }
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+};
+
+// Device memory owned by a graph (plain cudaMalloc, freed by hm_free).
+template <class T>
+T* dalloc(size_t count) {
+  T* p = nullptr;
+  if (count) HM_CUDA(cudaMalloc((void**)&p, count * sizeof(T)));
+  return p;
+}
+
+// ------------------------------------------------------------------ primitives (prims.cu)
+// Exclusive scan: out[0..n] with out[n] = total. in and out may alias only if
+// in == out is not required (they must not alias).
+void scan_exclusive_u64(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s);
+void scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);
+// Stable LSD radix sort of n keys on their low `bits` bits; vals (nullable)
+// are permuted alongside.
+void radix_sort_u64(uint64_t* keys, uint64_t* vals, int64_t n, int bits, cudaStream_t s);
+// Stable LSD radix sort of 128-bit keys (hi, lo) lexicographically, on the low
+// lo_bits of lo and the low hi_bits of hi.
+void radix_sort_u128(uint64_t* hi, uint64_t* lo, int64_t n, int hi_bits, int lo_bits,
+                     cudaStream_t s);
+// Remove adjacent duplicates of a sorted key array in place; returns the
+// number kept (synchronises the stream). hi may be NULL for 64-bit keys.
+int64_t unique_sorted(uint64_t* hi, uint64_t* lo, int64_t n, cudaStream_t s);
+// off[v] = first index i with (key[i] >> shift) >= v, for v in [0, num_nodes];
+// keys sorted ascending.
+void csr_offsets(const uint64_t* keys, int64_t n, int shift, int32_t num_nodes, int64_t* off,
+                 cudaStream_t s);
+
+// ------------------------------------------------------------------ hashing
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  // SplitMix64 finaliser (Steele, Lea, Flood 2014)
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return z;
+}
+
+__host__ __device__ __forceinline__ uint64_t pair_key(int32_t a, int32_t b) {
+  // sorted pair packed as (min << 32) | max
+  uint32_t x = (uint32_t)(a < b ? a : b), y = (uint32_t)(a < b ? b : a);
+  return ((uint64_t)x << 32) | y;
+}
+
+__host__ __device__ __forceinline__ uint64_t hash_pair(uint64_t key) { return mix64(key); }
+
+__host__ __device__ __forceinline__ uint64_t hash_tuple(int32_t a, int32_t b, int32_t c,
+                                                        int32_t d) {
+  uint64_t x = ((uint64_t)(uint32_t)a << 32) | (uint32_t)b;
+  uint64_t y = ((uint64_t)(uint32_t)c << 32) | (uint32_t)d;
+  return mix64(x ^ mix64(y + 0x9E3779B97F4A7C15ull));
+}
+
+constexpr uint64_t EMPTY64 = ~0ull;
+
+// ------------------------------------------------------------------ graph
+// Read-only view handed to kernels by value.
+struct DevGraph {
+  int32_t n;
+  // distinct hyperedges in ascending order
+  const uint64_t* e2;  // (u << 32) | v, u < v
+  const int4* e3;      // (a, b, c, -1), a < b < c
+  const int4* e4;      // (a, b, c, d), a < b < c < d
+  int64_t m2, m3, m4;
+  // open-addressing hash sets (linear probing), capacity mask + 1 (power of 2)
+  const uint64_t* h2;
+  uint64_t h2_mask;
+  const int4* h3;
+  uint64_t h3_mask;
+  const int4* h4;
+  uint64_t h4_mask;
+  // node -> pair neighbours (sorted), node -> triples containing it (ascending index)
+  const int64_t* off2;
+  const int32_t* adj2;
+  const int64_t* off3;
+  const int32_t* inc3;
+  // per pair p = (u, v): position of v in N2(u) and of u in N2(v)
+  const int2* pairpos;
+  // optional dense pair-adjacency bitmap: row u holds bwords 32-bit words
+  const uint32_t* bits2;
+  int32_t bwords;
+};
+
+__device__ __forceinline__ bool has_pair(const DevGraph& g, int32_t a, int32_t b) {
+  if (g.bits2) {
+    uint32_t w = __ldg(g.bits2 + (size_t)a * g.bwords + (b >> 5));
+    return (w >> (b & 31)) & 1u;
+  }
+  if (g.m2 == 0) return false;
+  uint64_t key = pair_key(a, b);
+  uint64_t slot = hash_pair(key) & g.h2_mask;
+  for (uint64_t it = 0; it <= g.h2_mask; ++it) {
+    uint64_t v = __ldg(g.h2 + slot);
+    if (v == key) return true;
+    if (v == EMPTY64) return false;
+    slot = (slot + 1) & g.h2_mask;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void sort3(int32_t& a, int32_t& b, int32_t& c) {
+  int32_t t;
+  if (a > b) { t = a; a = b; b = t; }
+  if (b > c) { t = b; b = c; c = t; }
+  if (a > b) { t = a; a = b; b = t; }
+}
+
+__device__ __forceinline__ void sort4(int32_t& a, int32_t& b, int32_t& c, int32_t& d) {
+  int32_t t;
+  if (a > b) { t = a; a = b; b = t; }
+  if (c > d) { t = c; c = d; d = t; }
+  if (a > c) { t = a; a = c; c = t; }
+  if (b > d) { t = b; b = d; d = t; }
+  if (b > c) { t = b; b = c; c = t; }
+}
+
+__device__ __forceinline__ bool probe_tuple(const int4* table, uint64_t mask, int32_t a, int32_t b,
+                                            int32_t c, int32_t d) {
+  uint64_t slot = hash_tuple(a, b, c, d) & mask;
+  for (uint64_t it = 0; it <= mask; ++it) {
+    int4 v = __ldg(table + slot);
+    if (v.x == a && v.y == b && v.z == c && v.w == d) return true;
+    if (v.x == -1) return false;
+    slot = (slot + 1) & mask;
+  }
+  return false;
+}
+
+// existence of the 3-hyperedge {a, b, c} (any order)
+__device__ __forceinline__ bool has_triple(const DevGraph& g, int32_t a, int32_t b, int32_t c) {
+  if (g.m3 == 0) return false;
+  sort3(a, b, c);
+  return probe_tuple(g.h3, g.h3_mask, a, b, c, -1);
+}
+
+// existence of the 4-hyperedge {a, b, c, d} (any order)
+__device__ __forceinline__ bool has_quad(const DevGraph& g, int32_t a, int32_t b, int32_t c,
+                                         int32_t d) {
+  if (g.m4 == 0) return false;
+  sort4(a, b, c, d);
+  return probe_tuple(g.h4, g.h4_mask, a, b, c, d);
+}
+
+// ------------------------------------------------------------------ tracing (trace.cu)
+bool trace_on();
+void trace_begin(cudaStream_t s, cudaEvent_t* a);
+void trace_end(const char* name, cudaStream_t s, cudaEvent_t a);
+
+// ------------------------------------------------------------------ classes (classes.cu)
+struct ClassTables {
+  int k;
+  int ncls;
+  std::vector<uint8_t> lut;       // labelled mask -> class id, 0xFF if disconnected
+  std::vector<uint32_t> canon;    // class id -> canonical mask
+  std::vector<int32_t> maxcard, countmax;
+};
+const ClassTables& class_tables(int k);
+// device copy of the LUT of order k for the current device
+const uint8_t* device_lut(int k);
+
+}  // namespace hm
+
+struct hm_graph;
+namespace hm {
+// build.cu
+void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets, int64_t m,
+                 int32_t n, int kmax, cudaStream_t s);
+void free_graph(hm_graph* g);
+// census.cu
+void prepare_census(hm_graph* g, int order, cudaStream_t s);
+void launch_census(const hm_graph* g, int order, unsigned long long* hist, cudaStream_t s);
+}  // namespace hm
+
+// ------------------------------------------------------------------ graph object
+struct hm_graph {
+  int device = 0;
+  int32_t n = 0;
+  int kmax = 0;
+  int64_t m_in = 0;
+  int64_t counts[8] = {0};
+  int bits = 1;  // bits per node id in packed sort keys
+  // owned device arrays (cudaMalloc)
+  uint64_t* e2 = nullptr;
+  int4* e3 = nullptr;
+  int4* e4 = nullptr;
+  uint64_t* h2 = nullptr;
+  uint64_t h2_mask = 0;
+  int4* h3 = nullptr;
+  uint64_t h3_mask = 0;
+  int4* h4 = nullptr;
+  uint64_t h4_mask = 0;
+  int64_t* off2 = nullptr;
+  int32_t* adj2 = nullptr;
+  int64_t* off3 = nullptr;
+  int32_t* inc3 = nullptr;
+  int2* pairpos = nullptr;
+  uint32_t* bits2 = nullptr;
+  int32_t bwords = 0;
+  int32_t max_d2 = 0;
+  // cached work spaces (prefix sums over anchors), per family
+  struct Space {
+    uint64_t* ws = nullptr;  // [anchors + 1]
+    int64_t anchors = 0;
+    uint64_t total = 0;
+    bool ready = false;
+  };
+  Space W, S, P, TX;
+  std::vector<void*> owned;  // everything above, for hm_free
+
+  hm::DevGraph view() const {
+    hm::DevGraph g;
+    g.n = n;
+    g.e2 = e2;
+    g.e3 = e3;
+    g.e4 = e4;
+    g.m2 = counts[2];
+    g.m3 = kmax >= 3 ? counts[3] : 0;
+    g.m4 = kmax >= 4 ? counts[4] : 0;
+    g.h2 = h2;
+    g.h2_mask = h2_mask;
+    g.h3 = h3;
+    g.h3_mask = h3_mask;
+    g.h4 = h4;
+    g.h4_mask = h4_mask;
+    g.off2 = off2;
+    g.adj2 = adj2;
+    g.off3 = off3;
+    g.inc3 = inc3;
+    g.pairpos = pairpos;
+    g.bits2 = bits2;
+    g.bwords = bwords;
+    return g;
+  }
+};

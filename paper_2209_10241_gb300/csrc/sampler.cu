@@ -1,0 +1,576 @@
+// Stratified hyperedge-sampling estimator (Alg. 4, Sec. 5).
+//
+// For every stratum s (hyperedge size 2..k) S_s hyperedges are drawn with
+// replacement: draw t uses Philox4x32-10 (Salmon et al., SC'11) with key =
+// seed and counter = (t lo, t hi, s, "SAMP"), and the 64-bit value
+// (r0 << 32) | r1 picks mulhi64(value, |E_s|) -- or, with proposal weights q,
+// the inverse CDF of q at mulhi64(value, Q_s). For each draw every k-node set
+// V' containing the drawn hyperedge e with H[V'] connected and no hyperedge
+// larger than e is enumerated and counted by class (the max-cardinality rule
+// of Sec. 5). Counts accumulate as integers (weighted draws add
+// floor(2^63 / q_e) into 128-bit sums), so the result is independent of the
+// order of the atomic updates; the correction factor of Alg. 4 is applied in
+// IEEE double in a fixed order.
+//
+// Per-sample enumeration (each set once per draw):
+//   s = k        the drawn hyperedge itself (families T3 / Q with a map)
+//   k=4, s=3     nodes d joined to e by a hyperedge h of size 2 or 3 through
+//                x in e: kept when x = min(h ∩ e), h is the smallest hyperedge
+//                containing d and there is no 4-hyperedge (TX without the
+//                anchor-minimality test)
+//   s=2, e={a,b} L1 = N2(a)\{b} followed by N2(b)\{a}, entries of the second
+//                part also adjacent to a dropped. k=3: {a,b,c}, c in L1.
+//                k=4: {c,d} from two L1 entries, or c in L1 and d a
+//                pair-neighbour of c outside L1 ∪ e. Sets holding a 3- or
+//                4-hyperedge are dropped (max-cardinality rule).
+#include <cmath>
+
+#include "families.cuh"
+
+namespace hm {
+namespace {
+
+using namespace fam;
+
+constexpr uint32_t TAG_SAMPLE = 0x53414D50u;  // "SAMP"
+constexpr int64_t SAMPLE_BATCH = 1 << 20;
+constexpr int SAMPLE_THREADS = 256;
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+    const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+__device__ __forceinline__ int32_t deg2(const DevGraph& g, int32_t v) {
+  return (int32_t)(g.off2[v + 1] - g.off2[v]);
+}
+
+// entry i of L1 = N2(a)\{b} ++ N2(b)\{a}
+struct PairList {
+  int32_t a, b;
+  int64_t ao, bo;
+  uint32_t la, pa, pb;
+};
+
+__device__ __forceinline__ PairList pair_list(const DevGraph& g, int64_t p) {
+  PairList L;
+  const uint64_t ab = g.e2[p];
+  L.a = (int32_t)(ab >> 32);
+  L.b = (int32_t)(ab & 0xFFFFFFFFull);
+  L.ao = g.off2[L.a];
+  L.bo = g.off2[L.b];
+  L.la = (uint32_t)(g.off2[L.a + 1] - L.ao - 1);
+  const int2 pp = g.pairpos[p];
+  L.pa = (uint32_t)pp.x;
+  L.pb = (uint32_t)pp.y;
+  return L;
+}
+
+__device__ __forceinline__ int32_t list_elem(const DevGraph& g, const PairList& L, uint32_t i) {
+  if (i < L.la) return g.adj2[L.ao + i + (i >= L.pa ? 1 : 0)];
+  const uint32_t j = i - L.la;
+  return g.adj2[L.bo + j + (j >= L.pb ? 1 : 0)];
+}
+
+struct DrawArgs {
+  uint64_t seed;
+  int s, order;
+  uint64_t t0;
+  int64_t count;
+  int64_t len;
+  const uint64_t* P;  // exclusive prefix of q over E_s (len + 1), NULL = uniform
+  const uint32_t* q;  // weights of E_s
+};
+
+// Draws of one batch, the drawn hyperedge, its weight and its enumeration size.
+__global__ void k_draw(const DevGraph g, const DrawArgs d, int64_t* __restrict__ sidx,
+                       uint64_t* __restrict__ wt, uint64_t* __restrict__ work,
+                       uint64_t* __restrict__ lsize) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t t = d.t0 + (uint64_t)i;
+    uint32_t c[4] = {(uint32_t)t, (uint32_t)(t >> 32), (uint32_t)d.s, TAG_SAMPLE};
+    philox4x32_10(c, (uint32_t)d.seed, (uint32_t)(d.seed >> 32));
+    const uint64_t v = ((uint64_t)c[0] << 32) | c[1];
+    int64_t idx;
+    if (!d.P) {
+      idx = (int64_t)__umul64hi(v, (uint64_t)d.len);
+    } else {
+      const uint64_t r = __umul64hi(v, d.P[d.len]);
+      int64_t lo = 0, hi = d.len;  // last idx with P[idx] <= r
+      while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (d.P[mid] <= r)
+          lo = mid;
+        else
+          hi = mid;
+      }
+      idx = lo;
+    }
+    sidx[i] = idx;
+    wt[i] = d.P ? (1ull << 63) / (uint64_t)d.q[idx] : 1ull;
+    uint64_t w = 1, l = 0;
+    if (d.s == 2 && d.s < d.order) {
+      const uint64_t ab = g.e2[idx];
+      const int32_t a = (int32_t)(ab >> 32), b = (int32_t)(ab & 0xFFFFFFFFull);
+      l = (uint64_t)(deg2(g, a) - 1) + (uint64_t)(deg2(g, b) - 1);
+      w = d.order == 3 ? l : choose2(l);
+    } else if (d.s == 3 && d.order == 4) {
+      const int4 e = g.e3[idx];
+      const int32_t xs[3] = {e.x, e.y, e.z};
+      w = 0;
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        w += (uint64_t)deg2(g, xs[j]) + (uint64_t)(g.off3[xs[j] + 1] - g.off3[xs[j]]);
+    }
+    work[i] = w;
+    if (lsize) lsize[i] = l;
+  }
+}
+
+// L1 entries of every drawn pair (order 4), with the pair-degree of each
+// valid entry as its enumeration size.
+__global__ void k_elements(const DevGraph g, const int64_t* __restrict__ sidx, int64_t count,
+                           const uint64_t* __restrict__ eoff, int2* __restrict__ elems,
+                           uint64_t* __restrict__ ework) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const PairList L = pair_list(g, sidx[i]);
+    const uint64_t base = eoff[i], n = eoff[i + 1] - base;
+    for (uint64_t j = 0; j < n; ++j) {
+      const int32_t c = list_elem(g, L, (uint32_t)j);
+      const bool valid = j < L.la || !has_pair(g, L.a, c);
+      elems[base + j] = make_int2((int32_t)i, valid ? c : -1);
+      ework[base + j] = valid ? (uint64_t)deg2(g, c) : 0ull;
+    }
+  }
+}
+
+// k=3, s=2: {a, b, c}, c in L1
+struct SamP3 {
+  static constexpr const char* kName = "sample_P3";
+  static constexpr bool kDirect = false;
+  const int64_t* map;
+  struct State {
+    PairList L;
+    uint32_t i;
+  };
+  __device__ void begin(const DevGraph& g, int64_t a, uint64_t r, State& s) const {
+    s.L = pair_list(g, map[a]);
+    s.i = (uint32_t)r;
+  }
+  __device__ void next(State& s) const { ++s.i; }
+  __device__ bool item(const DevGraph& g, int64_t, State& s, uint32_t& mask) const {
+    const PairList& L = s.L;
+    const int32_t c = list_elem(g, L, s.i);
+    const bool first = s.i < L.la;
+    if (!first && has_pair(g, L.a, c)) return false;  // already listed from a
+    if (has_triple(g, L.a, L.b, c)) return false;     // larger hyperedge than e
+    const bool ac = first, bc = first ? has_pair(g, L.b, c) : true;
+    mask = 1u | (ac ? 2u : 0u) | (bc ? 4u : 0u);  // a=0, b=1, c=2
+    return true;
+  }
+};
+
+// k=4, s=2: {a, b, c, d} with c, d two entries of L1
+struct SamPA {
+  static constexpr const char* kName = "sample_PA";
+  static constexpr bool kDirect = false;
+  const int64_t* map;
+  struct State {
+    PairList L;
+    uint32_t i, j;
+  };
+  __device__ void begin(const DevGraph& g, int64_t a, uint64_t r, State& s) const {
+    s.L = pair_list(g, map[a]);
+    unrank2(r, s.i, s.j);
+  }
+  __device__ void next(State& s) const {
+    if (++s.i == s.j) {
+      s.i = 0;
+      ++s.j;
+    }
+  }
+  __device__ bool item(const DevGraph& g, int64_t, State& s, uint32_t& mask) const {
+    const PairList& L = s.L;
+    const int32_t a = L.a, b = L.b;
+    const int32_t c = list_elem(g, L, s.i), d = list_elem(g, L, s.j);
+    const bool cfirst = s.i < L.la, dfirst = s.j < L.la;
+    const bool ac = cfirst ? true : has_pair(g, a, c);
+    const bool ad = dfirst ? true : has_pair(g, a, d);
+    if ((!cfirst && ac) || (!dfirst && ad)) return false;  // already listed from a
+    const bool bc = cfirst ? has_pair(g, b, c) : true;
+    const bool bd = dfirst ? has_pair(g, b, d) : true;
+    const bool cd = has_pair(g, c, d);
+    if (has_triple(g, a, b, c) || has_triple(g, a, b, d) || has_triple(g, a, c, d) ||
+        has_triple(g, b, c, d) || has_quad(g, a, b, c, d))
+      return false;
+    mask = 1u | (ac ? 2u : 0u) | (ad ? 4u : 0u) | (bc ? 8u : 0u) | (bd ? 16u : 0u) |
+           (cd ? 32u : 0u);  // a=0, b=1, c=2, d=3
+    return true;
+  }
+};
+
+// k=4, s=2: {a, b, c, d} with c in L1 and d a pair-neighbour of c outside L1 ∪ e
+struct SamPB {
+  static constexpr const char* kName = "sample_PB";
+  static constexpr bool kDirect = false;
+  const int64_t* map;
+  const int2* elems;
+  struct State {
+    int32_t a, b, c;
+    int64_t co;
+    uint64_t r;
+  };
+  __device__ void begin(const DevGraph& g, int64_t j, uint64_t r, State& s) const {
+    const int2 el = elems[j];
+    const uint64_t ab = g.e2[map[el.x]];
+    s.a = (int32_t)(ab >> 32);
+    s.b = (int32_t)(ab & 0xFFFFFFFFull);
+    s.c = el.y;
+    s.co = g.off2[el.y];
+    s.r = r;
+  }
+  __device__ void next(State& s) const { ++s.r; }
+  __device__ bool item(const DevGraph& g, int64_t, State& s, uint32_t& mask) const {
+    const int32_t a = s.a, b = s.b, c = s.c;
+    const int32_t d = g.adj2[s.co + s.r];
+    if (d == a || d == b || has_pair(g, a, d) || has_pair(g, b, d)) return false;
+    if (has_triple(g, a, b, c) || has_triple(g, a, b, d) || has_triple(g, a, c, d) ||
+        has_triple(g, b, c, d) || has_quad(g, a, b, c, d))
+      return false;
+    const bool ac = has_pair(g, a, c), bc = has_pair(g, b, c);
+    mask = 1u | (ac ? 2u : 0u) | (bc ? 8u : 0u) | 32u;  // pairs ab, (ac), (bc), cd
+    return true;
+  }
+};
+
+template <class F>
+__device__ __forceinline__ int64_t sample_of(const F&, int64_t a) {
+  return a;
+}
+__device__ __forceinline__ int64_t sample_of(const SamPB& f, int64_t a) { return f.elems[a].x; }
+
+// Same index-space walk as the census driver; each counted set adds the
+// weight of its draw (1 for uniform draws) into (lo, hi) 128-bit class sums.
+template <class F, bool kWeighted>
+__global__ void __launch_bounds__(SAMPLE_THREADS)
+    k_sample(const DevGraph g, const F fam, const uint64_t* __restrict__ ws, int64_t A,
+             uint64_t total, const uint64_t* __restrict__ wt, const uint8_t* __restrict__ lut_g,
+             int nmask, int ncls, unsigned long long* __restrict__ raw) {
+  __shared__ unsigned long long blo[176], bhi[176];
+  __shared__ uint8_t lut[2048];
+  for (int i = threadIdx.x; i < nmask; i += blockDim.x) lut[i] = lut_g[i];
+  for (int i = threadIdx.x; i < ncls; i += blockDim.x) blo[i] = bhi[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint64_t nchunks = (total + CHUNK - 1) / CHUNK;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t cb = warp * 32; cb < nchunks; cb += nwarps * 32) {
+    const uint64_t g0 = (cb + lane) * CHUNK;
+    const uint64_t g1 = min(g0 + CHUNK, total);
+    typename F::State st;
+    int64_t a = 0;
+    uint64_t r = 0, wa = 0;
+    if (!F::kDirect && g0 < total) {
+      a = anchor_of(ws, A, g0);
+      r = g0 - ws[a];
+      wa = ws[a + 1] - ws[a];
+      fam.begin(g, a, r, st);
+    }
+    for (int it = 0; it < CHUNK; ++it) {
+      const uint64_t gi = g0 + it;
+      int cls = -1;
+      int64_t anchor = 0;
+      if (gi < g1) {
+        uint32_t mask = 0;
+        bool ok;
+        if (F::kDirect) {
+          anchor = (int64_t)gi;
+          ok = fam.item(g, anchor, st, mask);
+        } else {
+          if (r == wa) {
+            do {
+              ++a;
+            } while (ws[a + 1] == ws[a]);
+            r = 0;
+            wa = ws[a + 1] - ws[a];
+            fam.begin(g, a, 0, st);
+          }
+          anchor = a;
+          ok = fam.item(g, a, st, mask);
+          ++r;
+          fam.next(st);
+        }
+        if (ok) {
+          const uint8_t c = lut[mask];
+          cls = c == 0xFF ? -1 : (int)c;
+        }
+      }
+      if (!kWeighted) {
+        const unsigned peers = __match_any_sync(0xffffffffu, cls);
+        if (cls >= 0 && lane == __ffs(peers) - 1)
+          atomicAdd(&blo[cls], (unsigned long long)__popc(peers));
+      } else if (cls >= 0) {
+        const unsigned long long w = wt[sample_of(fam, anchor)];
+        const unsigned long long old = atomicAdd(&blo[cls], w);
+        if (old + w < old) atomicAdd(&bhi[cls], 1ull);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < ncls; i += blockDim.x) {
+    const unsigned long long lo = blo[i], hi = bhi[i];
+    if (lo | hi) {
+      const unsigned long long old = atomicAdd(&raw[2 * i], lo);
+      const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+      if (hi + carry) atomicAdd(&raw[2 * i + 1], hi + carry);
+    }
+  }
+}
+
+struct EstArgs {
+  double S[5];
+  uint64_t E[5];  // |E_s|
+  int weighted;
+  int ncls;
+  int8_t maxcard[176];
+  int8_t countmax[176];
+};
+
+// Correction of Alg. 4: (n_c |E_m|) / (S_m countmax_c), or with weights
+// (A_c 2^-63 Q_m) / (S_m countmax_c); round-to-nearest at every step, no
+// contraction, in this order.
+__global__ void k_estimate(const EstArgs e, const uint64_t* __restrict__ Q,
+                           const unsigned long long* __restrict__ raw, double* __restrict__ est) {
+  for (int c = threadIdx.x; c < e.ncls; c += blockDim.x) {
+    const int m = e.maxcard[c];
+    if (e.S[m] == 0.0 || e.E[m] == 0) {
+      est[c] = 0.0;
+      continue;
+    }
+    double a;
+    if (e.weighted) {
+      a = __dadd_rn(__dmul_rn(__ull2double_rn(raw[2 * c + 1]), 18446744073709551616.0),
+                    __ull2double_rn(raw[2 * c]));
+      a = __dmul_rn(a, 0x1p-63);
+    } else {
+      a = __ull2double_rn(raw[2 * c]);
+    }
+    const double num = __dmul_rn(a, __ull2double_rn(Q[m]));
+    const double den = __dmul_rn(e.S[m], (double)e.countmax[c]);
+    est[c] = __ddiv_rn(num, den);
+  }
+}
+
+__global__ void k_widen(const uint32_t* __restrict__ q, int64_t n, uint64_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = q[i];
+}
+
+__global__ void k_bad_weight(const uint32_t* __restrict__ q, int64_t n, int* flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (q[i] == 0) atomicOr(flag, 1);
+}
+
+unsigned grid_n(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > 152 * 64) b = 152 * 64;
+  return (unsigned)b;
+}
+
+int sample_blocks(const void* kernel, uint64_t total) {
+  int dev = 0, sms = 0, per_sm = 0;
+  HM_CUDA(cudaGetDevice(&dev));
+  HM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, SAMPLE_THREADS, 0));
+  if (per_sm < 1) per_sm = 1;
+  const uint64_t need = ((total + CHUNK - 1) / CHUNK + SAMPLE_THREADS - 1) / SAMPLE_THREADS;
+  uint64_t b = (uint64_t)sms * per_sm;
+  if (need < b) b = need;
+  return (int)(b < 1 ? 1 : b);
+}
+
+template <class F>
+void launch_sample(const hm_graph* g, const F& f, const uint64_t* ws, int64_t A, uint64_t total,
+                   const uint64_t* wt, bool weighted, int order, unsigned long long* raw,
+                   cudaStream_t s) {
+  if (total == 0) return;
+  const ClassTables& T = class_tables(order);
+  const uint8_t* lut = device_lut(order);
+  cudaEvent_t ev = nullptr;
+  const bool tr = trace_on();
+  if (tr) trace_begin(s, &ev);
+  if (weighted) {
+    k_sample<F, true><<<sample_blocks((const void*)k_sample<F, true>, total), SAMPLE_THREADS, 0,
+                        s>>>(g->view(), f, ws, A, total, wt, lut, (int)T.lut.size(), T.ncls, raw);
+  } else {
+    k_sample<F, false><<<sample_blocks((const void*)k_sample<F, false>, total), SAMPLE_THREADS, 0,
+                         s>>>(g->view(), f, ws, A, total, wt, lut, (int)T.lut.size(), T.ncls, raw);
+  }
+  HM_KCHECK();
+  if (tr) trace_end(F::kName, s, ev);
+}
+
+uint64_t scan_total(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s) {
+  scan_exclusive_u64(in, out, n, s);
+  uint64_t tot = 0;
+  HM_CUDA(cudaMemcpyAsync(&tot, out + n, sizeof tot, cudaMemcpyDeviceToHost, s));
+  HM_CUDA(cudaStreamSynchronize(s));
+  return tot;
+}
+
+// One batch of draws of stratum s.
+void sample_batch(const hm_graph* g, int order, int s, const DrawArgs& da, bool weighted,
+                  unsigned long long* raw, cudaStream_t st) {
+  const int64_t cnt = da.count;
+  DBuf<int64_t> sidx(cnt, st);
+  DBuf<uint64_t> wt(cnt, st), work(cnt, st), lsize(cnt, st), ws(cnt + 1, st);
+  k_draw<<<grid_n(cnt), 256, 0, st>>>(g->view(), da, sidx.p, wt.p, work.p, lsize.p);
+  HM_KCHECK();
+  if (s == order) {
+    if (order == 3) {
+      FamT3 f;
+      f.map = sidx.p;
+      launch_sample(g, f, nullptr, 0, (uint64_t)cnt, wt.p, weighted, order, raw, st);
+    } else {
+      FamQ f;
+      f.map = sidx.p;
+      launch_sample(g, f, nullptr, 0, (uint64_t)cnt, wt.p, weighted, order, raw, st);
+    }
+    return;
+  }
+  const uint64_t total = scan_total(work.p, ws.p, cnt, st);
+  if (order == 4 && s == 3) {
+    FamTXT<false> f;
+    f.map = sidx.p;
+    launch_sample(g, f, ws.p, cnt, total, wt.p, weighted, order, raw, st);
+  } else if (order == 3) {
+    SamP3 f{sidx.p};
+    launch_sample(g, f, ws.p, cnt, total, wt.p, weighted, order, raw, st);
+  } else {
+    SamPA fa{sidx.p};
+    launch_sample(g, fa, ws.p, cnt, total, wt.p, weighted, order, raw, st);
+    DBuf<uint64_t> eoff(cnt + 1, st);
+    const uint64_t ne = scan_total(lsize.p, eoff.p, cnt, st);
+    if (ne == 0) return;
+    DBuf<int2> elems(ne, st);
+    DBuf<uint64_t> ework(ne, st), ews(ne + 1, st);
+    k_elements<<<grid_n(cnt), 256, 0, st>>>(g->view(), sidx.p, cnt, eoff.p, elems.p, ework.p);
+    HM_KCHECK();
+    const uint64_t tb = scan_total(ework.p, ews.p, (int64_t)ne, st);
+    SamPB fb{sidx.p, elems.p};
+    launch_sample(g, fb, ews.p, (int64_t)ne, tb, wt.p, weighted, order, raw, st);
+  }
+}
+
+}  // namespace
+
+void count_sampled(hm_graph* g, int order, const uint64_t* S, uint64_t seed, const uint32_t* d_q,
+                   double* d_est, uint64_t* d_raw, cudaStream_t st) {
+  const ClassTables& T = class_tables(order);
+  DBuf<unsigned long long> raw_tmp(d_raw ? 0 : 2 * T.ncls, st);
+  unsigned long long* raw = d_raw ? (unsigned long long*)d_raw : raw_tmp.p;
+  HM_CUDA(cudaMemsetAsync(raw, 0, 2 * T.ncls * sizeof(unsigned long long), st));
+  DBuf<uint64_t> Q(5, st);
+  uint64_t hostQ[5] = {0, 0, 0, 0, 0};
+  for (int s = 2; s <= order; ++s) hostQ[s] = (uint64_t)g->counts[s];
+  HM_CUDA(cudaMemcpyAsync(Q.p, hostQ, sizeof hostQ, cudaMemcpyHostToDevice, st));
+  const bool weighted = d_q != nullptr;
+  int64_t qoff = 0;
+  for (int s = 2; s <= order; ++s) {
+    const int64_t len = g->counts[s];
+    DBuf<uint64_t> P;
+    if (weighted && len > 0) {
+      DBuf<int> bad(1, st);
+      HM_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+      k_bad_weight<<<grid_n(len), 256, 0, st>>>(d_q + qoff, len, bad.p);
+      HM_KCHECK();
+      int hb = 0;
+      HM_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof hb, cudaMemcpyDeviceToHost, st));
+      DBuf<uint64_t> wide(len, st);
+      P.alloc(len + 1, st);
+      k_widen<<<grid_n(len), 256, 0, st>>>(d_q + qoff, len, wide.p);
+      HM_KCHECK();
+      scan_exclusive_u64(wide.p, P.p, len, st);
+      HM_CUDA(cudaMemcpyAsync(Q.p + s, P.p + len, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+      HM_CUDA(cudaStreamSynchronize(st));
+      HM_CHECK(hb == 0, HM_EINVAL, "proposal weights must be >= 1");
+    }
+    if (len > 0) {
+      for (uint64_t t0 = 0; t0 < S[s]; t0 += SAMPLE_BATCH) {
+        DrawArgs da;
+        da.seed = seed;
+        da.s = s;
+        da.order = order;
+        da.t0 = t0;
+        da.count = (int64_t)std::min<uint64_t>(SAMPLE_BATCH, S[s] - t0);
+        da.len = len;
+        da.P = weighted ? P.p : nullptr;
+        da.q = weighted ? d_q + qoff : nullptr;
+        sample_batch(g, order, s, da, weighted, raw, st);
+      }
+    }
+    qoff += len;
+  }
+  EstArgs e{};
+  for (int s = 2; s <= order; ++s) {
+    e.S[s] = (double)S[s];
+    e.E[s] = (uint64_t)g->counts[s];
+  }
+  e.weighted = weighted ? 1 : 0;
+  e.ncls = T.ncls;
+  for (int c = 0; c < T.ncls; ++c) {
+    e.maxcard[c] = (int8_t)T.maxcard[c];
+    e.countmax[c] = (int8_t)T.countmax[c];
+  }
+  k_estimate<<<1, 256, 0, st>>>(e, Q.p, raw, d_est);
+  HM_KCHECK();
+}
+
+}  // namespace hm
+
+extern "C" hm_status hm_count_sampled(hm_graph* g, int order, const uint64_t* samples_per_size,
+                                      uint64_t total_samples, uint64_t seed, const uint32_t* d_q,
+                                      double* d_est, uint64_t* d_raw, void* stream) {
+  return hm::guarded([&] {
+    HM_CHECK(g != nullptr, HM_EINVAL, "NULL graph");
+    HM_CHECK(order == 3 || order == 4, HM_EINVAL, "order must be 3 or 4");
+    HM_CHECK(order <= g->kmax, HM_EUNSUPPORTED, "order exceeds the graph's max_order");
+    HM_CHECK(d_est != nullptr, HM_EINVAL, "NULL estimate buffer");
+    int dev = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    HM_CHECK(dev == g->device, HM_EINVAL, "graph was built on another device");
+    uint64_t S[5] = {0, 0, 0, 0, 0};
+    if (samples_per_size) {
+      for (int s = 2; s <= order; ++s) S[s] = samples_per_size[s];
+    } else if (order == 4) {
+      S[2] = total_samples / 6;
+      S[4] = total_samples / 3;
+      S[3] = total_samples - S[2] - S[4];
+    } else {
+      S[2] = total_samples / 4;
+      S[3] = total_samples - S[2];
+    }
+    for (int s = 2; s <= order; ++s)
+      HM_CHECK(g->counts[s] == 0 || S[s] > 0, HM_EINVAL,
+               "a non-empty stratum has no samples (S_s == 0 with |E_s| > 0)");
+    hm::count_sampled(g, order, S, seed, d_q, d_est, d_raw, (cudaStream_t)stream);
+  });
+}

@@ -1,0 +1,80 @@
+// Kernel timing trace: when enabled, each census kernel launch is bracketed
+// by CUDA events recorded on the stream it is launched on, so a caller can
+// attribute device time to kernels without a profiler.
+#include <atomic>
+#include <cstring>
+#include <mutex>
+
+#include "hm_internal.cuh"
+
+namespace hm {
+namespace {
+
+struct Entry {
+  const char* name;
+  cudaEvent_t a, b;
+};
+
+std::mutex g_mu;
+bool g_on = false;
+std::vector<Entry> g_entries;
+
+}  // namespace
+
+bool trace_on() { return g_on; }
+
+static std::atomic<uint64_t> g_launches{0};
+uint64_t launch_count_add(uint64_t n) { return g_launches.fetch_add(n) + n; }
+
+void trace_begin(cudaStream_t s, cudaEvent_t* a) {
+  HM_CUDA(cudaEventCreate(a));
+  HM_CUDA(cudaEventRecord(*a, s));
+}
+
+void trace_end(const char* name, cudaStream_t s, cudaEvent_t a) {
+  cudaEvent_t b;
+  HM_CUDA(cudaEventCreate(&b));
+  HM_CUDA(cudaEventRecord(b, s));
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_entries.push_back(Entry{name, a, b});
+}
+
+}  // namespace hm
+
+extern "C" {
+
+uint64_t hm_launch_count(void) { return hm::launch_count_add(0); }
+
+hm_status hm_trace_enable(int on) {
+  return hm::guarded([&] {
+    std::lock_guard<std::mutex> lock(hm::g_mu);
+    hm::g_on = on != 0;
+  });
+}
+
+hm_status hm_trace_read(int max_entries, char* names, int name_len, float* ms, int* count) {
+  return hm::guarded([&] {
+    HM_CHECK(count, HM_EINVAL, "NULL count");
+    std::lock_guard<std::mutex> lock(hm::g_mu);
+    int n = 0;
+    for (auto& e : hm::g_entries) {
+      if (n < max_entries) {
+        float t = 0.f;
+        HM_CUDA(cudaEventSynchronize(e.b));
+        HM_CUDA(cudaEventElapsedTime(&t, e.a, e.b));
+        if (ms) ms[n] = t;
+        if (names && name_len > 0) {
+          std::strncpy(names + (size_t)n * name_len, e.name, name_len - 1);
+          names[(size_t)n * name_len + name_len - 1] = 0;
+        }
+        ++n;
+      }
+      cudaEventDestroy(e.a);
+      cudaEventDestroy(e.b);
+    }
+    hm::g_entries.clear();
+    *count = n;
+  });
+}
+
+}  // extern "C"

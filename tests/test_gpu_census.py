@@ -1,0 +1,167 @@
+"""GPU parity of the exact census (hm_build + hm_count_exact) against the CPU oracle.
+
+Counts are integers and must match bit for bit. Cases span tiny hypergraphs
+with every normalisation edge case, closed-form families, the workloads at
+their full sizes (stored oracle histograms), both pair-probe paths (dense
+bitmap and hash set) and the error paths of the C ABI.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2209_10241_gb300 import synth
+from tests.golden.make_golden import input_digest
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(params=["bitmap", "hash"])
+def pair_path(request, monkeypatch):
+    monkeypatch.setenv("HM_PAIR_BITMAP", "1" if request.param == "bitmap" else "0")
+    return request.param
+
+
+def _gpu_hist(hm, h, k, kmax=4):
+    g = hm.from_host(h, kmax)
+    out = hm.count_exact(g, k).cpu().numpy().astype(np.uint64)
+    return out, g
+
+
+def _oracle_hist(h, k, kmax=4):
+    return oracle.Graph.from_hypergraph(h, kmax).census(k, threads=os.cpu_count() or 1)[0]
+
+
+@pytest.mark.parametrize("seed", range(16))
+@pytest.mark.parametrize("k", [3, 4])
+def test_tiny_random(hm, pair_path, seed, k):
+    n = 6 + seed % 5
+    h = synth.random_tiny(n, 8 + 3 * seed, max_size=6, seed=seed, dup_frac=0.3)
+    got, g = _gpu_hist(hm, h, k)
+    want = _oracle_hist(h, k)
+    assert (got == want).all(), (got, want)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_denser_random(hm, pair_path, seed):
+    # many overlapping hyperedges on few nodes: every family and rule fires
+    h = synth.random_tiny(14, 160, max_size=4, seed=100 + seed, dup_frac=0.1)
+    for k in (3, 4):
+        got, _ = _gpu_hist(hm, h, k)
+        assert (got == _oracle_hist(h, k)).all()
+
+
+def test_normalised_hyperedges_match_oracle(hm):
+    h = synth.random_tiny(40, 600, max_size=6, seed=5, dup_frac=0.5)
+    g = hm.from_host(h, 4)
+    og = oracle.Graph.from_hypergraph(h, 4)
+    for s in (2, 3, 4):
+        assert g.count(s) == og.count(s)
+        assert (g.edges(s).cpu().numpy() == og.edges(s)).all()
+    assert g.counts[5] == og.count(5)
+
+
+@pytest.mark.parametrize("name", ["K7", "star9", "path12", "cycle13", "tri6", "mixed"])
+def test_closed_forms(hm, name):
+    n = 14
+    edges = {
+        "K7": [[a, b] for a in range(7) for b in range(a + 1, 7)],
+        "star9": [[0, i] for i in range(1, 10)],
+        "path12": [[i, i + 1] for i in range(11)],
+        "cycle13": [[i, (i + 1) % 13] for i in range(13)],
+        "tri6": [[a, b, c] for a in range(6) for b in range(a + 1, 6) for c in range(b + 1, 6)],
+        "mixed": [[0, 1, 2, 3], [0, 1, 2], [1, 2], [2, 3], [3, 4], [4, 5, 6], [0, 1, 2, 3, 4]],
+    }[name]
+    h = synth.from_edges(edges, n)
+    for k in (3, 4):
+        got, _ = _gpu_hist(hm, h, k)
+        assert (got == _oracle_hist(h, k)).all()
+
+
+def _golden(case):
+    with open(os.path.join(GOLDEN, f"census_{case}.json")) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("case", ["uniform-200", "f2f-330", "coauth-1m-s001"])
+@pytest.mark.parametrize("k", [3, 4])
+def test_workloads_against_stored_oracle(hm, case, k):
+    rec = _golden(case)
+    h = synth.workload(rec["workload"], seed=rec["seed"], scale=rec["scale"])
+    assert input_digest(h) == rec["input_sha256"], "generator drift: regenerate goldens"
+    got, g = _gpu_hist(hm, h, k)
+    for s in (2, 3, 4):
+        assert g.count(s) == rec["distinct_per_size"][str(s)]
+    assert got.tolist() == rec["hist"][str(k)]
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_workload_hash_path(hm, monkeypatch, k):
+    monkeypatch.setenv("HM_PAIR_BITMAP", "0")
+    rec = _golden("f2f-330")
+    h = synth.workload("f2f-330")
+    got, _ = _gpu_hist(hm, h, k)
+    assert got.tolist() == rec["hist"][str(k)]
+
+
+def test_relabel_and_duplicate_invariance(hm):
+    h = synth.workload("uniform-200")
+    base = {k: _gpu_hist(hm, h, k)[0] for k in (3, 4)}
+    st = synth.Stream(7, 1)
+    perm = np.argsort(st.u64(h.num_nodes), kind="stable").astype(np.int32)
+    edges = [list(perm[np.asarray(e)]) for e in h.edges()]
+    edges = edges[::-1] + edges[:500] + [[e[0]] for e in edges[:50]]
+    h2 = synth.from_edges(edges, h.num_nodes)
+    for k in (3, 4):
+        assert (_gpu_hist(hm, h2, k)[0] == base[k]).all()
+
+
+def test_repeated_counts_are_identical(hm):
+    h = synth.workload("uniform-200")
+    g = hm.from_host(h, 4)
+    a = hm.count_exact(g, 4).cpu()
+    b = hm.count_exact(g, 4).cpu()
+    assert torch.equal(a, b)
+
+
+def test_empty_and_degenerate_inputs(hm):
+    # no hyperedges
+    h = synth.from_edges([], 5)
+    for k in (3, 4):
+        assert _gpu_hist(hm, h, k)[0].sum() == 0
+    # singletons, repeated members only, oversized hyperedges only
+    h = synth.from_edges([[1], [2, 2, 2], [0, 1, 2, 3, 4]], 6)
+    g = hm.from_host(h, 4)
+    assert [g.count(s) for s in (2, 3, 4)] == [0, 0, 0] and g.counts[5] == 1
+    assert hm.count_exact(g, 4).sum().item() == 0
+    # a single node
+    h = synth.from_edges([[0, 0]], 1)
+    assert _gpu_hist(hm, h, 3)[0].sum() == 0
+
+
+def test_abi_errors(hm):
+    h = synth.from_edges([[0, 1], [1, 7]], 5)   # member 7 outside [0, 5)
+    with pytest.raises(hm.HMError) as e:
+        hm.from_host(h, 4)
+    assert e.value.status == 1
+    g = hm.from_host(synth.from_edges([[0, 1], [1, 2]], 3), 3)
+    with pytest.raises(hm.HMError) as e:
+        hm.count_exact(g, 4)
+    assert e.value.status == 6
+    with pytest.raises(hm.HMError) as e:
+        hm.count_exact(g, 5)
+    assert e.value.status == 1
+    assert hm.num_classes(3) == 6 and hm.num_classes(4) == 171 and hm.num_classes(5) == -1
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_class_table_matches_oracle(hm, k):
+    canon, mc, cm = oracle.class_info(k)
+    for c in range(len(canon)):
+        assert hm.class_info(k, c) == (int(canon[c]), int(mc[c]), int(cm[c]))
+    for mask in range(1 << (4 if k == 3 else 11)):
+        assert hm.class_of_mask(k, mask) == oracle.class_of(k, mask)
