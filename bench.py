@@ -32,6 +32,24 @@ UNIT = "sets/s"
 WORKLOAD = "f2f-330"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
+# Roofline of the census kernels. Their tables are L2/L1-resident on this
+# workload (ncu: DRAM traffic ~0), so they are bound by the integer/logic
+# (ALU) pipe: peak = SMs x 64 int32 lanes per clock x SM clock. Achieved =
+# work units of one launch x ALU lane-operations per unit (measured with ncu
+# on this workload, `profiles/`) / event-timed launch duration.
+SMS = 152
+ALU_LANES_PER_SM_CLK = 64
+# kernel -> (unit, ALU lane-ops per unit, DRAM bytes per launch); None = not measured
+ROOFLINE = {
+    "census_Sb": ("item", None, None),
+    "census_Pb": ("item", None, None),
+    "census_Wb": ("item", None, None),
+    "census_S": ("candidate", None, None),
+    "census_P": ("candidate", None, None),
+    "census_TX": ("candidate", None, None),
+    "census_Q": ("candidate", None, None),
+}
+
 
 def _env_int(name, default):
     try:
@@ -218,7 +236,7 @@ def main():
             g.free()
         barrier()
     hm.trace_enable(False)
-    launches = hm.launch_count() - launches0
+    gpu_launches = hm.launch_count() - launches0
     trace = hm.trace_read()
     assert int(hist.sum().item()) == sets_per_step
     t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
@@ -266,14 +284,22 @@ def main():
         c[0] += 1
         c[1] += ms
     dom = max(per, key=lambda k: per[k][1])
-    launches, dom_ms = per[dom][0], per[dom][1]
-    avg_s = dom_ms / launches / 1e3
+    dom_launches, dom_ms = per[dom][0], per[dom][1]
+    avg_s = dom_ms / dom_launches / 1e3
     peaks, src = _peaks()
-    gens = totals[dom]
-    bytes_per_gen = {"census_P": 256, "census_S": 256, "census_TX": 288, "census_Q": 320,
-                     "census_W": 64, "census_T3": 96}[dom]
-    achieved = gens * bytes_per_gen / avg_s / 1e9
     clocks = clk.summary()
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    unit, ops_per_unit, traffic = ROOFLINE.get(dom, ("item", None, None))
+    units = totals.get(dom)
+    peak_tops = SMS * ALU_LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+    achieved = (units * ops_per_unit / avg_s / 1e12) if (units and ops_per_unit) else None
+    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak_tops,
+                "unit": "Tops/s (int32 lane-ops)",
+                "frac": (achieved / peak_tops) if achieved else None, "traffic": traffic,
+                "units_per_launch": units, "unit_kind": unit, "ops_per_unit": ops_per_unit,
+                "launch_ms": avg_s * 1e3,
+                "peak_source": f"{SMS} SMs x {ALU_LANES_PER_SM_CLK} lanes x {sm_mhz:.0f} MHz "
+                               f"(sampled clock; HBM {peaks['hbm_gbs']} GB/s {src}, unused)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -286,12 +312,9 @@ def main():
         "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4),
                         "share": round(v[1] / sum(x[1] for x in per.values()), 4)}
                     for k, v in sorted(per.items(), key=lambda kv: -kv[1][1])},
-        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved,
-                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                     "peak_source": src},
+        "roofline": roofline,
         "clocks": clocks,
-        "gpu_launches": launches,
+        "gpu_launches": gpu_launches,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(h.members.nbytes + h.offsets.nbytes),
                 "d2h_bytes_per_step": ncls * 8},

@@ -197,12 +197,14 @@ def trace_read(max_entries: int = 4096):
             for i in range(cnt.value)]
 
 
-FAMILIES = {3: ("census_T3", "census_W"), 4: ("census_Q", "census_TX", "census_S", "census_P")}
+FAMILIES = {3: ("census_T3", "census_W", "census_Wb", "uses_Wb"),
+            4: ("census_Q", "census_TX", "census_S", "census_P", "census_Sb", "census_Pb",
+                "uses_Sb", "uses_Pb")}
 
 
 def work_totals(g: Graph, order: int, stream=None) -> dict:
-    """Candidates per family of the exact census {kernel name: count}."""
-    arr = (ctypes.c_uint64 * 4)()
+    """Index-space sizes of the exact census {kernel name: items} (see hm.h)."""
+    arr = (ctypes.c_uint64 * 8)()
     _check(load().hm_work_totals(g._h, order, arr, _stream(stream)))
     return {name: int(arr[i]) for i, name in enumerate(FAMILIES[order])}
 

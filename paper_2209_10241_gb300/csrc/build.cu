@@ -234,6 +234,19 @@ __global__ void k_bitmap(const uint64_t* __restrict__ e2, int64_t m, int32_t bw,
   }
 }
 
+// bits of every pair of members of each s-tuple (s = 3 or 4)
+__global__ void k_bitmap_tuples(const int4* __restrict__ e, int64_t m, int s, int32_t bw,
+                                uint32_t* __restrict__ bits) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int4 k = e[t];
+    const int32_t v[4] = {k.x, k.y, k.z, k.w};
+    for (int i = 0; i < s; ++i)
+      for (int j = 0; j < s; ++j)
+        if (i != j) atomicOr(bits + (size_t)v[i] * bw + (v[j] >> 5), 1u << (v[j] & 31));
+  }
+}
+
 __global__ void k_max_degree(const int64_t* __restrict__ off, int32_t n, int* out) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x)
@@ -431,6 +444,18 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
       k_bitmap<<<grid1d(m2), T256, 0, s>>>(g->e2, m2, g->bwords, g->bits2);
       HM_KCHECK();
     }
+    g->bits3 = keep(g, dalloc<uint32_t>(words));
+    HM_CUDA(cudaMemsetAsync(g->bits3, 0, words * sizeof(uint32_t), s));
+    if (m3) {
+      k_bitmap_tuples<<<grid1d(m3), T256, 0, s>>>(g->e3, m3, 3, g->bwords, g->bits3);
+      HM_KCHECK();
+    }
+    g->bits4 = keep(g, dalloc<uint32_t>(words));
+    HM_CUDA(cudaMemsetAsync(g->bits4, 0, words * sizeof(uint32_t), s));
+    if (m4) {
+      k_bitmap_tuples<<<grid1d(m4), T256, 0, s>>>(g->e4, m4, 4, g->bwords, g->bits4);
+      HM_KCHECK();
+    }
   }
   {
     DBuf<int> mx(1, s);
@@ -447,7 +472,7 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
 void free_graph(hm_graph* g) {
   if (!g) return;
   for (void* p : g->owned) cudaFree(p);
-  for (auto* sp : {&g->W, &g->S, &g->P, &g->TX})
+  for (auto* sp : {&g->W, &g->S, &g->P, &g->TX, &g->Wb, &g->Sb, &g->Pb})
     if (sp->ws) cudaFree(sp->ws);
   delete g;
 }

@@ -29,6 +29,7 @@
 // labelled mask in the class table; counts are aggregated per warp
 // (__match_any_sync) into shared-memory bins and flushed once per block.
 #include <cmath>
+#include <cstdlib>
 
 #include "families.cuh"
 
@@ -100,6 +101,47 @@ __global__ void __launch_bounds__(CENSUS_THREADS)
     if (bins[i]) atomicAdd(&hist[i], bins[i]);
 }
 
+// Bit-sliced families: each item evaluates up to bwords*32 candidates and
+// adds its class counts to the block's bins.
+constexpr int BITS_CHUNK = 4;
+
+template <class F>
+__global__ void __launch_bounds__(CENSUS_THREADS)
+    k_census_bits(const DevGraph g, const F fam, const uint64_t* __restrict__ ws, int64_t A,
+                  uint64_t total, const uint8_t* __restrict__ lut_g, int nmask, int ncls,
+                  unsigned long long* __restrict__ hist) {
+  __shared__ unsigned long long bins[176];
+  __shared__ uint8_t lut[2048];
+  for (int i = threadIdx.x; i < nmask; i += blockDim.x) lut[i] = lut_g[i];
+  for (int i = threadIdx.x; i < ncls; i += blockDim.x) bins[i] = 0;
+  __syncthreads();
+  const uint64_t nchunks = (total + BITS_CHUNK - 1) / BITS_CHUNK;
+  for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
+       c += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t g0 = c * BITS_CHUNK, g1 = min(g0 + BITS_CHUNK, total);
+    typename F::State st;
+    int64_t a = anchor_of(ws, A, g0);
+    uint64_t r = g0 - ws[a], wa = ws[a + 1] - ws[a];
+    fam.begin(g, a, r, st);
+    for (uint64_t gi = g0; gi < g1; ++gi) {
+      if (r == wa) {
+        do {
+          ++a;
+        } while (ws[a + 1] == ws[a]);
+        r = 0;
+        wa = ws[a + 1] - ws[a];
+        fam.begin(g, a, 0, st);
+      }
+      fam.item(g, a, st, lut, bins);
+      ++r;
+      fam.next(st);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < ncls; i += blockDim.x)
+    if (bins[i]) atomicAdd(&hist[i], bins[i]);
+}
+
 // ---------------------------------------------------------------- work spaces
 __global__ void k_ws_nodes(const int64_t* __restrict__ off2, int32_t n, int choose,
                            uint64_t* __restrict__ w) {
@@ -107,6 +149,26 @@ __global__ void k_ws_nodes(const int64_t* __restrict__ off2, int32_t n, int choo
        v += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t d = (uint64_t)(off2[v + 1] - off2[v]);
     w[v] = choose == 2 ? choose2(d) : choose3(d);
+  }
+}
+
+// bit-sliced spaces: W -> d (d >= 2), S -> C(d, 2) per node; P -> d(u) - 1 per pair (u, v)
+__global__ void k_ws_nodes_bits(const int64_t* __restrict__ off2, int32_t n, int choose,
+                                uint64_t* __restrict__ w) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t d = (uint64_t)(off2[v + 1] - off2[v]);
+    w[v] = choose == 2 ? (d >= 2 ? d : 0) : choose2(d);
+  }
+}
+
+__global__ void k_ws_pairs_bits(const uint64_t* __restrict__ e2, int64_t m,
+                                const int64_t* __restrict__ off2, uint64_t* __restrict__ w) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = (int32_t)(e2[p] >> 32), v = (int32_t)(e2[p] & 0xFFFFFFFFull);
+    const uint64_t du = (uint64_t)(off2[u + 1] - off2[u]), dv = (uint64_t)(off2[v + 1] - off2[v]);
+    w[p] = dv > 1 ? du - 1 : 0;
   }
 }
 
@@ -147,6 +209,8 @@ void ensure_space(hm_graph* g, hm_graph::Space& sp, char fam, cudaStream_t s) {
   if (fam == 'W' || fam == 'S') A = g->n;
   if (fam == 'P') A = g->counts[2];
   if (fam == 'X') A = g->kmax >= 3 ? g->counts[3] : 0;
+  if (fam == 'w' || fam == 's') A = g->n;
+  if (fam == 'p') A = g->counts[2];
   DBuf<uint64_t> w(A, s);
   uint64_t* ws = dalloc<uint64_t>((size_t)A + 1);
   try {
@@ -165,6 +229,14 @@ void ensure_space(hm_graph* g, hm_graph::Space& sp, char fam, cudaStream_t s) {
       }
       if (fam == 'X') {
         k_ws_triples<<<grid1d(A), 256, 0, s>>>(g->e3, A, g->off2, g->off3, w.p);
+        HM_KCHECK();
+      }
+      if (fam == 'w' || fam == 's') {
+        k_ws_nodes_bits<<<grid1d(A), 256, 0, s>>>(g->off2, g->n, fam == 'w' ? 2 : 3, w.p);
+        HM_KCHECK();
+      }
+      if (fam == 'p') {
+        k_ws_pairs_bits<<<grid1d(A), 256, 0, s>>>(g->e2, A, g->off2, w.p);
         HM_KCHECK();
       }
     }
@@ -198,6 +270,35 @@ int census_blocks(const void* kernel, uint64_t total) {
 }
 
 template <class F>
+void launch_bits(const hm_graph* g, const F& fam, const hm_graph::Space& sp, int order,
+                 unsigned long long* hist, cudaStream_t s) {
+  if (sp.total == 0) return;
+  const ClassTables& T = class_tables(order);
+  const uint8_t* lut = device_lut(order);
+  int blocks = census_blocks((const void*)k_census_bits<F>, sp.total);
+  // census_blocks sizes for CHUNK items per lane; bit-sliced lanes take BITS_CHUNK
+  const uint64_t need = ((sp.total + BITS_CHUNK - 1) / BITS_CHUNK + CENSUS_THREADS - 1) /
+                        CENSUS_THREADS;
+  if ((uint64_t)blocks > need) blocks = (int)(need < 1 ? 1 : need);
+  if ((uint64_t)blocks < need) {
+    int per_sm = 0, sms = 0, dev = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    HM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_census_bits<F>,
+                                                          CENSUS_THREADS, 0));
+    const uint64_t full = (uint64_t)sms * (per_sm < 1 ? 1 : per_sm);
+    blocks = (int)(need < full ? need : full);
+  }
+  cudaEvent_t ev = nullptr;
+  const bool tr = trace_on();
+  if (tr) trace_begin(s, &ev);
+  k_census_bits<F><<<blocks, CENSUS_THREADS, 0, s>>>(g->view(), fam, sp.ws, sp.anchors, sp.total,
+                                                    lut, (int)T.lut.size(), T.ncls, hist);
+  HM_KCHECK();
+  if (tr) trace_end(F::kName, s, ev);
+}
+
+template <class F>
 void launch_family(const hm_graph* g, const F& fam, const hm_graph::Space* sp, uint64_t total,
                    int order, unsigned long long* hist, cudaStream_t s) {
   if (total == 0) return;
@@ -218,27 +319,58 @@ void launch_family(const hm_graph* g, const F& fam, const hm_graph::Space* sp, u
 
 // Work spaces and launches of the census of one order; shared with the
 // null-model batch.
+// The bit-sliced variant of a family is used when its items times bitmap
+// words is well below the number of candidates it replaces (each word costs
+// a few candidates' worth of instructions). HM_DENSE_FAMILIES=0 / 1 forces
+// the per-candidate / bit-sliced variants (the latter whenever bitmaps exist).
+bool prefer_bits(const hm_graph* g, const hm_graph::Space& bits, uint64_t candidates) {
+  if (!g->bits2) return false;
+  const char* env = std::getenv("HM_DENSE_FAMILIES");
+  if (env && env[0] == '0') return false;
+  if (env && env[0] == '1') return true;
+  return (double)bits.total * (double)g->bwords * 1.5 < (double)candidates;
+}
+
 void prepare_census(hm_graph* g, int order, cudaStream_t s) {
   if (order == 3) {
     ensure_space(g, g->W, 'W', s);
+    if (g->bits2) {
+      ensure_space(g, g->Wb, 'w', s);
+      g->useWb = prefer_bits(g, g->Wb, g->W.total);
+    }
   } else {
     HM_CHECK(g->max_d2 < (1 << 21), HM_EUNSUPPORTED,
              "a node has 2^21 or more pair neighbours; order-4 star space overflows");
     ensure_space(g, g->S, 'S', s);
     ensure_space(g, g->P, 'P', s);
     ensure_space(g, g->TX, 'X', s);
+    if (g->bits2) {
+      ensure_space(g, g->Sb, 's', s);
+      ensure_space(g, g->Pb, 'p', s);
+      g->useSb = prefer_bits(g, g->Sb, g->S.total);
+      g->usePb = prefer_bits(g, g->Pb, g->P.total);
+    }
   }
 }
 
 void launch_census(const hm_graph* g, int order, unsigned long long* hist, cudaStream_t s) {
   if (order == 3) {
     launch_family(g, FamT3{}, nullptr, (uint64_t)g->counts[3], 3, hist, s);
-    launch_family(g, FamW{}, &g->W, g->W.total, 3, hist, s);
+    if (g->useWb)
+      launch_bits(g, BitsW{}, g->Wb, 3, hist, s);
+    else
+      launch_family(g, FamW{}, &g->W, g->W.total, 3, hist, s);
   } else {
     launch_family(g, FamQ{}, nullptr, (uint64_t)g->counts[4], 4, hist, s);
     launch_family(g, FamTX{}, &g->TX, g->TX.total, 4, hist, s);
-    launch_family(g, FamS{}, &g->S, g->S.total, 4, hist, s);
-    launch_family(g, FamP{}, &g->P, g->P.total, 4, hist, s);
+    if (g->useSb)
+      launch_bits(g, BitsS{}, g->Sb, 4, hist, s);
+    else
+      launch_family(g, FamS{}, &g->S, g->S.total, 4, hist, s);
+    if (g->usePb)
+      launch_bits(g, BitsP{}, g->Pb, 4, hist, s);
+    else
+      launch_family(g, FamP{}, &g->P, g->P.total, 4, hist, s);
   }
 }
 
@@ -302,14 +434,21 @@ extern "C" hm_status hm_work_totals(hm_graph* g, int order, uint64_t* totals, vo
     HM_CHECK(order == 3 || order == 4, HM_EINVAL, "order must be 3 or 4");
     HM_CHECK(order <= g->kmax, HM_EUNSUPPORTED, "order exceeds the graph's max_order");
     hm::prepare_census(g, order, (cudaStream_t)stream);
+    for (int i = 0; i < 8; ++i) totals[i] = 0;
     if (order == 3) {
       totals[0] = (uint64_t)g->counts[3];
       totals[1] = g->W.total;
+      totals[2] = g->Wb.total;
+      totals[3] = g->useWb ? 1 : 0;
     } else {
       totals[0] = (uint64_t)g->counts[4];
       totals[1] = g->TX.total;
       totals[2] = g->S.total;
       totals[3] = g->P.total;
+      totals[4] = g->Sb.total;
+      totals[5] = g->Pb.total;
+      totals[6] = g->useSb ? 1 : 0;
+      totals[7] = g->usePb ? 1 : 0;
     }
   });
 }

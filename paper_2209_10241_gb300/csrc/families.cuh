@@ -320,5 +320,209 @@ __device__ __forceinline__ int64_t anchor_of(const uint64_t* __restrict__ ws, in
   return lo;
 }
 
+// ---------------------------------------------------------------- bit-sliced families
+// On graphs small enough for dense bitmaps, the last node of W, S and P runs
+// over 32 node ids per bitmap word: the fill-in bits of 32 candidates come
+// from word-wide ANDs, the canonical rules become masks, and each candidate
+// group is counted with one popc. A 3-/4-hyperedge can only lie in a
+// candidate whose node pairs all co-occur in some 3-/4-hyperedge, so those
+// bitmaps mark the few "risky" candidates that get exact hash probes; every
+// other candidate is proven free of larger hyperedges.
+__device__ __forceinline__ const uint32_t* brow(const uint32_t* bm, int32_t bw, int32_t v) {
+  return bm + (size_t)v * bw;
+}
+__device__ __forceinline__ bool btest(const uint32_t* bm, int32_t bw, int32_t a, int32_t b) {
+  return (__ldg(bm + (size_t)a * bw + (b >> 5)) >> (b & 31)) & 1u;
+}
+// bits of word w whose node id exceeds t
+__device__ __forceinline__ uint32_t above(int32_t w, int32_t t) {
+  const int32_t tw = t >> 5;
+  if (w < tw) return 0u;
+  if (w > tw) return ~0u;
+  const int32_t b = t & 31;
+  return b == 31 ? 0u : (~0u << (b + 1));
+}
+
+// k = 3, pairs-only triples: anchor v, item x in N2(v), y over ids > x in N2(v)
+struct BitsW {
+  static constexpr const char* kName = "census_Wb";
+  struct State {
+    int64_t o;
+    uint32_t i;
+  };
+  __device__ void begin(const DevGraph& g, int64_t v, uint64_t r, State& s) const {
+    s.o = g.off2[v];
+    s.i = (uint32_t)r;
+  }
+  __device__ void next(State& s) const { ++s.i; }
+  __device__ void item(const DevGraph& g, int64_t a, State& s, const uint8_t* lut,
+                       unsigned long long* bins) const {
+    const int32_t v = (int32_t)a, bw = g.bwords;
+    const int32_t x = g.adj2[s.o + s.i];
+    const uint32_t *Bv = brow(g.bits2, bw, v), *Bx = brow(g.bits2, bw, x);
+    const uint32_t *Tv = brow(g.bits3, bw, v), *Tx = brow(g.bits3, bw, x);
+    const bool tvx = btest(g.bits3, bw, v, x);
+    const bool tri_ok = x > v;  // a triangle is kept at its smallest node
+    unsigned long long nw = 0, nt = 0;
+    for (int32_t w = x >> 5; w < bw; ++w) {
+      const uint32_t Y = __ldg(Bv + w) & above(w, x);
+      if (!Y) continue;
+      const uint32_t bx = __ldg(Bx + w);
+      const uint32_t tri = tri_ok ? (Y & bx) : 0u, wed = Y & ~bx;
+      const uint32_t risky = tvx ? (__ldg(Tv + w) & __ldg(Tx + w)) : 0u;
+      nt += __popc(tri & ~risky);
+      nw += __popc(wed & ~risky);
+      uint32_t rb = (tri | wed) & risky;
+      while (rb) {
+        const int b = __ffs(rb) - 1;
+        rb &= rb - 1;
+        if (!has_triple(g, v, x, w * 32 + b)) {
+          if ((tri >> b) & 1u)
+            ++nt;
+          else
+            ++nw;
+        }
+      }
+    }
+    if (nw) atomicAdd(&bins[lut[3]], nw);   // v=0, x=1, y=2: pairs 01, 02
+    if (nt) atomicAdd(&bins[lut[7]], nt);   // + pair 12
+  }
+};
+
+// k = 4, stars: anchor v, item x < y in N2(v), z over ids > y in N2(v)
+struct BitsS {
+  static constexpr const char* kName = "census_Sb";
+  struct State {
+    uint32_t i, j;
+    int64_t o;
+  };
+  __device__ void begin(const DevGraph& g, int64_t v, uint64_t r, State& s) const {
+    s.o = g.off2[v];
+    unrank2(r, s.i, s.j);
+  }
+  __device__ void next(State& s) const {
+    if (++s.i == s.j) {
+      s.i = 0;
+      ++s.j;
+    }
+  }
+  __device__ void item(const DevGraph& g, int64_t a, State& s, const uint8_t* lut,
+                       unsigned long long* bins) const {
+    const int32_t v = (int32_t)a, bw = g.bwords;
+    const int32_t x = g.adj2[s.o + s.i], y = g.adj2[s.o + s.j];
+    const bool tvx = btest(g.bits3, bw, v, x), tvy = btest(g.bits3, bw, v, y),
+               txy = btest(g.bits3, bw, x, y);
+    if (tvx && tvy && txy && has_triple(g, v, x, y)) return;
+    const bool qd = btest(g.bits4, bw, v, x) && btest(g.bits4, bw, v, y) &&
+                    btest(g.bits4, bw, x, y);
+    const bool xy = btest(g.bits2, bw, x, y);
+    // a node of degree 3 smaller than v rejects the set
+    const bool rx = xy && x < v, ry = xy && y < v;
+    const uint32_t *Bv = brow(g.bits2, bw, v), *Bx = brow(g.bits2, bw, x), *By = brow(g.bits2, bw, y);
+    const uint32_t *Tv = brow(g.bits3, bw, v), *Tx = brow(g.bits3, bw, x), *Ty = brow(g.bits3, bw, y);
+    const uint32_t *Qv = brow(g.bits4, bw, v), *Qx = brow(g.bits4, bw, x), *Qy = brow(g.bits4, bw, y);
+    unsigned long long c[4] = {0, 0, 0, 0};  // (xz, yz) = 00, 10, 01, 11
+    for (int32_t w = y >> 5; w < bw; ++w) {
+      const uint32_t Z = __ldg(Bv + w) & above(w, y);
+      if (!Z) continue;
+      const uint32_t bx = __ldg(Bx + w), by = __ldg(By + w);
+      uint32_t grp[4];
+      grp[0] = Z & ~bx & ~by;
+      grp[1] = rx ? 0u : (Z & bx & ~by);
+      grp[2] = ry ? 0u : (Z & ~bx & by);
+      grp[3] = (rx || ry) ? 0u : (Z & bx & by & above(w, v));
+      uint32_t risky = 0u;
+      if (tvx) risky |= __ldg(Tv + w) & __ldg(Tx + w);
+      if (tvy) risky |= __ldg(Tv + w) & __ldg(Ty + w);
+      if (txy) risky |= __ldg(Tx + w) & __ldg(Ty + w);
+      if (qd) risky |= __ldg(Qv + w) & __ldg(Qx + w) & __ldg(Qy + w);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) c[k] += __popc(grp[k] & ~risky);
+      uint32_t rb = (grp[0] | grp[1] | grp[2] | grp[3]) & risky;
+      while (rb) {
+        const int b = __ffs(rb) - 1;
+        rb &= rb - 1;
+        const int32_t z = w * 32 + b;
+        if (has_triple(g, v, x, z) || has_triple(g, v, y, z) || has_triple(g, x, y, z) ||
+            has_quad(g, v, x, y, z))
+          continue;
+        ++c[((bx >> b) & 1u) | (((by >> b) & 1u) << 1)];
+      }
+    }
+    const uint32_t base = 7u | (xy ? 8u : 0u);  // v=0, x=1, y=2, z=3
+    if (c[0]) atomicAdd(&bins[lut[base]], c[0]);
+    if (c[1]) atomicAdd(&bins[lut[base | 16u]], c[1]);
+    if (c[2]) atomicAdd(&bins[lut[base | 32u]], c[2]);
+    if (c[3]) atomicAdd(&bins[lut[base | 48u]], c[3]);
+  }
+};
+
+// k = 4, paths and 4-cycles: anchor pair (u, v), u < v, item x in N2(u)\{v},
+// y over N2(v) \ N2[u]
+struct BitsP {
+  static constexpr const char* kName = "census_Pb";
+  struct State {
+    int32_t u, v;
+    int64_t ou;
+    uint32_t pu, i;
+  };
+  __device__ void begin(const DevGraph& g, int64_t p, uint64_t r, State& s) const {
+    const uint64_t uv = g.e2[p];
+    s.u = (int32_t)(uv >> 32);
+    s.v = (int32_t)(uv & 0xFFFFFFFFull);
+    s.ou = g.off2[s.u];
+    s.pu = (uint32_t)g.pairpos[p].x;
+    s.i = (uint32_t)r;
+  }
+  __device__ void next(State& s) const { ++s.i; }
+  __device__ void item(const DevGraph& g, int64_t, State& s, const uint8_t* lut,
+                       unsigned long long* bins) const {
+    const int32_t u = s.u, v = s.v, bw = g.bwords;
+    const int32_t x = g.adj2[s.ou + s.i + (s.i >= s.pu ? 1 : 0)];
+    if (btest(g.bits2, bw, v, x)) return;  // v would have degree 3: family S
+    const bool tuv = btest(g.bits3, bw, u, v), tux = btest(g.bits3, bw, u, x),
+               tvx = btest(g.bits3, bw, v, x);
+    if (tuv && tux && tvx && has_triple(g, u, v, x)) return;
+    const bool qd = btest(g.bits4, bw, u, v) && btest(g.bits4, bw, u, x) &&
+                    btest(g.bits4, bw, v, x);
+    const bool c4ok = x > v;  // a 4-cycle is kept at its smallest pair: x > v, y > u
+    const uint32_t *Bu = brow(g.bits2, bw, u), *Bv = brow(g.bits2, bw, v), *Bx = brow(g.bits2, bw, x);
+    const uint32_t *Tu = brow(g.bits3, bw, u), *Tv = brow(g.bits3, bw, v), *Tx = brow(g.bits3, bw, x);
+    const uint32_t *Qu = brow(g.bits4, bw, u), *Qv = brow(g.bits4, bw, v), *Qx = brow(g.bits4, bw, x);
+    const int32_t uw = u >> 5;
+    const uint32_t ubit = 1u << (u & 31);
+    unsigned long long np = 0, nc = 0;
+    for (int32_t w = 0; w < bw; ++w) {
+      uint32_t Y = __ldg(Bv + w) & ~__ldg(Bu + w);
+      if (w == uw) Y &= ~ubit;
+      if (!Y) continue;
+      const uint32_t bx = __ldg(Bx + w);
+      const uint32_t c4 = c4ok ? (Y & bx & above(w, u)) : 0u, p4 = Y & ~bx;
+      uint32_t risky = 0u;
+      if (tuv) risky |= __ldg(Tu + w) & __ldg(Tv + w);
+      if (tux) risky |= __ldg(Tu + w) & __ldg(Tx + w);
+      if (tvx) risky |= __ldg(Tv + w) & __ldg(Tx + w);
+      if (qd) risky |= __ldg(Qu + w) & __ldg(Qv + w) & __ldg(Qx + w);
+      np += __popc(p4 & ~risky);
+      nc += __popc(c4 & ~risky);
+      uint32_t rb = (c4 | p4) & risky;
+      while (rb) {
+        const int b = __ffs(rb) - 1;
+        rb &= rb - 1;
+        const int32_t y = w * 32 + b;
+        if (has_triple(g, u, v, y) || has_triple(g, u, x, y) || has_triple(g, v, x, y) ||
+            has_quad(g, u, v, x, y))
+          continue;
+        if ((c4 >> b) & 1u)
+          ++nc;
+        else
+          ++np;
+      }
+    }
+    if (np) atomicAdd(&bins[lut[19]], np);  // u=0, v=1, x=2, y=3: pairs 01, 02, 13
+    if (nc) atomicAdd(&bins[lut[51]], nc);  // + pair 23
+  }
+};
+
 }  // namespace fam
 }  // namespace hm

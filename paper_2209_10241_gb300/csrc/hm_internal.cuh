@@ -171,8 +171,12 @@ struct DevGraph {
   const int32_t* inc3;
   // per pair p = (u, v): position of v in N2(u) and of u in N2(v)
   const int2* pairpos;
-  // optional dense pair-adjacency bitmap: row u holds bwords 32-bit words
+  // optional dense bitmaps, row u holding bwords 32-bit words: bits2 = pair
+  // adjacency; bits3 / bits4 = u and v lie together in some 3- / 4-hyperedge
+  // (a filter: a 3-hyperedge {a,b,c} can only exist if all its pairs are set)
   const uint32_t* bits2;
+  const uint32_t* bits3;
+  const uint32_t* bits4;
   int32_t bwords;
 };
 
@@ -290,6 +294,8 @@ struct hm_graph {
   int32_t* inc3 = nullptr;
   int2* pairpos = nullptr;
   uint32_t* bits2 = nullptr;
+  uint32_t* bits3 = nullptr;
+  uint32_t* bits4 = nullptr;
   int32_t bwords = 0;
   int32_t max_d2 = 0;
   // cached work spaces (prefix sums over anchors), per family
@@ -300,6 +306,10 @@ struct hm_graph {
     bool ready = false;
   };
   Space W, S, P, TX;
+  // bit-sliced variants of W, S, P (dense graphs): items are (anchor, first
+  // neighbour[s]) and the last node runs over bitmap words
+  Space Wb, Sb, Pb;
+  bool useWb = false, useSb = false, usePb = false;
   std::vector<void*> owned;  // everything above, for hm_free
 
   hm::DevGraph view() const {
@@ -323,6 +333,8 @@ struct hm_graph {
     g.inc3 = inc3;
     g.pairpos = pairpos;
     g.bits2 = bits2;
+    g.bits3 = bits3;
+    g.bits4 = bits4;
     g.bwords = bwords;
     return g;
   }

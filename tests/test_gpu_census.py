@@ -2,8 +2,9 @@
 
 Counts are integers and must match bit for bit. Cases span tiny hypergraphs
 with every normalisation edge case, closed-form families, the workloads at
-their full sizes (stored oracle histograms), both pair-probe paths (dense
-bitmap and hash set) and the error paths of the C ABI.
+their full sizes (stored oracle histograms), every candidate-evaluation path
+(pair probes in the hash set or the dense bitmap, per-candidate or
+bit-sliced families) and the error paths of the C ABI.
 """
 import json
 import os
@@ -20,9 +21,12 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-@pytest.fixture(params=["bitmap", "hash"])
+@pytest.fixture(params=["hash", "bitmap", "sliced"])
 def pair_path(request, monkeypatch):
-    monkeypatch.setenv("HM_PAIR_BITMAP", "1" if request.param == "bitmap" else "0")
+    """hash: pair probes in the hash set; bitmap: pair probes in the dense
+    bitmap, one candidate at a time; sliced: bit-sliced W/S/P families."""
+    monkeypatch.setenv("HM_PAIR_BITMAP", "0" if request.param == "hash" else "1")
+    monkeypatch.setenv("HM_DENSE_FAMILIES", "1" if request.param == "sliced" else "0")
     return request.param
 
 
@@ -66,7 +70,7 @@ def test_normalised_hyperedges_match_oracle(hm):
 
 
 @pytest.mark.parametrize("name", ["K7", "star9", "path12", "cycle13", "tri6", "mixed"])
-def test_closed_forms(hm, name):
+def test_closed_forms(hm, pair_path, name):
     n = 14
     edges = {
         "K7": [[a, b] for a in range(7) for b in range(a + 1, 7)],
@@ -99,16 +103,19 @@ def test_workloads_against_stored_oracle(hm, case, k):
     assert got.tolist() == rec["hist"][str(k)]
 
 
+@pytest.mark.parametrize("case", ["f2f-330", "coauth-1m-s001"])
 @pytest.mark.parametrize("k", [3, 4])
-def test_workload_hash_path(hm, monkeypatch, k):
-    monkeypatch.setenv("HM_PAIR_BITMAP", "0")
-    rec = _golden("f2f-330")
-    h = synth.workload("f2f-330")
+@pytest.mark.parametrize("mode", ["hash", "bitmap", "sliced"])
+def test_workload_every_path(hm, monkeypatch, case, k, mode):
+    monkeypatch.setenv("HM_PAIR_BITMAP", "0" if mode == "hash" else "1")
+    monkeypatch.setenv("HM_DENSE_FAMILIES", "1" if mode == "sliced" else "0")
+    rec = _golden(case)
+    h = synth.workload(rec["workload"], seed=rec["seed"], scale=rec["scale"])
     got, _ = _gpu_hist(hm, h, k)
     assert got.tolist() == rec["hist"][str(k)]
 
 
-def test_relabel_and_duplicate_invariance(hm):
+def test_relabel_and_duplicate_invariance(hm, pair_path):
     h = synth.workload("uniform-200")
     base = {k: _gpu_hist(hm, h, k)[0] for k in (3, 4)}
     st = synth.Stream(7, 1)
