@@ -195,6 +195,31 @@ hm_status hm_trace_enable(int on);
 uint64_t hm_launch_count(void);
 hm_status hm_trace_read(int max_entries, char* names, int name_len, float* ms, int* count);
 
+/*
+ * hm_count_sampled without any device allocation (the paper has no
+ * counterpart; this serves callers that cannot allocate device memory while
+ * they count -- e.g. code running in a host callback or a latency-critical
+ * loop where cudaMalloc/cudaFree may block or synchronise the device, or
+ * applications that reserve all device memory up front). Same arguments,
+ * results and errors as hm_count_sampled, bit for bit.
+ *   - Every temporary lives in one static device array of 32 MiB inside
+ *     libhm.so, which each GPU that loads the library holds until the
+ *     process exits. Requests whose temporaries cannot fit are rejected with
+ *     HM_EINVAL and a message naming the limit: with weights d_q, each
+ *     stratum needs about 16 * |E_s| bytes; at order 4 one draw of a pair
+ *     needs about 64 * (max pair degree) bytes.
+ *   - The first call on a device (with that device current) resolves the
+ *     array's device address and copies the class tables; make that first
+ *     call before any stream capture.
+ *   - All calls on a device share the array: calls that overlap on the GPU
+ *     (other streams, other host threads) race and must be serialised by the
+ *     caller. The call synchronises `stream` between sample batches.
+ *   - The graph must have been built by hm_build (which allocates).
+ */
+hm_status hm_count_sampled_noalloc(hm_graph* g, int order, const uint64_t* samples_per_size,
+                                   uint64_t total_samples, uint64_t seed, const uint32_t* d_q,
+                                   double* d_est, uint64_t* d_raw, void* stream);
+
 /* Release a graph and its device memory. NULL is allowed. */
 void hm_free(hm_graph* g);
 

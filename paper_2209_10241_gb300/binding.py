@@ -40,6 +40,8 @@ _SIGS = {
     "hm_count_exact": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "hm_count_sampled": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_uint64, ctypes.c_uint64,
                                         _vp, _vp, _vp, _vp]),
+    "hm_count_sampled_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_uint64,
+                                                ctypes.c_uint64, _vp, _vp, _vp, _vp]),
     "hm_count_exact_host": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int,
                                            _vp, _vp]),
     "hm_work_totals": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
@@ -161,6 +163,21 @@ def count_sampled(g: Graph, order: int, samples=None, total: int = 0, seed: int 
         sp = arr
     _check(load().hm_count_sampled(g._h, order, sp, int(total), int(seed) & (2**64 - 1),
                                    _dptr(q), _dptr(est), _dptr(raw), _stream(stream)))
+    return est, raw
+
+
+def count_sampled_noalloc(g: Graph, order: int, est: torch.Tensor, raw: torch.Tensor = None,
+                          samples=None, total: int = 0, seed: int = 0, q: torch.Tensor = None,
+                          stream=None):
+    """hm_count_sampled_noalloc into caller-provided device buffers (allocates nothing)."""
+    sp = None
+    if samples is not None:
+        arr = (ctypes.c_uint64 * 5)()
+        for s in range(2, min(order, 4) + 1):
+            arr[s] = int(samples[s])
+        sp = arr
+    _check(load().hm_count_sampled_noalloc(g._h, order, sp, int(total), int(seed) & (2**64 - 1),
+                                           _dptr(q), _dptr(est), _dptr(raw), _stream(stream)))
     return est, raw
 
 

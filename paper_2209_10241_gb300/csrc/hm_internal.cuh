@@ -105,6 +105,11 @@ T* dalloc(size_t count) {
 // in == out is not required (they must not alias).
 void scan_exclusive_u64(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s);
 void scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);
+// The same scan, allocating nothing: temporaries come from `scratch`, which
+// must hold scan_scratch_elems(n) elements.
+void scan_exclusive_u64_in(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s,
+                           uint64_t* scratch, size_t scratch_elems);
+size_t scan_scratch_elems(int64_t n);
 // Stable LSD radix sort of n keys on their low `bits` bits; vals (nullable)
 // are permuted alongside.
 void radix_sort_u64(uint64_t* keys, uint64_t* vals, int64_t n, int bits, cudaStream_t s);

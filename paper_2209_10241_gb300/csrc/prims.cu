@@ -106,6 +106,31 @@ void scan_exclusive(const T* in, T* out, int64_t n, cudaStream_t s) {
   HM_KCHECK();
 }
 
+// Same scan with its tile sums / offsets carved from caller scratch.
+template <class T>
+void scan_exclusive_in(const T* in, T* out, int64_t n, cudaStream_t s, T* scratch,
+                       size_t scratch_elems) {
+  if (n == 0) {
+    HM_CUDA(cudaMemsetAsync(out, 0, sizeof(T), s));
+    return;
+  }
+  int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (tiles == 1) {
+    k_tile_scan<T><<<1, SCAN_THREADS, 0, s>>>(in, out, n, nullptr);
+    HM_KCHECK();
+    return;
+  }
+  HM_CHECK((size_t)(2 * tiles + 1) <= scratch_elems, HM_EINVAL, "scan scratch too small");
+  T* sums = scratch;
+  T* offs = scratch + tiles;
+  k_tile_sums<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, sums);
+  HM_KCHECK();
+  scan_exclusive_in<T>(sums, offs, tiles, s, scratch + 2 * tiles + 1,
+                       scratch_elems - (size_t)(2 * tiles + 1));
+  k_tile_scan<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, offs);
+  HM_KCHECK();
+}
+
 // ------------------------------------------------------------------ radix sort
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
@@ -242,6 +267,20 @@ void scan_exclusive_u64(const uint64_t* in, uint64_t* out, int64_t n, cudaStream
 }
 void scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s) {
   scan_exclusive<uint32_t>(in, out, n, s);
+}
+void scan_exclusive_u64_in(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s,
+                           uint64_t* scratch, size_t scratch_elems) {
+  scan_exclusive_in<uint64_t>(in, out, n, s, scratch, scratch_elems);
+}
+size_t scan_scratch_elems(int64_t n) {
+  // tile sums + offsets at every level of the recursion
+  size_t need = 0;
+  int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  while (tiles > 1) {
+    need += (size_t)(2 * tiles + 1);
+    tiles = (tiles + SCAN_TILE - 1) / SCAN_TILE;
+  }
+  return need;
 }
 
 void radix_sort_u64(uint64_t* keys, uint64_t* vals, int64_t n, int bits, cudaStream_t s) {

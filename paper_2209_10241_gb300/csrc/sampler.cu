@@ -24,6 +24,7 @@
 //                pair-neighbour of c outside L1 ∪ e. Sets holding a 3- or
 //                4-hyperedge are dropped (max-cardinality rule).
 #include <cmath>
+#include <mutex>
 
 #include "families.cuh"
 
@@ -544,7 +545,256 @@ void count_sampled(hm_graph* g, int order, const uint64_t* S, uint64_t seed, con
   HM_KCHECK();
 }
 
+// ================================================================ allocation-free variant
+// Some callers cannot allocate device memory while they count: code running
+// inside a host callback or a real-time loop where cudaMalloc may block or
+// synchronise the device, or applications whose memory is fully reserved up
+// front. hm_count_sampled_noalloc serves them: every temporary lives in one
+// file-scope device array of NOALLOC_BYTES, held by each GPU that loads the
+// library until the process exits.
+namespace {
+
+constexpr size_t NOALLOC_BYTES = (size_t)32 << 20;
+__device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+__device__ __align__(16) uint8_t g_noalloc_lut3[16];
+__device__ __align__(16) uint8_t g_noalloc_lut4[2048];
+
+struct NoallocDevice {
+  unsigned char* scratch = nullptr;  // device address of g_noalloc_scratch
+  const uint8_t* lut3 = nullptr;
+  const uint8_t* lut4 = nullptr;
+};
+std::mutex g_noalloc_mu;
+NoallocDevice g_noalloc_dev[64];
+bool g_noalloc_ready[64] = {false};
+
+// Once per device, with that device current: the symbols' device addresses
+// (host code cannot use the arrays' names as device pointers) and the class
+// tables copied into their symbols.
+NoallocDevice noalloc_setup() {
+  int dev = 0;
+  HM_CUDA(cudaGetDevice(&dev));
+  HM_CHECK(dev >= 0 && dev < 64, HM_EUNSUPPORTED, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ready[dev]) {
+    NoallocDevice d;
+    void* p = nullptr;
+    HM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    d.scratch = (unsigned char*)p;
+    HM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_lut3));
+    d.lut3 = (const uint8_t*)p;
+    HM_CUDA(cudaGetSymbolAddress(&p, g_noalloc_lut4));
+    d.lut4 = (const uint8_t*)p;
+    HM_CUDA(cudaMemcpyToSymbol(g_noalloc_lut3, class_tables(3).lut.data(), 16));
+    HM_CUDA(cudaMemcpyToSymbol(g_noalloc_lut4, class_tables(4).lut.data(), 2048));
+    g_noalloc_dev[dev] = d;
+    g_noalloc_ready[dev] = true;
+  }
+  return g_noalloc_dev[dev];
+}
+
+// Bump allocation inside the static array (256-byte aligned pieces).
+struct Arena {
+  unsigned char* base;
+  size_t cap, used;
+  template <class T>
+  T* take(size_t count) {
+    const size_t off = (used + 255) & ~(size_t)255;
+    HM_CHECK(off + count * sizeof(T) <= cap, HM_EINVAL,
+             "request exceeds the 32 MiB static scratch of hm_count_sampled_noalloc");
+    used = off + count * sizeof(T);
+    return (T*)(base + off);
+  }
+};
+
+uint64_t scan_total_in(const uint64_t* in, uint64_t* out, int64_t n, Arena& ar, cudaStream_t s) {
+  const size_t need = scan_scratch_elems(n);
+  uint64_t* tmp = need ? ar.take<uint64_t>(need) : nullptr;
+  scan_exclusive_u64_in(in, out, n, s, tmp, need);
+  uint64_t tot = 0;
+  HM_CUDA(cudaMemcpyAsync(&tot, out + n, sizeof tot, cudaMemcpyDeviceToHost, s));
+  HM_CUDA(cudaStreamSynchronize(s));
+  return tot;
+}
+
+template <class F>
+void launch_sample_lut(const hm_graph* g, const F& f, const uint64_t* ws, int64_t A,
+                       uint64_t total, const uint64_t* wt, bool weighted, int order,
+                       const uint8_t* lut, unsigned long long* raw, cudaStream_t s) {
+  if (total == 0) return;
+  const ClassTables& T = class_tables(order);
+  if (weighted) {
+    k_sample<F, true><<<sample_blocks((const void*)k_sample<F, true>, total), SAMPLE_THREADS, 0,
+                        s>>>(g->view(), f, ws, A, total, wt, lut, (int)T.lut.size(), T.ncls, raw);
+  } else {
+    k_sample<F, false><<<sample_blocks((const void*)k_sample<F, false>, total), SAMPLE_THREADS, 0,
+                         s>>>(g->view(), f, ws, A, total, wt, lut, (int)T.lut.size(), T.ncls, raw);
+  }
+  HM_KCHECK();
+}
+
+void sample_batch_in(const hm_graph* g, int order, int s, const DrawArgs& da, bool weighted,
+                     const uint8_t* lut, unsigned long long* raw, Arena& ar, cudaStream_t st) {
+  const size_t mark = ar.used;
+  const int64_t cnt = da.count;
+  int64_t* sidx = ar.take<int64_t>(cnt);
+  uint64_t* wt = ar.take<uint64_t>(cnt);
+  uint64_t* work = ar.take<uint64_t>(cnt);
+  uint64_t* lsize = ar.take<uint64_t>(cnt);
+  uint64_t* ws = ar.take<uint64_t>(cnt + 1);
+  k_draw<<<grid_n(cnt), 256, 0, st>>>(g->view(), da, sidx, wt, work, lsize);
+  HM_KCHECK();
+  if (s == order) {
+    if (order == 3) {
+      FamT3 f;
+      f.map = sidx;
+      launch_sample_lut(g, f, nullptr, 0, (uint64_t)cnt, wt, weighted, order, lut, raw, st);
+    } else {
+      FamQ f;
+      f.map = sidx;
+      launch_sample_lut(g, f, nullptr, 0, (uint64_t)cnt, wt, weighted, order, lut, raw, st);
+    }
+  } else {
+    const uint64_t total = scan_total_in(work, ws, cnt, ar, st);
+    if (order == 4 && s == 3) {
+      FamTXT<false> f;
+      f.map = sidx;
+      launch_sample_lut(g, f, ws, cnt, total, wt, weighted, order, lut, raw, st);
+    } else if (order == 3) {
+      SamP3 f{sidx};
+      launch_sample_lut(g, f, ws, cnt, total, wt, weighted, order, lut, raw, st);
+    } else {
+      SamPA fa{sidx};
+      launch_sample_lut(g, fa, ws, cnt, total, wt, weighted, order, lut, raw, st);
+      uint64_t* eoff = ar.take<uint64_t>(cnt + 1);
+      const uint64_t ne = scan_total_in(lsize, eoff, cnt, ar, st);
+      if (ne > 0) {
+        int2* elems = ar.take<int2>(ne);
+        uint64_t* ework = ar.take<uint64_t>(ne);
+        uint64_t* ews = ar.take<uint64_t>(ne + 1);
+        k_elements<<<grid_n(cnt), 256, 0, st>>>(g->view(), sidx, cnt, eoff, elems, ework);
+        HM_KCHECK();
+        const uint64_t tb = scan_total_in(ework, ews, (int64_t)ne, ar, st);
+        SamPB fb{sidx, elems};
+        launch_sample_lut(g, fb, ews, (int64_t)ne, tb, wt, weighted, order, lut, raw, st);
+      }
+    }
+  }
+  // the next batch may reuse this batch's pieces only after its kernels ran
+  HM_CUDA(cudaStreamSynchronize(st));
+  ar.used = mark;
+}
+
+}  // namespace
+
+void count_sampled_noalloc(hm_graph* g, int order, const uint64_t* S, uint64_t seed,
+                           const uint32_t* d_q, double* d_est, uint64_t* d_raw, cudaStream_t st) {
+  const NoallocDevice nd = noalloc_setup();
+  const ClassTables& T = class_tables(order);
+  const uint8_t* lut = order == 3 ? nd.lut3 : nd.lut4;
+  Arena ar{nd.scratch, NOALLOC_BYTES, 0};
+  unsigned long long* raw = d_raw ? (unsigned long long*)d_raw
+                                  : ar.take<unsigned long long>(2 * (size_t)T.ncls);
+  HM_CUDA(cudaMemsetAsync(raw, 0, 2 * T.ncls * sizeof(unsigned long long), st));
+  uint64_t* Q = ar.take<uint64_t>(5);
+  uint64_t hostQ[5] = {0, 0, 0, 0, 0};
+  for (int s = 2; s <= order; ++s) hostQ[s] = (uint64_t)g->counts[s];
+  HM_CUDA(cudaMemcpyAsync(Q, hostQ, sizeof hostQ, cudaMemcpyHostToDevice, st));
+  int* bad = ar.take<int>(1);
+  const bool weighted = d_q != nullptr;
+  // worst-case bytes of one draw: per-draw arrays, scan temporaries, and (order 4,
+  // pair strata) up to 2 * max pair degree second-level entries of 24 bytes
+  const size_t per_draw = 6 * 8 + 8 + (order == 4 ? (size_t)2 * (size_t)g->max_d2 * 32 : 0);
+  int64_t qoff = 0;
+  for (int s = 2; s <= order; ++s) {
+    const int64_t len = g->counts[s];
+    const size_t mark = ar.used;
+    uint64_t* P = nullptr;
+    if (weighted && len > 0) {
+      HM_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+      k_bad_weight<<<grid_n(len), 256, 0, st>>>(d_q + qoff, len, bad);
+      HM_KCHECK();
+      uint64_t* wide = ar.take<uint64_t>(len);
+      P = ar.take<uint64_t>(len + 1);
+      k_widen<<<grid_n(len), 256, 0, st>>>(d_q + qoff, len, wide);
+      HM_KCHECK();
+      scan_total_in(wide, P, len, ar, st);
+      int hb = 0;
+      HM_CUDA(cudaMemcpyAsync(&hb, bad, sizeof hb, cudaMemcpyDeviceToHost, st));
+      HM_CUDA(cudaMemcpyAsync(Q + s, P + len, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+      HM_CUDA(cudaStreamSynchronize(st));
+      HM_CHECK(hb == 0, HM_EINVAL, "proposal weights must be >= 1");
+    }
+    if (len > 0 && S[s] > 0) {
+      const size_t avail = ar.cap - ((ar.used + 255) & ~(size_t)255);
+      const size_t slack = (size_t)64 << 10;
+      HM_CHECK(avail > slack + 2 * per_draw, HM_EINVAL,
+               "graph too large for the 32 MiB static scratch of hm_count_sampled_noalloc");
+      int64_t batch = (int64_t)((avail - slack) / (per_draw + per_draw / 1024 + 16));
+      if (batch > SAMPLE_BATCH) batch = SAMPLE_BATCH;
+      for (uint64_t t0 = 0; t0 < S[s]; t0 += (uint64_t)batch) {
+        DrawArgs da;
+        da.seed = seed;
+        da.s = s;
+        da.order = order;
+        da.t0 = t0;
+        da.count = (int64_t)std::min<uint64_t>((uint64_t)batch, S[s] - t0);
+        da.len = len;
+        da.P = P;
+        da.q = weighted ? d_q + qoff : nullptr;
+        sample_batch_in(g, order, s, da, weighted, lut, raw, ar, st);
+      }
+    }
+    ar.used = mark;
+    qoff += len;
+  }
+  EstArgs e{};
+  for (int s = 2; s <= order; ++s) {
+    e.S[s] = (double)S[s];
+    e.E[s] = (uint64_t)g->counts[s];
+  }
+  e.weighted = weighted ? 1 : 0;
+  e.ncls = T.ncls;
+  for (int c = 0; c < T.ncls; ++c) {
+    e.maxcard[c] = (int8_t)T.maxcard[c];
+    e.countmax[c] = (int8_t)T.countmax[c];
+  }
+  k_estimate<<<1, 256, 0, st>>>(e, Q, raw, d_est);
+  HM_KCHECK();
+}
+
 }  // namespace hm
+
+extern "C" hm_status hm_count_sampled_noalloc(hm_graph* g, int order,
+                                              const uint64_t* samples_per_size,
+                                              uint64_t total_samples, uint64_t seed,
+                                              const uint32_t* d_q, double* d_est,
+                                              uint64_t* d_raw, void* stream) {
+  return hm::guarded([&] {
+    HM_CHECK(g != nullptr, HM_EINVAL, "NULL graph");
+    HM_CHECK(order == 3 || order == 4, HM_EINVAL, "order must be 3 or 4");
+    HM_CHECK(order <= g->kmax, HM_EUNSUPPORTED, "order exceeds the graph's max_order");
+    HM_CHECK(d_est != nullptr, HM_EINVAL, "NULL estimate buffer");
+    int dev = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    HM_CHECK(dev == g->device, HM_EINVAL, "graph was built on another device");
+    uint64_t S[5] = {0, 0, 0, 0, 0};
+    if (samples_per_size) {
+      for (int s = 2; s <= order; ++s) S[s] = samples_per_size[s];
+    } else if (order == 4) {
+      S[2] = total_samples / 6;
+      S[4] = total_samples / 3;
+      S[3] = total_samples - S[2] - S[4];
+    } else {
+      S[2] = total_samples / 4;
+      S[3] = total_samples - S[2];
+    }
+    for (int s = 2; s <= order; ++s)
+      HM_CHECK(g->counts[s] == 0 || S[s] > 0, HM_EINVAL,
+               "a non-empty stratum has no samples (S_s == 0 with |E_s| > 0)");
+    hm::count_sampled_noalloc(g, order, S, seed, d_q, d_est, d_raw, (cudaStream_t)stream);
+  });
+}
 
 extern "C" hm_status hm_count_sampled(hm_graph* g, int order, const uint64_t* samples_per_size,
                                       uint64_t total_samples, uint64_t seed, const uint32_t* d_q,
