@@ -608,13 +608,13 @@ int64_t orc_sample(void* gp, int k, const uint64_t* samples, uint64_t seed, cons
 
 // Stub-shuffling null model (configuration-model stand-in, Sec. 6.3): the
 // stubs (members in input order) are reordered by the keys
-// (draw64(seed, i, model, TAG_NULL), i) and cut again into the input sizes.
-// out_members has offsets[m] entries; the offsets stay the same.
+// (draw64(seed, i, model, TAG_NULL) >> 6, i) and cut again into the input
+// sizes. out_members has offsets[m] entries; the offsets stay the same.
 void orc_stub_shuffle(const int32_t* members, const int64_t* offsets, int64_t m, uint64_t seed,
                       uint32_t model, int32_t* out_members) {
   int64_t M = offsets[m];
   std::vector<std::pair<uint64_t, int64_t>> key(M);
-  for (int64_t i = 0; i < M; ++i) key[i] = {draw64(seed, (uint64_t)i, model, TAG_NULL), i};
+  for (int64_t i = 0; i < M; ++i) key[i] = {draw64(seed, (uint64_t)i, model, TAG_NULL) >> 6, i};
   std::sort(key.begin(), key.end());
   for (int64_t i = 0; i < M; ++i) out_members[i] = members[key[i].second];
 }
