@@ -40,14 +40,15 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SMS = 152
 ALU_LANES_PER_SM_CLK = 64
 # kernel -> (unit, ALU lane-ops per unit, DRAM bytes per launch); None = not measured
+# (ops = sm__sass_thread_inst_executed_op_{integer,bit}_pred_on per unit, profiles/census_bits_f2f-330.md)
 ROOFLINE = {
-    "census_Sb": ("item", None, None),
-    "census_Pb": ("item", None, None),
+    "census_Sb": ("item", 969.4, 1_025_000),
+    "census_Pb": ("item", 987.9, 820_000),
+    "census_TX": ("candidate", 283.6, 656_000),
+    "census_Q": ("candidate", 384.6, 298_000),
     "census_Wb": ("item", None, None),
     "census_S": ("candidate", None, None),
     "census_P": ("candidate", None, None),
-    "census_TX": ("candidate", None, None),
-    "census_Q": ("candidate", None, None),
 }
 
 
