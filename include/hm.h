@@ -196,6 +196,34 @@ uint64_t hm_launch_count(void);
 hm_status hm_trace_read(int max_entries, char* names, int name_len, float* ms, int* count);
 
 /*
+ * Null-model batch: the counting step repeated on randomised hypergraphs
+ * (Sec. 6.3 compares observed frequencies with those of configuration-model
+ * draws; the model is realised here as stub shuffling). For base b in
+ * [0, num_bases) and j in [0, models_per_base), model t = b*models_per_base+j
+ * is base b's stubs (its members in input order) reordered by the keys
+ * (v >> 6, i), v = (r0 << 32) | r1 of Philox4x32-10 with key = seed and
+ * counter (i lo, i hi, t, 0x4E554C4C), cut again into the base's hyperedge
+ * sizes, normalised as by hm_build, and counted exactly at `order` as by
+ * hm_count_exact.
+ *   d_members, d_offsets  every base's hyperedges in one CSR (device; offsets
+ *                         index d_members globally)
+ *   h_base_edges          host int64[num_bases + 1]: base b owns hyperedges
+ *                         [h_base_edges[b], h_base_edges[b+1])
+ *   h_num_nodes           host int32[num_nodes]: base b's ids lie in [0, n_b)
+ *   d_hists               device uint64[num_bases * models_per_base *
+ *                         hm_num_classes(order)]; row t = model t
+ * Up to 64 models are counted together as one disjoint union (model t's node
+ * v becomes t * max(n_b) + v): one ingest and one persistent launch per
+ * candidate family for the whole group, whatever the models' sizes.
+ * Synchronous. Errors: HM_EINVAL (bad ranges, max(n_b) * 64 >= 2^31, a member
+ * outside its base's [0, n_b)), HM_ENOMEM, HM_ECUDA.
+ */
+hm_status hm_count_null_batch(int num_bases, const int32_t* d_members, const int64_t* d_offsets,
+                              const int64_t* h_base_edges, const int32_t* h_num_nodes, int order,
+                              int models_per_base, uint64_t seed, uint64_t* d_hists,
+                              void* stream);
+
+/*
  * hm_count_sampled without any device allocation (the paper has no
  * counterpart; this serves callers that cannot allocate device memory while
  * they count -- e.g. code running in a host callback or a latency-critical

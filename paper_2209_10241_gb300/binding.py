@@ -42,6 +42,8 @@ _SIGS = {
                                         _vp, _vp, _vp, _vp]),
     "hm_count_sampled_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_uint64,
                                                 ctypes.c_uint64, _vp, _vp, _vp, _vp]),
+    "hm_count_null_batch": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_uint64, _vp, _vp]),
     "hm_count_exact_host": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int,
                                            _vp, _vp]),
     "hm_work_totals": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
@@ -179,6 +181,29 @@ def count_sampled_noalloc(g: Graph, order: int, est: torch.Tensor, raw: torch.Te
     _check(load().hm_count_sampled_noalloc(g._h, order, sp, int(total), int(seed) & (2**64 - 1),
                                            _dptr(q), _dptr(est), _dptr(raw), _stream(stream)))
     return est, raw
+
+
+def null_batch(bases, order: int, models_per_base: int, seed: int, stream=None) -> torch.Tensor:
+    """hm_count_null_batch over host hypergraphs (synth.Hypergraph); returns an
+    int64 device tensor [len(bases) * models_per_base, ncls] of uint64 counts."""
+    import numpy as np
+    mem = np.concatenate([b.members for b in bases]) if bases else np.zeros(0, np.int32)
+    offs, edges, shift = [np.zeros(1, np.int64)], [0], 0
+    for b in bases:
+        offs.append(b.offsets[1:] + shift)
+        shift += int(b.offsets[-1])
+        edges.append(edges[-1] + b.num_hyperedges)
+    off = np.concatenate(offs)
+    dmem = torch.from_numpy(mem.astype(np.int32)).cuda()
+    doff = torch.from_numpy(off.astype(np.int64)).cuda()
+    hedges = (ctypes.c_int64 * len(edges))(*edges)
+    hn = (ctypes.c_int32 * len(bases))(*[b.num_nodes for b in bases])
+    nc = num_classes(order)
+    out = torch.empty((len(bases) * models_per_base, max(1, nc)), dtype=torch.int64, device="cuda")
+    _check(load().hm_count_null_batch(len(bases), _dptr(dmem), _dptr(doff), hedges, hn, order,
+                                      models_per_base, int(seed) & (2**64 - 1), _dptr(out),
+                                      _stream(stream)))
+    return out
 
 
 def from_host(h, max_order: int = 4, device="cuda") -> Graph:

@@ -224,26 +224,35 @@ __global__ void k_pairpos(const uint64_t* __restrict__ e2, int64_t m, const int6
   }
 }
 
-__global__ void k_bitmap(const uint64_t* __restrict__ e2, int64_t m, int32_t bw,
-                         uint32_t* __restrict__ bits) {
+// column of node b in the bitmap row of node a (rows span a's block of ids)
+__device__ __forceinline__ int32_t bit_col(int32_t a, int32_t b, int32_t block, uint64_t inv) {
+  return block ? b - (int32_t)__umul64hi((uint64_t)(uint32_t)a, inv) * block : b;
+}
+
+__global__ void k_bitmap(const uint64_t* __restrict__ e2, int64_t m, int32_t bw, int32_t block,
+                         uint64_t inv, uint32_t* __restrict__ bits) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m;
        p += (int64_t)gridDim.x * blockDim.x) {
     int32_t u = (int32_t)(e2[p] >> 32), v = (int32_t)(e2[p] & 0xFFFFFFFFull);
-    atomicOr(bits + (size_t)u * bw + (v >> 5), 1u << (v & 31));
-    atomicOr(bits + (size_t)v * bw + (u >> 5), 1u << (u & 31));
+    const int32_t cv = bit_col(u, v, block, inv), cu = bit_col(v, u, block, inv);
+    atomicOr(bits + (size_t)u * bw + (cv >> 5), 1u << (cv & 31));
+    atomicOr(bits + (size_t)v * bw + (cu >> 5), 1u << (cu & 31));
   }
 }
 
 // bits of every pair of members of each s-tuple (s = 3 or 4)
 __global__ void k_bitmap_tuples(const int4* __restrict__ e, int64_t m, int s, int32_t bw,
-                                uint32_t* __restrict__ bits) {
+                                int32_t block, uint64_t inv, uint32_t* __restrict__ bits) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int4 k = e[t];
     const int32_t v[4] = {k.x, k.y, k.z, k.w};
     for (int i = 0; i < s; ++i)
       for (int j = 0; j < s; ++j)
-        if (i != j) atomicOr(bits + (size_t)v[i] * bw + (v[j] >> 5), 1u << (v[j] & 31));
+        if (i != j) {
+          const int32_t c = bit_col(v[i], v[j], block, inv);
+          atomicOr(bits + (size_t)v[i] * bw + (c >> 5), 1u << (c & 31));
+        }
   }
 }
 
@@ -276,10 +285,10 @@ uint64_t table_capacity(int64_t m) {
   return c;
 }
 
-bool use_bitmap(int64_t n) {
+bool use_bitmap(int64_t n, int64_t row_ids) {
   const char* env = std::getenv("HM_PAIR_BITMAP");
   if (env && env[0] == '0') return false;
-  const int64_t bytes = n * ((n + 31) / 32) * 4;
+  const int64_t bytes = n * ((row_ids + 31) / 32) * 4;
   if (env && env[0] == '1') return bytes <= (1ll << 31);
   return bytes <= (32ll << 20);
 }
@@ -293,9 +302,10 @@ T* keep(hm_graph* g, T* p) {
 }  // namespace
 
 void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets, int64_t m,
-                 int32_t n, int kmax, cudaStream_t s) {
+                 int32_t n, int kmax, cudaStream_t s, int32_t block) {
   g->n = n;
   g->kmax = kmax;
+  g->block = block;
   g->m_in = m;
   HM_CUDA(cudaGetDevice(&g->device));
   const int b = bits_for((int64_t)n - 1);
@@ -435,25 +445,29 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     k_pairpos<<<grid1d(m2), T256, 0, s>>>(g->e2, m2, g->off2, g->adj2, g->pairpos);
     HM_KCHECK();
   }
-  if (use_bitmap(n)) {
-    g->bwords = (n + 31) / 32;
+  if (use_bitmap(n, block ? block : n)) {
+    g->bwords = ((block ? block : n) + 31) / 32;
+    const hm::DevGraph gv = g->view();
     size_t words = (size_t)n * g->bwords;
     g->bits2 = keep(g, dalloc<uint32_t>(words));
     HM_CUDA(cudaMemsetAsync(g->bits2, 0, words * sizeof(uint32_t), s));
     if (m2) {
-      k_bitmap<<<grid1d(m2), T256, 0, s>>>(g->e2, m2, g->bwords, g->bits2);
+      k_bitmap<<<grid1d(m2), T256, 0, s>>>(g->e2, m2, g->bwords, gv.block, gv.block_inv,
+                                           g->bits2);
       HM_KCHECK();
     }
     g->bits3 = keep(g, dalloc<uint32_t>(words));
     HM_CUDA(cudaMemsetAsync(g->bits3, 0, words * sizeof(uint32_t), s));
     if (m3) {
-      k_bitmap_tuples<<<grid1d(m3), T256, 0, s>>>(g->e3, m3, 3, g->bwords, g->bits3);
+      k_bitmap_tuples<<<grid1d(m3), T256, 0, s>>>(g->e3, m3, 3, g->bwords, gv.block,
+                                                  gv.block_inv, g->bits3);
       HM_KCHECK();
     }
     g->bits4 = keep(g, dalloc<uint32_t>(words));
     HM_CUDA(cudaMemsetAsync(g->bits4, 0, words * sizeof(uint32_t), s));
     if (m4) {
-      k_bitmap_tuples<<<grid1d(m4), T256, 0, s>>>(g->e4, m4, 4, g->bwords, g->bits4);
+      k_bitmap_tuples<<<grid1d(m4), T256, 0, s>>>(g->e4, m4, 4, g->bwords, gv.block,
+                                                  gv.block_inv, g->bits4);
       HM_KCHECK();
     }
   }

@@ -38,15 +38,26 @@ namespace {
 
 using namespace fam;
 
-template <class F>
+// Union of graphs (null-model batch): at most this many graphs per launch,
+// each with its own histogram row; block bins are then uint32 (the launch
+// keeps every block below 2^31 candidates).
+constexpr int MAX_GRAPHS = 64;
+constexpr int BIN_STRIDE = 176;
+
+template <class F, bool kBatched>
 __global__ void __launch_bounds__(CENSUS_THREADS)
     k_census(const DevGraph g, const F fam, const uint64_t* __restrict__ ws, int64_t A,
              uint64_t total, const uint8_t* __restrict__ lut_g, int nmask, int ncls,
-             unsigned long long* __restrict__ hist) {
-  __shared__ unsigned long long bins[176];
+             int ngraphs, unsigned long long* __restrict__ hist) {
+  __shared__ unsigned long long bins[kBatched ? 1 : BIN_STRIDE];
+  __shared__ unsigned int gbins[kBatched ? MAX_GRAPHS * BIN_STRIDE : 1];
   __shared__ uint8_t lut[2048];
   for (int i = threadIdx.x; i < nmask; i += blockDim.x) lut[i] = lut_g[i];
-  for (int i = threadIdx.x; i < ncls; i += blockDim.x) bins[i] = 0;
+  if (kBatched) {
+    for (int i = threadIdx.x; i < ngraphs * BIN_STRIDE; i += blockDim.x) gbins[i] = 0;
+  } else {
+    for (int i = threadIdx.x; i < ncls; i += blockDim.x) bins[i] = 0;
+  }
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
@@ -58,21 +69,25 @@ __global__ void __launch_bounds__(CENSUS_THREADS)
     const uint64_t g1 = min(g0 + CHUNK, total);
     typename F::State st;
     int64_t a = 0;
+    int32_t gid = 0;
     uint64_t r = 0, wa = 0;
     if (!F::kDirect && g0 < total) {
       a = anchor_of(ws, A, g0);
       r = g0 - ws[a];
       wa = ws[a + 1] - ws[a];
       fam.begin(g, a, r, st);
+      if (kBatched) gid = graph_of(g, fam.graph_node(g, a));
     }
     for (int it = 0; it < CHUNK; ++it) {
       const uint64_t gi = g0 + it;
-      int cls = -1;
+      int key = -1;
       if (gi < g1) {
         uint32_t mask = 0;
+        int32_t nd[4];
         bool ok;
         if (F::kDirect) {
-          ok = fam.item(g, (int64_t)gi, st, mask);
+          ok = fam.item(g, (int64_t)gi, st, mask, nd);
+          if (kBatched) gid = graph_of(g, fam.graph_node(g, (int64_t)gi));
         } else {
           if (r == wa) {
             do {
@@ -81,39 +96,54 @@ __global__ void __launch_bounds__(CENSUS_THREADS)
             r = 0;
             wa = ws[a + 1] - ws[a];
             fam.begin(g, a, 0, st);
+            if (kBatched) gid = graph_of(g, fam.graph_node(g, a));
           }
-          ok = fam.item(g, a, st, mask);
+          ok = fam.item(g, a, st, mask, nd);
           ++r;
           fam.next(st);
         }
         if (ok) {
           const uint8_t c = lut[mask];
-          cls = c == 0xFF ? -1 : (int)c;
+          key = c == 0xFF ? -1 : (kBatched ? gid * BIN_STRIDE : 0) + (int)c;
         }
       }
-      const unsigned peers = __match_any_sync(0xffffffffu, cls);
-      if (cls >= 0 && lane == __ffs(peers) - 1)
-        atomicAdd(&bins[cls], (unsigned long long)__popc(peers));
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      if (key >= 0 && lane == __ffs(peers) - 1) {
+        if (kBatched)
+          atomicAdd(&gbins[key], (unsigned int)__popc(peers));
+        else
+          atomicAdd(&bins[key], (unsigned long long)__popc(peers));
+      }
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < ncls; i += blockDim.x)
-    if (bins[i]) atomicAdd(&hist[i], bins[i]);
+  if (kBatched) {
+    for (int i = threadIdx.x; i < ngraphs * BIN_STRIDE; i += blockDim.x)
+      if (gbins[i]) atomicAdd(&hist[(i / BIN_STRIDE) * ncls + i % BIN_STRIDE], (unsigned long long)gbins[i]);
+  } else {
+    for (int i = threadIdx.x; i < ncls; i += blockDim.x)
+      if (bins[i]) atomicAdd(&hist[i], bins[i]);
+  }
 }
 
 // Bit-sliced families: each item evaluates up to bwords*32 candidates and
 // adds its class counts to the block's bins.
 constexpr int BITS_CHUNK = 4;
 
-template <class F>
+template <class F, bool kBatched>
 __global__ void __launch_bounds__(CENSUS_THREADS)
     k_census_bits(const DevGraph g, const F fam, const uint64_t* __restrict__ ws, int64_t A,
                   uint64_t total, const uint8_t* __restrict__ lut_g, int nmask, int ncls,
-                  unsigned long long* __restrict__ hist) {
-  __shared__ unsigned long long bins[176];
+                  int ngraphs, unsigned long long* __restrict__ hist) {
+  __shared__ unsigned long long bins[kBatched ? 1 : BIN_STRIDE];
+  __shared__ unsigned int gbins[kBatched ? MAX_GRAPHS * BIN_STRIDE : 1];
   __shared__ uint8_t lut[2048];
   for (int i = threadIdx.x; i < nmask; i += blockDim.x) lut[i] = lut_g[i];
-  for (int i = threadIdx.x; i < ncls; i += blockDim.x) bins[i] = 0;
+  if (kBatched) {
+    for (int i = threadIdx.x; i < ngraphs * BIN_STRIDE; i += blockDim.x) gbins[i] = 0;
+  } else {
+    for (int i = threadIdx.x; i < ncls; i += blockDim.x) bins[i] = 0;
+  }
   __syncthreads();
   const uint64_t nchunks = (total + BITS_CHUNK - 1) / BITS_CHUNK;
   for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
@@ -123,6 +153,7 @@ __global__ void __launch_bounds__(CENSUS_THREADS)
     int64_t a = anchor_of(ws, A, g0);
     uint64_t r = g0 - ws[a], wa = ws[a + 1] - ws[a];
     fam.begin(g, a, r, st);
+    int32_t gid = kBatched ? graph_of(g, fam.graph_node(g, a)) : 0;
     for (uint64_t gi = g0; gi < g1; ++gi) {
       if (r == wa) {
         do {
@@ -131,15 +162,24 @@ __global__ void __launch_bounds__(CENSUS_THREADS)
         r = 0;
         wa = ws[a + 1] - ws[a];
         fam.begin(g, a, 0, st);
+        if (kBatched) gid = graph_of(g, fam.graph_node(g, a));
       }
-      fam.item(g, a, st, lut, bins);
+      if (kBatched)
+        fam.item(g, a, st, lut, gbins + gid * BIN_STRIDE);
+      else
+        fam.item(g, a, st, lut, bins);
       ++r;
       fam.next(st);
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < ncls; i += blockDim.x)
-    if (bins[i]) atomicAdd(&hist[i], bins[i]);
+  if (kBatched) {
+    for (int i = threadIdx.x; i < ngraphs * BIN_STRIDE; i += blockDim.x)
+      if (gbins[i]) atomicAdd(&hist[(i / BIN_STRIDE) * ncls + i % BIN_STRIDE], (unsigned long long)gbins[i]);
+  } else {
+    for (int i = threadIdx.x; i < ncls; i += blockDim.x)
+      if (bins[i]) atomicAdd(&hist[i], bins[i]);
+  }
 }
 
 // ---------------------------------------------------------------- work spaces
@@ -252,48 +292,68 @@ void ensure_space(hm_graph* g, hm_graph::Space& sp, char fam, cudaStream_t s) {
   sp.ready = true;
 }
 
-int census_blocks(const void* kernel, uint64_t total) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    HM_CUDA(cudaGetDevice(&dev));
-    HM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  }
-  int per_sm = 0;
+// Persistent grid: SMs x resident blocks, capped by the work; with a union
+// of graphs, enough blocks that no block counts 2^31 candidates.
+int grid_for(const void* kernel, uint64_t lanes_needed, uint64_t max_candidates, bool batched) {
+  int dev = 0, sms = 0, per_sm = 0;
+  HM_CUDA(cudaGetDevice(&dev));
+  HM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, CENSUS_THREADS, 0));
   if (per_sm < 1) per_sm = 1;
-  const uint64_t chunks = (total + CHUNK - 1) / CHUNK;
-  const uint64_t need = (chunks + CENSUS_THREADS - 1) / CENSUS_THREADS;
+  const uint64_t need = (lanes_needed + CENSUS_THREADS - 1) / CENSUS_THREADS;
   uint64_t blocks = (uint64_t)sms * per_sm;
+  if (batched) {
+    const uint64_t floor_blocks = max_candidates / (1ull << 31) + 1;
+    if (blocks < floor_blocks) blocks = floor_blocks;
+  }
   if (need < blocks) blocks = need;
+  if (blocks > (1ull << 30)) blocks = 1ull << 30;
   return (int)(blocks < 1 ? 1 : blocks);
+}
+
+int num_graphs(const hm_graph* g) { return g->block ? (g->n + g->block - 1) / g->block : 1; }
+
+template <class F, bool kBatched>
+void launch_bits_t(const hm_graph* g, const F& fam, const hm_graph::Space& sp, int order,
+                   unsigned long long* hist, cudaStream_t s) {
+  const ClassTables& T = class_tables(order);
+  const uint8_t* lut = device_lut(order);
+  const uint64_t lanes = (sp.total + BITS_CHUNK - 1) / BITS_CHUNK;
+  const uint64_t max_cand = sp.total * (uint64_t)g->bwords * 32;
+  const int blocks = grid_for((const void*)k_census_bits<F, kBatched>, lanes, max_cand, kBatched);
+  cudaEvent_t ev = nullptr;
+  const bool tr = trace_on();
+  if (tr) trace_begin(s, &ev);
+  k_census_bits<F, kBatched><<<blocks, CENSUS_THREADS, 0, s>>>(
+      g->view(), fam, sp.ws, sp.anchors, sp.total, lut, (int)T.lut.size(), T.ncls, num_graphs(g),
+      hist);
+  HM_KCHECK();
+  if (tr) trace_end(F::kName, s, ev);
 }
 
 template <class F>
 void launch_bits(const hm_graph* g, const F& fam, const hm_graph::Space& sp, int order,
                  unsigned long long* hist, cudaStream_t s) {
   if (sp.total == 0) return;
+  if (g->block)
+    launch_bits_t<F, true>(g, fam, sp, order, hist, s);
+  else
+    launch_bits_t<F, false>(g, fam, sp, order, hist, s);
+}
+
+template <class F, bool kBatched>
+void launch_family_t(const hm_graph* g, const F& fam, const hm_graph::Space* sp, uint64_t total,
+                     int order, unsigned long long* hist, cudaStream_t s) {
   const ClassTables& T = class_tables(order);
   const uint8_t* lut = device_lut(order);
-  int blocks = census_blocks((const void*)k_census_bits<F>, sp.total);
-  // census_blocks sizes for CHUNK items per lane; bit-sliced lanes take BITS_CHUNK
-  const uint64_t need = ((sp.total + BITS_CHUNK - 1) / BITS_CHUNK + CENSUS_THREADS - 1) /
-                        CENSUS_THREADS;
-  if ((uint64_t)blocks > need) blocks = (int)(need < 1 ? 1 : need);
-  if ((uint64_t)blocks < need) {
-    int per_sm = 0, sms = 0, dev = 0;
-    HM_CUDA(cudaGetDevice(&dev));
-    HM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_census_bits<F>,
-                                                          CENSUS_THREADS, 0));
-    const uint64_t full = (uint64_t)sms * (per_sm < 1 ? 1 : per_sm);
-    blocks = (int)(need < full ? need : full);
-  }
+  const int blocks = grid_for((const void*)k_census<F, kBatched>, (total + CHUNK - 1) / CHUNK,
+                              total, kBatched);
   cudaEvent_t ev = nullptr;
   const bool tr = trace_on();
   if (tr) trace_begin(s, &ev);
-  k_census_bits<F><<<blocks, CENSUS_THREADS, 0, s>>>(g->view(), fam, sp.ws, sp.anchors, sp.total,
-                                                    lut, (int)T.lut.size(), T.ncls, hist);
+  k_census<F, kBatched><<<blocks, CENSUS_THREADS, 0, s>>>(
+      g->view(), fam, sp ? sp->ws : nullptr, sp ? sp->anchors : 0, total, lut,
+      (int)T.lut.size(), T.ncls, num_graphs(g), hist);
   HM_KCHECK();
   if (tr) trace_end(F::kName, s, ev);
 }
@@ -302,17 +362,10 @@ template <class F>
 void launch_family(const hm_graph* g, const F& fam, const hm_graph::Space* sp, uint64_t total,
                    int order, unsigned long long* hist, cudaStream_t s) {
   if (total == 0) return;
-  const ClassTables& T = class_tables(order);
-  const uint8_t* lut = device_lut(order);
-  const int blocks = census_blocks((const void*)k_census<F>, total);
-  cudaEvent_t ev = nullptr;
-  const bool tr = trace_on();
-  if (tr) trace_begin(s, &ev);
-  k_census<F><<<blocks, CENSUS_THREADS, 0, s>>>(g->view(), fam, sp ? sp->ws : nullptr,
-                                               sp ? sp->anchors : 0, total, lut,
-                                               (int)T.lut.size(), T.ncls, hist);
-  HM_KCHECK();
-  if (tr) trace_end(F::kName, s, ev);
+  if (g->block)
+    launch_family_t<F, true>(g, fam, sp, total, order, hist, s);
+  else
+    launch_family_t<F, false>(g, fam, sp, total, order, hist, s);
 }
 
 }  // namespace

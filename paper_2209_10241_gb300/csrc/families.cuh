@@ -60,12 +60,19 @@ struct FamT3 {
   static constexpr bool kDirect = true;
   const int64_t* map = nullptr;
   struct State {};
+  __device__ int32_t graph_node(const DevGraph& g, int64_t t) const {
+    return g.e3[map ? map[t] : t].x;
+  }
   __device__ void begin(const DevGraph&, int64_t, uint64_t, State&) const {}
   __device__ void next(State&) const {}
-  __device__ bool item(const DevGraph& g, int64_t t, State&, uint32_t& mask) const {
+  __device__ bool item(const DevGraph& g, int64_t t, State&, uint32_t& mask,
+                       int32_t (&nd)[4]) const {
     const int4 e = g.e3[map ? map[t] : t];
     mask = (has_pair(g, e.x, e.y) ? 1u : 0u) | (has_pair(g, e.x, e.z) ? 2u : 0u) |
            (has_pair(g, e.y, e.z) ? 4u : 0u) | 8u;
+    nd[0] = e.x;
+    nd[1] = e.y;
+    nd[2] = e.z;
     return true;
   }
 };
@@ -75,11 +82,19 @@ struct FamQ {
   static constexpr bool kDirect = true;
   const int64_t* map = nullptr;
   struct State {};
+  __device__ int32_t graph_node(const DevGraph& g, int64_t q) const {
+    return g.e4[map ? map[q] : q].x;
+  }
   __device__ void begin(const DevGraph&, int64_t, uint64_t, State&) const {}
   __device__ void next(State&) const {}
-  __device__ bool item(const DevGraph& g, int64_t q, State&, uint32_t& mask) const {
+  __device__ bool item(const DevGraph& g, int64_t q, State&, uint32_t& mask,
+                       int32_t (&nd)[4]) const {
     const int4 e = g.e4[map ? map[q] : q];
     const int32_t a = e.x, b = e.y, c = e.z, d = e.w;
+    nd[0] = a;
+    nd[1] = b;
+    nd[2] = c;
+    nd[3] = d;
     mask = (has_pair(g, a, b) ? 1u : 0u) | (has_pair(g, a, c) ? 2u : 0u) |
            (has_pair(g, a, d) ? 4u : 0u) | (has_pair(g, b, c) ? 8u : 0u) |
            (has_pair(g, b, d) ? 16u : 0u) | (has_pair(g, c, d) ? 32u : 0u) |
@@ -92,6 +107,7 @@ struct FamQ {
 struct FamW {
   static constexpr const char* kName = "census_W";
   static constexpr bool kDirect = false;
+  __device__ int32_t graph_node(const DevGraph&, int64_t v) const { return (int32_t)v; }
   struct State {
     uint32_t i, j;
     int64_t o;
@@ -106,9 +122,13 @@ struct FamW {
       ++s.j;
     }
   }
-  __device__ bool item(const DevGraph& g, int64_t a, State& s, uint32_t& mask) const {
+  __device__ bool item(const DevGraph& g, int64_t a, State& s, uint32_t& mask,
+                       int32_t (&nd)[4]) const {
     const int32_t v = (int32_t)a;
     const int32_t x = g.adj2[s.o + s.i], y = g.adj2[s.o + s.j];
+    nd[0] = v;
+    nd[1] = x;
+    nd[2] = y;
     const bool xy = has_pair(g, x, y);
     if (xy && (x < v || y < v)) return false;  // a triangle is kept at its smallest node
     if (has_triple(g, v, x, y)) return false;  // counted with its 3-hyperedge
@@ -120,6 +140,7 @@ struct FamW {
 struct FamS {
   static constexpr const char* kName = "census_S";
   static constexpr bool kDirect = false;
+  __device__ int32_t graph_node(const DevGraph&, int64_t v) const { return (int32_t)v; }
   struct State {
     uint32_t i, j, l;
     int64_t o;
@@ -137,9 +158,14 @@ struct FamS {
       }
     }
   }
-  __device__ bool item(const DevGraph& g, int64_t a, State& s, uint32_t& mask) const {
+  __device__ bool item(const DevGraph& g, int64_t a, State& s, uint32_t& mask,
+                       int32_t (&nd)[4]) const {
     const int32_t v = (int32_t)a;
     const int32_t x = g.adj2[s.o + s.i], y = g.adj2[s.o + s.j], z = g.adj2[s.o + s.l];
+    nd[0] = v;
+    nd[1] = x;
+    nd[2] = y;
+    nd[3] = z;
     const bool xy = has_pair(g, x, y), xz = has_pair(g, x, z), yz = has_pair(g, y, z);
     // v has induced degree 3; it must be the smallest node of degree 3
     if ((xy && xz && x < v) || (xy && yz && y < v) || (xz && yz && z < v)) return false;
@@ -154,6 +180,9 @@ struct FamS {
 struct FamP {
   static constexpr const char* kName = "census_P";
   static constexpr bool kDirect = false;
+  __device__ int32_t graph_node(const DevGraph& g, int64_t p) const {
+    return (int32_t)(g.e2[p] >> 32);
+  }
   struct State {
     int32_t u, v;
     int64_t ou, ov;
@@ -178,10 +207,15 @@ struct FamP {
       ++s.i2;
     }
   }
-  __device__ bool item(const DevGraph& g, int64_t, State& s, uint32_t& mask) const {
+  __device__ bool item(const DevGraph& g, int64_t, State& s, uint32_t& mask,
+                       int32_t (&nd)[4]) const {
     const int32_t u = s.u, v = s.v;
     const int32_t x = g.adj2[s.ou + s.i2 + (s.i2 >= s.pu ? 1 : 0)];  // N2(u) \ {v}
     const int32_t y = g.adj2[s.ov + s.j2 + (s.j2 >= s.pv ? 1 : 0)];  // N2(v) \ {u}
+    nd[0] = u;
+    nd[1] = v;
+    nd[2] = x;
+    nd[3] = y;
     if (x == y) return false;
     if (has_pair(g, u, y) || has_pair(g, v, x)) return false;  // a degree-3 node: family S
     const bool xy = has_pair(g, x, y);
@@ -206,6 +240,9 @@ struct FamTXT {
   static constexpr const char* kName = kCensus ? "census_TX" : "sample_TX";
   static constexpr bool kDirect = false;
   const int64_t* map = nullptr;
+  __device__ int32_t graph_node(const DevGraph& g, int64_t a) const {
+    return g.e3[kCensus ? a : map[a]].x;
+  }
   struct State {
     int32_t x[3];
     int32_t d2[3];
@@ -229,7 +266,8 @@ struct FamTXT {
     s.r = r;
   }
   __device__ void next(State& s) const { ++s.r; }
-  __device__ bool item(const DevGraph& g, int64_t, State& s, uint32_t& mask) const {
+  __device__ bool item(const DevGraph& g, int64_t, State& s, uint32_t& mask,
+                       int32_t (&nd)[4]) const {
     const int64_t t = s.t;
     uint64_t r = s.r;
     int which = 0;
@@ -297,6 +335,10 @@ struct FamTXT {
       if (!tri_eq(htri, mn)) return false;
     }
     if (has_quad(g, a, b, c, d)) return false;  // holds a 4-hyperedge (family Q)
+    nd[0] = a;
+    nd[1] = b;
+    nd[2] = c;
+    nd[3] = d;
     const bool ab = has_pair(g, a, b), ac = has_pair(g, a, c), bc = has_pair(g, b, c);
     mask = (ab ? 1u : 0u) | (ac ? 2u : 0u) | (ad ? 4u : 0u) | (bc ? 8u : 0u) |
            (bd ? 16u : 0u) | (cd ? 32u : 0u) | 64u | (abd ? 128u : 0u) | (acd ? 256u : 0u) |
@@ -331,10 +373,12 @@ __device__ __forceinline__ int64_t anchor_of(const uint64_t* __restrict__ ws, in
 __device__ __forceinline__ const uint32_t* brow(const uint32_t* bm, int32_t bw, int32_t v) {
   return bm + (size_t)v * bw;
 }
-__device__ __forceinline__ bool btest(const uint32_t* bm, int32_t bw, int32_t a, int32_t b) {
-  return (__ldg(bm + (size_t)a * bw + (b >> 5)) >> (b & 31)) & 1u;
+// bit of node b in the row of node a (rows span a's block of ids)
+__device__ __forceinline__ bool btest(const DevGraph& g, const uint32_t* bm, int32_t a, int32_t b) {
+  const int32_t c = b - graph_base(g, a);
+  return (__ldg(bm + (size_t)a * g.bwords + (c >> 5)) >> (c & 31)) & 1u;
 }
-// bits of word w whose node id exceeds t
+// bits of word w whose (local) id exceeds t
 __device__ __forceinline__ uint32_t above(int32_t w, int32_t t) {
   const int32_t tw = t >> 5;
   if (w < tw) return 0u;
@@ -350,22 +394,23 @@ struct BitsW {
     int64_t o;
     uint32_t i;
   };
+  __device__ int32_t graph_node(const DevGraph&, int64_t v) const { return (int32_t)v; }
   __device__ void begin(const DevGraph& g, int64_t v, uint64_t r, State& s) const {
     s.o = g.off2[v];
     s.i = (uint32_t)r;
   }
   __device__ void next(State& s) const { ++s.i; }
-  __device__ void item(const DevGraph& g, int64_t a, State& s, const uint8_t* lut,
-                       unsigned long long* bins) const {
-    const int32_t v = (int32_t)a, bw = g.bwords;
-    const int32_t x = g.adj2[s.o + s.i];
+  template <class Bin>
+  __device__ void item(const DevGraph& g, int64_t a, State& s, const uint8_t* lut, Bin* bins) const {
+    const int32_t v = (int32_t)a, bw = g.bwords, base = graph_base(g, v);
+    const int32_t x = g.adj2[s.o + s.i], xl = x - base;
     const uint32_t *Bv = brow(g.bits2, bw, v), *Bx = brow(g.bits2, bw, x);
     const uint32_t *Tv = brow(g.bits3, bw, v), *Tx = brow(g.bits3, bw, x);
-    const bool tvx = btest(g.bits3, bw, v, x);
+    const bool tvx = btest(g, g.bits3, v, x);
     const bool tri_ok = x > v;  // a triangle is kept at its smallest node
     unsigned long long nw = 0, nt = 0;
-    for (int32_t w = x >> 5; w < bw; ++w) {
-      const uint32_t Y = __ldg(Bv + w) & above(w, x);
+    for (int32_t w = xl >> 5; w < bw; ++w) {
+      const uint32_t Y = __ldg(Bv + w) & above(w, xl);
       if (!Y) continue;
       const uint32_t bx = __ldg(Bx + w);
       const uint32_t tri = tri_ok ? (Y & bx) : 0u, wed = Y & ~bx;
@@ -376,7 +421,7 @@ struct BitsW {
       while (rb) {
         const int b = __ffs(rb) - 1;
         rb &= rb - 1;
-        if (!has_triple(g, v, x, w * 32 + b)) {
+        if (!has_triple(g, v, x, base + w * 32 + b)) {
           if ((tri >> b) & 1u)
             ++nt;
           else
@@ -384,8 +429,8 @@ struct BitsW {
         }
       }
     }
-    if (nw) atomicAdd(&bins[lut[3]], nw);   // v=0, x=1, y=2: pairs 01, 02
-    if (nt) atomicAdd(&bins[lut[7]], nt);   // + pair 12
+    if (nw) atomicAdd(&bins[lut[3]], (Bin)nw);  // v=0, x=1, y=2: pairs 01, 02
+    if (nt) atomicAdd(&bins[lut[7]], (Bin)nt);  // + pair 12
   }
 };
 
@@ -396,6 +441,7 @@ struct BitsS {
     uint32_t i, j;
     int64_t o;
   };
+  __device__ int32_t graph_node(const DevGraph&, int64_t v) const { return (int32_t)v; }
   __device__ void begin(const DevGraph& g, int64_t v, uint64_t r, State& s) const {
     s.o = g.off2[v];
     unrank2(r, s.i, s.j);
@@ -406,31 +452,32 @@ struct BitsS {
       ++s.j;
     }
   }
-  __device__ void item(const DevGraph& g, int64_t a, State& s, const uint8_t* lut,
-                       unsigned long long* bins) const {
-    const int32_t v = (int32_t)a, bw = g.bwords;
+  template <class Bin>
+  __device__ void item(const DevGraph& g, int64_t a, State& s, const uint8_t* lut, Bin* bins) const {
+    const int32_t v = (int32_t)a, bw = g.bwords, base = graph_base(g, v);
     const int32_t x = g.adj2[s.o + s.i], y = g.adj2[s.o + s.j];
-    const bool tvx = btest(g.bits3, bw, v, x), tvy = btest(g.bits3, bw, v, y),
-               txy = btest(g.bits3, bw, x, y);
+    const int32_t vl = v - base, yl = y - base;
+    const bool tvx = btest(g, g.bits3, v, x), tvy = btest(g, g.bits3, v, y),
+               txy = btest(g, g.bits3, x, y);
     if (tvx && tvy && txy && has_triple(g, v, x, y)) return;
-    const bool qd = btest(g.bits4, bw, v, x) && btest(g.bits4, bw, v, y) &&
-                    btest(g.bits4, bw, x, y);
-    const bool xy = btest(g.bits2, bw, x, y);
+    const bool qd = btest(g, g.bits4, v, x) && btest(g, g.bits4, v, y) &&
+                    btest(g, g.bits4, x, y);
+    const bool xy = btest(g, g.bits2, x, y);
     // a node of degree 3 smaller than v rejects the set
     const bool rx = xy && x < v, ry = xy && y < v;
     const uint32_t *Bv = brow(g.bits2, bw, v), *Bx = brow(g.bits2, bw, x), *By = brow(g.bits2, bw, y);
     const uint32_t *Tv = brow(g.bits3, bw, v), *Tx = brow(g.bits3, bw, x), *Ty = brow(g.bits3, bw, y);
     const uint32_t *Qv = brow(g.bits4, bw, v), *Qx = brow(g.bits4, bw, x), *Qy = brow(g.bits4, bw, y);
     unsigned long long c[4] = {0, 0, 0, 0};  // (xz, yz) = 00, 10, 01, 11
-    for (int32_t w = y >> 5; w < bw; ++w) {
-      const uint32_t Z = __ldg(Bv + w) & above(w, y);
+    for (int32_t w = yl >> 5; w < bw; ++w) {
+      const uint32_t Z = __ldg(Bv + w) & above(w, yl);
       if (!Z) continue;
       const uint32_t bx = __ldg(Bx + w), by = __ldg(By + w);
       uint32_t grp[4];
       grp[0] = Z & ~bx & ~by;
       grp[1] = rx ? 0u : (Z & bx & ~by);
       grp[2] = ry ? 0u : (Z & ~bx & by);
-      grp[3] = (rx || ry) ? 0u : (Z & bx & by & above(w, v));
+      grp[3] = (rx || ry) ? 0u : (Z & bx & by & above(w, vl));
       uint32_t risky = 0u;
       if (tvx) risky |= __ldg(Tv + w) & __ldg(Tx + w);
       if (tvy) risky |= __ldg(Tv + w) & __ldg(Ty + w);
@@ -442,18 +489,18 @@ struct BitsS {
       while (rb) {
         const int b = __ffs(rb) - 1;
         rb &= rb - 1;
-        const int32_t z = w * 32 + b;
+        const int32_t z = base + w * 32 + b;
         if (has_triple(g, v, x, z) || has_triple(g, v, y, z) || has_triple(g, x, y, z) ||
             has_quad(g, v, x, y, z))
           continue;
         ++c[((bx >> b) & 1u) | (((by >> b) & 1u) << 1)];
       }
     }
-    const uint32_t base = 7u | (xy ? 8u : 0u);  // v=0, x=1, y=2, z=3
-    if (c[0]) atomicAdd(&bins[lut[base]], c[0]);
-    if (c[1]) atomicAdd(&bins[lut[base | 16u]], c[1]);
-    if (c[2]) atomicAdd(&bins[lut[base | 32u]], c[2]);
-    if (c[3]) atomicAdd(&bins[lut[base | 48u]], c[3]);
+    const uint32_t basem = 7u | (xy ? 8u : 0u);  // v=0, x=1, y=2, z=3
+    if (c[0]) atomicAdd(&bins[lut[basem]], (Bin)c[0]);
+    if (c[1]) atomicAdd(&bins[lut[basem | 16u]], (Bin)c[1]);
+    if (c[2]) atomicAdd(&bins[lut[basem | 32u]], (Bin)c[2]);
+    if (c[3]) atomicAdd(&bins[lut[basem | 48u]], (Bin)c[3]);
   }
 };
 
@@ -466,6 +513,9 @@ struct BitsP {
     int64_t ou;
     uint32_t pu, i;
   };
+  __device__ int32_t graph_node(const DevGraph& g, int64_t p) const {
+    return (int32_t)(g.e2[p] >> 32);
+  }
   __device__ void begin(const DevGraph& g, int64_t p, uint64_t r, State& s) const {
     const uint64_t uv = g.e2[p];
     s.u = (int32_t)(uv >> 32);
@@ -475,29 +525,30 @@ struct BitsP {
     s.i = (uint32_t)r;
   }
   __device__ void next(State& s) const { ++s.i; }
-  __device__ void item(const DevGraph& g, int64_t, State& s, const uint8_t* lut,
-                       unsigned long long* bins) const {
-    const int32_t u = s.u, v = s.v, bw = g.bwords;
+  template <class Bin>
+  __device__ void item(const DevGraph& g, int64_t, State& s, const uint8_t* lut, Bin* bins) const {
+    const int32_t u = s.u, v = s.v, bw = g.bwords, base = graph_base(g, u);
     const int32_t x = g.adj2[s.ou + s.i + (s.i >= s.pu ? 1 : 0)];
-    if (btest(g.bits2, bw, v, x)) return;  // v would have degree 3: family S
-    const bool tuv = btest(g.bits3, bw, u, v), tux = btest(g.bits3, bw, u, x),
-               tvx = btest(g.bits3, bw, v, x);
+    if (btest(g, g.bits2, v, x)) return;  // v would have degree 3: family S
+    const bool tuv = btest(g, g.bits3, u, v), tux = btest(g, g.bits3, u, x),
+               tvx = btest(g, g.bits3, v, x);
     if (tuv && tux && tvx && has_triple(g, u, v, x)) return;
-    const bool qd = btest(g.bits4, bw, u, v) && btest(g.bits4, bw, u, x) &&
-                    btest(g.bits4, bw, v, x);
+    const bool qd = btest(g, g.bits4, u, v) && btest(g, g.bits4, u, x) &&
+                    btest(g, g.bits4, v, x);
     const bool c4ok = x > v;  // a 4-cycle is kept at its smallest pair: x > v, y > u
+    const int32_t ul = u - base;
     const uint32_t *Bu = brow(g.bits2, bw, u), *Bv = brow(g.bits2, bw, v), *Bx = brow(g.bits2, bw, x);
     const uint32_t *Tu = brow(g.bits3, bw, u), *Tv = brow(g.bits3, bw, v), *Tx = brow(g.bits3, bw, x);
     const uint32_t *Qu = brow(g.bits4, bw, u), *Qv = brow(g.bits4, bw, v), *Qx = brow(g.bits4, bw, x);
-    const int32_t uw = u >> 5;
-    const uint32_t ubit = 1u << (u & 31);
+    const int32_t uw = ul >> 5;
+    const uint32_t ubit = 1u << (ul & 31);
     unsigned long long np = 0, nc = 0;
     for (int32_t w = 0; w < bw; ++w) {
       uint32_t Y = __ldg(Bv + w) & ~__ldg(Bu + w);
       if (w == uw) Y &= ~ubit;
       if (!Y) continue;
       const uint32_t bx = __ldg(Bx + w);
-      const uint32_t c4 = c4ok ? (Y & bx & above(w, u)) : 0u, p4 = Y & ~bx;
+      const uint32_t c4 = c4ok ? (Y & bx & above(w, ul)) : 0u, p4 = Y & ~bx;
       uint32_t risky = 0u;
       if (tuv) risky |= __ldg(Tu + w) & __ldg(Tv + w);
       if (tux) risky |= __ldg(Tu + w) & __ldg(Tx + w);
@@ -509,7 +560,7 @@ struct BitsP {
       while (rb) {
         const int b = __ffs(rb) - 1;
         rb &= rb - 1;
-        const int32_t y = w * 32 + b;
+        const int32_t y = base + w * 32 + b;
         if (has_triple(g, u, v, y) || has_triple(g, u, x, y) || has_triple(g, v, x, y) ||
             has_quad(g, u, v, x, y))
           continue;
@@ -519,8 +570,8 @@ struct BitsP {
           ++np;
       }
     }
-    if (np) atomicAdd(&bins[lut[19]], np);  // u=0, v=1, x=2, y=3: pairs 01, 02, 13
-    if (nc) atomicAdd(&bins[lut[51]], nc);  // + pair 23
+    if (np) atomicAdd(&bins[lut[19]], (Bin)np);  // u=0, v=1, x=2, y=3: pairs 01, 02, 13
+    if (nc) atomicAdd(&bins[lut[51]], (Bin)nc);  // + pair 23
   }
 };
 

@@ -153,6 +153,33 @@ __host__ __device__ __forceinline__ uint64_t hash_tuple(int32_t a, int32_t b, in
 
 constexpr uint64_t EMPTY64 = ~0ull;
 
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter c (in/out),
+// key (k0, k1); ten rounds, the key bumped by the Weyl constants between them.
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+    const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+// 64-bit draw (r0 << 32) | r1 for counter (index lo, index hi, lane, tag), key = seed
+__device__ __forceinline__ uint64_t philox_draw64(uint64_t seed, uint64_t index, uint32_t lane,
+                                                  uint32_t tag) {
+  uint32_t c[4] = {(uint32_t)index, (uint32_t)(index >> 32), lane, tag};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  return ((uint64_t)c[0] << 32) | c[1];
+}
+
 // ------------------------------------------------------------------ graph
 // Read-only view handed to kernels by value.
 struct DevGraph {
@@ -183,12 +210,26 @@ struct DevGraph {
   const uint32_t* bits3;
   const uint32_t* bits4;
   int32_t bwords;
+  // 0 for one graph. Otherwise the graph is a disjoint union of graphs whose
+  // node ids occupy consecutive blocks of `block` ids (graph of node v =
+  // v / block, computed as mulhi(v, block_inv) with block_inv = ceil(2^64 /
+  // block), exact for v < 2^31); bitmap rows then span one block.
+  int32_t block;
+  uint64_t block_inv;
 };
+
+__device__ __forceinline__ int32_t graph_of(const DevGraph& g, int32_t v) {
+  return g.block ? (int32_t)__umul64hi((uint64_t)(uint32_t)v, g.block_inv) : 0;
+}
+__device__ __forceinline__ int32_t graph_base(const DevGraph& g, int32_t v) {
+  return g.block ? graph_of(g, v) * g.block : 0;
+}
 
 __device__ __forceinline__ bool has_pair(const DevGraph& g, int32_t a, int32_t b) {
   if (g.bits2) {
-    uint32_t w = __ldg(g.bits2 + (size_t)a * g.bwords + (b >> 5));
-    return (w >> (b & 31)) & 1u;
+    const int32_t c = b - graph_base(g, a);
+    uint32_t w = __ldg(g.bits2 + (size_t)a * g.bwords + (c >> 5));
+    return (w >> (c & 31)) & 1u;
   }
   if (g.m2 == 0) return false;
   uint64_t key = pair_key(a, b);
@@ -267,11 +308,13 @@ const uint8_t* device_lut(int k);
 struct hm_graph;
 namespace hm {
 // build.cu
+// block > 0: the input is a disjoint union of graphs of `block` node ids each
 void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets, int64_t m,
-                 int32_t n, int kmax, cudaStream_t s);
+                 int32_t n, int kmax, cudaStream_t s, int32_t block = 0);
 void free_graph(hm_graph* g);
 // census.cu
 void prepare_census(hm_graph* g, int order, cudaStream_t s);
+// hist holds hm_num_classes(order) counters per graph of the union (one graph: one row)
 void launch_census(const hm_graph* g, int order, unsigned long long* hist, cudaStream_t s);
 }  // namespace hm
 
@@ -302,6 +345,7 @@ struct hm_graph {
   uint32_t* bits3 = nullptr;
   uint32_t* bits4 = nullptr;
   int32_t bwords = 0;
+  int32_t block = 0;  // see DevGraph::block
   int32_t max_d2 = 0;
   // cached work spaces (prefix sums over anchors), per family
   struct Space {
@@ -341,6 +385,8 @@ struct hm_graph {
     g.bits3 = bits3;
     g.bits4 = bits4;
     g.bwords = bwords;
+    g.block = block;
+    g.block_inv = block > 1 ? (uint64_t)((((unsigned __int128)1 << 64) + block - 1) / block) : 0;
     return g;
   }
 };

@@ -37,23 +37,6 @@ constexpr uint32_t TAG_SAMPLE = 0x53414D50u;  // "SAMP"
 constexpr int64_t SAMPLE_BATCH = 1 << 20;
 constexpr int SAMPLE_THREADS = 256;
 
-__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-    const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
-    const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
-    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-    c[0] = n0;
-    c[1] = lo1;
-    c[2] = n2;
-    c[3] = lo0;
-  }
-}
-
 __device__ __forceinline__ int32_t deg2(const DevGraph& g, int32_t v) {
   return (int32_t)(g.off2[v + 1] - g.off2[v]);
 }
@@ -173,9 +156,13 @@ struct SamP3 {
     s.i = (uint32_t)r;
   }
   __device__ void next(State& s) const { ++s.i; }
-  __device__ bool item(const DevGraph& g, int64_t, State& s, uint32_t& mask) const {
+  __device__ bool item(const DevGraph& g, int64_t, State& s, uint32_t& mask,
+                       int32_t (&nd)[4]) const {
     const PairList& L = s.L;
     const int32_t c = list_elem(g, L, s.i);
+    nd[0] = L.a;
+    nd[1] = L.b;
+    nd[2] = c;
     const bool first = s.i < L.la;
     if (!first && has_pair(g, L.a, c)) return false;  // already listed from a
     if (has_triple(g, L.a, L.b, c)) return false;     // larger hyperedge than e
@@ -204,10 +191,15 @@ struct SamPA {
       ++s.j;
     }
   }
-  __device__ bool item(const DevGraph& g, int64_t, State& s, uint32_t& mask) const {
+  __device__ bool item(const DevGraph& g, int64_t, State& s, uint32_t& mask,
+                       int32_t (&nd)[4]) const {
     const PairList& L = s.L;
     const int32_t a = L.a, b = L.b;
     const int32_t c = list_elem(g, L, s.i), d = list_elem(g, L, s.j);
+    nd[0] = a;
+    nd[1] = b;
+    nd[2] = c;
+    nd[3] = d;
     const bool cfirst = s.i < L.la, dfirst = s.j < L.la;
     const bool ac = cfirst ? true : has_pair(g, a, c);
     const bool ad = dfirst ? true : has_pair(g, a, d);
@@ -245,9 +237,14 @@ struct SamPB {
     s.r = r;
   }
   __device__ void next(State& s) const { ++s.r; }
-  __device__ bool item(const DevGraph& g, int64_t, State& s, uint32_t& mask) const {
+  __device__ bool item(const DevGraph& g, int64_t, State& s, uint32_t& mask,
+                       int32_t (&nd)[4]) const {
     const int32_t a = s.a, b = s.b, c = s.c;
     const int32_t d = g.adj2[s.co + s.r];
+    nd[0] = a;
+    nd[1] = b;
+    nd[2] = c;
+    nd[3] = d;
     if (d == a || d == b || has_pair(g, a, d) || has_pair(g, b, d)) return false;
     if (has_triple(g, a, b, c) || has_triple(g, a, b, d) || has_triple(g, a, c, d) ||
         has_triple(g, b, c, d) || has_quad(g, a, b, c, d))
@@ -298,10 +295,11 @@ __global__ void __launch_bounds__(SAMPLE_THREADS)
       int64_t anchor = 0;
       if (gi < g1) {
         uint32_t mask = 0;
+        int32_t nd[4];
         bool ok;
         if (F::kDirect) {
           anchor = (int64_t)gi;
-          ok = fam.item(g, anchor, st, mask);
+          ok = fam.item(g, anchor, st, mask, nd);
         } else {
           if (r == wa) {
             do {
@@ -312,7 +310,7 @@ __global__ void __launch_bounds__(SAMPLE_THREADS)
             fam.begin(g, a, 0, st);
           }
           anchor = a;
-          ok = fam.item(g, a, st, mask);
+          ok = fam.item(g, a, st, mask, nd);
           ++r;
           fam.next(st);
         }
