@@ -141,6 +141,83 @@ def cpu_baseline(h, order: int, budget_s: float = 15.0):
                       f"({sets} connected sets in {t_used:.1f} s)"}
 
 
+def _event_ms(fn, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def measure_sampler(hm, stream, scale=0.004, budgets=(12_000, 60_000, 300_000), seeds=5):
+    """Alg. 4 with uniform and learned proposals: relative error vs GPU time.
+
+    Communication-shaped graph (comm-5m generator at `scale`); the proposal is
+    trained on a separate instance of the same generator from exact
+    per-hyperedge contributions; error = mean over classes with T_c >= 100 of
+    |T^_c - T_c| / T_c against the exact census, averaged over seeds.
+    """
+    import numpy as np
+    import torch
+    from paper_2209_10241_gb300 import synth
+    k = 4
+    tr = synth.workload("comm-5m", seed=7, scale=scale)
+    gt = hm.from_host(tr, 4)
+    t_train = time.perf_counter()
+    contrib = hm.contributions(gt, k)
+    exact_t = hm.count_exact(gt, k)
+    tgt = hm.proposal_targets(gt, k, contrib, exact_t, eps=1e-9)
+    feat = hm.features(gt, k)
+    params = torch.from_numpy(synth.mlp_init_params(1)).cuda()
+    losses = hm.mlp_train(params, feat, tgt, epochs=30, batch=4096, lr=3e-3, seed=3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t_train
+    h = synth.workload("comm-5m", seed=9, scale=scale)
+    g = hm.from_host(h, 4)
+    exact_ms, T = _event_ms(lambda: hm.count_exact(g, k), stream)
+    T = T.cpu().numpy().astype(np.float64)
+    big = T >= 100
+    q_ms, q = _event_ms(lambda: hm.proposal_weights(g, k, params, lam=0.1), stream)
+    rows = []
+    for S in budgets:
+        split = {2: S // 6, 4: S // 3}
+        split[3] = S - split[2] - split[4]
+        rec = {"S": S}
+        for name, qq in (("uniform", None), ("learned", q)):
+            ms, errs = [], []
+            for r in range(seeds):
+                t, (est, _) = _event_ms(lambda: hm.count_sampled(g, k, samples=split,
+                                                                 seed=100 + r, q=qq), stream)
+                e = est.cpu().numpy()
+                ms.append(t)
+                errs.append(float(np.mean(np.abs(e[big] - T[big]) / T[big])))
+            rec[name] = {"ms": float(np.median(ms)), "mre": float(np.mean(errs))}
+        rows.append(rec)
+    return {"workload": f"comm-5m generator at scale {scale}: {h.num_nodes} nodes, "
+                        f"{h.num_hyperedges} hyperedges", "order": k,
+            "classes_T_ge_100": int(big.sum()), "exact_census_ms": exact_ms,
+            "proposal_weights_ms": q_ms, "train_s": train_s,
+            "train_loss_first_last": [losses[0], losses[-1]], "by_budget": rows}
+
+
+def measure_null(hm, stream, hyperedges=(50_000, 69_000, 97_000, 134_000, 186_000, 259_000,
+                                         360_000, 500_000), models=8):
+    """Null-model batch: len(hyperedges) face-to-face-shaped bases x `models`
+    stub shuffles counted at order 4 (64 uneven graphs, one union per 64)."""
+    from paper_2209_10241_gb300 import synth
+    bases = [synth.null_base(H, seed=100 + i) for i, H in enumerate(hyperedges)]
+    hm.null_batch(bases[:1], 4, 1, seed=1)  # warm-up
+    ms, out = _event_ms(lambda: hm.null_batch(bases, 4, models, seed=1), stream)
+    sets = int(out.sum().item())
+    return {"bases": [b.num_hyperedges for b in bases], "nodes": [b.num_nodes for b in bases],
+            "models": len(bases) * models, "ms": ms, "sets": sets,
+            "sets_per_s": sets / (ms / 1e3)}
+
+
 def run_reference(args, rank: int):
     if rank != 0:
         return
@@ -174,6 +251,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--order", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the sampler and null-batch measurements")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -320,6 +399,9 @@ def main():
                 "h2d_bytes_per_step": int(h.members.nbytes + h.offsets.nbytes),
                 "d2h_bytes_per_step": ncls * 8},
     }
+    if world == 1 and not args.no_extras:
+        line["sampler"] = measure_sampler(hm, stream)
+        line["null_batch"] = measure_null(hm, stream)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(h, args.order)
     print(json.dumps(line), flush=True)

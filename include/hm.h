@@ -195,6 +195,83 @@ hm_status hm_trace_enable(int on);
 uint64_t hm_launch_count(void);
 hm_status hm_trace_read(int max_entries, char* names, int name_len, float* ms, int* count);
 
+/* ---------------------------------------------------------------- learned proposal
+ * An extension of Alg. 4 (Sec. 5), which samples uniformly within each
+ * stratum: a small MLP maps per-hyperedge features to importance weights q
+ * for hm_count_sampled (whose Hansen-Hurwitz reweighting keeps the estimate
+ * unbiased for any q >= 1). Rows are E_2, E_3, ..., E_order in the order of
+ * hm_graph_edges.
+ */
+
+/*
+ * Per-hyperedge exact contributions: d_contrib[row * ncls + c] (device
+ * uint32, overwritten) = the number of connected order-node sets of class c
+ * in which hyperedge `row` is one of the hyperedges of maximum cardinality --
+ * the count a draw of that hyperedge adds in Alg. 4 (max-cardinality rule,
+ * Sec. 5). Summed over rows: countmax_c * hm_count_exact's count. Counters
+ * wrap at 2^32. Synchronous only if the census work spaces are not yet built.
+ */
+hm_status hm_contributions(hm_graph* g, int order, uint32_t* d_contrib, void* stream);
+
+/*
+ * Per-hyperedge features, device float32[rows][16]: 1, |e|/4,
+ * log1p(min, mean, max pair degree of the members), log1p(min, mean, max
+ * number of 3-hyperedges through the members), log1p(member pairs that are
+ * hyperedges), log1p(sets a draw of e enumerates at this order), log1p(sum
+ * of pair degrees), log1p(sum of 3-hyperedge counts), then 4 zeros.
+ */
+hm_status hm_features(hm_graph* g, int order, float* d_feat, void* stream);
+
+/*
+ * The MLP 16 -> 64 -> 64 -> 1 (ReLU) on BF16 tensor cores with FP32
+ * accumulation. Parameters: device float32[hm_mlp_num_params()] packed as
+ * W1[16][64] | b1[64] | W2[64][64] | b2[64] | w3[64] | b3 (W[in][out]).
+ * bf16 rounding is applied to the inputs, the weights, both hidden
+ * activations and the back-propagated dz2, dz1 entering matrix products.
+ *   hm_mlp_forward  y[i] = f(x[i]) for n rows of 16 floats.
+ *   hm_mlp_backward d_grad (overwritten) = gradient of mean_i (y_i - t_i)^2;
+ *                   *d_loss_sum (may be NULL) = sum_i (y_i - t_i)^2;
+ *                   d_scratch: device buffer of n * 416 bytes.
+ *   hm_mlp_adam     one Adam step (beta 0.9 / 0.999, eps 1e-8, bias
+ *                   correction for `step` >= 1) on params, moments m and v.
+ *   hm_mlp_train    `epochs` passes of minibatch Adam (batch rows, learning
+ *                   rate lr) over the rows shuffled once with Philox(seed);
+ *                   h_loss (host, may be NULL) receives each epoch's mean
+ *                   loss. Synchronous.
+ */
+int hm_mlp_num_params(void);
+hm_status hm_mlp_forward(const float* d_params, const float* d_x, int64_t n, float* d_y,
+                         void* stream);
+hm_status hm_mlp_backward(const float* d_params, const float* d_x, const float* d_target,
+                          int64_t n, float* d_grad, float* d_loss_sum, void* d_scratch,
+                          void* stream);
+hm_status hm_mlp_adam(float* d_params, const float* d_grad, float* d_m, float* d_v, int step,
+                      float lr, void* stream);
+hm_status hm_mlp_train(float* d_params, const float* d_x, const float* d_target, int64_t n,
+                       int epochs, int64_t batch, float lr, uint64_t seed, float* h_loss,
+                       void* stream);
+
+/*
+ * Training targets: d_target[row] = log(sqrt(sum_c (n_{e,c} / countmax_c /
+ * T_c)^2) + eps) over classes with T_c > 0, from hm_contributions' output and
+ * the exact counts d_exact_hist (uint64[ncls]); sqrt(sum ...) is the
+ * per-hyperedge importance that minimises sum_c Var(T^_c) / T_c^2 for
+ * with-replacement Hansen-Hurwitz sampling. Synchronous.
+ */
+hm_status hm_proposal_targets(hm_graph* g, int order, const uint32_t* d_contrib,
+                              const uint64_t* d_exact_hist, float eps, float* d_target,
+                              void* stream);
+
+/*
+ * Integer proposal for hm_count_sampled: within stratum s,
+ * w_e = exp(f(x_e) - max_s f), p_e = (1 - lambda) w_e / sum_s w + lambda /
+ * |E_s| (0 < lambda <= 1 keeps every p_e > 0), and
+ * d_q[row] = min(2^32 - 1, 1 + floor(p_e * |E_s| * 1024)) (device uint32).
+ * Reductions run in a fixed order: q is reproducible. Synchronous.
+ */
+hm_status hm_proposal_weights(hm_graph* g, int order, const float* d_params, float lambda,
+                              uint32_t* d_q, void* stream);
+
 /*
  * Null-model batch: the counting step repeated on randomised hypergraphs
  * (Sec. 6.3 compares observed frequencies with those of configuration-model

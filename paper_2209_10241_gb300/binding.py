@@ -44,6 +44,16 @@ _SIGS = {
                                                 ctypes.c_uint64, _vp, _vp, _vp, _vp]),
     "hm_count_null_batch": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int,
                                            ctypes.c_int, ctypes.c_uint64, _vp, _vp]),
+    "hm_contributions": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "hm_features": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "hm_mlp_num_params": (ctypes.c_int, []),
+    "hm_mlp_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, _vp]),
+    "hm_mlp_backward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp]),
+    "hm_mlp_adam": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_float, _vp]),
+    "hm_mlp_train": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
+                                    ctypes.c_float, ctypes.c_uint64, _vp, _vp]),
+    "hm_proposal_targets": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_float, _vp, _vp]),
+    "hm_proposal_weights": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_float, _vp, _vp]),
     "hm_count_exact_host": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int,
                                            _vp, _vp]),
     "hm_work_totals": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
@@ -254,3 +264,74 @@ def work_totals(g: Graph, order: int, stream=None) -> dict:
 def launch_count() -> int:
     """Kernels launched by libhm.so so far in this process."""
     return int(load().hm_launch_count())
+
+
+def _rows(g: Graph, order: int) -> int:
+    return sum(g.count(s) for s in range(2, order + 1))
+
+
+def contributions(g: Graph, order: int, stream=None) -> torch.Tensor:
+    """hm_contributions: int32 device tensor [rows, ncls] holding the uint32 counts n_{e,c}."""
+    out = torch.empty((_rows(g, order), num_classes(order)), dtype=torch.int32, device="cuda")
+    _check(load().hm_contributions(g._h, order, _dptr(out), _stream(stream)))
+    return out
+
+
+def features(g: Graph, order: int, stream=None) -> torch.Tensor:
+    """hm_features: float32 device tensor [rows, 16]."""
+    out = torch.empty((_rows(g, order), 16), dtype=torch.float32, device="cuda")
+    _check(load().hm_features(g._h, order, _dptr(out), _stream(stream)))
+    return out
+
+
+def mlp_num_params() -> int:
+    return int(load().hm_mlp_num_params())
+
+
+def mlp_forward(params: torch.Tensor, x: torch.Tensor, stream=None) -> torch.Tensor:
+    y = torch.empty(x.shape[0], dtype=torch.float32, device="cuda")
+    _check(load().hm_mlp_forward(_dptr(params), _dptr(x), x.shape[0], _dptr(y), _stream(stream)))
+    return y
+
+
+def mlp_backward(params: torch.Tensor, x: torch.Tensor, target: torch.Tensor, stream=None):
+    """Gradient of mean((y - target)^2); returns (grad float32[P], sum of squared errors)."""
+    n = x.shape[0]
+    grad = torch.empty(mlp_num_params(), dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    scratch = torch.empty(max(1, n * (16 + 3 * 64) * 2), dtype=torch.uint8, device="cuda")
+    _check(load().hm_mlp_backward(_dptr(params), _dptr(x), _dptr(target), n, _dptr(grad),
+                                  _dptr(loss), _dptr(scratch), _stream(stream)))
+    return grad, loss
+
+
+def mlp_adam(params, grad, m, v, step: int, lr: float, stream=None):
+    _check(load().hm_mlp_adam(_dptr(params), _dptr(grad), _dptr(m), _dptr(v), int(step),
+                              float(lr), _stream(stream)))
+
+
+def mlp_train(params: torch.Tensor, x: torch.Tensor, target: torch.Tensor, epochs: int,
+              batch: int = 8192, lr: float = 1e-3, seed: int = 0, stream=None):
+    """hm_mlp_train in place on params; returns the mean loss of every epoch."""
+    losses = (ctypes.c_float * max(1, epochs))()
+    _check(load().hm_mlp_train(_dptr(params), _dptr(x), _dptr(target), x.shape[0], int(epochs),
+                               int(batch), float(lr), int(seed) & (2**64 - 1), losses,
+                               _stream(stream)))
+    return [float(losses[i]) for i in range(epochs)]
+
+
+def proposal_targets(g: Graph, order: int, contrib: torch.Tensor, exact: torch.Tensor,
+                     eps: float = 1e-9, stream=None) -> torch.Tensor:
+    out = torch.empty(contrib.shape[0], dtype=torch.float32, device="cuda")
+    _check(load().hm_proposal_targets(g._h, order, _dptr(contrib), _dptr(exact), float(eps),
+                                      _dptr(out), _stream(stream)))
+    return out
+
+
+def proposal_weights(g: Graph, order: int, params: torch.Tensor, lam: float = 0.1,
+                     stream=None) -> torch.Tensor:
+    """Integer proposal q (int32 tensor holding uint32) for hm_count_sampled."""
+    q = torch.empty(_rows(g, order), dtype=torch.int32, device="cuda")
+    _check(load().hm_proposal_weights(g._h, order, _dptr(params), float(lam), _dptr(q),
+                                      _stream(stream)))
+    return q

@@ -248,3 +248,20 @@ def random_tiny(n: int, m: int, max_size: int, seed: int, dup_frac: float = 0.0)
             e = e + [e[0]]
         edges.append(e)
     return from_edges(edges, n, name=f"tiny-{n}-{m}-{seed}")
+
+
+def mlp_init_params(seed: int) -> np.ndarray:
+    """Seeded He-uniform initial weights of the 16-64-64-1 proposal MLP
+    (packed W1[16][64] | b1 | W2[64][64] | b2 | w3[64] | b3, float32)."""
+    n_in, hid = 16, 64
+    sizes = [n_in * hid, hid, hid * hid, hid, hid, 1]
+    total = sum(sizes)
+    st = Stream(seed, 11)
+    u = (st.u64(total) >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    p = np.zeros(total)
+    o_w1, o_w2 = 0, n_in * hid + hid
+    o_w3 = o_w2 + hid * hid + hid
+    p[o_w1:o_w1 + n_in * hid] = (2 * u[o_w1:o_w1 + n_in * hid] - 1) * np.sqrt(6.0 / n_in)
+    p[o_w2:o_w2 + hid * hid] = (2 * u[o_w2:o_w2 + hid * hid] - 1) * np.sqrt(6.0 / hid)
+    p[o_w3:o_w3 + hid] = (2 * u[o_w3:o_w3 + hid] - 1) * np.sqrt(6.0 / hid)
+    return p.astype(np.float32)
