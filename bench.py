@@ -42,10 +42,10 @@ ALU_LANES_PER_SM_CLK = 64
 # kernel -> (unit, ALU lane-ops per unit, DRAM bytes per launch); None = not measured
 # (ops = sm__sass_thread_inst_executed_op_{integer,bit}_pred_on per unit, profiles/census_bits_f2f-330.md)
 ROOFLINE = {
-    "census_Sb": ("item", 969.4, 1_025_000),
-    "census_Pb": ("item", 987.9, 820_000),
-    "census_TX": ("candidate", 283.6, 656_000),
-    "census_Q": ("candidate", 384.6, 298_000),
+    "census_Sb": ("item", None, None),
+    "census_Pb": ("item", None, None),
+    "census_TX": ("candidate", None, None),
+    "census_Q": ("candidate", None, None),
     "census_Wb": ("item", None, None),
     "census_S": ("candidate", None, None),
     "census_P": ("candidate", None, None),
@@ -158,8 +158,10 @@ def measure_sampler(hm, stream, scale=0.004, budgets=(12_000, 60_000, 300_000), 
 
     Communication-shaped graph (comm-5m generator at `scale`); the proposal is
     trained on a separate instance of the same generator from exact
-    per-hyperedge contributions; error = mean over classes with T_c >= 100 of
-    |T^_c - T_c| / T_c against the exact census, averaged over seeds.
+    per-hyperedge contributions; "learned" weights draws by t_e / sqrt(cost_e)
+    (beta = 1/2, error per unit of GPU time), "learned_per_draw" by t_e
+    (beta = 0); error = mean over classes with T_c >= 100 of |T^_c - T_c| / T_c
+    against the exact census, averaged over seeds.
     """
     import numpy as np
     import torch
@@ -181,13 +183,14 @@ def measure_sampler(hm, stream, scale=0.004, budgets=(12_000, 60_000, 300_000), 
     exact_ms, T = _event_ms(lambda: hm.count_exact(g, k), stream)
     T = T.cpu().numpy().astype(np.float64)
     big = T >= 100
-    q_ms, q = _event_ms(lambda: hm.proposal_weights(g, k, params, lam=0.1), stream)
+    q_ms, q = _event_ms(lambda: hm.proposal_weights(g, k, params, lam=0.1, beta=0.5), stream)
+    q0 = hm.proposal_weights(g, k, params, lam=0.1, beta=0.0)
     rows = []
     for S in budgets:
         split = {2: S // 6, 4: S // 3}
         split[3] = S - split[2] - split[4]
         rec = {"S": S}
-        for name, qq in (("uniform", None), ("learned", q)):
+        for name, qq in (("uniform", None), ("learned", q), ("learned_per_draw", q0)):
             ms, errs = [], []
             for r in range(seeds):
                 t, (est, _) = _event_ms(lambda: hm.count_sampled(g, k, samples=split,
@@ -204,8 +207,10 @@ def measure_sampler(hm, stream, scale=0.004, budgets=(12_000, 60_000, 300_000), 
             "train_loss_first_last": [losses[0], losses[-1]], "by_budget": rows}
 
 
-def measure_null(hm, stream, hyperedges=(50_000, 69_000, 97_000, 134_000, 186_000, 259_000,
-                                         360_000, 500_000), models=8):
+NULL_BASES = (50_000, 69_000, 97_000, 134_000, 186_000, 259_000, 360_000, 500_000)
+
+
+def measure_null(hm, stream, hyperedges=NULL_BASES, models=8):
     """Null-model batch: len(hyperedges) face-to-face-shaped bases x `models`
     stub shuffles counted at order 4 (64 uneven graphs, one union per 64)."""
     from paper_2209_10241_gb300 import synth
@@ -253,6 +258,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sampler and null-batch measurements")
+    ap.add_argument("--only", choices=["sampler", "null"], default=None,
+                    help="run one of the extra measurements alone (for profiling)")
+    ap.add_argument("--null-bases", type=int, default=8,
+                    help="number of null-model bases (log-spaced 50k-500k hyperedges)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -268,6 +277,13 @@ def main():
     from paper_2209_10241_gb300 import synth
 
     torch.cuda.set_device(local)
+    if args.only:
+        hm.load()
+        stream = torch.cuda.current_stream()
+        res = (measure_sampler(hm, stream) if args.only == "sampler"
+               else measure_null(hm, stream, hyperedges=NULL_BASES[:args.null_bases]))
+        print(json.dumps({"only": args.only, **res}), flush=True)
+        return
     if world > 1:
         dist.init_process_group("nccl")
     hm.load()
@@ -401,7 +417,7 @@ def main():
     }
     if world == 1 and not args.no_extras:
         line["sampler"] = measure_sampler(hm, stream)
-        line["null_batch"] = measure_null(hm, stream)
+        line["null_batch"] = measure_null(hm, stream, hyperedges=NULL_BASES[:args.null_bases])
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(h, args.order)
     print(json.dumps(line), flush=True)

@@ -263,14 +263,18 @@ hm_status hm_proposal_targets(hm_graph* g, int order, const uint32_t* d_contrib,
                               void* stream);
 
 /*
- * Integer proposal for hm_count_sampled: within stratum s,
- * w_e = exp(f(x_e) - max_s f), p_e = (1 - lambda) w_e / sum_s w + lambda /
- * |E_s| (0 < lambda <= 1 keeps every p_e > 0), and
- * d_q[row] = min(2^32 - 1, 1 + floor(p_e * |E_s| * 1024)) (device uint32).
- * Reductions run in a fixed order: q is reproducible. Synchronous.
+ * Integer proposal for hm_count_sampled: within stratum s, with
+ * z_e = f(x_e) - beta * log1p(cost_e), cost_e = the number of sets a draw of
+ * e enumerates (feature 9), w_e = exp(z_e - max_s z),
+ * p_e = (1 - lambda) w_e / sum_s w + lambda / |E_s| (0 < lambda <= 1 keeps
+ * every p_e > 0), and d_q[row] = min(2^32 - 1, 1 + floor(p_e * |E_s| * 1024))
+ * (device uint32). beta in [0, 1]: 0 minimises the variance per draw, 1/2
+ * the variance per unit of enumeration work (draw probability proportional
+ * to t_e / sqrt(cost_e)). Reductions run in a fixed order: q is
+ * reproducible. Synchronous.
  */
 hm_status hm_proposal_weights(hm_graph* g, int order, const float* d_params, float lambda,
-                              uint32_t* d_q, void* stream);
+                              float beta, uint32_t* d_q, void* stream);
 
 /*
  * Null-model batch: the counting step repeated on randomised hypergraphs

@@ -53,7 +53,8 @@ _SIGS = {
     "hm_mlp_train": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
                                     ctypes.c_float, ctypes.c_uint64, _vp, _vp]),
     "hm_proposal_targets": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_float, _vp, _vp]),
-    "hm_proposal_weights": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_float, _vp, _vp]),
+    "hm_proposal_weights": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_float,
+                                           ctypes.c_float, _vp, _vp]),
     "hm_count_exact_host": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int,
                                            _vp, _vp]),
     "hm_work_totals": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
@@ -329,9 +330,9 @@ def proposal_targets(g: Graph, order: int, contrib: torch.Tensor, exact: torch.T
 
 
 def proposal_weights(g: Graph, order: int, params: torch.Tensor, lam: float = 0.1,
-                     stream=None) -> torch.Tensor:
+                     beta: float = 0.0, stream=None) -> torch.Tensor:
     """Integer proposal q (int32 tensor holding uint32) for hm_count_sampled."""
     q = torch.empty(_rows(g, order), dtype=torch.int32, device="cuda")
-    _check(load().hm_proposal_weights(g._h, order, _dptr(params), float(lam), _dptr(q),
-                                      _stream(stream)))
+    _check(load().hm_proposal_weights(g._h, order, _dptr(params), float(lam), float(beta),
+                                      _dptr(q), _stream(stream)))
     return q

@@ -256,6 +256,23 @@ __global__ void k_bitmap_tuples(const int4* __restrict__ e, int64_t m, int s, in
   }
 }
 
+// exact triple rows: for 3-hyperedge {a, b, c}, bit c of rows (a, b), (b, a),
+// bit b of rows (a, c), (c, a), bit a of rows (b, c), (c, b)
+__global__ void k_tri3_rows(const int4* __restrict__ e3, int64_t m, int32_t n, int32_t bw,
+                            uint32_t* __restrict__ rows) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int4 e = e3[t];
+    const int32_t v[3] = {e.x, e.y, e.z};
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        if (i == j) continue;
+        const int32_t c = v[3 - i - j];
+        atomicOr(rows + ((size_t)v[i] * n + v[j]) * bw + (c >> 5), 1u << (c & 31));
+      }
+  }
+}
+
 __global__ void k_max_degree(const int64_t* __restrict__ off, int32_t n, int* out) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x)
@@ -285,12 +302,25 @@ uint64_t table_capacity(int64_t m) {
   return c;
 }
 
-bool use_bitmap(int64_t n, int64_t row_ids) {
+// Dense pair bitmaps: up to 32 MB for one graph; up to 1 GB for a union of
+// graphs (block-diagonal rows of one block each), whose alternative is hash
+// probes into tables far larger than L2.
+bool use_bitmap(int64_t n, int64_t row_ids, bool union_of_graphs) {
   const char* env = std::getenv("HM_PAIR_BITMAP");
   if (env && env[0] == '0') return false;
   const int64_t bytes = n * ((row_ids + 31) / 32) * 4;
   if (env && env[0] == '1') return bytes <= (1ll << 31);
-  return bytes <= (32ll << 20);
+  return bytes <= (union_of_graphs ? (1ll << 30) : (32ll << 20));
+}
+
+// exact triple rows cost n * n * ceil(n/32) words: kept for one graph up to
+// 64 MB (n <= ~800); HM_TRIPLE_ROWS=0 disables them
+bool use_tri3(int64_t n, int32_t block) {
+  if (block) return false;
+  const char* env = std::getenv("HM_TRIPLE_ROWS");
+  if (env && env[0] == '0') return false;
+  if (env && env[0] == '1') return n * n * ((n + 31) / 32) * 4 <= (1ll << 31);
+  return n * n * ((n + 31) / 32) * 4 <= (64ll << 20);
 }
 
 template <class T>
@@ -303,6 +333,7 @@ T* keep(hm_graph* g, T* p) {
 
 void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets, int64_t m,
                  int32_t n, int kmax, cudaStream_t s, int32_t block) {
+  keep_pool_memory();
   g->n = n;
   g->kmax = kmax;
   g->block = block;
@@ -340,38 +371,43 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
                                                  err.p, c2.p, c3hi.p, c3lo.p, c4hi.p, c4lo.p);
     HM_KCHECK();
   }
-  // sort + unique per size: the ascending order of E_s
+  // sort + unique per size: the ascending order of E_s (one synchronisation)
+  DBuf<uint32_t> kept(3, s);
+  HM_CUDA(cudaMemsetAsync(kept.p, 0, 3 * sizeof(uint32_t), s));
   radix_sort_u64(c2.p, nullptr, (int64_t)hc[2], 2 * b, s);
-  const int64_t m2 = unique_sorted(nullptr, c2.p, (int64_t)hc[2], s);
-  int64_t m3 = 0, m4 = 0;
+  unique_sorted_async(nullptr, c2.p, (int64_t)hc[2], kept.p, s);
   if (kmax >= 3) {
     int bits3 = 3 * b;
     radix_sort_u128(c3hi.p, c3lo.p, (int64_t)hc[3], bits3 > 64 ? bits3 - 64 : 0,
                     bits3 > 64 ? 64 : bits3, s);
-    m3 = unique_sorted(c3hi.p, c3lo.p, (int64_t)hc[3], s);
+    unique_sorted_async(c3hi.p, c3lo.p, (int64_t)hc[3], kept.p + 1, s);
   }
   if (kmax >= 4) {
     int bits4 = 4 * b;
     radix_sort_u128(c4hi.p, c4lo.p, (int64_t)hc[4], bits4 > 64 ? bits4 - 64 : 0,
                     bits4 > 64 ? 64 : bits4, s);
-    m4 = unique_sorted(c4hi.p, c4lo.p, (int64_t)hc[4], s);
+    unique_sorted_async(c4hi.p, c4lo.p, (int64_t)hc[4], kept.p + 2, s);
   }
+  uint32_t hk[3] = {0, 0, 0};
+  HM_CUDA(cudaMemcpyAsync(hk, kept.p, sizeof hk, cudaMemcpyDeviceToHost, s));
+  HM_CUDA(cudaStreamSynchronize(s));
+  const int64_t m2 = hk[0], m3 = kmax >= 3 ? hk[1] : 0, m4 = kmax >= 4 ? hk[2] : 0;
   g->counts[2] = m2;
   if (kmax >= 3) g->counts[3] = m3;
   if (kmax >= 4) g->counts[4] = m4;
 
-  g->e2 = keep(g, dalloc<uint64_t>(m2));
+  g->e2 = keep(g, dalloc<uint64_t>(m2, s));
   if (m2) {
     k_unpack2<<<grid1d(m2), T256, 0, s>>>(c2.p, m2, b, g->e2);
     HM_KCHECK();
   }
   if (m3) {
-    g->e3 = keep(g, dalloc<int4>(m3));
+    g->e3 = keep(g, dalloc<int4>(m3, s));
     k_unpack34<<<grid1d(m3), T256, 0, s>>>(c3hi.p, c3lo.p, m3, 3, b, g->e3);
     HM_KCHECK();
   }
   if (m4) {
-    g->e4 = keep(g, dalloc<int4>(m4));
+    g->e4 = keep(g, dalloc<int4>(m4, s));
     k_unpack34<<<grid1d(m4), T256, 0, s>>>(c4hi.p, c4lo.p, m4, 4, b, g->e4);
     HM_KCHECK();
   }
@@ -385,7 +421,7 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   // hash sets (load <= 0.5)
   {
     uint64_t cap = table_capacity(m2);
-    g->h2 = keep(g, dalloc<uint64_t>(cap));
+    g->h2 = keep(g, dalloc<uint64_t>(cap, s));
     g->h2_mask = cap - 1;
     HM_CUDA(cudaMemsetAsync(g->h2, 0xFF, cap * sizeof(uint64_t), s));
     if (m2) {
@@ -395,7 +431,7 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   }
   if (m3) {
     uint64_t cap = table_capacity(m3);
-    g->h3 = keep(g, dalloc<int4>(cap));
+    g->h3 = keep(g, dalloc<int4>(cap, s));
     g->h3_mask = cap - 1;
     HM_CUDA(cudaMemsetAsync(g->h3, 0xFF, cap * sizeof(int4), s));
     k_insert4<<<grid1d(m3), T256, 0, s>>>(g->e3, m3, g->h3, g->h3_mask, err.p);
@@ -403,7 +439,7 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   }
   if (m4) {
     uint64_t cap = table_capacity(m4);
-    g->h4 = keep(g, dalloc<int4>(cap));
+    g->h4 = keep(g, dalloc<int4>(cap, s));
     g->h4_mask = cap - 1;
     HM_CUDA(cudaMemsetAsync(g->h4, 0xFF, cap * sizeof(int4), s));
     k_insert4<<<grid1d(m4), T256, 0, s>>>(g->e4, m4, g->h4, g->h4_mask, err.p);
@@ -412,8 +448,8 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   HM_CUDA(cudaGetLastError());
 
   // CSR of pair neighbours, sorted
-  g->off2 = keep(g, dalloc<int64_t>((size_t)n + 1));
-  g->adj2 = keep(g, dalloc<int32_t>(2 * m2));
+  g->off2 = keep(g, dalloc<int64_t>((size_t)n + 1, s));
+  g->adj2 = keep(g, dalloc<int32_t>(2 * m2, s));
   {
     DBuf<uint64_t> keys(2 * m2, s);
     if (m2) {
@@ -426,9 +462,9 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     csr_offsets(keys.p, 2 * m2, b, n, g->off2, s);
   }
   // CSR of triple incidence, ascending triple index
-  g->off3 = keep(g, dalloc<int64_t>((size_t)n + 1));
+  g->off3 = keep(g, dalloc<int64_t>((size_t)n + 1, s));
   if (m3) {
-    g->inc3 = keep(g, dalloc<int32_t>(3 * m3));
+    g->inc3 = keep(g, dalloc<int32_t>(3 * m3, s));
     const int tb = bits_for(m3);
     DBuf<uint64_t> keys(3 * m3, s);
     k_triple_incidence<<<grid1d(m3), T256, 0, s>>>(g->e3, m3, tb, keys.p);
@@ -441,34 +477,43 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     HM_CUDA(cudaMemsetAsync(g->off3, 0, ((size_t)n + 1) * sizeof(int64_t), s));
   }
   if (m2) {
-    g->pairpos = keep(g, dalloc<int2>(m2));
+    g->pairpos = keep(g, dalloc<int2>(m2, s));
     k_pairpos<<<grid1d(m2), T256, 0, s>>>(g->e2, m2, g->off2, g->adj2, g->pairpos);
     HM_KCHECK();
   }
-  if (use_bitmap(n, block ? block : n)) {
+  if (use_bitmap(n, block ? block : n, block != 0)) {
     g->bwords = ((block ? block : n) + 31) / 32;
     const hm::DevGraph gv = g->view();
     size_t words = (size_t)n * g->bwords;
-    g->bits2 = keep(g, dalloc<uint32_t>(words));
+    g->bits2 = keep(g, dalloc<uint32_t>(words, s));
     HM_CUDA(cudaMemsetAsync(g->bits2, 0, words * sizeof(uint32_t), s));
     if (m2) {
       k_bitmap<<<grid1d(m2), T256, 0, s>>>(g->e2, m2, g->bwords, gv.block, gv.block_inv,
                                            g->bits2);
       HM_KCHECK();
     }
-    g->bits3 = keep(g, dalloc<uint32_t>(words));
+    g->bits3 = keep(g, dalloc<uint32_t>(words, s));
     HM_CUDA(cudaMemsetAsync(g->bits3, 0, words * sizeof(uint32_t), s));
     if (m3) {
       k_bitmap_tuples<<<grid1d(m3), T256, 0, s>>>(g->e3, m3, 3, g->bwords, gv.block,
                                                   gv.block_inv, g->bits3);
       HM_KCHECK();
     }
-    g->bits4 = keep(g, dalloc<uint32_t>(words));
+    g->bits4 = keep(g, dalloc<uint32_t>(words, s));
     HM_CUDA(cudaMemsetAsync(g->bits4, 0, words * sizeof(uint32_t), s));
     if (m4) {
       k_bitmap_tuples<<<grid1d(m4), T256, 0, s>>>(g->e4, m4, 4, g->bwords, gv.block,
                                                   gv.block_inv, g->bits4);
       HM_KCHECK();
+    }
+    if (use_tri3(n, block)) {
+      const size_t tw = (size_t)n * n * g->bwords;
+      g->tri3 = keep(g, dalloc<uint32_t>(tw, s));
+      HM_CUDA(cudaMemsetAsync(g->tri3, 0, tw * sizeof(uint32_t), s));
+      if (m3) {
+        k_tri3_rows<<<grid1d(m3), T256, 0, s>>>(g->e3, m3, n, g->bwords, g->tri3);
+        HM_KCHECK();
+      }
     }
   }
   {
@@ -483,11 +528,27 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   HM_CHECK(!(herr & ERR_TABLE), HM_ETABLEFULL, "hash insertion exceeded its probe bound");
 }
 
+// Freed memory stays in the device pool for the next graph instead of going
+// back to the driver (process-local setting of this device's default pool).
+void keep_pool_memory() {
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep_all = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep_all);
+  }
+  done[dev] = true;
+}
+
 void free_graph(hm_graph* g) {
   if (!g) return;
-  for (void* p : g->owned) cudaFree(p);
+  // work that reads the graph may still be queued on any stream
+  cudaDeviceSynchronize();
+  for (void* p : g->owned) cudaFreeAsync(p, 0);
   for (auto* sp : {&g->W, &g->S, &g->P, &g->TX, &g->Wb, &g->Sb, &g->Pb})
-    if (sp->ws) cudaFree(sp->ws);
+    if (sp->ws) cudaFreeAsync(sp->ws, 0);
   delete g;
 }
 

@@ -29,7 +29,10 @@
 // labelled mask in the class table; counts are aggregated per warp
 // (__match_any_sync) into shared-memory bins and flushed once per block.
 #include <cmath>
+#include <algorithm>
 #include <cstdlib>
+#include <initializer_list>
+#include <vector>
 
 #include "families.cuh"
 
@@ -47,7 +50,7 @@ constexpr int BIN_STRIDE = 176;
 template <class F, bool kBatched>
 __global__ void __launch_bounds__(CENSUS_THREADS)
     k_census(const DevGraph g, const F fam, const uint64_t* __restrict__ ws, int64_t A,
-             uint64_t total, const uint8_t* __restrict__ lut_g, int nmask, int ncls,
+             uint64_t total, int chunk, const uint8_t* __restrict__ lut_g, int nmask, int ncls,
              int ngraphs, unsigned long long* __restrict__ hist) {
   __shared__ unsigned long long bins[kBatched ? 1 : BIN_STRIDE];
   __shared__ unsigned int gbins[kBatched ? MAX_GRAPHS * BIN_STRIDE : 1];
@@ -61,12 +64,12 @@ __global__ void __launch_bounds__(CENSUS_THREADS)
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
-  const uint64_t nchunks = (total + CHUNK - 1) / CHUNK;
+  const uint64_t nchunks = (total + chunk - 1) / chunk;
   const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t cb = warp * 32; cb < nchunks; cb += nwarps * 32) {
-    const uint64_t g0 = (cb + lane) * CHUNK;
-    const uint64_t g1 = min(g0 + CHUNK, total);
+    const uint64_t g0 = (cb + lane) * chunk;
+    const uint64_t g1 = min(g0 + chunk, total);
     typename F::State st;
     int64_t a = 0;
     int32_t gid = 0;
@@ -78,7 +81,7 @@ __global__ void __launch_bounds__(CENSUS_THREADS)
       fam.begin(g, a, r, st);
       if (kBatched) gid = graph_of(g, fam.graph_node(g, a));
     }
-    for (int it = 0; it < CHUNK; ++it) {
+    for (int it = 0; it < chunk; ++it) {
       const uint64_t gi = g0 + it;
       int key = -1;
       if (gi < g1) {
@@ -243,53 +246,57 @@ unsigned grid1d(int64_t n) {
   return (unsigned)b;
 }
 
-void ensure_space(hm_graph* g, hm_graph::Space& sp, char fam, cudaStream_t s) {
-  if (sp.ready) return;
-  int64_t A = 0;
-  if (fam == 'W' || fam == 'S') A = g->n;
-  if (fam == 'P') A = g->counts[2];
-  if (fam == 'X') A = g->kmax >= 3 ? g->counts[3] : 0;
-  if (fam == 'w' || fam == 's') A = g->n;
-  if (fam == 'p') A = g->counts[2];
-  DBuf<uint64_t> w(A, s);
-  uint64_t* ws = dalloc<uint64_t>((size_t)A + 1);
+// Prefix sums of the candidates per anchor for every family in `todo`, with
+// one host synchronisation for all of them (the totals size the launches).
+void ensure_spaces(hm_graph* g, std::initializer_list<std::pair<hm_graph::Space*, char>> todo,
+                   cudaStream_t s) {
+  std::vector<std::pair<hm_graph::Space*, char>> need;
+  for (auto& t : todo)
+    if (!t.first->ready) need.push_back(t);
+  if (need.empty()) return;
+  DBuf<uint64_t> totals(need.size(), s);
+  std::vector<uint64_t*> made;
   try {
-    if (A > 0) {
-      if (fam == 'W') {
-        k_ws_nodes<<<grid1d(A), 256, 0, s>>>(g->off2, g->n, 2, w.p);
+    for (size_t i = 0; i < need.size(); ++i) {
+      hm_graph::Space& sp = *need[i].first;
+      const char fam = need[i].second;
+      int64_t A = 0;
+      if (fam == 'W' || fam == 'S' || fam == 'w' || fam == 's') A = g->n;
+      if (fam == 'P' || fam == 'p') A = g->counts[2];
+      if (fam == 'X') A = g->kmax >= 3 ? g->counts[3] : 0;
+      DBuf<uint64_t> w(A, s);
+      uint64_t* ws = dalloc<uint64_t>((size_t)A + 1, s);
+      made.push_back(ws);
+      if (A > 0) {
+        if (fam == 'W' || fam == 'S')
+          k_ws_nodes<<<grid1d(A), 256, 0, s>>>(g->off2, g->n, fam == 'W' ? 2 : 3, w.p);
+        else if (fam == 'w' || fam == 's')
+          k_ws_nodes_bits<<<grid1d(A), 256, 0, s>>>(g->off2, g->n, fam == 'w' ? 2 : 3, w.p);
+        else if (fam == 'P')
+          k_ws_pairs<<<grid1d(A), 256, 0, s>>>(g->e2, A, g->off2, w.p);
+        else if (fam == 'p')
+          k_ws_pairs_bits<<<grid1d(A), 256, 0, s>>>(g->e2, A, g->off2, w.p);
+        else
+          k_ws_triples<<<grid1d(A), 256, 0, s>>>(g->e3, A, g->off2, g->off3, w.p);
         HM_KCHECK();
       }
-      if (fam == 'S') {
-        k_ws_nodes<<<grid1d(A), 256, 0, s>>>(g->off2, g->n, 3, w.p);
-        HM_KCHECK();
-      }
-      if (fam == 'P') {
-        k_ws_pairs<<<grid1d(A), 256, 0, s>>>(g->e2, A, g->off2, w.p);
-        HM_KCHECK();
-      }
-      if (fam == 'X') {
-        k_ws_triples<<<grid1d(A), 256, 0, s>>>(g->e3, A, g->off2, g->off3, w.p);
-        HM_KCHECK();
-      }
-      if (fam == 'w' || fam == 's') {
-        k_ws_nodes_bits<<<grid1d(A), 256, 0, s>>>(g->off2, g->n, fam == 'w' ? 2 : 3, w.p);
-        HM_KCHECK();
-      }
-      if (fam == 'p') {
-        k_ws_pairs_bits<<<grid1d(A), 256, 0, s>>>(g->e2, A, g->off2, w.p);
-        HM_KCHECK();
-      }
+      scan_exclusive_u64(w.p, ws, A, s);
+      HM_CUDA(cudaMemcpyAsync(totals.p + i, ws + A, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+      sp.anchors = A;
     }
-    scan_exclusive_u64(w.p, ws, A, s);
-    HM_CUDA(cudaMemcpyAsync(&sp.total, ws + A, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    std::vector<uint64_t> h(need.size());
+    HM_CUDA(cudaMemcpyAsync(h.data(), totals.p, h.size() * sizeof(uint64_t),
+                            cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < need.size(); ++i) {
+      need[i].first->ws = made[i];
+      need[i].first->total = h[i];
+      need[i].first->ready = true;
+    }
   } catch (...) {
-    cudaFree(ws);
+    for (uint64_t* p : made) cudaFreeAsync(p, s);
     throw;
   }
-  sp.ws = ws;
-  sp.anchors = A;
-  sp.ready = true;
 }
 
 // Persistent grid: SMs x resident blocks, capped by the work; with a union
@@ -346,13 +353,24 @@ void launch_family_t(const hm_graph* g, const F& fam, const hm_graph::Space* sp,
                      int order, unsigned long long* hist, cudaStream_t s) {
   const ClassTables& T = class_tables(order);
   const uint8_t* lut = device_lut(order);
-  const int blocks = grid_for((const void*)k_census<F, kBatched>, (total + CHUNK - 1) / CHUNK,
+  // consecutive candidates per lane: up to CHUNK, fewer when the family is
+  // too small to fill the GPU that way (every lane of a warp takes the same)
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    HM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const uint64_t lanes_wanted = (uint64_t)sms * 2048;
+  int chunk = (int)std::min<uint64_t>(CHUNK, (total + lanes_wanted - 1) / lanes_wanted);
+  if (chunk < 1) chunk = 1;
+  const int blocks = grid_for((const void*)k_census<F, kBatched>, (total + chunk - 1) / chunk,
                               total, kBatched);
   cudaEvent_t ev = nullptr;
   const bool tr = trace_on();
   if (tr) trace_begin(s, &ev);
   k_census<F, kBatched><<<blocks, CENSUS_THREADS, 0, s>>>(
-      g->view(), fam, sp ? sp->ws : nullptr, sp ? sp->anchors : 0, total, lut,
+      g->view(), fam, sp ? sp->ws : nullptr, sp ? sp->anchors : 0, total, chunk, lut,
       (int)T.lut.size(), T.ncls, num_graphs(g), hist);
   HM_KCHECK();
   if (tr) trace_end(F::kName, s, ev);
@@ -386,20 +404,20 @@ bool prefer_bits(const hm_graph* g, const hm_graph::Space& bits, uint64_t candid
 
 void prepare_census(hm_graph* g, int order, cudaStream_t s) {
   if (order == 3) {
-    ensure_space(g, g->W, 'W', s);
-    if (g->bits2) {
-      ensure_space(g, g->Wb, 'w', s);
-      g->useWb = prefer_bits(g, g->Wb, g->W.total);
-    }
+    if (g->bits2)
+      ensure_spaces(g, {{&g->W, 'W'}, {&g->Wb, 'w'}}, s);
+    else
+      ensure_spaces(g, {{&g->W, 'W'}}, s);
+    if (g->bits2) g->useWb = prefer_bits(g, g->Wb, g->W.total);
   } else {
     HM_CHECK(g->max_d2 < (1 << 21), HM_EUNSUPPORTED,
              "a node has 2^21 or more pair neighbours; order-4 star space overflows");
-    ensure_space(g, g->S, 'S', s);
-    ensure_space(g, g->P, 'P', s);
-    ensure_space(g, g->TX, 'X', s);
+    if (g->bits2)
+      ensure_spaces(g, {{&g->S, 'S'}, {&g->P, 'P'}, {&g->TX, 'X'}, {&g->Sb, 's'}, {&g->Pb, 'p'}},
+                    s);
+    else
+      ensure_spaces(g, {{&g->S, 'S'}, {&g->P, 'P'}, {&g->TX, 'X'}}, s);
     if (g->bits2) {
-      ensure_space(g, g->Sb, 's', s);
-      ensure_space(g, g->Pb, 'p', s);
       g->useSb = prefer_bits(g, g->Sb, g->S.total);
       g->usePb = prefer_bits(g, g->Pb, g->P.total);
     }

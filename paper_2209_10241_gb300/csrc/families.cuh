@@ -408,13 +408,16 @@ struct BitsW {
     const uint32_t *Tv = brow(g.bits3, bw, v), *Tx = brow(g.bits3, bw, x);
     const bool tvx = btest(g, g.bits3, v, x);
     const bool tri_ok = x > v;  // a triangle is kept at its smallest node
+    // exact rows: the 3-hyperedges {v, x, y} are known per word
+    const uint32_t* Rvx = g.tri3 ? g.tri3 + ((size_t)v * g.n + x) * bw : nullptr;
     unsigned long long nw = 0, nt = 0;
     for (int32_t w = xl >> 5; w < bw; ++w) {
-      const uint32_t Y = __ldg(Bv + w) & above(w, xl);
+      uint32_t Y = __ldg(Bv + w) & above(w, xl);
+      if (Rvx) Y &= ~__ldg(Rvx + w);
       if (!Y) continue;
       const uint32_t bx = __ldg(Bx + w);
       const uint32_t tri = tri_ok ? (Y & bx) : 0u, wed = Y & ~bx;
-      const uint32_t risky = tvx ? (__ldg(Tv + w) & __ldg(Tx + w)) : 0u;
+      const uint32_t risky = (tvx && !Rvx) ? (__ldg(Tv + w) & __ldg(Tx + w)) : 0u;
       nt += __popc(tri & ~risky);
       nw += __popc(wed & ~risky);
       uint32_t rb = (tri | wed) & risky;
@@ -457,9 +460,20 @@ struct BitsS {
     const int32_t v = (int32_t)a, bw = g.bwords, base = graph_base(g, v);
     const int32_t x = g.adj2[s.o + s.i], y = g.adj2[s.o + s.j];
     const int32_t vl = v - base, yl = y - base;
-    const bool tvx = btest(g, g.bits3, v, x), tvy = btest(g, g.bits3, v, y),
-               txy = btest(g, g.bits3, x, y);
-    if (tvx && tvy && txy && has_triple(g, v, x, y)) return;
+    // exact rows (when present) decide every 3-hyperedge of the candidates;
+    // otherwise the co-occurrence bitmaps filter and the risky bits are probed
+    const uint32_t* R = g.tri3;
+    const bool exact = R != nullptr;
+    const bool tvx = !exact && btest(g, g.bits3, v, x), tvy = !exact && btest(g, g.bits3, v, y),
+               txy = !exact && btest(g, g.bits3, x, y);
+    if (exact) {
+      if (btest(g, R + (size_t)v * g.n * bw, x, y)) return;  // {v, x, y}
+    } else if (tvx && tvy && txy && has_triple(g, v, x, y)) {
+      return;
+    }
+    const uint32_t* Rvx = exact ? R + ((size_t)v * g.n + x) * bw : nullptr;
+    const uint32_t* Rvy = exact ? R + ((size_t)v * g.n + y) * bw : nullptr;
+    const uint32_t* Rxy = exact ? R + ((size_t)x * g.n + y) * bw : nullptr;
     const bool qd = btest(g, g.bits4, v, x) && btest(g, g.bits4, v, y) &&
                     btest(g, g.bits4, x, y);
     const bool xy = btest(g, g.bits2, x, y);
@@ -470,7 +484,8 @@ struct BitsS {
     const uint32_t *Qv = brow(g.bits4, bw, v), *Qx = brow(g.bits4, bw, x), *Qy = brow(g.bits4, bw, y);
     unsigned long long c[4] = {0, 0, 0, 0};  // (xz, yz) = 00, 10, 01, 11
     for (int32_t w = yl >> 5; w < bw; ++w) {
-      const uint32_t Z = __ldg(Bv + w) & above(w, yl);
+      uint32_t Z = __ldg(Bv + w) & above(w, yl);
+      if (exact && Z) Z &= ~(__ldg(Rvx + w) | __ldg(Rvy + w) | __ldg(Rxy + w));
       if (!Z) continue;
       const uint32_t bx = __ldg(Bx + w), by = __ldg(By + w);
       uint32_t grp[4];
@@ -490,7 +505,8 @@ struct BitsS {
         const int b = __ffs(rb) - 1;
         rb &= rb - 1;
         const int32_t z = base + w * 32 + b;
-        if (has_triple(g, v, x, z) || has_triple(g, v, y, z) || has_triple(g, x, y, z) ||
+        if ((!exact && (has_triple(g, v, x, z) || has_triple(g, v, y, z) ||
+                        has_triple(g, x, y, z))) ||
             has_quad(g, v, x, y, z))
           continue;
         ++c[((bx >> b) & 1u) | (((by >> b) & 1u) << 1)];
@@ -530,9 +546,18 @@ struct BitsP {
     const int32_t u = s.u, v = s.v, bw = g.bwords, base = graph_base(g, u);
     const int32_t x = g.adj2[s.ou + s.i + (s.i >= s.pu ? 1 : 0)];
     if (btest(g, g.bits2, v, x)) return;  // v would have degree 3: family S
-    const bool tuv = btest(g, g.bits3, u, v), tux = btest(g, g.bits3, u, x),
-               tvx = btest(g, g.bits3, v, x);
-    if (tuv && tux && tvx && has_triple(g, u, v, x)) return;
+    const uint32_t* R = g.tri3;
+    const bool exact = R != nullptr;
+    const bool tuv = !exact && btest(g, g.bits3, u, v), tux = !exact && btest(g, g.bits3, u, x),
+               tvx = !exact && btest(g, g.bits3, v, x);
+    if (exact) {
+      if (btest(g, R + (size_t)u * g.n * bw, v, x)) return;  // {u, v, x}
+    } else if (tuv && tux && tvx && has_triple(g, u, v, x)) {
+      return;
+    }
+    const uint32_t* Ruv = exact ? R + ((size_t)u * g.n + v) * bw : nullptr;
+    const uint32_t* Rux = exact ? R + ((size_t)u * g.n + x) * bw : nullptr;
+    const uint32_t* Rvx = exact ? R + ((size_t)v * g.n + x) * bw : nullptr;
     const bool qd = btest(g, g.bits4, u, v) && btest(g, g.bits4, u, x) &&
                     btest(g, g.bits4, v, x);
     const bool c4ok = x > v;  // a 4-cycle is kept at its smallest pair: x > v, y > u
@@ -546,6 +571,7 @@ struct BitsP {
     for (int32_t w = 0; w < bw; ++w) {
       uint32_t Y = __ldg(Bv + w) & ~__ldg(Bu + w);
       if (w == uw) Y &= ~ubit;
+      if (exact && Y) Y &= ~(__ldg(Ruv + w) | __ldg(Rux + w) | __ldg(Rvx + w));
       if (!Y) continue;
       const uint32_t bx = __ldg(Bx + w);
       const uint32_t c4 = c4ok ? (Y & bx & above(w, ul)) : 0u, p4 = Y & ~bx;
@@ -561,7 +587,8 @@ struct BitsP {
         const int b = __ffs(rb) - 1;
         rb &= rb - 1;
         const int32_t y = base + w * 32 + b;
-        if (has_triple(g, u, v, y) || has_triple(g, u, x, y) || has_triple(g, v, x, y) ||
+        if ((!exact && (has_triple(g, u, v, y) || has_triple(g, u, x, y) ||
+                        has_triple(g, v, x, y))) ||
             has_quad(g, u, v, x, y))
           continue;
         if ((c4 >> b) & 1u)

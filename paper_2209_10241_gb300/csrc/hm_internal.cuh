@@ -92,11 +92,13 @@ struct DBuf {
   DBuf& operator=(const DBuf&) = delete;
 };
 
-// Device memory owned by a graph (plain cudaMalloc, freed by hm_free).
+// Device memory owned by a graph: taken from the device's stream-ordered
+// pool on the building stream, returned to it by hm_free.
+void keep_pool_memory();
 template <class T>
-T* dalloc(size_t count) {
+T* dalloc(size_t count, cudaStream_t s) {
   T* p = nullptr;
-  if (count) HM_CUDA(cudaMalloc((void**)&p, count * sizeof(T)));
+  if (count) HM_CUDA(cudaMallocAsync((void**)&p, count * sizeof(T), s));
   return p;
 }
 
@@ -120,6 +122,9 @@ void radix_sort_u128(uint64_t* hi, uint64_t* lo, int64_t n, int hi_bits, int lo_
 // Remove adjacent duplicates of a sorted key array in place; returns the
 // number kept (synchronises the stream). hi may be NULL for 64-bit keys.
 int64_t unique_sorted(uint64_t* hi, uint64_t* lo, int64_t n, cudaStream_t s);
+// The same without a host synchronisation: the number kept goes to *d_kept.
+void unique_sorted_async(uint64_t* hi, uint64_t* lo, int64_t n, uint32_t* d_kept,
+                         cudaStream_t s);
 // off[v] = first index i with (key[i] >> shift) >= v, for v in [0, num_nodes];
 // keys sorted ascending.
 void csr_offsets(const uint64_t* keys, int64_t n, int shift, int32_t num_nodes, int64_t* off,
@@ -209,6 +214,10 @@ struct DevGraph {
   const uint32_t* bits2;
   const uint32_t* bits3;
   const uint32_t* bits4;
+  // optional exact 3-hyperedge rows (one graph, small n): the row of the
+  // ordered pair (a, b) starts at word (a * n + b) * bwords and has bit c set
+  // iff {a, b, c} is a 3-hyperedge
+  const uint32_t* tri3;
   int32_t bwords;
   // 0 for one graph. Otherwise the graph is a disjoint union of graphs whose
   // node ids occupy consecutive blocks of `block` ids (graph of node v =
@@ -344,6 +353,7 @@ struct hm_graph {
   uint32_t* bits2 = nullptr;
   uint32_t* bits3 = nullptr;
   uint32_t* bits4 = nullptr;
+  uint32_t* tri3 = nullptr;
   int32_t bwords = 0;
   int32_t block = 0;  // see DevGraph::block
   int32_t max_d2 = 0;
@@ -384,6 +394,7 @@ struct hm_graph {
     g.bits2 = bits2;
     g.bits3 = bits3;
     g.bits4 = bits4;
+    g.tri3 = tri3;
     g.bwords = bwords;
     g.block = block;
     g.block_inv = block > 1 ? (uint64_t)((((unsigned __int128)1 << 64) + block - 1) / block) : 0;

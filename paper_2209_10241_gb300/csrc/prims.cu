@@ -243,6 +243,8 @@ __global__ void k_unique_scatter(const uint64_t* hi, const uint64_t* lo, int64_t
   }
 }
 
+__global__ void k_set_u32(uint32_t* p, uint32_t v) { *p = v; }
+
 __global__ void k_csr_offsets(const uint64_t* keys, int64_t n, int shift, int32_t nn,
                               int64_t* off) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n;
@@ -312,6 +314,26 @@ int64_t unique_sorted(uint64_t* hi, uint64_t* lo, int64_t n, cudaStream_t s) {
   HM_CUDA(cudaMemcpyAsync(lo, lo2.p, kept * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
   if (hi) HM_CUDA(cudaMemcpyAsync(hi, hi2.p, kept * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
   return kept;
+}
+
+void unique_sorted_async(uint64_t* hi, uint64_t* lo, int64_t n, uint32_t* d_kept,
+                         cudaStream_t s) {
+  if (n <= 1) {
+    k_set_u32<<<1, 1, 0, s>>>(d_kept, (uint32_t)n);
+    HM_KCHECK();
+    return;
+  }
+  DBuf<uint32_t> f(n, s), pos(n + 1, s);
+  DBuf<uint64_t> lo2(n, s), hi2(hi ? n : 0, s);
+  k_unique_flags<<<grid_for(n, 256), 256, 0, s>>>(hi, lo, n, f.p);
+  HM_KCHECK();
+  scan_exclusive<uint32_t>(f.p, pos.p, n, s);
+  k_unique_scatter<<<grid_for(n, 256), 256, 0, s>>>(hi, lo, n, f.p, pos.p, hi2.p, lo2.p);
+  HM_KCHECK();
+  HM_CUDA(cudaMemcpyAsync(d_kept, pos.p + n, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  // the first `kept` entries are the distinct keys; the rest is left over
+  HM_CUDA(cudaMemcpyAsync(lo, lo2.p, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+  if (hi) HM_CUDA(cudaMemcpyAsync(hi, hi2.p, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
 }
 
 void csr_offsets(const uint64_t* keys, int64_t n, int shift, int32_t num_nodes, int64_t* off,

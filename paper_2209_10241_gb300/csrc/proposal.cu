@@ -8,7 +8,10 @@
 // per-hyperedge contributions of contrib.cu, T_c the exact counts). The MLP
 // regresses log(t_e + eps) on the hyperedge's features.
 //
-// Proposal. Within stratum s: w_e = exp(f(x_e) - max_s f),
+// Proposal. Within stratum s, with z_e = f(x_e) - beta log1p(cost_e) (cost_e =
+// the number of sets a draw of e enumerates; beta = 1/2 makes the draw
+// probability proportional to t_e / sqrt(cost_e), the optimum when the
+// budget is GPU time rather than draws): w_e = exp(z_e - max_s z),
 // p_e = (1 - lambda) w_e / sum_s w + lambda / |E_s| (a defensive mixture, so
 // p_e > 0 everywhere and the estimator stays unbiased), and the integer
 // weight the sampler consumes is q_e = min(2^32 - 1, 1 + floor(p_e |E_s| 2^10)).
@@ -104,6 +107,15 @@ __global__ void k_combine_sum(const double* __restrict__ part, int nb, double* _
   }
 }
 
+// z_e = f(x_e) - beta * log1p(work_e): feature 9 is log1p of the number of
+// sets a draw of e enumerates, the cost of the draw
+__global__ void k_cost_adjust(float* __restrict__ y, const float* __restrict__ feat, int64_t n,
+                              float beta) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] -= beta * feat[i * 16 + 9];
+}
+
 __global__ void k_quantise(const float* __restrict__ y, int64_t n, const float* __restrict__ mx,
                            const double* __restrict__ sum, float lambda,
                            uint32_t* __restrict__ q) {
@@ -160,7 +172,7 @@ void proposal_targets(const hm_graph* g, int order, const uint32_t* contrib,
 }
 
 void proposal_weights(const hm_graph* g, int order, const float* params, float lambda,
-                      uint32_t* q, cudaStream_t s) {
+                      float beta, uint32_t* q, cudaStream_t s) {
   int64_t rows = 0;
   for (int k = 2; k <= order; ++k) rows += g->counts[k];
   if (rows == 0) return;
@@ -168,6 +180,10 @@ void proposal_weights(const hm_graph* g, int order, const float* params, float l
   DBuf<double> dpart(RED_BLOCKS, s), sum(1, s);
   features(g, order, feat.p, s);
   mlp_forward(params, feat.p, rows, y.p, s);
+  if (beta != 0.f) {
+    k_cost_adjust<<<grid_n(rows), 256, 0, s>>>(y.p, feat.p, rows, beta);
+    HM_KCHECK();
+  }
   int64_t off = 0;
   for (int k = 2; k <= order; ++k) {
     const int64_t n = g->counts[k];
@@ -242,13 +258,14 @@ hm_status hm_proposal_targets(hm_graph* g, int order, const uint32_t* d_contrib,
 }
 
 hm_status hm_proposal_weights(hm_graph* g, int order, const float* d_params, float lambda,
-                              uint32_t* d_q, void* stream) {
+                              float beta, uint32_t* d_q, void* stream) {
   return hm::guarded([&] {
     HM_CHECK(g && d_params && d_q, HM_EINVAL, "NULL argument");
     HM_CHECK(order == 3 || order == 4, HM_EINVAL, "order must be 3 or 4");
     HM_CHECK(order <= g->kmax, HM_EUNSUPPORTED, "order exceeds the graph's max_order");
     HM_CHECK(lambda > 0.f && lambda <= 1.f, HM_EINVAL, "lambda must be in (0, 1]");
-    hm::proposal_weights(g, order, d_params, lambda, d_q, (cudaStream_t)stream);
+    HM_CHECK(beta >= 0.f && beta <= 1.f, HM_EINVAL, "beta must be in [0, 1]");
+    hm::proposal_weights(g, order, d_params, lambda, beta, d_q, (cudaStream_t)stream);
   });
 }
 

@@ -21,12 +21,22 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-@pytest.fixture(params=["hash", "bitmap", "sliced"])
-def pair_path(request, monkeypatch):
+MODES = ["hash", "bitmap", "sliced", "sliced_filter"]
+
+
+def _set_mode(monkeypatch, mode):
     """hash: pair probes in the hash set; bitmap: pair probes in the dense
-    bitmap, one candidate at a time; sliced: bit-sliced W/S/P families."""
-    monkeypatch.setenv("HM_PAIR_BITMAP", "0" if request.param == "hash" else "1")
-    monkeypatch.setenv("HM_DENSE_FAMILIES", "1" if request.param == "sliced" else "0")
+    bitmap, one candidate at a time; sliced: bit-sliced W/S/P families with
+    exact 3-hyperedge rows; sliced_filter: bit-sliced with the co-occurrence
+    filter and exact probes of the risky candidates."""
+    monkeypatch.setenv("HM_PAIR_BITMAP", "0" if mode == "hash" else "1")
+    monkeypatch.setenv("HM_DENSE_FAMILIES", "1" if mode.startswith("sliced") else "0")
+    monkeypatch.setenv("HM_TRIPLE_ROWS", "0" if mode == "sliced_filter" else "1")
+
+
+@pytest.fixture(params=MODES)
+def pair_path(request, monkeypatch):
+    _set_mode(monkeypatch, request.param)
     return request.param
 
 
@@ -105,10 +115,9 @@ def test_workloads_against_stored_oracle(hm, case, k):
 
 @pytest.mark.parametrize("case", ["f2f-330", "coauth-1m-s001"])
 @pytest.mark.parametrize("k", [3, 4])
-@pytest.mark.parametrize("mode", ["hash", "bitmap", "sliced"])
+@pytest.mark.parametrize("mode", MODES)
 def test_workload_every_path(hm, monkeypatch, case, k, mode):
-    monkeypatch.setenv("HM_PAIR_BITMAP", "0" if mode == "hash" else "1")
-    monkeypatch.setenv("HM_DENSE_FAMILIES", "1" if mode == "sliced" else "0")
+    _set_mode(monkeypatch, mode)
     rec = _golden(case)
     h = synth.workload(rec["workload"], seed=rec["seed"], scale=rec["scale"])
     got, _ = _gpu_hist(hm, h, k)

@@ -32,6 +32,7 @@ def _oracle_rows(bases, k, J, seed):
 def test_uneven_models(hm, monkeypatch, mode, k):
     monkeypatch.setenv("HM_PAIR_BITMAP", "0" if mode == "hash" else "1")
     monkeypatch.setenv("HM_DENSE_FAMILIES", "1" if mode == "sliced" else "0")
+    monkeypatch.setenv("HM_TRIPLE_ROWS", "1")  # unions never use them: still the filter path
     bases = [synth.workload("f2f-330", seed=1, scale=0.05),
              synth.random_tiny(25, 120, max_size=5, seed=3),
              synth.workload("uniform-200", seed=2, scale=0.3)]

@@ -127,11 +127,13 @@ def test_proposal_weights_and_sampler_parity(hm, trained):
     k = 4
     h = synth.workload("comm-5m", seed=8, scale=0.002)
     g = hm.from_host(h, 4)
-    q = hm.proposal_weights(g, k, trained["params"], lam=0.1)
+    q = hm.proposal_weights(g, k, trained["params"], lam=0.1, beta=0.5)
     qn = q.cpu().numpy().view(np.uint32).astype(np.uint64)
     assert (qn >= 1).all()
     # recompute q from the network's outputs: floor boundaries may move by one
-    y = hm.mlp_forward(trained["params"], hm.features(g, k)).cpu().numpy().astype(np.float64)
+    feat = hm.features(g, k)
+    y = hm.mlp_forward(trained["params"], feat).cpu().numpy().astype(np.float64)
+    y = y - 0.5 * feat.cpu().numpy()[:, 9].astype(np.float64)
     off = 0
     for s in range(2, k + 1):
         n = g.count(s)
