@@ -223,6 +223,49 @@ def measure_null(hm, stream, hyperedges=NULL_BASES, models=8):
             "sets_per_s": sets / (ms / 1e3)}
 
 
+def cpu_baseline_rows(budget_s: float = 8.0):
+    """The oracle beside the sampler and null-batch rows, each on a bounded sample."""
+    import oracle
+    from paper_2209_10241_gb300 import synth
+    threads = os.cpu_count() or 1
+    out = {}
+    # Alg. 4 as the oracle runs it, sample by sample (single-threaded)
+    h = synth.workload("comm-5m", seed=9, scale=0.004)
+    g = oracle.Graph.from_hypergraph(h, 4)
+    draws, t_used, S = 0, 0.0, 60
+    while t_used < budget_s and S < 1_000_000:
+        split = {2: S // 6, 4: S // 3}
+        split[3] = S - split[2] - split[4]
+        t0 = time.perf_counter()
+        g.sample(4, split, seed=100)
+        t_used += time.perf_counter() - t0
+        draws += S
+        S *= 2
+    out["sampler"] = {"value": draws / t_used, "unit": "draws/s", "cores": 1, "kind": "oracle",
+                      "sample": f"Alg. 4 on the comm-5m generator at scale 0.004 "
+                                f"({draws} draws in {t_used:.1f} s)"}
+    # one stub-shuffled null model of the smallest base, over a bounded set of ESU roots
+    b = synth.null_base(NULL_BASES[0], seed=100)
+    mem = oracle.stub_shuffle(b.members, b.offsets, seed=1, model=0)
+    gm = oracle.Graph(mem, b.offsets, b.num_nodes, 4)
+    # ESU root v enumerates the sets whose smallest id is v: the top ids are the
+    # light roots, so the sample grows downwards from the largest id
+    lo, t_used, sets, step = b.num_nodes, 0.0, 0, max(threads, 8)
+    while t_used < budget_s and lo > 0:
+        new_lo = max(0, lo - step)
+        t0 = time.perf_counter()
+        hist, _ = gm.census(4, threads=threads, roots=(new_lo, lo))
+        t_used += time.perf_counter() - t0
+        sets += int(hist.sum())
+        lo = new_lo
+        step *= 2
+    out["null_batch"] = {"value": sets / t_used, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"stub shuffle 0 of the {NULL_BASES[0]}-hyperedge base: ESU "
+                                   f"roots [{lo}, {b.num_nodes}) of {b.num_nodes} ({sets} sets "
+                                   f"in {t_used:.1f} s)"}
+    return out
+
+
 def run_reference(args, rank: int):
     if rank != 0:
         return
@@ -374,9 +417,9 @@ def main():
         return
 
     # dominant kernel from the trace (events on the launching stream)
-    per = {}
+    per, phases = {}, {}
     for name, ms in trace:
-        c = per.setdefault(name, [0, 0.0])
+        c = (phases if name.startswith("ingest_") else per).setdefault(name, [0, 0.0])
         c[0] += 1
         c[1] += ms
     dom = max(per, key=lambda k: per[k][1])
@@ -408,6 +451,7 @@ def main():
         "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4),
                         "share": round(v[1] / sum(x[1] for x in per.values()), 4)}
                     for k, v in sorted(per.items(), key=lambda kv: -kv[1][1])},
+        "ingest_ms_per_step": {k: round(v[1] / v[0], 4) for k, v in phases.items()},
         "roofline": roofline,
         "clocks": clocks,
         "gpu_launches": gpu_launches,
@@ -420,6 +464,8 @@ def main():
         line["null_batch"] = measure_null(hm, stream, hyperedges=NULL_BASES[:args.null_bases])
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(h, args.order)
+        if not args.no_extras:
+            line["cpu_baseline"]["rows"] = cpu_baseline_rows()
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

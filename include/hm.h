@@ -184,8 +184,9 @@ hm_status hm_count_exact_host(const int32_t* h_members, const int64_t* h_offsets
 
 /*
  * Kernel timing trace (no counterpart in the paper; instrumentation). While
- * enabled, every census kernel launch is bracketed by CUDA events recorded on
- * its launching stream. hm_trace_read waits for the recorded events, writes
+ * enabled, every census kernel launch, and each phase of hm_build's ingest
+ * (entries named "ingest_*", several launches each), is bracketed by CUDA
+ * events recorded on its launching stream. hm_trace_read waits for the recorded events, writes
  * up to max_entries (name, milliseconds) pairs -- names as NUL-terminated
  * strings in rows of name_len bytes of `names` (may be NULL), times in `ms`
  * (may be NULL) -- sets *count, and clears the trace.

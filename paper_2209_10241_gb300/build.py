@@ -46,11 +46,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
     headers.append(os.path.join(INCLUDE, "hm.h"))
     flags = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
                     "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
+    # tuning knobs for experiments, e.g. HM_NVCC_EXTRA="-DHM_BITS_MINBLOCKS=3"
+    flags += os.environ.get("HM_NVCC_EXTRA", "").split()
     procs, objs = [], []
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        if force or _stale(obj, [src] + headers):
+        if force or _stale(obj, [src] + headers) or os.environ.get("HM_NVCC_EXTRA"):
             cmd = [nvcc] + flags + ["-c", src, "-o", obj]
             if verbose:
                 print(" ".join(cmd), flush=True)

@@ -308,7 +308,7 @@ uint64_t table_capacity(int64_t m) {
 bool use_bitmap(int64_t n, int64_t row_ids, bool union_of_graphs) {
   const char* env = std::getenv("HM_PAIR_BITMAP");
   if (env && env[0] == '0') return false;
-  const int64_t bytes = n * ((row_ids + 31) / 32) * 4;
+  const int64_t bytes = n * ((row_ids + 127) / 128) * 16;
   if (env && env[0] == '1') return bytes <= (1ll << 31);
   return bytes <= (union_of_graphs ? (1ll << 30) : (32ll << 20));
 }
@@ -319,8 +319,9 @@ bool use_tri3(int64_t n, int32_t block) {
   if (block) return false;
   const char* env = std::getenv("HM_TRIPLE_ROWS");
   if (env && env[0] == '0') return false;
-  if (env && env[0] == '1') return n * n * ((n + 31) / 32) * 4 <= (1ll << 31);
-  return n * n * ((n + 31) / 32) * 4 <= (64ll << 20);
+  const int64_t bytes = n * n * ((n + 127) / 128) * 16;
+  if (env && env[0] == '1') return bytes <= (1ll << 31);
+  return bytes <= (64ll << 20);
 }
 
 template <class T>
@@ -342,6 +343,7 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   const int b = bits_for((int64_t)n - 1);
   g->bits = b;
 
+  TraceSpan span_norm("ingest_normalize", s);
   DBuf<unsigned long long> cnt(8, s), cnt2(8, s);
   DBuf<int> err(1, s);
   HM_CUDA(cudaMemsetAsync(cnt.p, 0, 8 * sizeof(unsigned long long), s));
@@ -353,6 +355,7 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
                                                   nullptr);
     HM_KCHECK();
   }
+  span_norm.end();
   unsigned long long hc[8];
   int herr = 0;
   HM_CUDA(cudaMemcpyAsync(hc, cnt.p, sizeof hc, cudaMemcpyDeviceToHost, s));
@@ -364,6 +367,7 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   g->counts[1] = m;
   g->counts[kmax + 1] = (int64_t)hc[kmax + 1];
 
+  TraceSpan span_sort("ingest_sort_unique", s);
   DBuf<uint64_t> c2(hc[2], s), c3hi(kmax >= 3 ? hc[3] : 0, s), c3lo(kmax >= 3 ? hc[3] : 0, s),
       c4hi(kmax >= 4 ? hc[4] : 0, s), c4lo(kmax >= 4 ? hc[4] : 0, s);
   if (m > 0) {
@@ -388,6 +392,7 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
                     bits4 > 64 ? 64 : bits4, s);
     unique_sorted_async(c4hi.p, c4lo.p, (int64_t)hc[4], kept.p + 2, s);
   }
+  span_sort.end();
   uint32_t hk[3] = {0, 0, 0};
   HM_CUDA(cudaMemcpyAsync(hk, kept.p, sizeof hk, cudaMemcpyDeviceToHost, s));
   HM_CUDA(cudaStreamSynchronize(s));
@@ -396,6 +401,7 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   if (kmax >= 3) g->counts[3] = m3;
   if (kmax >= 4) g->counts[4] = m4;
 
+  TraceSpan span_tables("ingest_tables", s);
   g->e2 = keep(g, dalloc<uint64_t>(m2, s));
   if (m2) {
     k_unpack2<<<grid1d(m2), T256, 0, s>>>(c2.p, m2, b, g->e2);
@@ -447,7 +453,9 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   }
   HM_CUDA(cudaGetLastError());
 
+  span_tables.end();
   // CSR of pair neighbours, sorted
+  TraceSpan span_csr("ingest_csr", s);
   g->off2 = keep(g, dalloc<int64_t>((size_t)n + 1, s));
   g->adj2 = keep(g, dalloc<int32_t>(2 * m2, s));
   {
@@ -481,8 +489,11 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     k_pairpos<<<grid1d(m2), T256, 0, s>>>(g->e2, m2, g->off2, g->adj2, g->pairpos);
     HM_KCHECK();
   }
+  span_csr.end();
+  TraceSpan span_bits("ingest_bitmaps", s);
   if (use_bitmap(n, block ? block : n, block != 0)) {
-    g->bwords = ((block ? block : n) + 31) / 32;
+    // rows padded to a multiple of four words: 16-byte aligned row loads
+    g->bwords = (((block ? block : n) + 127) / 128) * 4;
     const hm::DevGraph gv = g->view();
     size_t words = (size_t)n * g->bwords;
     g->bits2 = keep(g, dalloc<uint32_t>(words, s));
@@ -516,6 +527,7 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
       }
     }
   }
+  span_bits.end();
   {
     DBuf<int> mx(1, s);
     HM_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(int), s));

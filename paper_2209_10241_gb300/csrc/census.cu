@@ -132,9 +132,12 @@ __global__ void __launch_bounds__(CENSUS_THREADS)
 // Bit-sliced families: each item evaluates up to bwords*32 candidates and
 // adds its class counts to the block's bins.
 constexpr int BITS_CHUNK = 4;
+#ifndef HM_BITS_MINBLOCKS
+#define HM_BITS_MINBLOCKS 4  // resident blocks per SM the register budget targets
+#endif
 
 template <class F, bool kBatched>
-__global__ void __launch_bounds__(CENSUS_THREADS)
+__global__ void __launch_bounds__(CENSUS_THREADS, HM_BITS_MINBLOCKS)
     k_census_bits(const DevGraph g, const F fam, const uint64_t* __restrict__ ws, int64_t A,
                   uint64_t total, const uint8_t* __restrict__ lut_g, int nmask, int ncls,
                   int ngraphs, unsigned long long* __restrict__ hist) {
@@ -390,16 +393,22 @@ void launch_family(const hm_graph* g, const F& fam, const hm_graph::Space* sp, u
 
 // Work spaces and launches of the census of one order; shared with the
 // null-model batch.
-// The bit-sliced variant of a family is used when its items times bitmap
-// words is well below the number of candidates it replaces (each word costs
-// a few candidates' worth of instructions). HM_DENSE_FAMILIES=0 / 1 forces
-// the per-candidate / bit-sliced variants (the latter whenever bitmaps exist).
-bool prefer_bits(const hm_graph* g, const hm_graph::Space& bits, uint64_t candidates) {
+// The bit-sliced variant of a family is used when its estimated cost, items
+// x bitmap words scanned x the cost of a word relative to one per-candidate
+// evaluation (measured on this GPU: ~0.35 with 4-word loads, where the
+// per-candidate kernels run at ~12 % SIMT efficiency), is below the number of
+// candidates it replaces. Star and wedge items scan the words above their
+// second node (half a row on average), path items the whole row.
+// HM_DENSE_FAMILIES=0 / 1 forces the per-candidate / bit-sliced variants (the
+// latter whenever bitmaps exist).
+bool prefer_bits(const hm_graph* g, const hm_graph::Space& bits, uint64_t candidates,
+                 double row_fraction) {
   if (!g->bits2) return false;
   const char* env = std::getenv("HM_DENSE_FAMILIES");
   if (env && env[0] == '0') return false;
   if (env && env[0] == '1') return true;
-  return (double)bits.total * (double)g->bwords * 1.5 < (double)candidates;
+  const double words = 2.0 + (double)g->bwords * row_fraction;
+  return (double)bits.total * words * 0.35 < (double)candidates;
 }
 
 void prepare_census(hm_graph* g, int order, cudaStream_t s) {
@@ -408,7 +417,7 @@ void prepare_census(hm_graph* g, int order, cudaStream_t s) {
       ensure_spaces(g, {{&g->W, 'W'}, {&g->Wb, 'w'}}, s);
     else
       ensure_spaces(g, {{&g->W, 'W'}}, s);
-    if (g->bits2) g->useWb = prefer_bits(g, g->Wb, g->W.total);
+    if (g->bits2) g->useWb = prefer_bits(g, g->Wb, g->W.total, 0.5);
   } else {
     HM_CHECK(g->max_d2 < (1 << 21), HM_EUNSUPPORTED,
              "a node has 2^21 or more pair neighbours; order-4 star space overflows");
@@ -418,8 +427,8 @@ void prepare_census(hm_graph* g, int order, cudaStream_t s) {
     else
       ensure_spaces(g, {{&g->S, 'S'}, {&g->P, 'P'}, {&g->TX, 'X'}}, s);
     if (g->bits2) {
-      g->useSb = prefer_bits(g, g->Sb, g->S.total);
-      g->usePb = prefer_bits(g, g->Pb, g->P.total);
+      g->useSb = prefer_bits(g, g->Sb, g->S.total, 0.5);
+      g->usePb = prefer_bits(g, g->Pb, g->P.total, 1.0);
     }
   }
 }
@@ -427,19 +436,25 @@ void prepare_census(hm_graph* g, int order, cudaStream_t s) {
 void launch_census(const hm_graph* g, int order, unsigned long long* hist, cudaStream_t s) {
   if (order == 3) {
     launch_family(g, FamT3{}, nullptr, (uint64_t)g->counts[3], 3, hist, s);
-    if (g->useWb)
-      launch_bits(g, BitsW{}, g->Wb, 3, hist, s);
+    if (g->useWb && g->tri3)
+      launch_bits(g, BitsWT<true>{}, g->Wb, 3, hist, s);
+    else if (g->useWb)
+      launch_bits(g, BitsWT<false>{}, g->Wb, 3, hist, s);
     else
       launch_family(g, FamW{}, &g->W, g->W.total, 3, hist, s);
   } else {
     launch_family(g, FamQ{}, nullptr, (uint64_t)g->counts[4], 4, hist, s);
     launch_family(g, FamTX{}, &g->TX, g->TX.total, 4, hist, s);
-    if (g->useSb)
-      launch_bits(g, BitsS{}, g->Sb, 4, hist, s);
+    if (g->useSb && g->tri3)
+      launch_bits(g, BitsST<true>{}, g->Sb, 4, hist, s);
+    else if (g->useSb)
+      launch_bits(g, BitsST<false>{}, g->Sb, 4, hist, s);
     else
       launch_family(g, FamS{}, &g->S, g->S.total, 4, hist, s);
-    if (g->usePb)
-      launch_bits(g, BitsP{}, g->Pb, 4, hist, s);
+    if (g->usePb && g->tri3)
+      launch_bits(g, BitsPT<true>{}, g->Pb, 4, hist, s);
+    else if (g->usePb)
+      launch_bits(g, BitsPT<false>{}, g->Pb, 4, hist, s);
     else
       launch_family(g, FamP{}, &g->P, g->P.total, 4, hist, s);
   }

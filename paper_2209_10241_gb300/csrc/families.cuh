@@ -378,6 +378,16 @@ __device__ __forceinline__ bool btest(const DevGraph& g, const uint32_t* bm, int
   const int32_t c = b - graph_base(g, a);
   return (__ldg(bm + (size_t)a * g.bwords + (c >> 5)) >> (c & 31)) & 1u;
 }
+// four consecutive words of a bitmap row (rows are padded to a multiple of
+// four words, so w % 4 == 0 is 16-byte aligned)
+__device__ __forceinline__ void ld4(const uint32_t* p, uint32_t (&o)[4]) {
+  const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+  o[0] = v.x;
+  o[1] = v.y;
+  o[2] = v.z;
+  o[3] = v.w;
+}
+
 // bits of word w whose (local) id exceeds t
 __device__ __forceinline__ uint32_t above(int32_t w, int32_t t) {
   const int32_t tw = t >> 5;
@@ -387,8 +397,11 @@ __device__ __forceinline__ uint32_t above(int32_t w, int32_t t) {
   return b == 31 ? 0u : (~0u << (b + 1));
 }
 
-// k = 3, pairs-only triples: anchor v, item x in N2(v), y over ids > x in N2(v)
-struct BitsW {
+// k = 3, pairs-only triples: anchor v, item x in N2(v), y over ids > x in N2(v).
+// kExact: the graph has exact 3-hyperedge rows (otherwise the co-occurrence
+// filter and exact probes of the risky candidates).
+template <bool kExact>
+struct BitsWT {
   static constexpr const char* kName = "census_Wb";
   struct State {
     int64_t o;
@@ -406,29 +419,43 @@ struct BitsW {
     const int32_t x = g.adj2[s.o + s.i], xl = x - base;
     const uint32_t *Bv = brow(g.bits2, bw, v), *Bx = brow(g.bits2, bw, x);
     const uint32_t *Tv = brow(g.bits3, bw, v), *Tx = brow(g.bits3, bw, x);
-    const bool tvx = btest(g, g.bits3, v, x);
+    const bool tvx = !kExact && btest(g, g.bits3, v, x);
     const bool tri_ok = x > v;  // a triangle is kept at its smallest node
     // exact rows: the 3-hyperedges {v, x, y} are known per word
-    const uint32_t* Rvx = g.tri3 ? g.tri3 + ((size_t)v * g.n + x) * bw : nullptr;
+    const uint32_t* Rvx = kExact ? g.tri3 + ((size_t)v * g.n + x) * bw : nullptr;
     unsigned long long nw = 0, nt = 0;
-    for (int32_t w = xl >> 5; w < bw; ++w) {
-      uint32_t Y = __ldg(Bv + w) & above(w, xl);
-      if (Rvx) Y &= ~__ldg(Rvx + w);
-      if (!Y) continue;
-      const uint32_t bx = __ldg(Bx + w);
-      const uint32_t tri = tri_ok ? (Y & bx) : 0u, wed = Y & ~bx;
-      const uint32_t risky = (tvx && !Rvx) ? (__ldg(Tv + w) & __ldg(Tx + w)) : 0u;
-      nt += __popc(tri & ~risky);
-      nw += __popc(wed & ~risky);
-      uint32_t rb = (tri | wed) & risky;
-      while (rb) {
-        const int b = __ffs(rb) - 1;
-        rb &= rb - 1;
-        if (!has_triple(g, v, x, base + w * 32 + b)) {
-          if ((tri >> b) & 1u)
-            ++nt;
-          else
-            ++nw;
+    for (int32_t w4 = (xl >> 5) & ~3; w4 < bw; w4 += 4) {
+      uint32_t Y4[4], bx4[4], r4[4] = {0, 0, 0, 0}, tv4[4] = {0, 0, 0, 0}, tx4[4] = {0, 0, 0, 0};
+      ld4(Bv + w4, Y4);
+      if (!((Y4[0] & above(w4, xl)) | (Y4[1] & above(w4 + 1, xl)) | (Y4[2] & above(w4 + 2, xl)) |
+            (Y4[3] & above(w4 + 3, xl))))
+        continue;
+      ld4(Bx + w4, bx4);
+      if (kExact) ld4(Rvx + w4, r4);
+      if (!kExact && tvx) {
+        ld4(Tv + w4, tv4);
+        ld4(Tx + w4, tx4);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int32_t w = w4 + k;
+        const uint32_t Y = Y4[k] & above(w, xl) & ~r4[k];
+        if (!Y) continue;
+        const uint32_t bx = bx4[k];
+        const uint32_t tri = tri_ok ? (Y & bx) : 0u, wed = Y & ~bx;
+        const uint32_t risky = tv4[k] & tx4[k];
+        nt += __popc(tri & ~risky);
+        nw += __popc(wed & ~risky);
+        uint32_t rb = (tri | wed) & risky;
+        while (rb) {
+          const int b = __ffs(rb) - 1;
+          rb &= rb - 1;
+          if (!has_triple(g, v, x, base + w * 32 + b)) {
+            if ((tri >> b) & 1u)
+              ++nt;
+            else
+              ++nw;
+          }
         }
       }
     }
@@ -438,7 +465,8 @@ struct BitsW {
 };
 
 // k = 4, stars: anchor v, item x < y in N2(v), z over ids > y in N2(v)
-struct BitsS {
+template <bool kExact>
+struct BitsST {
   static constexpr const char* kName = "census_Sb";
   struct State {
     uint32_t i, j;
@@ -463,7 +491,7 @@ struct BitsS {
     // exact rows (when present) decide every 3-hyperedge of the candidates;
     // otherwise the co-occurrence bitmaps filter and the risky bits are probed
     const uint32_t* R = g.tri3;
-    const bool exact = R != nullptr;
+    constexpr bool exact = kExact;
     const bool tvx = !exact && btest(g, g.bits3, v, x), tvy = !exact && btest(g, g.bits3, v, y),
                txy = !exact && btest(g, g.bits3, x, y);
     if (exact) {
@@ -483,33 +511,70 @@ struct BitsS {
     const uint32_t *Tv = brow(g.bits3, bw, v), *Tx = brow(g.bits3, bw, x), *Ty = brow(g.bits3, bw, y);
     const uint32_t *Qv = brow(g.bits4, bw, v), *Qx = brow(g.bits4, bw, x), *Qy = brow(g.bits4, bw, y);
     unsigned long long c[4] = {0, 0, 0, 0};  // (xz, yz) = 00, 10, 01, 11
-    for (int32_t w = yl >> 5; w < bw; ++w) {
-      uint32_t Z = __ldg(Bv + w) & above(w, yl);
-      if (exact && Z) Z &= ~(__ldg(Rvx + w) | __ldg(Rvy + w) | __ldg(Rxy + w));
-      if (!Z) continue;
-      const uint32_t bx = __ldg(Bx + w), by = __ldg(By + w);
-      uint32_t grp[4];
-      grp[0] = Z & ~bx & ~by;
-      grp[1] = rx ? 0u : (Z & bx & ~by);
-      grp[2] = ry ? 0u : (Z & ~bx & by);
-      grp[3] = (rx || ry) ? 0u : (Z & bx & by & above(w, vl));
-      uint32_t risky = 0u;
-      if (tvx) risky |= __ldg(Tv + w) & __ldg(Tx + w);
-      if (tvy) risky |= __ldg(Tv + w) & __ldg(Ty + w);
-      if (txy) risky |= __ldg(Tx + w) & __ldg(Ty + w);
-      if (qd) risky |= __ldg(Qv + w) & __ldg(Qx + w) & __ldg(Qy + w);
+    for (int32_t w4 = (yl >> 5) & ~3; w4 < bw; w4 += 4) {
+      uint32_t Z4[4];
+      ld4(Bv + w4, Z4);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) c[k] += __popc(grp[k] & ~risky);
-      uint32_t rb = (grp[0] | grp[1] | grp[2] | grp[3]) & risky;
-      while (rb) {
-        const int b = __ffs(rb) - 1;
-        rb &= rb - 1;
-        const int32_t z = base + w * 32 + b;
-        if ((!exact && (has_triple(g, v, x, z) || has_triple(g, v, y, z) ||
-                        has_triple(g, x, y, z))) ||
-            has_quad(g, v, x, y, z))
-          continue;
-        ++c[((bx >> b) & 1u) | (((by >> b) & 1u) << 1)];
+      for (int k = 0; k < 4; ++k) Z4[k] &= above(w4 + k, yl);
+      if (!(Z4[0] | Z4[1] | Z4[2] | Z4[3])) continue;
+      if (exact) {
+        uint32_t a4[4], b4[4], c4[4];
+        ld4(Rvx + w4, a4);
+        ld4(Rvy + w4, b4);
+        ld4(Rxy + w4, c4);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) Z4[k] &= ~(a4[k] | b4[k] | c4[k]);
+      }
+      uint32_t bx4[4], by4[4];
+      ld4(Bx + w4, bx4);
+      ld4(By + w4, by4);
+      uint32_t rk4[4] = {0, 0, 0, 0};
+      if (!exact && (tvx || tvy || txy)) {
+        uint32_t tv4[4], tx4[4], ty4[4];
+        ld4(Tv + w4, tv4);
+        ld4(Tx + w4, tx4);
+        ld4(Ty + w4, ty4);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          rk4[k] = (tvx ? tv4[k] & tx4[k] : 0u) | (tvy ? tv4[k] & ty4[k] : 0u) |
+                   (txy ? tx4[k] & ty4[k] : 0u);
+      }
+      if (qd) {
+        uint32_t qv4[4], qx4[4], qy4[4];
+        ld4(Qv + w4, qv4);
+        ld4(Qx + w4, qx4);
+        ld4(Qy + w4, qy4);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) rk4[k] |= qv4[k] & qx4[k] & qy4[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int32_t w = w4 + k;
+        const uint32_t Z = Z4[k];
+        if (!Z) continue;
+        const uint32_t bx = bx4[k], by = by4[k], risky = rk4[k];
+        uint32_t grp[4];
+        grp[0] = Z & ~bx & ~by;
+        grp[1] = rx ? 0u : (Z & bx & ~by);
+        grp[2] = ry ? 0u : (Z & ~bx & by);
+        grp[3] = (rx || ry) ? 0u : (Z & bx & by & above(w, vl));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) c[q] += __popc(grp[q] & ~risky);
+        uint32_t rb = (grp[0] | grp[1] | grp[2] | grp[3]) & risky;
+        while (rb) {
+          const int b = __ffs(rb) - 1;
+          rb &= rb - 1;
+          const int32_t z = base + w * 32 + b;
+          if ((!exact && (has_triple(g, v, x, z) || has_triple(g, v, y, z) ||
+                          has_triple(g, x, y, z))) ||
+              has_quad(g, v, x, y, z))
+            continue;
+          const uint32_t gi = ((bx >> b) & 1u) | (((by >> b) & 1u) << 1);
+          c[0] += gi == 0u;
+          c[1] += gi == 1u;
+          c[2] += gi == 2u;
+          c[3] += gi == 3u;
+        }
       }
     }
     const uint32_t basem = 7u | (xy ? 8u : 0u);  // v=0, x=1, y=2, z=3
@@ -522,7 +587,8 @@ struct BitsS {
 
 // k = 4, paths and 4-cycles: anchor pair (u, v), u < v, item x in N2(u)\{v},
 // y over N2(v) \ N2[u]
-struct BitsP {
+template <bool kExact>
+struct BitsPT {
   static constexpr const char* kName = "census_Pb";
   struct State {
     int32_t u, v;
@@ -547,7 +613,7 @@ struct BitsP {
     const int32_t x = g.adj2[s.ou + s.i + (s.i >= s.pu ? 1 : 0)];
     if (btest(g, g.bits2, v, x)) return;  // v would have degree 3: family S
     const uint32_t* R = g.tri3;
-    const bool exact = R != nullptr;
+    constexpr bool exact = kExact;
     const bool tuv = !exact && btest(g, g.bits3, u, v), tux = !exact && btest(g, g.bits3, u, x),
                tvx = !exact && btest(g, g.bits3, v, x);
     if (exact) {
@@ -568,33 +634,68 @@ struct BitsP {
     const int32_t uw = ul >> 5;
     const uint32_t ubit = 1u << (ul & 31);
     unsigned long long np = 0, nc = 0;
-    for (int32_t w = 0; w < bw; ++w) {
-      uint32_t Y = __ldg(Bv + w) & ~__ldg(Bu + w);
-      if (w == uw) Y &= ~ubit;
-      if (exact && Y) Y &= ~(__ldg(Ruv + w) | __ldg(Rux + w) | __ldg(Rvx + w));
-      if (!Y) continue;
-      const uint32_t bx = __ldg(Bx + w);
-      const uint32_t c4 = c4ok ? (Y & bx & above(w, ul)) : 0u, p4 = Y & ~bx;
-      uint32_t risky = 0u;
-      if (tuv) risky |= __ldg(Tu + w) & __ldg(Tv + w);
-      if (tux) risky |= __ldg(Tu + w) & __ldg(Tx + w);
-      if (tvx) risky |= __ldg(Tv + w) & __ldg(Tx + w);
-      if (qd) risky |= __ldg(Qu + w) & __ldg(Qv + w) & __ldg(Qx + w);
-      np += __popc(p4 & ~risky);
-      nc += __popc(c4 & ~risky);
-      uint32_t rb = (c4 | p4) & risky;
-      while (rb) {
-        const int b = __ffs(rb) - 1;
-        rb &= rb - 1;
-        const int32_t y = base + w * 32 + b;
-        if ((!exact && (has_triple(g, u, v, y) || has_triple(g, u, x, y) ||
-                        has_triple(g, v, x, y))) ||
-            has_quad(g, u, v, x, y))
-          continue;
-        if ((c4 >> b) & 1u)
-          ++nc;
-        else
-          ++np;
+    for (int32_t w4 = 0; w4 < bw; w4 += 4) {
+      uint32_t Y4[4], u4[4];
+      ld4(Bv + w4, Y4);
+      ld4(Bu + w4, u4);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        Y4[k] &= ~u4[k];
+        if (w4 + k == uw) Y4[k] &= ~ubit;
+      }
+      if (!(Y4[0] | Y4[1] | Y4[2] | Y4[3])) continue;
+      if (exact) {
+        uint32_t a4[4], b4[4], e4[4];
+        ld4(Ruv + w4, a4);
+        ld4(Rux + w4, b4);
+        ld4(Rvx + w4, e4);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) Y4[k] &= ~(a4[k] | b4[k] | e4[k]);
+      }
+      uint32_t bx4[4];
+      ld4(Bx + w4, bx4);
+      uint32_t rk4[4] = {0, 0, 0, 0};
+      if (!exact && (tuv || tux || tvx)) {
+        uint32_t tu4[4], tv4[4], tx4[4];
+        ld4(Tu + w4, tu4);
+        ld4(Tv + w4, tv4);
+        ld4(Tx + w4, tx4);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          rk4[k] = (tuv ? tu4[k] & tv4[k] : 0u) | (tux ? tu4[k] & tx4[k] : 0u) |
+                   (tvx ? tv4[k] & tx4[k] : 0u);
+      }
+      if (qd) {
+        uint32_t qu4[4], qv4[4], qx4[4];
+        ld4(Qu + w4, qu4);
+        ld4(Qv + w4, qv4);
+        ld4(Qx + w4, qx4);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) rk4[k] |= qu4[k] & qv4[k] & qx4[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int32_t w = w4 + k;
+        const uint32_t Y = Y4[k];
+        if (!Y) continue;
+        const uint32_t bx = bx4[k], risky = rk4[k];
+        const uint32_t c4 = c4ok ? (Y & bx & above(w, ul)) : 0u, p4 = Y & ~bx;
+        np += __popc(p4 & ~risky);
+        nc += __popc(c4 & ~risky);
+        uint32_t rb = (c4 | p4) & risky;
+        while (rb) {
+          const int b = __ffs(rb) - 1;
+          rb &= rb - 1;
+          const int32_t y = base + w * 32 + b;
+          if ((!exact && (has_triple(g, u, v, y) || has_triple(g, u, x, y) ||
+                          has_triple(g, v, x, y))) ||
+              has_quad(g, u, v, x, y))
+            continue;
+          if ((c4 >> b) & 1u)
+            ++nc;
+          else
+            ++np;
+        }
       }
     }
     if (np) atomicAdd(&bins[lut[19]], (Bin)np);  // u=0, v=1, x=2, y=3: pairs 01, 02, 13

@@ -300,6 +300,29 @@ bool trace_on();
 void trace_begin(cudaStream_t s, cudaEvent_t* a);
 void trace_end(const char* name, cudaStream_t s, cudaEvent_t a);
 
+// A named span of stream work (several launches) for the trace; end() records
+// it, an abandoned span (an error was thrown) only releases its event.
+struct TraceSpan {
+  const char* name;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  TraceSpan(const char* n, cudaStream_t st) : name(n), s(st) {
+    if (trace_on()) trace_begin(s, &a);
+  }
+  void end() {
+    if (a) {
+      cudaEvent_t e = a;
+      a = nullptr;
+      trace_end(name, s, e);
+    }
+  }
+  ~TraceSpan() {
+    if (a) cudaEventDestroy(a);
+  }
+  TraceSpan(const TraceSpan&) = delete;
+  TraceSpan& operator=(const TraceSpan&) = delete;
+};
+
 // ------------------------------------------------------------------ classes (classes.cu)
 struct ClassTables {
   int k;

@@ -1,6 +1,6 @@
-// Kernel timing trace: when enabled, each census kernel launch is bracketed
-// by CUDA events recorded on the stream it is launched on, so a caller can
-// attribute device time to kernels without a profiler.
+// Kernel timing trace: when enabled, each census kernel launch and each ingest
+// phase is bracketed by CUDA events recorded on the stream it is launched on,
+// so a caller can attribute device time to kernels without a profiler.
 #include <atomic>
 #include <cstring>
 #include <mutex>
