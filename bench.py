@@ -33,8 +33,8 @@ WORKLOAD = "f2f-330"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 # Roofline of the census kernels. Their tables are L2/L1-resident on this
-# workload (ncu: DRAM traffic ~0), so they are bound by the integer/logic
-# (ALU) pipe: peak = SMs x 64 int32 lanes per clock x SM clock. Achieved =
+# workload (ncu: a few MB of DRAM traffic per launch), so they are bound by
+# the integer/logic (ALU) pipe: peak = SMs x 64 int32 lanes per clock x SM clock. Achieved =
 # work units of one launch x ALU lane-operations per unit (measured with ncu
 # on this workload, `profiles/`) / event-timed launch duration.
 SMS = 152
@@ -42,10 +42,10 @@ ALU_LANES_PER_SM_CLK = 64
 # kernel -> (unit, ALU lane-ops per unit, DRAM bytes per launch); None = not measured
 # (ops = sm__sass_thread_inst_executed_op_{integer,bit}_pred_on per unit, profiles/census_bits_f2f-330.md)
 ROOFLINE = {
-    "census_Sb": ("item", None, None),
-    "census_Pb": ("item", None, None),
-    "census_TX": ("candidate", None, None),
-    "census_Q": ("candidate", None, None),
+    "census_Sb": ("item", 612.8, 4_378_000),
+    "census_Pb": ("item", 480.6, 5_733_000),
+    "census_TX": ("candidate", 332.9, 659_000),
+    "census_Q": ("candidate", 522.3, 301_000),
     "census_Wb": ("item", None, None),
     "census_S": ("candidate", None, None),
     "census_P": ("candidate", None, None),
@@ -121,24 +121,47 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class _Chunks:
+    """Sizes a sample taken in chunks of units that may grow heavier (ESU roots
+    towards the most active nodes): each chunk at most doubles, and is cut to
+    what the budget left allows at the last cost per unit times its last
+    growth; 0 means stop."""
+
+    def __init__(self, first, smallest, budget_s):
+        self.next, self.smallest, self.budget = first, smallest, budget_s
+        self.used, self.prev = 0.0, None
+
+    def done(self, units, seconds):
+        self.used += seconds
+        per = seconds / max(units, 1)
+        growth = max(1.0, per / self.prev) if self.prev else 2.0
+        self.prev = max(per, 1e-9)
+        fit = int((self.budget - self.used) / (self.prev * growth))
+        self.next = min(2 * units, fit) if fit >= self.smallest else 0
+        return self.next
+
+
 def cpu_baseline(h, order: int, budget_s: float = 15.0):
     """The oracle (plain ESU + fill-in) on a bounded sample of ESU roots."""
     import oracle
     threads = os.cpu_count() or 1
     g = oracle.Graph.from_hypergraph(h, 4)
-    roots, t_used, sets = 0, 0.0, 0
-    step = max(threads, 8)
-    while t_used < budget_s and roots < h.num_nodes:
-        hi = min(h.num_nodes, roots + step)
+    # ESU root v enumerates the sets whose smallest id is v; the generator's
+    # low ids are its most active nodes, so the light roots are the top ids and
+    # the sample grows downwards from the largest id, in budget-sized chunks
+    lo, sets = h.num_nodes, 0
+    ch = _Chunks(max(threads, 8), threads, budget_s)
+    while ch.next and lo > 0:
+        new_lo = max(0, lo - ch.next)
         t0 = time.perf_counter()
-        hist, _ = g.census(order, threads=threads, roots=(roots, hi))
-        t_used += time.perf_counter() - t0
+        hist, _ = g.census(order, threads=threads, roots=(new_lo, lo))
+        ch.done(lo - new_lo, time.perf_counter() - t0)
         sets += int(hist.sum())
-        roots = hi
-        step *= 2
+        lo = new_lo
+    t_used = ch.used
     return {"value": sets / t_used, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{WORKLOAD} order-{order}: ESU roots [0, {roots}) of {h.num_nodes} "
-                      f"({sets} connected sets in {t_used:.1f} s)"}
+            "sample": f"{WORKLOAD} order-{order}: ESU roots [{lo}, {h.num_nodes}) of "
+                      f"{h.num_nodes} ({sets} connected sets in {t_used:.1f} s)"}
 
 
 def _event_ms(fn, stream):
@@ -223,6 +246,35 @@ def measure_null(hm, stream, hyperedges=NULL_BASES, models=8):
             "sets_per_s": sets / (ms / 1e3)}
 
 
+def measure_large(hm, stream, names=("coauth-1m", "comm-5m")):
+    """Exact order-4 census of the full-size co-authorship- and communication-
+    shaped workloads: device ingest + census, event-timed once each (the
+    census of one of them runs for seconds, so there is no L2 effect to
+    flush). Not part of the default run: generating comm-5m takes ~1.5 min."""
+    import torch
+    from paper_2209_10241_gb300 import synth
+    out = {}
+    for name in names:
+        t0 = time.perf_counter()
+        h = synth.workload(name)
+        gen_s = time.perf_counter() - t0
+        mem = torch.from_numpy(h.members).cuda()
+        off = torch.from_numpy(h.offsets).cuda()
+        torch.cuda.synchronize()
+        build_ms, g = _event_ms(lambda: hm.build(mem, off, h.num_nodes, 4), stream)
+        census_ms, hist = _event_ms(lambda: hm.count_exact(g, 4), stream)
+        totals = hm.work_totals(g, 4)
+        sets = int(hist.sum().item())
+        out[name] = {"nodes": h.num_nodes, "hyperedges": h.num_hyperedges,
+                     "graph_counts": [int(x) for x in g.counts],
+                     "generate_s": gen_s, "build_ms": build_ms, "census_ms": census_ms,
+                     "sets": sets, "sets_per_s": sets / ((build_ms + census_ms) / 1e3),
+                     "census_sets_per_s": sets / (census_ms / 1e3), "work": totals}
+        g.free()
+        del mem, off
+    return out
+
+
 def cpu_baseline_rows(budget_s: float = 8.0):
     """The oracle beside the sampler and null-batch rows, each on a bounded sample."""
     import oracle
@@ -232,15 +284,17 @@ def cpu_baseline_rows(budget_s: float = 8.0):
     # Alg. 4 as the oracle runs it, sample by sample (single-threaded)
     h = synth.workload("comm-5m", seed=9, scale=0.004)
     g = oracle.Graph.from_hypergraph(h, 4)
-    draws, t_used, S = 0, 0.0, 60
-    while t_used < budget_s and S < 1_000_000:
+    draws = 0
+    ch = _Chunks(60, 60, budget_s)
+    while ch.next and draws < 1_000_000:
+        S = ch.next
         split = {2: S // 6, 4: S // 3}
         split[3] = S - split[2] - split[4]
         t0 = time.perf_counter()
-        g.sample(4, split, seed=100)
-        t_used += time.perf_counter() - t0
+        g.sample(4, split, seed=100 + draws)
+        ch.done(S, time.perf_counter() - t0)
         draws += S
-        S *= 2
+    t_used = ch.used
     out["sampler"] = {"value": draws / t_used, "unit": "draws/s", "cores": 1, "kind": "oracle",
                       "sample": f"Alg. 4 on the comm-5m generator at scale 0.004 "
                                 f"({draws} draws in {t_used:.1f} s)"}
@@ -250,15 +304,16 @@ def cpu_baseline_rows(budget_s: float = 8.0):
     gm = oracle.Graph(mem, b.offsets, b.num_nodes, 4)
     # ESU root v enumerates the sets whose smallest id is v: the top ids are the
     # light roots, so the sample grows downwards from the largest id
-    lo, t_used, sets, step = b.num_nodes, 0.0, 0, max(threads, 8)
-    while t_used < budget_s and lo > 0:
-        new_lo = max(0, lo - step)
+    lo, sets = b.num_nodes, 0
+    ch = _Chunks(max(threads, 8), threads, budget_s)
+    while ch.next and lo > 0:
+        new_lo = max(0, lo - ch.next)
         t0 = time.perf_counter()
         hist, _ = gm.census(4, threads=threads, roots=(new_lo, lo))
-        t_used += time.perf_counter() - t0
+        ch.done(lo - new_lo, time.perf_counter() - t0)
         sets += int(hist.sum())
         lo = new_lo
-        step *= 2
+    t_used = ch.used
     out["null_batch"] = {"value": sets / t_used, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"stub shuffle 0 of the {NULL_BASES[0]}-hyperedge base: ESU "
                                    f"roots [{lo}, {b.num_nodes}) of {b.num_nodes} ({sets} sets "
@@ -301,7 +356,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sampler and null-batch measurements")
-    ap.add_argument("--only", choices=["sampler", "null"], default=None,
+    ap.add_argument("--only", choices=["sampler", "null", "large"], default=None,
                     help="run one of the extra measurements alone (for profiling)")
     ap.add_argument("--null-bases", type=int, default=8,
                     help="number of null-model bases (log-spaced 50k-500k hyperedges)")
@@ -323,8 +378,12 @@ def main():
     if args.only:
         hm.load()
         stream = torch.cuda.current_stream()
-        res = (measure_sampler(hm, stream) if args.only == "sampler"
-               else measure_null(hm, stream, hyperedges=NULL_BASES[:args.null_bases]))
+        if args.only == "sampler":
+            res = measure_sampler(hm, stream)
+        elif args.only == "null":
+            res = measure_null(hm, stream, hyperedges=NULL_BASES[:args.null_bases])
+        else:
+            res = measure_large(hm, stream)
         print(json.dumps({"only": args.only, **res}), flush=True)
         return
     if world > 1:

@@ -232,7 +232,10 @@ hm_status hm_features(hm_graph* g, int order, float* d_feat, void* stream);
  *   hm_mlp_forward  y[i] = f(x[i]) for n rows of 16 floats.
  *   hm_mlp_backward d_grad (overwritten) = gradient of mean_i (y_i - t_i)^2;
  *                   *d_loss_sum (may be NULL) = sum_i (y_i - t_i)^2;
- *                   d_scratch: device buffer of n * 416 bytes.
+ *                   d_scratch: device buffer of hm_mlp_scratch_bytes(n)
+ *                   bytes, 16-byte aligned. Every sum is taken in a fixed
+ *                   order, so the gradient is the same bit for bit on
+ *                   every call with the same inputs.
  *   hm_mlp_adam     one Adam step (beta 0.9 / 0.999, eps 1e-8, bias
  *                   correction for `step` >= 1) on params, moments m and v.
  *   hm_mlp_train    `epochs` passes of minibatch Adam (batch rows, learning
@@ -241,6 +244,7 @@ hm_status hm_features(hm_graph* g, int order, float* d_feat, void* stream);
  *                   loss. Synchronous.
  */
 int hm_mlp_num_params(void);
+size_t hm_mlp_scratch_bytes(int64_t n);
 hm_status hm_mlp_forward(const float* d_params, const float* d_x, int64_t n, float* d_y,
                          void* stream);
 hm_status hm_mlp_backward(const float* d_params, const float* d_x, const float* d_target,

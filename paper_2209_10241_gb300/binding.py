@@ -47,6 +47,7 @@ _SIGS = {
     "hm_contributions": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "hm_features": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "hm_mlp_num_params": (ctypes.c_int, []),
+    "hm_mlp_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
     "hm_mlp_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, _vp]),
     "hm_mlp_backward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp, _vp]),
     "hm_mlp_adam": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_float, _vp]),
@@ -300,7 +301,8 @@ def mlp_backward(params: torch.Tensor, x: torch.Tensor, target: torch.Tensor, st
     n = x.shape[0]
     grad = torch.empty(mlp_num_params(), dtype=torch.float32, device="cuda")
     loss = torch.empty(1, dtype=torch.float32, device="cuda")
-    scratch = torch.empty(max(1, n * (16 + 3 * 64) * 2), dtype=torch.uint8, device="cuda")
+    scratch = torch.empty(max(1, load().hm_mlp_scratch_bytes(n)), dtype=torch.uint8,
+                          device="cuda")
     _check(load().hm_mlp_backward(_dptr(params), _dptr(x), _dptr(target), n, _dptr(grad),
                                   _dptr(loss), _dptr(scratch), _stream(stream)))
     return grad, loss

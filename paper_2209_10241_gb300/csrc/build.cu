@@ -104,30 +104,6 @@ __global__ void k_normalize(const int32_t* __restrict__ mem, const int64_t* __re
   }
 }
 
-__global__ void k_unpack2(const uint64_t* __restrict__ c, int64_t m, int b, uint64_t* __restrict__ e2) {
-  const uint64_t mask = (1ull << b) - 1;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t k = c[i];
-    e2[i] = ((k >> b) << 32) | (k & mask);
-  }
-}
-
-__global__ void k_unpack34(const uint64_t* __restrict__ hi, const uint64_t* __restrict__ lo,
-                           int64_t m, int s, int b, int4* __restrict__ e) {
-  const uint64_t mask = (1ull << b) - 1;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    unsigned __int128 key = ((unsigned __int128)hi[i] << 64) | lo[i];
-    int32_t v[4] = {-1, -1, -1, -1};
-    for (int j = s - 1; j >= 0; --j) {
-      v[j] = (int32_t)((uint64_t)key & mask);
-      key >>= b;
-    }
-    e[i] = make_int4(v[0], v[1], v[2], v[3]);
-  }
-}
-
 __global__ void k_insert2(const uint64_t* __restrict__ e2, int64_t m, uint64_t* table,
                           uint64_t mask, int* err) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
@@ -240,6 +216,54 @@ __global__ void k_bitmap(const uint64_t* __restrict__ e2, int64_t m, int32_t bw,
   }
 }
 
+// Pair degrees from the bitmap rows: one warp per node.
+__global__ void k_bits_degree(const uint32_t* __restrict__ bits, int32_t n, int32_t bw,
+                              uint64_t* __restrict__ deg) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const uint32_t* row = bits + (size_t)v * bw;
+    uint32_t c = 0;
+    for (int w = lane; w < bw; w += 32) c += __popc(__ldg(row + w));
+#pragma unroll
+    for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+    if (lane == 0) deg[v] = c;
+  }
+}
+
+// Sorted pair neighbours from the bitmap rows (the set bits of row v in
+// ascending column order, offset by the first id of v's graph): one warp per
+// node, 32 words per round, each lane writing its word's ids at its prefix.
+__global__ void k_bits_adjacency(const uint32_t* __restrict__ bits, int32_t n, int32_t bw,
+                                 int32_t block, uint64_t inv, const int64_t* __restrict__ off,
+                                 int32_t* __restrict__ adj) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const uint32_t* row = bits + (size_t)v * bw;
+    const int32_t base = block ? (int32_t)__umul64hi((uint64_t)v, inv) * block : 0;
+    int64_t pos = off[v];
+    for (int w0 = 0; w0 < bw; w0 += 32) {
+      const int w = w0 + lane;
+      uint32_t word = w < bw ? __ldg(row + w) : 0u;
+      const uint32_t c = __popc(word);
+      uint32_t incl = c;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+      }
+      int64_t p = pos + (incl - c);
+      while (word) {
+        const int j = __ffs(word) - 1;
+        word &= word - 1;
+        adj[p++] = base + w * 32 + j;
+      }
+      pos += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+}
+
 // bits of every pair of members of each s-tuple (s = 3 or 4)
 __global__ void k_bitmap_tuples(const int4* __restrict__ e, int64_t m, int s, int32_t bw,
                                 int32_t block, uint64_t inv, uint32_t* __restrict__ bits) {
@@ -324,6 +348,9 @@ bool use_tri3(int64_t n, int32_t block) {
   return bytes <= (64ll << 20);
 }
 
+// bytes of the kept counts written for sizes 2..kmax
+size_t nj_kept_bytes(int kmax) { return (size_t)(kmax - 1) * sizeof(uint32_t); }
+
 template <class T>
 T* keep(hm_graph* g, T* p) {
   if (p) g->owned.push_back((void*)p);
@@ -375,159 +402,179 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
                                                  err.p, c2.p, c3hi.p, c3lo.p, c4hi.p, c4lo.p);
     HM_KCHECK();
   }
-  // sort + unique per size: the ascending order of E_s (one synchronisation)
+  // sort + unique per size, all sizes in one batch: the ascending order of
+  // E_s, written straight into the graph's arrays (sized for the keys before
+  // dedup) in their final layout (one synchronisation)
+  g->e2 = keep(g, dalloc<uint64_t>(hc[2], s));
+  if (kmax >= 3 && hc[3]) g->e3 = keep(g, dalloc<int4>(hc[3], s));
+  if (kmax >= 4 && hc[4]) g->e4 = keep(g, dalloc<int4>(hc[4], s));
   DBuf<uint32_t> kept(3, s);
-  HM_CUDA(cudaMemsetAsync(kept.p, 0, 3 * sizeof(uint32_t), s));
-  radix_sort_u64(c2.p, nullptr, (int64_t)hc[2], 2 * b, s);
-  unique_sorted_async(nullptr, c2.p, (int64_t)hc[2], kept.p, s);
-  if (kmax >= 3) {
-    int bits3 = 3 * b;
-    radix_sort_u128(c3hi.p, c3lo.p, (int64_t)hc[3], bits3 > 64 ? bits3 - 64 : 0,
-                    bits3 > 64 ? 64 : bits3, s);
-    unique_sorted_async(c3hi.p, c3lo.p, (int64_t)hc[3], kept.p + 1, s);
-  }
-  if (kmax >= 4) {
-    int bits4 = 4 * b;
-    radix_sort_u128(c4hi.p, c4lo.p, (int64_t)hc[4], bits4 > 64 ? bits4 - 64 : 0,
-                    bits4 > 64 ? 64 : bits4, s);
-    unique_sorted_async(c4hi.p, c4lo.p, (int64_t)hc[4], kept.p + 2, s);
+  {
+    SortJob jobs[3];
+    int nj = 0;
+    auto add = [&](uint64_t* lo, uint64_t* hi, int64_t cnt, int size, int unpack, void* out) {
+      SortJob& J = jobs[nj];
+      J.a = lo;
+      J.b = hi;
+      J.b_is_key = hi != nullptr;
+      J.n = cnt;
+      const int bits = size * b, lo_bits = bits > 64 ? 64 : bits, hi_bits = bits - lo_bits;
+      for (int sh = 0; sh < lo_bits; sh += 8) {
+        J.arr[J.passes] = 0;
+        J.shift[J.passes++] = (int8_t)sh;
+      }
+      for (int sh = 0; sh < hi_bits; sh += 8) {
+        J.arr[J.passes] = 1;
+        J.shift[J.passes++] = (int8_t)sh;
+      }
+      J.unique = 1;
+      J.unpack = unpack;
+      J.member_bits = b;
+      J.out = out;
+      J.d_kept = kept.p + (size - 2);
+      ++nj;
+    };
+    add(c2.p, nullptr, (int64_t)hc[2], 2, SortJob::PAIR, g->e2);
+    if (kmax >= 3) add(c3lo.p, c3hi.p, (int64_t)hc[3], 3, SortJob::TRIPLE, g->e3);
+    if (kmax >= 4) add(c4lo.p, c4hi.p, (int64_t)hc[4], 4, SortJob::QUAD, g->e4);
+    sort_batch(jobs, nj, s);
   }
   span_sort.end();
   uint32_t hk[3] = {0, 0, 0};
-  HM_CUDA(cudaMemcpyAsync(hk, kept.p, sizeof hk, cudaMemcpyDeviceToHost, s));
+  HM_CUDA(cudaMemcpyAsync(hk, kept.p, nj_kept_bytes(kmax), cudaMemcpyDeviceToHost, s));
   HM_CUDA(cudaStreamSynchronize(s));
   const int64_t m2 = hk[0], m3 = kmax >= 3 ? hk[1] : 0, m4 = kmax >= 4 ? hk[2] : 0;
   g->counts[2] = m2;
   if (kmax >= 3) g->counts[3] = m3;
   if (kmax >= 4) g->counts[4] = m4;
-
-  TraceSpan span_tables("ingest_tables", s);
-  g->e2 = keep(g, dalloc<uint64_t>(m2, s));
-  if (m2) {
-    k_unpack2<<<grid1d(m2), T256, 0, s>>>(c2.p, m2, b, g->e2);
-    HM_KCHECK();
-  }
-  if (m3) {
-    g->e3 = keep(g, dalloc<int4>(m3, s));
-    k_unpack34<<<grid1d(m3), T256, 0, s>>>(c3hi.p, c3lo.p, m3, 3, b, g->e3);
-    HM_KCHECK();
-  }
-  if (m4) {
-    g->e4 = keep(g, dalloc<int4>(m4, s));
-    k_unpack34<<<grid1d(m4), T256, 0, s>>>(c4hi.p, c4lo.p, m4, 4, b, g->e4);
-    HM_KCHECK();
-  }
-  HM_CUDA(cudaGetLastError());
   c2.release();
   c3hi.release();
   c3lo.release();
   c4hi.release();
   c4lo.release();
 
-  // hash sets (load <= 0.5)
+  TraceSpan span_tables("ingest_structures", s);
+  // Outputs and temporaries on `s`; then four independent chains run
+  // concurrently: hash sets (s), pair CSR + pair positions (f[0]), triple
+  // incidence CSR (f[1]), dense bitmaps and triple rows (f[2]).
+  const uint64_t cap2 = table_capacity(m2), cap3 = m3 ? table_capacity(m3) : 0,
+                 cap4 = m4 ? table_capacity(m4) : 0;
+  g->h2 = keep(g, dalloc<uint64_t>(cap2, s));
+  g->h2_mask = cap2 - 1;
+  HM_CUDA(cudaMemsetAsync(g->h2, 0xFF, cap2 * sizeof(uint64_t), s));
+  if (m3) {
+    g->h3 = keep(g, dalloc<int4>(cap3, s));
+    g->h3_mask = cap3 - 1;
+    HM_CUDA(cudaMemsetAsync(g->h3, 0xFF, cap3 * sizeof(int4), s));
+  }
+  if (m4) {
+    g->h4 = keep(g, dalloc<int4>(cap4, s));
+    g->h4_mask = cap4 - 1;
+    HM_CUDA(cudaMemsetAsync(g->h4, 0xFF, cap4 * sizeof(int4), s));
+  }
+  g->off2 = keep(g, dalloc<int64_t>((size_t)n + 1, s));
+  g->adj2 = keep(g, dalloc<int32_t>(2 * m2, s));
+  if (m2) g->pairpos = keep(g, dalloc<int2>(m2, s));
+  g->off3 = keep(g, dalloc<int64_t>((size_t)n + 1, s));
+  if (m3) g->inc3 = keep(g, dalloc<int32_t>(3 * m3, s));
+  else HM_CUDA(cudaMemsetAsync(g->off3, 0, ((size_t)n + 1) * sizeof(int64_t), s));
+  const bool bitmaps = use_bitmap(n, block ? block : n, block != 0);
+  size_t words = 0, tw = 0;
+  if (bitmaps) {
+    // rows padded to a multiple of four words: 16-byte aligned row loads
+    g->bwords = (((block ? block : n) + 127) / 128) * 4;
+    words = (size_t)n * g->bwords;
+    g->bits2 = keep(g, dalloc<uint32_t>(words, s));
+    g->bits3 = keep(g, dalloc<uint32_t>(words, s));
+    g->bits4 = keep(g, dalloc<uint32_t>(words, s));
+    HM_CUDA(cudaMemsetAsync(g->bits2, 0, words * sizeof(uint32_t), s));
+    HM_CUDA(cudaMemsetAsync(g->bits3, 0, words * sizeof(uint32_t), s));
+    HM_CUDA(cudaMemsetAsync(g->bits4, 0, words * sizeof(uint32_t), s));
+    if (use_tri3(n, block)) {
+      tw = (size_t)n * n * g->bwords;
+      g->tri3 = keep(g, dalloc<uint32_t>(tw, s));
+      HM_CUDA(cudaMemsetAsync(g->tri3, 0, tw * sizeof(uint32_t), s));
+    }
+  }
+  DBuf<uint64_t> pkeys(bitmaps ? 0 : 2 * m2, s), tkeys(3 * m3, s), pdeg(bitmaps ? n : 0, s);
+  const int tb = bits_for(m3);
   {
-    uint64_t cap = table_capacity(m2);
-    g->h2 = keep(g, dalloc<uint64_t>(cap, s));
-    g->h2_mask = cap - 1;
-    HM_CUDA(cudaMemsetAsync(g->h2, 0xFF, cap * sizeof(uint64_t), s));
+    Fork f(s);
+    // hash sets (load <= 0.5)
     if (m2) {
       k_insert2<<<grid1d(m2), T256, 0, s>>>(g->e2, m2, g->h2, g->h2_mask, err.p);
       HM_KCHECK();
     }
-  }
-  if (m3) {
-    uint64_t cap = table_capacity(m3);
-    g->h3 = keep(g, dalloc<int4>(cap, s));
-    g->h3_mask = cap - 1;
-    HM_CUDA(cudaMemsetAsync(g->h3, 0xFF, cap * sizeof(int4), s));
-    k_insert4<<<grid1d(m3), T256, 0, s>>>(g->e3, m3, g->h3, g->h3_mask, err.p);
-    HM_KCHECK();
-  }
-  if (m4) {
-    uint64_t cap = table_capacity(m4);
-    g->h4 = keep(g, dalloc<int4>(cap, s));
-    g->h4_mask = cap - 1;
-    HM_CUDA(cudaMemsetAsync(g->h4, 0xFF, cap * sizeof(int4), s));
-    k_insert4<<<grid1d(m4), T256, 0, s>>>(g->e4, m4, g->h4, g->h4_mask, err.p);
-    HM_KCHECK();
-  }
-  HM_CUDA(cudaGetLastError());
-
-  span_tables.end();
-  // CSR of pair neighbours, sorted
-  TraceSpan span_csr("ingest_csr", s);
-  g->off2 = keep(g, dalloc<int64_t>((size_t)n + 1, s));
-  g->adj2 = keep(g, dalloc<int32_t>(2 * m2, s));
-  {
-    DBuf<uint64_t> keys(2 * m2, s);
-    if (m2) {
-      k_directed_pairs<<<grid1d(m2), T256, 0, s>>>(g->e2, m2, b, keys.p);
-      HM_KCHECK();
-      radix_sort_u64(keys.p, nullptr, 2 * m2, 2 * b, s);
-      k_low_bits<<<grid1d(2 * m2), T256, 0, s>>>(keys.p, 2 * m2, b, g->adj2);
-      HM_KCHECK();
-    }
-    csr_offsets(keys.p, 2 * m2, b, n, g->off2, s);
-  }
-  // CSR of triple incidence, ascending triple index
-  g->off3 = keep(g, dalloc<int64_t>((size_t)n + 1, s));
-  if (m3) {
-    g->inc3 = keep(g, dalloc<int32_t>(3 * m3, s));
-    const int tb = bits_for(m3);
-    DBuf<uint64_t> keys(3 * m3, s);
-    k_triple_incidence<<<grid1d(m3), T256, 0, s>>>(g->e3, m3, tb, keys.p);
-    HM_KCHECK();
-    radix_sort_u64(keys.p, nullptr, 3 * m3, b + tb, s);
-    k_low_bits<<<grid1d(3 * m3), T256, 0, s>>>(keys.p, 3 * m3, tb, g->inc3);
-    HM_KCHECK();
-    csr_offsets(keys.p, 3 * m3, tb, n, g->off3, s);
-  } else {
-    HM_CUDA(cudaMemsetAsync(g->off3, 0, ((size_t)n + 1) * sizeof(int64_t), s));
-  }
-  if (m2) {
-    g->pairpos = keep(g, dalloc<int2>(m2, s));
-    k_pairpos<<<grid1d(m2), T256, 0, s>>>(g->e2, m2, g->off2, g->adj2, g->pairpos);
-    HM_KCHECK();
-  }
-  span_csr.end();
-  TraceSpan span_bits("ingest_bitmaps", s);
-  if (use_bitmap(n, block ? block : n, block != 0)) {
-    // rows padded to a multiple of four words: 16-byte aligned row loads
-    g->bwords = (((block ? block : n) + 127) / 128) * 4;
-    const hm::DevGraph gv = g->view();
-    size_t words = (size_t)n * g->bwords;
-    g->bits2 = keep(g, dalloc<uint32_t>(words, s));
-    HM_CUDA(cudaMemsetAsync(g->bits2, 0, words * sizeof(uint32_t), s));
-    if (m2) {
-      k_bitmap<<<grid1d(m2), T256, 0, s>>>(g->e2, m2, g->bwords, gv.block, gv.block_inv,
-                                           g->bits2);
-      HM_KCHECK();
-    }
-    g->bits3 = keep(g, dalloc<uint32_t>(words, s));
-    HM_CUDA(cudaMemsetAsync(g->bits3, 0, words * sizeof(uint32_t), s));
     if (m3) {
-      k_bitmap_tuples<<<grid1d(m3), T256, 0, s>>>(g->e3, m3, 3, g->bwords, gv.block,
-                                                  gv.block_inv, g->bits3);
+      k_insert4<<<grid1d(m3), T256, 0, s>>>(g->e3, m3, g->h3, g->h3_mask, err.p);
       HM_KCHECK();
     }
-    g->bits4 = keep(g, dalloc<uint32_t>(words, s));
-    HM_CUDA(cudaMemsetAsync(g->bits4, 0, words * sizeof(uint32_t), s));
     if (m4) {
-      k_bitmap_tuples<<<grid1d(m4), T256, 0, s>>>(g->e4, m4, 4, g->bwords, gv.block,
-                                                  gv.block_inv, g->bits4);
+      k_insert4<<<grid1d(m4), T256, 0, s>>>(g->e4, m4, g->h4, g->h4_mask, err.p);
       HM_KCHECK();
     }
-    if (use_tri3(n, block)) {
-      const size_t tw = (size_t)n * n * g->bwords;
-      g->tri3 = keep(g, dalloc<uint32_t>(tw, s));
-      HM_CUDA(cudaMemsetAsync(g->tri3, 0, tw * sizeof(uint32_t), s));
+    // CSR of pair neighbours, sorted, and the position of each pair in it:
+    // read off the pair bitmap where there is one, else a stable sort
+    if (bitmaps) {
+      const hm::DevGraph gv = g->view();
+      if (m2) {
+        k_bitmap<<<grid1d(m2), T256, 0, f[0]>>>(g->e2, m2, g->bwords, gv.block, gv.block_inv,
+                                                g->bits2);
+        HM_KCHECK();
+      }
+      k_bits_degree<<<grid1d((int64_t)n * 32), T256, 0, f[0]>>>(g->bits2, n, g->bwords,
+                                                                 pdeg.p);
+      HM_KCHECK();
+      scan_exclusive_u64(pdeg.p, reinterpret_cast<uint64_t*>(g->off2), n, f[0]);
+      k_bits_adjacency<<<grid1d((int64_t)n * 32), T256, 0, f[0]>>>(
+          g->bits2, n, g->bwords, gv.block, gv.block_inv, g->off2, g->adj2);
+      HM_KCHECK();
+    } else if (m2) {
+      k_directed_pairs<<<grid1d(m2), T256, 0, f[0]>>>(g->e2, m2, b, pkeys.p);
+      HM_KCHECK();
+      // Stable by the first node only: for node x the keys (x, u) of pairs
+      // {u < x} precede the keys (x, v) of pairs {x < v} in E_2 order, and
+      // each group is ascending, so every row comes out sorted.
+      radix_sort_u64(pkeys.p, nullptr, 2 * m2, b, f[0], b);
+      k_low_bits<<<grid1d(2 * m2), T256, 0, f[0]>>>(pkeys.p, 2 * m2, b, g->adj2);
+      HM_KCHECK();
+    }
+    if (!bitmaps) csr_offsets(pkeys.p, 2 * m2, b, n, g->off2, f[0]);
+    if (m2) {
+      k_pairpos<<<grid1d(m2), T256, 0, f[0]>>>(g->e2, m2, g->off2, g->adj2, g->pairpos);
+      HM_KCHECK();
+    }
+    // CSR of triple incidence, ascending triple index
+    if (m3) {
+      k_triple_incidence<<<grid1d(m3), T256, 0, f[1]>>>(g->e3, m3, tb, tkeys.p);
+      HM_KCHECK();
+      // stable by node only: keys are generated in ascending triple index
+      radix_sort_u64(tkeys.p, nullptr, 3 * m3, b, f[1], tb);
+      k_low_bits<<<grid1d(3 * m3), T256, 0, f[1]>>>(tkeys.p, 3 * m3, tb, g->inc3);
+      HM_KCHECK();
+      csr_offsets(tkeys.p, 3 * m3, tb, n, g->off3, f[1]);
+    }
+    // dense bitmaps
+    if (bitmaps) {
+      const hm::DevGraph gv = g->view();
       if (m3) {
-        k_tri3_rows<<<grid1d(m3), T256, 0, s>>>(g->e3, m3, n, g->bwords, g->tri3);
+        k_bitmap_tuples<<<grid1d(m3), T256, 0, f[2]>>>(g->e3, m3, 3, g->bwords, gv.block,
+                                                       gv.block_inv, g->bits3);
+        HM_KCHECK();
+      }
+      if (m4) {
+        k_bitmap_tuples<<<grid1d(m4), T256, 0, f[2]>>>(g->e4, m4, 4, g->bwords, gv.block,
+                                                       gv.block_inv, g->bits4);
+        HM_KCHECK();
+      }
+      if (g->tri3 && m3) {
+        k_tri3_rows<<<grid1d(m3), T256, 0, f[2]>>>(g->e3, m3, n, g->bwords, g->tri3);
         HM_KCHECK();
       }
     }
+    f.join();
   }
-  span_bits.end();
+  span_tables.end();
   {
     DBuf<int> mx(1, s);
     HM_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(int), s));
@@ -536,7 +583,10 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     HM_CUDA(cudaMemcpyAsync(&g->max_d2, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   }
   HM_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof herr, cudaMemcpyDeviceToHost, s));
+  unsigned timeouts = 0;
+  wait_timeouts_async(&timeouts, s);
   HM_CUDA(cudaStreamSynchronize(s));
+  wait_timeouts_check(timeouts, s);
   HM_CHECK(!(herr & ERR_TABLE), HM_ETABLEFULL, "hash insertion exceeded its probe bound");
 }
 

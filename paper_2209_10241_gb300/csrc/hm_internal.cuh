@@ -102,6 +102,25 @@ T* dalloc(size_t count, cudaStream_t s) {
   return p;
 }
 
+// Fork-join concurrency inside one call: up to kSide streams of this device
+// (created once per device, non-blocking) start after everything already
+// queued on `main`, and join() makes `main` wait for all of them. Buffers the
+// side streams use must be allocated on `main` before the fork and released
+// on it after the join; a Fork destroyed without join() (an error unwinds)
+// still joins.
+struct Fork {
+  static constexpr int kSide = 3;
+  cudaStream_t main;
+  cudaStream_t side[kSide] = {};
+  bool joined = false;
+  explicit Fork(cudaStream_t s);
+  cudaStream_t operator[](int i) const { return side[i]; }
+  void join();
+  ~Fork();
+  Fork(const Fork&) = delete;
+  Fork& operator=(const Fork&) = delete;
+};
+
 // ------------------------------------------------------------------ primitives (prims.cu)
 // Exclusive scan: out[0..n] with out[n] = total. in and out may alias only if
 // in == out is not required (they must not alias).
@@ -112,19 +131,47 @@ void scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream
 void scan_exclusive_u64_in(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s,
                            uint64_t* scratch, size_t scratch_elems);
 size_t scan_scratch_elems(int64_t n);
-// Stable LSD radix sort of n keys on their low `bits` bits; vals (nullable)
-// are permuted alongside.
-void radix_sort_u64(uint64_t* keys, uint64_t* vals, int64_t n, int bits, cudaStream_t s);
+// Device-side bounded waits that gave up (see radix sort): enqueue a copy of
+// the count to host memory on s; after s is synchronised, check it (throws
+// HM_ETIMEOUT and clears the count when it is not zero).
+void wait_timeouts_async(unsigned* h_count, cudaStream_t s);
+void wait_timeouts_check(unsigned count, cudaStream_t s);
+// One array for sort_batch (sort.cu): keys are the words a (and b, when
+// b_is_key) -- or a with values b -- sorted stably by the listed 8-bit digit
+// passes (arr 0 = a, 1 = b; shift), in place unless `unique`. With unique, the
+// distinct keys go to `out` (and out_b) in the layout `unpack` names and
+// their count to *d_kept (device); a and b are then left in an unspecified
+// order. PAIR: key (u << member_bits) | v -> uint64 (u << 32) | v. TRIPLE /
+// QUAD: 3 / 4 members of member_bits bits each, most significant first, in
+// (b, a) as one 128-bit key -> int4 (pad -1).
+struct SortJob {
+  enum Unpack { RAW = 0, PAIR = 1, TRIPLE = 2, QUAD = 3 };
+  uint64_t* a = nullptr;
+  uint64_t* b = nullptr;
+  int64_t n = 0;
+  int passes = 0;
+  int8_t arr[16] = {};
+  int8_t shift[16] = {};
+  int b_is_key = 0;
+  int unique = 0;
+  int unpack = RAW;
+  int member_bits = 0;
+  void* out = nullptr;
+  uint64_t* out_b = nullptr;
+  uint32_t* d_kept = nullptr;
+};
+// Sorts 1-4 independent arrays together (one temporary allocation, one
+// launch per pass index for all of them).
+void sort_batch(const SortJob* jobs, int njobs, cudaStream_t s);
+// Stable LSD radix sort of n keys on bits [lo_bit, lo_bit + bits); vals
+// (nullable) are permuted alongside. Keys equal on those bits keep their input
+// order.
+void radix_sort_u64(uint64_t* keys, uint64_t* vals, int64_t n, int bits, cudaStream_t s,
+                    int lo_bit = 0);
 // Stable LSD radix sort of 128-bit keys (hi, lo) lexicographically, on the low
 // lo_bits of lo and the low hi_bits of hi.
 void radix_sort_u128(uint64_t* hi, uint64_t* lo, int64_t n, int hi_bits, int lo_bits,
                      cudaStream_t s);
-// Remove adjacent duplicates of a sorted key array in place; returns the
-// number kept (synchronises the stream). hi may be NULL for 64-bit keys.
-int64_t unique_sorted(uint64_t* hi, uint64_t* lo, int64_t n, cudaStream_t s);
-// The same without a host synchronisation: the number kept goes to *d_kept.
-void unique_sorted_async(uint64_t* hi, uint64_t* lo, int64_t n, uint32_t* d_kept,
-                         cudaStream_t s);
 // off[v] = first index i with (key[i] >> shift) >= v, for v in [0, num_nodes];
 // keys sorted ascending.
 void csr_offsets(const uint64_t* keys, int64_t n, int shift, int32_t num_nodes, int64_t* off,

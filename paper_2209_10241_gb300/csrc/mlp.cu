@@ -25,6 +25,7 @@ constexpr int IN = 16, HID = 64;
 constexpr int P_W1 = 0, P_B1 = 1024, P_W2 = 1088, P_B2 = 5184, P_W3 = 5248, P_B3 = 5312;
 constexpr int NPARAM = 5313;
 constexpr int MLP_THREADS = 256;
+constexpr int BWD_PART = 3 * 64 + 2;  // per-block backward partial: db1 | db2 | dw3 | db3 | loss
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -178,14 +179,12 @@ __global__ void __launch_bounds__(MLP_THREADS)
 __global__ void __launch_bounds__(MLP_THREADS)
     k_mlp_backward(const float* __restrict__ params, const float* __restrict__ X,
                    const float* __restrict__ target, int64_t n, float inv_n,
-                   float* __restrict__ grad, __nv_bfloat16* __restrict__ Xb,
+                   float* __restrict__ part, __nv_bfloat16* __restrict__ Xb,
                    __nv_bfloat16* __restrict__ H1b, __nv_bfloat16* __restrict__ DZ2b,
-                   __nv_bfloat16* __restrict__ DZ1b, float* __restrict__ loss) {
+                   __nv_bfloat16* __restrict__ DZ1b) {
   __shared__ Smem s;
-  __shared__ float gs[HID * 3 + 2];  // db1 | db2 | dw3 | db3 | loss
+  __shared__ float gs[MLP_THREADS / 32][BWD_PART];  // per warp: db1 | db2 | dw3 | db3 | loss
   stage_params(s, params);
-  for (int i = threadIdx.x; i < HID * 3 + 2; i += blockDim.x) gs[i] = 0.f;
-  __syncthreads();
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const int64_t tiles = (n + 15) / 16;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -267,7 +266,9 @@ __global__ void __launch_bounds__(MLP_THREADS)
       *reinterpret_cast<uint32_t*>(Xb + rb * IN + 2 * t + 8) = pack_bf16(p[2 * t + 8], p[2 * t + 9]);
     }
   }
-  // reduce over the 8 row groups of the warp, then over the block, then global
+  // Fixed-order reductions (results do not depend on scheduling): over the 8
+  // row groups of the warp by shuffles, over the warps of the block in warp
+  // order, and over blocks by k_sum_partials in block order.
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
 #pragma unroll
@@ -277,41 +278,66 @@ __global__ void __launch_bounds__(MLP_THREADS)
       dw3[i] += __shfl_xor_sync(0xffffffffu, dw3[i], o);
     }
   }
+#pragma unroll
+  for (int o = 4; o < 32; o <<= 1) {
+    db3 += __shfl_xor_sync(0xffffffffu, db3, o);
+    lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+  }
+  const int wib = threadIdx.x >> 5;
   if (g == 0) {
 #pragma unroll
     for (int j = 0; j < 8; ++j)
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const int c = 8 * j + 2 * t + e;
-        atomicAdd(&gs[c], db1[2 * j + e]);
-        atomicAdd(&gs[HID + c], db2[2 * j + e]);
-        atomicAdd(&gs[2 * HID + c], dw3[2 * j + e]);
+        gs[wib][c] = db1[2 * j + e];
+        gs[wib][HID + c] = db2[2 * j + e];
+        gs[wib][2 * HID + c] = dw3[2 * j + e];
       }
   }
-  if (t == 0) {
-    atomicAdd(&gs[3 * HID], db3);
-    atomicAdd(&gs[3 * HID + 1], lsum);
+  if (lane == 0) {
+    gs[wib][3 * HID] = db3;
+    gs[wib][3 * HID + 1] = lsum;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < HID; i += blockDim.x) {
-    atomicAdd(&grad[P_B1 + i], gs[i]);
-    atomicAdd(&grad[P_B2 + i], gs[HID + i]);
-    atomicAdd(&grad[P_W3 + i], gs[2 * HID + i]);
-  }
-  if (threadIdx.x == 0) {
-    atomicAdd(&grad[P_B3], gs[3 * HID]);
-    if (loss) atomicAdd(loss, gs[3 * HID + 1]);
+  for (int i = threadIdx.x; i < BWD_PART; i += blockDim.x) {
+    float a = 0.f;
+#pragma unroll
+    for (int w = 0; w < MLP_THREADS / 32; ++w) a += gs[w][i];
+    part[(int64_t)blockIdx.x * BWD_PART + i] = a;
   }
 }
 
-// dW[ka][64] += A^T B over rows, A: [n][ka] bf16, B: [n][64] bf16 (ka = 16 or
-// 64). Each block takes a contiguous range of rows in 16-row steps staged in
-// shared memory; warp w owns output rows 16w..16w+15 (8 n-tiles in registers)
-// and reads A^T / B fragments with ldmatrix.trans.
+// Sum over blocks b, in block order, of part[b * width + i], written to
+// grad[grad_off + i]; grad_off < 0 selects the backward partial's layout
+// (db1 | db2 | dw3 | db3 | loss sum), scattered to its parameters and *loss.
+__global__ void k_sum_partials(const float* __restrict__ part, int nblocks, int width,
+                               float* __restrict__ grad, int grad_off, float* __restrict__ loss) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < width; i += gridDim.x * blockDim.x) {
+    float a = 0.f;
+    for (int b = 0; b < nblocks; ++b) a += part[(int64_t)b * width + i];
+    if (grad_off >= 0) {
+      grad[grad_off + i] = a;
+    } else {
+      // backward layout: db1 | db2 | dw3 | db3 | loss
+      if (i < HID) grad[P_B1 + i] = a;
+      else if (i < 2 * HID) grad[P_B2 + i - HID] = a;
+      else if (i < 3 * HID) grad[P_W3 + i - 2 * HID] = a;
+      else if (i == 3 * HID) grad[P_B3] = a;
+      else if (loss) *loss = a;
+    }
+  }
+}
+
+// Partial dW[ka][64] = A^T B over one block's rows, A: [n][ka] bf16, B: [n][64]
+// bf16 (ka = 16 or 64), written to part[block]. Each block takes a contiguous
+// range of rows in 16-row steps staged in shared memory; warp w owns output
+// rows 16w..16w+15 (8 n-tiles in registers) and reads A^T / B fragments with
+// ldmatrix.trans.
 template <int KA>
 __global__ void __launch_bounds__(KA * 2)
     k_mlp_wgrad(const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restrict__ B,
-                int64_t n, int64_t rows_per_block, float* __restrict__ dW) {
+                int64_t n, int64_t rows_per_block, float* __restrict__ part) {
   constexpr int WARPS = KA / 16;
   constexpr int AS = KA + 8, BS = HID + 8;  // padded row strides (bank spread)
   __shared__ __align__(16) __nv_bfloat16 As[16 * AS];
@@ -363,13 +389,12 @@ __global__ void __launch_bounds__(KA * 2)
   }
   if (warp < WARPS) {
     const int g = lane >> 2, t = lane & 3;
+    float* out = part + (int64_t)blockIdx.x * (KA * HID);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int c = 8 * j + 2 * t, ra = 16 * warp + g, rb = ra + 8;
-      atomicAdd(&dW[ra * HID + c], acc[j][0]);
-      atomicAdd(&dW[ra * HID + c + 1], acc[j][1]);
-      atomicAdd(&dW[rb * HID + c], acc[j][2]);
-      atomicAdd(&dW[rb * HID + c + 1], acc[j][3]);
+      *reinterpret_cast<float2*>(out + ra * HID + c) = make_float2(acc[j][0], acc[j][1]);
+      *reinterpret_cast<float2*>(out + rb * HID + c) = make_float2(acc[j][2], acc[j][3]);
     }
   }
 }
@@ -394,9 +419,27 @@ int mlp_blocks(int64_t n) {
   return (int)(b < 1 ? 1 : b);
 }
 
+// weight-gradient blocks: at least 1024 rows each, at most 256 blocks
+int64_t wgrad_rows_per_block(int64_t n) {
+  const int64_t r = (n + 255) / 256;
+  return r < 1024 ? 1024 : ((r + 15) / 16) * 16;
+}
+int wgrad_blocks(int64_t n) {
+  const int64_t b = (n + wgrad_rows_per_block(n) - 1) / wgrad_rows_per_block(n);
+  return (int)(b < 1 ? 1 : b);
+}
+
 }  // namespace
 
 int mlp_num_params() { return NPARAM; }
+
+size_t mlp_scratch_bytes(int64_t n) {
+  if (n <= 0) return 0;
+  const size_t mats = (size_t)n * (IN + 3 * HID) * sizeof(__nv_bfloat16);
+  const size_t parts = ((size_t)mlp_blocks(n) * BWD_PART +
+                        (size_t)wgrad_blocks(n) * (HID * HID + IN * HID)) * sizeof(float);
+  return ((mats + 255) / 256) * 256 + parts;
+}
 
 void mlp_forward(const float* params, const float* X, int64_t n, float* y, cudaStream_t s) {
   if (n == 0) return;
@@ -408,22 +451,33 @@ void mlp_forward(const float* params, const float* X, int64_t n, float* y, cudaS
 // here); scratch holds 2 * n * (16 + 3 * 64) bytes of bf16 matrices.
 void mlp_backward(const float* params, const float* X, const float* target, int64_t n,
                   float* grad, float* loss_sum, void* scratch, cudaStream_t s) {
-  HM_CUDA(cudaMemsetAsync(grad, 0, NPARAM * sizeof(float), s));
-  if (loss_sum) HM_CUDA(cudaMemsetAsync(loss_sum, 0, sizeof(float), s));
-  if (n == 0) return;
+  if (n == 0) {
+    HM_CUDA(cudaMemsetAsync(grad, 0, NPARAM * sizeof(float), s));
+    if (loss_sum) HM_CUDA(cudaMemsetAsync(loss_sum, 0, sizeof(float), s));
+    return;
+  }
   __nv_bfloat16* Xb = (__nv_bfloat16*)scratch;
   __nv_bfloat16* H1b = Xb + n * IN;
   __nv_bfloat16* DZ2b = H1b + n * HID;
   __nv_bfloat16* DZ1b = DZ2b + n * HID;
-  k_mlp_backward<<<mlp_blocks(n), MLP_THREADS, 0, s>>>(params, X, target, n, 1.f / (float)n, grad,
-                                                       Xb, H1b, DZ2b, DZ1b, loss_sum);
+  const size_t mats = (size_t)n * (IN + 3 * HID) * sizeof(__nv_bfloat16);
+  float* part_b = (float*)((char*)scratch + ((mats + 255) / 256) * 256);
+  const int bb = mlp_blocks(n), wb = wgrad_blocks(n);
+  float* part_w2 = part_b + (size_t)bb * BWD_PART;
+  float* part_w1 = part_w2 + (size_t)wb * HID * HID;
+  k_mlp_backward<<<bb, MLP_THREADS, 0, s>>>(params, X, target, n, 1.f / (float)n, part_b, Xb,
+                                            H1b, DZ2b, DZ1b);
   HM_KCHECK();
-  const int64_t rows_per_block = 1024;
-  const unsigned blocks = (unsigned)((n + rows_per_block - 1) / rows_per_block);
-  k_mlp_wgrad<HID><<<blocks, HID * 2, 0, s>>>(H1b, DZ2b, n, rows_per_block, grad + P_W2);
+  const int64_t rows = wgrad_rows_per_block(n);
+  k_mlp_wgrad<HID><<<wb, HID * 2, 0, s>>>(H1b, DZ2b, n, rows, part_w2);
   HM_KCHECK();
-  k_mlp_wgrad<IN><<<blocks, IN * 2 < 32 ? 32 : IN * 2, 0, s>>>(Xb, DZ1b, n, rows_per_block,
-                                                               grad + P_W1);
+  k_mlp_wgrad<IN><<<wb, IN * 2 < 32 ? 32 : IN * 2, 0, s>>>(Xb, DZ1b, n, rows, part_w1);
+  HM_KCHECK();
+  k_sum_partials<<<1, 256, 0, s>>>(part_b, bb, BWD_PART, grad, -1, loss_sum);
+  HM_KCHECK();
+  k_sum_partials<<<16, 256, 0, s>>>(part_w2, wb, HID * HID, grad, P_W2, nullptr);
+  HM_KCHECK();
+  k_sum_partials<<<4, 256, 0, s>>>(part_w1, wb, IN * HID, grad, P_W1, nullptr);
   HM_KCHECK();
 }
 
@@ -441,6 +495,8 @@ void mlp_adam(float* params, const float* grad, float* m, float* v, int step, fl
 extern "C" {
 
 int hm_mlp_num_params(void) { return hm::mlp_num_params(); }
+
+size_t hm_mlp_scratch_bytes(int64_t n) { return hm::mlp_scratch_bytes(n); }
 
 hm_status hm_mlp_forward(const float* d_params, const float* d_x, int64_t n, float* d_y,
                          void* stream) {

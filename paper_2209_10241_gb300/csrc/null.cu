@@ -167,8 +167,11 @@ void count_null_batch(int num_bases, const int32_t* d_members, const int64_t* d_
         HM_KCHECK();
       }
       int herr = 0;
+      unsigned timeouts = 0;
       HM_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof herr, cudaMemcpyDeviceToHost, s));
+      wait_timeouts_async(&timeouts, s);
       HM_CUDA(cudaStreamSynchronize(s));
+      wait_timeouts_check(timeouts, s);
       HM_CHECK(herr == 0, HM_EINVAL, "a member lies outside its base's [0, num_nodes)");
     }
     k_union_offsets<<<grid_n(edges + 1), 256, 0, s>>>(dmi.p, nt, edges, stubs, d_offsets, uoff.p);

@@ -30,6 +30,7 @@ void mlp_backward(const float* params, const float* X, const float* target, int6
 void mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr,
               cudaStream_t s);
 int mlp_num_params();
+size_t mlp_scratch_bytes(int64_t n);
 
 namespace {
 
@@ -212,7 +213,7 @@ void mlp_train(float* params, const float* X, const float* target, int64_t n, in
   HM_CUDA(cudaMemsetAsync(v.p, 0, np * sizeof(float), s));
   if (n == 0) return;
   if (batch <= 0 || batch > n) batch = n;
-  DBuf<unsigned char> scratch((size_t)batch * (16 + 3 * 64) * 2, s);
+  DBuf<unsigned char> scratch(mlp_scratch_bytes(batch), s);
   DBuf<float> Xs(n * 16, s), ts(n, s);
   {
     DBuf<uint64_t> keys(n, s), idx(n, s);
@@ -238,7 +239,10 @@ void mlp_train(float* params, const float* X, const float* target, int64_t n, in
     }
     if (h_loss) h_loss[e] = (float)(eloss / (double)n);
   }
+  unsigned timeouts = 0;
+  wait_timeouts_async(&timeouts, s);
   HM_CUDA(cudaStreamSynchronize(s));
+  wait_timeouts_check(timeouts, s);
 }
 
 }  // namespace hm

@@ -323,10 +323,19 @@ __global__ void __launch_bounds__(SAMPLE_THREADS)
         const unsigned peers = __match_any_sync(0xffffffffu, cls);
         if (cls >= 0 && lane == __ffs(peers) - 1)
           atomicAdd(&blo[cls], (unsigned long long)__popc(peers));
-      } else if (cls >= 0) {
-        const unsigned long long w = wt[sample_of(fam, anchor)];
-        const unsigned long long old = atomicAdd(&blo[cls], w);
-        if (old + w < old) atomicAdd(&bhi[cls], 1ull);
+      } else {
+        // lanes that counted the same class for the same sample add one
+        // product weight x count (128-bit, exact in any order)
+        const uint64_t sid = cls >= 0 ? (uint64_t)sample_of(fam, anchor) : ~0ull;
+        const unsigned long long key = (sid << 8) | (uint64_t)(uint8_t)cls;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (cls >= 0 && lane == __ffs(peers) - 1) {
+          const unsigned long long w = wt[sid], c = (unsigned long long)__popc(peers);
+          const unsigned long long lo = w * c, hi = __umul64hi(w, c);
+          const unsigned long long old = atomicAdd(&blo[cls], lo);
+          const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+          if (hi + carry) atomicAdd(&bhi[cls], hi + carry);
+        }
       }
     }
   }

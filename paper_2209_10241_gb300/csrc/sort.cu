@@ -1,0 +1,507 @@
+// Batched stable LSD radix sort (8-bit digits) with an optional unique +
+// unpack step, for up to SORT_MAX_JOBS independent key arrays at once.
+//
+// One launch takes the digit histograms of every pass of every job (a
+// digit's total does not depend on the key order); then one launch per pass
+// index serves every job that still has a pass, each tile finding its offset
+// for every digit by decoupled look-back over the tiles before it; a final
+// launch drops repeated keys (again with look-back, for the output position)
+// and writes the kept keys in their final layout. Temporaries come from one
+// allocation, so a batch costs a handful of runtime calls whatever its size.
+//
+// Tiles take ids from an atomic counter in the order their blocks start, so a
+// tile only ever waits on tiles that already run; every wait is still bounded
+// and one that gives up counts into g_wait_timeouts (read by the host).
+#include <algorithm>
+#include <vector>
+
+#include "hm_internal.cuh"
+
+namespace hm {
+
+// device-side bounded waits that gave up (see look_back)
+__device__ unsigned int g_wait_timeouts;
+
+namespace {
+
+constexpr int SORT_MAX_JOBS = 4;
+constexpr int SORT_MAX_PASSES = 16;
+constexpr int TPB = 256;               // threads per block
+constexpr int IPT = 8;                 // keys per thread
+constexpr int TILE = TPB * IPT;        // keys per tile
+constexpr uint64_t ST_AGG = 1ull << 62, ST_PREFIX = 2ull << 62, ST_VALUE = (1ull << 62) - 1;
+constexpr uint32_t SPIN_LIMIT = 1u << 20;
+
+struct JobDev {
+  uint64_t* a[2];  // primary word: [0] = caller's array, [1] = temporary
+  uint64_t* b[2];  // second word (high key word or values), may be null
+  int64_t n, tiles;
+  int np;
+  int8_t arr[SORT_MAX_PASSES];
+  int8_t shift[SORT_MAX_PASSES];
+  int b_is_key;       // unique compares b too
+  int unique;         // 0: sort only
+  int unpack;         // SortJob::Unpack
+  int member_bits;
+  void* out;
+  uint64_t* out_b;
+  uint32_t* d_kept;
+  uint32_t* ghist;    // [np][256]
+  uint32_t* gbase;    // [np][256]
+  uint64_t* status[2];  // [tiles][256] per pass parity
+  uint64_t* ustatus;    // [tiles] for unique
+  uint32_t* ctr;        // [np + 1] tile tickets (last one: unique)
+};
+
+struct Batch {
+  int nj;
+  JobDev j[SORT_MAX_JOBS];
+};
+
+// Blocks of a launch covering several jobs: job k owns blocks [first[k], first[k+1]).
+struct Grid {
+  int nj;
+  int job[SORT_MAX_JOBS];
+  int8_t on_b[SORT_MAX_JOBS];   // pass launches: digit of word b
+  int8_t shift[SORT_MAX_JOBS];  // pass launches: digit shift
+  int64_t first[SORT_MAX_JOBS + 1];
+};
+
+// Grid entry e of block blk: its job is G.job[e], its blocks G.first[e]..G.first[e+1).
+__device__ __forceinline__ int grid_entry(const Grid& G, int64_t blk) {
+  int e = 0;
+  while (e + 1 < G.nj && blk >= G.first[e + 1]) ++e;
+  return e;
+}
+
+__device__ __forceinline__ uint64_t ld_status(const uint64_t* p) {
+  return *(const volatile uint64_t*)p;
+}
+__device__ __forceinline__ void st_status(uint64_t* p, uint64_t v) { *(volatile uint64_t*)p = v; }
+
+// Sum of the values published by tiles before `tile` (tile >= 1) in a
+// [tiles][stride] status array, column col: aggregates are added until an
+// inclusive prefix is met.
+__device__ uint64_t look_back(const uint64_t* status, int64_t tile, int stride, int col) {
+  uint64_t excl = 0;
+  int64_t j = tile - 1;
+  uint32_t spins = 0;
+  while (j >= 0) {
+    const uint64_t v = ld_status(status + j * stride + col);
+    if ((v & ~ST_VALUE) == 0) {
+      if (++spins > SPIN_LIMIT) {  // cannot happen with in-order tile tickets
+        atomicAdd(&g_wait_timeouts, 1u);
+        break;
+      }
+      continue;
+    }
+    excl += v & ST_VALUE;
+    if (v & ST_PREFIX) break;
+    --j;
+  }
+  return excl;
+}
+
+// Histograms of all passes of all jobs; the last block to finish turns them
+// into exclusive digit offsets (one warp per (job, pass)) and writes 0 kept
+// keys for empty unique jobs.
+__global__ void __launch_bounds__(TPB)
+    k_sort_hist(const Batch B, const Grid G, uint32_t* done) {
+  __shared__ uint32_t h[SORT_MAX_PASSES][256];
+  __shared__ bool last;
+  if (G.nj) {
+    const int e = grid_entry(G, blockIdx.x);
+    const JobDev& J = B.j[G.job[e]];
+    const int64_t lb = blockIdx.x - G.first[e], jblocks = G.first[e + 1] - G.first[e];
+    for (int i = threadIdx.x; i < J.np * 256; i += TPB) (&h[0][0])[i] = 0;
+    __syncthreads();
+    for (int64_t i = lb * TPB + threadIdx.x; i < J.n; i += jblocks * TPB) {
+      const uint64_t ka = J.a[0][i], kb = J.b[0] ? J.b[0][i] : 0;
+      for (int p = 0; p < J.np; ++p)
+        atomicAdd(&h[p][((J.arr[p] ? kb : ka) >> J.shift[p]) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < J.np * 256; i += TPB)
+      if ((&h[0][0])[i]) atomicAdd(&J.ghist[i], (&h[0][0])[i]);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int total = 0;
+  for (int k = 0; k < B.nj; ++k) total += B.j[k].np;
+  for (int w = warp; w < total; w += TPB / 32) {
+    int k = 0, p = w;
+    while (p >= B.j[k].np) p -= B.j[k++].np;
+    const JobDev& J = B.j[k];
+    const volatile uint32_t* src = J.ghist + p * 256 + lane * 8;
+    uint32_t v[8], sum = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      v[i] = src[i];
+      sum += v[i];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      J.gbase[p * 256 + lane * 8 + i] = run;
+      run += v[i];
+    }
+  }
+  if (threadIdx.x < B.nj) {
+    const JobDev& J = B.j[threadIdx.x];
+    if (J.unique && J.n == 0 && J.d_kept) *J.d_kept = 0;
+  }
+}
+
+// Pass p of every job in the grid.
+__global__ void __launch_bounds__(TPB) k_sort_pass(const Batch B, const Grid G, int p) {
+  __shared__ uint32_t wcnt[TPB / 32][256];
+  __shared__ uint64_t toff[256];
+  __shared__ uint32_t tile_s;
+  const int e = grid_entry(G, blockIdx.x);
+  const JobDev& J = B.j[G.job[e]];
+  if (threadIdx.x == 0) tile_s = atomicAdd(&J.ctr[p], 1u);
+  for (int i = threadIdx.x; i < (TPB / 32) * 256; i += TPB) (&wcnt[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t tile = tile_s;
+  // the next pass's status array was the previous pass's: clear this row
+  J.status[(p + 1) & 1][tile * 256 + threadIdx.x] = 0;
+  const int shift = G.shift[e];
+  const bool on_b = G.on_b[e] != 0;
+  const uint64_t* sa = J.a[p & 1];
+  const uint64_t* sb = J.b[0] ? J.b[p & 1] : nullptr;
+  uint64_t* da = J.a[(p + 1) & 1];
+  uint64_t* db = J.b[0] ? J.b[(p + 1) & 1] : nullptr;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t base = tile * TILE + warp * (32 * IPT);
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t dig[IPT], rank[IPT];
+  uint64_t ka[IPT], kb[IPT];
+#pragma unroll
+  for (int it = 0; it < IPT; ++it) {
+    const int64_t idx = base + it * 32 + lane;
+    ka[it] = idx < J.n ? sa[idx] : 0;
+    kb[it] = (sb && idx < J.n) ? sb[idx] : 0;
+  }
+#pragma unroll
+  for (int it = 0; it < IPT; ++it) {
+    const int64_t idx = base + it * 32 + lane;
+    const bool valid = idx < J.n;
+    const uint32_t d = valid ? (uint32_t)(((on_b ? kb[it] : ka[it]) >> shift) & 255u) : 256u;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t before = valid ? wcnt[warp][d] : 0u;
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = before + __popc(peers);
+    __syncwarp();
+    dig[it] = d;
+    rank[it] = before + __popc(peers & lt);
+  }
+  __syncthreads();
+  {
+    const int d = threadIdx.x;
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < TPB / 32; ++w) {
+      const uint32_t c = wcnt[w][d];
+      wcnt[w][d] = run;
+      run += c;
+    }
+    uint64_t* status = J.status[p & 1];
+    uint64_t excl = 0;
+    if (tile == 0) {
+      st_status(status + d, ST_PREFIX | run);
+    } else {
+      st_status(status + tile * 256 + d, ST_AGG | run);
+      excl = look_back(status, tile, 256, d);
+      st_status(status + tile * 256 + d, ST_PREFIX | (excl + run));
+    }
+    toff[d] = (uint64_t)J.gbase[p * 256 + d] + excl;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < IPT; ++it) {
+    const int64_t idx = base + it * 32 + lane;
+    if (idx < J.n) {
+      const uint32_t d = dig[it];
+      const uint64_t pos = toff[d] + wcnt[warp][d] + rank[it];
+      da[pos] = ka[it];
+      if (db) db[pos] = kb[it];
+    }
+  }
+}
+
+// Unique + unpack of every unique job in the grid: a key is kept when it
+// differs from its predecessor; its output position is the number of kept
+// keys before it (block scan + look-back over tiles).
+__global__ void __launch_bounds__(TPB) k_sort_unique(const Batch B, const Grid G) {
+  __shared__ uint32_t wtot[TPB / 32];
+  __shared__ uint64_t tile_excl;
+  __shared__ uint32_t tile_s;
+  const JobDev& J = B.j[G.job[grid_entry(G, blockIdx.x)]];
+  if (threadIdx.x == 0) tile_s = atomicAdd(&J.ctr[J.np], 1u);
+  __syncthreads();
+  const int64_t tile = tile_s;
+  const uint64_t* sa = J.a[J.np & 1];
+  const uint64_t* sb = J.b[0] ? J.b[J.np & 1] : nullptr;
+  const int64_t i0 = tile * TILE + (int64_t)threadIdx.x * IPT;
+  uint32_t keep = 0, cnt = 0;
+#pragma unroll
+  for (int it = 0; it < IPT; ++it) {
+    const int64_t i = i0 + it;
+    if (i < J.n) {
+      bool k = i == 0 || sa[i] != sa[i - 1];
+      if (!k && J.b_is_key && sb) k = sb[i] != sb[i - 1];
+      if (k) {
+        keep |= 1u << it;
+        ++cnt;
+      }
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += y;
+  }
+  if (lane == 31) wtot[warp] = incl;
+  __syncthreads();
+  uint32_t before = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < TPB / 32; ++w) {
+    before += w < warp ? wtot[w] : 0u;
+    total += wtot[w];
+  }
+  if (threadIdx.x == 0) {
+    uint64_t excl = 0;
+    if (tile == 0) {
+      st_status(J.ustatus, ST_PREFIX | total);
+    } else {
+      st_status(J.ustatus + tile, ST_AGG | total);
+      excl = look_back(J.ustatus, tile, 1, 0);
+      st_status(J.ustatus + tile, ST_PREFIX | (excl + total));
+    }
+    tile_excl = excl;
+    if (tile == J.tiles - 1 && J.d_kept) *J.d_kept = (uint32_t)(excl + total);
+  }
+  __syncthreads();
+  uint64_t pos = tile_excl + before + incl - cnt;
+  const int mb = J.member_bits;
+  const uint64_t mask = (1ull << mb) - 1;
+#pragma unroll
+  for (int it = 0; it < IPT; ++it) {
+    if (!((keep >> it) & 1u)) continue;
+    const int64_t i = i0 + it;
+    const uint64_t ka = sa[i], kb = sb ? sb[i] : 0;
+    if (J.unpack == SortJob::RAW) {
+      static_cast<uint64_t*>(J.out)[pos] = ka;
+      if (J.out_b) J.out_b[pos] = kb;
+    } else if (J.unpack == SortJob::PAIR) {
+      static_cast<uint64_t*>(J.out)[pos] = ((ka >> mb) << 32) | (ka & mask);
+    } else {
+      // members most significant first: the last member in the lowest bits
+      unsigned __int128 key = ((unsigned __int128)kb << 64) | ka;
+      const int32_t m3 = (int32_t)((uint64_t)key & mask);
+      key >>= mb;
+      const int32_t m2 = (int32_t)((uint64_t)key & mask);
+      key >>= mb;
+      const int32_t m1 = (int32_t)((uint64_t)key & mask);
+      key >>= mb;
+      const int32_t m0 = (int32_t)((uint64_t)key & mask);
+      static_cast<int4*>(J.out)[pos] = J.unpack == SortJob::TRIPLE
+                                           ? make_int4(m1, m2, m3, -1)
+                                           : make_int4(m0, m1, m2, m3);
+    }
+    ++pos;
+  }
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+void sort_batch(const SortJob* jobs, int njobs, cudaStream_t s) {
+  HM_CHECK(njobs >= 1 && njobs <= SORT_MAX_JOBS, HM_EINVAL, "sort batch of 1-4 jobs");
+  Batch B{};
+  B.nj = njobs;
+  // scratch: [zeroed: per job status[0] | ustatus | ghist | ctr ; done] [per job: status[1] |
+  // gbase | temporaries]
+  size_t zbytes = 0, bytes = 0;
+  std::vector<size_t> zoff(njobs), off(njobs);
+  for (int k = 0; k < njobs; ++k) {
+    const SortJob& S = jobs[k];
+    HM_CHECK(S.n >= 0 && S.n < (1ll << 31), HM_EINVAL, "sort input too large");
+    HM_CHECK(S.passes >= 0 && S.passes <= SORT_MAX_PASSES, HM_EINVAL, "too many radix passes");
+    HM_CHECK(!S.unique || S.out || S.n == 0, HM_EINVAL, "unique sort without an output");
+    JobDev& J = B.j[k];
+    J.n = S.n;
+    J.tiles = (S.n + TILE - 1) / TILE;
+    J.np = S.n > 1 ? S.passes : 0;
+    for (int p = 0; p < S.passes; ++p) {
+      J.arr[p] = S.arr[p];
+      J.shift[p] = S.shift[p];
+    }
+    J.b_is_key = S.b_is_key;
+    J.unique = S.unique;
+    J.unpack = S.unpack;
+    J.member_bits = S.member_bits;
+    J.out = S.out;
+    J.out_b = S.out_b;
+    J.d_kept = S.d_kept;
+    zoff[k] = zbytes;
+    zbytes += align256((size_t)J.tiles * 256 * 8) + align256((size_t)J.tiles * 8) +
+              align256((size_t)SORT_MAX_PASSES * 256 * 4) + align256((SORT_MAX_PASSES + 1) * 4);
+  }
+  zbytes += 256;  // done counter
+  bytes = zbytes;
+  for (int k = 0; k < njobs; ++k) {
+    off[k] = bytes;
+    const JobDev& J = B.j[k];
+    bytes += align256((size_t)J.tiles * 256 * 8) + align256((size_t)SORT_MAX_PASSES * 256 * 4);
+    if (J.np > 0) bytes += align256((size_t)J.n * 8) * (jobs[k].b ? 2 : 1);
+  }
+  DBuf<unsigned char> scratch(bytes, s);
+  unsigned char* base = scratch.p;
+  for (int k = 0; k < njobs; ++k) {
+    JobDev& J = B.j[k];
+    const SortJob& S = jobs[k];
+    unsigned char* z = base + zoff[k];
+    J.status[0] = reinterpret_cast<uint64_t*>(z);
+    z += align256((size_t)J.tiles * 256 * 8);
+    J.ustatus = reinterpret_cast<uint64_t*>(z);
+    z += align256((size_t)J.tiles * 8);
+    J.ghist = reinterpret_cast<uint32_t*>(z);
+    z += align256((size_t)SORT_MAX_PASSES * 256 * 4);
+    J.ctr = reinterpret_cast<uint32_t*>(z);
+    unsigned char* q = base + off[k];
+    J.status[1] = reinterpret_cast<uint64_t*>(q);
+    q += align256((size_t)J.tiles * 256 * 8);
+    J.gbase = reinterpret_cast<uint32_t*>(q);
+    q += align256((size_t)SORT_MAX_PASSES * 256 * 4);
+    J.a[0] = S.a;
+    J.b[0] = S.b;
+    J.a[1] = J.np > 0 ? reinterpret_cast<uint64_t*>(q) : S.a;
+    if (J.np > 0) q += align256((size_t)J.n * 8);
+    J.b[1] = (J.np > 0 && S.b) ? reinterpret_cast<uint64_t*>(q) : S.b;
+  }
+  uint32_t* done = reinterpret_cast<uint32_t*>(base + zbytes - 256);
+  HM_CUDA(cudaMemsetAsync(base, 0, zbytes, s));
+
+  // histograms (at least one block, for the offsets and empty jobs)
+  {
+    Grid G{};
+    int64_t blocks = 0;
+    for (int k = 0; k < njobs; ++k) {
+      if (B.j[k].np == 0) continue;
+      int64_t hb = (B.j[k].n + 4095) / 4096;
+      if (hb > 152 * 2) hb = 152 * 2;
+      G.job[G.nj] = k;
+      G.first[G.nj] = blocks;
+      blocks += hb;
+      ++G.nj;
+    }
+    G.first[G.nj] = blocks;
+    k_sort_hist<<<(unsigned)(blocks > 0 ? blocks : 1), TPB, 0, s>>>(B, G, done);
+    HM_KCHECK();
+  }
+  int maxp = 0;
+  for (int k = 0; k < njobs; ++k) maxp = std::max(maxp, B.j[k].np);
+  for (int p = 0; p < maxp; ++p) {
+    Grid G{};
+    int64_t blocks = 0;
+    for (int k = 0; k < njobs; ++k) {
+      if (B.j[k].np <= p) continue;
+      G.job[G.nj] = k;
+      G.on_b[G.nj] = B.j[k].arr[p];
+      G.shift[G.nj] = B.j[k].shift[p];
+      G.first[G.nj] = blocks;
+      blocks += B.j[k].tiles;
+      ++G.nj;
+    }
+    G.first[G.nj] = blocks;
+    k_sort_pass<<<(unsigned)blocks, TPB, 0, s>>>(B, G, p);
+    HM_KCHECK();
+  }
+  {
+    Grid G{};
+    int64_t blocks = 0;
+    for (int k = 0; k < njobs; ++k) {
+      if (!B.j[k].unique || B.j[k].n == 0) continue;
+      G.job[G.nj] = k;
+      G.first[G.nj] = blocks;
+      blocks += B.j[k].tiles;
+      ++G.nj;
+    }
+    G.first[G.nj] = blocks;
+    if (blocks) {
+      k_sort_unique<<<(unsigned)blocks, TPB, 0, s>>>(B, G);
+      HM_KCHECK();
+    }
+  }
+  // sort-only jobs whose last pass ended in the temporaries: copy back
+  for (int k = 0; k < njobs; ++k) {
+    const JobDev& J = B.j[k];
+    if (J.unique || (J.np & 1) == 0) continue;
+    HM_CUDA(cudaMemcpyAsync(J.a[0], J.a[1], J.n * 8, cudaMemcpyDeviceToDevice, s));
+    if (J.b[0]) HM_CUDA(cudaMemcpyAsync(J.b[0], J.b[1], J.n * 8, cudaMemcpyDeviceToDevice, s));
+  }
+}
+
+void wait_timeouts_async(unsigned* h_count, cudaStream_t s) {
+  HM_CUDA(cudaMemcpyFromSymbolAsync(h_count, g_wait_timeouts, sizeof(unsigned), 0,
+                                    cudaMemcpyDeviceToHost, s));
+}
+
+void wait_timeouts_check(unsigned count, cudaStream_t s) {
+  if (!count) return;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_wait_timeouts) == cudaSuccess)
+    cudaMemsetAsync(p, 0, sizeof(unsigned), s);
+  HM_CHECK(false, HM_ETIMEOUT, "a device-side wait gave up (decoupled look-back)");
+}
+
+void radix_sort_u64(uint64_t* keys, uint64_t* vals, int64_t n, int bits, cudaStream_t s,
+                    int lo_bit) {
+  SortJob J{};
+  J.a = keys;
+  J.b = vals;
+  J.n = n;
+  for (int sh = 0; sh < bits; sh += 8) {
+    J.arr[J.passes] = 0;
+    J.shift[J.passes++] = (int8_t)(lo_bit + sh);
+  }
+  if (n <= 1 || J.passes == 0) return;
+  sort_batch(&J, 1, s);
+}
+
+void radix_sort_u128(uint64_t* hi, uint64_t* lo, int64_t n, int hi_bits, int lo_bits,
+                     cudaStream_t s) {
+  SortJob J{};
+  J.a = lo;
+  J.b = hi;
+  J.n = n;
+  J.b_is_key = 1;
+  J.passes = 0;
+  for (int sh = 0; sh < lo_bits; sh += 8) {
+    J.arr[J.passes] = 0;
+    J.shift[J.passes++] = (int8_t)sh;
+  }
+  for (int sh = 0; sh < hi_bits; sh += 8) {
+    J.arr[J.passes] = 1;
+    J.shift[J.passes++] = (int8_t)sh;
+  }
+  if (n <= 1 || J.passes == 0) return;
+  sort_batch(&J, 1, s);
+}
+
+}  // namespace hm

@@ -111,6 +111,21 @@ def trained(hm):
                 exact=exact, g=g, h=h)
 
 
+def test_backward_and_training_are_deterministic(hm, trained):
+    """Fixed-order reductions: the same inputs give the same bits."""
+    p = mlp.init_params(5)
+    X, t = _mlp_data(33333, 4)
+    dp, dX, dt = (torch.from_numpy(a).cuda() for a in (p, X, t))
+    g1, l1 = hm.mlp_backward(dp, dX, dt)
+    g2, l2 = hm.mlp_backward(dp, dX, dt)
+    assert torch.equal(g1, g2) and torch.equal(l1, l2)
+    q = torch.from_numpy(mlp.init_params(1)).cuda()
+    losses = hm.mlp_train(q, trained["feat"], trained["targets"], epochs=30, batch=4096,
+                          lr=3e-3, seed=3)
+    assert torch.equal(q, trained["params"])
+    assert list(losses) == list(trained["losses"])
+
+
 def test_training_lowers_the_loss(trained):
     L = trained["losses"]
     assert all(np.isfinite(L)) and L[-1] < 0.5 * L[0], L
