@@ -198,7 +198,7 @@ def measure_sampler(hm, stream, scale=0.004, budgets=(12_000, 60_000, 300_000), 
     tgt = hm.proposal_targets(gt, k, contrib, exact_t, eps=1e-9)
     feat = hm.features(gt, k)
     params = torch.from_numpy(synth.mlp_init_params(1)).cuda()
-    losses = hm.mlp_train(params, feat, tgt, epochs=30, batch=4096, lr=3e-3, seed=3)
+    losses = hm.mlp_train(params, feat, tgt, epochs=300, batch=4096, lr=1e-3, seed=3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t_train
     h = synth.workload("comm-5m", seed=9, scale=scale)
@@ -244,6 +244,67 @@ def measure_null(hm, stream, hyperedges=NULL_BASES, models=8):
     return {"bases": [b.num_hyperedges for b in bases], "nodes": [b.num_nodes for b in bases],
             "models": len(bases) * models, "ms": ms, "sets": sets,
             "sets_per_s": sets / (ms / 1e3)}
+
+
+def measure_sampler_full(hm, stream, budgets=(100_000, 1_000_000, 10_000_000), seeds=5,
+                         run_limit_s=60.0):
+    """Alg. 4 on the full communication-shaped workload (5M nodes, 10M
+    hyperedges): uniform vs learned (beta = 1/2) proposal at S draws, the
+    proposal trained on a 500k-hyperedge instance of the same generator (scale
+    0.05, another seed); error against the exact census of the full graph. A
+    budget whose single run exceeds run_limit_s ends the sweep."""
+    import numpy as np
+    import torch
+    from paper_2209_10241_gb300 import synth
+    k = 4
+    t0 = time.perf_counter()
+    tr = synth.workload("comm-5m", seed=7, scale=0.05)
+    gt = hm.from_host(tr, 4)
+    contrib = hm.contributions(gt, k)
+    exact_t = hm.count_exact(gt, k)
+    tgt = hm.proposal_targets(gt, k, contrib, exact_t, eps=1e-9)
+    feat = hm.features(gt, k)
+    params = torch.from_numpy(synth.mlp_init_params(1)).cuda()
+    losses = hm.mlp_train(params, feat, tgt, epochs=300, batch=8192, lr=1e-3, seed=3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del contrib, feat, tgt, gt
+    h = synth.workload("comm-5m", seed=0)
+    g = hm.from_host(h, 4)
+    exact_ms, T = _event_ms(lambda: hm.count_exact(g, k), stream)
+    T = T.cpu().numpy().astype(np.float64)
+    q_ms, q = _event_ms(lambda: hm.proposal_weights(g, k, params, lam=0.1, beta=0.5), stream)
+    masks = {"T>=100": T >= 100, "T>=1000": T >= 1000}
+    rows = []
+    for S in budgets:
+        split = {2: S // 6, 4: S // 3}
+        split[3] = S - split[2] - split[4]
+        rec = {"S": S}
+        slow = False
+        for name, qq in (("uniform", None), ("learned", q)):
+            ms, errs = [], {m: [] for m in masks}
+            for r in range(seeds):
+                t, (est, _) = _event_ms(lambda: hm.count_sampled(g, k, samples=split,
+                                                                 seed=100 + r, q=qq), stream)
+                e = est.cpu().numpy()
+                ms.append(t)
+                for m, big in masks.items():
+                    errs[m].append(float(np.mean(np.abs(e[big] - T[big]) / T[big])))
+                if t > run_limit_s * 1e3:
+                    slow = True
+                    break
+            rec[name] = {"ms": float(np.median(ms)), "runs": len(ms),
+                         **{f"mre_{m}": float(np.mean(v)) for m, v in errs.items()}}
+        rows.append(rec)
+        if slow:
+            break
+    return {"workload": f"comm-5m generator, full size: {h.num_nodes} nodes, "
+                        f"{h.num_hyperedges} hyperedges; proposal trained on {tr.num_hyperedges} "
+                        f"hyperedges (scale 0.05, seed 7)", "order": k,
+            "classes_T_ge_100": int(masks["T>=100"].sum()),
+            "classes_T_ge_1000": int(masks["T>=1000"].sum()), "exact_census_ms": exact_ms,
+            "proposal_weights_ms": q_ms, "train_s": train_s,
+            "train_loss_first_last": [losses[0], losses[-1]], "by_budget": rows}
 
 
 def measure_large(hm, stream, names=("coauth-1m", "comm-5m")):
@@ -356,7 +417,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sampler and null-batch measurements")
-    ap.add_argument("--only", choices=["sampler", "null", "large"], default=None,
+    ap.add_argument("--only", choices=["sampler", "null", "large", "sampler-full"], default=None,
                     help="run one of the extra measurements alone (for profiling)")
     ap.add_argument("--null-bases", type=int, default=8,
                     help="number of null-model bases (log-spaced 50k-500k hyperedges)")
@@ -382,6 +443,8 @@ def main():
             res = measure_sampler(hm, stream)
         elif args.only == "null":
             res = measure_null(hm, stream, hyperedges=NULL_BASES[:args.null_bases])
+        elif args.only == "sampler-full":
+            res = measure_sampler_full(hm, stream)
         else:
             res = measure_large(hm, stream)
         print(json.dumps({"only": args.only, **res}), flush=True)

@@ -5,7 +5,9 @@ d2 = pair degree, t3 = number of 3-hyperedges through a node:
   0: 1, 1: |e|/4, 2-4: log1p(min/mean/max d2), 5-7: log1p(min/mean/max t3),
   8: log1p(#member pairs that are hyperedges), 9: log1p(the number of sets a
   draw of e enumerates at order k), 10: log1p(sum d2), 11: log1p(sum t3),
-  12-15: 0.
+  12: log1p(#3-hyperedges other than e sharing at least two nodes with e),
+  13: log1p(#3-hyperedges inside e), 14-15: 0.
+Features 12-13 are counted directly here, triple by triple.
 """
 from __future__ import annotations
 
@@ -24,6 +26,12 @@ def features(g, k: int) -> np.ndarray:
         for tri in E[3]:
             t3[tri] += 1
     pairs = set(map(tuple, E[2].tolist()))
+    tri = [frozenset(t) for t in E[3].tolist()] if 3 in E else []
+    # the 3-hyperedges through each node, to meet every triple sharing a node with e
+    through = {}
+    for t in tri:
+        for v in t:
+            through.setdefault(v, []).append(t)
     rows = []
     for s in range(2, k + 1):
         for e in E[s].tolist():
@@ -46,6 +54,10 @@ def features(g, k: int) -> np.ndarray:
             f[9] = np.log1p(work)
             f[10] = np.log1p(d.sum())
             f[11] = np.log1p(t.sum())
+            es = frozenset(e)
+            near = {u for v in e for u in through.get(v, [])}
+            f[12] = np.log1p(sum(1 for u in near if u != es and len(u & es) >= 2))
+            f[13] = np.log1p(sum(1 for u in near if u <= es and u != es))
             rows.append(f)
     return np.array(rows).reshape(-1, 16)
 

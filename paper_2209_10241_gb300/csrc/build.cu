@@ -575,17 +575,26 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     f.join();
   }
   span_tables.end();
-  {
-    DBuf<int> mx(1, s);
-    HM_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(int), s));
-    k_max_degree<<<grid1d(n), T256, 0, s>>>(g->off2, n, mx.p);
-    HM_KCHECK();
-    HM_CUDA(cudaMemcpyAsync(&g->max_d2, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-  }
-  HM_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof herr, cudaMemcpyDeviceToHost, s));
+  // the census work spaces of max_order, ready before the final
+  // synchronisation (a census then starts without one)
+  PendingSpaces pend;
+  DBuf<int> mx(1, s);
+  HM_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(int), s));
+  k_max_degree<<<grid1d(n), T256, 0, s>>>(g->off2, n, mx.p);
+  HM_KCHECK();
+  spaces_enqueue(g, census_spaces(g, kmax), s, pend);
   unsigned timeouts = 0;
-  wait_timeouts_async(&timeouts, s);
-  HM_CUDA(cudaStreamSynchronize(s));
+  try {
+    HM_CUDA(cudaMemcpyAsync(&g->max_d2, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof herr, cudaMemcpyDeviceToHost, s));
+    wait_timeouts_async(&timeouts, s);
+    HM_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    for (uint64_t* p : pend.made) cudaFreeAsync(p, s);
+    throw;
+  }
+  spaces_finish(pend);
+  choose_variants(g, kmax);
   wait_timeouts_check(timeouts, s);
   HM_CHECK(!(herr & ERR_TABLE), HM_ETABLEFULL, "hash insertion exceeded its probe bound");
 }

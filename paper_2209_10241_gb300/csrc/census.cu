@@ -33,6 +33,10 @@
 #include <cstdlib>
 #include <initializer_list>
 #include <vector>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <string>
 
 #include "families.cuh"
 
@@ -50,8 +54,8 @@ constexpr int BIN_STRIDE = 176;
 template <class F, bool kBatched>
 __global__ void __launch_bounds__(CENSUS_THREADS)
     k_census(const DevGraph g, const F fam, const uint64_t* __restrict__ ws, int64_t A,
-             uint64_t total, int chunk, const uint8_t* __restrict__ lut_g, int nmask, int ncls,
-             int ngraphs, unsigned long long* __restrict__ hist) {
+             uint64_t begin, uint64_t total, int chunk, const uint8_t* __restrict__ lut_g,
+             int nmask, int ncls, int ngraphs, unsigned long long* __restrict__ hist) {
   __shared__ unsigned long long bins[kBatched ? 1 : BIN_STRIDE];
   __shared__ unsigned int gbins[kBatched ? MAX_GRAPHS * BIN_STRIDE : 1];
   __shared__ uint8_t lut[2048];
@@ -64,11 +68,12 @@ __global__ void __launch_bounds__(CENSUS_THREADS)
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
-  const uint64_t nchunks = (total + chunk - 1) / chunk;
+  // candidates [begin, total) in chunks of `chunk` consecutive ones per lane
+  const uint64_t nchunks = (total - begin + chunk - 1) / chunk;
   const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t cb = warp * 32; cb < nchunks; cb += nwarps * 32) {
-    const uint64_t g0 = (cb + lane) * chunk;
+    const uint64_t g0 = begin + (cb + lane) * chunk;
     const uint64_t g1 = min(g0 + chunk, total);
     typename F::State st;
     int64_t a = 0;
@@ -139,8 +144,8 @@ constexpr int BITS_CHUNK = 4;
 template <class F, bool kBatched>
 __global__ void __launch_bounds__(CENSUS_THREADS, HM_BITS_MINBLOCKS)
     k_census_bits(const DevGraph g, const F fam, const uint64_t* __restrict__ ws, int64_t A,
-                  uint64_t total, const uint8_t* __restrict__ lut_g, int nmask, int ncls,
-                  int ngraphs, unsigned long long* __restrict__ hist) {
+                  uint64_t begin, uint64_t total, const uint8_t* __restrict__ lut_g, int nmask,
+                  int ncls, int ngraphs, unsigned long long* __restrict__ hist) {
   __shared__ unsigned long long bins[kBatched ? 1 : BIN_STRIDE];
   __shared__ unsigned int gbins[kBatched ? MAX_GRAPHS * BIN_STRIDE : 1];
   __shared__ uint8_t lut[2048];
@@ -151,10 +156,11 @@ __global__ void __launch_bounds__(CENSUS_THREADS, HM_BITS_MINBLOCKS)
     for (int i = threadIdx.x; i < ncls; i += blockDim.x) bins[i] = 0;
   }
   __syncthreads();
-  const uint64_t nchunks = (total + BITS_CHUNK - 1) / BITS_CHUNK;
+  // items [begin, total), BITS_CHUNK consecutive ones per thread
+  const uint64_t nchunks = (total - begin + BITS_CHUNK - 1) / BITS_CHUNK;
   for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
        c += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t g0 = c * BITS_CHUNK, g1 = min(g0 + BITS_CHUNK, total);
+    const uint64_t g0 = begin + c * BITS_CHUNK, g1 = min(g0 + BITS_CHUNK, total);
     typename F::State st;
     int64_t a = anchor_of(ws, A, g0);
     uint64_t r = g0 - ws[a], wa = ws[a + 1] - ws[a];
@@ -249,57 +255,88 @@ unsigned grid1d(int64_t n) {
   return (unsigned)b;
 }
 
-// Prefix sums of the candidates per anchor for every family in `todo`, with
-// one host synchronisation for all of them (the totals size the launches).
-void ensure_spaces(hm_graph* g, std::initializer_list<std::pair<hm_graph::Space*, char>> todo,
-                   cudaStream_t s) {
-  std::vector<std::pair<hm_graph::Space*, char>> need;
+}  // namespace
+
+// Prefix sums of the candidates per anchor for every family in `todo` that is
+// not ready: enqueued on s (one temporary for all families), with the totals
+// copied to P.h; spaces_finish, after s has completed, marks them ready.
+void spaces_enqueue(hm_graph* g, const std::vector<std::pair<hm_graph::Space*, char>>& todo,
+                    cudaStream_t s, PendingSpaces& P) {
+  P.need.clear();
+  P.made.clear();
   for (auto& t : todo)
-    if (!t.first->ready) need.push_back(t);
-  if (need.empty()) return;
-  DBuf<uint64_t> totals(need.size(), s);
-  std::vector<uint64_t*> made;
+    if (!t.first->ready) P.need.push_back(t);
+  if (P.need.empty()) return;
+  HM_CHECK(P.need.size() <= 8, HM_EINVAL, "too many work spaces");
+  std::vector<int64_t> A(P.need.size());
+  size_t tmp = 0;
+  for (size_t i = 0; i < P.need.size(); ++i) {
+    const char fam = P.need[i].second;
+    int64_t a = 0;
+    if (fam == 'W' || fam == 'S' || fam == 'w' || fam == 's') a = g->n;
+    if (fam == 'P' || fam == 'p') a = g->counts[2];
+    if (fam == 'X') a = g->kmax >= 3 ? g->counts[3] : 0;
+    A[i] = a;
+    tmp = std::max<size_t>(tmp, (size_t)a);
+  }
+  DBuf<uint64_t> w(tmp, s), totals(P.need.size(), s);
   try {
-    for (size_t i = 0; i < need.size(); ++i) {
-      hm_graph::Space& sp = *need[i].first;
-      const char fam = need[i].second;
-      int64_t A = 0;
-      if (fam == 'W' || fam == 'S' || fam == 'w' || fam == 's') A = g->n;
-      if (fam == 'P' || fam == 'p') A = g->counts[2];
-      if (fam == 'X') A = g->kmax >= 3 ? g->counts[3] : 0;
-      DBuf<uint64_t> w(A, s);
-      uint64_t* ws = dalloc<uint64_t>((size_t)A + 1, s);
-      made.push_back(ws);
-      if (A > 0) {
+    for (size_t i = 0; i < P.need.size(); ++i) {
+      const char fam = P.need[i].second;
+      const int64_t a = A[i];
+      uint64_t* ws = dalloc<uint64_t>((size_t)a + 1, s);
+      P.made.push_back(ws);
+      if (a > 0) {
         if (fam == 'W' || fam == 'S')
-          k_ws_nodes<<<grid1d(A), 256, 0, s>>>(g->off2, g->n, fam == 'W' ? 2 : 3, w.p);
+          k_ws_nodes<<<grid1d(a), 256, 0, s>>>(g->off2, g->n, fam == 'W' ? 2 : 3, w.p);
         else if (fam == 'w' || fam == 's')
-          k_ws_nodes_bits<<<grid1d(A), 256, 0, s>>>(g->off2, g->n, fam == 'w' ? 2 : 3, w.p);
+          k_ws_nodes_bits<<<grid1d(a), 256, 0, s>>>(g->off2, g->n, fam == 'w' ? 2 : 3, w.p);
         else if (fam == 'P')
-          k_ws_pairs<<<grid1d(A), 256, 0, s>>>(g->e2, A, g->off2, w.p);
+          k_ws_pairs<<<grid1d(a), 256, 0, s>>>(g->e2, a, g->off2, w.p);
         else if (fam == 'p')
-          k_ws_pairs_bits<<<grid1d(A), 256, 0, s>>>(g->e2, A, g->off2, w.p);
+          k_ws_pairs_bits<<<grid1d(a), 256, 0, s>>>(g->e2, a, g->off2, w.p);
         else
-          k_ws_triples<<<grid1d(A), 256, 0, s>>>(g->e3, A, g->off2, g->off3, w.p);
+          k_ws_triples<<<grid1d(a), 256, 0, s>>>(g->e3, a, g->off2, g->off3, w.p);
         HM_KCHECK();
       }
-      scan_exclusive_u64(w.p, ws, A, s);
-      HM_CUDA(cudaMemcpyAsync(totals.p + i, ws + A, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
-      sp.anchors = A;
+      scan_exclusive_u64(w.p, ws, a, s);
+      HM_CUDA(cudaMemcpyAsync(totals.p + i, ws + a, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+      P.need[i].first->anchors = a;
     }
-    std::vector<uint64_t> h(need.size());
-    HM_CUDA(cudaMemcpyAsync(h.data(), totals.p, h.size() * sizeof(uint64_t),
+    HM_CUDA(cudaMemcpyAsync(P.h, totals.p, P.need.size() * sizeof(uint64_t),
                             cudaMemcpyDeviceToHost, s));
-    HM_CUDA(cudaStreamSynchronize(s));
-    for (size_t i = 0; i < need.size(); ++i) {
-      need[i].first->ws = made[i];
-      need[i].first->total = h[i];
-      need[i].first->ready = true;
-    }
   } catch (...) {
-    for (uint64_t* p : made) cudaFreeAsync(p, s);
+    for (uint64_t* p : P.made) cudaFreeAsync(p, s);
+    P.made.clear();
+    P.need.clear();
     throw;
   }
+}
+
+void spaces_finish(PendingSpaces& P) {
+  for (size_t i = 0; i < P.need.size(); ++i) {
+    P.need[i].first->ws = P.made[i];
+    P.need[i].first->total = P.h[i];
+    P.need[i].first->ready = true;
+  }
+  P.need.clear();
+  P.made.clear();
+}
+
+namespace {
+
+void ensure_spaces(hm_graph* g, const std::vector<std::pair<hm_graph::Space*, char>>& todo,
+                   cudaStream_t s) {
+  PendingSpaces P;
+  spaces_enqueue(g, todo, s, P);
+  if (P.need.empty()) return;
+  try {
+    HM_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    for (uint64_t* p : P.made) cudaFreeAsync(p, s);
+    throw;
+  }
+  spaces_finish(P);
 }
 
 // Persistent grid: SMs x resident blocks, capped by the work; with a union
@@ -323,41 +360,41 @@ int grid_for(const void* kernel, uint64_t lanes_needed, uint64_t max_candidates,
 
 int num_graphs(const hm_graph* g) { return g->block ? (g->n + g->block - 1) / g->block : 1; }
 
+// Launch one family over its index range [begin, end) (items for bit-sliced
+// families, candidates otherwise). chunk = candidates per lane of a
+// per-candidate family; 0 = as many as fill the GPU, at most CHUNK.
 template <class F, bool kBatched>
-void launch_bits_t(const hm_graph* g, const F& fam, const hm_graph::Space& sp, int order,
-                   unsigned long long* hist, cudaStream_t s) {
+void launch_bits_t(const hm_graph* g, const F& fam, const hm_graph::Space& sp, uint64_t begin,
+                   uint64_t end, int order, unsigned long long* hist, cudaStream_t s,
+                   bool traced) {
   const ClassTables& T = class_tables(order);
   const uint8_t* lut = device_lut(order);
-  const uint64_t lanes = (sp.total + BITS_CHUNK - 1) / BITS_CHUNK;
-  const uint64_t max_cand = sp.total * (uint64_t)g->bwords * 32;
+  const uint64_t lanes = (end - begin + BITS_CHUNK - 1) / BITS_CHUNK;
+  const uint64_t max_cand = (end - begin) * (uint64_t)g->bwords * 32;
   const int blocks = grid_for((const void*)k_census_bits<F, kBatched>, lanes, max_cand, kBatched);
   cudaEvent_t ev = nullptr;
-  const bool tr = trace_on();
+  const bool tr = traced && trace_on();
   if (tr) trace_begin(s, &ev);
   k_census_bits<F, kBatched><<<blocks, CENSUS_THREADS, 0, s>>>(
-      g->view(), fam, sp.ws, sp.anchors, sp.total, lut, (int)T.lut.size(), T.ncls, num_graphs(g),
-      hist);
+      g->view(), fam, sp.ws, sp.anchors, begin, end, lut, (int)T.lut.size(), T.ncls,
+      num_graphs(g), hist);
   HM_KCHECK();
   if (tr) trace_end(F::kName, s, ev);
 }
 
 template <class F>
 void launch_bits(const hm_graph* g, const F& fam, const hm_graph::Space& sp, int order,
-                 unsigned long long* hist, cudaStream_t s) {
-  if (sp.total == 0) return;
+                 unsigned long long* hist, cudaStream_t s, uint64_t begin = 0,
+                 uint64_t end = ~0ull, bool traced = true) {
+  if (end > sp.total) end = sp.total;
+  if (begin >= end) return;
   if (g->block)
-    launch_bits_t<F, true>(g, fam, sp, order, hist, s);
+    launch_bits_t<F, true>(g, fam, sp, begin, end, order, hist, s, traced);
   else
-    launch_bits_t<F, false>(g, fam, sp, order, hist, s);
+    launch_bits_t<F, false>(g, fam, sp, begin, end, order, hist, s, traced);
 }
 
-template <class F, bool kBatched>
-void launch_family_t(const hm_graph* g, const F& fam, const hm_graph::Space* sp, uint64_t total,
-                     int order, unsigned long long* hist, cudaStream_t s) {
-  const ClassTables& T = class_tables(order);
-  const uint8_t* lut = device_lut(order);
-  // consecutive candidates per lane: up to CHUNK, fewer when the family is
-  // too small to fill the GPU that way (every lane of a warp takes the same)
+int fill_chunk(uint64_t candidates) {
   static int sms = 0;
   if (!sms) {
     int dev = 0;
@@ -365,15 +402,26 @@ void launch_family_t(const hm_graph* g, const F& fam, const hm_graph::Space* sp,
     HM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   }
   const uint64_t lanes_wanted = (uint64_t)sms * 2048;
-  int chunk = (int)std::min<uint64_t>(CHUNK, (total + lanes_wanted - 1) / lanes_wanted);
-  if (chunk < 1) chunk = 1;
-  const int blocks = grid_for((const void*)k_census<F, kBatched>, (total + chunk - 1) / chunk,
-                              total, kBatched);
+  const int chunk = (int)std::min<uint64_t>(CHUNK, (candidates + lanes_wanted - 1) / lanes_wanted);
+  return chunk < 1 ? 1 : chunk;
+}
+
+template <class F, bool kBatched>
+void launch_family_t(const hm_graph* g, const F& fam, const hm_graph::Space* sp, uint64_t begin,
+                     uint64_t end, int chunk, int order, unsigned long long* hist,
+                     cudaStream_t s, bool traced) {
+  const ClassTables& T = class_tables(order);
+  const uint8_t* lut = device_lut(order);
+  // consecutive candidates per lane (every lane of a warp takes the same)
+  if (chunk <= 0) chunk = fill_chunk(end - begin);
+  if (chunk > CHUNK) chunk = CHUNK;
+  const int blocks = grid_for((const void*)k_census<F, kBatched>, (end - begin + chunk - 1) / chunk,
+                              end - begin, kBatched);
   cudaEvent_t ev = nullptr;
-  const bool tr = trace_on();
+  const bool tr = traced && trace_on();
   if (tr) trace_begin(s, &ev);
   k_census<F, kBatched><<<blocks, CENSUS_THREADS, 0, s>>>(
-      g->view(), fam, sp ? sp->ws : nullptr, sp ? sp->anchors : 0, total, chunk, lut,
+      g->view(), fam, sp ? sp->ws : nullptr, sp ? sp->anchors : 0, begin, end, chunk, lut,
       (int)T.lut.size(), T.ncls, num_graphs(g), hist);
   HM_KCHECK();
   if (tr) trace_end(F::kName, s, ev);
@@ -381,12 +429,14 @@ void launch_family_t(const hm_graph* g, const F& fam, const hm_graph::Space* sp,
 
 template <class F>
 void launch_family(const hm_graph* g, const F& fam, const hm_graph::Space* sp, uint64_t total,
-                   int order, unsigned long long* hist, cudaStream_t s) {
-  if (total == 0) return;
+                   int order, unsigned long long* hist, cudaStream_t s, int chunk = 0,
+                   uint64_t begin = 0, uint64_t end = ~0ull, bool traced = true) {
+  if (end > total) end = total;
+  if (begin >= end) return;
   if (g->block)
-    launch_family_t<F, true>(g, fam, sp, total, order, hist, s);
+    launch_family_t<F, true>(g, fam, sp, begin, end, chunk, order, hist, s, traced);
   else
-    launch_family_t<F, false>(g, fam, sp, total, order, hist, s);
+    launch_family_t<F, false>(g, fam, sp, begin, end, chunk, order, hist, s, traced);
 }
 
 }  // namespace
@@ -411,53 +461,328 @@ bool prefer_bits(const hm_graph* g, const hm_graph::Space& bits, uint64_t candid
   return (double)bits.total * words * 0.35 < (double)candidates;
 }
 
-void prepare_census(hm_graph* g, int order, cudaStream_t s) {
+std::vector<std::pair<hm_graph::Space*, char>> census_spaces(hm_graph* g, int order) {
   if (order == 3) {
-    if (g->bits2)
-      ensure_spaces(g, {{&g->W, 'W'}, {&g->Wb, 'w'}}, s);
-    else
-      ensure_spaces(g, {{&g->W, 'W'}}, s);
-    if (g->bits2) g->useWb = prefer_bits(g, g->Wb, g->W.total, 0.5);
+    if (g->bits2) return {{&g->W, 'W'}, {&g->Wb, 'w'}};
+    return {{&g->W, 'W'}};
+  }
+  if (g->bits2) return {{&g->S, 'S'}, {&g->P, 'P'}, {&g->TX, 'X'}, {&g->Sb, 's'}, {&g->Pb, 'p'}};
+  return {{&g->S, 'S'}, {&g->P, 'P'}, {&g->TX, 'X'}};
+}
+
+void choose_variants(hm_graph* g, int order) {
+  if (!g->bits2) return;
+  if (order == 3) {
+    g->useWb = prefer_bits(g, g->Wb, g->W.total, 0.5);
   } else {
-    HM_CHECK(g->max_d2 < (1 << 21), HM_EUNSUPPORTED,
-             "a node has 2^21 or more pair neighbours; order-4 star space overflows");
-    if (g->bits2)
-      ensure_spaces(g, {{&g->S, 'S'}, {&g->P, 'P'}, {&g->TX, 'X'}, {&g->Sb, 's'}, {&g->Pb, 'p'}},
-                    s);
-    else
-      ensure_spaces(g, {{&g->S, 'S'}, {&g->P, 'P'}, {&g->TX, 'X'}}, s);
-    if (g->bits2) {
-      g->useSb = prefer_bits(g, g->Sb, g->S.total, 0.5);
-      g->usePb = prefer_bits(g, g->Pb, g->P.total, 1.0);
-    }
+    g->useSb = prefer_bits(g, g->Sb, g->S.total, 0.5);
+    g->usePb = prefer_bits(g, g->Pb, g->P.total, 1.0);
   }
 }
 
-void launch_census(const hm_graph* g, int order, unsigned long long* hist, cudaStream_t s) {
-  if (order == 3) {
-    launch_family(g, FamT3{}, nullptr, (uint64_t)g->counts[3], 3, hist, s);
-    if (g->useWb && g->tri3)
-      launch_bits(g, BitsWT<true>{}, g->Wb, 3, hist, s);
-    else if (g->useWb)
-      launch_bits(g, BitsWT<false>{}, g->Wb, 3, hist, s);
-    else
-      launch_family(g, FamW{}, &g->W, g->W.total, 3, hist, s);
-  } else {
-    launch_family(g, FamQ{}, nullptr, (uint64_t)g->counts[4], 4, hist, s);
-    launch_family(g, FamTX{}, &g->TX, g->TX.total, 4, hist, s);
-    if (g->useSb && g->tri3)
-      launch_bits(g, BitsST<true>{}, g->Sb, 4, hist, s);
-    else if (g->useSb)
-      launch_bits(g, BitsST<false>{}, g->Sb, 4, hist, s);
-    else
-      launch_family(g, FamS{}, &g->S, g->S.total, 4, hist, s);
-    if (g->usePb && g->tri3)
-      launch_bits(g, BitsPT<true>{}, g->Pb, 4, hist, s);
-    else if (g->usePb)
-      launch_bits(g, BitsPT<false>{}, g->Pb, 4, hist, s);
-    else
-      launch_family(g, FamP{}, &g->P, g->P.total, 4, hist, s);
+void schedule_census(hm_graph* g, int order, cudaStream_t s);
+
+void prepare_census(hm_graph* g, int order, cudaStream_t s) {
+  if (order == 4)
+    HM_CHECK(g->max_d2 < (1 << 21), HM_EUNSUPPORTED,
+             "a node has 2^21 or more pair neighbours; order-4 star space overflows");
+  ensure_spaces(g, census_spaces(g, order), s);
+  if (!g->tuned[order]) choose_variants(g, order);
+  schedule_census(g, order, s);
+}
+
+namespace {
+
+// One family of the census over the range [b, e) of the chosen variant's index
+// space (bits: the bit-sliced space, else the per-candidate one).
+void launch_one(const hm_graph* g, char fam, bool bits, int chunk, int order,
+                unsigned long long* hist, cudaStream_t s, uint64_t b = 0, uint64_t e = ~0ull,
+                bool traced = true) {
+  switch (fam) {
+    case 'W':
+      if (bits && g->tri3)
+        launch_bits(g, BitsWT<true>{}, g->Wb, order, hist, s, b, e, traced);
+      else if (bits)
+        launch_bits(g, BitsWT<false>{}, g->Wb, order, hist, s, b, e, traced);
+      else
+        launch_family(g, FamW{}, &g->W, g->W.total, order, hist, s, chunk, b, e, traced);
+      break;
+    case 'S':
+      if (bits && g->tri3)
+        launch_bits(g, BitsST<true>{}, g->Sb, order, hist, s, b, e, traced);
+      else if (bits)
+        launch_bits(g, BitsST<false>{}, g->Sb, order, hist, s, b, e, traced);
+      else
+        launch_family(g, FamS{}, &g->S, g->S.total, order, hist, s, chunk, b, e, traced);
+      break;
+    case 'P':
+      if (bits && g->tri3)
+        launch_bits(g, BitsPT<true>{}, g->Pb, order, hist, s, b, e, traced);
+      else if (bits)
+        launch_bits(g, BitsPT<false>{}, g->Pb, order, hist, s, b, e, traced);
+      else
+        launch_family(g, FamP{}, &g->P, g->P.total, order, hist, s, chunk, b, e, traced);
+      break;
+    default:
+      launch_family(g, FamTX{}, &g->TX, g->TX.total, order, hist, s, chunk, b, e, traced);
+      break;
   }
+}
+
+}  // namespace
+
+// HM_CENSUS_CHUNK=c forces c candidates per lane on every per-candidate family
+void launch_census(const hm_graph* g, int order, unsigned long long* hist, cudaStream_t s) {
+  const char* env = std::getenv("HM_CENSUS_CHUNK");
+  const int forced = env ? std::atoi(env) : 0;
+  auto pick = [&](int c) { return forced > 0 ? forced : c; };
+  if (order == 3) {
+    launch_family(g, FamT3{}, nullptr, (uint64_t)g->counts[3], 3, hist, s, pick(0));
+    launch_one(g, 'W', g->useWb, pick(g->chunkW), 3, hist, s);
+  } else {
+    launch_family(g, FamQ{}, nullptr, (uint64_t)g->counts[4], 4, hist, s, pick(0));
+    launch_one(g, 'X', false, pick(g->chunkTX), 4, hist, s);
+    launch_one(g, 'S', g->useSb, pick(g->chunkS), 4, hist, s);
+    launch_one(g, 'P', g->usePb, pick(g->chunkP), 4, hist, s);
+  }
+}
+
+// ------------------------------------------------------------------ autotuner
+// Schedules of the census: for each family with alternatives, the variant
+// (bit-sliced or per-candidate, where bitmaps exist) and the candidates per
+// lane (8, 16 or 32) of the per-candidate kernel, picked by timing the
+// alternatives on the same node sets: 8 evenly spaced slices of the family's
+// anchors, together sized for ~1e7 per-candidate candidates (all anchors
+// when the family is smaller than 2e7). The cost rule's choice is timed
+// first and kept unless another is 5 % faster; when it is the bit-sliced
+// variant, the per-candidate kernel is tried with 32 candidates per lane only. Choices are cached by graph shape
+// (order, nodes, block, row words, exact rows, and the binary orders of
+// magnitude of |E_2|, |E_3|, |E_4| and of each family's size), so graphs of
+// one shape are tuned once. HM_AUTOTUNE=0 keeps the cost rule.
+namespace {
+
+struct FamChoice {
+  bool bits = false;
+  int chunk = 0;
+};
+struct TuneEntry {
+  FamChoice f[4];  // W, S, P, TX
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneEntry> g_tune_cache;
+
+int ilog2(uint64_t x) { return x ? 63 - __builtin_clzll(x) : -1; }
+
+std::string shape_key(const hm_graph* g, int order) {
+  char buf[256];
+  std::snprintf(buf, sizeof buf, "o%d n%d b%d bw%d t%d m%d,%d,%d s%d,%d,%d,%d", order, g->n,
+                g->block, g->bwords, g->tri3 ? 1 : 0, ilog2((uint64_t)g->counts[2]),
+                g->kmax >= 3 ? ilog2((uint64_t)g->counts[3]) : -1,
+                g->kmax >= 4 ? ilog2((uint64_t)g->counts[4]) : -1, ilog2(g->W.total),
+                ilog2(g->S.total), ilog2(g->P.total), ilog2(g->TX.total));
+  return buf;
+}
+
+// off with HM_AUTOTUNE=0, and while a variant or chunk is forced
+bool autotune_on() {
+  const char* env = std::getenv("HM_AUTOTUNE");
+  if (env && env[0] == '0') return false;
+  return !std::getenv("HM_DENSE_FAMILIES") && !std::getenv("HM_CENSUS_CHUNK");
+}
+
+__global__ void k_gather_u64(const uint64_t* const* __restrict__ src,
+                             const int64_t* __restrict__ idx, int n, uint64_t* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = src[i][idx[i]];
+}
+
+// Anchor slices [lo, hi) of one family and their index ranges in the
+// per-candidate space (pc) and the bit-sliced space (bt).
+struct Slices {
+  int k = 0;
+  int64_t lo[8] = {}, hi[8] = {};
+  uint64_t pc_b[8] = {}, pc_e[8] = {}, bt_b[8] = {}, bt_e[8] = {};
+};
+
+void plan_slices(const hm_graph::Space& pc, Slices& sl) {
+  const int64_t A = pc.anchors;
+  sl.k = 0;
+  if (A <= 0 || pc.total == 0) return;
+  double f = 1e7 / (double)pc.total;
+  if (f < 1.0 / 1024) f = 1.0 / 1024;
+  if (f >= 0.5) {
+    sl.k = 1;
+    sl.lo[0] = 0;
+    sl.hi[0] = A;
+    return;
+  }
+  sl.k = 8;
+  int64_t w = (int64_t)((double)A * f / 8);
+  if (w < 1) w = 1;
+  if (w > A) w = A;
+  for (int i = 0; i < 8; ++i) {
+    int64_t lo = (int64_t)((2 * i + 1) * (double)A / 16) - w / 2;
+    if (lo < 0) lo = 0;
+    if (lo + w > A) lo = A - w;
+    sl.lo[i] = lo;
+    sl.hi[i] = lo + w;
+  }
+}
+
+struct Tuned {
+  char id;
+  hm_graph::Space* pc;
+  hm_graph::Space* bt;
+  Slices sl;
+};
+
+void tune_census(hm_graph* g, int order, cudaStream_t s) {
+  const ClassTables& T = class_tables(order);
+  DBuf<unsigned long long> scratch((size_t)T.ncls * num_graphs(g), s);
+  std::vector<Tuned> fams;
+  if (order == 3) {
+    fams.push_back({'W', &g->W, g->bits2 ? &g->Wb : nullptr, {}});
+  } else {
+    fams.push_back({'S', &g->S, g->bits2 ? &g->Sb : nullptr, {}});
+    fams.push_back({'P', &g->P, g->bits2 ? &g->Pb : nullptr, {}});
+    fams.push_back({'X', &g->TX, nullptr, {}});
+  }
+  // slice boundaries in both spaces (bt = pc where there is no bit-sliced
+  // variant), read back in one copy
+  std::vector<const uint64_t*> src;
+  std::vector<int64_t> idx;
+  for (auto& F : fams) {
+    plan_slices(*F.pc, F.sl);
+    const uint64_t* bws = (F.bt && F.bt->ready && F.bt->ws) ? F.bt->ws : F.pc->ws;
+    for (int i = 0; i < F.sl.k; ++i) {
+      src.push_back(F.pc->ws);
+      idx.push_back(F.sl.lo[i]);
+      src.push_back(F.pc->ws);
+      idx.push_back(F.sl.hi[i]);
+      src.push_back(bws);
+      idx.push_back(F.sl.lo[i]);
+      src.push_back(bws);
+      idx.push_back(F.sl.hi[i]);
+    }
+  }
+  if (!idx.empty()) {
+    const int nq = (int)idx.size();
+    DBuf<const uint64_t*> dsrc(nq, s);
+    DBuf<int64_t> didx(nq, s);
+    DBuf<uint64_t> dout(nq, s);
+    HM_CUDA(cudaMemcpyAsync(dsrc.p, src.data(), nq * sizeof(void*), cudaMemcpyHostToDevice, s));
+    HM_CUDA(cudaMemcpyAsync(didx.p, idx.data(), nq * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    k_gather_u64<<<(nq + 127) / 128, 128, 0, s>>>(dsrc.p, didx.p, nq, dout.p);
+    HM_KCHECK();
+    std::vector<uint64_t> h(nq);
+    HM_CUDA(cudaMemcpyAsync(h.data(), dout.p, nq * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaStreamSynchronize(s));
+    size_t q = 0;
+    for (auto& F : fams)
+      for (int i = 0; i < F.sl.k; ++i) {
+        F.sl.pc_b[i] = h[q++];
+        F.sl.pc_e[i] = h[q++];
+        F.sl.bt_b[i] = h[q++];
+        F.sl.bt_e[i] = h[q++];
+      }
+  }
+  TuneEntry out;
+  out.f[0] = {g->useWb, g->chunkW};
+  out.f[1] = {g->useSb, g->chunkS};
+  out.f[2] = {g->usePb, g->chunkP};
+  out.f[3] = {false, g->chunkTX};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  HM_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    HM_CHECK(false, HM_ECUDA, "cudaEventCreate failed");
+  }
+  try {
+    for (auto& F : fams) {
+      if (F.sl.k == 0) continue;
+      // the cost rule's choice first: another one must be 5 % faster to win
+      std::vector<FamChoice> cands;
+      const int slot0 = F.id == 'W' ? 0 : F.id == 'S' ? 1 : F.id == 'P' ? 2 : 3;
+      const bool rule_bits = out.f[slot0].bits && F.bt && F.bt->ready && F.bt->total;
+      cands.push_back({rule_bits, rule_bits ? 0 : 32});
+      if (rule_bits) {
+        cands.push_back({false, 32});
+      } else {
+        cands.push_back({false, 8});
+        cands.push_back({false, 16});
+        if (F.bt && F.bt->ready && F.bt->total) cands.push_back({true, 0});
+      }
+      auto run = [&](const FamChoice& c, bool warm) {
+        for (int i = 0; i < F.sl.k; ++i) {
+          const uint64_t b = c.bits ? F.sl.bt_b[i] : F.sl.pc_b[i];
+          uint64_t e = c.bits ? F.sl.bt_e[i] : F.sl.pc_e[i];
+          if (warm && e > b + 4096) e = b + 4096;  // a kernel's first launch loads it
+          launch_one(g, F.id, c.bits, c.chunk, order, scratch.p, s, b, e, false);
+          if (warm) break;
+        }
+      };
+      float best = 0.f;
+      FamChoice pick = cands[0];
+      for (size_t ci = 0; ci < cands.size(); ++ci) {
+        run(cands[ci], true);
+        HM_CUDA(cudaEventRecord(e0, s));
+        run(cands[ci], false);
+        HM_CUDA(cudaEventRecord(e1, s));
+        HM_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        HM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ci == 0 || ms < 0.95f * best) {
+          best = ms;
+          pick = cands[ci];
+        }
+      }
+      const int slot = F.id == 'W' ? 0 : F.id == 'S' ? 1 : F.id == 'P' ? 2 : 3;
+      out.f[slot] = pick;
+    }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[shape_key(g, order)] = out;
+  }
+  g->useWb = out.f[0].bits;
+  g->chunkW = out.f[0].chunk;
+  g->useSb = out.f[1].bits;
+  g->chunkS = out.f[1].chunk;
+  g->usePb = out.f[2].bits;
+  g->chunkP = out.f[2].chunk;
+  g->chunkTX = out.f[3].chunk;
+}
+
+}  // namespace
+
+// Schedules of one order: from the cache, else by tuning (one synchronisation
+// and a few slices of each family), unless HM_AUTOTUNE=0 (the cost rule).
+void schedule_census(hm_graph* g, int order, cudaStream_t s) {
+  if (g->tuned[order] || !autotune_on()) return;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(shape_key(g, order));
+    if (it != g_tune_cache.end()) {
+      const TuneEntry& t = it->second;
+      g->useWb = t.f[0].bits && g->bits2;
+      g->chunkW = t.f[0].chunk;
+      g->useSb = t.f[1].bits && g->bits2;
+      g->chunkS = t.f[1].chunk;
+      g->usePb = t.f[2].bits && g->bits2;
+      g->chunkP = t.f[2].chunk;
+      g->chunkTX = t.f[3].chunk;
+      g->tuned[order] = true;
+      return;
+    }
+  }
+  tune_census(g, order, s);
+  g->tuned[order] = true;
 }
 
 }  // namespace hm

@@ -151,6 +151,24 @@ __global__ void __launch_bounds__(256)
 
 __device__ __forceinline__ float lg(float x) { return log1pf(x); }
 
+// Number of 3-hyperedges containing both x and y: the shorter incidence list
+// of the two, each triple checked for the other node.
+__device__ int64_t common_triples(const DevGraph& g, int32_t x, int32_t y) {
+  int64_t a0 = g.off3[x], a1 = g.off3[x + 1], b0 = g.off3[y], b1 = g.off3[y + 1];
+  int32_t other = y;
+  if (b1 - b0 < a1 - a0) {
+    a0 = b0;
+    a1 = b1;
+    other = x;
+  }
+  int64_t c = 0;
+  for (int64_t i = a0; i < a1; ++i) {
+    const int4 t = g.e3[g.inc3[i]];
+    c += (t.x == other || t.y == other || t.z == other) ? 1 : 0;
+  }
+  return c;
+}
+
 __global__ void k_features(const DevGraph g, int order, int64_t rows, float* __restrict__ out) {
   const int64_t m2 = g.m2, m3 = g.m3;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
@@ -187,8 +205,21 @@ __global__ void k_features(const DevGraph g, int order, int64_t rows, float* __r
       tsum += t;
     }
     int npairs = 0;
+    int64_t shared = 0;  // sum over member pairs of the 3-hyperedges through both
     for (int i = 0; i < s; ++i)
-      for (int j = i + 1; j < s; ++j) npairs += has_pair(g, x[i], x[j]) ? 1 : 0;
+      for (int j = i + 1; j < s; ++j) {
+        npairs += has_pair(g, x[i], x[j]) ? 1 : 0;
+        if (m3) shared += common_triples(g, x[i], x[j]);
+      }
+    // 3-hyperedges inside a 4-hyperedge; then the 3-hyperedges other than e
+    // sharing at least two nodes with e (a sub-triple of a quad is met at
+    // three of its pairs, e itself at its three pairs)
+    int nsub = 0;
+    if (s == 4 && m3) {
+      nsub = (has_triple(g, x[0], x[1], x[2]) ? 1 : 0) + (has_triple(g, x[0], x[1], x[3]) ? 1 : 0) +
+             (has_triple(g, x[0], x[2], x[3]) ? 1 : 0) + (has_triple(g, x[1], x[2], x[3]) ? 1 : 0);
+    }
+    const int64_t overlap = s == 2 ? shared : s == 3 ? shared - 3 : shared - 2 * nsub;
     double work = 1.0;
     if (s == 2 && order > 2) {
       const double l = (double)(dsum - 2.f);
@@ -209,7 +240,9 @@ __global__ void k_features(const DevGraph g, int order, int64_t rows, float* __r
     f[9] = lg((float)work);
     f[10] = lg(dsum);
     f[11] = lg(tsum);
-    f[12] = f[13] = f[14] = f[15] = 0.f;
+    f[12] = lg((float)overlap);
+    f[13] = lg((float)nsub);
+    f[14] = f[15] = 0.f;
   }
 }
 

@@ -439,6 +439,9 @@ struct hm_graph {
   // neighbour[s]) and the last node runs over bitmap words
   Space Wb, Sb, Pb;
   bool useWb = false, useSb = false, usePb = false;
+  // candidates per lane of the per-candidate families (0 = fill the GPU)
+  int chunkW = 0, chunkS = 0, chunkP = 0, chunkTX = 0;
+  bool tuned[5] = {false, false, false, false, false};  // by order
   std::vector<void*> owned;  // everything above, for hm_free
 
   hm::DevGraph view() const {
@@ -471,3 +474,18 @@ struct hm_graph {
     return g;
   }
 };
+
+namespace hm {
+// Work spaces enqueued without a synchronisation (hm_build prepares those of
+// its max_order this way, before its own final synchronisation).
+struct PendingSpaces {
+  std::vector<std::pair<hm_graph::Space*, char>> need;
+  std::vector<uint64_t*> made;
+  uint64_t h[8] = {};
+};
+std::vector<std::pair<hm_graph::Space*, char>> census_spaces(hm_graph* g, int order);
+void spaces_enqueue(hm_graph* g, const std::vector<std::pair<hm_graph::Space*, char>>& todo,
+                    cudaStream_t s, PendingSpaces& P);
+void spaces_finish(PendingSpaces& P);
+void choose_variants(hm_graph* g, int order);
+}  // namespace hm

@@ -21,14 +21,25 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-MODES = ["hash", "bitmap", "sliced", "sliced_filter"]
+MODES = ["hash", "bitmap", "sliced", "sliced_filter", "tuned", "chunk8", "chunk32"]
 
 
 def _set_mode(monkeypatch, mode):
     """hash: pair probes in the hash set; bitmap: pair probes in the dense
     bitmap, one candidate at a time; sliced: bit-sliced W/S/P families with
     exact 3-hyperedge rows; sliced_filter: bit-sliced with the co-occurrence
-    filter and exact probes of the risky candidates."""
+    filter and exact probes of the risky candidates; tuned: the library's
+    defaults, schedules picked by the autotuner; chunk8 / chunk32: hash
+    probes with 8 / 32 candidates per lane on every per-candidate family."""
+    for var in ("HM_PAIR_BITMAP", "HM_DENSE_FAMILIES", "HM_TRIPLE_ROWS", "HM_AUTOTUNE",
+                "HM_CENSUS_CHUNK"):
+        monkeypatch.delenv(var, raising=False)
+    if mode == "tuned":
+        return
+    if mode.startswith("chunk"):
+        monkeypatch.setenv("HM_PAIR_BITMAP", "0")
+        monkeypatch.setenv("HM_CENSUS_CHUNK", mode[5:])
+        return
     monkeypatch.setenv("HM_PAIR_BITMAP", "0" if mode == "hash" else "1")
     monkeypatch.setenv("HM_DENSE_FAMILIES", "1" if mode.startswith("sliced") else "0")
     monkeypatch.setenv("HM_TRIPLE_ROWS", "0" if mode == "sliced_filter" else "1")

@@ -81,7 +81,28 @@ def test_features_by_hand():
     assert np.allclose(r[:12], [1, 0.75, np.log1p(2), np.log1p(7 / 3), np.log1p(3), np.log1p(1),
                                 np.log1p(1), np.log1p(1), np.log1p(3), np.log1p(10),
                                 np.log1p(7), np.log1p(3)])
-    assert (f[:, 12:] == 0).all() and d2[3] == 1
+    # 3-hyperedges sharing >= 2 nodes / inside: the pair (0,1) meets triple 012; the
+    # triple has none besides itself; the quad 0123 holds 012 (one sub-triple)
+    assert np.isclose(f[0, 12], np.log1p(1)) and f[0, 13] == 0
+    assert f[4, 12] == 0 and f[4, 13] == 0
+    assert np.isclose(f[5, 12], np.log1p(1)) and np.isclose(f[5, 13], np.log1p(1))
+    assert (f[:, 14:] == 0).all() and d2[3] == 1
+
+
+def test_overlap_features_brute_force():
+    """Features 12-13 against counting over every pair of hyperedges."""
+    for seed in range(6):
+        h = synth.random_tiny(9, 40, max_size=4, seed=seed)
+        g = oracle.Graph.from_hypergraph(h, 4)
+        f = F.features(g, 4)
+        edges = [tuple(e) for s in (2, 3, 4) for e in g.edges(s).tolist()]
+        triples = [set(e) for e in edges if len(e) == 3]
+        for r, e in enumerate(edges):
+            se = set(e)
+            share = sum(1 for t in triples if t != se and len(t & se) >= 2)
+            inside = sum(1 for t in triples if t < se)
+            assert np.isclose(f[r, 12], np.log1p(share)), (seed, e)
+            assert np.isclose(f[r, 13], np.log1p(inside)), (seed, e)
 
 
 def test_targets_formula():
