@@ -46,6 +46,7 @@ ROOFLINE = {
     "census_Pb": ("item", 480.6, 5_733_000),
     "census_TX": ("candidate", 332.9, 659_000),
     "census_Q": ("candidate", 522.3, 301_000),
+    "census_TXb": ("item", None, None),
     "census_Wb": ("item", None, None),
     "census_S": ("candidate", None, None),
     "census_P": ("candidate", None, None),

@@ -156,15 +156,17 @@ hm_status hm_count_sampled(hm_graph* g, int order, const uint64_t* samples_per_s
 
 /*
  * Sizes of the index spaces hm_count_exact walks, written to host
- * totals[8] (d2 = pair degree, t3 = number of 3-hyperedges through a node):
+ * totals[10] (d2 = pair degree, t3 = number of 3-hyperedges through a node):
  *   order 3: {T3 = |E_3|, W = sum_v C(d2(v), 2), Wb = sum_{v: d2>=2} d2(v),
  *             1 if the bit-sliced W variant is used}
  *   order 4: {Q = |E_4|, TX = sum_{e in E_3} sum_{x in e} (d2(x) + t3(x)),
  *             S = sum_v C(d2(v), 3), P = sum_{(u,v) in E_2} (d2(u)-1)(d2(v)-1),
  *             Sb = sum_v C(d2(v), 2), Pb = sum_{(u<v), d2(v)>1} (d2(u)-1),
- *             1 if bit-sliced S is used, 1 if bit-sliced P is used}
- * W, S, P count candidate node sets; Wb, Sb, Pb count the items of the
- * bit-sliced variants (each item scans the bitmap words of one row). The
+ *             1 if bit-sliced S is used, 1 if bit-sliced P is used,
+ *             TXb = |E_3| * (4-word groups per bitmap row), 1 if bit-sliced
+ *             TX is used}
+ * W, S, P, TX count candidate node sets; Wb, Sb, Pb, TXb count the items of
+ * the bit-sliced variants (each item scans bitmap words of one row). The
  * bit-sliced sizes are 0 when the graph has no dense bitmaps. Synchronous.
  */
 hm_status hm_work_totals(hm_graph* g, int order, uint64_t* totals, void* stream);

@@ -253,12 +253,12 @@ def trace_read(max_entries: int = 4096):
 
 FAMILIES = {3: ("census_T3", "census_W", "census_Wb", "uses_Wb"),
             4: ("census_Q", "census_TX", "census_S", "census_P", "census_Sb", "census_Pb",
-                "uses_Sb", "uses_Pb")}
+                "uses_Sb", "uses_Pb", "census_TXb", "uses_TXb")}
 
 
 def work_totals(g: Graph, order: int, stream=None) -> dict:
     """Index-space sizes of the exact census {kernel name: items} (see hm.h)."""
-    arr = (ctypes.c_uint64 * 8)()
+    arr = (ctypes.c_uint64 * 10)()
     _check(load().hm_work_totals(g._h, order, arr, _stream(stream)))
     return {name: int(arr[i]) for i, name in enumerate(FAMILIES[order])}
 

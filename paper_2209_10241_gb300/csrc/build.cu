@@ -371,23 +371,25 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   g->bits = b;
 
   TraceSpan span_norm("ingest_normalize", s);
-  DBuf<unsigned long long> cnt(8, s), cnt2(8, s);
-  DBuf<int> err(1, s);
-  HM_CUDA(cudaMemsetAsync(cnt.p, 0, 8 * sizeof(unsigned long long), s));
-  HM_CUDA(cudaMemsetAsync(cnt2.p, 0, 8 * sizeof(unsigned long long), s));
-  HM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+  // counters of the two normalisation passes and the error word, zeroed at once
+  DBuf<unsigned long long> counters(17, s);
+  HM_CUDA(cudaMemsetAsync(counters.p, 0, 17 * sizeof(unsigned long long), s));
+  unsigned long long* cnt = counters.p;
+  unsigned long long* cnt2 = counters.p + 8;
+  int* err_p = reinterpret_cast<int*>(counters.p + 16);
   if (m > 0) {
-    k_normalize<false><<<grid1d(m), T256, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt.p,
-                                                  err.p, nullptr, nullptr, nullptr, nullptr,
+    k_normalize<false><<<grid1d(m), T256, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt,
+                                                  err_p, nullptr, nullptr, nullptr, nullptr,
                                                   nullptr);
     HM_KCHECK();
   }
   span_norm.end();
-  unsigned long long hc[8];
-  int herr = 0;
-  HM_CUDA(cudaMemcpyAsync(hc, cnt.p, sizeof hc, cudaMemcpyDeviceToHost, s));
-  HM_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof herr, cudaMemcpyDeviceToHost, s));
+  uint64_t* pin = pinned_words();
+  HM_CUDA(cudaMemcpyAsync(pin, counters.p, 17 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   HM_CUDA(cudaStreamSynchronize(s));
+  unsigned long long hc[8];
+  for (int i = 0; i < 8; ++i) hc[i] = pin[i];
+  int herr = (int)(uint32_t)pin[16];
   HM_CHECK(!(herr & ERR_OFFSETS), HM_EINVAL, "offsets are negative or not non-decreasing");
   HM_CHECK(!(herr & ERR_RANGE), HM_EINVAL, "a member lies outside [0, num_nodes)");
   g->counts[0] = n;
@@ -395,19 +397,28 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   g->counts[kmax + 1] = (int64_t)hc[kmax + 1];
 
   TraceSpan span_sort("ingest_sort_unique", s);
-  DBuf<uint64_t> c2(hc[2], s), c3hi(kmax >= 3 ? hc[3] : 0, s), c3lo(kmax >= 3 ? hc[3] : 0, s),
-      c4hi(kmax >= 4 ? hc[4] : 0, s), c4lo(kmax >= 4 ? hc[4] : 0, s);
+  const size_t h2n = hc[2], h3n = kmax >= 3 ? hc[3] : 0, h4n = kmax >= 4 ? hc[4] : 0;
+  DBuf<uint64_t> keys(h2n + 2 * h3n + 2 * h4n, s);
+  uint64_t* c2 = keys.p;
+  uint64_t* c3hi = c2 + h2n;
+  uint64_t* c3lo = c3hi + h3n;
+  uint64_t* c4hi = c3lo + h3n;
+  uint64_t* c4lo = c4hi + h4n;
   if (m > 0) {
-    k_normalize<true><<<grid1d(m), T256, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt2.p,
-                                                 err.p, c2.p, c3hi.p, c3lo.p, c4hi.p, c4lo.p);
+    k_normalize<true><<<grid1d(m), T256, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt2,
+                                                 err_p, c2, c3hi, c3lo, c4hi, c4lo);
     HM_KCHECK();
   }
   // sort + unique per size, all sizes in one batch: the ascending order of
   // E_s, written straight into the graph's arrays (sized for the keys before
   // dedup) in their final layout (one synchronisation)
-  g->e2 = keep(g, dalloc<uint64_t>(hc[2], s));
-  if (kmax >= 3 && hc[3]) g->e3 = keep(g, dalloc<int4>(hc[3], s));
-  if (kmax >= 4 && hc[4]) g->e4 = keep(g, dalloc<int4>(hc[4], s));
+  {
+    const size_t b2 = (h2n * 8 + 255) & ~(size_t)255, b3 = (h3n * 16 + 255) & ~(size_t)255;
+    unsigned char* eb = keep(g, dalloc<unsigned char>(b2 + b3 + h4n * 16 + 16, s));
+    g->e2 = reinterpret_cast<uint64_t*>(eb);
+    if (h3n) g->e3 = reinterpret_cast<int4*>(eb + b2);
+    if (h4n) g->e4 = reinterpret_cast<int4*>(eb + b2 + b3);
+  }
   DBuf<uint32_t> kept(3, s);
   {
     SortJob jobs[3];
@@ -434,24 +445,21 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
       J.d_kept = kept.p + (size - 2);
       ++nj;
     };
-    add(c2.p, nullptr, (int64_t)hc[2], 2, SortJob::PAIR, g->e2);
-    if (kmax >= 3) add(c3lo.p, c3hi.p, (int64_t)hc[3], 3, SortJob::TRIPLE, g->e3);
-    if (kmax >= 4) add(c4lo.p, c4hi.p, (int64_t)hc[4], 4, SortJob::QUAD, g->e4);
+    add(c2, nullptr, (int64_t)h2n, 2, SortJob::PAIR, g->e2);
+    if (kmax >= 3) add(c3lo, c3hi, (int64_t)h3n, 3, SortJob::TRIPLE, g->e3);
+    if (kmax >= 4) add(c4lo, c4hi, (int64_t)h4n, 4, SortJob::QUAD, g->e4);
     sort_batch(jobs, nj, s);
   }
   span_sort.end();
-  uint32_t hk[3] = {0, 0, 0};
+  uint32_t* hk = reinterpret_cast<uint32_t*>(pin + 32);
+  hk[0] = hk[1] = hk[2] = 0;
   HM_CUDA(cudaMemcpyAsync(hk, kept.p, nj_kept_bytes(kmax), cudaMemcpyDeviceToHost, s));
   HM_CUDA(cudaStreamSynchronize(s));
   const int64_t m2 = hk[0], m3 = kmax >= 3 ? hk[1] : 0, m4 = kmax >= 4 ? hk[2] : 0;
   g->counts[2] = m2;
   if (kmax >= 3) g->counts[3] = m3;
   if (kmax >= 4) g->counts[4] = m4;
-  c2.release();
-  c3hi.release();
-  c3lo.release();
-  c4hi.release();
-  c4lo.release();
+  keys.release();
 
   TraceSpan span_tables("ingest_structures", s);
   // Outputs and temporaries on `s`; then four independent chains run
@@ -459,58 +467,87 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   // incidence CSR (f[1]), dense bitmaps and triple rows (f[2]).
   const uint64_t cap2 = table_capacity(m2), cap3 = m3 ? table_capacity(m3) : 0,
                  cap4 = m4 ? table_capacity(m4) : 0;
-  g->h2 = keep(g, dalloc<uint64_t>(cap2, s));
   g->h2_mask = cap2 - 1;
-  HM_CUDA(cudaMemsetAsync(g->h2, 0xFF, cap2 * sizeof(uint64_t), s));
-  if (m3) {
-    g->h3 = keep(g, dalloc<int4>(cap3, s));
-    g->h3_mask = cap3 - 1;
-    HM_CUDA(cudaMemsetAsync(g->h3, 0xFF, cap3 * sizeof(int4), s));
-  }
-  if (m4) {
-    g->h4 = keep(g, dalloc<int4>(cap4, s));
-    g->h4_mask = cap4 - 1;
-    HM_CUDA(cudaMemsetAsync(g->h4, 0xFF, cap4 * sizeof(int4), s));
-  }
-  g->off2 = keep(g, dalloc<int64_t>((size_t)n + 1, s));
-  g->adj2 = keep(g, dalloc<int32_t>(2 * m2, s));
-  if (m2) g->pairpos = keep(g, dalloc<int2>(m2, s));
-  g->off3 = keep(g, dalloc<int64_t>((size_t)n + 1, s));
-  if (m3) g->inc3 = keep(g, dalloc<int32_t>(3 * m3, s));
-  else HM_CUDA(cudaMemsetAsync(g->off3, 0, ((size_t)n + 1) * sizeof(int64_t), s));
+  g->h3_mask = cap3 ? cap3 - 1 : 0;
+  g->h4_mask = cap4 ? cap4 - 1 : 0;
   const bool bitmaps = use_bitmap(n, block ? block : n, block != 0);
   size_t words = 0, tw = 0;
   if (bitmaps) {
     // rows padded to a multiple of four words: 16-byte aligned row loads
     g->bwords = (((block ? block : n) + 127) / 128) * 4;
     words = (size_t)n * g->bwords;
-    g->bits2 = keep(g, dalloc<uint32_t>(words, s));
-    g->bits3 = keep(g, dalloc<uint32_t>(words, s));
-    g->bits4 = keep(g, dalloc<uint32_t>(words, s));
-    HM_CUDA(cudaMemsetAsync(g->bits2, 0, words * sizeof(uint32_t), s));
-    HM_CUDA(cudaMemsetAsync(g->bits3, 0, words * sizeof(uint32_t), s));
-    HM_CUDA(cudaMemsetAsync(g->bits4, 0, words * sizeof(uint32_t), s));
-    if (use_tri3(n, block)) {
-      tw = (size_t)n * n * g->bwords;
-      g->tri3 = keep(g, dalloc<uint32_t>(tw, s));
-      HM_CUDA(cudaMemsetAsync(g->tri3, 0, tw * sizeof(uint32_t), s));
-    }
+    if (use_tri3(n, block)) tw = (size_t)n * n * g->bwords;
   }
-  DBuf<uint64_t> pkeys(bitmaps ? 0 : 2 * m2, s), tkeys(3 * m3, s), pdeg(bitmaps ? n : 0, s);
+  // One allocation for the graph's structures, laid out so that two memsets
+  // initialise them: the hash tables (empty = all ones), then the regions that
+  // start at zero (bitmaps, triple rows, triple offsets), then the rest.
+  {
+    auto al = [](size_t bytes) { return (bytes + 255) & ~(size_t)255; };
+    size_t o = 0;
+    const size_t o_h2 = o;
+    o += al(cap2 * 8);
+    const size_t o_h3 = o;
+    o += al(cap3 * 16);
+    const size_t o_h4 = o;
+    o += al(cap4 * 16);
+    const size_t ff_end = o;
+    const size_t o_b2 = o;
+    o += al(words * 4);
+    const size_t o_b3 = o;
+    o += al(words * 4);
+    const size_t o_b4 = o;
+    o += al(words * 4);
+    const size_t o_t3 = o;
+    o += al(tw * 4);
+    const size_t o_off3 = o;
+    o += al(((size_t)n + 1) * 8);
+    const size_t zero_end = o;
+    const size_t o_off2 = o;
+    o += al(((size_t)n + 1) * 8);
+    const size_t o_adj2 = o;
+    o += al((size_t)2 * m2 * 4);
+    const size_t o_pp = o;
+    o += al((size_t)m2 * 8);
+    const size_t o_inc3 = o;
+    o += al((size_t)3 * m3 * 4);
+    unsigned char* arena = keep(g, dalloc<unsigned char>(o, s));
+    g->h2 = reinterpret_cast<uint64_t*>(arena + o_h2);
+    if (m3) g->h3 = reinterpret_cast<int4*>(arena + o_h3);
+    if (m4) g->h4 = reinterpret_cast<int4*>(arena + o_h4);
+    if (bitmaps) {
+      g->bits2 = reinterpret_cast<uint32_t*>(arena + o_b2);
+      g->bits3 = reinterpret_cast<uint32_t*>(arena + o_b3);
+      g->bits4 = reinterpret_cast<uint32_t*>(arena + o_b4);
+      if (tw) g->tri3 = reinterpret_cast<uint32_t*>(arena + o_t3);
+    }
+    g->off3 = reinterpret_cast<int64_t*>(arena + o_off3);
+    g->off2 = reinterpret_cast<int64_t*>(arena + o_off2);
+    g->adj2 = reinterpret_cast<int32_t*>(arena + o_adj2);
+    if (m2) g->pairpos = reinterpret_cast<int2*>(arena + o_pp);
+    if (m3) g->inc3 = reinterpret_cast<int32_t*>(arena + o_inc3);
+    HM_CUDA(cudaMemsetAsync(arena, 0xFF, ff_end, s));
+    HM_CUDA(cudaMemsetAsync(arena + ff_end, 0, zero_end - ff_end, s));
+  }
+  // temporaries of the chains: directed pair keys, triple incidence keys, degrees
+  const size_t np_keys = bitmaps ? 0 : 2 * m2, nt_keys = 3 * m3, n_deg = bitmaps ? n : 0;
+  DBuf<uint64_t> chain_tmp(np_keys + nt_keys + n_deg, s);
+  uint64_t* pkeys = chain_tmp.p;
+  uint64_t* tkeys = chain_tmp.p + np_keys;
+  uint64_t* pdeg = chain_tmp.p + np_keys + nt_keys;
   const int tb = bits_for(m3);
   {
     Fork f(s);
     // hash sets (load <= 0.5)
     if (m2) {
-      k_insert2<<<grid1d(m2), T256, 0, s>>>(g->e2, m2, g->h2, g->h2_mask, err.p);
+      k_insert2<<<grid1d(m2), T256, 0, s>>>(g->e2, m2, g->h2, g->h2_mask, err_p);
       HM_KCHECK();
     }
     if (m3) {
-      k_insert4<<<grid1d(m3), T256, 0, s>>>(g->e3, m3, g->h3, g->h3_mask, err.p);
+      k_insert4<<<grid1d(m3), T256, 0, s>>>(g->e3, m3, g->h3, g->h3_mask, err_p);
       HM_KCHECK();
     }
     if (m4) {
-      k_insert4<<<grid1d(m4), T256, 0, s>>>(g->e4, m4, g->h4, g->h4_mask, err.p);
+      k_insert4<<<grid1d(m4), T256, 0, s>>>(g->e4, m4, g->h4, g->h4_mask, err_p);
       HM_KCHECK();
     }
     // CSR of pair neighbours, sorted, and the position of each pair in it:
@@ -523,36 +560,36 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
         HM_KCHECK();
       }
       k_bits_degree<<<grid1d((int64_t)n * 32), T256, 0, f[0]>>>(g->bits2, n, g->bwords,
-                                                                 pdeg.p);
+                                                                 pdeg);
       HM_KCHECK();
-      scan_exclusive_u64(pdeg.p, reinterpret_cast<uint64_t*>(g->off2), n, f[0]);
+      scan_exclusive_u64(pdeg, reinterpret_cast<uint64_t*>(g->off2), n, f[0]);
       k_bits_adjacency<<<grid1d((int64_t)n * 32), T256, 0, f[0]>>>(
           g->bits2, n, g->bwords, gv.block, gv.block_inv, g->off2, g->adj2);
       HM_KCHECK();
     } else if (m2) {
-      k_directed_pairs<<<grid1d(m2), T256, 0, f[0]>>>(g->e2, m2, b, pkeys.p);
+      k_directed_pairs<<<grid1d(m2), T256, 0, f[0]>>>(g->e2, m2, b, pkeys);
       HM_KCHECK();
       // Stable by the first node only: for node x the keys (x, u) of pairs
       // {u < x} precede the keys (x, v) of pairs {x < v} in E_2 order, and
       // each group is ascending, so every row comes out sorted.
-      radix_sort_u64(pkeys.p, nullptr, 2 * m2, b, f[0], b);
-      k_low_bits<<<grid1d(2 * m2), T256, 0, f[0]>>>(pkeys.p, 2 * m2, b, g->adj2);
+      radix_sort_u64(pkeys, nullptr, 2 * m2, b, f[0], b);
+      k_low_bits<<<grid1d(2 * m2), T256, 0, f[0]>>>(pkeys, 2 * m2, b, g->adj2);
       HM_KCHECK();
     }
-    if (!bitmaps) csr_offsets(pkeys.p, 2 * m2, b, n, g->off2, f[0]);
+    if (!bitmaps) csr_offsets(pkeys, 2 * m2, b, n, g->off2, f[0]);
     if (m2) {
       k_pairpos<<<grid1d(m2), T256, 0, f[0]>>>(g->e2, m2, g->off2, g->adj2, g->pairpos);
       HM_KCHECK();
     }
     // CSR of triple incidence, ascending triple index
     if (m3) {
-      k_triple_incidence<<<grid1d(m3), T256, 0, f[1]>>>(g->e3, m3, tb, tkeys.p);
+      k_triple_incidence<<<grid1d(m3), T256, 0, f[1]>>>(g->e3, m3, tb, tkeys);
       HM_KCHECK();
       // stable by node only: keys are generated in ascending triple index
-      radix_sort_u64(tkeys.p, nullptr, 3 * m3, b, f[1], tb);
-      k_low_bits<<<grid1d(3 * m3), T256, 0, f[1]>>>(tkeys.p, 3 * m3, tb, g->inc3);
+      radix_sort_u64(tkeys, nullptr, 3 * m3, b, f[1], tb);
+      k_low_bits<<<grid1d(3 * m3), T256, 0, f[1]>>>(tkeys, 3 * m3, tb, g->inc3);
       HM_KCHECK();
-      csr_offsets(tkeys.p, 3 * m3, tb, n, g->off3, f[1]);
+      csr_offsets(tkeys, 3 * m3, tb, n, g->off3, f[1]);
     }
     // dense bitmaps
     if (bitmaps) {
@@ -583,19 +620,22 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   k_max_degree<<<grid1d(n), T256, 0, s>>>(g->off2, n, mx.p);
   HM_KCHECK();
   spaces_enqueue(g, census_spaces(g, kmax), s, pend);
-  unsigned timeouts = 0;
+  unsigned* tail = reinterpret_cast<unsigned*>(pin + 40);  // max degree, error word
+  unsigned* timeouts = reinterpret_cast<unsigned*>(pin + 80);
   try {
-    HM_CUDA(cudaMemcpyAsync(&g->max_d2, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    HM_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof herr, cudaMemcpyDeviceToHost, s));
-    wait_timeouts_async(&timeouts, s);
+    HM_CUDA(cudaMemcpyAsync(tail, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaMemcpyAsync(tail + 1, err_p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    wait_timeouts_async(timeouts, s);
     HM_CUDA(cudaStreamSynchronize(s));
   } catch (...) {
     for (uint64_t* p : pend.made) cudaFreeAsync(p, s);
     throw;
   }
+  g->max_d2 = (int)tail[0];
+  herr = (int)tail[1];
   spaces_finish(pend);
   choose_variants(g, kmax);
-  wait_timeouts_check(timeouts, s);
+  wait_timeouts_check(*timeouts, s);
   HM_CHECK(!(herr & ERR_TABLE), HM_ETABLEFULL, "hash insertion exceeded its probe bound");
 }
 
@@ -617,9 +657,7 @@ void free_graph(hm_graph* g) {
   if (!g) return;
   // work that reads the graph may still be queued on any stream
   cudaDeviceSynchronize();
-  for (void* p : g->owned) cudaFreeAsync(p, 0);
-  for (auto* sp : {&g->W, &g->S, &g->P, &g->TX, &g->Wb, &g->Sb, &g->Pb})
-    if (sp->ws) cudaFreeAsync(sp->ws, 0);
+  for (void* p : g->owned) cudaFreeAsync(p, 0);  // includes the work spaces
   delete g;
 }
 

@@ -136,7 +136,10 @@ __global__ void __launch_bounds__(CENSUS_THREADS)
 
 // Bit-sliced families: each item evaluates up to bwords*32 candidates and
 // adds its class counts to the block's bins.
-constexpr int BITS_CHUNK = 4;
+#ifndef HM_BITS_CHUNK
+#define HM_BITS_CHUNK 1  // consecutive items per thread (1: best balance, measured)
+#endif
+constexpr int BITS_CHUNK = HM_BITS_CHUNK;
 #ifndef HM_BITS_MINBLOCKS
 #define HM_BITS_MINBLOCKS 4  // resident blocks per SM the register budget targets
 #endif
@@ -195,56 +198,42 @@ __global__ void __launch_bounds__(CENSUS_THREADS, HM_BITS_MINBLOCKS)
 }
 
 // ---------------------------------------------------------------- work spaces
-__global__ void k_ws_nodes(const int64_t* __restrict__ off2, int32_t n, int choose,
-                           uint64_t* __restrict__ w) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t d = (uint64_t)(off2[v + 1] - off2[v]);
-    w[v] = choose == 2 ? choose2(d) : choose3(d);
-  }
-}
+// Candidates per anchor of up to 8 families in one pass over the anchors.
+struct WsArgs {
+  int nj;
+  char fam[8];
+  int64_t A[8];
+  uint64_t* out[8];
+  uint64_t groups;  // 4-word groups per row (bit-sliced TX items per 3-hyperedge)
+};
 
-// bit-sliced spaces: W -> d (d >= 2), S -> C(d, 2) per node; P -> d(u) - 1 per pair (u, v)
-__global__ void k_ws_nodes_bits(const int64_t* __restrict__ off2, int32_t n, int choose,
-                                uint64_t* __restrict__ w) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t d = (uint64_t)(off2[v + 1] - off2[v]);
-    w[v] = choose == 2 ? (d >= 2 ? d : 0) : choose2(d);
-  }
-}
-
-__global__ void k_ws_pairs_bits(const uint64_t* __restrict__ e2, int64_t m,
-                                const int64_t* __restrict__ off2, uint64_t* __restrict__ w) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t u = (int32_t)(e2[p] >> 32), v = (int32_t)(e2[p] & 0xFFFFFFFFull);
-    const uint64_t du = (uint64_t)(off2[u + 1] - off2[u]), dv = (uint64_t)(off2[v + 1] - off2[v]);
-    w[p] = dv > 1 ? du - 1 : 0;
-  }
-}
-
-__global__ void k_ws_pairs(const uint64_t* __restrict__ e2, int64_t m, const int64_t* __restrict__ off2,
-                           uint64_t* __restrict__ w) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t u = (int32_t)(e2[p] >> 32), v = (int32_t)(e2[p] & 0xFFFFFFFFull);
-    const uint64_t du = (uint64_t)(off2[u + 1] - off2[u]), dv = (uint64_t)(off2[v + 1] - off2[v]);
-    w[p] = (du - 1) * (dv - 1);
-  }
-}
-
-__global__ void k_ws_triples(const int4* __restrict__ e3, int64_t m, const int64_t* __restrict__ off2,
-                             const int64_t* __restrict__ off3, uint64_t* __restrict__ w) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int4 e = e3[t];
-    uint64_t s = 0;
-    const int32_t xs[3] = {e.x, e.y, e.z};
+__global__ void k_ws_all(const int64_t* __restrict__ off2, const int64_t* __restrict__ off3,
+                         const uint64_t* __restrict__ e2, const int4* __restrict__ e3,
+                         const WsArgs W, int64_t maxA) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < maxA;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    for (int k = 0; k < W.nj; ++k) {
+      if (i >= W.A[k]) continue;
+      const char f = W.fam[k];
+      uint64_t v = 0;
+      if (f == 'W' || f == 'S' || f == 'w' || f == 's') {
+        const uint64_t d = (uint64_t)(off2[i + 1] - off2[i]);
+        v = f == 'W' ? choose2(d) : f == 'S' ? choose3(d) : f == 'w' ? (d >= 2 ? d : 0) : choose2(d);
+      } else if (f == 'P' || f == 'p') {
+        const int32_t u = (int32_t)(e2[i] >> 32), x = (int32_t)(e2[i] & 0xFFFFFFFFull);
+        const uint64_t du = (uint64_t)(off2[u + 1] - off2[u]), dx = (uint64_t)(off2[x + 1] - off2[x]);
+        v = f == 'P' ? (du - 1) * (dx - 1) : (dx > 1 ? du - 1 : 0);
+      } else if (f == 'x') {
+        v = W.groups;
+      } else {
+        const int4 e = e3[i];
+        const int32_t xs[3] = {e.x, e.y, e.z};
 #pragma unroll
-    for (int j = 0; j < 3; ++j)
-      s += (uint64_t)(off2[xs[j] + 1] - off2[xs[j]]) + (uint64_t)(off3[xs[j] + 1] - off3[xs[j]]);
-    w[t] = s;
+        for (int j = 0; j < 3; ++j)
+          v += (uint64_t)(off2[xs[j] + 1] - off2[xs[j]]) + (uint64_t)(off3[xs[j] + 1] - off3[xs[j]]);
+      }
+      W.out[k][i] = v;
+    }
   }
 }
 
@@ -262,49 +251,53 @@ unsigned grid1d(int64_t n) {
 // copied to P.h; spaces_finish, after s has completed, marks them ready.
 void spaces_enqueue(hm_graph* g, const std::vector<std::pair<hm_graph::Space*, char>>& todo,
                     cudaStream_t s, PendingSpaces& P) {
+  P.g = g;
   P.need.clear();
   P.made.clear();
   for (auto& t : todo)
     if (!t.first->ready) P.need.push_back(t);
   if (P.need.empty()) return;
-  HM_CHECK(P.need.size() <= 8, HM_EINVAL, "too many work spaces");
-  std::vector<int64_t> A(P.need.size());
-  size_t tmp = 0;
-  for (size_t i = 0; i < P.need.size(); ++i) {
+  const int nj = (int)P.need.size();
+  HM_CHECK(nj <= 8, HM_EINVAL, "too many work spaces");
+  // one allocation for all prefix-sum arrays (anchors + 1 entries each)
+  WsArgs W{};
+  W.nj = nj;
+  W.groups = (uint64_t)(g->bwords / 4);
+  int64_t maxA = 0;
+  size_t bytes = 0;
+  size_t off[8];
+  for (int i = 0; i < nj; ++i) {
     const char fam = P.need[i].second;
     int64_t a = 0;
     if (fam == 'W' || fam == 'S' || fam == 'w' || fam == 's') a = g->n;
     if (fam == 'P' || fam == 'p') a = g->counts[2];
-    if (fam == 'X') a = g->kmax >= 3 ? g->counts[3] : 0;
-    A[i] = a;
-    tmp = std::max<size_t>(tmp, (size_t)a);
+    if (fam == 'X' || fam == 'x') a = g->kmax >= 3 ? g->counts[3] : 0;
+    W.fam[i] = fam;
+    W.A[i] = a;
+    maxA = std::max(maxA, a);
+    off[i] = bytes;
+    bytes += (((size_t)a + 1) * sizeof(uint64_t) + 255) & ~(size_t)255;
   }
-  DBuf<uint64_t> w(tmp, s), totals(P.need.size(), s);
+  unsigned char* base = dalloc<unsigned char>(bytes, s);
+  P.made.push_back(reinterpret_cast<uint64_t*>(base));
   try {
-    for (size_t i = 0; i < P.need.size(); ++i) {
-      const char fam = P.need[i].second;
-      const int64_t a = A[i];
-      uint64_t* ws = dalloc<uint64_t>((size_t)a + 1, s);
-      P.made.push_back(ws);
-      if (a > 0) {
-        if (fam == 'W' || fam == 'S')
-          k_ws_nodes<<<grid1d(a), 256, 0, s>>>(g->off2, g->n, fam == 'W' ? 2 : 3, w.p);
-        else if (fam == 'w' || fam == 's')
-          k_ws_nodes_bits<<<grid1d(a), 256, 0, s>>>(g->off2, g->n, fam == 'w' ? 2 : 3, w.p);
-        else if (fam == 'P')
-          k_ws_pairs<<<grid1d(a), 256, 0, s>>>(g->e2, a, g->off2, w.p);
-        else if (fam == 'p')
-          k_ws_pairs_bits<<<grid1d(a), 256, 0, s>>>(g->e2, a, g->off2, w.p);
-        else
-          k_ws_triples<<<grid1d(a), 256, 0, s>>>(g->e3, a, g->off2, g->off3, w.p);
-        HM_KCHECK();
-      }
-      scan_exclusive_u64(w.p, ws, a, s);
-      HM_CUDA(cudaMemcpyAsync(totals.p + i, ws + a, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
-      P.need[i].first->anchors = a;
+    DBuf<uint64_t> totals(nj, s);
+    ScanJob jobs[8];
+    for (int i = 0; i < nj; ++i) {
+      W.out[i] = reinterpret_cast<uint64_t*>(base + off[i]);
+      jobs[i].a = W.out[i];
+      jobs[i].n = W.A[i];
+      jobs[i].total = totals.p + i;
+      P.ws[i] = W.out[i];
+      P.need[i].first->anchors = W.A[i];
     }
-    HM_CUDA(cudaMemcpyAsync(P.h, totals.p, P.need.size() * sizeof(uint64_t),
-                            cudaMemcpyDeviceToHost, s));
+    if (maxA > 0) {
+      k_ws_all<<<grid1d(maxA), 256, 0, s>>>(g->off2, g->off3, g->e2, g->e3, W, maxA);
+      HM_KCHECK();
+    }
+    scan_batch_inplace(jobs, nj, s);
+    P.h = pinned_words() + 64;
+    HM_CUDA(cudaMemcpyAsync(P.h, totals.p, nj * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   } catch (...) {
     for (uint64_t* p : P.made) cudaFreeAsync(p, s);
     P.made.clear();
@@ -315,10 +308,11 @@ void spaces_enqueue(hm_graph* g, const std::vector<std::pair<hm_graph::Space*, c
 
 void spaces_finish(PendingSpaces& P) {
   for (size_t i = 0; i < P.need.size(); ++i) {
-    P.need[i].first->ws = P.made[i];
+    P.need[i].first->ws = P.ws[i];
     P.need[i].first->total = P.h[i];
     P.need[i].first->ready = true;
   }
+  for (uint64_t* p : P.made) P.g->owned.push_back(p);
   P.need.clear();
   P.made.clear();
 }
@@ -466,7 +460,8 @@ std::vector<std::pair<hm_graph::Space*, char>> census_spaces(hm_graph* g, int or
     if (g->bits2) return {{&g->W, 'W'}, {&g->Wb, 'w'}};
     return {{&g->W, 'W'}};
   }
-  if (g->bits2) return {{&g->S, 'S'}, {&g->P, 'P'}, {&g->TX, 'X'}, {&g->Sb, 's'}, {&g->Pb, 'p'}};
+  if (g->bits2)
+    return {{&g->S, 'S'}, {&g->P, 'P'}, {&g->TX, 'X'}, {&g->Sb, 's'}, {&g->Pb, 'p'}, {&g->TXb, 'x'}};
   return {{&g->S, 'S'}, {&g->P, 'P'}, {&g->TX, 'X'}};
 }
 
@@ -477,6 +472,8 @@ void choose_variants(hm_graph* g, int order) {
   } else {
     g->useSb = prefer_bits(g, g->Sb, g->S.total, 0.5);
     g->usePb = prefer_bits(g, g->Pb, g->P.total, 1.0);
+    // a bit-sliced TX item scans one 4-word group
+    g->useTXb = g->bwords >= 4 && prefer_bits(g, g->TXb, g->TX.total, 4.0 / g->bwords);
   }
 }
 
@@ -524,7 +521,12 @@ void launch_one(const hm_graph* g, char fam, bool bits, int chunk, int order,
         launch_family(g, FamP{}, &g->P, g->P.total, order, hist, s, chunk, b, e, traced);
       break;
     default:
-      launch_family(g, FamTX{}, &g->TX, g->TX.total, order, hist, s, chunk, b, e, traced);
+      if (bits && g->tri3)
+        launch_bits(g, BitsXT<true>{}, g->TXb, order, hist, s, b, e, traced);
+      else if (bits)
+        launch_bits(g, BitsXT<false>{}, g->TXb, order, hist, s, b, e, traced);
+      else
+        launch_family(g, FamTX{}, &g->TX, g->TX.total, order, hist, s, chunk, b, e, traced);
       break;
   }
 }
@@ -541,7 +543,7 @@ void launch_census(const hm_graph* g, int order, unsigned long long* hist, cudaS
     launch_one(g, 'W', g->useWb, pick(g->chunkW), 3, hist, s);
   } else {
     launch_family(g, FamQ{}, nullptr, (uint64_t)g->counts[4], 4, hist, s, pick(0));
-    launch_one(g, 'X', false, pick(g->chunkTX), 4, hist, s);
+    launch_one(g, 'X', g->useTXb, pick(g->chunkTX), 4, hist, s);
     launch_one(g, 'S', g->useSb, pick(g->chunkS), 4, hist, s);
     launch_one(g, 'P', g->usePb, pick(g->chunkP), 4, hist, s);
   }
@@ -645,7 +647,7 @@ void tune_census(hm_graph* g, int order, cudaStream_t s) {
   } else {
     fams.push_back({'S', &g->S, g->bits2 ? &g->Sb : nullptr, {}});
     fams.push_back({'P', &g->P, g->bits2 ? &g->Pb : nullptr, {}});
-    fams.push_back({'X', &g->TX, nullptr, {}});
+    fams.push_back({'X', &g->TX, g->bits2 ? &g->TXb : nullptr, {}});
   }
   // slice boundaries in both spaces (bt = pc where there is no bit-sliced
   // variant), read back in one copy
@@ -690,7 +692,7 @@ void tune_census(hm_graph* g, int order, cudaStream_t s) {
   out.f[0] = {g->useWb, g->chunkW};
   out.f[1] = {g->useSb, g->chunkS};
   out.f[2] = {g->usePb, g->chunkP};
-  out.f[3] = {false, g->chunkTX};
+  out.f[3] = {g->useTXb, g->chunkTX};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   HM_CUDA(cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -756,6 +758,7 @@ void tune_census(hm_graph* g, int order, cudaStream_t s) {
   g->chunkS = out.f[1].chunk;
   g->usePb = out.f[2].bits;
   g->chunkP = out.f[2].chunk;
+  g->useTXb = out.f[3].bits;
   g->chunkTX = out.f[3].chunk;
 }
 
@@ -776,6 +779,7 @@ void schedule_census(hm_graph* g, int order, cudaStream_t s) {
       g->chunkS = t.f[1].chunk;
       g->usePb = t.f[2].bits && g->bits2;
       g->chunkP = t.f[2].chunk;
+      g->useTXb = t.f[3].bits && g->bits2;
       g->chunkTX = t.f[3].chunk;
       g->tuned[order] = true;
       return;
@@ -845,7 +849,7 @@ extern "C" hm_status hm_work_totals(hm_graph* g, int order, uint64_t* totals, vo
     HM_CHECK(order == 3 || order == 4, HM_EINVAL, "order must be 3 or 4");
     HM_CHECK(order <= g->kmax, HM_EUNSUPPORTED, "order exceeds the graph's max_order");
     hm::prepare_census(g, order, (cudaStream_t)stream);
-    for (int i = 0; i < 8; ++i) totals[i] = 0;
+    for (int i = 0; i < 10; ++i) totals[i] = 0;
     if (order == 3) {
       totals[0] = (uint64_t)g->counts[3];
       totals[1] = g->W.total;
@@ -860,6 +864,8 @@ extern "C" hm_status hm_work_totals(hm_graph* g, int order, uint64_t* totals, vo
       totals[5] = g->Pb.total;
       totals[6] = g->useSb ? 1 : 0;
       totals[7] = g->usePb ? 1 : 0;
+      totals[8] = g->TXb.total;
+      totals[9] = g->useTXb ? 1 : 0;
     }
   });
 }

@@ -102,6 +102,12 @@ T* dalloc(size_t count, cudaStream_t s) {
   return p;
 }
 
+// Pinned host words of the calling thread (512, allocated once and kept):
+// small results are read back into them, because a copy into pageable
+// memory makes the host wait for the device at every copy. Slots: [0, 64)
+// hm_build, [64, 72) work-space totals, [80] device wait timeouts.
+uint64_t* pinned_words();
+
 // Fork-join concurrency inside one call: up to kSide streams of this device
 // (created once per device, non-blocking) start after everything already
 // queued on `main`, and join() makes `main` wait for all of them. Buffers the
@@ -163,6 +169,15 @@ struct SortJob {
 // Sorts 1-4 independent arrays together (one temporary allocation, one
 // launch per pass index for all of them).
 void sort_batch(const SortJob* jobs, int njobs, cudaStream_t s);
+// Exclusive scans of 1-8 arrays in place, in one launch: a[0..n) becomes the
+// prefix sums of its inputs and a[n] (which must exist) the total, also
+// written to *total (device, may be NULL).
+struct ScanJob {
+  uint64_t* a = nullptr;
+  int64_t n = 0;
+  uint64_t* total = nullptr;
+};
+void scan_batch_inplace(const ScanJob* jobs, int njobs, cudaStream_t s);
 // Stable LSD radix sort of n keys on bits [lo_bit, lo_bit + bits); vals
 // (nullable) are permuted alongside. Keys equal on those bits keep their input
 // order.
@@ -438,7 +453,9 @@ struct hm_graph {
   // bit-sliced variants of W, S, P (dense graphs): items are (anchor, first
   // neighbour[s]) and the last node runs over bitmap words
   Space Wb, Sb, Pb;
-  bool useWb = false, useSb = false, usePb = false;
+  // bit-sliced TX: items are (3-hyperedge, 4-word group of the rows)
+  Space TXb;
+  bool useWb = false, useSb = false, usePb = false, useTXb = false;
   // candidates per lane of the per-candidate families (0 = fill the GPU)
   int chunkW = 0, chunkS = 0, chunkP = 0, chunkTX = 0;
   bool tuned[5] = {false, false, false, false, false};  // by order
@@ -479,9 +496,11 @@ namespace hm {
 // Work spaces enqueued without a synchronisation (hm_build prepares those of
 // its max_order this way, before its own final synchronisation).
 struct PendingSpaces {
+  hm_graph* g = nullptr;
   std::vector<std::pair<hm_graph::Space*, char>> need;
-  std::vector<uint64_t*> made;
-  uint64_t h[8] = {};
+  std::vector<uint64_t*> made;  // allocations, owned by the graph once finished
+  uint64_t* ws[8] = {};
+  uint64_t* h = nullptr;  // the totals, in the calling thread's pinned words
 };
 std::vector<std::pair<hm_graph::Space*, char>> census_spaces(hm_graph* g, int order);
 void spaces_enqueue(hm_graph* g, const std::vector<std::pair<hm_graph::Space*, char>>& todo,

@@ -419,10 +419,12 @@ int mlp_blocks(int64_t n) {
   return (int)(b < 1 ? 1 : b);
 }
 
-// weight-gradient blocks: at least 1024 rows each, at most 256 blocks
+// weight-gradient blocks: at least 128 rows each (a multiple of 16), at most
+// 512 blocks, so that a minibatch of a few thousand rows still spreads over
+// tens of SMs
 int64_t wgrad_rows_per_block(int64_t n) {
-  const int64_t r = (n + 255) / 256;
-  return r < 1024 ? 1024 : ((r + 15) / 16) * 16;
+  const int64_t r = (n + 511) / 512;
+  return r < 128 ? 128 : ((r + 15) / 16) * 16;
 }
 int wgrad_blocks(int64_t n) {
   const int64_t b = (n + wgrad_rows_per_block(n) - 1) / wgrad_rows_per_block(n);

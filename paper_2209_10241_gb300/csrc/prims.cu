@@ -152,18 +152,28 @@ unsigned grid_for(int64_t n, int threads) {
 
 }  // namespace
 
+uint64_t* pinned_words() {
+  thread_local uint64_t* p = nullptr;
+  if (!p) HM_CUDA(cudaMallocHost((void**)&p, 512 * sizeof(uint64_t)));
+  return p;
+}
+
 // ------------------------------------------------------------------ fork-join
 namespace {
 std::mutex g_side_mu;
 cudaStream_t g_side[64][Fork::kSide] = {};
 
-void link(cudaStream_t from, cudaStream_t to) {
-  cudaEvent_t e;
-  HM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-  cudaError_t r = cudaEventRecord(e, from);
-  if (r == cudaSuccess) r = cudaStreamWaitEvent(to, e, 0);
-  cudaEventDestroy(e);  // released once the recorded work completes
-  HM_CUDA(r);
+// Events of this host thread on one device, created once: [0] marks the
+// fork, [1 + i] the end of side stream i.
+struct ForkEvents {
+  cudaEvent_t e[1 + Fork::kSide] = {};
+};
+ForkEvents& fork_events(int dev) {
+  thread_local ForkEvents ev[64];
+  ForkEvents& f = ev[dev];
+  if (!f.e[0])
+    for (auto& e : f.e) HM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return f;
 }
 }  // namespace
 
@@ -179,24 +189,32 @@ Fork::Fork(cudaStream_t s) : main(s) {
       side[i] = g_side[dev][i];
     }
   }
-  for (int i = 0; i < kSide; ++i) link(main, side[i]);
+  ForkEvents& ev = fork_events(dev);
+  HM_CUDA(cudaEventRecord(ev.e[0], main));
+  for (int i = 0; i < kSide; ++i) HM_CUDA(cudaStreamWaitEvent(side[i], ev.e[0], 0));
 }
 
 void Fork::join() {
   if (joined) return;
   joined = true;
-  for (int i = 0; i < kSide; ++i) link(side[i], main);
+  int dev = 0;
+  HM_CUDA(cudaGetDevice(&dev));
+  ForkEvents& ev = fork_events(dev);
+  for (int i = 0; i < kSide; ++i) {
+    HM_CUDA(cudaEventRecord(ev.e[1 + i], side[i]));
+    HM_CUDA(cudaStreamWaitEvent(main, ev.e[1 + i], 0));
+  }
 }
 
 Fork::~Fork() {
   if (joined) return;
   joined = true;
-  for (int i = 0; i < kSide; ++i) {
-    cudaEvent_t e;
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) continue;
-    if (cudaEventRecord(e, side[i]) == cudaSuccess) cudaStreamWaitEvent(main, e, 0);
-    cudaEventDestroy(e);
-  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  ForkEvents& ev = fork_events(dev);
+  for (int i = 0; i < kSide; ++i)
+    if (cudaEventRecord(ev.e[1 + i], side[i]) == cudaSuccess)
+      cudaStreamWaitEvent(main, ev.e[1 + i], 0);
 }
 
 void scan_exclusive_u64(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s) {

@@ -505,3 +505,116 @@ void radix_sort_u128(uint64_t* hi, uint64_t* lo, int64_t n, int hi_bits, int lo_
 }
 
 }  // namespace hm
+
+// ------------------------------------------------------------------ batched scan
+namespace hm {
+namespace {
+
+constexpr int SCAN_JOBS = 8;
+
+struct ScanDev {
+  uint64_t* a;
+  int64_t n, tiles;
+  uint64_t* total;
+  uint64_t* status;  // [tiles]
+  uint32_t* ctr;
+};
+struct ScanBatch {
+  int nj;
+  ScanDev j[SCAN_JOBS];
+  int64_t first[SCAN_JOBS + 1];
+};
+
+// In place: a[i] = sum of the input a[0..i), a[n] = total (and *total). Each
+// tile reads its 2048 inputs before anything of it is written, and no tile
+// reads another's inputs, so in-place is safe.
+__global__ void __launch_bounds__(TPB) k_scan_batch(const ScanBatch B) {
+  __shared__ uint64_t wtot[TPB / 32];
+  __shared__ uint64_t tile_excl;
+  __shared__ uint32_t tile_s;
+  int e = 0;
+  while (e + 1 < B.nj && (int64_t)blockIdx.x >= B.first[e + 1]) ++e;
+  const ScanDev& J = B.j[e];
+  if (threadIdx.x == 0) tile_s = atomicAdd(J.ctr, 1u);
+  __syncthreads();
+  const int64_t tile = tile_s;
+  const int64_t i0 = tile * TILE + (int64_t)threadIdx.x * IPT;
+  uint64_t v[IPT], sum = 0;
+#pragma unroll
+  for (int it = 0; it < IPT; ++it) {
+    v[it] = i0 + it < J.n ? J.a[i0 + it] : 0;
+    sum += v[it];
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint64_t incl = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += y;
+  }
+  if (lane == 31) wtot[warp] = incl;
+  __syncthreads();
+  uint64_t before = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < TPB / 32; ++w) {
+    before += w < warp ? wtot[w] : 0ull;
+    total += wtot[w];
+  }
+  if (threadIdx.x == 0) {
+    uint64_t excl = 0;
+    if (tile == 0) {
+      st_status(J.status, ST_PREFIX | total);
+    } else {
+      st_status(J.status + tile, ST_AGG | total);
+      excl = look_back(J.status, tile, 1, 0);
+      st_status(J.status + tile, ST_PREFIX | (excl + total));
+    }
+    tile_excl = excl;
+    if (tile == J.tiles - 1) {
+      J.a[J.n] = excl + total;
+      if (J.total) *J.total = excl + total;
+    }
+  }
+  __syncthreads();
+  uint64_t run = tile_excl + before + incl - sum;
+#pragma unroll
+  for (int it = 0; it < IPT; ++it) {
+    if (i0 + it < J.n) J.a[i0 + it] = run;
+    run += v[it];
+  }
+}
+
+}  // namespace
+
+void scan_batch_inplace(const ScanJob* jobs, int njobs, cudaStream_t s) {
+  HM_CHECK(njobs >= 1 && njobs <= SCAN_JOBS, HM_EINVAL, "scan batch of 1-8 arrays");
+  ScanBatch B{};
+  B.nj = njobs;
+  size_t bytes = 256;
+  std::vector<size_t> off(njobs);
+  int64_t blocks = 0;
+  for (int k = 0; k < njobs; ++k) {
+    HM_CHECK(jobs[k].n >= 0 && jobs[k].a, HM_EINVAL, "bad scan array");
+    ScanDev& J = B.j[k];
+    J.a = jobs[k].a;
+    J.n = jobs[k].n;
+    J.tiles = std::max<int64_t>(1, (J.n + TILE - 1) / TILE);
+    J.total = jobs[k].total;
+    off[k] = bytes;
+    bytes += align256((size_t)J.tiles * 8) + 256;
+    B.first[k] = blocks;
+    blocks += J.tiles;
+  }
+  B.first[njobs] = blocks;
+  HM_CHECK(blocks < (1ll << 31), HM_EINVAL, "scan too large");
+  DBuf<unsigned char> scratch(bytes, s);
+  for (int k = 0; k < njobs; ++k) {
+    B.j[k].status = reinterpret_cast<uint64_t*>(scratch.p + off[k]);
+    B.j[k].ctr = reinterpret_cast<uint32_t*>(scratch.p + off[k] + align256((size_t)B.j[k].tiles * 8));
+  }
+  HM_CUDA(cudaMemsetAsync(scratch.p, 0, bytes, s));
+  k_scan_batch<<<(unsigned)blocks, TPB, 0, s>>>(B);
+  HM_KCHECK();
+}
+
+}  // namespace hm

@@ -18,6 +18,21 @@ struct Entry {
 std::mutex g_mu;
 bool g_on = false;
 std::vector<Entry> g_entries;
+std::vector<cudaEvent_t> g_pool;  // events read back, reused by later spans
+
+cudaEvent_t take_event() {
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_pool.empty()) {
+      cudaEvent_t e = g_pool.back();
+      g_pool.pop_back();
+      return e;
+    }
+  }
+  cudaEvent_t e;
+  HM_CUDA(cudaEventCreate(&e));
+  return e;
+}
 
 }  // namespace
 
@@ -27,13 +42,12 @@ static std::atomic<uint64_t> g_launches{0};
 uint64_t launch_count_add(uint64_t n) { return g_launches.fetch_add(n) + n; }
 
 void trace_begin(cudaStream_t s, cudaEvent_t* a) {
-  HM_CUDA(cudaEventCreate(a));
+  *a = take_event();
   HM_CUDA(cudaEventRecord(*a, s));
 }
 
 void trace_end(const char* name, cudaStream_t s, cudaEvent_t a) {
-  cudaEvent_t b;
-  HM_CUDA(cudaEventCreate(&b));
+  cudaEvent_t b = take_event();
   HM_CUDA(cudaEventRecord(b, s));
   std::lock_guard<std::mutex> lock(g_mu);
   g_entries.push_back(Entry{name, a, b});
@@ -69,8 +83,8 @@ hm_status hm_trace_read(int max_entries, char* names, int name_len, float* ms, i
         }
         ++n;
       }
-      cudaEventDestroy(e.a);
-      cudaEventDestroy(e.b);
+      hm::g_pool.push_back(e.a);
+      hm::g_pool.push_back(e.b);
     }
     hm::g_entries.clear();
     *count = n;
