@@ -46,8 +46,10 @@ namespace {
 using namespace fam;
 
 // Union of graphs (null-model batch): at most this many graphs per launch,
-// each with its own histogram row; block bins are then uint32 (the launch
-// keeps every block below 2^31 candidates).
+// each with its own histogram row; block bins are then uint32, read as signed
+// when flushed (the launch keeps every block below 2^31 candidates, and a
+// block's net count of a class may be negative when its sets are subtracted
+// for the graphlet census).
 constexpr int MAX_GRAPHS = 64;
 constexpr int BIN_STRIDE = 176;
 
@@ -55,7 +57,7 @@ template <class F, bool kBatched>
 __global__ void __launch_bounds__(CENSUS_THREADS)
     k_census(const DevGraph g, const F fam, const uint64_t* __restrict__ ws, int64_t A,
              uint64_t begin, uint64_t total, int chunk, const uint8_t* __restrict__ lut_g,
-             int nmask, int ncls, int ngraphs, unsigned long long* __restrict__ hist) {
+             int nmask, int ncls, int ngraphs, int sub, unsigned long long* __restrict__ hist) {
   __shared__ unsigned long long bins[kBatched ? 1 : BIN_STRIDE];
   __shared__ unsigned int gbins[kBatched ? MAX_GRAPHS * BIN_STRIDE : 1];
   __shared__ uint8_t lut[2048];
@@ -88,7 +90,7 @@ __global__ void __launch_bounds__(CENSUS_THREADS)
     }
     for (int it = 0; it < chunk; ++it) {
       const uint64_t gi = g0 + it;
-      int key = -1;
+      int key = -1, key2 = -1;
       if (gi < g1) {
         uint32_t mask = 0;
         int32_t nd[4];
@@ -113,6 +115,9 @@ __global__ void __launch_bounds__(CENSUS_THREADS)
         if (ok) {
           const uint8_t c = lut[mask];
           key = c == 0xFF ? -1 : (kBatched ? gid * BIN_STRIDE : 0) + (int)c;
+          // the graphlet census counts this set under its pair pattern too
+          const uint8_t c2 = sub ? lut[mask & 63u] : (uint8_t)0xFF;
+          if (c2 != 0xFF) key2 = (kBatched ? gid * BIN_STRIDE : 0) + (int)c2;
         }
       }
       const unsigned peers = __match_any_sync(0xffffffffu, key);
@@ -122,12 +127,23 @@ __global__ void __launch_bounds__(CENSUS_THREADS)
         else
           atomicAdd(&bins[key], (unsigned long long)__popc(peers));
       }
+      if (sub) {
+        const unsigned peers2 = __match_any_sync(0xffffffffu, key2);
+        if (key2 >= 0 && lane == __ffs(peers2) - 1) {
+          if (kBatched)
+            atomicAdd(&gbins[key2], 0u - (unsigned int)__popc(peers2));
+          else
+            atomicAdd(&bins[key2], 0ull - (unsigned long long)__popc(peers2));
+        }
+      }
     }
   }
   __syncthreads();
   if (kBatched) {
     for (int i = threadIdx.x; i < ngraphs * BIN_STRIDE; i += blockDim.x)
-      if (gbins[i]) atomicAdd(&hist[(i / BIN_STRIDE) * ncls + i % BIN_STRIDE], (unsigned long long)gbins[i]);
+      if (gbins[i])
+        atomicAdd(&hist[(i / BIN_STRIDE) * ncls + i % BIN_STRIDE],
+                  (unsigned long long)(long long)(int)gbins[i]);
   } else {
     for (int i = threadIdx.x; i < ncls; i += blockDim.x)
       if (bins[i]) atomicAdd(&hist[i], bins[i]);
@@ -190,7 +206,9 @@ __global__ void __launch_bounds__(CENSUS_THREADS, HM_BITS_MINBLOCKS)
   __syncthreads();
   if (kBatched) {
     for (int i = threadIdx.x; i < ngraphs * BIN_STRIDE; i += blockDim.x)
-      if (gbins[i]) atomicAdd(&hist[(i / BIN_STRIDE) * ncls + i % BIN_STRIDE], (unsigned long long)gbins[i]);
+      if (gbins[i])
+        atomicAdd(&hist[(i / BIN_STRIDE) * ncls + i % BIN_STRIDE],
+                  (unsigned long long)(long long)(int)gbins[i]);
   } else {
     for (int i = threadIdx.x; i < ncls; i += blockDim.x)
       if (bins[i]) atomicAdd(&hist[i], bins[i]);
@@ -403,7 +421,7 @@ int fill_chunk(uint64_t candidates) {
 template <class F, bool kBatched>
 void launch_family_t(const hm_graph* g, const F& fam, const hm_graph::Space* sp, uint64_t begin,
                      uint64_t end, int chunk, int order, unsigned long long* hist,
-                     cudaStream_t s, bool traced) {
+                     cudaStream_t s, bool traced, int sub) {
   const ClassTables& T = class_tables(order);
   const uint8_t* lut = device_lut(order);
   // consecutive candidates per lane (every lane of a warp takes the same)
@@ -416,7 +434,7 @@ void launch_family_t(const hm_graph* g, const F& fam, const hm_graph::Space* sp,
   if (tr) trace_begin(s, &ev);
   k_census<F, kBatched><<<blocks, CENSUS_THREADS, 0, s>>>(
       g->view(), fam, sp ? sp->ws : nullptr, sp ? sp->anchors : 0, begin, end, chunk, lut,
-      (int)T.lut.size(), T.ncls, num_graphs(g), hist);
+      (int)T.lut.size(), T.ncls, num_graphs(g), sub, hist);
   HM_KCHECK();
   if (tr) trace_end(F::kName, s, ev);
 }
@@ -424,13 +442,13 @@ void launch_family_t(const hm_graph* g, const F& fam, const hm_graph::Space* sp,
 template <class F>
 void launch_family(const hm_graph* g, const F& fam, const hm_graph::Space* sp, uint64_t total,
                    int order, unsigned long long* hist, cudaStream_t s, int chunk = 0,
-                   uint64_t begin = 0, uint64_t end = ~0ull, bool traced = true) {
+                   uint64_t begin = 0, uint64_t end = ~0ull, bool traced = true, int sub = 0) {
   if (end > total) end = total;
   if (begin >= end) return;
   if (g->block)
-    launch_family_t<F, true>(g, fam, sp, begin, end, chunk, order, hist, s, traced);
+    launch_family_t<F, true>(g, fam, sp, begin, end, chunk, order, hist, s, traced, sub);
   else
-    launch_family_t<F, false>(g, fam, sp, begin, end, chunk, order, hist, s, traced);
+    launch_family_t<F, false>(g, fam, sp, begin, end, chunk, order, hist, s, traced, sub);
 }
 
 }  // namespace
@@ -465,6 +483,23 @@ std::vector<std::pair<hm_graph::Space*, char>> census_spaces(hm_graph* g, int or
   return {{&g->S, 'S'}, {&g->P, 'P'}, {&g->TX, 'X'}};
 }
 
+// The graphlet census replaces S and P when its word operations (a word
+// operation taken as a tenth of one candidate's evaluation) cost less than the
+// cheaper variant of each. HM_GRAPHLETS=0 / 1 forces it off / on (on needs
+// pair bitmaps); HM_DENSE_FAMILIES, which forces the S and P variants, keeps
+// it off unless HM_GRAPHLETS=1.
+bool prefer_graphlets(const hm_graph* g) {
+  if (!g->bits2) return false;
+  const char* env = std::getenv("HM_GRAPHLETS");
+  if (env && env[0] == '0') return false;
+  if (env && env[0] == '1') return true;
+  if (std::getenv("HM_DENSE_FAMILIES")) return false;
+  const double bw = g->bwords;
+  const double s_cost = std::min((double)g->S.total, (double)g->Sb.total * (2 + bw * 0.5) * 0.35);
+  const double p_cost = std::min((double)g->P.total, (double)g->Pb.total * (2 + bw) * 0.35);
+  return graphlet_cost(g) * 0.1 < s_cost + p_cost;
+}
+
 void choose_variants(hm_graph* g, int order) {
   if (!g->bits2) return;
   if (order == 3) {
@@ -474,6 +509,7 @@ void choose_variants(hm_graph* g, int order) {
     g->usePb = prefer_bits(g, g->Pb, g->P.total, 1.0);
     // a bit-sliced TX item scans one 4-word group
     g->useTXb = g->bwords >= 4 && prefer_bits(g, g->TXb, g->TX.total, 4.0 / g->bwords);
+    g->useGL = prefer_graphlets(g);
   }
 }
 
@@ -492,9 +528,10 @@ namespace {
 
 // One family of the census over the range [b, e) of the chosen variant's index
 // space (bits: the bit-sliced space, else the per-candidate one).
+// sub: the set's pair pattern is subtracted too (graphlet census, TX only).
 void launch_one(const hm_graph* g, char fam, bool bits, int chunk, int order,
                 unsigned long long* hist, cudaStream_t s, uint64_t b = 0, uint64_t e = ~0ull,
-                bool traced = true) {
+                bool traced = true, bool sub = false) {
   switch (fam) {
     case 'W':
       if (bits && g->tri3)
@@ -521,12 +558,18 @@ void launch_one(const hm_graph* g, char fam, bool bits, int chunk, int order,
         launch_family(g, FamP{}, &g->P, g->P.total, order, hist, s, chunk, b, e, traced);
       break;
     default:
-      if (bits && g->tri3)
-        launch_bits(g, BitsXT<true>{}, g->TXb, order, hist, s, b, e, traced);
-      else if (bits)
-        launch_bits(g, BitsXT<false>{}, g->TXb, order, hist, s, b, e, traced);
-      else
-        launch_family(g, FamTX{}, &g->TX, g->TX.total, order, hist, s, chunk, b, e, traced);
+      if (bits && g->tri3) {
+        BitsXT<true> f;
+        f.sub = sub;
+        launch_bits(g, f, g->TXb, order, hist, s, b, e, traced);
+      } else if (bits) {
+        BitsXT<false> f;
+        f.sub = sub;
+        launch_bits(g, f, g->TXb, order, hist, s, b, e, traced);
+      } else {
+        launch_family(g, FamTX{}, &g->TX, g->TX.total, order, hist, s, chunk, b, e, traced,
+                      sub ? 1 : 0);
+      }
       break;
   }
 }
@@ -542,10 +585,18 @@ void launch_census(const hm_graph* g, int order, unsigned long long* hist, cudaS
     launch_family(g, FamT3{}, nullptr, (uint64_t)g->counts[3], 3, hist, s, pick(0));
     launch_one(g, 'W', g->useWb, pick(g->chunkW), 3, hist, s);
   } else {
-    launch_family(g, FamQ{}, nullptr, (uint64_t)g->counts[4], 4, hist, s, pick(0));
-    launch_one(g, 'X', g->useTXb, pick(g->chunkTX), 4, hist, s);
-    launch_one(g, 'S', g->useSb, pick(g->chunkS), 4, hist, s);
-    launch_one(g, 'P', g->usePb, pick(g->chunkP), 4, hist, s);
+    // with the graphlet census, Q and TX subtract their sets from the class of
+    // their pair pattern, and the graphlet launches replace S and P
+    const bool gl = g->useGL;
+    launch_family(g, FamQ{}, nullptr, (uint64_t)g->counts[4], 4, hist, s, pick(0), 0, ~0ull,
+                  true, gl ? 1 : 0);
+    launch_one(g, 'X', g->useTXb, pick(g->chunkTX), 4, hist, s, 0, ~0ull, true, gl);
+    if (gl) {
+      launch_graphlets(g, hist, s);
+    } else {
+      launch_one(g, 'S', g->useSb, pick(g->chunkS), 4, hist, s);
+      launch_one(g, 'P', g->usePb, pick(g->chunkP), 4, hist, s);
+    }
   }
 }
 
@@ -645,8 +696,10 @@ void tune_census(hm_graph* g, int order, cudaStream_t s) {
   if (order == 3) {
     fams.push_back({'W', &g->W, g->bits2 ? &g->Wb : nullptr, {}});
   } else {
-    fams.push_back({'S', &g->S, g->bits2 ? &g->Sb : nullptr, {}});
-    fams.push_back({'P', &g->P, g->bits2 ? &g->Pb : nullptr, {}});
+    if (!g->useGL) {  // the graphlet census replaces S and P
+      fams.push_back({'S', &g->S, g->bits2 ? &g->Sb : nullptr, {}});
+      fams.push_back({'P', &g->P, g->bits2 ? &g->Pb : nullptr, {}});
+    }
     fams.push_back({'X', &g->TX, g->bits2 ? &g->TXb : nullptr, {}});
   }
   // slice boundaries in both spaces (bt = pc where there is no bit-sliced

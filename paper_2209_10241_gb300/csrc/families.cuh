@@ -729,6 +729,9 @@ __device__ __forceinline__ uint32_t selfbit(int32_t w, int32_t t) {
 template <bool kExact>
 struct BitsXT {
   static constexpr const char* kName = "census_TXb";
+  // subtract each counted set from the class of its pair pattern (the
+  // graphlet census counts all sets by pair pattern)
+  bool sub = false;
   struct State {
     uint32_t grp;
   };
@@ -815,6 +818,7 @@ struct BitsXT {
                               (bd ? 16u : 0u) | (cd ? 32u : 0u) | 64u | (abd ? 128u : 0u) |
                               (acd ? 256u : 0u) | (bcd ? 512u : 0u);  // a=0, b=1, c=2, d=3
         atomicAdd(&bins[lut[mask]], (Bin)1);
+        if (sub && lut[mask & 63u] != 0xFF) atomicAdd(&bins[lut[mask & 63u]], (Bin)0 - (Bin)1);
       }
     }
     const uint32_t fixed = (ab ? 1u : 0u) | (ac ? 2u : 0u) | (bc ? 8u : 0u) | 64u;
@@ -823,6 +827,7 @@ struct BitsXT {
       if (n[m]) {
         const uint32_t mask = fixed | ((m & 1) ? 4u : 0u) | ((m & 2) ? 16u : 0u) | ((m & 4) ? 32u : 0u);
         atomicAdd(&bins[lut[mask]], (Bin)n[m]);
+        if (sub && lut[mask & 63u] != 0xFF) atomicAdd(&bins[lut[mask & 63u]], (Bin)0 - (Bin)n[m]);
       }
   }
 };

@@ -408,6 +408,10 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
 void free_graph(hm_graph* g);
 // census.cu
 void prepare_census(hm_graph* g, int order, cudaStream_t s);
+// graphlet.cu: the pairs-only 4-node sets of a graph with pair bitmaps, by
+// pattern, into hist (the Q and TX launches must subtract their sets)
+void launch_graphlets(const hm_graph* g, unsigned long long* hist, cudaStream_t s);
+double graphlet_cost(const hm_graph* g);
 // hist holds hm_num_classes(order) counters per graph of the union (one graph: one row)
 void launch_census(const hm_graph* g, int order, unsigned long long* hist, cudaStream_t s);
 }  // namespace hm
@@ -456,6 +460,8 @@ struct hm_graph {
   // bit-sliced TX: items are (3-hyperedge, 4-word group of the rows)
   Space TXb;
   bool useWb = false, useSb = false, usePb = false, useTXb = false;
+  // order 4: pairs-only sets from graphlet identities instead of S and P
+  bool useGL = false;
   // candidates per lane of the per-candidate families (0 = fill the GPU)
   int chunkW = 0, chunkS = 0, chunkP = 0, chunkTX = 0;
   bool tuned[5] = {false, false, false, false, false};  // by order

@@ -21,7 +21,8 @@ pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-MODES = ["hash", "bitmap", "sliced", "sliced_filter", "tuned", "chunk8", "chunk32"]
+MODES = ["hash", "bitmap", "sliced", "sliced_filter", "tuned", "chunk8", "chunk32", "graphlets",
+         "graphlets_filter", "graphlets_pc"]
 
 
 def _set_mode(monkeypatch, mode):
@@ -30,11 +31,20 @@ def _set_mode(monkeypatch, mode):
     exact 3-hyperedge rows; sliced_filter: bit-sliced with the co-occurrence
     filter and exact probes of the risky candidates; tuned: the library's
     defaults, schedules picked by the autotuner; chunk8 / chunk32: hash
-    probes with 8 / 32 candidates per lane on every per-candidate family."""
+    probes with 8 / 32 candidates per lane on every per-candidate family;
+    graphlets*: pairs-only sets from graphlet identities, with the bit-sliced
+    TX family on exact rows / on the co-occurrence filter / per candidate."""
     for var in ("HM_PAIR_BITMAP", "HM_DENSE_FAMILIES", "HM_TRIPLE_ROWS", "HM_AUTOTUNE",
-                "HM_CENSUS_CHUNK"):
+                "HM_CENSUS_CHUNK", "HM_GRAPHLETS"):
         monkeypatch.delenv(var, raising=False)
     if mode == "tuned":
+        return
+    if mode.startswith("graphlets"):
+        monkeypatch.setenv("HM_PAIR_BITMAP", "1")
+        monkeypatch.setenv("HM_GRAPHLETS", "1")
+        monkeypatch.setenv("HM_AUTOTUNE", "0")
+        monkeypatch.setenv("HM_TRIPLE_ROWS", "0" if mode == "graphlets_filter" else "1")
+        monkeypatch.setenv("HM_DENSE_FAMILIES", "0" if mode == "graphlets_pc" else "1")
         return
     if mode.startswith("chunk"):
         monkeypatch.setenv("HM_PAIR_BITMAP", "0")
