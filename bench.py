@@ -47,6 +47,8 @@ ROOFLINE = {
     "census_TX": ("candidate", 332.9, 659_000),
     "census_Q": ("candidate", 522.3, 301_000),
     "census_TXb": ("item", None, None),
+    "census_gl_edges": ("pair", None, None),
+    "census_gl_pairs": ("node pair", None, None),
     "census_Wb": ("item", None, None),
     "census_S": ("candidate", None, None),
     "census_P": ("candidate", None, None),
@@ -470,6 +472,7 @@ def main():
     for _ in range(args.warmup):
         g = step()
     totals = hm.work_totals(g, args.order)
+    g_counts = list(g.counts)
     g.free()
     torch.cuda.synchronize()
     sets_per_step = int(hist.sum().item())
@@ -552,7 +555,8 @@ def main():
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     unit, ops_per_unit, traffic = ROOFLINE.get(dom, ("item", None, None))
-    units = totals.get(dom)
+    units = totals.get(dom) or {"census_gl_edges": g_counts[2],
+                                "census_gl_pairs": n * (n - 1) // 2}.get(dom)
     peak_tops = SMS * ALU_LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e12
     achieved = (units * ops_per_unit / avg_s / 1e12) if (units and ops_per_unit) else None
     roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak_tops,

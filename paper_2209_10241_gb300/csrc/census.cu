@@ -215,6 +215,141 @@ __global__ void __launch_bounds__(CENSUS_THREADS, HM_BITS_MINBLOCKS)
   }
 }
 
+// Bit-sliced TX, sets whose largest hyperedges have 3 members: one warp per
+// 3-hyperedge e = {a < b < c}, lane l taking the row words l, l + 32, ...; the
+// fourth node d runs over the ids joined to e by a pair or a 3-hyperedge. A
+// set is kept at its smallest 3-hyperedge -- {a,b,d} < e iff d < c,
+// {a,c,d} < e iff d < b, {b,c,d} < e iff d < a -- and when it holds no
+// 4-hyperedge. Candidates with no 3-hyperedge besides e and no possible
+// 4-hyperedge are counted by popcount per pattern of their pairs to e (summed
+// over the warp); the others one by one. kExact: exact triple rows decide the
+// 3-hyperedges; otherwise the co-occurrence rows mark the candidates that get
+// hash probes. sub: subtract every set from the class of its pair pattern too
+// (graphlet census).
+template <bool kExact, bool kBatched>
+__global__ void __launch_bounds__(CENSUS_THREADS)
+    k_census_txw(const DevGraph g, int64_t t0, int64_t t1, const uint8_t* __restrict__ lut_g,
+                 int nmask, int ncls, int ngraphs, int sub, unsigned long long* __restrict__ hist) {
+  __shared__ unsigned long long bins[kBatched ? 1 : BIN_STRIDE];
+  __shared__ unsigned int gbins[kBatched ? MAX_GRAPHS * BIN_STRIDE : 1];
+  __shared__ uint8_t lut[2048];
+  for (int i = threadIdx.x; i < nmask; i += blockDim.x) lut[i] = lut_g[i];
+  if (kBatched) {
+    for (int i = threadIdx.x; i < ngraphs * BIN_STRIDE; i += blockDim.x) gbins[i] = 0;
+  } else {
+    for (int i = threadIdx.x; i < ncls; i += blockDim.x) bins[i] = 0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int32_t bw = g.bwords;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = t0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < t1;
+       t += warps) {
+    const int4 e = g.e3[t];
+    const int32_t a = e.x, b = e.y, c = e.z, base = graph_base(g, a);
+    const int32_t al = a - base, bl = b - base, cl = c - base;
+    const bool ab = btest(g, g.bits2, a, b), ac = btest(g, g.bits2, a, c),
+               bc = btest(g, g.bits2, b, c);
+    const bool qd = btest(g, g.bits4, a, b) && btest(g, g.bits4, a, c) &&
+                    btest(g, g.bits4, b, c);
+    const uint32_t *Ba = brow(g.bits2, bw, a), *Bb = brow(g.bits2, bw, b),
+                   *Bc = brow(g.bits2, bw, c);
+    const uint32_t* R1 = kExact ? g.tri3 + ((size_t)a * g.n + b) * bw : brow(g.bits3, bw, a);
+    const uint32_t* R2 = kExact ? g.tri3 + ((size_t)a * g.n + c) * bw : brow(g.bits3, bw, b);
+    const uint32_t* R3 = kExact ? g.tri3 + ((size_t)b * g.n + c) * bw : brow(g.bits3, bw, c);
+    unsigned int* gb = kBatched ? gbins + graph_of(g, a) * BIN_STRIDE : nullptr;
+    uint32_t n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int32_t w = lane; w < bw; w += 32) {
+      const uint32_t pa = __ldg(Ba + w), pb = __ldg(Bb + w), pc = __ldg(Bc + w);
+      uint32_t r1, r2, r3;
+      if (kExact) {
+        r1 = __ldg(R1 + w);  // abd
+        r2 = __ldg(R2 + w);  // acd
+        r3 = __ldg(R3 + w);  // bcd
+      } else {
+        const uint32_t ta = __ldg(R1 + w), tb = __ldg(R2 + w), tc = __ldg(R3 + w);
+        r1 = ta & tb;
+        r2 = ta & tc;
+        r3 = tb & tc;
+      }
+      const uint32_t self = selfbit(w, al) | selfbit(w, bl) | selfbit(w, cl);
+      const uint32_t tr = r1 | r2 | r3;
+      uint32_t z = (pa | pb | pc | tr) & ~self;
+      if (kExact) z &= ~((r1 & below(w, cl)) | (r2 & below(w, bl)) | (r3 & below(w, al)));
+      if (!z) continue;
+      const uint32_t risky = qd ? (__ldg(brow(g.bits4, bw, a) + w) & __ldg(brow(g.bits4, bw, b) + w) &
+                                   __ldg(brow(g.bits4, bw, c) + w))
+                                : 0u;
+      const uint32_t fast = z & ~tr & ~risky;
+#pragma unroll
+      for (int m = 1; m < 8; ++m)
+        n[m] += __popc(fast & ((m & 1) ? pa : ~pa) & ((m & 2) ? pb : ~pb) & ((m & 4) ? pc : ~pc));
+      uint32_t slow = z & (tr | risky);
+      while (slow) {
+        const int j = __ffs(slow) - 1;
+        slow &= slow - 1;
+        const int32_t d = base + w * 32 + j;
+        const bool ad = (pa >> j) & 1u, bd = (pb >> j) & 1u, cd = (pc >> j) & 1u;
+        bool abd, acd, bcd;
+        if (kExact) {
+          abd = (r1 >> j) & 1u;
+          acd = (r2 >> j) & 1u;
+          bcd = (r3 >> j) & 1u;
+        } else {
+          abd = ((r1 >> j) & 1u) && has_triple(g, a, b, d);
+          acd = ((r2 >> j) & 1u) && has_triple(g, a, c, d);
+          bcd = ((r3 >> j) & 1u) && has_triple(g, b, c, d);
+          if ((abd && d < c) || (acd && d < b) || (bcd && d < a)) continue;
+        }
+        if (!(ad || bd || cd || abd || acd || bcd)) continue;
+        if (((risky >> j) & 1u) && has_quad(g, a, b, c, d)) continue;
+        const uint32_t mask = (ab ? 1u : 0u) | (ac ? 2u : 0u) | (ad ? 4u : 0u) | (bc ? 8u : 0u) |
+                              (bd ? 16u : 0u) | (cd ? 32u : 0u) | 64u | (abd ? 128u : 0u) |
+                              (acd ? 256u : 0u) | (bcd ? 512u : 0u);  // a=0, b=1, c=2, d=3
+        const uint8_t c1 = lut[mask], c2 = sub ? lut[mask & 63u] : (uint8_t)0xFF;
+        if (kBatched) {
+          atomicAdd(&gb[c1], 1u);
+          if (c2 != 0xFF) atomicAdd(&gb[c2], 0u - 1u);
+        } else {
+          atomicAdd(&bins[c1], 1ull);
+          if (c2 != 0xFF) atomicAdd(&bins[c2], 0ull - 1ull);
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 1; m < 8; ++m)
+#pragma unroll
+      for (int o = 16; o; o >>= 1) n[m] += __shfl_xor_sync(0xffffffffu, n[m], o);
+    if (lane == 0) {
+      const uint32_t fixed = (ab ? 1u : 0u) | (ac ? 2u : 0u) | (bc ? 8u : 0u) | 64u;
+#pragma unroll
+      for (int m = 1; m < 8; ++m) {
+        if (!n[m]) continue;
+        const uint32_t mask =
+            fixed | ((m & 1) ? 4u : 0u) | ((m & 2) ? 16u : 0u) | ((m & 4) ? 32u : 0u);
+        const uint8_t c1 = lut[mask], c2 = sub ? lut[mask & 63u] : (uint8_t)0xFF;
+        if (kBatched) {
+          atomicAdd(&gb[c1], n[m]);
+          if (c2 != 0xFF) atomicAdd(&gb[c2], 0u - n[m]);
+        } else {
+          atomicAdd(&bins[c1], (unsigned long long)n[m]);
+          if (c2 != 0xFF) atomicAdd(&bins[c2], 0ull - (unsigned long long)n[m]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (kBatched) {
+    for (int i = threadIdx.x; i < ngraphs * BIN_STRIDE; i += blockDim.x)
+      if (gbins[i])
+        atomicAdd(&hist[(i / BIN_STRIDE) * ncls + i % BIN_STRIDE],
+                  (unsigned long long)(long long)(int)gbins[i]);
+  } else {
+    for (int i = threadIdx.x; i < ncls; i += blockDim.x)
+      if (bins[i]) atomicAdd(&hist[i], bins[i]);
+  }
+}
+
 // ---------------------------------------------------------------- work spaces
 // Candidates per anchor of up to 8 families in one pass over the anchors.
 struct WsArgs {
@@ -528,6 +663,46 @@ namespace {
 
 // One family of the census over the range [b, e) of the chosen variant's index
 // space (bits: the bit-sliced space, else the per-candidate one).
+// Bit-sliced TX over the items [b, e) of its space (whole 3-hyperedges:
+// item index = 3-hyperedge x groups + group), one warp per 3-hyperedge.
+template <bool kExact, bool kBatched>
+void launch_txw_t(const hm_graph* g, int64_t t0, int64_t t1, unsigned long long* hist,
+                  cudaStream_t s, bool traced, bool sub) {
+  const ClassTables& T = class_tables(4);
+  const uint8_t* lut = device_lut(4);
+  const int64_t warps_per_block = CENSUS_THREADS / 32;
+  int64_t blocks = (t1 - t0 + warps_per_block - 1) / warps_per_block;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (kBatched) {  // every block below 2^31 candidates (its uint32 bins)
+    const int64_t floor_blocks = (int64_t)(((uint64_t)(t1 - t0) * g->bwords * 32) >> 31) + 1;
+    if (blocks < floor_blocks) blocks = floor_blocks;
+  }
+  if (blocks < 1) blocks = 1;
+  cudaEvent_t ev = nullptr;
+  const bool tr = traced && trace_on();
+  if (tr) trace_begin(s, &ev);
+  k_census_txw<kExact, kBatched><<<(unsigned)blocks, CENSUS_THREADS, 0, s>>>(
+      g->view(), t0, t1, lut, (int)T.lut.size(), T.ncls, num_graphs(g), sub ? 1 : 0, hist);
+  HM_KCHECK();
+  if (tr) trace_end("census_TXb", s, ev);
+}
+
+void launch_txw(const hm_graph* g, uint64_t b, uint64_t e, unsigned long long* hist,
+                cudaStream_t s, bool traced, bool sub) {
+  const uint64_t groups = (uint64_t)(g->bwords / 4);
+  if (groups == 0) return;
+  if (e > g->TXb.total) e = g->TXb.total;
+  const int64_t t0 = (int64_t)(b / groups), t1 = (int64_t)((e + groups - 1) / groups);
+  if (t0 >= t1) return;
+  if (g->tri3) {
+    if (g->block) launch_txw_t<true, true>(g, t0, t1, hist, s, traced, sub);
+    else launch_txw_t<true, false>(g, t0, t1, hist, s, traced, sub);
+  } else {
+    if (g->block) launch_txw_t<false, true>(g, t0, t1, hist, s, traced, sub);
+    else launch_txw_t<false, false>(g, t0, t1, hist, s, traced, sub);
+  }
+}
+
 // sub: the set's pair pattern is subtracted too (graphlet census, TX only).
 void launch_one(const hm_graph* g, char fam, bool bits, int chunk, int order,
                 unsigned long long* hist, cudaStream_t s, uint64_t b = 0, uint64_t e = ~0ull,
@@ -558,14 +733,8 @@ void launch_one(const hm_graph* g, char fam, bool bits, int chunk, int order,
         launch_family(g, FamP{}, &g->P, g->P.total, order, hist, s, chunk, b, e, traced);
       break;
     default:
-      if (bits && g->tri3) {
-        BitsXT<true> f;
-        f.sub = sub;
-        launch_bits(g, f, g->TXb, order, hist, s, b, e, traced);
-      } else if (bits) {
-        BitsXT<false> f;
-        f.sub = sub;
-        launch_bits(g, f, g->TXb, order, hist, s, b, e, traced);
+      if (bits) {
+        launch_txw(g, b, e, hist, s, traced, sub);
       } else {
         launch_family(g, FamTX{}, &g->TX, g->TX.total, order, hist, s, chunk, b, e, traced,
                       sub ? 1 : 0);
@@ -588,12 +757,23 @@ void launch_census(const hm_graph* g, int order, unsigned long long* hist, cudaS
     // with the graphlet census, Q and TX subtract their sets from the class of
     // their pair pattern, and the graphlet launches replace S and P
     const bool gl = g->useGL;
-    launch_family(g, FamQ{}, nullptr, (uint64_t)g->counts[4], 4, hist, s, pick(0), 0, ~0ull,
-                  true, gl ? 1 : 0);
-    launch_one(g, 'X', g->useTXb, pick(g->chunkTX), 4, hist, s, 0, ~0ull, true, gl);
     if (gl) {
-      launch_graphlets(g, hist, s);
+      // four independent launches, each too small to fill the GPU, run side
+      // by side: Q, TX, the graphlet pair sums, the graphlet node-pair sums;
+      // then the finisher
+      GraphletScratch G;
+      graphlet_prepare(g, G, s);
+      Fork f(s);
+      launch_family(g, FamQ{}, nullptr, (uint64_t)g->counts[4], 4, hist, s, pick(0), 0, ~0ull,
+                    true, 1);
+      launch_one(g, 'X', g->useTXb, pick(g->chunkTX), 4, hist, f[0], 0, ~0ull, true, true);
+      graphlet_edges(g, G, f[1]);
+      graphlet_pairs(g, G, f[2]);
+      f.join();
+      graphlet_finish(g, G, hist, s);
     } else {
+      launch_family(g, FamQ{}, nullptr, (uint64_t)g->counts[4], 4, hist, s, pick(0));
+      launch_one(g, 'X', g->useTXb, pick(g->chunkTX), 4, hist, s);
       launch_one(g, 'S', g->useSb, pick(g->chunkS), 4, hist, s);
       launch_one(g, 'P', g->usePb, pick(g->chunkP), 4, hist, s);
     }

@@ -716,121 +716,5 @@ __device__ __forceinline__ uint32_t selfbit(int32_t w, int32_t t) {
   return (t >> 5) == w ? (1u << (t & 31)) : 0u;
 }
 
-// k = 4, sets whose largest hyperedges have 3 members, bit-sliced: anchor a
-// 3-hyperedge e = {a, b, c}, item one 4-word group of the rows; the fourth
-// node d runs over the group's ids joined to e by a pair or a 3-hyperedge.
-// A set is kept at its smallest 3-hyperedge: {a,b,d} < e iff d < c,
-// {a,c,d} < e iff d < b, {b,c,d} < e iff d < a (ids sorted a < b < c), and
-// when it holds no 4-hyperedge. Candidates with no 3-hyperedge besides e and
-// no possible 4-hyperedge are counted by popcount per pattern of their pairs
-// to e; the others one by one. kExact: exact triple rows decide the
-// 3-hyperedges; otherwise the co-occurrence bitmaps mark the candidates that
-// get hash probes.
-template <bool kExact>
-struct BitsXT {
-  static constexpr const char* kName = "census_TXb";
-  // subtract each counted set from the class of its pair pattern (the
-  // graphlet census counts all sets by pair pattern)
-  bool sub = false;
-  struct State {
-    uint32_t grp;
-  };
-  __device__ int32_t graph_node(const DevGraph& g, int64_t t) const { return g.e3[t].x; }
-  __device__ void begin(const DevGraph&, int64_t, uint64_t r, State& s) const {
-    s.grp = (uint32_t)r;
-  }
-  __device__ void next(State& s) const { ++s.grp; }
-  template <class Bin>
-  __device__ void item(const DevGraph& g, int64_t t, State& s, const uint8_t* lut, Bin* bins) const {
-    const int4 e = g.e3[t];
-    const int32_t a = e.x, b = e.y, c = e.z, bw = g.bwords, base = graph_base(g, a);
-    const int32_t al = a - base, bl = b - base, cl = c - base;
-    const int32_t w4 = (int32_t)s.grp * 4;
-    const bool ab = btest(g, g.bits2, a, b), ac = btest(g, g.bits2, a, c),
-               bc = btest(g, g.bits2, b, c);
-    const bool qd = btest(g, g.bits4, a, b) && btest(g, g.bits4, a, c) &&
-                    btest(g, g.bits4, b, c);
-    uint32_t ba4[4], bb4[4], bc4[4], r1[4] = {0, 0, 0, 0}, r2[4] = {0, 0, 0, 0},
-                                     r3[4] = {0, 0, 0, 0}, qa[4] = {0, 0, 0, 0},
-                                     qb[4] = {0, 0, 0, 0}, qc[4] = {0, 0, 0, 0};
-    ld4(brow(g.bits2, bw, a) + w4, ba4);
-    ld4(brow(g.bits2, bw, b) + w4, bb4);
-    ld4(brow(g.bits2, bw, c) + w4, bc4);
-    if (kExact) {
-      // rows (a,b), (a,c), (b,c) of the exact triple rows: r1/r2/r3 = abd/acd/bcd
-      ld4(g.tri3 + ((size_t)a * g.n + b) * bw + w4, r1);
-      ld4(g.tri3 + ((size_t)a * g.n + c) * bw + w4, r2);
-      ld4(g.tri3 + ((size_t)b * g.n + c) * bw + w4, r3);
-    } else {
-      // co-occurrence rows: a d that may form a 3-hyperedge with two of e
-      uint32_t ta[4], tb[4], tc[4];
-      ld4(brow(g.bits3, bw, a) + w4, ta);
-      ld4(brow(g.bits3, bw, b) + w4, tb);
-      ld4(brow(g.bits3, bw, c) + w4, tc);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        r1[k] = ta[k] & tb[k];
-        r2[k] = ta[k] & tc[k];
-        r3[k] = tb[k] & tc[k];
-      }
-    }
-    if (qd) {
-      ld4(brow(g.bits4, bw, a) + w4, qa);
-      ld4(brow(g.bits4, bw, b) + w4, qb);
-      ld4(brow(g.bits4, bw, c) + w4, qc);
-    }
-    uint32_t n[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // by (ad, bd, cd) without other triples
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int32_t w = w4 + k;
-      const uint32_t self = selfbit(w, al) | selfbit(w, bl) | selfbit(w, cl);
-      const uint32_t pa = ba4[k], pb = bb4[k], pc = bc4[k];
-      const uint32_t tr = r1[k] | r2[k] | r3[k];
-      uint32_t z = (pa | pb | pc | tr) & ~self;
-      if (kExact)
-        z &= ~((r1[k] & below(w, cl)) | (r2[k] & below(w, bl)) | (r3[k] & below(w, al)));
-      if (!z) continue;
-      const uint32_t risky = qa[k] & qb[k] & qc[k];
-      const uint32_t fast = z & ~tr & ~risky;
-#pragma unroll
-      for (int m = 1; m < 8; ++m)
-        n[m] += __popc(fast & ((m & 1) ? pa : ~pa) & ((m & 2) ? pb : ~pb) & ((m & 4) ? pc : ~pc));
-      uint32_t slow = z & (tr | risky);
-      while (slow) {
-        const int j = __ffs(slow) - 1;
-        slow &= slow - 1;
-        const int32_t d = base + w * 32 + j;
-        const bool ad = (pa >> j) & 1u, bd = (pb >> j) & 1u, cd = (pc >> j) & 1u;
-        bool abd, acd, bcd;
-        if (kExact) {
-          abd = (r1[k] >> j) & 1u;
-          acd = (r2[k] >> j) & 1u;
-          bcd = (r3[k] >> j) & 1u;
-        } else {
-          abd = ((r1[k] >> j) & 1u) && has_triple(g, a, b, d);
-          acd = ((r2[k] >> j) & 1u) && has_triple(g, a, c, d);
-          bcd = ((r3[k] >> j) & 1u) && has_triple(g, b, c, d);
-          if ((abd && d < c) || (acd && d < b) || (bcd && d < a)) continue;
-        }
-        if (!(ad || bd || cd || abd || acd || bcd)) continue;
-        if (((risky >> j) & 1u) && has_quad(g, a, b, c, d)) continue;
-        const uint32_t mask = (ab ? 1u : 0u) | (ac ? 2u : 0u) | (ad ? 4u : 0u) | (bc ? 8u : 0u) |
-                              (bd ? 16u : 0u) | (cd ? 32u : 0u) | 64u | (abd ? 128u : 0u) |
-                              (acd ? 256u : 0u) | (bcd ? 512u : 0u);  // a=0, b=1, c=2, d=3
-        atomicAdd(&bins[lut[mask]], (Bin)1);
-        if (sub && lut[mask & 63u] != 0xFF) atomicAdd(&bins[lut[mask & 63u]], (Bin)0 - (Bin)1);
-      }
-    }
-    const uint32_t fixed = (ab ? 1u : 0u) | (ac ? 2u : 0u) | (bc ? 8u : 0u) | 64u;
-#pragma unroll
-    for (int m = 1; m < 8; ++m)
-      if (n[m]) {
-        const uint32_t mask = fixed | ((m & 1) ? 4u : 0u) | ((m & 2) ? 16u : 0u) | ((m & 4) ? 32u : 0u);
-        atomicAdd(&bins[lut[mask]], (Bin)n[m]);
-        if (sub && lut[mask & 63u] != 0xFF) atomicAdd(&bins[lut[mask & 63u]], (Bin)0 - (Bin)n[m]);
-      }
-  }
-};
-
 }  // namespace fam
 }  // namespace hm

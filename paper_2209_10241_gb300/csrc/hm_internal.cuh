@@ -409,8 +409,21 @@ void free_graph(hm_graph* g);
 // census.cu
 void prepare_census(hm_graph* g, int order, cudaStream_t s);
 // graphlet.cu: the pairs-only 4-node sets of a graph with pair bitmaps, by
-// pattern, into hist (the Q and TX launches must subtract their sets)
-void launch_graphlets(const hm_graph* g, unsigned long long* hist, cudaStream_t s);
+// pattern, into hist (the Q and TX launches must subtract their sets):
+// prepare (zeroed scratch), then edges and pairs (independent of each other),
+// then finish.
+struct GraphletScratch {
+  DBuf<unsigned char> buf;
+  uint32_t* tnode = nullptr;
+  unsigned long long* agg = nullptr;
+  int ngraphs = 1;
+  int32_t per = 0;
+};
+void graphlet_prepare(const hm_graph* g, GraphletScratch& G, cudaStream_t s);
+void graphlet_edges(const hm_graph* g, GraphletScratch& G, cudaStream_t s);
+void graphlet_pairs(const hm_graph* g, GraphletScratch& G, cudaStream_t s);
+void graphlet_finish(const hm_graph* g, GraphletScratch& G, unsigned long long* hist,
+                     cudaStream_t s);
 double graphlet_cost(const hm_graph* g);
 // hist holds hm_num_classes(order) counters per graph of the union (one graph: one row)
 void launch_census(const hm_graph* g, int order, unsigned long long* hist, cudaStream_t s);
