@@ -31,17 +31,42 @@ int bits_for(int64_t maxval) {
 
 enum { ERR_RANGE = 1, ERR_OFFSETS = 2, ERR_TABLE = 4 };
 
+// column of node b in the bitmap row of node a (rows span a's block of ids)
+__device__ __forceinline__ int32_t bit_col(int32_t a, int32_t b, int32_t block, uint64_t inv) {
+  return block ? b - (int32_t)__umul64hi((uint64_t)(uint32_t)a, inv) * block : b;
+}
+
+// Dense bitmaps written while normalising (graphs with pair bitmaps): pair
+// rows, co-occurrence rows of 3- and 4-hyperedges, exact triple rows (may be
+// NULL: the 3-hyperedges then go to sort keys).
+struct BitsOut {
+  uint32_t* bits2;
+  uint32_t* bits3;
+  uint32_t* bits4;
+  uint32_t* tri3;
+  int32_t bw, block, n;
+  uint64_t inv;
+};
+
+__device__ __forceinline__ void set_bit(const BitsOut& o, uint32_t* bm, int32_t a, int32_t b) {
+  const int32_t c = bit_col(a, b, o.block, o.inv);
+  atomicOr(bm + (size_t)a * o.bw + (c >> 5), 1u << (c & 31));
+}
+
 // One thread per input hyperedge: the set of its members (sorted, repeats
-// collapsed) as long as it has at most kmax distinct members. WRITE=false
-// only counts per size; WRITE=true emits the packed sort key of each kept
-// hyperedge (members concatenated with b bits each, most significant first).
-template <bool WRITE>
+// collapsed) as long as it has at most kmax distinct members. MODE 0 only
+// counts per size; MODE 1 emits the packed sort key of each kept hyperedge
+// (members concatenated with b bits each, most significant first); MODE 2
+// sets the bitmap bits of each kept hyperedge instead (pairs, co-occurrence,
+// exact triple rows) and emits sort keys only for 4-hyperedges and, without
+// exact triple rows, 3-hyperedges.
+template <int MODE>
 __global__ void k_normalize(const int32_t* __restrict__ mem, const int64_t* __restrict__ off,
                             int64_t m, int32_t n, int kmax, int b,
                             unsigned long long* __restrict__ cnt, int* __restrict__ err,
                             uint64_t* __restrict__ c2, uint64_t* __restrict__ c3hi,
                             uint64_t* __restrict__ c3lo, uint64_t* __restrict__ c4hi,
-                            uint64_t* __restrict__ c4lo) {
+                            uint64_t* __restrict__ c4lo, const BitsOut bo) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
        j += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s0 = off[j], s1 = off[j + 1];
@@ -81,12 +106,27 @@ __global__ void k_normalize(const int32_t* __restrict__ mem, const int64_t* __re
       continue;
     }
     if (big) {
-      if (!WRITE) atomicAdd(&cnt[kmax + 1], 1ull);
+      if (MODE == 0) atomicAdd(&cnt[kmax + 1], 1ull);
       continue;
     }
     if (cntd < 2) continue;
+    if (MODE == 2) {
+      for (int i = 0; i < cntd; ++i)
+        for (int j = 0; j < cntd; ++j)
+          if (i != j)
+            set_bit(bo, cntd == 2 ? bo.bits2 : cntd == 3 ? bo.bits3 : bo.bits4, v[i], v[j]);
+      if (cntd == 3 && bo.tri3) {
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) {
+            if (i == j) continue;
+            const int32_t c = v[3 - i - j];
+            atomicOr(bo.tri3 + ((size_t)v[i] * bo.n + v[j]) * bo.bw + (c >> 5), 1u << (c & 31));
+          }
+      }
+      if (cntd == 2 || (cntd == 3 && bo.tri3)) continue;
+    }
     const unsigned long long slot = atomicAdd(&cnt[cntd], 1ull);
-    if (WRITE) {
+    if (MODE >= 1) {
       unsigned __int128 key = 0;
 #pragma unroll
       for (int i = 0; i < 4; ++i)
@@ -200,21 +240,7 @@ __global__ void k_pairpos(const uint64_t* __restrict__ e2, int64_t m, const int6
   }
 }
 
-// column of node b in the bitmap row of node a (rows span a's block of ids)
-__device__ __forceinline__ int32_t bit_col(int32_t a, int32_t b, int32_t block, uint64_t inv) {
-  return block ? b - (int32_t)__umul64hi((uint64_t)(uint32_t)a, inv) * block : b;
-}
 
-__global__ void k_bitmap(const uint64_t* __restrict__ e2, int64_t m, int32_t bw, int32_t block,
-                         uint64_t inv, uint32_t* __restrict__ bits) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    int32_t u = (int32_t)(e2[p] >> 32), v = (int32_t)(e2[p] & 0xFFFFFFFFull);
-    const int32_t cv = bit_col(u, v, block, inv), cu = bit_col(v, u, block, inv);
-    atomicOr(bits + (size_t)u * bw + (cv >> 5), 1u << (cv & 31));
-    atomicOr(bits + (size_t)v * bw + (cu >> 5), 1u << (cu & 31));
-  }
-}
 
 // Pair degrees from the bitmap rows: one warp per node.
 __global__ void k_bits_degree(const uint32_t* __restrict__ bits, int32_t n, int32_t bw,
@@ -264,38 +290,120 @@ __global__ void k_bits_adjacency(const uint32_t* __restrict__ bits, int32_t n, i
   }
 }
 
-// bits of every pair of members of each s-tuple (s = 3 or 4)
-__global__ void k_bitmap_tuples(const int4* __restrict__ e, int64_t m, int s, int32_t bw,
-                                int32_t block, uint64_t inv, uint32_t* __restrict__ bits) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int4 k = e[t];
-    const int32_t v[4] = {k.x, k.y, k.z, k.w};
-    for (int i = 0; i < s; ++i)
-      for (int j = 0; j < s; ++j)
-        if (i != j) {
-          const int32_t c = bit_col(v[i], v[j], block, inv);
-          atomicOr(bits + (size_t)v[i] * bw + (c >> 5), 1u << (c & 31));
-        }
+// E_2 from the pair rows (graphs with bitmaps): row u's ids above u are its
+// pairs (u, v), in ascending order, so the rows in order give E_2 sorted and
+// without repeats. Counts per row (one warp per row), then the pairs.
+__global__ void k_upper_counts(const uint32_t* __restrict__ bits, int32_t n, int32_t bw,
+                               int32_t block, uint64_t inv, uint64_t* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+    const int32_t ul = bit_col((int32_t)u, (int32_t)u, block, inv);
+    const uint32_t* row = bits + (size_t)u * bw;
+    uint32_t c = 0;
+    for (int32_t w = lane; w < bw; w += 32) {
+      const int32_t tw = ul >> 5;
+      const uint32_t above = w < tw ? 0u : w > tw ? ~0u : ((ul & 31) == 31 ? 0u : (~0u << ((ul & 31) + 1)));
+      c += __popc(__ldg(row + w) & above);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) cnt[u] = c;
   }
 }
 
-// exact triple rows: for 3-hyperedge {a, b, c}, bit c of rows (a, b), (b, a),
-// bit b of rows (a, c), (c, a), bit a of rows (b, c), (c, b)
-__global__ void k_tri3_rows(const int4* __restrict__ e3, int64_t m, int32_t n, int32_t bw,
-                            uint32_t* __restrict__ rows) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int4 e = e3[t];
-    const int32_t v[3] = {e.x, e.y, e.z};
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) {
-        if (i == j) continue;
-        const int32_t c = v[3 - i - j];
-        atomicOr(rows + ((size_t)v[i] * n + v[j]) * bw + (c >> 5), 1u << (c & 31));
+__global__ void k_upper_emit(const uint32_t* __restrict__ bits, int32_t n, int32_t bw,
+                             int32_t block, uint64_t inv, const uint64_t* __restrict__ off,
+                             uint64_t* __restrict__ e2) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+    const int32_t ul = bit_col((int32_t)u, (int32_t)u, block, inv);
+    const int32_t base = (int32_t)u - ul;
+    const uint32_t* row = bits + (size_t)u * bw;
+    uint64_t pos = off[u];
+    for (int32_t w0 = 0; w0 < bw; w0 += 32) {
+      const int32_t w = w0 + lane, tw = ul >> 5;
+      const uint32_t above = w < tw ? 0u : w > tw ? ~0u : ((ul & 31) == 31 ? 0u : (~0u << ((ul & 31) + 1)));
+      uint32_t word = w < bw ? (__ldg(row + w) & above) : 0u;
+      const uint32_t c = __popc(word);
+      uint32_t incl = c;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
       }
+      uint64_t p = pos + (incl - c);
+      while (word) {
+        const int j = __ffs(word) - 1;
+        word &= word - 1;
+        e2[p++] = ((uint64_t)u << 32) | (uint32_t)(base + w * 32 + j);
+      }
+      pos += __shfl_sync(0xffffffffu, incl, 31);
+    }
   }
 }
+
+// E_3 from the exact triple rows (one graph): row (a, b), a < b, holds the c
+// of the 3-hyperedges {a, b, c}; its ids above b, rows in order, give E_3
+// sorted and without repeats. One warp per row.
+__global__ void k_tri_counts(const uint32_t* __restrict__ tri3, int32_t n, int32_t bw,
+                             uint64_t* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t rows = (int64_t)n * n;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
+    const int32_t a = (int32_t)(r / n), b = (int32_t)(r - (int64_t)a * n);
+    uint32_t c = 0;
+    if (a < b) {
+      const uint32_t* row = tri3 + (size_t)r * bw;
+      for (int32_t w = lane; w < bw; w += 32) {
+        const int32_t tw = b >> 5;
+        const uint32_t above =
+            w < tw ? 0u : w > tw ? ~0u : ((b & 31) == 31 ? 0u : (~0u << ((b & 31) + 1)));
+        c += __popc(__ldg(row + w) & above);
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if (lane == 0) cnt[r] = c;
+  }
+}
+
+__global__ void k_tri_emit(const uint32_t* __restrict__ tri3, int32_t n, int32_t bw,
+                           const uint64_t* __restrict__ off, int4* __restrict__ e3) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t rows = (int64_t)n * n;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
+    const int32_t a = (int32_t)(r / n), b = (int32_t)(r - (int64_t)a * n);
+    if (a >= b || off[r + 1] == off[r]) continue;
+    const uint32_t* row = tri3 + (size_t)r * bw;
+    uint64_t pos = off[r];
+    for (int32_t w0 = 0; w0 < bw; w0 += 32) {
+      const int32_t w = w0 + lane, tw = b >> 5;
+      const uint32_t above =
+          w < tw ? 0u : w > tw ? ~0u : ((b & 31) == 31 ? 0u : (~0u << ((b & 31) + 1)));
+      uint32_t word = w < bw ? (__ldg(row + w) & above) : 0u;
+      const uint32_t c = __popc(word);
+      uint32_t incl = c;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+      }
+      uint64_t p = pos + (incl - c);
+      while (word) {
+        const int j = __ffs(word) - 1;
+        word &= word - 1;
+        e3[p++] = make_int4(a, b, w * 32 + j, -1);
+      }
+      pos += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+}
+
+
 
 __global__ void k_max_degree(const int64_t* __restrict__ off, int32_t n, int* out) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
@@ -348,9 +456,6 @@ bool use_tri3(int64_t n, int32_t block) {
   return bytes <= (64ll << 20);
 }
 
-// bytes of the kept counts written for sizes 2..kmax
-size_t nj_kept_bytes(int kmax) { return (size_t)(kmax - 1) * sizeof(uint32_t); }
-
 template <class T>
 T* keep(hm_graph* g, T* p) {
   if (p) g->owned.push_back((void*)p);
@@ -378,9 +483,9 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   unsigned long long* cnt2 = counters.p + 8;
   int* err_p = reinterpret_cast<int*>(counters.p + 16);
   if (m > 0) {
-    k_normalize<false><<<grid1d(m), T256, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt,
-                                                  err_p, nullptr, nullptr, nullptr, nullptr,
-                                                  nullptr);
+    k_normalize<0><<<grid1d(m), T256, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt, err_p,
+                                              nullptr, nullptr, nullptr, nullptr, nullptr,
+                                              BitsOut{});
     HM_KCHECK();
   }
   span_norm.end();
@@ -397,21 +502,49 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   g->counts[kmax + 1] = (int64_t)hc[kmax + 1];
 
   TraceSpan span_sort("ingest_sort_unique", s);
+  const bool bitmaps = use_bitmap(n, block ? block : n, block != 0);
+  const bool tri_rows = bitmaps && kmax >= 3 && use_tri3(n, block);
+  size_t words = 0, tw = 0;
+  BitsOut bo{};
+  if (bitmaps) {
+    // rows padded to a multiple of four words: 16-byte aligned row loads
+    g->bwords = (((block ? block : n) + 127) / 128) * 4;
+    words = (size_t)n * g->bwords;
+    if (tri_rows) tw = (size_t)n * n * g->bwords;
+    auto al = [](size_t bytes) { return (bytes + 255) & ~(size_t)255; };
+    const size_t bb = al(words * 4);
+    unsigned char* bits = keep(g, dalloc<unsigned char>(3 * bb + al(tw * 4) + 256, s));
+    HM_CUDA(cudaMemsetAsync(bits, 0, 3 * bb + al(tw * 4), s));
+    g->bits2 = reinterpret_cast<uint32_t*>(bits);
+    g->bits3 = reinterpret_cast<uint32_t*>(bits + bb);
+    g->bits4 = reinterpret_cast<uint32_t*>(bits + 2 * bb);
+    if (tw) g->tri3 = reinterpret_cast<uint32_t*>(bits + 3 * bb);
+    const hm::DevGraph gv = g->view();
+    bo = BitsOut{g->bits2, g->bits3, g->bits4, g->tri3, g->bwords, gv.block, n, gv.block_inv};
+  }
+  // Sort keys: every size without bitmaps; with bitmaps only the 4-hyperedges
+  // and, without exact triple rows, the 3-hyperedges (pairs and triples are
+  // read off the rows, sorted and without repeats by construction).
   const size_t h2n = hc[2], h3n = kmax >= 3 ? hc[3] : 0, h4n = kmax >= 4 ? hc[4] : 0;
-  DBuf<uint64_t> keys(h2n + 2 * h3n + 2 * h4n, s);
+  const size_t k2 = bitmaps ? 0 : h2n, k3 = tri_rows ? 0 : h3n;
+  DBuf<uint64_t> keys(k2 + 2 * k3 + 2 * h4n, s);
   uint64_t* c2 = keys.p;
-  uint64_t* c3hi = c2 + h2n;
-  uint64_t* c3lo = c3hi + h3n;
-  uint64_t* c4hi = c3lo + h3n;
+  uint64_t* c3hi = c2 + k2;
+  uint64_t* c3lo = c3hi + k3;
+  uint64_t* c4hi = c3lo + k3;
   uint64_t* c4lo = c4hi + h4n;
   if (m > 0) {
-    k_normalize<true><<<grid1d(m), T256, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt2,
-                                                 err_p, c2, c3hi, c3lo, c4hi, c4lo);
+    if (bitmaps)
+      k_normalize<2><<<grid1d(m), T256, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt2, err_p,
+                                                c2, c3hi, c3lo, c4hi, c4lo, bo);
+    else
+      k_normalize<1><<<grid1d(m), T256, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt2, err_p,
+                                                c2, c3hi, c3lo, c4hi, c4lo, bo);
     HM_KCHECK();
   }
-  // sort + unique per size, all sizes in one batch: the ascending order of
-  // E_s, written straight into the graph's arrays (sized for the keys before
-  // dedup) in their final layout (one synchronisation)
+  // E_2, E_3, E_4 in ascending order, written into the graph's arrays (sized
+  // for the hyperedges before dedup) in their final layout; their sizes land
+  // in kept[] (one synchronisation)
   {
     const size_t b2 = (h2n * 8 + 255) & ~(size_t)255, b3 = (h3n * 16 + 255) & ~(size_t)255;
     unsigned char* eb = keep(g, dalloc<unsigned char>(b2 + b3 + h4n * 16 + 16, s));
@@ -419,7 +552,8 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     if (h3n) g->e3 = reinterpret_cast<int4*>(eb + b2);
     if (h4n) g->e4 = reinterpret_cast<int4*>(eb + b2 + b3);
   }
-  DBuf<uint32_t> kept(3, s);
+  DBuf<uint64_t> kept(4, s);
+  HM_CUDA(cudaMemsetAsync(kept.p, 0, 4 * sizeof(uint64_t), s));
   {
     SortJob jobs[3];
     int nj = 0;
@@ -442,20 +576,52 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
       J.unpack = unpack;
       J.member_bits = b;
       J.out = out;
-      J.d_kept = kept.p + (size - 2);
+      // the count, 32 bits, into the low half of a zeroed 64-bit slot
+      J.d_kept = reinterpret_cast<uint32_t*>(kept.p + (size - 2));
       ++nj;
     };
-    add(c2, nullptr, (int64_t)h2n, 2, SortJob::PAIR, g->e2);
-    if (kmax >= 3) add(c3lo, c3hi, (int64_t)h3n, 3, SortJob::TRIPLE, g->e3);
+    if (!bitmaps) add(c2, nullptr, (int64_t)h2n, 2, SortJob::PAIR, g->e2);
+    if (kmax >= 3 && !tri_rows) add(c3lo, c3hi, (int64_t)h3n, 3, SortJob::TRIPLE, g->e3);
     if (kmax >= 4) add(c4lo, c4hi, (int64_t)h4n, 4, SortJob::QUAD, g->e4);
-    sort_batch(jobs, nj, s);
+    if (bitmaps) {
+      // pair rows -> E_2 (f[0]), exact triple rows -> E_3 (f[1]), sorts (s)
+      const size_t rows3 = tri_rows ? (size_t)n * n : 0;
+      DBuf<uint64_t> rc(((size_t)n + 1) + (tri_rows ? rows3 + 1 : 0), s);
+      uint64_t* rc2 = rc.p;
+      uint64_t* rc3 = rc.p + n + 1;
+      Fork f(s);
+      const hm::DevGraph gv = g->view();
+      k_upper_counts<<<grid1d((int64_t)n * 32), T256, 0, f[0]>>>(g->bits2, n, g->bwords,
+                                                                 gv.block, gv.block_inv, rc2);
+      HM_KCHECK();
+      ScanJob sj{rc2, n, kept.p};
+      scan_batch_inplace(&sj, 1, f[0]);
+      k_upper_emit<<<grid1d((int64_t)n * 32), T256, 0, f[0]>>>(g->bits2, n, g->bwords, gv.block,
+                                                               gv.block_inv, rc2, g->e2);
+      HM_KCHECK();
+      if (tri_rows) {
+        k_tri_counts<<<grid1d((int64_t)rows3 * 32), T256, 0, f[1]>>>(g->tri3, n, g->bwords, rc3);
+        HM_KCHECK();
+        ScanJob tj{rc3, (int64_t)rows3, kept.p + 1};
+        scan_batch_inplace(&tj, 1, f[1]);
+        if (h3n) {
+          k_tri_emit<<<grid1d((int64_t)rows3 * 32), T256, 0, f[1]>>>(g->tri3, n, g->bwords, rc3,
+                                                                     g->e3);
+          HM_KCHECK();
+        }
+      }
+      if (nj) sort_batch(jobs, nj, s);
+      f.join();
+    } else {
+      sort_batch(jobs, nj, s);
+    }
   }
   span_sort.end();
-  uint32_t* hk = reinterpret_cast<uint32_t*>(pin + 32);
-  hk[0] = hk[1] = hk[2] = 0;
-  HM_CUDA(cudaMemcpyAsync(hk, kept.p, nj_kept_bytes(kmax), cudaMemcpyDeviceToHost, s));
+  uint64_t* hk = pin + 32;
+  HM_CUDA(cudaMemcpyAsync(hk, kept.p, 3 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   HM_CUDA(cudaStreamSynchronize(s));
-  const int64_t m2 = hk[0], m3 = kmax >= 3 ? hk[1] : 0, m4 = kmax >= 4 ? hk[2] : 0;
+  const int64_t m2 = (int64_t)hk[0], m3 = kmax >= 3 ? (int64_t)hk[1] : 0,
+                m4 = kmax >= 4 ? (int64_t)hk[2] : 0;
   g->counts[2] = m2;
   if (kmax >= 3) g->counts[3] = m3;
   if (kmax >= 4) g->counts[4] = m4;
@@ -470,17 +636,9 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   g->h2_mask = cap2 - 1;
   g->h3_mask = cap3 ? cap3 - 1 : 0;
   g->h4_mask = cap4 ? cap4 - 1 : 0;
-  const bool bitmaps = use_bitmap(n, block ? block : n, block != 0);
-  size_t words = 0, tw = 0;
-  if (bitmaps) {
-    // rows padded to a multiple of four words: 16-byte aligned row loads
-    g->bwords = (((block ? block : n) + 127) / 128) * 4;
-    words = (size_t)n * g->bwords;
-    if (use_tri3(n, block)) tw = (size_t)n * n * g->bwords;
-  }
   // One allocation for the graph's structures, laid out so that two memsets
   // initialise them: the hash tables (empty = all ones), then the regions that
-  // start at zero (bitmaps, triple rows, triple offsets), then the rest.
+  // start at zero (triple offsets), then the rest.
   {
     auto al = [](size_t bytes) { return (bytes + 255) & ~(size_t)255; };
     size_t o = 0;
@@ -491,14 +649,6 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     const size_t o_h4 = o;
     o += al(cap4 * 16);
     const size_t ff_end = o;
-    const size_t o_b2 = o;
-    o += al(words * 4);
-    const size_t o_b3 = o;
-    o += al(words * 4);
-    const size_t o_b4 = o;
-    o += al(words * 4);
-    const size_t o_t3 = o;
-    o += al(tw * 4);
     const size_t o_off3 = o;
     o += al(((size_t)n + 1) * 8);
     const size_t zero_end = o;
@@ -514,12 +664,6 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     g->h2 = reinterpret_cast<uint64_t*>(arena + o_h2);
     if (m3) g->h3 = reinterpret_cast<int4*>(arena + o_h3);
     if (m4) g->h4 = reinterpret_cast<int4*>(arena + o_h4);
-    if (bitmaps) {
-      g->bits2 = reinterpret_cast<uint32_t*>(arena + o_b2);
-      g->bits3 = reinterpret_cast<uint32_t*>(arena + o_b3);
-      g->bits4 = reinterpret_cast<uint32_t*>(arena + o_b4);
-      if (tw) g->tri3 = reinterpret_cast<uint32_t*>(arena + o_t3);
-    }
     g->off3 = reinterpret_cast<int64_t*>(arena + o_off3);
     g->off2 = reinterpret_cast<int64_t*>(arena + o_off2);
     g->adj2 = reinterpret_cast<int32_t*>(arena + o_adj2);
@@ -554,11 +698,6 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     // read off the pair bitmap where there is one, else a stable sort
     if (bitmaps) {
       const hm::DevGraph gv = g->view();
-      if (m2) {
-        k_bitmap<<<grid1d(m2), T256, 0, f[0]>>>(g->e2, m2, g->bwords, gv.block, gv.block_inv,
-                                                g->bits2);
-        HM_KCHECK();
-      }
       k_bits_degree<<<grid1d((int64_t)n * 32), T256, 0, f[0]>>>(g->bits2, n, g->bwords,
                                                                  pdeg);
       HM_KCHECK();
@@ -590,24 +729,6 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
       k_low_bits<<<grid1d(3 * m3), T256, 0, f[1]>>>(tkeys, 3 * m3, tb, g->inc3);
       HM_KCHECK();
       csr_offsets(tkeys, 3 * m3, tb, n, g->off3, f[1]);
-    }
-    // dense bitmaps
-    if (bitmaps) {
-      const hm::DevGraph gv = g->view();
-      if (m3) {
-        k_bitmap_tuples<<<grid1d(m3), T256, 0, f[2]>>>(g->e3, m3, 3, g->bwords, gv.block,
-                                                       gv.block_inv, g->bits3);
-        HM_KCHECK();
-      }
-      if (m4) {
-        k_bitmap_tuples<<<grid1d(m4), T256, 0, f[2]>>>(g->e4, m4, 4, g->bwords, gv.block,
-                                                       gv.block_inv, g->bits4);
-        HM_KCHECK();
-      }
-      if (g->tri3 && m3) {
-        k_tri3_rows<<<grid1d(m3), T256, 0, f[2]>>>(g->e3, m3, n, g->bwords, g->tri3);
-        HM_KCHECK();
-      }
     }
     f.join();
   }

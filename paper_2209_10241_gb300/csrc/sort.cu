@@ -102,6 +102,40 @@ __device__ uint64_t look_back(const uint64_t* status, int64_t tile, int stride, 
   return excl;
 }
 
+// Warp-wide look-back for one status word per tile (stride 1): lanes read the
+// 32 tiles before the window's end at once; the sum of their aggregates up to
+// the nearest inclusive prefix is the tile's exclusive prefix. All 32 lanes of
+// the calling warp must call it; every lane gets the result. Bounded like
+// look_back.
+__device__ uint64_t look_back_warp(const uint64_t* status, int64_t tile) {
+  const int lane = threadIdx.x & 31;
+  uint64_t excl = 0;
+  int64_t end = tile;  // window: tiles [end - 32, end)
+  uint32_t spins = 0;
+  while (end > 0) {
+    const int64_t j = end - 1 - lane;
+    uint64_t v = j >= 0 ? ld_status(status + j) : ST_PREFIX;  // before tile 0: prefix 0
+    // wait until every tile of the window has published something
+    while (__any_sync(0xffffffffu, (v & ~ST_VALUE) == 0)) {
+      if (++spins > SPIN_LIMIT) {  // cannot happen with in-order tile tickets
+        if (lane == 0) atomicAdd(&g_wait_timeouts, 1u);
+        return __shfl_sync(0xffffffffu, excl, 0);
+      }
+      if ((v & ~ST_VALUE) == 0) v = ld_status(status + j);
+    }
+    // nearest inclusive prefix in the window (lowest lane = highest tile)
+    const unsigned pre = __ballot_sync(0xffffffffu, (v & ST_PREFIX) != 0);
+    const int stop = pre ? __ffs(pre) - 1 : 32;
+    uint64_t mine = lane <= stop && j >= 0 ? (v & ST_VALUE) : 0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    excl += mine;
+    if (pre) break;
+    end -= 32;
+  }
+  return excl;
+}
+
 // Histograms of all passes of all jobs; the last block to finish turns them
 // into exclusive digit offsets (one warp per (job, pass)) and writes 0 kept
 // keys for empty unique jobs.
@@ -282,17 +316,19 @@ __global__ void __launch_bounds__(TPB) k_sort_unique(const Batch B, const Grid G
     before += w < warp ? wtot[w] : 0u;
     total += wtot[w];
   }
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
     uint64_t excl = 0;
     if (tile == 0) {
-      st_status(J.ustatus, ST_PREFIX | total);
+      if (threadIdx.x == 0) st_status(J.ustatus, ST_PREFIX | total);
     } else {
-      st_status(J.ustatus + tile, ST_AGG | total);
-      excl = look_back(J.ustatus, tile, 1, 0);
-      st_status(J.ustatus + tile, ST_PREFIX | (excl + total));
+      if (threadIdx.x == 0) st_status(J.ustatus + tile, ST_AGG | total);
+      excl = look_back_warp(J.ustatus, tile);
+      if (threadIdx.x == 0) st_status(J.ustatus + tile, ST_PREFIX | (excl + total));
     }
-    tile_excl = excl;
-    if (tile == J.tiles - 1 && J.d_kept) *J.d_kept = (uint32_t)(excl + total);
+    if (threadIdx.x == 0) {
+      tile_excl = excl;
+      if (tile == J.tiles - 1 && J.d_kept) *J.d_kept = (uint32_t)(excl + total);
+    }
   }
   __syncthreads();
   uint64_t pos = tile_excl + before + incl - cnt;
@@ -310,6 +346,150 @@ __global__ void __launch_bounds__(TPB) k_sort_unique(const Batch B, const Grid G
       static_cast<uint64_t*>(J.out)[pos] = ((ka >> mb) << 32) | (ka & mask);
     } else {
       // members most significant first: the last member in the lowest bits
+      unsigned __int128 key = ((unsigned __int128)kb << 64) | ka;
+      const int32_t m3 = (int32_t)((uint64_t)key & mask);
+      key >>= mb;
+      const int32_t m2 = (int32_t)((uint64_t)key & mask);
+      key >>= mb;
+      const int32_t m1 = (int32_t)((uint64_t)key & mask);
+      key >>= mb;
+      const int32_t m0 = (int32_t)((uint64_t)key & mask);
+      static_cast<int4*>(J.out)[pos] = J.unpack == SortJob::TRIPLE
+                                           ? make_int4(m1, m2, m3, -1)
+                                           : make_int4(m0, m1, m2, m3);
+    }
+    ++pos;
+  }
+}
+
+// A job of at most one tile (TILE keys), sorted, deduplicated and written out
+// by one block in one launch: the keys stay in shared memory, every pass ranks
+// them as k_sort_pass does, and the digit offsets come from the block's own
+// counts. One block per job of the batch given in `which`.
+__global__ void __launch_bounds__(TPB) k_sort_small(const Batch B, const Grid G) {
+  __shared__ uint64_t ka_s[TILE], kb_s[TILE];
+  __shared__ uint32_t wcnt[TPB / 32][256];
+  __shared__ uint32_t dbase[256];
+  __shared__ uint32_t wtot[TPB / 32];
+  const JobDev& J = B.j[G.job[blockIdx.x]];
+  const int64_t n = J.n;
+  const bool has_b = J.b[0] != nullptr;
+  for (int i = threadIdx.x; i < TILE; i += TPB) {
+    ka_s[i] = i < n ? J.a[0][i] : 0;
+    kb_s[i] = (has_b && i < n) ? J.b[0][i] : 0;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int p = 0; p < J.np; ++p) {
+    const int shift = J.shift[p];
+    const bool on_b = J.arr[p] != 0;
+    for (int i = threadIdx.x; i < (TPB / 32) * 256; i += TPB) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    uint32_t dig[IPT], rank[IPT];
+    uint64_t ka[IPT], kb[IPT];
+#pragma unroll
+    for (int it = 0; it < IPT; ++it) {
+      const int idx = warp * (32 * IPT) + it * 32 + lane;
+      ka[it] = ka_s[idx];
+      kb[it] = kb_s[idx];
+      const bool valid = idx < n;
+      const uint32_t d = valid ? (uint32_t)(((on_b ? kb[it] : ka[it]) >> shift) & 255u) : 256u;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t before = valid ? wcnt[warp][d] : 0u;
+      __syncwarp();
+      if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = before + __popc(peers);
+      __syncwarp();
+      dig[it] = d;
+      rank[it] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    {
+      // digit totals over the warps, then their exclusive prefix over digits
+      const int d = threadIdx.x;
+      uint32_t run = 0;
+#pragma unroll
+      for (int w = 0; w < TPB / 32; ++w) {
+        const uint32_t c = wcnt[w][d];
+        wcnt[w][d] = run;
+        run += c;
+      }
+      uint32_t incl = run;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (lane == 31) wtot[warp] = incl;
+      __syncthreads();
+      uint32_t before = 0;
+      for (int w = 0; w < warp; ++w) before += wtot[w];
+      dbase[d] = before + incl - run;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < IPT; ++it) {
+      const int idx = warp * (32 * IPT) + it * 32 + lane;
+      if (idx < n) {
+        const uint32_t d = dig[it];
+        const uint32_t pos = dbase[d] + wcnt[warp][d] + rank[it];
+        ka_s[pos] = ka[it];
+        kb_s[pos] = kb[it];
+      }
+    }
+    __syncthreads();
+  }
+  if (!J.unique) {
+    for (int i = threadIdx.x; i < n; i += TPB) {
+      J.a[0][i] = ka_s[i];
+      if (has_b) J.b[0][i] = kb_s[i];
+    }
+    return;
+  }
+  // unique: a key is kept when it differs from its predecessor; thread t owns
+  // keys [t * IPT, (t + 1) * IPT)
+  const int i0 = threadIdx.x * IPT;
+  uint32_t keep = 0, cnt = 0;
+#pragma unroll
+  for (int it = 0; it < IPT; ++it) {
+    const int i = i0 + it;
+    if (i < n) {
+      bool k = i == 0 || ka_s[i] != ka_s[i - 1];
+      if (!k && J.b_is_key && has_b) k = kb_s[i] != kb_s[i - 1];
+      if (k) {
+        keep |= 1u << it;
+        ++cnt;
+      }
+    }
+  }
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  __syncthreads();
+  if (lane == 31) wtot[warp] = incl;
+  __syncthreads();
+  uint32_t before = 0, total = 0;
+  for (int w = 0; w < TPB / 32; ++w) {
+    before += w < warp ? wtot[w] : 0u;
+    total += wtot[w];
+  }
+  if (threadIdx.x == 0 && J.d_kept) *J.d_kept = total;
+  uint64_t pos = before + incl - cnt;
+  const int mb = J.member_bits;
+  const uint64_t mask = (1ull << mb) - 1;
+#pragma unroll
+  for (int it = 0; it < IPT; ++it) {
+    if (!((keep >> it) & 1u)) continue;
+    const int i = i0 + it;
+    const uint64_t ka = ka_s[i], kb = kb_s[i];
+    if (J.unpack == SortJob::RAW) {
+      static_cast<uint64_t*>(J.out)[pos] = ka;
+      if (J.out_b) J.out_b[pos] = kb;
+    } else if (J.unpack == SortJob::PAIR) {
+      static_cast<uint64_t*>(J.out)[pos] = ((ka >> mb) << 32) | (ka & mask);
+    } else {
       unsigned __int128 key = ((unsigned __int128)kb << 64) | ka;
       const int32_t m3 = (int32_t)((uint64_t)key & mask);
       key >>= mb;
@@ -396,13 +576,24 @@ void sort_batch(const SortJob* jobs, int njobs, cudaStream_t s) {
   }
   uint32_t* done = reinterpret_cast<uint32_t*>(base + zbytes - 256);
   HM_CUDA(cudaMemsetAsync(base, 0, zbytes, s));
+  // jobs of one tile: one block each, everything in one launch
+  auto small = [&](int k) { return B.j[k].n >= 1 && B.j[k].tiles == 1; };
+  {
+    Grid G{};
+    for (int k = 0; k < njobs; ++k)
+      if (small(k)) G.job[G.nj++] = k;
+    if (G.nj) {
+      k_sort_small<<<(unsigned)G.nj, TPB, 0, s>>>(B, G);
+      HM_KCHECK();
+    }
+  }
 
   // histograms (at least one block, for the offsets and empty jobs)
   {
     Grid G{};
     int64_t blocks = 0;
     for (int k = 0; k < njobs; ++k) {
-      if (B.j[k].np == 0) continue;
+      if (B.j[k].np == 0 || small(k)) continue;
       int64_t hb = (B.j[k].n + 4095) / 4096;
       if (hb > 152 * 2) hb = 152 * 2;
       G.job[G.nj] = k;
@@ -411,16 +602,21 @@ void sort_batch(const SortJob* jobs, int njobs, cudaStream_t s) {
       ++G.nj;
     }
     G.first[G.nj] = blocks;
-    k_sort_hist<<<(unsigned)(blocks > 0 ? blocks : 1), TPB, 0, s>>>(B, G, done);
-    HM_KCHECK();
+    bool empty_unique = false;
+    for (int k = 0; k < njobs; ++k) empty_unique |= B.j[k].unique && B.j[k].n == 0;
+    if (blocks > 0 || empty_unique) {
+      k_sort_hist<<<(unsigned)(blocks > 0 ? blocks : 1), TPB, 0, s>>>(B, G, done);
+      HM_KCHECK();
+    }
   }
   int maxp = 0;
-  for (int k = 0; k < njobs; ++k) maxp = std::max(maxp, B.j[k].np);
+  for (int k = 0; k < njobs; ++k)
+    if (!small(k)) maxp = std::max(maxp, B.j[k].np);
   for (int p = 0; p < maxp; ++p) {
     Grid G{};
     int64_t blocks = 0;
     for (int k = 0; k < njobs; ++k) {
-      if (B.j[k].np <= p) continue;
+      if (B.j[k].np <= p || small(k)) continue;
       G.job[G.nj] = k;
       G.on_b[G.nj] = B.j[k].arr[p];
       G.shift[G.nj] = B.j[k].shift[p];
@@ -436,7 +632,7 @@ void sort_batch(const SortJob* jobs, int njobs, cudaStream_t s) {
     Grid G{};
     int64_t blocks = 0;
     for (int k = 0; k < njobs; ++k) {
-      if (!B.j[k].unique || B.j[k].n == 0) continue;
+      if (!B.j[k].unique || B.j[k].n == 0 || small(k)) continue;
       G.job[G.nj] = k;
       G.first[G.nj] = blocks;
       blocks += B.j[k].tiles;
@@ -451,7 +647,7 @@ void sort_batch(const SortJob* jobs, int njobs, cudaStream_t s) {
   // sort-only jobs whose last pass ended in the temporaries: copy back
   for (int k = 0; k < njobs; ++k) {
     const JobDev& J = B.j[k];
-    if (J.unique || (J.np & 1) == 0) continue;
+    if (J.unique || (J.np & 1) == 0 || small(k)) continue;
     HM_CUDA(cudaMemcpyAsync(J.a[0], J.a[1], J.n * 8, cudaMemcpyDeviceToDevice, s));
     if (J.b[0]) HM_CUDA(cudaMemcpyAsync(J.b[0], J.b[1], J.n * 8, cudaMemcpyDeviceToDevice, s));
   }
@@ -560,19 +756,21 @@ __global__ void __launch_bounds__(TPB) k_scan_batch(const ScanBatch B) {
     before += w < warp ? wtot[w] : 0ull;
     total += wtot[w];
   }
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
     uint64_t excl = 0;
     if (tile == 0) {
-      st_status(J.status, ST_PREFIX | total);
+      if (threadIdx.x == 0) st_status(J.status, ST_PREFIX | total);
     } else {
-      st_status(J.status + tile, ST_AGG | total);
-      excl = look_back(J.status, tile, 1, 0);
-      st_status(J.status + tile, ST_PREFIX | (excl + total));
+      if (threadIdx.x == 0) st_status(J.status + tile, ST_AGG | total);
+      excl = look_back_warp(J.status, tile);
+      if (threadIdx.x == 0) st_status(J.status + tile, ST_PREFIX | (excl + total));
     }
-    tile_excl = excl;
-    if (tile == J.tiles - 1) {
-      J.a[J.n] = excl + total;
-      if (J.total) *J.total = excl + total;
+    if (threadIdx.x == 0) {
+      tile_excl = excl;
+      if (tile == J.tiles - 1) {
+        J.a[J.n] = excl + total;
+        if (J.total) *J.total = excl + total;
+      }
     }
   }
   __syncthreads();
