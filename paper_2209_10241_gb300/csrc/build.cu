@@ -144,48 +144,75 @@ __global__ void k_normalize(const int32_t* __restrict__ mem, const int64_t* __re
   }
 }
 
-__global__ void k_insert2(const uint64_t* __restrict__ e2, int64_t m, uint64_t* table,
-                          uint64_t mask, int* err) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t key = e2[i];
-    uint64_t slot = hash_pair(key) & mask;
-    bool done = false;
-    for (uint64_t it = 0; it <= mask; ++it) {
-      unsigned long long old =
-          atomicCAS((unsigned long long*)(table + slot), (unsigned long long)EMPTY64,
-                    (unsigned long long)key);
-      if (old == EMPTY64) {
-        done = true;
-        break;
-      }
-      slot = (slot + 1) & mask;
-    }
-    if (!done) atomicOr(err, ERR_TABLE);
+__device__ __forceinline__ void insert_pair(uint64_t key, uint64_t* table, uint64_t mask,
+                                            int* err) {
+  uint64_t slot = hash_pair(key) & mask;
+  for (uint64_t it = 0; it <= mask; ++it) {
+    const unsigned long long old = atomicCAS((unsigned long long*)(table + slot),
+                                             (unsigned long long)EMPTY64, (unsigned long long)key);
+    if (old == EMPTY64) return;
+    slot = (slot + 1) & mask;
   }
+  atomicOr(err, ERR_TABLE);
 }
 
 // Keys are distinct, so a slot is claimed by a CAS on its first 8 bytes and
 // the second half is then stored plainly; probes run in later kernels.
-__global__ void k_insert4(const int4* __restrict__ e, int64_t m, int4* table, uint64_t mask,
-                          int* err) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int4 k = e[i];
-    uint64_t slot = hash_tuple(k.x, k.y, k.z, k.w) & mask;
-    const unsigned long long first = (uint64_t)(uint32_t)k.x | ((uint64_t)(uint32_t)k.y << 32);
-    const unsigned long long second = (uint64_t)(uint32_t)k.z | ((uint64_t)(uint32_t)k.w << 32);
-    bool done = false;
-    for (uint64_t it = 0; it <= mask; ++it) {
-      unsigned long long* w = (unsigned long long*)(table + slot);
-      if (atomicCAS(w, (unsigned long long)EMPTY64, first) == EMPTY64) {
-        w[1] = second;
-        done = true;
-        break;
-      }
-      slot = (slot + 1) & mask;
+__device__ __forceinline__ void insert_tuple(int4 k, int4* table, uint64_t mask, int* err) {
+  uint64_t slot = hash_tuple(k.x, k.y, k.z, k.w) & mask;
+  const unsigned long long first = (uint64_t)(uint32_t)k.x | ((uint64_t)(uint32_t)k.y << 32);
+  const unsigned long long second = (uint64_t)(uint32_t)k.z | ((uint64_t)(uint32_t)k.w << 32);
+  for (uint64_t it = 0; it <= mask; ++it) {
+    unsigned long long* w = (unsigned long long*)(table + slot);
+    if (atomicCAS(w, (unsigned long long)EMPTY64, first) == EMPTY64) {
+      w[1] = second;
+      return;
     }
-    if (!done) atomicOr(err, ERR_TABLE);
+    slot = (slot + 1) & mask;
+  }
+  atomicOr(err, ERR_TABLE);
+}
+
+// The three hash sets in one launch: thread i inserts pair i, then 3- and
+// 4-hyperedges after the pairs.
+__global__ void k_insert_all(const uint64_t* __restrict__ e2, int64_t m2, const int4* __restrict__ e3,
+                             int64_t m3, const int4* __restrict__ e4, int64_t m4, uint64_t* h2,
+                             uint64_t mask2, int4* h3, uint64_t mask3, int4* h4, uint64_t mask4,
+                             int* err) {
+  const int64_t total = m2 + m3 + m4;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < m2)
+      insert_pair(e2[i], h2, mask2, err);
+    else if (i < m2 + m3)
+      insert_tuple(e3[i - m2], h3, mask3, err);
+    else
+      insert_tuple(e4[i - m2 - m3], h4, mask4, err);
+  }
+}
+
+// Triple incidence lists by counting and placement: counts of 3-hyperedges
+// per node, then each 3-hyperedge placed at its members' cursors. The order
+// within a list is that of the atomic cursors; every user of the lists
+// (candidate generation, features, contributions) only enumerates them.
+__global__ void k_deg3(const int4* __restrict__ e3, int64_t m, uint64_t* __restrict__ deg) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int4 e = e3[t];
+    atomicAdd((unsigned long long*)&deg[e.x], 1ull);
+    atomicAdd((unsigned long long*)&deg[e.y], 1ull);
+    atomicAdd((unsigned long long*)&deg[e.z], 1ull);
+  }
+}
+
+__global__ void k_place3(const int4* __restrict__ e3, int64_t m, const int64_t* __restrict__ off,
+                         uint32_t* __restrict__ cursor, int32_t* __restrict__ inc) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int4 e = e3[t];
+    inc[off[e.x] + atomicAdd(&cursor[e.x], 1u)] = (int32_t)t;
+    inc[off[e.y] + atomicAdd(&cursor[e.y], 1u)] = (int32_t)t;
+    inc[off[e.z] + atomicAdd(&cursor[e.z], 1u)] = (int32_t)t;
   }
 }
 
@@ -205,17 +232,6 @@ __global__ void k_low_bits(const uint64_t* __restrict__ keys, int64_t m, int b,
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (int32_t)(keys[i] & mask);
-}
-
-__global__ void k_triple_incidence(const int4* __restrict__ e3, int64_t m, int tb,
-                                   uint64_t* __restrict__ keys) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int4 e = e3[t];
-    keys[3 * t] = ((uint64_t)e.x << tb) | (uint64_t)t;
-    keys[3 * t + 1] = ((uint64_t)e.y << tb) | (uint64_t)t;
-    keys[3 * t + 2] = ((uint64_t)e.z << tb) | (uint64_t)t;
-  }
 }
 
 __device__ int32_t find_pos(const int32_t* __restrict__ a, int64_t lo, int64_t hi, int32_t x) {
@@ -672,26 +688,23 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     HM_CUDA(cudaMemsetAsync(arena, 0xFF, ff_end, s));
     HM_CUDA(cudaMemsetAsync(arena + ff_end, 0, zero_end - ff_end, s));
   }
-  // temporaries of the chains: directed pair keys, triple incidence keys, degrees
-  const size_t np_keys = bitmaps ? 0 : 2 * m2, nt_keys = 3 * m3, n_deg = bitmaps ? n : 0;
-  DBuf<uint64_t> chain_tmp(np_keys + nt_keys + n_deg, s);
+  // temporaries of the chains: directed pair keys, pair degrees; the triple
+  // cursors (zeroed) and the maximum pair degree
+  const size_t np_keys = bitmaps ? 0 : 2 * m2, n_deg = bitmaps ? n : 0;
+  DBuf<uint64_t> chain_tmp(np_keys + n_deg + ((size_t)n + 1) / 2 + 1, s);
   uint64_t* pkeys = chain_tmp.p;
-  uint64_t* tkeys = chain_tmp.p + np_keys;
-  uint64_t* pdeg = chain_tmp.p + np_keys + nt_keys;
-  const int tb = bits_for(m3);
+  uint64_t* pdeg = chain_tmp.p + np_keys;
+  uint32_t* cursor3 = reinterpret_cast<uint32_t*>(chain_tmp.p + np_keys + n_deg);
+  int* mx_p = reinterpret_cast<int*>(cursor3 + n);
+  HM_CUDA(cudaMemsetAsync(cursor3, 0, ((size_t)n + 1) * sizeof(uint32_t), s));
+
   {
     Fork f(s);
-    // hash sets (load <= 0.5)
-    if (m2) {
-      k_insert2<<<grid1d(m2), T256, 0, s>>>(g->e2, m2, g->h2, g->h2_mask, err_p);
-      HM_KCHECK();
-    }
-    if (m3) {
-      k_insert4<<<grid1d(m3), T256, 0, s>>>(g->e3, m3, g->h3, g->h3_mask, err_p);
-      HM_KCHECK();
-    }
-    if (m4) {
-      k_insert4<<<grid1d(m4), T256, 0, s>>>(g->e4, m4, g->h4, g->h4_mask, err_p);
+    // hash sets (load <= 0.5), all sizes in one launch
+    if (m2 + m3 + m4) {
+      k_insert_all<<<grid1d(m2 + m3 + m4), T256, 0, s>>>(g->e2, m2, g->e3, m3, g->e4, m4, g->h2,
+                                                         g->h2_mask, g->h3, g->h3_mask, g->h4,
+                                                         g->h4_mask, err_p);
       HM_KCHECK();
     }
     // CSR of pair neighbours, sorted, and the position of each pair in it:
@@ -720,15 +733,16 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
       k_pairpos<<<grid1d(m2), T256, 0, f[0]>>>(g->e2, m2, g->off2, g->adj2, g->pairpos);
       HM_KCHECK();
     }
-    // CSR of triple incidence, ascending triple index
+    k_max_degree<<<grid1d(n), T256, 0, f[0]>>>(g->off2, n, mx_p);
+    HM_KCHECK();
+    // triple incidence lists: counts (into off3, zeroed), offsets, placement
     if (m3) {
-      k_triple_incidence<<<grid1d(m3), T256, 0, f[1]>>>(g->e3, m3, tb, tkeys);
+      k_deg3<<<grid1d(m3), T256, 0, f[1]>>>(g->e3, m3, reinterpret_cast<uint64_t*>(g->off3));
       HM_KCHECK();
-      // stable by node only: keys are generated in ascending triple index
-      radix_sort_u64(tkeys, nullptr, 3 * m3, b, f[1], tb);
-      k_low_bits<<<grid1d(3 * m3), T256, 0, f[1]>>>(tkeys, 3 * m3, tb, g->inc3);
+      ScanJob oj{reinterpret_cast<uint64_t*>(g->off3), n, nullptr};
+      scan_batch_inplace(&oj, 1, f[1]);
+      k_place3<<<grid1d(m3), T256, 0, f[1]>>>(g->e3, m3, g->off3, cursor3, g->inc3);
       HM_KCHECK();
-      csr_offsets(tkeys, 3 * m3, tb, n, g->off3, f[1]);
     }
     f.join();
   }
@@ -736,15 +750,11 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   // the census work spaces of max_order, ready before the final
   // synchronisation (a census then starts without one)
   PendingSpaces pend;
-  DBuf<int> mx(1, s);
-  HM_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(int), s));
-  k_max_degree<<<grid1d(n), T256, 0, s>>>(g->off2, n, mx.p);
-  HM_KCHECK();
   spaces_enqueue(g, census_spaces(g, kmax), s, pend);
   unsigned* tail = reinterpret_cast<unsigned*>(pin + 40);  // max degree, error word
   unsigned* timeouts = reinterpret_cast<unsigned*>(pin + 80);
   try {
-    HM_CUDA(cudaMemcpyAsync(tail, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaMemcpyAsync(tail, mx_p, sizeof(int), cudaMemcpyDeviceToHost, s));
     HM_CUDA(cudaMemcpyAsync(tail + 1, err_p, sizeof(int), cudaMemcpyDeviceToHost, s));
     wait_timeouts_async(timeouts, s);
     HM_CUDA(cudaStreamSynchronize(s));
