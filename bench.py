@@ -36,19 +36,20 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # workload (ncu: a few MB of DRAM traffic per launch), so they are bound by
 # the integer/logic (ALU) pipe: peak = SMs x 64 int32 lanes per clock x SM clock. Achieved =
 # work units of one launch x ALU lane-operations per unit (measured with ncu
-# on this workload, `profiles/`) / event-timed launch duration.
+# on this workload) / event-timed launch duration.
 SMS = 152
 ALU_LANES_PER_SM_CLK = 64
 # kernel -> (unit, ALU lane-ops per unit, DRAM bytes per launch); None = not measured
-# (ops = sm__sass_thread_inst_executed_op_{integer,bit}_pred_on per unit, profiles/census_bits_f2f-330.md)
+# (ops = sm__sass_thread_inst_executed_op_{integer,bit}_pred_on per unit, measured by ncu on this
+# workload; traffic = dram__bytes_read.sum + dram__bytes_write.sum of the same capture)
 ROOFLINE = {
+    "census_gl_edges": ("pair", 2508.6, 137_000),
+    "census_gl_pairs": ("node pair", 89.2, 26_000),
+    "census_TXb": ("item", 2266.0, 1_652_000),
+    "census_Q": ("candidate", 527.8, 302_000),
     "census_Sb": ("item", 612.8, 4_378_000),
     "census_Pb": ("item", 480.6, 5_733_000),
     "census_TX": ("candidate", 332.9, 659_000),
-    "census_Q": ("candidate", 522.3, 301_000),
-    "census_TXb": ("item", None, None),
-    "census_gl_edges": ("pair", None, None),
-    "census_gl_pairs": ("node pair", None, None),
     "census_Wb": ("item", None, None),
     "census_S": ("candidate", None, None),
     "census_P": ("candidate", None, None),

@@ -35,15 +35,39 @@ __device__ __forceinline__ int32_t degree(const DevGraph& g, int32_t v) {
   return (int32_t)(g.off2[v + 1] - g.off2[v]);
 }
 
-// One warp per pair (u < v): lane l takes words l, l+32, ... of the rows.
-// t(e) = popcount of the rows' AND (warp sum); the 4-cliques whose two
-// smallest nodes are u < v: each lane takes the common neighbours w > v in
-// its words and counts the common neighbours z > w of u, v and w. Then the
-// per-pair sums, and t(e) added at both ends.
-__global__ void k_graphlet_edges(const DevGraph g, uint32_t* __restrict__ tnode,
-                                 unsigned long long* __restrict__ agg) {
-  const int32_t bw = g.bwords;
+constexpr int GL_WARPS = 8;      // warps per block of the pair kernel
+constexpr int GL_MAXW = 512;     // row words kept in shared memory (n <= 16384)
+constexpr int GL_LIST = 1024;    // common neighbours listed per round (32 words)
+
+// 4-cliques of pair (u, v) over the listed common neighbours w > v: lanes take
+// the listed w in turn and count the common neighbours z > w of u, v and w.
+__device__ __forceinline__ uint64_t k4_of_list(const DevGraph& g, int32_t base, const uint32_t* cw,
+                                               const int16_t* list, int count) {
   const int lane = threadIdx.x & 31;
+  const int32_t bw = g.bwords;
+  uint64_t k4 = 0;
+  for (int i = lane; i < count; i += 32) {
+    const int32_t wl = list[i];
+    const uint32_t* Bw = brow(g.bits2, bw, base + wl);
+    for (int32_t x = wl >> 5; x < bw; ++x) k4 += __popc(cw[x] & __ldg(Bw + x) & above(x, wl));
+  }
+  return k4;
+}
+
+// One warp per pair (u < v): t(e) = popcount of the rows' AND (lanes over
+// words, kept in shared memory), the 4-cliques whose two smallest nodes are
+// u < v (common neighbours w > v listed in shared memory and shared out over
+// the lanes), then the per-pair sums and t(e) added at both ends. Rows longer
+// than GL_MAXW words take the lanes over words directly.
+__global__ void __launch_bounds__(GL_WARPS * 32)
+    k_graphlet_edges(const DevGraph g, uint32_t* __restrict__ tnode,
+                     unsigned long long* __restrict__ agg) {
+  __shared__ uint32_t cw_s[GL_WARPS][GL_MAXW];
+  __shared__ int16_t wl_s[GL_WARPS][GL_LIST];
+  const int32_t bw = g.bwords;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t* cw = cw_s[wid];
+  int16_t* list = wl_s[wid];
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < g.m2; p += warps) {
     const int32_t u = (int32_t)(g.e2[p] >> 32), v = (int32_t)(g.e2[p] & 0xFFFFFFFFull);
@@ -52,17 +76,54 @@ __global__ void k_graphlet_edges(const DevGraph g, uint32_t* __restrict__ tnode,
     const uint32_t* Bv = brow(g.bits2, bw, v);
     uint32_t t = 0;
     uint64_t k4 = 0;
-    for (int32_t w = lane; w < bw; w += 32) {
-      const uint32_t c = __ldg(Bu + w) & __ldg(Bv + w);
-      t += __popc(c);
-      uint32_t ws = c & above(w, vl);
-      while (ws) {
-        const int j = __ffs(ws) - 1;
-        ws &= ws - 1;
-        const int32_t wl = w * 32 + j;
-        const uint32_t* Bw = brow(g.bits2, bw, base + wl);
-        for (int32_t x = w; x < bw; ++x)
-          k4 += __popc(__ldg(Bu + x) & __ldg(Bv + x) & __ldg(Bw + x) & above(x, wl));
+    if (bw <= GL_MAXW) {
+      for (int32_t w = lane; w < bw; w += 32) {
+        const uint32_t c = __ldg(Bu + w) & __ldg(Bv + w);
+        cw[w] = c;
+        t += __popc(c);
+      }
+      __syncwarp();
+      int count = 0;
+      for (int32_t w0 = 0; w0 < bw; w0 += 32) {
+        const int32_t w = w0 + lane;
+        uint32_t word = w < bw ? (cw[w] & above(w, vl)) : 0u;
+        const uint32_t c = __popc(word);
+        uint32_t incl = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+          if (lane >= d) incl += y;
+        }
+        const int round = (int)__shfl_sync(0xffffffffu, incl, 31);
+        if (count + round > GL_LIST) {  // list full: count its cliques first
+          k4 += k4_of_list(g, base, cw, list, count);
+          __syncwarp();
+          count = 0;
+        }
+        int pos = count + (int)(incl - c);
+        while (word) {
+          const int j = __ffs(word) - 1;
+          word &= word - 1;
+          list[pos++] = (int16_t)(w * 32 + j);
+        }
+        count += round;
+        __syncwarp();
+      }
+      k4 += k4_of_list(g, base, cw, list, count);
+      __syncwarp();
+    } else {
+      for (int32_t w = lane; w < bw; w += 32) {
+        const uint32_t c = __ldg(Bu + w) & __ldg(Bv + w);
+        t += __popc(c);
+        uint32_t ws = c & above(w, vl);
+        while (ws) {
+          const int j = __ffs(ws) - 1;
+          ws &= ws - 1;
+          const int32_t wl = w * 32 + j;
+          const uint32_t* Bw = brow(g.bits2, bw, base + wl);
+          for (int32_t x = w; x < bw; ++x)
+            k4 += __popc(__ldg(Bu + x) & __ldg(Bv + x) & __ldg(Bw + x) & above(x, wl));
+        }
       }
     }
 #pragma unroll
@@ -187,7 +248,8 @@ void graphlet_prepare(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
 void graphlet_edges(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
   if (g->counts[2] == 0) return;
   TraceSpan span("census_gl_edges", s);
-  k_graphlet_edges<<<grid_n((uint64_t)g->counts[2] * 32), 256, 0, s>>>(g->view(), G.tnode, G.agg);
+  k_graphlet_edges<<<grid_n((uint64_t)g->counts[2] * 32), GL_WARPS * 32, 0, s>>>(g->view(), G.tnode,
+                                                                                 G.agg);
   HM_KCHECK();
   span.end();
 }
