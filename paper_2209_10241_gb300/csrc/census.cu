@@ -618,17 +618,20 @@ std::vector<std::pair<hm_graph::Space*, char>> census_spaces(hm_graph* g, int or
   return {{&g->S, 'S'}, {&g->P, 'P'}, {&g->TX, 'X'}};
 }
 
-// The graphlet census replaces S and P when its word operations (a word
-// operation taken as a tenth of one candidate's evaluation) cost less than the
-// cheaper variant of each. HM_GRAPHLETS=0 / 1 forces it off / on (on needs
-// pair bitmaps); HM_DENSE_FAMILIES, which forces the S and P variants, keeps
-// it off unless HM_GRAPHLETS=1.
+// The graphlet census replaces S and P: with pair bitmaps, when its word
+// operations (a word operation taken as a tenth of one candidate's
+// evaluation) cost less than the cheaper variant of each; without, when S and
+// P hold more than 5e8 candidates (its pair and 4-cycle passes cost about the
+// degrees squared, far less on such graphs). HM_GRAPHLETS=0 / 1 forces it off
+// / on; HM_DENSE_FAMILIES, which forces the S and P variants, keeps it off
+// unless HM_GRAPHLETS=1.
 bool prefer_graphlets(const hm_graph* g) {
-  if (!g->bits2) return false;
   const char* env = std::getenv("HM_GRAPHLETS");
   if (env && env[0] == '0') return false;
   if (env && env[0] == '1') return true;
   if (std::getenv("HM_DENSE_FAMILIES")) return false;
+  // without pair bitmaps (hash probes): when the S and P enumeration is large
+  if (!g->bits2) return (double)g->S.total + (double)g->P.total > 5e8;
   const double bw = g->bwords;
   const double s_cost = std::min((double)g->S.total, (double)g->Sb.total * (2 + bw * 0.5) * 0.35);
   const double p_cost = std::min((double)g->P.total, (double)g->Pb.total * (2 + bw) * 0.35);
@@ -636,6 +639,7 @@ bool prefer_graphlets(const hm_graph* g) {
 }
 
 void choose_variants(hm_graph* g, int order) {
+  if (order == 4) g->useGL = prefer_graphlets(g);
   if (!g->bits2) return;
   if (order == 3) {
     g->useWb = prefer_bits(g, g->Wb, g->W.total, 0.5);
@@ -644,7 +648,6 @@ void choose_variants(hm_graph* g, int order) {
     g->usePb = prefer_bits(g, g->Pb, g->P.total, 1.0);
     // a bit-sliced TX item scans one 4-word group
     g->useTXb = g->bwords >= 4 && prefer_bits(g, g->TXb, g->TX.total, 4.0 / g->bwords);
-    g->useGL = prefer_graphlets(g);
   }
 }
 

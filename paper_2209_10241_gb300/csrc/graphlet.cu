@@ -174,6 +174,114 @@ __global__ void k_graphlet_pairs(const DevGraph g, int32_t nodes_per_graph,
   }
 }
 
+// Graphs without pair bitmaps. One warp per pair (u < v): t(e) by hash probes
+// of the shorter adjacency list against the other endpoint; the common
+// neighbours w > v, in ascending order, go to the warp's list (capacity = the
+// largest pair degree) and every pair of them that is itself a pair closes a
+// 4-clique with u and v.
+__global__ void k_graphlet_edges_sparse(const DevGraph g, int32_t* __restrict__ lists, int64_t cap,
+                                        uint32_t* __restrict__ tnode,
+                                        unsigned long long* __restrict__ agg) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int32_t* list = lists + gw * cap;
+  for (int64_t p = gw; p < g.m2; p += warps) {
+    const int32_t u = (int32_t)(g.e2[p] >> 32), v = (int32_t)(g.e2[p] & 0xFFFFFFFFull);
+    const int32_t du = degree(g, u), dv = degree(g, v);
+    const int32_t a = du <= dv ? u : v, b = du <= dv ? v : u, da = du <= dv ? du : dv;
+    const int64_t oa = g.off2[a];
+    uint32_t t = 0;
+    int count = 0;
+    for (int32_t i0 = 0; i0 < da; i0 += 32) {
+      const int32_t i = i0 + lane;
+      const int32_t w = i < da ? g.adj2[oa + i] : -1;
+      const bool common = w >= 0 && w != b && has_pair(g, b, w);
+      t += common ? 1u : 0u;
+      const bool keep = common && w > v;
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      if (keep) list[count + __popc(bal & lt)] = w;
+      count += __popc(bal);
+    }
+    __syncwarp();
+    uint64_t k4 = 0;
+    for (int i = lane; i < count; i += 32) {
+      const int32_t wi = list[i];
+      for (int j = i + 1; j < count; ++j) k4 += has_pair(g, wi, list[j]) ? 1u : 0u;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      t += __shfl_xor_sync(0xffffffffu, t, o);
+      k4 += __shfl_xor_sync(0xffffffffu, k4, o);
+    }
+    if (lane == 0) {
+      const uint64_t tt = t;
+      atomicAdd(&tnode[u], t);
+      atomicAdd(&tnode[v], t);
+      unsigned long long* A = agg + (int64_t)graph_of(g, u) * NAGG;
+      atomicAdd(&A[1], (unsigned long long)((uint64_t)(du - 1) * (uint64_t)(dv - 1)));
+      atomicAdd(&A[2], (unsigned long long)tt);
+      if (tt > 1) atomicAdd(&A[4], (unsigned long long)(tt * (tt - 1) / 2));
+      if (k4) atomicAdd(&A[5], (unsigned long long)k4);
+    }
+  }
+}
+
+// 4-cycles of graphs without pair bitmaps, each at its highest-ranked node x
+// (rank = (degree, id)): the nodes z of lower rank reached by paths x - y - z
+// through a y of lower rank are counted (per-block dense counters, with the
+// list of the counters touched); every two such paths to one z close a
+// 4-cycle x - y - z - y'. Adds 2 C4 to the graph's sum, as the bitmap kernel
+// does.
+__global__ void k_graphlet_c4_sparse(const DevGraph g, int32_t nodes_per_graph,
+                                     uint32_t* __restrict__ acc_all, int32_t* __restrict__ touched_all,
+                                     unsigned long long* __restrict__ agg) {
+  __shared__ int tcount;
+  __shared__ unsigned long long part[32];
+  uint32_t* acc = acc_all + (size_t)blockIdx.x * g.n;
+  int32_t* touched = touched_all + (size_t)blockIdx.x * g.n;
+  for (int64_t x = blockIdx.x; x < g.n; x += gridDim.x) {
+    const int32_t dx = degree(g, (int32_t)x);
+    if (threadIdx.x == 0) tcount = 0;
+    __syncthreads();
+    const int64_t ox = g.off2[x];
+    for (int32_t i = threadIdx.x; i < dx; i += blockDim.x) {
+      const int32_t y = g.adj2[ox + i];
+      const int32_t dy = degree(g, y);
+      if (!(dy < dx || (dy == dx && y < x))) continue;
+      const int64_t oy = g.off2[y];
+      for (int32_t k = 0; k < dy; ++k) {
+        const int32_t z = g.adj2[oy + k];
+        if (z == x) continue;
+        const int32_t dz = degree(g, z);
+        if (!(dz < dx || (dz == dx && z < x))) continue;
+        if (atomicAdd(&acc[z], 1u) == 0u) touched[atomicAdd(&tcount, 1)] = z;
+      }
+    }
+    __syncthreads();
+    uint64_t sum = 0;
+    const int tc = tcount;
+    for (int i = threadIdx.x; i < tc; i += blockDim.x) {
+      const int32_t z = touched[i];
+      const uint64_t c = acc[z];
+      sum += c * (c - 1) / 2;
+      acc[z] = 0;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint64_t s = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
+      if (s) atomicAdd(&agg[(x / nodes_per_graph) * NAGG + 6], (unsigned long long)(2 * s));
+    }
+    __syncthreads();
+  }
+}
+
 struct PatternClasses {
   int cls[6];  // star, path, paw, c4, diamond, k4
 };
@@ -234,20 +342,43 @@ unsigned grid_n(uint64_t n) {
 // connected patterns, in the order star, path, paw, 4-cycle, diamond, 4-clique.
 static const uint32_t kPatternMask[6] = {7u, 41u, 15u, 45u, 31u, 63u};
 
+constexpr int SPARSE_C4_BLOCKS = 152;
+constexpr int SPARSE_EDGE_BLOCKS = 152 * 8;
+
 void graphlet_prepare(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
-  HM_CHECK(g->bits2 != nullptr, HM_EINVAL, "graphlet census needs pair bitmaps");
   G.ngraphs = g->block ? (g->n + g->block - 1) / g->block : 1;
   G.per = g->block ? g->block : g->n;
   const size_t tb = ((size_t)g->n * 4 + 255) & ~(size_t)255;
-  G.buf.alloc(tb + (size_t)G.ngraphs * NAGG * 8, s);
+  const size_t ab = ((size_t)G.ngraphs * NAGG * 8 + 255) & ~(size_t)255;
+  size_t zero = tb + ab, extra = 0;
+  if (!g->bits2) {
+    // 4-cycle counters (zero) and touched lists per block; pair lists per warp
+    G.cap = std::max<int64_t>(1, g->max_d2);
+    zero += (size_t)SPARSE_C4_BLOCKS * g->n * 4;
+    extra = (size_t)SPARSE_C4_BLOCKS * g->n * 4 + (size_t)SPARSE_EDGE_BLOCKS * 8 * G.cap * 4;
+  }
+  G.buf.alloc(zero + extra, s);
   G.tnode = reinterpret_cast<uint32_t*>(G.buf.p);
   G.agg = reinterpret_cast<unsigned long long*>(G.buf.p + tb);
-  HM_CUDA(cudaMemsetAsync(G.buf.p, 0, G.buf.n, s));
+  if (!g->bits2) {
+    G.acc = reinterpret_cast<uint32_t*>(G.buf.p + tb + ab);
+    G.touched = reinterpret_cast<int32_t*>(G.buf.p + zero);
+    G.lists = G.touched + (size_t)SPARSE_C4_BLOCKS * g->n;
+  }
+  HM_CUDA(cudaMemsetAsync(G.buf.p, 0, zero, s));
 }
 
 void graphlet_edges(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
   if (g->counts[2] == 0) return;
   TraceSpan span("census_gl_edges", s);
+  if (!g->bits2) {
+    const uint64_t want = ((uint64_t)g->counts[2] * 32 + 255) / 256;
+    const unsigned blocks = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, SPARSE_EDGE_BLOCKS));
+    k_graphlet_edges_sparse<<<blocks, 256, 0, s>>>(g->view(), G.lists, G.cap, G.tnode, G.agg);
+    HM_KCHECK();
+    span.end();
+    return;
+  }
   k_graphlet_edges<<<grid_n((uint64_t)g->counts[2] * 32), GL_WARPS * 32, 0, s>>>(g->view(), G.tnode,
                                                                                  G.agg);
   HM_KCHECK();
@@ -256,6 +387,13 @@ void graphlet_edges(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
 
 void graphlet_pairs(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
   TraceSpan span("census_gl_pairs", s);
+  if (!g->bits2) {
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(g->n, SPARSE_C4_BLOCKS));
+    k_graphlet_c4_sparse<<<blocks, 256, 0, s>>>(g->view(), G.per, G.acc, G.touched, G.agg);
+    HM_KCHECK();
+    span.end();
+    return;
+  }
   k_graphlet_pairs<<<grid_n((uint64_t)g->n * 32), 256, 0, s>>>(g->view(), G.per, G.agg);
   HM_KCHECK();
   span.end();

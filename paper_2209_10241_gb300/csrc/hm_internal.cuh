@@ -418,6 +418,12 @@ struct GraphletScratch {
   unsigned long long* agg = nullptr;
   int ngraphs = 1;
   int32_t per = 0;
+  // graphs without pair bitmaps: per-block 4-cycle counters and touched
+  // lists, per-warp lists of common neighbours (cap entries each)
+  uint32_t* acc = nullptr;
+  int32_t* touched = nullptr;
+  int32_t* lists = nullptr;
+  int64_t cap = 0;
 };
 void graphlet_prepare(const hm_graph* g, GraphletScratch& G, cudaStream_t s);
 void graphlet_edges(const hm_graph* g, GraphletScratch& G, cudaStream_t s);

@@ -22,7 +22,7 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 MODES = ["hash", "bitmap", "sliced", "sliced_filter", "tuned", "chunk8", "chunk32", "graphlets",
-         "graphlets_filter", "graphlets_pc"]
+         "graphlets_filter", "graphlets_pc", "graphlets_hash"]
 
 
 def _set_mode(monkeypatch, mode):
@@ -33,11 +33,18 @@ def _set_mode(monkeypatch, mode):
     defaults, schedules picked by the autotuner; chunk8 / chunk32: hash
     probes with 8 / 32 candidates per lane on every per-candidate family;
     graphlets*: pairs-only sets from graphlet identities, with the bit-sliced
-    TX family on exact rows / on the co-occurrence filter / per candidate."""
+    TX family on exact rows / on the co-occurrence filter / per candidate;
+    graphlets_hash: the same without pair bitmaps (hash probes, 4-cycles by
+    degree order)."""
     for var in ("HM_PAIR_BITMAP", "HM_DENSE_FAMILIES", "HM_TRIPLE_ROWS", "HM_AUTOTUNE",
                 "HM_CENSUS_CHUNK", "HM_GRAPHLETS"):
         monkeypatch.delenv(var, raising=False)
     if mode == "tuned":
+        return
+    if mode == "graphlets_hash":
+        monkeypatch.setenv("HM_PAIR_BITMAP", "0")
+        monkeypatch.setenv("HM_GRAPHLETS", "1")
+        monkeypatch.setenv("HM_AUTOTUNE", "0")
         return
     if mode.startswith("graphlets"):
         monkeypatch.setenv("HM_PAIR_BITMAP", "1")
@@ -165,7 +172,7 @@ def test_repeated_counts_are_identical(hm):
     assert torch.equal(a, b)
 
 
-def test_empty_and_degenerate_inputs(hm):
+def test_empty_and_degenerate_inputs(hm, pair_path):
     # no hyperedges
     h = synth.from_edges([], 5)
     for k in (3, 4):
