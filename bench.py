@@ -56,6 +56,24 @@ ROOFLINE = {
 }
 
 
+def max_over_ranks(x: float, device: str = "cuda") -> float:
+    """The largest x over the ranks of the initialised process group (x itself
+    without one): the whole job took as long as its slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_step: int, steps: int, world: int, max_ms: float) -> float:
+    """Units per second of the whole job: every rank processes units_per_step per
+    step (replicas, weak scaling) in the slowest rank's time."""
+    return units_per_step * steps * world / (max_ms / 1e3)
+
+
 def _env_int(name, default):
     try:
         return int(os.environ.get(name, default))
@@ -505,12 +523,9 @@ def main():
     gpu_launches = hm.launch_count() - launches0
     trace = hm.trace_read()
     assert int(hist.sum().item()) == sets_per_step
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms)
     ms_per_step = total_ms / args.steps
-    value = sets_per_step * args.steps * world / (total_ms / 1e3)
+    value = whole_job_rate(sets_per_step, args.steps, world, total_ms)
 
     # end-to-end through the C ABI with host buffers
     hmem = torch.from_numpy(h.members).pin_memory()
@@ -531,11 +546,8 @@ def main():
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
     assert int(hout.sum().item()) == sets_per_step
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_ms = float(t.item())
-    e2e_value = sets_per_step * args.steps * world / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(e2e_ms)
+    e2e_value = whole_job_rate(sets_per_step, args.steps, world, e2e_ms)
 
     if rank != 0:
         if world > 1:
