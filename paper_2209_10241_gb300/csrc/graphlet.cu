@@ -36,6 +36,7 @@ __device__ __forceinline__ int32_t degree(const DevGraph& g, int32_t v) {
 }
 
 constexpr int GL_WARPS = 8;      // warps per block of the pair kernel
+constexpr int SPARSE_WARPS = 8;  // warps per block of the hash-probe pair kernel
 constexpr int GL_MAXW = 512;     // row words kept in shared memory (n <= 16384)
 constexpr int GL_LIST = 1024;    // common neighbours listed per round (32 words)
 
@@ -54,6 +55,68 @@ __device__ __forceinline__ uint64_t k4_of_list(const DevGraph& g, int32_t base, 
   return k4;
 }
 
+// Per-pair sums (d(u)-1)(d(v)-1), t(e), C(t(e), 2) and the 4-cliques, added
+// to slots 1, 2, 4 and 5 of the pair's graph. Lane 0 of a warp keeps them in
+// registers while its pairs stay in one graph; at the end of the kernel the
+// block merges its warps' runs, so that each block issues one atomic per slot
+// and graph instead of one per pair (thousands of same-address atomics
+// otherwise serialise in L2).
+struct PairSums {
+  int32_t gi = -1;
+  uint64_t v[4] = {0, 0, 0, 0};
+};
+
+__device__ __forceinline__ void pair_sums_flush(unsigned long long* agg, const PairSums& P) {
+  if (P.gi < 0) return;
+  unsigned long long* A = agg + (int64_t)P.gi * NAGG;
+  if (P.v[0]) atomicAdd(&A[1], (unsigned long long)P.v[0]);
+  if (P.v[1]) atomicAdd(&A[2], (unsigned long long)P.v[1]);
+  if (P.v[2]) atomicAdd(&A[4], (unsigned long long)P.v[2]);
+  if (P.v[3]) atomicAdd(&A[5], (unsigned long long)P.v[3]);
+}
+
+__device__ __forceinline__ void pair_sums_add(PairSums& P, unsigned long long* agg, int32_t gi,
+                                              uint64_t du, uint64_t dv, uint64_t t, uint64_t k4) {
+  if (gi != P.gi) {
+    pair_sums_flush(agg, P);
+    P = PairSums{};
+    P.gi = gi;
+  }
+  P.v[0] += (du - 1) * (dv - 1);
+  P.v[1] += t;
+  P.v[2] += t * (t - (t > 0 ? 1 : 0)) / 2;
+  P.v[3] += k4;
+}
+
+// Called by every thread of the block (blockDim.x = 32 * NW) after the pair
+// loop; lane 0 of each warp holds its run.
+template <int NW>
+__device__ __forceinline__ void pair_sums_block(const PairSums& P, unsigned long long* agg) {
+  __shared__ int32_t gi_s[NW];
+  __shared__ uint64_t v_s[NW][4];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    gi_s[wid] = P.gi;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v_s[wid][i] = P.v[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    PairSums R;
+    for (int w = 0; w < NW; ++w) {
+      if (gi_s[w] < 0) continue;
+      if (gi_s[w] != R.gi) {
+        pair_sums_flush(agg, R);
+        R = PairSums{};
+        R.gi = gi_s[w];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) R.v[i] += v_s[w][i];
+    }
+    pair_sums_flush(agg, R);
+  }
+}
+
 // One warp per pair (u < v): t(e) = popcount of the rows' AND (lanes over
 // words, kept in shared memory), the 4-cliques whose two smallest nodes are
 // u < v (common neighbours w > v listed in shared memory and shared out over
@@ -69,6 +132,7 @@ __global__ void __launch_bounds__(GL_WARPS * 32)
   uint32_t* cw = cw_s[wid];
   int16_t* list = wl_s[wid];
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  PairSums P;
   for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < g.m2; p += warps) {
     const int32_t u = (int32_t)(g.e2[p] >> 32), v = (int32_t)(g.e2[p] & 0xFFFFFFFFull);
     const int32_t base = graph_base(g, u), vl = v - base;
@@ -132,16 +196,12 @@ __global__ void __launch_bounds__(GL_WARPS * 32)
       k4 += __shfl_xor_sync(0xffffffffu, k4, o);
     }
     if (lane == 0) {
-      const uint64_t du = (uint64_t)degree(g, u), dv = (uint64_t)degree(g, v), tt = t;
       atomicAdd(&tnode[u], t);
       atomicAdd(&tnode[v], t);
-      unsigned long long* A = agg + (int64_t)graph_of(g, u) * NAGG;
-      atomicAdd(&A[1], (unsigned long long)((du - 1) * (dv - 1)));
-      atomicAdd(&A[2], (unsigned long long)tt);
-      if (tt > 1) atomicAdd(&A[4], (unsigned long long)(tt * (tt - 1) / 2));
-      if (k4) atomicAdd(&A[5], (unsigned long long)k4);
+      pair_sums_add(P, agg, graph_of(g, u), (uint64_t)degree(g, u), (uint64_t)degree(g, v), t, k4);
     }
   }
+  pair_sums_block<GL_WARPS>(P, agg);
 }
 
 // Node pairs x < z of one graph: one warp per row x (grid-stride), lanes over
@@ -179,7 +239,8 @@ __global__ void k_graphlet_pairs(const DevGraph g, int32_t nodes_per_graph,
 // neighbours w > v, in ascending order, go to the warp's list (capacity = the
 // largest pair degree) and every pair of them that is itself a pair closes a
 // 4-clique with u and v.
-__global__ void k_graphlet_edges_sparse(const DevGraph g, int32_t* __restrict__ lists, int64_t cap,
+__global__ void __launch_bounds__(SPARSE_WARPS * 32)
+    k_graphlet_edges_sparse(const DevGraph g, int32_t* __restrict__ lists, int64_t cap,
                                         uint32_t* __restrict__ tnode,
                                         unsigned long long* __restrict__ agg) {
   const int lane = threadIdx.x & 31;
@@ -187,6 +248,7 @@ __global__ void k_graphlet_edges_sparse(const DevGraph g, int32_t* __restrict__ 
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   int32_t* list = lists + gw * cap;
+  PairSums P;
   for (int64_t p = gw; p < g.m2; p += warps) {
     const int32_t u = (int32_t)(g.e2[p] >> 32), v = (int32_t)(g.e2[p] & 0xFFFFFFFFull);
     const int32_t du = degree(g, u), dv = degree(g, v);
@@ -217,16 +279,12 @@ __global__ void k_graphlet_edges_sparse(const DevGraph g, int32_t* __restrict__ 
       k4 += __shfl_xor_sync(0xffffffffu, k4, o);
     }
     if (lane == 0) {
-      const uint64_t tt = t;
       atomicAdd(&tnode[u], t);
       atomicAdd(&tnode[v], t);
-      unsigned long long* A = agg + (int64_t)graph_of(g, u) * NAGG;
-      atomicAdd(&A[1], (unsigned long long)((uint64_t)(du - 1) * (uint64_t)(dv - 1)));
-      atomicAdd(&A[2], (unsigned long long)tt);
-      if (tt > 1) atomicAdd(&A[4], (unsigned long long)(tt * (tt - 1) / 2));
-      if (k4) atomicAdd(&A[5], (unsigned long long)k4);
+      pair_sums_add(P, agg, graph_of(g, u), (uint64_t)du, (uint64_t)dv, t, k4);
     }
   }
+  pair_sums_block<SPARSE_WARPS>(P, agg);
 }
 
 // 4-cycles of graphs without pair bitmaps, each at its highest-ranked node x
@@ -242,6 +300,9 @@ __global__ void k_graphlet_c4_sparse(const DevGraph g, int32_t nodes_per_graph,
   __shared__ unsigned long long part[32];
   uint32_t* acc = acc_all + (size_t)blockIdx.x * g.n;
   int32_t* touched = touched_all + (size_t)blockIdx.x * g.n;
+  // thread 0: the block's running sum for graph gcur, one atomic per graph
+  int64_t gcur = -1;
+  uint64_t scur = 0;
   for (int64_t x = blockIdx.x; x < g.n; x += gridDim.x) {
     const int32_t dx = degree(g, (int32_t)x);
     if (threadIdx.x == 0) tcount = 0;
@@ -276,10 +337,17 @@ __global__ void k_graphlet_c4_sparse(const DevGraph g, int32_t nodes_per_graph,
     if (threadIdx.x == 0) {
       uint64_t s = 0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
-      if (s) atomicAdd(&agg[(x / nodes_per_graph) * NAGG + 6], (unsigned long long)(2 * s));
+      const int64_t gi = x / nodes_per_graph;
+      if (gi != gcur) {
+        if (scur) atomicAdd(&agg[gcur * NAGG + 6], (unsigned long long)(2 * scur));
+        gcur = gi;
+        scur = 0;
+      }
+      scur += s;
     }
     __syncthreads();
   }
+  if (threadIdx.x == 0 && scur) atomicAdd(&agg[gcur * NAGG + 6], (unsigned long long)(2 * scur));
 }
 
 struct PatternClasses {
@@ -355,7 +423,7 @@ void graphlet_prepare(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
     // 4-cycle counters (zero) and touched lists per block; pair lists per warp
     G.cap = std::max<int64_t>(1, g->max_d2);
     zero += (size_t)SPARSE_C4_BLOCKS * g->n * 4;
-    extra = (size_t)SPARSE_C4_BLOCKS * g->n * 4 + (size_t)SPARSE_EDGE_BLOCKS * 8 * G.cap * 4;
+    extra = (size_t)SPARSE_C4_BLOCKS * g->n * 4 + (size_t)SPARSE_EDGE_BLOCKS * SPARSE_WARPS * G.cap * 4;
   }
   G.buf.alloc(zero + extra, s);
   G.tnode = reinterpret_cast<uint32_t*>(G.buf.p);
@@ -374,7 +442,7 @@ void graphlet_edges(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
   if (!g->bits2) {
     const uint64_t want = ((uint64_t)g->counts[2] * 32 + 255) / 256;
     const unsigned blocks = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, SPARSE_EDGE_BLOCKS));
-    k_graphlet_edges_sparse<<<blocks, 256, 0, s>>>(g->view(), G.lists, G.cap, G.tnode, G.agg);
+    k_graphlet_edges_sparse<<<blocks, SPARSE_WARPS * 32, 0, s>>>(g->view(), G.lists, G.cap, G.tnode, G.agg);
     HM_KCHECK();
     span.end();
     return;

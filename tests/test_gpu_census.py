@@ -152,6 +152,32 @@ def test_workload_every_path(hm, monkeypatch, case, k, mode):
     assert got.tolist() == rec["hist"][str(k)]
 
 
+@pytest.mark.parametrize("count", [1, 2047, 2048, 2049, 5000, 8193, 20000])
+@pytest.mark.parametrize("bitmap", ["0", "1"])
+def test_ingest_sort_sizes(hm, monkeypatch, count, bitmap):
+    # exactly `count` 3- and 4-hyperedges each (a fifth of them repeats): the
+    # one-block sort (<= 2048 keys) and the multi-tile sort, each side of the
+    # threshold, with and without pair bitmaps
+    monkeypatch.setenv("HM_PAIR_BITMAP", bitmap)
+    n = 300
+    st = synth.Stream(11, count)
+    edges = []
+    for size in (3, 4):
+        u = st.u64(2 * count * size).reshape(2 * count, size)
+        rows = [sorted(set(int(x) for x in r)) for r in (u % n)]
+        rows = [r for r in rows if len(r) == size]
+        base = count - count // 5
+        rows = rows[:base] + rows[: count - base]
+        assert len(rows) == count
+        edges += rows
+    h = synth.from_edges(edges, n)
+    g = hm.from_host(h, 4)
+    og = oracle.Graph.from_hypergraph(h, 4)
+    for s in (2, 3, 4):
+        assert g.count(s) == og.count(s)
+        assert (g.edges(s).cpu().numpy() == og.edges(s)).all()
+
+
 def test_relabel_and_duplicate_invariance(hm, pair_path):
     h = synth.workload("uniform-200")
     base = {k: _gpu_hist(hm, h, k)[0] for k in (3, 4)}
