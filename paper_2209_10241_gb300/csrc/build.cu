@@ -58,8 +58,7 @@ __device__ __forceinline__ void set_bit(const BitsOut& o, uint32_t* bm, int32_t 
 // counts per size; MODE 1 emits the packed sort key of each kept hyperedge
 // (members concatenated with b bits each, most significant first); MODE 2
 // sets the bitmap bits of each kept hyperedge instead (pairs, co-occurrence,
-// exact triple rows) and emits sort keys only for 4-hyperedges and, without
-// exact triple rows, 3-hyperedges.
+// exact triple rows) and emits sort keys only for 3- and 4-hyperedges.
 template <int MODE>
 __global__ void k_normalize(const int32_t* __restrict__ mem, const int64_t* __restrict__ off,
                             int64_t m, int32_t n, int kmax, int b,
@@ -123,7 +122,7 @@ __global__ void k_normalize(const int32_t* __restrict__ mem, const int64_t* __re
             atomicOr(bo.tri3 + ((size_t)v[i] * bo.n + v[j]) * bo.bw + (c >> 5), 1u << (c & 31));
           }
       }
-      if (cntd == 2 || (cntd == 3 && bo.tri3)) continue;
+      if (cntd == 2) continue;
     }
     const unsigned long long slot = atomicAdd(&cnt[cntd], 1ull);
     if (MODE >= 1) {
@@ -360,67 +359,6 @@ __global__ void k_upper_emit(const uint32_t* __restrict__ bits, int32_t n, int32
   }
 }
 
-// E_3 from the exact triple rows (one graph): row (a, b), a < b, holds the c
-// of the 3-hyperedges {a, b, c}; its ids above b, rows in order, give E_3
-// sorted and without repeats. One warp per row.
-__global__ void k_tri_counts(const uint32_t* __restrict__ tri3, int32_t n, int32_t bw,
-                             uint64_t* __restrict__ cnt) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t rows = (int64_t)n * n;
-  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
-    const int32_t a = (int32_t)(r / n), b = (int32_t)(r - (int64_t)a * n);
-    uint32_t c = 0;
-    if (a < b) {
-      const uint32_t* row = tri3 + (size_t)r * bw;
-      for (int32_t w = lane; w < bw; w += 32) {
-        const int32_t tw = b >> 5;
-        const uint32_t above =
-            w < tw ? 0u : w > tw ? ~0u : ((b & 31) == 31 ? 0u : (~0u << ((b & 31) + 1)));
-        c += __popc(__ldg(row + w) & above);
-      }
-#pragma unroll
-      for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    }
-    if (lane == 0) cnt[r] = c;
-  }
-}
-
-__global__ void k_tri_emit(const uint32_t* __restrict__ tri3, int32_t n, int32_t bw,
-                           const uint64_t* __restrict__ off, int4* __restrict__ e3) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t rows = (int64_t)n * n;
-  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
-    const int32_t a = (int32_t)(r / n), b = (int32_t)(r - (int64_t)a * n);
-    if (a >= b || off[r + 1] == off[r]) continue;
-    const uint32_t* row = tri3 + (size_t)r * bw;
-    uint64_t pos = off[r];
-    for (int32_t w0 = 0; w0 < bw; w0 += 32) {
-      const int32_t w = w0 + lane, tw = b >> 5;
-      const uint32_t above =
-          w < tw ? 0u : w > tw ? ~0u : ((b & 31) == 31 ? 0u : (~0u << ((b & 31) + 1)));
-      uint32_t word = w < bw ? (__ldg(row + w) & above) : 0u;
-      const uint32_t c = __popc(word);
-      uint32_t incl = c;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += y;
-      }
-      uint64_t p = pos + (incl - c);
-      while (word) {
-        const int j = __ffs(word) - 1;
-        word &= word - 1;
-        e3[p++] = make_int4(a, b, w * 32 + j, -1);
-      }
-      pos += __shfl_sync(0xffffffffu, incl, 31);
-    }
-  }
-}
-
-
-
 __global__ void k_max_degree(const int64_t* __restrict__ off, int32_t n, int* out) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x)
@@ -538,11 +476,11 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     const hm::DevGraph gv = g->view();
     bo = BitsOut{g->bits2, g->bits3, g->bits4, g->tri3, g->bwords, gv.block, n, gv.block_inv};
   }
-  // Sort keys: every size without bitmaps; with bitmaps only the 4-hyperedges
-  // and, without exact triple rows, the 3-hyperedges (pairs and triples are
-  // read off the rows, sorted and without repeats by construction).
+  // Sort keys: every size without bitmaps; with bitmaps only the 3- and
+  // 4-hyperedges (pairs are read off the pair rows, sorted and without repeats
+  // by construction).
   const size_t h2n = hc[2], h3n = kmax >= 3 ? hc[3] : 0, h4n = kmax >= 4 ? hc[4] : 0;
-  const size_t k2 = bitmaps ? 0 : h2n, k3 = tri_rows ? 0 : h3n;
+  const size_t k2 = bitmaps ? 0 : h2n, k3 = h3n;
   DBuf<uint64_t> keys(k2 + 2 * k3 + 2 * h4n, s);
   uint64_t* c2 = keys.p;
   uint64_t* c3hi = c2 + k2;
@@ -597,14 +535,12 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
       ++nj;
     };
     if (!bitmaps) add(c2, nullptr, (int64_t)h2n, 2, SortJob::PAIR, g->e2);
-    if (kmax >= 3 && !tri_rows) add(c3lo, c3hi, (int64_t)h3n, 3, SortJob::TRIPLE, g->e3);
+    if (kmax >= 3) add(c3lo, c3hi, (int64_t)h3n, 3, SortJob::TRIPLE, g->e3);
     if (kmax >= 4) add(c4lo, c4hi, (int64_t)h4n, 4, SortJob::QUAD, g->e4);
     if (bitmaps) {
-      // pair rows -> E_2 (f[0]), exact triple rows -> E_3 (f[1]), sorts (s)
-      const size_t rows3 = tri_rows ? (size_t)n * n : 0;
-      DBuf<uint64_t> rc(((size_t)n + 1) + (tri_rows ? rows3 + 1 : 0), s);
+      // pair rows -> E_2 (f[0]), sorts (s)
+      DBuf<uint64_t> rc((size_t)n + 1, s);
       uint64_t* rc2 = rc.p;
-      uint64_t* rc3 = rc.p + n + 1;
       Fork f(s);
       const hm::DevGraph gv = g->view();
       k_upper_counts<<<grid1d((int64_t)n * 32), T256, 0, f[0]>>>(g->bits2, n, g->bwords,
@@ -615,17 +551,6 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
       k_upper_emit<<<grid1d((int64_t)n * 32), T256, 0, f[0]>>>(g->bits2, n, g->bwords, gv.block,
                                                                gv.block_inv, rc2, g->e2);
       HM_KCHECK();
-      if (tri_rows) {
-        k_tri_counts<<<grid1d((int64_t)rows3 * 32), T256, 0, f[1]>>>(g->tri3, n, g->bwords, rc3);
-        HM_KCHECK();
-        ScanJob tj{rc3, (int64_t)rows3, kept.p + 1};
-        scan_batch_inplace(&tj, 1, f[1]);
-        if (h3n) {
-          k_tri_emit<<<grid1d((int64_t)rows3 * 32), T256, 0, f[1]>>>(g->tri3, n, g->bwords, rc3,
-                                                                     g->e3);
-          HM_KCHECK();
-        }
-      }
       if (nj) sort_batch(jobs, nj, s);
       f.join();
     } else {

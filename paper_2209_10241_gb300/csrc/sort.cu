@@ -13,6 +13,7 @@
 // tile only ever waits on tiles that already run; every wait is still bounded
 // and one that gives up counts into g_wait_timeouts (read by the host).
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "hm_internal.cuh"
@@ -362,34 +363,76 @@ __global__ void __launch_bounds__(TPB) k_sort_unique(const Batch B, const Grid G
   }
 }
 
-// A job of at most one tile (TILE keys), sorted, deduplicated and written out
-// by one block in one launch: the keys stay in shared memory, every pass ranks
-// them as k_sort_pass does, and the digit offsets come from the block's own
-// counts. One block per job of the batch given in `which`.
-__global__ void __launch_bounds__(TPB) k_sort_small(const Batch B, const Grid G) {
-  __shared__ uint64_t ka_s[TILE], kb_s[TILE];
-  __shared__ uint32_t wcnt[TPB / 32][256];
-  __shared__ uint32_t dbase[256];
-  __shared__ uint32_t wtot[TPB / 32];
+// Jobs of at most SMALL_KEYS keys: one block of SMALL_BT threads per job
+// (the jobs listed in G), everything in one launch. The keys stay in shared
+// memory; each thread holds ipt = ceil(n / SMALL_BT) of them (1..8), so small
+// jobs run short per-warp chains. A pass ranks each key within its warp
+// (match on the digit, per-warp counters), turns the (digit, warp) counters
+// into offsets with one block-wide scan in digit-major order, and scatters;
+// order among equal digits is kept, as LSD radix sort needs.
+constexpr int SMALL_BT = 1024, SMALL_NW = SMALL_BT / 32, SMALL_IPT = 8;
+constexpr int64_t SMALL_KEYS = (int64_t)SMALL_BT * SMALL_IPT;
+constexpr size_t SMALL_SMEM = (size_t)SMALL_KEYS * 16 + (size_t)SMALL_NW * 256 * 4 + 64 * 4;
+
+// Exclusive scan of one value per thread over a block of SMALL_BT threads;
+// `total` gets the block's sum. Uses wtot[SMALL_NW]; ends with a barrier.
+__device__ __forceinline__ uint32_t small_block_scan(uint32_t x, uint32_t* wtot, uint32_t& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wtot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v = lane < SMALL_NW ? wtot[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    if (lane < SMALL_NW) wtot[lane] = v;
+  }
+  __syncthreads();
+  total = wtot[SMALL_NW - 1];
+  const uint32_t r = (warp ? wtot[warp - 1] : 0u) + incl - x;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(SMALL_BT) k_sort_small(const Batch B, const Grid G) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* ka_s = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* kb_s = ka_s + SMALL_KEYS;
+  uint32_t(*wcnt)[256] = reinterpret_cast<uint32_t(*)[256]>(kb_s + SMALL_KEYS);
+  uint32_t* wtot = reinterpret_cast<uint32_t*>(wcnt + SMALL_NW);
   const JobDev& J = B.j[G.job[blockIdx.x]];
-  const int64_t n = J.n;
+  const int n = (int)J.n;
+  const int ipt = (n + SMALL_BT - 1) / SMALL_BT;  // 1..SMALL_IPT
+  const int cap = ipt * SMALL_BT;
   const bool has_b = J.b[0] != nullptr;
-  for (int i = threadIdx.x; i < TILE; i += TPB) {
+  for (int i = threadIdx.x; i < cap; i += SMALL_BT) {
     ka_s[i] = i < n ? J.a[0][i] : 0;
     kb_s[i] = (has_b && i < n) ? J.b[0][i] : 0;
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
+  // scan ownership: thread t sums the counters of digit t / 4 over warps
+  // 8 (t % 4) .. 8 (t % 4) + 7, so thread order is digit-major
+  const int sd = threadIdx.x >> 2, sw = (threadIdx.x & 3) * 8;
   for (int p = 0; p < J.np; ++p) {
     const int shift = J.shift[p];
     const bool on_b = J.arr[p] != 0;
-    for (int i = threadIdx.x; i < (TPB / 32) * 256; i += TPB) (&wcnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < SMALL_NW * 256; i += SMALL_BT) (&wcnt[0][0])[i] = 0;
     __syncthreads();
-    uint32_t dig[IPT], rank[IPT];
-    uint64_t ka[IPT], kb[IPT];
+    uint32_t dig[SMALL_IPT], rank[SMALL_IPT];
+    uint64_t ka[SMALL_IPT], kb[SMALL_IPT];
 #pragma unroll
-    for (int it = 0; it < IPT; ++it) {
-      const int idx = warp * (32 * IPT) + it * 32 + lane;
+    for (int it = 0; it < SMALL_IPT; ++it) {
+      if (it >= ipt) break;
+      const int idx = warp * (32 * ipt) + it * 32 + lane;
       ka[it] = ka_s[idx];
       kb[it] = kb_s[idx];
       const bool valid = idx < n;
@@ -404,34 +447,27 @@ __global__ void __launch_bounds__(TPB) k_sort_small(const Batch B, const Grid G)
     }
     __syncthreads();
     {
-      // digit totals over the warps, then their exclusive prefix over digits
-      const int d = threadIdx.x;
-      uint32_t run = 0;
+      uint32_t c[8], sum = 0;
 #pragma unroll
-      for (int w = 0; w < TPB / 32; ++w) {
-        const uint32_t c = wcnt[w][d];
-        wcnt[w][d] = run;
-        run += c;
+      for (int k = 0; k < 8; ++k) {
+        c[k] = wcnt[sw + k][sd];
+        sum += c[k];
       }
-      uint32_t incl = run;
+      uint32_t total;
+      uint32_t run = small_block_scan(sum, wtot, total);
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
+      for (int k = 0; k < 8; ++k) {
+        wcnt[sw + k][sd] = run;
+        run += c[k];
       }
-      if (lane == 31) wtot[warp] = incl;
-      __syncthreads();
-      uint32_t before = 0;
-      for (int w = 0; w < warp; ++w) before += wtot[w];
-      dbase[d] = before + incl - run;
     }
     __syncthreads();
 #pragma unroll
-    for (int it = 0; it < IPT; ++it) {
-      const int idx = warp * (32 * IPT) + it * 32 + lane;
+    for (int it = 0; it < SMALL_IPT; ++it) {
+      if (it >= ipt) break;
+      const int idx = warp * (32 * ipt) + it * 32 + lane;
       if (idx < n) {
-        const uint32_t d = dig[it];
-        const uint32_t pos = dbase[d] + wcnt[warp][d] + rank[it];
+        const uint32_t pos = wcnt[warp][dig[it]] + rank[it];
         ka_s[pos] = ka[it];
         kb_s[pos] = kb[it];
       }
@@ -439,18 +475,19 @@ __global__ void __launch_bounds__(TPB) k_sort_small(const Batch B, const Grid G)
     __syncthreads();
   }
   if (!J.unique) {
-    for (int i = threadIdx.x; i < n; i += TPB) {
+    for (int i = threadIdx.x; i < n; i += SMALL_BT) {
       J.a[0][i] = ka_s[i];
       if (has_b) J.b[0][i] = kb_s[i];
     }
     return;
   }
   // unique: a key is kept when it differs from its predecessor; thread t owns
-  // keys [t * IPT, (t + 1) * IPT)
-  const int i0 = threadIdx.x * IPT;
+  // keys [t * ipt, (t + 1) * ipt)
+  const int i0 = threadIdx.x * ipt;
   uint32_t keep = 0, cnt = 0;
 #pragma unroll
-  for (int it = 0; it < IPT; ++it) {
+  for (int it = 0; it < SMALL_IPT; ++it) {
+    if (it >= ipt) break;
     const int i = i0 + it;
     if (i < n) {
       bool k = i == 0 || ka_s[i] != ka_s[i - 1];
@@ -461,26 +498,13 @@ __global__ void __launch_bounds__(TPB) k_sort_small(const Batch B, const Grid G)
       }
     }
   }
-  uint32_t incl = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  __syncthreads();
-  if (lane == 31) wtot[warp] = incl;
-  __syncthreads();
-  uint32_t before = 0, total = 0;
-  for (int w = 0; w < TPB / 32; ++w) {
-    before += w < warp ? wtot[w] : 0u;
-    total += wtot[w];
-  }
+  uint32_t total;
+  uint64_t pos = small_block_scan(cnt, wtot, total);
   if (threadIdx.x == 0 && J.d_kept) *J.d_kept = total;
-  uint64_t pos = before + incl - cnt;
   const int mb = J.member_bits;
   const uint64_t mask = (1ull << mb) - 1;
 #pragma unroll
-  for (int it = 0; it < IPT; ++it) {
+  for (int it = 0; it < SMALL_IPT; ++it) {
     if (!((keep >> it) & 1u)) continue;
     const int i = i0 + it;
     const uint64_t ka = ka_s[i], kb = kb_s[i];
@@ -504,6 +528,19 @@ __global__ void __launch_bounds__(TPB) k_sort_small(const Batch B, const Grid G)
     }
     ++pos;
   }
+}
+
+// The one-block sort's shared memory is above the default 48 KB: opt in once
+// per device.
+void small_sort_attr() {
+  static std::atomic<uint64_t> done{0};
+  int dev = 0;
+  HM_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return;
+  HM_CUDA(cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)SMALL_SMEM));
+  done.fetch_or(bit, std::memory_order_acq_rel);
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -576,14 +613,15 @@ void sort_batch(const SortJob* jobs, int njobs, cudaStream_t s) {
   }
   uint32_t* done = reinterpret_cast<uint32_t*>(base + zbytes - 256);
   HM_CUDA(cudaMemsetAsync(base, 0, zbytes, s));
-  // jobs of one tile: one block each, everything in one launch
-  auto small = [&](int k) { return B.j[k].n >= 1 && B.j[k].tiles == 1; };
+  // jobs of up to SMALL_KEYS keys: one block each, everything in one launch
+  auto small = [&](int k) { return B.j[k].n >= 1 && B.j[k].n <= SMALL_KEYS; };
   {
     Grid G{};
     for (int k = 0; k < njobs; ++k)
       if (small(k)) G.job[G.nj++] = k;
     if (G.nj) {
-      k_sort_small<<<(unsigned)G.nj, TPB, 0, s>>>(B, G);
+      small_sort_attr();
+      k_sort_small<<<(unsigned)G.nj, SMALL_BT, SMALL_SMEM, s>>>(B, G);
       HM_KCHECK();
     }
   }

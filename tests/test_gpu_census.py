@@ -152,12 +152,12 @@ def test_workload_every_path(hm, monkeypatch, case, k, mode):
     assert got.tolist() == rec["hist"][str(k)]
 
 
-@pytest.mark.parametrize("count", [1, 2047, 2048, 2049, 5000, 8193, 20000])
+@pytest.mark.parametrize("count", [1, 1023, 1024, 1025, 2049, 5000, 8192, 8193, 20000])
 @pytest.mark.parametrize("bitmap", ["0", "1"])
 def test_ingest_sort_sizes(hm, monkeypatch, count, bitmap):
     # exactly `count` 3- and 4-hyperedges each (a fifth of them repeats): the
-    # one-block sort (<= 2048 keys) and the multi-tile sort, each side of the
-    # threshold, with and without pair bitmaps
+    # one-block sort (1..8 keys per thread, <= 8192 keys) and the multi-tile
+    # sort, each side of every threshold, with and without pair bitmaps
     monkeypatch.setenv("HM_PAIR_BITMAP", bitmap)
     n = 300
     st = synth.Stream(11, count)
