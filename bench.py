@@ -43,10 +43,10 @@ ALU_LANES_PER_SM_CLK = 64
 # (ops = sm__sass_thread_inst_executed_op_{integer,bit}_pred_on per unit, measured by ncu on this
 # workload; traffic = dram__bytes_read.sum + dram__bytes_write.sum of the same capture)
 ROOFLINE = {
-    "census_gl_edges": ("pair", 2508.6, 137_000),
+    "census_gl_edges": ("pair", 4045.4, 155_000),
     "census_gl_pairs": ("node pair", 89.2, 26_000),
-    "census_TXb": ("item", 2266.0, 1_652_000),
-    "census_Q": ("candidate", 527.8, 302_000),
+    "census_TXb": ("item", 1971.0, 1_653_000),
+    "census_Q": ("candidate", 496.0, 302_000),
     "census_Sb": ("item", 612.8, 4_378_000),
     "census_Pb": ("item", 480.6, 5_733_000),
     "census_TX": ("candidate", 332.9, 659_000),

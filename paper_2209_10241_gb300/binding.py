@@ -89,8 +89,17 @@ def _check(status: int):
         raise HMError(status, load().hm_last_error().decode())
 
 
-def _stream(stream):
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
+def _stream(stream, device=None):
+    """The CUDA stream handle to pass: `stream`, else the current stream of
+    `device` (a tensor's device index; the current device when None). The raw
+    query skips building a torch Stream object, a few microseconds per call."""
     if stream is None:
+        if _raw_stream is not None:
+            return ctypes.c_void_p(_raw_stream(torch.cuda.current_device() if device is None
+                                               else device))
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
 
@@ -147,11 +156,13 @@ def build(members: torch.Tensor, offsets: torch.Tensor, num_nodes: int, max_orde
           stream=None) -> Graph:
     """hm_build on device tensors (int32 members, int64 offsets)."""
     assert members.is_cuda and offsets.is_cuda
-    members = members.contiguous().to(torch.int32)
-    offsets = offsets.contiguous().to(torch.int64)
+    if members.dtype != torch.int32 or not members.is_contiguous():
+        members = members.contiguous().to(torch.int32)
+    if offsets.dtype != torch.int64 or not offsets.is_contiguous():
+        offsets = offsets.contiguous().to(torch.int64)
     h = ctypes.c_void_p()
     _check(load().hm_build(_dptr(members), _dptr(offsets), offsets.numel() - 1, int(num_nodes),
-                           int(max_order), _stream(stream), ctypes.byref(h)))
+                           int(max_order), _stream(stream, members.device.index), ctypes.byref(h)))
     return Graph(h, max_order)
 
 
@@ -159,7 +170,7 @@ def count_exact(g: Graph, order: int, out: torch.Tensor = None, stream=None) -> 
     """hm_count_exact; returns an int64 device tensor holding the uint64 counts."""
     if out is None:
         out = torch.empty(max(1, num_classes(order)), dtype=torch.int64, device="cuda")
-    _check(load().hm_count_exact(g._h, order, _dptr(out), _stream(stream)))
+    _check(load().hm_count_exact(g._h, order, _dptr(out), _stream(stream, out.device.index)))
     return out
 
 

@@ -4,6 +4,7 @@
 // the candidate generators walk.
 #include <cstdlib>
 #include <mutex>
+#include <tuple>
 
 #include "hm_internal.cuh"
 
@@ -51,6 +52,19 @@ struct BitsOut {
 __device__ __forceinline__ void set_bit(const BitsOut& o, uint32_t* bm, int32_t a, int32_t b) {
   const int32_t c = bit_col(a, b, o.block, o.inv);
   atomicOr(bm + (size_t)a * o.bw + (c >> 5), 1u << (c & 31));
+}
+
+// Slot of this lane in counter cnt[size]: the lanes of the warp that reach
+// this point with the same size share one atomic (tens of thousands of
+// same-address atomics otherwise serialise in L2).
+__device__ __forceinline__ unsigned long long agg_slot(unsigned long long* cnt, int size) {
+  const unsigned am = __activemask();
+  const unsigned peers = __match_any_sync(am, size);
+  const int leader = __ffs(peers) - 1, lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(&cnt[size], (unsigned long long)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  return base + (unsigned long long)__popc(peers & ((1u << lane) - 1u));
 }
 
 // One thread per input hyperedge: the set of its members (sorted, repeats
@@ -105,7 +119,7 @@ __global__ void k_normalize(const int32_t* __restrict__ mem, const int64_t* __re
       continue;
     }
     if (big) {
-      if (MODE == 0) atomicAdd(&cnt[kmax + 1], 1ull);
+      if (MODE == 0) agg_slot(cnt, kmax + 1);
       continue;
     }
     if (cntd < 2) continue;
@@ -124,7 +138,7 @@ __global__ void k_normalize(const int32_t* __restrict__ mem, const int64_t* __re
       }
       if (cntd == 2) continue;
     }
-    const unsigned long long slot = atomicAdd(&cnt[cntd], 1ull);
+    const unsigned long long slot = agg_slot(cnt, cntd);
     if (MODE >= 1) {
       unsigned __int128 key = 0;
 #pragma unroll
@@ -359,10 +373,15 @@ __global__ void k_upper_emit(const uint32_t* __restrict__ bits, int32_t n, int32
   }
 }
 
+// Largest pair degree: a thread's maximum over its nodes, then one atomic per
+// warp.
 __global__ void k_max_degree(const int64_t* __restrict__ off, int32_t n, int* out) {
+  int mx = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x)
-    atomicMax(out, (int)(off[v + 1] - off[v]));
+    mx = max(mx, (int)(off[v + 1] - off[v]));
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(out, mx);
 }
 
 __global__ void k_edges_out(const uint64_t* __restrict__ e2, const int4* __restrict__ e34,
@@ -459,60 +478,58 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   const bool bitmaps = use_bitmap(n, block ? block : n, block != 0);
   const bool tri_rows = bitmaps && kmax >= 3 && use_tri3(n, block);
   size_t words = 0, tw = 0;
-  BitsOut bo{};
+  auto al = [](size_t bytes) { return (bytes + 255) & ~(size_t)255; };
+  // Two allocations for this phase, each with its zeroed part first: one the
+  // graph keeps (bitmaps, then E_2 / E_3 / E_4, sized for the hyperedges
+  // before dedup) and one of temporaries (kept counts, sort scratch, sort
+  // keys, pair-row counts).
+  const size_t h2n = hc[2], h3n = kmax >= 3 ? hc[3] : 0, h4n = kmax >= 4 ? hc[4] : 0;
+  size_t bb = 0;
   if (bitmaps) {
     // rows padded to a multiple of four words: 16-byte aligned row loads
     g->bwords = (((block ? block : n) + 127) / 128) * 4;
     words = (size_t)n * g->bwords;
     if (tri_rows) tw = (size_t)n * n * g->bwords;
-    auto al = [](size_t bytes) { return (bytes + 255) & ~(size_t)255; };
-    const size_t bb = al(words * 4);
-    unsigned char* bits = keep(g, dalloc<unsigned char>(3 * bb + al(tw * 4) + 256, s));
-    HM_CUDA(cudaMemsetAsync(bits, 0, 3 * bb + al(tw * 4), s));
-    g->bits2 = reinterpret_cast<uint32_t*>(bits);
-    g->bits3 = reinterpret_cast<uint32_t*>(bits + bb);
-    g->bits4 = reinterpret_cast<uint32_t*>(bits + 2 * bb);
-    if (tw) g->tri3 = reinterpret_cast<uint32_t*>(bits + 3 * bb);
+    bb = al(words * 4);
+  }
+  const size_t bits_bytes = bitmaps ? 3 * bb + al(tw * 4) : 0;
+  const size_t b2 = al(h2n * 8), b3 = al(h3n * 16);
+  unsigned char* owned = keep(g, dalloc<unsigned char>(bits_bytes + b2 + b3 + h4n * 16 + 256, s));
+  BitsOut bo{};
+  if (bitmaps) {
+    g->bits2 = reinterpret_cast<uint32_t*>(owned);
+    g->bits3 = reinterpret_cast<uint32_t*>(owned + bb);
+    g->bits4 = reinterpret_cast<uint32_t*>(owned + 2 * bb);
+    if (tw) g->tri3 = reinterpret_cast<uint32_t*>(owned + 3 * bb);
     const hm::DevGraph gv = g->view();
     bo = BitsOut{g->bits2, g->bits3, g->bits4, g->tri3, g->bwords, gv.block, n, gv.block_inv};
   }
-  // Sort keys: every size without bitmaps; with bitmaps only the 3- and
-  // 4-hyperedges (pairs are read off the pair rows, sorted and without repeats
-  // by construction).
-  const size_t h2n = hc[2], h3n = kmax >= 3 ? hc[3] : 0, h4n = kmax >= 4 ? hc[4] : 0;
-  const size_t k2 = bitmaps ? 0 : h2n, k3 = h3n;
-  DBuf<uint64_t> keys(k2 + 2 * k3 + 2 * h4n, s);
-  uint64_t* c2 = keys.p;
-  uint64_t* c3hi = c2 + k2;
-  uint64_t* c3lo = c3hi + k3;
-  uint64_t* c4hi = c3lo + k3;
-  uint64_t* c4lo = c4hi + h4n;
-  if (m > 0) {
-    if (bitmaps)
-      k_normalize<2><<<grid1d(m), T256, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt2, err_p,
-                                                c2, c3hi, c3lo, c4hi, c4lo, bo);
-    else
-      k_normalize<1><<<grid1d(m), T256, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt2, err_p,
-                                                c2, c3hi, c3lo, c4hi, c4lo, bo);
-    HM_KCHECK();
-  }
-  // E_2, E_3, E_4 in ascending order, written into the graph's arrays (sized
-  // for the hyperedges before dedup) in their final layout; their sizes land
-  // in kept[] (one synchronisation)
   {
-    const size_t b2 = (h2n * 8 + 255) & ~(size_t)255, b3 = (h3n * 16 + 255) & ~(size_t)255;
-    unsigned char* eb = keep(g, dalloc<unsigned char>(b2 + b3 + h4n * 16 + 16, s));
+    unsigned char* eb = owned + bits_bytes;
     g->e2 = reinterpret_cast<uint64_t*>(eb);
     if (h3n) g->e3 = reinterpret_cast<int4*>(eb + b2);
     if (h4n) g->e4 = reinterpret_cast<int4*>(eb + b2 + b3);
   }
-  DBuf<uint64_t> kept(4, s);
-  HM_CUDA(cudaMemsetAsync(kept.p, 0, 4 * sizeof(uint64_t), s));
-  {
-    SortJob jobs[3];
-    int nj = 0;
+  // Sort keys: every size without bitmaps; with bitmaps only the 3- and
+  // 4-hyperedges (pairs are read off the pair rows, sorted and without repeats
+  // by construction). E_2, E_3, E_4 come out in ascending order in their final
+  // layout; their sizes land in kept[] (one synchronisation).
+  const size_t k2 = bitmaps ? 0 : h2n, k3 = h3n;
+  const size_t key_words = k2 + 2 * k3 + 2 * h4n;
+  SortJob jobs[3];
+  int nj = 0;
+  // key_base / kept_base: where the keys and counts will live (the sizing
+  // pass only needs which words exist)
+  auto make_jobs = [&](uint64_t* key_base, uint64_t* kept_base) {
+    uint64_t* c2 = key_base;
+    uint64_t* c3hi = c2 + k2;
+    uint64_t* c3lo = c3hi + k3;
+    uint64_t* c4hi = c3lo + k3;
+    uint64_t* c4lo = c4hi + h4n;
+    nj = 0;
     auto add = [&](uint64_t* lo, uint64_t* hi, int64_t cnt, int size, int unpack, void* out) {
       SortJob& J = jobs[nj];
+      J = SortJob{};
       J.a = lo;
       J.b = hi;
       J.b_is_key = hi != nullptr;
@@ -531,47 +548,70 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
       J.member_bits = b;
       J.out = out;
       // the count, 32 bits, into the low half of a zeroed 64-bit slot
-      J.d_kept = reinterpret_cast<uint32_t*>(kept.p + (size - 2));
+      J.d_kept = reinterpret_cast<uint32_t*>(kept_base + (size - 2));
       ++nj;
     };
     if (!bitmaps) add(c2, nullptr, (int64_t)h2n, 2, SortJob::PAIR, g->e2);
     if (kmax >= 3) add(c3lo, c3hi, (int64_t)h3n, 3, SortJob::TRIPLE, g->e3);
     if (kmax >= 4) add(c4lo, c4hi, (int64_t)h4n, 4, SortJob::QUAD, g->e4);
-    if (bitmaps) {
-      // pair rows -> E_2 (f[0]), sorts (s)
-      DBuf<uint64_t> rc((size_t)n + 1, s);
-      uint64_t* rc2 = rc.p;
-      Fork f(s);
-      const hm::DevGraph gv = g->view();
-      k_upper_counts<<<grid1d((int64_t)n * 32), T256, 0, f[0]>>>(g->bits2, n, g->bwords,
-                                                                 gv.block, gv.block_inv, rc2);
-      HM_KCHECK();
-      ScanJob sj{rc2, n, kept.p};
-      scan_batch_inplace(&sj, 1, f[0]);
-      k_upper_emit<<<grid1d((int64_t)n * 32), T256, 0, f[0]>>>(g->bits2, n, g->bwords, gv.block,
-                                                               gv.block_inv, rc2, g->e2);
-      HM_KCHECK();
-      if (nj) sort_batch(jobs, nj, s);
-      f.join();
-    } else {
-      sort_batch(jobs, nj, s);
-    }
+    return std::make_tuple(c2, c3hi, c3lo, c4hi, c4lo);
+  };
+  size_t sort_zero = 0, sort_bytes = 0;
+  {
+    uint64_t sizing[1];  // never dereferenced: only non-null matters
+    make_jobs(sizing, sizing);
+    if (nj) sort_bytes = sort_batch_scratch(jobs, nj, &sort_zero);
+  }
+  const size_t o_sort = 256, o_keys = o_sort + al(sort_bytes), o_rc = o_keys + al(key_words * 8);
+  DBuf<unsigned char> tmp(o_rc + ((size_t)n + 1) * 8, s);
+  uint64_t* kept = reinterpret_cast<uint64_t*>(tmp.p);
+  uint64_t* rc2 = reinterpret_cast<uint64_t*>(tmp.p + o_rc);
+  if (bitmaps) HM_CUDA(cudaMemsetAsync(owned, 0, bits_bytes, s));
+  HM_CUDA(cudaMemsetAsync(tmp.p, 0, o_sort + sort_zero, s));
+  const auto keyp = make_jobs(reinterpret_cast<uint64_t*>(tmp.p + o_keys), kept);
+  if (m > 0) {
+    uint64_t *c2, *c3hi, *c3lo, *c4hi, *c4lo;
+    std::tie(c2, c3hi, c3lo, c4hi, c4lo) = keyp;
+    if (bitmaps)
+      k_normalize<2><<<grid1d(m), T256, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt2, err_p,
+                                                c2, c3hi, c3lo, c4hi, c4lo, bo);
+    else
+      k_normalize<1><<<grid1d(m), T256, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt2, err_p,
+                                                c2, c3hi, c3lo, c4hi, c4lo, bo);
+    HM_KCHECK();
+  }
+  if (bitmaps) {
+    // pair rows -> E_2 (f[0]), sorts (s)
+    Fork f(s, 1);
+    const hm::DevGraph gv = g->view();
+    k_upper_counts<<<grid1d((int64_t)n * 32), T256, 0, f[0]>>>(g->bits2, n, g->bwords, gv.block,
+                                                               gv.block_inv, rc2);
+    HM_KCHECK();
+    ScanJob sj{rc2, n, kept};
+    scan_batch_inplace(&sj, 1, f[0]);
+    k_upper_emit<<<grid1d((int64_t)n * 32), T256, 0, f[0]>>>(g->bits2, n, g->bwords, gv.block,
+                                                             gv.block_inv, rc2, g->e2);
+    HM_KCHECK();
+    if (nj) sort_batch(jobs, nj, s, tmp.p + o_sort, true);
+    f.join();
+  } else if (nj) {
+    sort_batch(jobs, nj, s, tmp.p + o_sort, true);
   }
   span_sort.end();
   uint64_t* hk = pin + 32;
-  HM_CUDA(cudaMemcpyAsync(hk, kept.p, 3 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  HM_CUDA(cudaMemcpyAsync(hk, kept, 3 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   HM_CUDA(cudaStreamSynchronize(s));
   const int64_t m2 = (int64_t)hk[0], m3 = kmax >= 3 ? (int64_t)hk[1] : 0,
                 m4 = kmax >= 4 ? (int64_t)hk[2] : 0;
   g->counts[2] = m2;
   if (kmax >= 3) g->counts[3] = m3;
   if (kmax >= 4) g->counts[4] = m4;
-  keys.release();
+  tmp.release();
 
   TraceSpan span_tables("ingest_structures", s);
-  // Outputs and temporaries on `s`; then four independent chains run
+  // Outputs and temporaries on `s`; then three independent chains run
   // concurrently: hash sets (s), pair CSR + pair positions (f[0]), triple
-  // incidence CSR (f[1]), dense bitmaps and triple rows (f[2]).
+  // incidence CSR (f[1]).
   const uint64_t cap2 = table_capacity(m2), cap3 = m3 ? table_capacity(m3) : 0,
                  cap4 = m4 ? table_capacity(m4) : 0;
   g->h2_mask = cap2 - 1;
@@ -579,7 +619,10 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   g->h4_mask = cap4 ? cap4 - 1 : 0;
   // One allocation for the graph's structures, laid out so that two memsets
   // initialise them: the hash tables (empty = all ones), then the regions that
-  // start at zero (triple offsets), then the rest.
+  // start at zero (triple offsets, triple cursors), then the rest (with the
+  // pair degrees of the bitmap CSR).
+  uint32_t* cursor3 = nullptr;
+  uint64_t* pdeg = nullptr;
   {
     auto al = [](size_t bytes) { return (bytes + 255) & ~(size_t)255; };
     size_t o = 0;
@@ -592,6 +635,8 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     const size_t ff_end = o;
     const size_t o_off3 = o;
     o += al(((size_t)n + 1) * 8);
+    const size_t o_cur3 = o;
+    o += al(((size_t)n + 1) * 4);
     const size_t zero_end = o;
     const size_t o_off2 = o;
     o += al(((size_t)n + 1) * 8);
@@ -601,7 +646,11 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     o += al((size_t)m2 * 8);
     const size_t o_inc3 = o;
     o += al((size_t)3 * m3 * 4);
+    const size_t o_pdeg = o;
+    if (bitmaps) o += al((size_t)n * 8);
     unsigned char* arena = keep(g, dalloc<unsigned char>(o, s));
+    cursor3 = reinterpret_cast<uint32_t*>(arena + o_cur3);
+    if (bitmaps) pdeg = reinterpret_cast<uint64_t*>(arena + o_pdeg);
     g->h2 = reinterpret_cast<uint64_t*>(arena + o_h2);
     if (m3) g->h3 = reinterpret_cast<int4*>(arena + o_h3);
     if (m4) g->h4 = reinterpret_cast<int4*>(arena + o_h4);
@@ -613,18 +662,14 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     HM_CUDA(cudaMemsetAsync(arena, 0xFF, ff_end, s));
     HM_CUDA(cudaMemsetAsync(arena + ff_end, 0, zero_end - ff_end, s));
   }
-  // temporaries of the chains: directed pair keys, pair degrees; the triple
-  // cursors (zeroed) and the maximum pair degree
-  const size_t np_keys = bitmaps ? 0 : 2 * m2, n_deg = bitmaps ? n : 0;
-  DBuf<uint64_t> chain_tmp(np_keys + n_deg + ((size_t)n + 1) / 2 + 1, s);
-  uint64_t* pkeys = chain_tmp.p;
-  uint64_t* pdeg = chain_tmp.p + np_keys;
-  uint32_t* cursor3 = reinterpret_cast<uint32_t*>(chain_tmp.p + np_keys + n_deg);
-  int* mx_p = reinterpret_cast<int*>(cursor3 + n);
-  HM_CUDA(cudaMemsetAsync(cursor3, 0, ((size_t)n + 1) * sizeof(uint32_t), s));
+  // temporaries of the chains: directed pair keys (without bitmaps); the
+  // maximum pair degree goes to the zeroed counter word beside the error word
+  DBuf<uint64_t> pkeys_buf(bitmaps ? 0 : 2 * m2, s);
+  uint64_t* pkeys = pkeys_buf.p;
+  int* mx_p = reinterpret_cast<int*>(counters.p + 15);
 
   {
-    Fork f(s);
+    Fork f(s, 2);
     // hash sets (load <= 0.5), all sizes in one launch
     if (m2 + m3 + m4) {
       k_insert_all<<<grid1d(m2 + m3 + m4), T256, 0, s>>>(g->e2, m2, g->e3, m3, g->e4, m4, g->h2,
@@ -676,19 +721,18 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   // synchronisation (a census then starts without one)
   PendingSpaces pend;
   spaces_enqueue(g, census_spaces(g, kmax), s, pend);
-  unsigned* tail = reinterpret_cast<unsigned*>(pin + 40);  // max degree, error word
+  uint64_t* tail = pin + 40;  // max degree, error word (adjacent counter words)
   unsigned* timeouts = reinterpret_cast<unsigned*>(pin + 80);
   try {
-    HM_CUDA(cudaMemcpyAsync(tail, mx_p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    HM_CUDA(cudaMemcpyAsync(tail + 1, err_p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaMemcpyAsync(tail, counters.p + 15, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     wait_timeouts_async(timeouts, s);
     HM_CUDA(cudaStreamSynchronize(s));
   } catch (...) {
     for (uint64_t* p : pend.made) cudaFreeAsync(p, s);
     throw;
   }
-  g->max_d2 = (int)tail[0];
-  herr = (int)tail[1];
+  g->max_d2 = (int)(uint32_t)tail[0];
+  herr = (int)(uint32_t)tail[1];
   spaces_finish(pend);
   choose_variants(g, kmax);
   wait_timeouts_check(*timeouts, s);

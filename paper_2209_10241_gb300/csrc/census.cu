@@ -60,8 +60,8 @@ __global__ void __launch_bounds__(CENSUS_THREADS)
              int nmask, int ncls, int ngraphs, int sub, unsigned long long* __restrict__ hist) {
   __shared__ unsigned long long bins[kBatched ? 1 : BIN_STRIDE];
   __shared__ unsigned int gbins[kBatched ? MAX_GRAPHS * BIN_STRIDE : 1];
-  __shared__ uint8_t lut[2048];
-  for (int i = threadIdx.x; i < nmask; i += blockDim.x) lut[i] = lut_g[i];
+  __shared__ __align__(16) uint8_t lut[2048];
+  load_lut(lut, lut_g, nmask);
   if (kBatched) {
     for (int i = threadIdx.x; i < ngraphs * BIN_STRIDE; i += blockDim.x) gbins[i] = 0;
   } else {
@@ -167,8 +167,8 @@ __global__ void __launch_bounds__(CENSUS_THREADS, HM_BITS_MINBLOCKS)
                   int ncls, int ngraphs, unsigned long long* __restrict__ hist) {
   __shared__ unsigned long long bins[kBatched ? 1 : BIN_STRIDE];
   __shared__ unsigned int gbins[kBatched ? MAX_GRAPHS * BIN_STRIDE : 1];
-  __shared__ uint8_t lut[2048];
-  for (int i = threadIdx.x; i < nmask; i += blockDim.x) lut[i] = lut_g[i];
+  __shared__ __align__(16) uint8_t lut[2048];
+  load_lut(lut, lut_g, nmask);
   if (kBatched) {
     for (int i = threadIdx.x; i < ngraphs * BIN_STRIDE; i += blockDim.x) gbins[i] = 0;
   } else {
@@ -232,8 +232,8 @@ __global__ void __launch_bounds__(CENSUS_THREADS)
                  int nmask, int ncls, int ngraphs, int sub, unsigned long long* __restrict__ hist) {
   __shared__ unsigned long long bins[kBatched ? 1 : BIN_STRIDE];
   __shared__ unsigned int gbins[kBatched ? MAX_GRAPHS * BIN_STRIDE : 1];
-  __shared__ uint8_t lut[2048];
-  for (int i = threadIdx.x; i < nmask; i += blockDim.x) lut[i] = lut_g[i];
+  __shared__ __align__(16) uint8_t lut[2048];
+  load_lut(lut, lut_g, nmask);
   if (kBatched) {
     for (int i = threadIdx.x; i < ngraphs * BIN_STRIDE; i += blockDim.x) gbins[i] = 0;
   } else {
@@ -412,13 +412,14 @@ void spaces_enqueue(hm_graph* g, const std::vector<std::pair<hm_graph::Space*, c
   if (P.need.empty()) return;
   const int nj = (int)P.need.size();
   HM_CHECK(nj <= 8, HM_EINVAL, "too many work spaces");
-  // one allocation for all prefix-sum arrays (anchors + 1 entries each)
+  // one allocation: the scan's scratch (zeroed), the totals, then the
+  // prefix-sum arrays (anchors + 1 entries each)
   WsArgs W{};
   W.nj = nj;
   W.groups = (uint64_t)(g->bwords / 4);
   int64_t maxA = 0;
-  size_t bytes = 0;
   size_t off[8];
+  ScanJob jobs[8];
   for (int i = 0; i < nj; ++i) {
     const char fam = P.need[i].second;
     int64_t a = 0;
@@ -428,29 +429,34 @@ void spaces_enqueue(hm_graph* g, const std::vector<std::pair<hm_graph::Space*, c
     W.fam[i] = fam;
     W.A[i] = a;
     maxA = std::max(maxA, a);
+    jobs[i].n = a;
+  }
+  // scan_batch_scratch reads only the sizes
+  const size_t scan_bytes = (scan_batch_scratch(jobs, nj) + 255) & ~(size_t)255;
+  size_t bytes = scan_bytes + 256;  // totals
+  for (int i = 0; i < nj; ++i) {
     off[i] = bytes;
-    bytes += (((size_t)a + 1) * sizeof(uint64_t) + 255) & ~(size_t)255;
+    bytes += (((size_t)W.A[i] + 1) * sizeof(uint64_t) + 255) & ~(size_t)255;
   }
   unsigned char* base = dalloc<unsigned char>(bytes, s);
   P.made.push_back(reinterpret_cast<uint64_t*>(base));
   try {
-    DBuf<uint64_t> totals(nj, s);
-    ScanJob jobs[8];
+    uint64_t* totals = reinterpret_cast<uint64_t*>(base + scan_bytes);
     for (int i = 0; i < nj; ++i) {
       W.out[i] = reinterpret_cast<uint64_t*>(base + off[i]);
       jobs[i].a = W.out[i];
-      jobs[i].n = W.A[i];
-      jobs[i].total = totals.p + i;
+      jobs[i].total = totals + i;
       P.ws[i] = W.out[i];
       P.need[i].first->anchors = W.A[i];
     }
+    if (scan_bytes) HM_CUDA(cudaMemsetAsync(base, 0, scan_bytes, s));
     if (maxA > 0) {
       k_ws_all<<<grid1d(maxA), 256, 0, s>>>(g->off2, g->off3, g->e2, g->e3, W, maxA);
       HM_KCHECK();
     }
-    scan_batch_inplace(jobs, nj, s);
+    scan_batch_inplace(jobs, nj, s, scan_bytes ? base : nullptr, true);
     P.h = pinned_words() + 64;
-    HM_CUDA(cudaMemcpyAsync(P.h, totals.p, nj * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    HM_CUDA(cudaMemcpyAsync(P.h, totals, nj * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   } catch (...) {
     for (uint64_t* p : P.made) cudaFreeAsync(p, s);
     P.made.clear();

@@ -118,8 +118,9 @@ struct Fork {
   static constexpr int kSide = 3;
   cudaStream_t main;
   cudaStream_t side[kSide] = {};
+  int width;  // side streams in use, 1..kSide (each costs two runtime calls per fork-join)
   bool joined = false;
-  explicit Fork(cudaStream_t s);
+  explicit Fork(cudaStream_t s, int width = kSide);
   cudaStream_t operator[](int i) const { return side[i]; }
   void join();
   ~Fork();
@@ -168,7 +169,11 @@ struct SortJob {
 };
 // Sorts 1-4 independent arrays together (one temporary allocation, one
 // launch per pass index for all of them).
-void sort_batch(const SortJob* jobs, int njobs, cudaStream_t s);
+// With `scratch` (device, sort_batch_scratch bytes, 256-byte aligned) nothing
+// is allocated; `zeroed`: its first *zero_bytes bytes are already zero.
+void sort_batch(const SortJob* jobs, int njobs, cudaStream_t s, unsigned char* scratch = nullptr,
+                bool zeroed = false);
+size_t sort_batch_scratch(const SortJob* jobs, int njobs, size_t* zero_bytes);
 // Exclusive scans of 1-8 arrays in place, in one launch: a[0..n) becomes the
 // prefix sums of its inputs and a[n] (which must exist) the total, also
 // written to *total (device, may be NULL).
@@ -177,7 +182,11 @@ struct ScanJob {
   int64_t n = 0;
   uint64_t* total = nullptr;
 };
-void scan_batch_inplace(const ScanJob* jobs, int njobs, cudaStream_t s);
+void scan_batch_inplace(const ScanJob* jobs, int njobs, cudaStream_t s,
+                        unsigned char* scratch = nullptr, bool zeroed = false);
+// Bytes of `scratch` a batch needs (256-byte aligned, all of it zeroed unless
+// `zeroed`); 0 when every array fits one tile and no scratch is used.
+size_t scan_batch_scratch(const ScanJob* jobs, int njobs);
 // Stable LSD radix sort of n keys on bits [lo_bit, lo_bit + bits); vals
 // (nullable) are permuted alongside. Keys equal on those bits keep their input
 // order.
@@ -288,6 +297,14 @@ struct DevGraph {
   int32_t block;
   uint64_t block_inv;
 };
+
+// Copies a class LUT (nmask bytes, a multiple of 16, from a 16-byte aligned
+// device copy) into 16-byte aligned shared memory with 16-byte loads: one
+// round trip to memory instead of nmask / blockDim.x dependent byte loads.
+__device__ __forceinline__ void load_lut(uint8_t* lut_s, const uint8_t* lut_g, int nmask) {
+  for (int i = threadIdx.x; i < nmask / 16; i += blockDim.x)
+    reinterpret_cast<uint4*>(lut_s)[i] = __ldg(reinterpret_cast<const uint4*>(lut_g) + i);
+}
 
 __device__ __forceinline__ int32_t graph_of(const DevGraph& g, int32_t v) {
   return g.block ? (int32_t)__umul64hi((uint64_t)(uint32_t)v, g.block_inv) : 0;

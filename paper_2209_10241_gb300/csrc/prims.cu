@@ -177,7 +177,7 @@ ForkEvents& fork_events(int dev) {
 }
 }  // namespace
 
-Fork::Fork(cudaStream_t s) : main(s) {
+Fork::Fork(cudaStream_t s, int w) : main(s), width(w < 1 ? 1 : w > kSide ? kSide : w) {
   int dev = 0;
   HM_CUDA(cudaGetDevice(&dev));
   HM_CHECK(dev >= 0 && dev < 64, HM_ECUDA, "device ordinal above 63");
@@ -191,7 +191,7 @@ Fork::Fork(cudaStream_t s) : main(s) {
   }
   ForkEvents& ev = fork_events(dev);
   HM_CUDA(cudaEventRecord(ev.e[0], main));
-  for (int i = 0; i < kSide; ++i) HM_CUDA(cudaStreamWaitEvent(side[i], ev.e[0], 0));
+  for (int i = 0; i < width; ++i) HM_CUDA(cudaStreamWaitEvent(side[i], ev.e[0], 0));
 }
 
 void Fork::join() {
@@ -200,7 +200,7 @@ void Fork::join() {
   int dev = 0;
   HM_CUDA(cudaGetDevice(&dev));
   ForkEvents& ev = fork_events(dev);
-  for (int i = 0; i < kSide; ++i) {
+  for (int i = 0; i < width; ++i) {
     HM_CUDA(cudaEventRecord(ev.e[1 + i], side[i]));
     HM_CUDA(cudaStreamWaitEvent(main, ev.e[1 + i], 0));
   }
@@ -212,7 +212,7 @@ Fork::~Fork() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
   ForkEvents& ev = fork_events(dev);
-  for (int i = 0; i < kSide; ++i)
+  for (int i = 0; i < width; ++i)
     if (cudaEventRecord(ev.e[1 + i], side[i]) == cudaSuccess)
       cudaStreamWaitEvent(main, ev.e[1 + i], 0);
 }

@@ -269,8 +269,8 @@ __global__ void __launch_bounds__(SAMPLE_THREADS)
              uint64_t total, const uint64_t* __restrict__ wt, const uint8_t* __restrict__ lut_g,
              int nmask, int ncls, unsigned long long* __restrict__ raw) {
   __shared__ unsigned long long blo[176], bhi[176];
-  __shared__ uint8_t lut[2048];
-  for (int i = threadIdx.x; i < nmask; i += blockDim.x) lut[i] = lut_g[i];
+  __shared__ __align__(16) uint8_t lut[2048];
+  load_lut(lut, lut_g, nmask);
   for (int i = threadIdx.x; i < ncls; i += blockDim.x) blo[i] = bhi[i] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;

@@ -52,6 +52,7 @@ struct JobDev {
   uint64_t* status[2];  // [tiles][256] per pass parity
   uint64_t* ustatus;    // [tiles] for unique
   uint32_t* ctr;        // [np + 1] tile tickets (last one: unique)
+  uint32_t* rank;       // small jobs: [n] ranks (zeroed)
 };
 
 struct Batch {
@@ -363,22 +364,129 @@ __global__ void __launch_bounds__(TPB) k_sort_unique(const Batch B, const Grid G
   }
 }
 
-// Jobs of at most SMALL_KEYS keys: one block of SMALL_BT threads per job
-// (the jobs listed in G), everything in one launch. The keys stay in shared
-// memory; each thread holds ipt = ceil(n / SMALL_BT) of them (1..8), so small
-// jobs run short per-warp chains. A pass ranks each key within its warp
-// (match on the digit, per-warp counters), turns the (digit, warp) counters
-// into offsets with one block-wide scan in digit-major order, and scatters;
-// order among equal digits is kept, as LSD radix sort needs.
-constexpr int SMALL_BT = 1024, SMALL_NW = SMALL_BT / 32, SMALL_IPT = 8;
-constexpr int64_t SMALL_KEYS = (int64_t)SMALL_BT * SMALL_IPT;
-constexpr size_t SMALL_SMEM = (size_t)SMALL_KEYS * 16 + (size_t)SMALL_NW * 256 * 4 + 64 * 4;
+// Jobs of at most SMALL_KEYS keys, sorted by counting ranks over the whole
+// GPU: a key's place is the number of keys ordered before it, comparing only
+// the bits the job's digit passes cover (the high word b first) and breaking
+// ties by index, which keeps the sort stable. k_sort_rank: job k of G owns
+// T_k^2 blocks, T_k = ceil(n / RANK_T); block (it, jt) compares the keys of
+// tile it with those of tile jt (kept in shared memory) and adds the partial
+// ranks with atomics. k_sort_place: one block per job puts the keys at their
+// ranks in shared memory, drops repeats and writes the output. O(n^2)
+// comparisons, 67M at 8,192 keys, spread over every SM instead of the
+// latency chain of one block's radix passes.
+constexpr int RANK_T = 256;  // keys per tile = threads per block of k_sort_rank
+constexpr int PLACE_T = 1024;  // threads per block of k_sort_place
+constexpr int64_t SMALL_KEYS = 8192;
+constexpr size_t PLACE_SMEM = (size_t)SMALL_KEYS * 16 + 32 * 4;
 
-// Exclusive scan of one value per thread over a block of SMALL_BT threads;
-// `total` gets the block's sum. Uses wtot[SMALL_NW]; ends with a barrier.
-__device__ __forceinline__ uint32_t small_block_scan(uint32_t x, uint32_t* wtot, uint32_t& total) {
+__device__ __forceinline__ void rank_masks(const JobDev& J, uint64_t& ma, uint64_t& mb) {
+  ma = 0;
+  mb = 0;
+  for (int p = 0; p < J.np; ++p) {
+    const uint64_t m = 0xFFull << J.shift[p];
+    if (J.arr[p])
+      mb |= m;
+    else
+      ma |= m;
+  }
+}
+
+__global__ void __launch_bounds__(RANK_T) k_sort_rank(const Batch B, const Grid G) {
+  __shared__ __align__(16) uint64_t ja[RANK_T];
+  __shared__ uint64_t jb[RANK_T];
+  const int e = grid_entry(G, blockIdx.x);
+  const JobDev& J = B.j[G.job[e]];
+  const int n = (int)J.n;
+  const int T = (n + RANK_T - 1) / RANK_T;
+  const int q = (int)(blockIdx.x - G.first[e]);
+  const int it = q / T, jt = q - (q / T) * T;
+  uint64_t ma, mb;
+  rank_masks(J, ma, mb);
+  const bool has_b = J.b[0] != nullptr;
+  const int j0 = jt * RANK_T, m = min(RANK_T, n - j0);
+  const int i = it * RANK_T + threadIdx.x;
+  if (mb == 0 && (ma >> 51) == 0) {
+    // the sorted bits and the index fit one word: (key << 13) | index orders
+    // like (key, index) and is unique, so one compare per pair; slots past
+    // the tile hold the largest word, which ranks before nothing
+    const uint64_t cj = threadIdx.x < m
+                            ? ((J.a[0][j0 + threadIdx.x] & ma) << 13) | (uint64_t)(j0 + threadIdx.x)
+                            : ~0ull;
+    ja[threadIdx.x] = cj;
+    const uint64_t ci = i < n ? ((J.a[0][i] & ma) << 13) | (uint64_t)i : 0;
+    __syncthreads();
+    if (i < n) {
+      uint32_t c = 0;
+      const ulonglong2* j2 = reinterpret_cast<const ulonglong2*>(ja);
+#pragma unroll 8
+      for (int t = 0; t < RANK_T / 2; ++t) {
+        const ulonglong2 w = j2[t];
+        c += (w.x < ci ? 1u : 0u) + (w.y < ci ? 1u : 0u);
+      }
+      if (c) atomicAdd(&J.rank[i], c);
+    }
+    return;
+  }
+  if (threadIdx.x < m) {
+    ja[threadIdx.x] = J.a[0][j0 + threadIdx.x] & ma;
+    jb[threadIdx.x] = has_b ? (J.b[0][j0 + threadIdx.x] & mb) : 0;
+  }
+  uint64_t ai = 0, bi = 0;
+  if (i < n) {
+    ai = J.a[0][i] & ma;
+    bi = has_b ? (J.b[0][i] & mb) : 0;
+  }
+  __syncthreads();
+  if (i < n) {
+    uint32_t c = 0;
+    for (int t = 0; t < m; ++t) {
+      const uint64_t aj = ja[t], bj = jb[t];
+      const bool before = bj < bi || (bj == bi && (aj < ai || (aj == ai && j0 + t < i)));
+      c += before ? 1u : 0u;
+    }
+    if (c) atomicAdd(&J.rank[i], c);
+  }
+}
+
+__global__ void __launch_bounds__(PLACE_T) k_sort_place(const Batch B, const Grid G) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* ka_s = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* kb_s = ka_s + SMALL_KEYS;
+  uint32_t* wtot = reinterpret_cast<uint32_t*>(kb_s + SMALL_KEYS);
+  const JobDev& J = B.j[G.job[blockIdx.x]];
+  const int n = (int)J.n;
+  const bool has_b = J.b[0] != nullptr;
+  // ranks are a permutation of [0, n) (each counts fewer than n keys)
+  for (int k = threadIdx.x; k < n; k += PLACE_T) {
+    const uint32_t r = J.rank[k];
+    ka_s[r] = J.a[0][k];
+    kb_s[r] = has_b ? J.b[0][k] : 0;
+  }
+  __syncthreads();
+  if (!J.unique) {
+    for (int k = threadIdx.x; k < n; k += PLACE_T) {
+      J.a[0][k] = ka_s[k];
+      if (has_b) J.b[0][k] = kb_s[k];
+    }
+    return;
+  }
+  // unique: a key is kept when it differs from its predecessor; thread t owns
+  // keys [t * ipt, (t + 1) * ipt), ipt <= 8
+  const int ipt = (n + PLACE_T - 1) / PLACE_T;
+  const int i0 = threadIdx.x * ipt;
+  uint32_t keep = 0, cnt = 0;
+  for (int u = 0; u < ipt; ++u) {
+    const int k = i0 + u;
+    if (k >= n) break;
+    bool kp = k == 0 || ka_s[k] != ka_s[k - 1];
+    if (!kp && J.b_is_key && has_b) kp = kb_s[k] != kb_s[k - 1];
+    if (kp) {
+      keep |= 1u << u;
+      ++cnt;
+    }
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t incl = x;
+  uint32_t incl = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -387,140 +495,36 @@ __device__ __forceinline__ uint32_t small_block_scan(uint32_t x, uint32_t* wtot,
   if (lane == 31) wtot[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    uint32_t v = lane < SMALL_NW ? wtot[lane] : 0u;
+    uint32_t v = wtot[lane];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
       if (lane >= o) v += y;
     }
-    if (lane < SMALL_NW) wtot[lane] = v;
+    wtot[lane] = v;
   }
   __syncthreads();
-  total = wtot[SMALL_NW - 1];
-  const uint32_t r = (warp ? wtot[warp - 1] : 0u) + incl - x;
-  __syncthreads();
-  return r;
-}
-
-__global__ void __launch_bounds__(SMALL_BT) k_sort_small(const Batch B, const Grid G) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t* ka_s = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* kb_s = ka_s + SMALL_KEYS;
-  uint32_t(*wcnt)[256] = reinterpret_cast<uint32_t(*)[256]>(kb_s + SMALL_KEYS);
-  uint32_t* wtot = reinterpret_cast<uint32_t*>(wcnt + SMALL_NW);
-  const JobDev& J = B.j[G.job[blockIdx.x]];
-  const int n = (int)J.n;
-  const int ipt = (n + SMALL_BT - 1) / SMALL_BT;  // 1..SMALL_IPT
-  const int cap = ipt * SMALL_BT;
-  const bool has_b = J.b[0] != nullptr;
-  for (int i = threadIdx.x; i < cap; i += SMALL_BT) {
-    ka_s[i] = i < n ? J.a[0][i] : 0;
-    kb_s[i] = (has_b && i < n) ? J.b[0][i] : 0;
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  // scan ownership: thread t sums the counters of digit t / 4 over warps
-  // 8 (t % 4) .. 8 (t % 4) + 7, so thread order is digit-major
-  const int sd = threadIdx.x >> 2, sw = (threadIdx.x & 3) * 8;
-  for (int p = 0; p < J.np; ++p) {
-    const int shift = J.shift[p];
-    const bool on_b = J.arr[p] != 0;
-    for (int i = threadIdx.x; i < SMALL_NW * 256; i += SMALL_BT) (&wcnt[0][0])[i] = 0;
-    __syncthreads();
-    uint32_t dig[SMALL_IPT], rank[SMALL_IPT];
-    uint64_t ka[SMALL_IPT], kb[SMALL_IPT];
-#pragma unroll
-    for (int it = 0; it < SMALL_IPT; ++it) {
-      if (it >= ipt) break;
-      const int idx = warp * (32 * ipt) + it * 32 + lane;
-      ka[it] = ka_s[idx];
-      kb[it] = kb_s[idx];
-      const bool valid = idx < n;
-      const uint32_t d = valid ? (uint32_t)(((on_b ? kb[it] : ka[it]) >> shift) & 255u) : 256u;
-      const unsigned peers = __match_any_sync(0xffffffffu, d);
-      const uint32_t before = valid ? wcnt[warp][d] : 0u;
-      __syncwarp();
-      if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = before + __popc(peers);
-      __syncwarp();
-      dig[it] = d;
-      rank[it] = before + __popc(peers & lt);
-    }
-    __syncthreads();
-    {
-      uint32_t c[8], sum = 0;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        c[k] = wcnt[sw + k][sd];
-        sum += c[k];
-      }
-      uint32_t total;
-      uint32_t run = small_block_scan(sum, wtot, total);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        wcnt[sw + k][sd] = run;
-        run += c[k];
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int it = 0; it < SMALL_IPT; ++it) {
-      if (it >= ipt) break;
-      const int idx = warp * (32 * ipt) + it * 32 + lane;
-      if (idx < n) {
-        const uint32_t pos = wcnt[warp][dig[it]] + rank[it];
-        ka_s[pos] = ka[it];
-        kb_s[pos] = kb[it];
-      }
-    }
-    __syncthreads();
-  }
-  if (!J.unique) {
-    for (int i = threadIdx.x; i < n; i += SMALL_BT) {
-      J.a[0][i] = ka_s[i];
-      if (has_b) J.b[0][i] = kb_s[i];
-    }
-    return;
-  }
-  // unique: a key is kept when it differs from its predecessor; thread t owns
-  // keys [t * ipt, (t + 1) * ipt)
-  const int i0 = threadIdx.x * ipt;
-  uint32_t keep = 0, cnt = 0;
-#pragma unroll
-  for (int it = 0; it < SMALL_IPT; ++it) {
-    if (it >= ipt) break;
-    const int i = i0 + it;
-    if (i < n) {
-      bool k = i == 0 || ka_s[i] != ka_s[i - 1];
-      if (!k && J.b_is_key && has_b) k = kb_s[i] != kb_s[i - 1];
-      if (k) {
-        keep |= 1u << it;
-        ++cnt;
-      }
-    }
-  }
-  uint32_t total;
-  uint64_t pos = small_block_scan(cnt, wtot, total);
-  if (threadIdx.x == 0 && J.d_kept) *J.d_kept = total;
-  const int mb = J.member_bits;
-  const uint64_t mask = (1ull << mb) - 1;
-#pragma unroll
-  for (int it = 0; it < SMALL_IPT; ++it) {
-    if (!((keep >> it) & 1u)) continue;
-    const int i = i0 + it;
-    const uint64_t ka = ka_s[i], kb = kb_s[i];
+  if (threadIdx.x == 0 && J.d_kept) *J.d_kept = wtot[PLACE_T / 32 - 1];
+  uint64_t pos = (warp ? wtot[warp - 1] : 0u) + incl - cnt;
+  const int mbits = J.member_bits;
+  const uint64_t mask = (1ull << mbits) - 1;
+  for (int u = 0; u < ipt; ++u) {
+    if (!((keep >> u) & 1u)) continue;
+    const int k = i0 + u;
+    const uint64_t ka = ka_s[k], kb = kb_s[k];
     if (J.unpack == SortJob::RAW) {
       static_cast<uint64_t*>(J.out)[pos] = ka;
       if (J.out_b) J.out_b[pos] = kb;
     } else if (J.unpack == SortJob::PAIR) {
-      static_cast<uint64_t*>(J.out)[pos] = ((ka >> mb) << 32) | (ka & mask);
+      static_cast<uint64_t*>(J.out)[pos] = ((ka >> mbits) << 32) | (ka & mask);
     } else {
       unsigned __int128 key = ((unsigned __int128)kb << 64) | ka;
       const int32_t m3 = (int32_t)((uint64_t)key & mask);
-      key >>= mb;
+      key >>= mbits;
       const int32_t m2 = (int32_t)((uint64_t)key & mask);
-      key >>= mb;
+      key >>= mbits;
       const int32_t m1 = (int32_t)((uint64_t)key & mask);
-      key >>= mb;
+      key >>= mbits;
       const int32_t m0 = (int32_t)((uint64_t)key & mask);
       static_cast<int4*>(J.out)[pos] = J.unpack == SortJob::TRIPLE
                                            ? make_int4(m1, m2, m3, -1)
@@ -530,31 +534,38 @@ __global__ void __launch_bounds__(SMALL_BT) k_sort_small(const Batch B, const Gr
   }
 }
 
-// The one-block sort's shared memory is above the default 48 KB: opt in once
-// per device.
-void small_sort_attr() {
+// k_sort_place's shared memory is above the default 48 KB: opt in once per
+// device.
+void place_smem_attr() {
   static std::atomic<uint64_t> done{0};
   int dev = 0;
   HM_CUDA(cudaGetDevice(&dev));
   const uint64_t bit = 1ull << (dev & 63);
   if (done.load(std::memory_order_acquire) & bit) return;
-  HM_CUDA(cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)SMALL_SMEM));
+  HM_CUDA(cudaFuncSetAttribute(k_sort_place, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)PLACE_SMEM));
   done.fetch_or(bit, std::memory_order_acq_rel);
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-}  // namespace
-
-void sort_batch(const SortJob* jobs, int njobs, cudaStream_t s) {
-  HM_CHECK(njobs >= 1 && njobs <= SORT_MAX_JOBS, HM_EINVAL, "sort batch of 1-4 jobs");
+// Layout of a batch's scratch: [zeroed: per job status[0] | ustatus | ghist |
+// ctr | rank ; done] [per job: status[1] | gbase | temporaries].
+struct SortPlan {
   Batch B{};
-  B.nj = njobs;
-  // scratch: [zeroed: per job status[0] | ustatus | ghist | ctr ; done] [per job: status[1] |
-  // gbase | temporaries]
+  std::vector<size_t> zoff, off;
   size_t zbytes = 0, bytes = 0;
-  std::vector<size_t> zoff(njobs), off(njobs);
+};
+
+void plan_sort(const SortJob* jobs, int njobs, SortPlan& P) {
+  HM_CHECK(njobs >= 1 && njobs <= SORT_MAX_JOBS, HM_EINVAL, "sort batch of 1-4 jobs");
+  Batch& B = P.B;
+  B.nj = njobs;
+  size_t zbytes = 0, bytes = 0;
+  std::vector<size_t>& zoff = P.zoff;
+  std::vector<size_t>& off = P.off;
+  zoff.assign(njobs, 0);
+  off.assign(njobs, 0);
   for (int k = 0; k < njobs; ++k) {
     const SortJob& S = jobs[k];
     HM_CHECK(S.n >= 0 && S.n < (1ll << 31), HM_EINVAL, "sort input too large");
@@ -578,6 +589,7 @@ void sort_batch(const SortJob* jobs, int njobs, cudaStream_t s) {
     zoff[k] = zbytes;
     zbytes += align256((size_t)J.tiles * 256 * 8) + align256((size_t)J.tiles * 8) +
               align256((size_t)SORT_MAX_PASSES * 256 * 4) + align256((SORT_MAX_PASSES + 1) * 4);
+    if (J.n >= 1 && J.n <= SMALL_KEYS) zbytes += align256((size_t)J.n * 4);
   }
   zbytes += 256;  // done counter
   bytes = zbytes;
@@ -587,8 +599,29 @@ void sort_batch(const SortJob* jobs, int njobs, cudaStream_t s) {
     bytes += align256((size_t)J.tiles * 256 * 8) + align256((size_t)SORT_MAX_PASSES * 256 * 4);
     if (J.np > 0) bytes += align256((size_t)J.n * 8) * (jobs[k].b ? 2 : 1);
   }
-  DBuf<unsigned char> scratch(bytes, s);
-  unsigned char* base = scratch.p;
+  P.zbytes = zbytes;
+  P.bytes = bytes;
+}
+
+}  // namespace
+
+size_t sort_batch_scratch(const SortJob* jobs, int njobs, size_t* zero_bytes) {
+  SortPlan P;
+  plan_sort(jobs, njobs, P);
+  if (zero_bytes) *zero_bytes = P.zbytes;
+  return P.bytes;
+}
+
+void sort_batch(const SortJob* jobs, int njobs, cudaStream_t s, unsigned char* ext_scratch,
+                bool zeroed) {
+  SortPlan P;
+  plan_sort(jobs, njobs, P);
+  Batch& B = P.B;
+  const size_t zbytes = P.zbytes, bytes = P.bytes;
+  const std::vector<size_t>& zoff = P.zoff;
+  const std::vector<size_t>& off = P.off;
+  DBuf<unsigned char> scratch(ext_scratch ? 0 : bytes, s);
+  unsigned char* base = ext_scratch ? ext_scratch : scratch.p;
   for (int k = 0; k < njobs; ++k) {
     JobDev& J = B.j[k];
     const SortJob& S = jobs[k];
@@ -600,6 +633,8 @@ void sort_batch(const SortJob* jobs, int njobs, cudaStream_t s) {
     J.ghist = reinterpret_cast<uint32_t*>(z);
     z += align256((size_t)SORT_MAX_PASSES * 256 * 4);
     J.ctr = reinterpret_cast<uint32_t*>(z);
+    z += align256((SORT_MAX_PASSES + 1) * 4);
+    J.rank = (J.n >= 1 && J.n <= SMALL_KEYS) ? reinterpret_cast<uint32_t*>(z) : nullptr;
     unsigned char* q = base + off[k];
     J.status[1] = reinterpret_cast<uint64_t*>(q);
     q += align256((size_t)J.tiles * 256 * 8);
@@ -612,16 +647,27 @@ void sort_batch(const SortJob* jobs, int njobs, cudaStream_t s) {
     J.b[1] = (J.np > 0 && S.b) ? reinterpret_cast<uint64_t*>(q) : S.b;
   }
   uint32_t* done = reinterpret_cast<uint32_t*>(base + zbytes - 256);
-  HM_CUDA(cudaMemsetAsync(base, 0, zbytes, s));
-  // jobs of up to SMALL_KEYS keys: one block each, everything in one launch
+  if (!(ext_scratch && zeroed)) HM_CUDA(cudaMemsetAsync(base, 0, zbytes, s));
+  // jobs of up to SMALL_KEYS keys: ranks by counting, all such jobs in one
+  // launch (T^2 blocks per job, T = ceil(n / RANK_T))
   auto small = [&](int k) { return B.j[k].n >= 1 && B.j[k].n <= SMALL_KEYS; };
   {
     Grid G{};
-    for (int k = 0; k < njobs; ++k)
-      if (small(k)) G.job[G.nj++] = k;
+    int64_t blocks = 0;
+    for (int k = 0; k < njobs; ++k) {
+      if (!small(k)) continue;
+      const int64_t T = (B.j[k].n + RANK_T - 1) / RANK_T;
+      G.job[G.nj] = k;
+      G.first[G.nj] = blocks;
+      blocks += T * T;
+      ++G.nj;
+    }
+    G.first[G.nj] = blocks;
     if (G.nj) {
-      small_sort_attr();
-      k_sort_small<<<(unsigned)G.nj, SMALL_BT, SMALL_SMEM, s>>>(B, G);
+      k_sort_rank<<<(unsigned)blocks, RANK_T, 0, s>>>(B, G);
+      HM_KCHECK();
+      place_smem_attr();
+      k_sort_place<<<(unsigned)G.nj, PLACE_T, PLACE_SMEM, s>>>(B, G);
       HM_KCHECK();
     }
   }
@@ -755,6 +801,7 @@ struct ScanDev {
 };
 struct ScanBatch {
   int nj;
+  int single;  // every job is one tile: no tickets, no look-back, no scratch
   ScanDev j[SCAN_JOBS];
   int64_t first[SCAN_JOBS + 1];
 };
@@ -769,7 +816,7 @@ __global__ void __launch_bounds__(TPB) k_scan_batch(const ScanBatch B) {
   int e = 0;
   while (e + 1 < B.nj && (int64_t)blockIdx.x >= B.first[e + 1]) ++e;
   const ScanDev& J = B.j[e];
-  if (threadIdx.x == 0) tile_s = atomicAdd(J.ctr, 1u);
+  if (threadIdx.x == 0) tile_s = B.single ? 0u : atomicAdd(J.ctr, 1u);
   __syncthreads();
   const int64_t tile = tile_s;
   const int64_t i0 = tile * TILE + (int64_t)threadIdx.x * IPT;
@@ -797,7 +844,7 @@ __global__ void __launch_bounds__(TPB) k_scan_batch(const ScanBatch B) {
   if (threadIdx.x < 32) {
     uint64_t excl = 0;
     if (tile == 0) {
-      if (threadIdx.x == 0) st_status(J.status, ST_PREFIX | total);
+      if (threadIdx.x == 0 && !B.single) st_status(J.status, ST_PREFIX | total);
     } else {
       if (threadIdx.x == 0) st_status(J.status + tile, ST_AGG | total);
       excl = look_back_warp(J.status, tile);
@@ -822,7 +869,21 @@ __global__ void __launch_bounds__(TPB) k_scan_batch(const ScanBatch B) {
 
 }  // namespace
 
-void scan_batch_inplace(const ScanJob* jobs, int njobs, cudaStream_t s) {
+// Scratch of a multi-tile scan batch: per array its tile status words and
+// ticket counter, all of it to be zeroed; 0 when every array is one tile.
+size_t scan_batch_scratch(const ScanJob* jobs, int njobs) {
+  size_t bytes = 256;
+  int64_t blocks = 0;
+  for (int k = 0; k < njobs; ++k) {
+    const int64_t tiles = std::max<int64_t>(1, (jobs[k].n + TILE - 1) / TILE);
+    bytes += align256((size_t)tiles * 8) + 256;
+    blocks += tiles;
+  }
+  return blocks == njobs ? 0 : bytes;
+}
+
+void scan_batch_inplace(const ScanJob* jobs, int njobs, cudaStream_t s, unsigned char* ext_scratch,
+                        bool zeroed) {
   HM_CHECK(njobs >= 1 && njobs <= SCAN_JOBS, HM_EINVAL, "scan batch of 1-8 arrays");
   ScanBatch B{};
   B.nj = njobs;
@@ -843,12 +904,20 @@ void scan_batch_inplace(const ScanJob* jobs, int njobs, cudaStream_t s) {
   }
   B.first[njobs] = blocks;
   HM_CHECK(blocks < (1ll << 31), HM_EINVAL, "scan too large");
-  DBuf<unsigned char> scratch(bytes, s);
-  for (int k = 0; k < njobs; ++k) {
-    B.j[k].status = reinterpret_cast<uint64_t*>(scratch.p + off[k]);
-    B.j[k].ctr = reinterpret_cast<uint32_t*>(scratch.p + off[k] + align256((size_t)B.j[k].tiles * 8));
+  if (blocks == njobs) {
+    // one tile each: a block per array, nothing to allocate
+    B.single = 1;
+    k_scan_batch<<<(unsigned)blocks, TPB, 0, s>>>(B);
+    HM_KCHECK();
+    return;
   }
-  HM_CUDA(cudaMemsetAsync(scratch.p, 0, bytes, s));
+  DBuf<unsigned char> scratch(ext_scratch ? 0 : bytes, s);
+  unsigned char* base = ext_scratch ? ext_scratch : scratch.p;
+  for (int k = 0; k < njobs; ++k) {
+    B.j[k].status = reinterpret_cast<uint64_t*>(base + off[k]);
+    B.j[k].ctr = reinterpret_cast<uint32_t*>(base + off[k] + align256((size_t)B.j[k].tiles * 8));
+  }
+  if (!(ext_scratch && zeroed)) HM_CUDA(cudaMemsetAsync(base, 0, bytes, s));
   k_scan_batch<<<(unsigned)blocks, TPB, 0, s>>>(B);
   HM_KCHECK();
 }
