@@ -366,7 +366,7 @@ __global__ void k_ws_all(const int64_t* __restrict__ off2, const int64_t* __rest
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < maxA;
        i += (int64_t)gridDim.x * blockDim.x) {
     for (int k = 0; k < W.nj; ++k) {
-      if (i >= W.A[k]) continue;
+      if (i >= W.A[k] || W.fam[k] == 'c') continue;  // 'c': c4_bounds
       const char f = W.fam[k];
       uint64_t v = 0;
       if (f == 'W' || f == 'S' || f == 'w' || f == 's') {
@@ -423,7 +423,7 @@ void spaces_enqueue(hm_graph* g, const std::vector<std::pair<hm_graph::Space*, c
   for (int i = 0; i < nj; ++i) {
     const char fam = P.need[i].second;
     int64_t a = 0;
-    if (fam == 'W' || fam == 'S' || fam == 'w' || fam == 's') a = g->n;
+    if (fam == 'W' || fam == 'S' || fam == 'w' || fam == 's' || fam == 'c') a = g->n;
     if (fam == 'P' || fam == 'p') a = g->counts[2];
     if (fam == 'X' || fam == 'x') a = g->kmax >= 3 ? g->counts[3] : 0;
     W.fam[i] = fam;
@@ -454,6 +454,8 @@ void spaces_enqueue(hm_graph* g, const std::vector<std::pair<hm_graph::Space*, c
       k_ws_all<<<grid1d(maxA), 256, 0, s>>>(g->off2, g->off3, g->e2, g->e3, W, maxA);
       HM_KCHECK();
     }
+    for (int i = 0; i < nj; ++i)
+      if (W.fam[i] == 'c' && W.A[i] > 0) c4_bounds(g, W.out[i], s);
     scan_batch_inplace(jobs, nj, s, scan_bytes ? base : nullptr, true);
     P.h = pinned_words() + 64;
     HM_CUDA(cudaMemcpyAsync(P.h, totals, nj * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
@@ -494,11 +496,31 @@ void ensure_spaces(hm_graph* g, const std::vector<std::pair<hm_graph::Space*, ch
 
 // Persistent grid: SMs x resident blocks, capped by the work; with a union
 // of graphs, enough blocks that no block counts 2^31 candidates.
-int grid_for(const void* kernel, uint64_t lanes_needed, uint64_t max_candidates, bool batched) {
-  int dev = 0, sms = 0, per_sm = 0;
+// SM count and resident blocks per SM of a census kernel on the current
+// device, queried once per (kernel, device).
+void resident_blocks(const void* kernel, int& sms, int& per_sm) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, std::pair<int, int>> cache;
+  int dev = 0;
   HM_CUDA(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find({kernel, dev});
+    if (it != cache.end()) {
+      sms = it->second.first;
+      per_sm = it->second.second;
+      return;
+    }
+  }
   HM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, CENSUS_THREADS, 0));
+  std::lock_guard<std::mutex> lock(mu);
+  cache[{kernel, dev}] = {sms, per_sm};
+}
+
+int grid_for(const void* kernel, uint64_t lanes_needed, uint64_t max_candidates, bool batched) {
+  int sms = 0, per_sm = 0;
+  resident_blocks(kernel, sms, per_sm);
   if (per_sm < 1) per_sm = 1;
   const uint64_t need = (lanes_needed + CENSUS_THREADS - 1) / CENSUS_THREADS;
   uint64_t blocks = (uint64_t)sms * per_sm;
@@ -621,7 +643,7 @@ std::vector<std::pair<hm_graph::Space*, char>> census_spaces(hm_graph* g, int or
   }
   if (g->bits2)
     return {{&g->S, 'S'}, {&g->P, 'P'}, {&g->TX, 'X'}, {&g->Sb, 's'}, {&g->Pb, 'p'}, {&g->TXb, 'x'}};
-  return {{&g->S, 'S'}, {&g->P, 'P'}, {&g->TX, 'X'}};
+  return {{&g->S, 'S'}, {&g->P, 'P'}, {&g->TX, 'X'}, {&g->C4, 'c'}};
 }
 
 // The graphlet census replaces S and P: with pair bitmaps, when its word

@@ -21,6 +21,10 @@
 // its pair pattern, so the histogram ends with the pairs-only counts. All sums
 // are exact integers (uint64, subtraction modulo 2^64 with a non-negative
 // result).
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+
 #include "families.cuh"
 #include "hm_internal.cuh"
 
@@ -289,65 +293,221 @@ __global__ void __launch_bounds__(SPARSE_WARPS * 32)
 
 // 4-cycles of graphs without pair bitmaps, each at its highest-ranked node x
 // (rank = (degree, id)): the nodes z of lower rank reached by paths x - y - z
-// through a y of lower rank are counted (per-block dense counters, with the
-// list of the counters touched); every two such paths to one z close a
-// 4-cycle x - y - z - y'. Adds 2 C4 to the graph's sum, as the bitmap kernel
-// does.
-__global__ void k_graphlet_c4_sparse(const DevGraph g, int32_t nodes_per_graph,
-                                     uint32_t* __restrict__ acc_all, int32_t* __restrict__ touched_all,
-                                     unsigned long long* __restrict__ agg) {
-  __shared__ int tcount;
-  __shared__ unsigned long long part[32];
-  uint32_t* acc = acc_all + (size_t)blockIdx.x * g.n;
-  int32_t* touched = touched_all + (size_t)blockIdx.x * g.n;
-  // thread 0: the block's running sum for graph gcur, one atomic per graph
+// through a y of lower rank are counted, and every two such paths to one z
+// close a 4-cycle x - y - z - y'. Each pass adds 2 C4 to the graph's sum, as
+// the bitmap kernel does. The paths from x number at most ub(x) = the sum of
+// d(y) over its lower-ranked neighbours y, and the work sits in few nodes (on
+// a communication-shaped graph 1 % of the nodes hold 84 % of 2.2e8 paths, the
+// largest 3.6e5), so:
+//   ub <= warp bound: one warp per node counts in a shared-memory hash;
+//   above: the node's paths are written as keys (x << bits) | z into its
+//   slots (a prefix sum of the bounds, computed at build time; unused slots
+//   hold a sentinel), sorted, and each run of c equal keys adds C(c, 2).
+constexpr int C4_WARPS = 8;
+constexpr int C4_WARP_SLOTS = 512;
+constexpr uint32_t C4_WARP_UB = C4_WARP_SLOTS / 2;
+constexpr uint64_t C4_SENTINEL = ~0ull;
+
+// The warp tier's bound: C4_WARP_UB, or lower by HM_C4_UB (tests send small
+// graphs' nodes to the sort with it).
+uint32_t c4_warp_bound() {
+  uint32_t w = C4_WARP_UB;
+  if (const char* e = std::getenv("HM_C4_UB")) {
+    unsigned a = 0;
+    if (std::sscanf(e, "%u", &a) == 1) w = std::min<uint32_t>(a, C4_WARP_UB);
+  }
+  return w;
+}
+
+__device__ __forceinline__ bool lower_rank(int32_t dz, int32_t z, int32_t dx, int32_t x) {
+  return dz < dx || (dz == dx && z < x);
+}
+
+// Counts z in a table of 2^lg slots (keys -1 = empty). Every table holds
+// fewer distinct keys than slots, so a probe always ends; the bound on the
+// loop only makes that visible.
+__device__ __forceinline__ void c4_insert(int32_t* keys, uint32_t* cnt, int lg, int32_t z) {
+  const uint32_t mask = (1u << lg) - 1u;
+  uint32_t sl = ((uint32_t)z * 0x9E3779B1u) >> (32 - lg);
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    const int32_t k = atomicCAS(&keys[sl], -1, z);
+    if (k == -1 || k == z) {
+      atomicAdd(&cnt[sl], 1u);
+      return;
+    }
+    sl = (sl + 1) & mask;
+  }
+}
+
+__device__ __forceinline__ int c4_lg(uint32_t ub) {
+  int lg = 5;
+  while ((1u << lg) < 2 * ub) ++lg;
+  return lg;
+}
+
+// Running sum of one thread for graph gcur; one atomic per graph change.
+struct C4Sum {
   int64_t gcur = -1;
-  uint64_t scur = 0;
-  for (int64_t x = blockIdx.x; x < g.n; x += gridDim.x) {
-    const int32_t dx = degree(g, (int32_t)x);
-    if (threadIdx.x == 0) tcount = 0;
-    __syncthreads();
+  uint64_t s = 0;
+  __device__ void add(unsigned long long* agg, int64_t gi, uint64_t v) {
+    if (gi != gcur) {
+      flush(agg);
+      gcur = gi;
+      s = 0;
+    }
+    s += v;
+  }
+  __device__ void flush(unsigned long long* agg) {
+    if (gcur >= 0 && s) atomicAdd(&agg[gcur * NAGG + 6], (unsigned long long)(2 * s));
+  }
+};
+
+// Path bound of x over its lower-ranked neighbours, summed over the warp
+// (every lane gets it).
+__device__ __forceinline__ uint64_t c4_bound(const DevGraph& g, int32_t x, int64_t ox, int32_t dx) {
+  const int lane = threadIdx.x & 31;
+  uint64_t ub = 0;
+  for (int32_t i = lane; i < dx; i += 32) {
+    const int32_t y = g.adj2[ox + i];
+    const int32_t dy = degree(g, y);
+    if (lower_rank(dy, y, dx, x)) ub += (uint64_t)dy;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) ub += __shfl_xor_sync(0xffffffffu, ub, o);
+  return ub;
+}
+
+// Per node: its bound when above the warp tier's (its slots for the sort),
+// else 0. One warp per node.
+__global__ void k_c4_bound(const DevGraph g, uint32_t warp_ub, uint64_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t x64 = gw; x64 < g.n; x64 += warps) {
+    const int32_t x = (int32_t)x64;
     const int64_t ox = g.off2[x];
-    for (int32_t i = threadIdx.x; i < dx; i += blockDim.x) {
+    const uint64_t ub = c4_bound(g, x, ox, (int32_t)(g.off2[x + 1] - ox));
+    if (lane == 0) out[x] = ub > warp_ub ? ub : 0;
+  }
+}
+
+// Warp tier: one warp per node with a bound in [2, warp_ub].
+__global__ void __launch_bounds__(C4_WARPS * 32)
+    k_c4_warp(const DevGraph g, int32_t nodes_per_graph, uint32_t warp_ub,
+              unsigned long long* __restrict__ agg) {
+  __shared__ int32_t keys_s[C4_WARPS][C4_WARP_SLOTS];
+  __shared__ uint32_t cnt_s[C4_WARPS][C4_WARP_SLOTS];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t* keys = keys_s[wid];
+  uint32_t* cnt = cnt_s[wid];
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  C4Sum acc;
+  for (int64_t x64 = gw; x64 < g.n; x64 += warps) {
+    const int32_t x = (int32_t)x64;
+    const int64_t ox = g.off2[x];
+    const int32_t dx = (int32_t)(g.off2[x + 1] - ox);
+    const uint64_t ub = c4_bound(g, x, ox, dx);
+    if (ub < 2 || ub > warp_ub) continue;  // no 4-cycle at x / counted by sort
+    const int lg = c4_lg((uint32_t)ub);
+    for (int i = lane; i < (1 << lg); i += 32) {
+      keys[i] = -1;
+      cnt[i] = 0;
+    }
+    __syncwarp();
+    for (int32_t i = lane; i < dx; i += 32) {
       const int32_t y = g.adj2[ox + i];
       const int32_t dy = degree(g, y);
-      if (!(dy < dx || (dy == dx && y < x))) continue;
+      if (!lower_rank(dy, y, dx, x)) continue;
       const int64_t oy = g.off2[y];
       for (int32_t k = 0; k < dy; ++k) {
         const int32_t z = g.adj2[oy + k];
         if (z == x) continue;
-        const int32_t dz = degree(g, z);
-        if (!(dz < dx || (dz == dx && z < x))) continue;
-        if (atomicAdd(&acc[z], 1u) == 0u) touched[atomicAdd(&tcount, 1)] = z;
+        if (lower_rank(degree(g, z), z, dx, x)) c4_insert(keys, cnt, lg, z);
       }
     }
-    __syncthreads();
+    __syncwarp();
     uint64_t sum = 0;
-    const int tc = tcount;
-    for (int i = threadIdx.x; i < tc; i += blockDim.x) {
-      const int32_t z = touched[i];
-      const uint64_t c = acc[z];
-      sum += c * (c - 1) / 2;
-      acc[z] = 0;
+    for (int i = lane; i < (1 << lg); i += 32) {
+      const uint64_t c = keys[i] >= 0 ? cnt[i] : 0u;
+      sum += c * (c - (c > 0 ? 1 : 0)) / 2;
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = sum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      uint64_t s = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
-      const int64_t gi = x / nodes_per_graph;
-      if (gi != gcur) {
-        if (scur) atomicAdd(&agg[gcur * NAGG + 6], (unsigned long long)(2 * scur));
-        gcur = gi;
-        scur = 0;
-      }
-      scur += s;
-    }
-    __syncthreads();
+    if (lane == 0) acc.add(agg, x / nodes_per_graph, sum);
+    __syncwarp();
   }
-  if (threadIdx.x == 0 && scur) atomicAdd(&agg[gcur * NAGG + 6], (unsigned long long)(2 * scur));
+  if (lane == 0) acc.flush(agg);
+}
+
+// Sort tier, emission: one warp per node with slots [ws[x], ws[x+1]); the
+// lower-ranked neighbours y take consecutive sub-ranges of d(y) slots (a warp
+// scan per round of 32), each filled with the key of every kept z, else the
+// sentinel.
+__global__ void k_c4_emit(const DevGraph g, int bits, const uint64_t* __restrict__ ws,
+                          uint64_t* __restrict__ keys) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t x64 = gw; x64 < g.n; x64 += warps) {
+    const int32_t x = (int32_t)x64;
+    uint64_t base = ws[x];
+    if (ws[x + 1] == base) continue;
+    const int64_t ox = g.off2[x];
+    const int32_t dx = (int32_t)(g.off2[x + 1] - ox);
+    const uint64_t hi = (uint64_t)x << bits;
+    for (int32_t i0 = 0; i0 < dx; i0 += 32) {
+      const int32_t i = i0 + lane;
+      int32_t y = 0, dy = 0;
+      if (i < dx) {
+        y = g.adj2[ox + i];
+        dy = degree(g, y);
+        if (!lower_rank(dy, y, dx, x)) dy = 0;
+      }
+      uint32_t incl = (uint32_t)dy;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      uint64_t* out = keys + base + (incl - (uint32_t)dy);
+      if (dy) {
+        const int64_t oy = g.off2[y];
+        for (int32_t k = 0; k < dy; ++k) {
+          const int32_t z = g.adj2[oy + k];
+          const bool keep = z != x && lower_rank(degree(g, z), z, dx, x);
+          out[k] = keep ? (hi | (uint64_t)z) : C4_SENTINEL;
+        }
+      }
+      base += __shfl_sync(0xffffffffu, incl, 31);
+    }
+  }
+}
+
+// Sort tier, counting: each run of c equal keys (c paths from x to one z)
+// closes C(c, 2) 4-cycles at x.
+__global__ void k_c4_runs(const uint64_t* __restrict__ keys, uint64_t nkeys, int bits,
+                          int32_t nodes_per_graph, unsigned long long* __restrict__ agg) {
+  C4Sum acc;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nkeys;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = keys[i];
+    if (k == C4_SENTINEL || (i > 0 && keys[i - 1] == k)) continue;
+    uint64_t c = 1;
+    while (i + c < nkeys && keys[i + c] == k) ++c;
+    if (c > 1) acc.add(agg, (int64_t)(k >> bits) / nodes_per_graph, c * (c - 1) / 2);
+  }
+  // one flush per warp when its lanes share a graph
+  const int lane = threadIdx.x & 31;
+  const int64_t g0 = __shfl_sync(0xffffffffu, acc.gcur, 0);
+  if (__all_sync(0xffffffffu, acc.gcur == g0 || acc.gcur < 0 || acc.s == 0)) {
+    uint64_t s = acc.s;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0 && g0 >= 0 && s) atomicAdd(&agg[g0 * NAGG + 6], (unsigned long long)(2 * s));
+  } else {
+    acc.flush(agg);
+  }
 }
 
 struct PatternClasses {
@@ -410,7 +570,6 @@ unsigned grid_n(uint64_t n) {
 // connected patterns, in the order star, path, paw, 4-cycle, diamond, 4-clique.
 static const uint32_t kPatternMask[6] = {7u, 41u, 15u, 45u, 31u, 63u};
 
-constexpr int SPARSE_C4_BLOCKS = 152;
 constexpr int SPARSE_EDGE_BLOCKS = 152 * 8;
 
 void graphlet_prepare(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
@@ -419,21 +578,30 @@ void graphlet_prepare(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
   const size_t tb = ((size_t)g->n * 4 + 255) & ~(size_t)255;
   const size_t ab = ((size_t)G.ngraphs * NAGG * 8 + 255) & ~(size_t)255;
   size_t zero = tb + ab, extra = 0;
+  size_t keyb = 0;
   if (!g->bits2) {
-    // 4-cycle counters (zero) and touched lists per block; pair lists per warp
+    // the sort tier's path keys, then the per-warp pair lists
     G.cap = std::max<int64_t>(1, g->max_d2);
-    zero += (size_t)SPARSE_C4_BLOCKS * g->n * 4;
-    extra = (size_t)SPARSE_C4_BLOCKS * g->n * 4 + (size_t)SPARSE_EDGE_BLOCKS * SPARSE_WARPS * G.cap * 4;
+    HM_CHECK(g->C4.ready, HM_EINVAL, "4-cycle paths not sized");
+    keyb = ((size_t)g->C4.total * 8 + 255) & ~(size_t)255;
+    extra = keyb + (size_t)SPARSE_EDGE_BLOCKS * SPARSE_WARPS * G.cap * 4;
   }
   G.buf.alloc(zero + extra, s);
   G.tnode = reinterpret_cast<uint32_t*>(G.buf.p);
   G.agg = reinterpret_cast<unsigned long long*>(G.buf.p + tb);
   if (!g->bits2) {
-    G.acc = reinterpret_cast<uint32_t*>(G.buf.p + tb + ab);
-    G.touched = reinterpret_cast<int32_t*>(G.buf.p + zero);
-    G.lists = G.touched + (size_t)SPARSE_C4_BLOCKS * g->n;
+    G.c4_keys = g->C4.total ? reinterpret_cast<uint64_t*>(G.buf.p + zero) : nullptr;
+    G.lists = reinterpret_cast<int32_t*>(G.buf.p + zero + keyb);
   }
   HM_CUDA(cudaMemsetAsync(G.buf.p, 0, zero, s));
+}
+
+void c4_bounds(hm_graph* g, uint64_t* out, cudaStream_t s) {
+  g->c4_warp_ub = c4_warp_bound();
+  const uint64_t want = ((uint64_t)g->n * 32 + 255) / 256;
+  k_c4_bound<<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, 152 * 8)), 256, 0, s>>>(
+      g->view(), g->c4_warp_ub, out);
+  HM_KCHECK();
 }
 
 void graphlet_edges(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
@@ -456,9 +624,20 @@ void graphlet_edges(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
 void graphlet_pairs(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
   TraceSpan span("census_gl_pairs", s);
   if (!g->bits2) {
-    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(g->n, SPARSE_C4_BLOCKS));
-    k_graphlet_c4_sparse<<<blocks, 256, 0, s>>>(g->view(), G.per, G.acc, G.touched, G.agg);
+    // warp tier over all nodes, then the sort tier over the heavy nodes
+    const uint64_t want = ((uint64_t)g->n * 32 + C4_WARPS * 32 - 1) / (C4_WARPS * 32);
+    const unsigned wblocks = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, 152 * 6));
+    k_c4_warp<<<wblocks, C4_WARPS * 32, 0, s>>>(g->view(), G.per, g->c4_warp_ub, G.agg);
     HM_KCHECK();
+    const uint64_t nk = g->C4.total;
+    if (nk) {
+      k_c4_emit<<<wblocks, C4_WARPS * 32, 0, s>>>(g->view(), g->bits, g->C4.ws, G.c4_keys);
+      HM_KCHECK();
+      radix_sort_u64(G.c4_keys, nullptr, (int64_t)nk, 2 * g->bits, s);
+      const uint64_t rb = std::min<uint64_t>((nk + 255) / 256, 152 * 8);
+      k_c4_runs<<<(unsigned)rb, 256, 0, s>>>(G.c4_keys, nk, g->bits, G.per, G.agg);
+      HM_KCHECK();
+    }
     span.end();
     return;
   }

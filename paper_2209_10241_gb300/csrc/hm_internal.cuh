@@ -362,6 +362,10 @@ __device__ __forceinline__ bool probe_tuple(const int4* table, uint64_t mask, in
 // existence of the 3-hyperedge {a, b, c} (any order)
 __device__ __forceinline__ bool has_triple(const DevGraph& g, int32_t a, int32_t b, int32_t c) {
   if (g.m3 == 0) return false;
+  if (g.tri3) {  // exact rows: one load instead of a probe chain
+    const uint32_t w = __ldg(g.tri3 + ((size_t)a * g.n + b) * g.bwords + (c >> 5));
+    return (w >> (c & 31)) & 1u;
+  }
   sort3(a, b, c);
   return probe_tuple(g.h3, g.h3_mask, a, b, c, -1);
 }
@@ -435,14 +439,17 @@ struct GraphletScratch {
   unsigned long long* agg = nullptr;
   int ngraphs = 1;
   int32_t per = 0;
-  // graphs without pair bitmaps: per-block 4-cycle counters and touched
-  // lists, per-warp lists of common neighbours (cap entries each)
-  uint32_t* acc = nullptr;
-  int32_t* touched = nullptr;
+  // graphs without pair bitmaps: per-warp lists of common neighbours (cap
+  // entries each); the paths of the nodes whose 4-cycles are counted by sort
   int32_t* lists = nullptr;
   int64_t cap = 0;
+  uint64_t* c4_keys = nullptr;  // the heavy nodes' 4-cycle paths (C4.total keys)
 };
 void graphlet_prepare(const hm_graph* g, GraphletScratch& G, cudaStream_t s);
+// Per node of a graph without pair bitmaps, the 4-cycle paths it emits for
+// counting by sort: its path bound when above the warp tier's, else 0.
+// The bound in force is kept in the graph (the census splits the nodes by it).
+void c4_bounds(hm_graph* g, uint64_t* out, cudaStream_t s);
 void graphlet_edges(const hm_graph* g, GraphletScratch& G, cudaStream_t s);
 void graphlet_pairs(const hm_graph* g, GraphletScratch& G, cudaStream_t s);
 void graphlet_finish(const hm_graph* g, GraphletScratch& G, unsigned long long* hist,
@@ -495,6 +502,11 @@ struct hm_graph {
   Space Wb, Sb, Pb;
   // bit-sliced TX: items are (3-hyperedge, 4-word group of the rows)
   Space TXb;
+  // graphs without pair bitmaps: per node, the 4-cycle paths it emits for
+  // counting by sort (its path bound when above the warp tier's bound
+  // c4_warp_ub, else 0)
+  Space C4;
+  uint32_t c4_warp_ub = 0;
   bool useWb = false, useSb = false, usePb = false, useTXb = false;
   // order 4: pairs-only sets from graphlet identities instead of S and P
   bool useGL = false;

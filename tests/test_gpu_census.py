@@ -22,7 +22,7 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 MODES = ["hash", "bitmap", "sliced", "sliced_filter", "tuned", "chunk8", "chunk32", "graphlets",
-         "graphlets_filter", "graphlets_pc", "graphlets_hash"]
+         "graphlets_filter", "graphlets_pc", "graphlets_hash", "graphlets_tiers"]
 
 
 def _set_mode(monkeypatch, mode):
@@ -35,16 +35,20 @@ def _set_mode(monkeypatch, mode):
     graphlets*: pairs-only sets from graphlet identities, with the bit-sliced
     TX family on exact rows / on the co-occurrence filter / per candidate;
     graphlets_hash: the same without pair bitmaps (hash probes, 4-cycles by
-    degree order)."""
+    degree order); graphlets_tiers: graphlets_hash with the warp tier of the
+    4-cycle pass bounded at 4 paths, so that small graphs' nodes reach the
+    sort-based tier too."""
     for var in ("HM_PAIR_BITMAP", "HM_DENSE_FAMILIES", "HM_TRIPLE_ROWS", "HM_AUTOTUNE",
-                "HM_CENSUS_CHUNK", "HM_GRAPHLETS"):
+                "HM_CENSUS_CHUNK", "HM_GRAPHLETS", "HM_C4_UB"):
         monkeypatch.delenv(var, raising=False)
     if mode == "tuned":
         return
-    if mode == "graphlets_hash":
+    if mode in ("graphlets_hash", "graphlets_tiers"):
         monkeypatch.setenv("HM_PAIR_BITMAP", "0")
         monkeypatch.setenv("HM_GRAPHLETS", "1")
         monkeypatch.setenv("HM_AUTOTUNE", "0")
+        if mode == "graphlets_tiers":
+            monkeypatch.setenv("HM_C4_UB", "4")
         return
     if mode.startswith("graphlets"):
         monkeypatch.setenv("HM_PAIR_BITMAP", "1")
