@@ -46,7 +46,7 @@ ROOFLINE = {
     "census_gl_edges": ("pair", 4045.4, 155_000),
     "census_gl_pairs": ("node pair", 89.2, 26_000),
     "census_TXb": ("item", 1971.0, 1_653_000),
-    "census_Q": ("candidate", None, None),
+    "census_Q": ("candidate", 300.9, 510_000),
     "census_Sb": ("item", 612.8, 4_378_000),
     "census_Pb": ("item", 480.6, 5_733_000),
     "census_TX": ("candidate", 332.9, 659_000),

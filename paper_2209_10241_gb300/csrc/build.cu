@@ -188,6 +188,47 @@ __device__ __forceinline__ void insert_tuple(int4 k, int4* table, uint64_t mask,
 
 // The three hash sets in one launch: thread i inserts pair i, then 3- and
 // 4-hyperedges after the pairs.
+// Node signatures of graphs without pair bitmaps (zeroed, 3 n words): each
+// hyperedge sets, in every member's word of its size, the bits of the other
+// members. One thread per hyperedge of every size.
+__global__ void k_signatures(const uint64_t* __restrict__ e2, int64_t m2, const int4* __restrict__ e3,
+                             int64_t m3, const int4* __restrict__ e4, int64_t m4, int32_t n,
+                             unsigned long long* __restrict__ sig) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m2 + m3 + m4;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v[4];
+    int k;
+    unsigned long long* w;
+    if (i < m2) {
+      v[0] = (int32_t)(e2[i] >> 32);
+      v[1] = (int32_t)(e2[i] & 0xFFFFFFFFull);
+      k = 2;
+      w = sig;
+    } else if (i < m2 + m3) {
+      const int4 e = e3[i - m2];
+      v[0] = e.x;
+      v[1] = e.y;
+      v[2] = e.z;
+      k = 3;
+      w = sig + n;
+    } else {
+      const int4 e = e4[i - m2 - m3];
+      v[0] = e.x;
+      v[1] = e.y;
+      v[2] = e.z;
+      v[3] = e.w;
+      k = 4;
+      w = sig + 2 * (int64_t)n;
+    }
+    for (int a = 0; a < k; ++a) {
+      unsigned long long bits = 0;
+      for (int b = 0; b < k; ++b)
+        if (b != a) bits |= sig_bit(v[b]);
+      atomicOr(&w[v[a]], bits);
+    }
+  }
+}
+
 __global__ void k_insert_all(const uint64_t* __restrict__ e2, int64_t m2, const int4* __restrict__ e3,
                              int64_t m3, const int4* __restrict__ e4, int64_t m4, uint64_t* h2,
                              uint64_t mask2, int4* h3, uint64_t mask3, int4* h4, uint64_t mask4,
@@ -637,6 +678,8 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     o += al(((size_t)n + 1) * 8);
     const size_t o_cur3 = o;
     o += al(((size_t)n + 1) * 4);
+    const size_t o_sig = o;
+    if (!bitmaps) o += al((size_t)3 * n * 8);
     const size_t zero_end = o;
     const size_t o_off2 = o;
     o += al(((size_t)n + 1) * 8);
@@ -650,6 +693,7 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     if (bitmaps) o += al((size_t)n * 8);
     unsigned char* arena = keep(g, dalloc<unsigned char>(o, s));
     cursor3 = reinterpret_cast<uint32_t*>(arena + o_cur3);
+    if (!bitmaps) g->sig = reinterpret_cast<uint64_t*>(arena + o_sig);
     if (bitmaps) pdeg = reinterpret_cast<uint64_t*>(arena + o_pdeg);
     g->h2 = reinterpret_cast<uint64_t*>(arena + o_h2);
     if (m3) g->h3 = reinterpret_cast<int4*>(arena + o_h3);
@@ -676,6 +720,11 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
                                                          g->h2_mask, g->h3, g->h3_mask, g->h4,
                                                          g->h4_mask, err_p);
       HM_KCHECK();
+      if (g->sig) {
+        k_signatures<<<grid1d(m2 + m3 + m4), T256, 0, s>>>(
+            g->e2, m2, g->e3, m3, g->e4, m4, n, reinterpret_cast<unsigned long long*>(g->sig));
+        HM_KCHECK();
+      }
     }
     // CSR of pair neighbours, sorted, and the position of each pair in it:
     // read off the pair bitmap where there is one, else a stable sort

@@ -243,12 +243,17 @@ struct FamTXT {
   __device__ int32_t graph_node(const DevGraph& g, int64_t a) const {
     return g.e3[kCensus ? a : map[a]].x;
   }
+  // Per anchor: its members, their pair and triple degrees, its own pairs and
+  // (graphs with signatures) the members' signatures, so that a candidate d
+  // probes only what its signature bit allows.
   struct State {
     int32_t x[3];
     int32_t d2[3];
     uint64_t w[3];
     uint64_t r;
     int64_t t;
+    uint64_t s2[3], s3[3], s4;
+    bool ab, ac, bc;
   };
   __device__ void begin(const DevGraph& g, int64_t anchor, uint64_t r, State& s) const {
     const int64_t t = kCensus ? anchor : map[anchor];
@@ -264,6 +269,16 @@ struct FamTXT {
       s.w[j] = (uint64_t)s.d2[j] + (uint64_t)(g.off3[n + 1] - g.off3[n]);
     }
     s.r = r;
+    s.ab = has_pair(g, e.x, e.y);
+    s.ac = has_pair(g, e.x, e.z);
+    s.bc = has_pair(g, e.y, e.z);
+    s.s4 = ~0ull;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      s.s2[j] = g.sig ? g.sig[s.x[j]] : ~0ull;
+      s.s3[j] = g.sig ? g.sig[(int64_t)g.n + s.x[j]] : ~0ull;
+      if (g.sig) s.s4 &= g.sig[2 * (int64_t)g.n + s.x[j]];
+    }
   }
   __device__ void next(State& s) const { ++s.r; }
   __device__ bool item(const DevGraph& g, int64_t, State& s, uint32_t& mask,
@@ -309,8 +324,13 @@ struct FamTXT {
       hpair = false;
       htri = make_tri(h.x, h.y, h.z);
     }
-    // h must be the smallest hyperedge of the set containing d
-    const bool ad = has_pair(g, a, d), bd = has_pair(g, b, d), cd = has_pair(g, c, d);
+    // h must be the smallest hyperedge of the set containing d. A pair
+    // hyperedge h = {x, d} is known to exist; other probes run only where
+    // the members' signatures hold d's bit.
+    const uint64_t db = sig_bit(d);
+    const bool ad = (hpair && which == 0) || ((s.s2[0] & db) && has_pair(g, a, d));
+    const bool bd = (hpair && which == 1) || ((s.s2[1] & db) && has_pair(g, b, d));
+    const bool cd = (hpair && which == 2) || ((s.s2[2] & db) && has_pair(g, c, d));
     if (ad || bd || cd) {
       if (!hpair) return false;
       uint64_t mn = ~0ull;
@@ -319,8 +339,9 @@ struct FamTXT {
       if (cd) mn = min(mn, pair_key(c, d));
       if (pair_key(x, d) != mn) return false;
     }
-    const bool abd = has_triple(g, a, b, d), acd = has_triple(g, a, c, d),
-               bcd = has_triple(g, b, c, d);
+    const bool abd = (s.s3[0] & s.s3[1] & db) && has_triple(g, a, b, d);
+    const bool acd = (s.s3[0] & s.s3[2] & db) && has_triple(g, a, c, d);
+    const bool bcd = (s.s3[1] & s.s3[2] & db) && has_triple(g, b, c, d);
     const Tri e = make_tri(a, b, c);
     const Tri tabd = make_tri(a, b, d), tacd = make_tri(a, c, d), tbcd = make_tri(b, c, d);
     // census: e must be the smallest 3-hyperedge of the set
@@ -334,12 +355,12 @@ struct FamTXT {
       if (bcd && tri_less(tbcd, mn)) mn = tbcd;
       if (!tri_eq(htri, mn)) return false;
     }
-    if (has_quad(g, a, b, c, d)) return false;  // holds a 4-hyperedge (family Q)
+    if ((s.s4 & db) && has_quad(g, a, b, c, d)) return false;  // a 4-hyperedge (family Q)
     nd[0] = a;
     nd[1] = b;
     nd[2] = c;
     nd[3] = d;
-    const bool ab = has_pair(g, a, b), ac = has_pair(g, a, c), bc = has_pair(g, b, c);
+    const bool ab = s.ab, ac = s.ac, bc = s.bc;
     mask = (ab ? 1u : 0u) | (ac ? 2u : 0u) | (ad ? 4u : 0u) | (bc ? 8u : 0u) |
            (bd ? 16u : 0u) | (cd ? 32u : 0u) | 64u | (abd ? 128u : 0u) | (acd ? 256u : 0u) |
            (bcd ? 512u : 0u);  // a=0, b=1, c=2, d=3

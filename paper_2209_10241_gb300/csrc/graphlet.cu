@@ -516,15 +516,58 @@ struct PatternClasses {
 
 // One block per graph: the per-node sums C(d, 3) and t(v) (d - 2), then the
 // induced pattern counts into the graph's histogram row.
+// Per-node sums S3 and TT of large graphs over the whole grid, into slots 0
+// and 3 (one atomic pair per warp when its lanes share a graph).
+__global__ void k_graphlet_nodes(const DevGraph g, int32_t nodes_per_graph,
+                                 const uint32_t* __restrict__ tnode,
+                                 unsigned long long* __restrict__ agg) {
+  int64_t gcur = -1;
+  uint64_t s3 = 0, tt = 0;
+  auto flush = [&]() {
+    if (gcur < 0) return;
+    if (s3) atomicAdd(&agg[gcur * NAGG + 0], (unsigned long long)s3);
+    if (tt) atomicAdd(&agg[gcur * NAGG + 3], (unsigned long long)tt);
+  };
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < g.n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t gi = v / nodes_per_graph;
+    if (gi != gcur) {
+      flush();
+      gcur = gi;
+      s3 = tt = 0;
+    }
+    const uint64_t d = (uint64_t)degree(g, (int32_t)v), tv = tnode[v] / 2;
+    if (d >= 3) s3 += choose3(d);
+    if (d >= 2) tt += tv * (d - 2);
+  }
+  const int64_t g0 = __shfl_sync(0xffffffffu, gcur, 0);
+  if (__all_sync(0xffffffffu, gcur == g0 || gcur < 0 || (s3 == 0 && tt == 0))) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+      tt += __shfl_xor_sync(0xffffffffu, tt, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      gcur = g0;
+      flush();
+    }
+  } else {
+    flush();
+  }
+}
+
+// One block per graph: the per-node sums S3 and TT (or, with `node_sums`,
+// slots 0 and 3 that k_graphlet_nodes filled), then the induced counts.
 __global__ void k_graphlet_finish(const DevGraph g, int32_t nodes_per_graph,
                                   const uint32_t* __restrict__ tnode,
                                   const unsigned long long* __restrict__ agg, int ncls,
-                                  const PatternClasses P, unsigned long long* __restrict__ hist) {
+                                  const PatternClasses P, int node_sums,
+                                  unsigned long long* __restrict__ hist) {
   __shared__ unsigned long long part[2][8];
   const int64_t gi = blockIdx.x;
   const int64_t v0 = gi * nodes_per_graph, v1 = min((int64_t)g.n, v0 + nodes_per_graph);
   uint64_t s3 = 0, tt = 0;
-  for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+  for (int64_t v = v0 + threadIdx.x; v < v1 && !node_sums; v += blockDim.x) {
     const uint64_t d = (uint64_t)degree(g, (int32_t)v), tv = tnode[v] / 2;
     if (d >= 3) s3 += choose3(d);
     if (d >= 2) tt += tv * (d - 2);
@@ -540,12 +583,17 @@ __global__ void k_graphlet_finish(const DevGraph g, int32_t nodes_per_graph,
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
-  uint64_t S3 = 0, TT = 0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-    S3 += part[0][w];
-    TT += part[1][w];
-  }
   const unsigned long long* A = agg + gi * NAGG;
+  uint64_t S3 = 0, TT = 0;
+  if (node_sums) {
+    S3 = A[0];
+    TT = A[3];
+  } else {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      S3 += part[0][w];
+      TT += part[1][w];
+    }
+  }
   const uint64_t T = A[2] / 3, P3 = A[1] - 3 * T, D = A[4], K4 = A[5], C4 = A[6] / 2;
   const uint64_t k4 = K4, dia = D - 6 * K4, c4 = C4 - D + 3 * K4, paw = TT - 4 * D + 12 * K4;
   const uint64_t star = S3 - paw - 2 * dia - 4 * k4;
@@ -656,8 +704,16 @@ void graphlet_finish(const hm_graph* g, GraphletScratch& G, unsigned long long* 
     P.cls[k] = c;
   }
   TraceSpan span("census_gl_finish", s);
+  // graphs above 16K nodes: the per-node sums over the whole grid first
+  // (HM_GL_NODE_SUMS=1 forces it, for the tests)
+  const char* ns_env = std::getenv("HM_GL_NODE_SUMS");
+  const int node_sums = (G.per > 16384 || (ns_env && ns_env[0] == '1')) ? 1 : 0;
+  if (node_sums) {
+    k_graphlet_nodes<<<grid_n((uint64_t)g->n), 256, 0, s>>>(g->view(), G.per, G.tnode, G.agg);
+    HM_KCHECK();
+  }
   k_graphlet_finish<<<(unsigned)G.ngraphs, 256, 0, s>>>(g->view(), G.per, G.tnode, G.agg, T.ncls,
-                                                        P, hist);
+                                                        P, node_sums, hist);
   HM_KCHECK();
   span.end();
 }

@@ -290,6 +290,11 @@ struct DevGraph {
   // iff {a, b, c} is a 3-hyperedge
   const uint32_t* tri3;
   int32_t bwords;
+  // graphs without pair bitmaps: per node three 64-bit signatures (Bloom
+  // words, bit sig_bit(v) for every v): [0, n) its pair neighbours, [n, 2n)
+  // its co-members in 3-hyperedges, [2n, 3n) in 4-hyperedges. A clear bit
+  // proves that the pair / triple / quad is absent, before any probe.
+  const uint64_t* sig;
   // 0 for one graph. Otherwise the graph is a disjoint union of graphs whose
   // node ids occupy consecutive blocks of `block` ids (graph of node v =
   // v / block, computed as mulhi(v, block_inv) with block_inv = ceil(2^64 /
@@ -311,6 +316,11 @@ __device__ __forceinline__ int32_t graph_of(const DevGraph& g, int32_t v) {
 }
 __device__ __forceinline__ int32_t graph_base(const DevGraph& g, int32_t v) {
   return g.block ? graph_of(g, v) * g.block : 0;
+}
+
+// The signature bit of node v (one of 64, by a multiplicative hash).
+__device__ __forceinline__ uint64_t sig_bit(int32_t v) {
+  return 1ull << (((uint64_t)(uint32_t)v * 0x9E3779B97F4A7C15ull) >> 58);
 }
 
 __device__ __forceinline__ bool has_pair(const DevGraph& g, int32_t a, int32_t b) {
@@ -486,6 +496,7 @@ struct hm_graph {
   uint32_t* bits3 = nullptr;
   uint32_t* bits4 = nullptr;
   uint32_t* tri3 = nullptr;
+  uint64_t* sig = nullptr;  // graphs without pair bitmaps: 3 n node signatures
   int32_t bwords = 0;
   int32_t block = 0;  // see DevGraph::block
   int32_t max_d2 = 0;
@@ -540,6 +551,7 @@ struct hm_graph {
     g.bits4 = bits4;
     g.tri3 = tri3;
     g.bwords = bwords;
+    g.sig = sig;
     g.block = block;
     g.block_inv = block > 1 ? (uint64_t)((((unsigned __int128)1 << 64) + block - 1) / block) : 0;
     return g;

@@ -37,9 +37,9 @@ def _set_mode(monkeypatch, mode):
     graphlets_hash: the same without pair bitmaps (hash probes, 4-cycles by
     degree order); graphlets_tiers: graphlets_hash with the warp tier of the
     4-cycle pass bounded at 4 paths, so that small graphs' nodes reach the
-    sort-based tier too."""
+    sort-based tier too, and the per-node sums taken over the whole grid."""
     for var in ("HM_PAIR_BITMAP", "HM_DENSE_FAMILIES", "HM_TRIPLE_ROWS", "HM_AUTOTUNE",
-                "HM_CENSUS_CHUNK", "HM_GRAPHLETS", "HM_C4_UB"):
+                "HM_CENSUS_CHUNK", "HM_GRAPHLETS", "HM_C4_UB", "HM_GL_NODE_SUMS"):
         monkeypatch.delenv(var, raising=False)
     if mode == "tuned":
         return
@@ -49,6 +49,7 @@ def _set_mode(monkeypatch, mode):
         monkeypatch.setenv("HM_AUTOTUNE", "0")
         if mode == "graphlets_tiers":
             monkeypatch.setenv("HM_C4_UB", "4")
+            monkeypatch.setenv("HM_GL_NODE_SUMS", "1")
         return
     if mode.startswith("graphlets"):
         monkeypatch.setenv("HM_PAIR_BITMAP", "1")
