@@ -43,7 +43,7 @@ ALU_LANES_PER_SM_CLK = 64
 # (ops = sm__sass_thread_inst_executed_op_{integer,bit}_pred_on per unit, measured by ncu on this
 # workload; traffic = dram__bytes_read.sum + dram__bytes_write.sum of the same capture)
 ROOFLINE = {
-    "census_gl_edges": ("pair", 4045.4, 155_000),
+    "census_gl_edges": ("pair", 4411.7, 156_000),
     "census_gl_pairs": ("node pair", 89.2, 26_000),
     "census_TXb": ("item", 1971.0, 1_653_000),
     "census_Q": ("candidate", 300.9, 510_000),

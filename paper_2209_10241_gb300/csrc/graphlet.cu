@@ -126,7 +126,7 @@ __device__ __forceinline__ void pair_sums_block(const PairSums& P, unsigned long
 // u < v (common neighbours w > v listed in shared memory and shared out over
 // the lanes), then the per-pair sums and t(e) added at both ends. Rows longer
 // than GL_MAXW words take the lanes over words directly.
-__global__ void __launch_bounds__(GL_WARPS * 32)
+__global__ void __launch_bounds__(GL_WARPS * 32, 4)
     k_graphlet_edges(const DevGraph g, uint32_t* __restrict__ tnode,
                      unsigned long long* __restrict__ agg) {
   __shared__ uint32_t cw_s[GL_WARPS][GL_MAXW];
