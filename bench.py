@@ -33,27 +33,64 @@ WORKLOAD = "f2f-330"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 # Roofline of the census kernels. Their tables are L2/L1-resident on this
-# workload (ncu: a few MB of DRAM traffic per launch), so they are bound by
-# the integer/logic (ALU) pipe: peak = SMs x 64 int32 lanes per clock x SM clock. Achieved =
-# work units of one launch x ALU lane-operations per unit (measured with ncu
-# on this workload) / event-timed launch duration.
+# workload (ncu: under 2 MB of DRAM traffic per launch), so they are bound by
+# the integer/logic (ALU) pipe: peak = SMs x 64 int32 lanes per clock x SM
+# clock. Achieved = the algorithmic 32-bit word operations of one launch /
+# event-timed launch duration. The operations are what each method needs,
+# counted from the workload, independent of how lanes are mapped:
+#   census_gl_edges (per pair u < v of E_2): t(e) = AND, popcount and add over
+#     the bw words of the two rows (3 bw), plus, for every common neighbour
+#     w > v, AND, AND, popcount, add over the bw - w/32 words from w's word on;
+#   census_gl_pairs (per node pair x < z): AND, popcount, add per word (3 bw);
+#   census_Q (per 4-hyperedge): 10 membership tests of 3 ops (word index,
+#     shift, and);
+#   census_TXb (per item = 3-hyperedge x group of 4 row words): per word, 9
+#     row words combined into candidate / triple / risky masks (8 ops) and 7
+#     class counts of 5 ops (three masks, popcount, add) = 43 ops.
 SMS = 152
 ALU_LANES_PER_SM_CLK = 64
-# kernel -> (unit, ALU lane-ops per unit, DRAM bytes per launch); None = not measured
-# (ops = sm__sass_thread_inst_executed_op_{integer,bit}_pred_on per unit, measured by ncu on this
-# workload; traffic = dram__bytes_read.sum + dram__bytes_write.sum of the same capture)
+# kernel -> (unit, algorithmic ops per unit or None when counted from the
+# graph, DRAM bytes per launch from ncu on this workload or None)
+# (traffic = dram__bytes_read.sum + dram__bytes_write.sum of one capture)
 ROOFLINE = {
-    "census_gl_edges": ("pair", 4411.7, 156_000),
-    "census_gl_pairs": ("node pair", 89.2, 26_000),
-    "census_TXb": ("item", 1971.0, 1_653_000),
-    "census_Q": ("candidate", 300.9, 510_000),
-    "census_Sb": ("item", 612.8, 4_378_000),
-    "census_Pb": ("item", 480.6, 5_733_000),
-    "census_TX": ("candidate", 332.9, 659_000),
-    "census_Wb": ("item", None, None),
-    "census_S": ("candidate", None, None),
-    "census_P": ("candidate", None, None),
+    "census_gl_edges": ("pair", None, 145_000),
+    "census_gl_pairs": ("node pair", None, 26_000),
+    "census_TXb": ("item", 4 * 43, 1_653_000),
+    "census_Q": ("candidate", 30, 510_000),
 }
+
+
+def graphlet_pair_ops(e2, n: int, bw: int) -> int:
+    """Algorithmic word operations of one census_gl_edges launch on a graph of
+    n nodes (one graph, rows of bw words) with pairs e2 (int array (m2, 2),
+    u < v): 3 bw per pair plus 4 (bw - w // 32) per common neighbour w > v."""
+    import numpy as np
+    e2 = np.asarray(e2, dtype=np.int64)
+    A = np.zeros((n, n), dtype=np.int64)
+    A[e2[:, 0], e2[:, 1]] = 1
+    A[e2[:, 1], e2[:, 0]] = 1
+    words = bw - np.arange(n) // 32
+    ops = 3 * bw * len(e2)
+    for v in range(n):
+        us = e2[e2[:, 1] == v, 0]
+        if len(us):
+            ops += 4 * int((A[us][:, v + 1:] * (A[v, v + 1:] * words[v + 1:])).sum())
+    return ops
+
+
+def algorithmic_ops(kernel: str, units, n: int, e2):
+    """(ops per launch, ops per unit) of a census kernel on the bench graph, or
+    (None, None) for a kernel without a count."""
+    bw = ((n + 127) // 128) * 4
+    if kernel == "census_gl_edges":
+        ops = graphlet_pair_ops(e2, n, bw)
+    elif kernel == "census_gl_pairs":
+        ops = 3 * bw * units
+    elif kernel in ROOFLINE and ROOFLINE[kernel][1] is not None and units:
+        ops = ROOFLINE[kernel][1] * units
+    else:
+        return None, None
+    return ops, (ops / units if units else None)
 
 
 def max_over_ranks(x: float, device: str = "cuda") -> float:
@@ -499,6 +536,7 @@ def main():
         g = step()
     totals = hm.work_totals(g, args.order)
     g_counts = list(g.counts)
+    e2_host = g.edges(2).cpu().numpy()
     g.free()
     torch.cuda.synchronize()
     sets_per_step = int(hist.sum().item())
@@ -574,13 +612,14 @@ def main():
     peaks, src = _peaks()
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    unit, ops_per_unit, traffic = ROOFLINE.get(dom, ("item", None, None))
+    unit, _, traffic = ROOFLINE.get(dom, ("item", None, None))
     units = totals.get(dom) or {"census_gl_edges": g_counts[2],
                                 "census_gl_pairs": n * (n - 1) // 2}.get(dom)
+    ops, ops_per_unit = algorithmic_ops(dom, units, n, e2_host)
     peak_tops = SMS * ALU_LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e12
-    achieved = (units * ops_per_unit / avg_s / 1e12) if (units and ops_per_unit) else None
+    achieved = (ops / avg_s / 1e12) if ops else None
     roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak_tops,
-                "unit": "Tops/s (int32 lane-ops)",
+                "unit": "Tops/s (algorithmic int32 word-ops)",
                 "frac": (achieved / peak_tops) if achieved else None, "traffic": traffic,
                 "units_per_launch": units, "unit_kind": unit, "ops_per_unit": ops_per_unit,
                 "launch_ms": avg_s * 1e3,

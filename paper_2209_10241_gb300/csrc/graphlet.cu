@@ -92,22 +92,22 @@ __device__ __forceinline__ void pair_sums_add(PairSums& P, unsigned long long* a
   P.v[3] += k4;
 }
 
-// Called by every thread of the block (blockDim.x = 32 * NW) after the pair
-// loop; lane 0 of each warp holds its run.
-template <int NW>
-__device__ __forceinline__ void pair_sums_block(const PairSums& P, unsigned long long* agg) {
-  __shared__ int32_t gi_s[NW];
-  __shared__ uint64_t v_s[NW][4];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) {
-    gi_s[wid] = P.gi;
+// Called by every thread of the block after the pair loop; the leader of each
+// of the block's NG lane groups holds the group's run.
+template <int NG>
+__device__ __forceinline__ void pair_sums_groups(const PairSums& P, int grp, bool leader,
+                                                 unsigned long long* agg) {
+  __shared__ int32_t gi_s[NG];
+  __shared__ uint64_t v_s[NG][4];
+  if (leader) {
+    gi_s[grp] = P.gi;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) v_s[wid][i] = P.v[i];
+    for (int i = 0; i < 4; ++i) v_s[grp][i] = P.v[i];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     PairSums R;
-    for (int w = 0; w < NW; ++w) {
+    for (int w = 0; w < NG; ++w) {
       if (gi_s[w] < 0) continue;
       if (gi_s[w] != R.gi) {
         pair_sums_flush(agg, R);
@@ -119,6 +119,77 @@ __device__ __forceinline__ void pair_sums_block(const PairSums& P, unsigned long
     }
     pair_sums_flush(agg, R);
   }
+}
+
+// The same with one group per warp (blockDim.x = 32 * NW), lane 0 leading.
+template <int NW>
+__device__ __forceinline__ void pair_sums_block(const PairSums& P, unsigned long long* agg) {
+  pair_sums_groups<NW>(P, threadIdx.x >> 5, (threadIdx.x & 31) == 0, agg);
+}
+
+// Rows of at most 16 words: one half-warp per pair, lanes over words. t(e)
+// is the popcount of the rows' AND; the common neighbours w > v (at most
+// 16 x 32) are listed in shared memory and shared out over the 16 lanes for
+// the 4-cliques, as in k_graphlet_edges, with half the lanes of a warp per
+// pair.
+constexpr int GLH_LIST = 16 * 32;
+__global__ void __launch_bounds__(GL_WARPS * 32, 4)
+    k_graphlet_edges16(const DevGraph g, uint32_t* __restrict__ tnode,
+                       unsigned long long* __restrict__ agg) {
+  __shared__ uint32_t cw_s[GL_WARPS * 2][16];
+  __shared__ int16_t wl_s[GL_WARPS * 2][GLH_LIST];
+  const int32_t bw = g.bwords;
+  const int lane = threadIdx.x & 31, sub = lane >> 4, sl = lane & 15;
+  const int grp = (threadIdx.x >> 5) * 2 + sub;
+  const unsigned mask = 0xFFFFu << (sub * 16);
+  uint32_t* cw = cw_s[grp];
+  int16_t* list = wl_s[grp];
+  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) >> 4;
+  PairSums P;
+  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4; p < g.m2; p += groups) {
+    const int32_t u = (int32_t)(g.e2[p] >> 32), v = (int32_t)(g.e2[p] & 0xFFFFFFFFull);
+    const int32_t base = graph_base(g, u), vl = v - base;
+    uint32_t c = 0;
+    if (sl < bw) {
+      c = __ldg(brow(g.bits2, bw, u) + sl) & __ldg(brow(g.bits2, bw, v) + sl);
+      cw[sl] = c;
+    }
+    uint32_t t = __popc(c);
+    uint32_t word = sl < bw ? (c & above(sl, vl)) : 0u;
+    const uint32_t cc = __popc(word);
+    uint32_t incl = cc;
+#pragma unroll
+    for (int d = 1; d < 16; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(mask, incl, d, 16);
+      if (sl >= d) incl += y;
+    }
+    int pos = (int)(incl - cc);
+    while (word) {
+      const int j = __ffs(word) - 1;
+      word &= word - 1;
+      list[pos++] = (int16_t)(sl * 32 + j);
+    }
+    const int count = (int)__shfl_sync(mask, incl, 15, 16);
+    __syncwarp(mask);
+    uint64_t k4 = 0;
+    for (int i = sl; i < count; i += 16) {
+      const int32_t wl = list[i];
+      const uint32_t* Bw = brow(g.bits2, bw, base + wl);
+      for (int32_t x = wl >> 5; x < bw; ++x) k4 += __popc(cw[x] & __ldg(Bw + x) & above(x, wl));
+    }
+#pragma unroll
+    for (int o = 8; o; o >>= 1) {
+      t += __shfl_xor_sync(mask, t, o, 16);
+      k4 += __shfl_xor_sync(mask, k4, o, 16);
+    }
+    if (sl == 0) {
+      atomicAdd(&tnode[u], t);
+      atomicAdd(&tnode[v], t);
+      pair_sums_add(P, agg, graph_of(g, u), (uint64_t)degree(g, u), (uint64_t)degree(g, v), t, k4);
+    }
+    __syncwarp(mask);
+  }
+  pair_sums_groups<GL_WARPS * 2>(P, grp, sl == 0, agg);
 }
 
 // One warp per pair (u < v): t(e) = popcount of the rows' AND (lanes over
@@ -663,8 +734,14 @@ void graphlet_edges(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
     span.end();
     return;
   }
-  k_graphlet_edges<<<grid_n((uint64_t)g->counts[2] * 32), GL_WARPS * 32, 0, s>>>(g->view(), G.tnode,
-                                                                                 G.agg);
+  // HM_GL_WIDE=1 keeps a warp per pair on short rows too (tests cover both)
+  const char* wide = std::getenv("HM_GL_WIDE");
+  if (g->bwords <= 16 && !(wide && wide[0] == '1'))
+    k_graphlet_edges16<<<grid_n((uint64_t)g->counts[2] * 16), GL_WARPS * 32, 0, s>>>(
+        g->view(), G.tnode, G.agg);
+  else
+    k_graphlet_edges<<<grid_n((uint64_t)g->counts[2] * 32), GL_WARPS * 32, 0, s>>>(
+        g->view(), G.tnode, G.agg);
   HM_KCHECK();
   span.end();
 }

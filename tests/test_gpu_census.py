@@ -33,13 +33,14 @@ def _set_mode(monkeypatch, mode):
     defaults, schedules picked by the autotuner; chunk8 / chunk32: hash
     probes with 8 / 32 candidates per lane on every per-candidate family;
     graphlets*: pairs-only sets from graphlet identities, with the bit-sliced
-    TX family on exact rows / on the co-occurrence filter / per candidate;
+    TX family on exact rows / on the co-occurrence filter (and a warp per
+    pair on short rows) / per candidate;
     graphlets_hash: the same without pair bitmaps (hash probes, 4-cycles by
     degree order); graphlets_tiers: graphlets_hash with the warp tier of the
     4-cycle pass bounded at 4 paths, so that small graphs' nodes reach the
     sort-based tier too, and the per-node sums taken over the whole grid."""
     for var in ("HM_PAIR_BITMAP", "HM_DENSE_FAMILIES", "HM_TRIPLE_ROWS", "HM_AUTOTUNE",
-                "HM_CENSUS_CHUNK", "HM_GRAPHLETS", "HM_C4_UB", "HM_GL_NODE_SUMS"):
+                "HM_CENSUS_CHUNK", "HM_GRAPHLETS", "HM_C4_UB", "HM_GL_NODE_SUMS", "HM_GL_WIDE"):
         monkeypatch.delenv(var, raising=False)
     if mode == "tuned":
         return
@@ -56,6 +57,8 @@ def _set_mode(monkeypatch, mode):
         monkeypatch.setenv("HM_GRAPHLETS", "1")
         monkeypatch.setenv("HM_AUTOTUNE", "0")
         monkeypatch.setenv("HM_TRIPLE_ROWS", "0" if mode == "graphlets_filter" else "1")
+        if mode == "graphlets_filter":
+            monkeypatch.setenv("HM_GL_WIDE", "1")
         monkeypatch.setenv("HM_DENSE_FAMILIES", "0" if mode == "graphlets_pc" else "1")
         return
     if mode.startswith("chunk"):

@@ -100,4 +100,6 @@ def test_launch_counter_counts_library_kernels(hm):
     before = hm.launch_count()
     g = hm.from_host(h, 4)
     hm.count_exact(g, 4)
-    assert hm.launch_count() - before > 20
+    # ingest (normalise, sort, CSR, spaces) and census launches: at least 10
+    # on any path; the fused small-graph chains keep it near 16
+    assert hm.launch_count() - before >= 10
