@@ -194,6 +194,9 @@ hm_status hm_count_exact_host(const int32_t* h_members, const int64_t* h_offsets
  * (may be NULL) -- sets *count, and clears the trace.
  */
 hm_status hm_trace_enable(int on);
+/* Restricts the trace to spans named `name` (NULL or "" = every span), so
+ * that a timed run pays for the events of one kernel only. */
+hm_status hm_trace_only(const char* name);
 /* Number of kernels the library has launched in this process (instrumentation). */
 uint64_t hm_launch_count(void);
 hm_status hm_trace_read(int max_entries, char* names, int name_len, float* ms, int* count);

@@ -60,6 +60,7 @@ _SIGS = {
                                            _vp, _vp]),
     "hm_work_totals": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "hm_trace_enable": (ctypes.c_int, [ctypes.c_int]),
+    "hm_trace_only": (ctypes.c_int, [ctypes.c_char_p]),
     "hm_launch_count": (ctypes.c_uint64, []),
     "hm_trace_read": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]),
     "hm_free": (None, [_vp]),
@@ -248,6 +249,11 @@ def count_exact_host(members, offsets, num_nodes: int, order: int, out=None, str
 
 def trace_enable(on: bool = True):
     _check(load().hm_trace_enable(1 if on else 0))
+
+
+def trace_only(name: str = None):
+    """Trace only the spans named `name` (None = every span)."""
+    _check(load().hm_trace_only(name.encode() if name else None))
 
 
 def trace_read(max_entries: int = 4096):

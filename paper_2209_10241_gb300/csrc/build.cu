@@ -312,11 +312,13 @@ __global__ void k_pairpos(const uint64_t* __restrict__ e2, int64_t m, const int6
 
 
 
-// Pair degrees from the bitmap rows: one warp per node.
+// Pair degrees from the bitmap rows, one warp per node, and the largest
+// (one atomic per warp into the zeroed *mx).
 __global__ void k_bits_degree(const uint32_t* __restrict__ bits, int32_t n, int32_t bw,
-                              uint64_t* __restrict__ deg) {
+                              uint64_t* __restrict__ deg, int* __restrict__ mx) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  uint32_t most = 0;
   for (int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
     const uint32_t* row = bits + (size_t)v * bw;
     uint32_t c = 0;
@@ -324,7 +326,9 @@ __global__ void k_bits_degree(const uint32_t* __restrict__ bits, int32_t n, int3
 #pragma unroll
     for (int d = 16; d; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
     if (lane == 0) deg[v] = c;
+    most = max(most, c);
   }
+  if (lane == 0 && most) atomicMax(mx, (int)most);
 }
 
 // Sorted pair neighbours from the bitmap rows (the set bits of row v in
@@ -731,7 +735,7 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     if (bitmaps) {
       const hm::DevGraph gv = g->view();
       k_bits_degree<<<grid1d((int64_t)n * 32), T256, 0, f[0]>>>(g->bits2, n, g->bwords,
-                                                                 pdeg);
+                                                                 pdeg, mx_p);
       HM_KCHECK();
       scan_exclusive_u64(pdeg, reinterpret_cast<uint64_t*>(g->off2), n, f[0]);
       k_bits_adjacency<<<grid1d((int64_t)n * 32), T256, 0, f[0]>>>(
@@ -752,8 +756,10 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
       k_pairpos<<<grid1d(m2), T256, 0, f[0]>>>(g->e2, m2, g->off2, g->adj2, g->pairpos);
       HM_KCHECK();
     }
-    k_max_degree<<<grid1d(n), T256, 0, f[0]>>>(g->off2, n, mx_p);
-    HM_KCHECK();
+    if (!bitmaps) {  // with bitmaps k_bits_degree took the maximum
+      k_max_degree<<<grid1d(n), T256, 0, f[0]>>>(g->off2, n, mx_p);
+      HM_KCHECK();
+    }
     // triple incidence lists: counts (into off3, zeroed), offsets, placement
     if (m3) {
       k_deg3<<<grid1d(m3), T256, 0, f[1]>>>(g->e3, m3, reinterpret_cast<uint64_t*>(g->off3));

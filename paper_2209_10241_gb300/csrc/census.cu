@@ -548,7 +548,7 @@ void launch_bits_t(const hm_graph* g, const F& fam, const hm_graph::Space& sp, u
   const uint64_t max_cand = (end - begin) * (uint64_t)g->bwords * 32;
   const int blocks = grid_for((const void*)k_census_bits<F, kBatched>, lanes, max_cand, kBatched);
   cudaEvent_t ev = nullptr;
-  const bool tr = traced && trace_on();
+  const bool tr = traced && trace_on(F::kName);
   if (tr) trace_begin(s, &ev);
   k_census_bits<F, kBatched><<<blocks, CENSUS_THREADS, 0, s>>>(
       g->view(), fam, sp.ws, sp.anchors, begin, end, lut, (int)T.lut.size(), T.ncls,
@@ -593,7 +593,7 @@ void launch_family_t(const hm_graph* g, const F& fam, const hm_graph::Space* sp,
   const int blocks = grid_for((const void*)k_census<F, kBatched>, (end - begin + chunk - 1) / chunk,
                               end - begin, kBatched);
   cudaEvent_t ev = nullptr;
-  const bool tr = traced && trace_on();
+  const bool tr = traced && trace_on(F::kName);
   if (tr) trace_begin(s, &ev);
   k_census<F, kBatched><<<blocks, CENSUS_THREADS, 0, s>>>(
       g->view(), fam, sp ? sp->ws : nullptr, sp ? sp->anchors : 0, begin, end, chunk, lut,
@@ -710,7 +710,7 @@ void launch_txw_t(const hm_graph* g, int64_t t0, int64_t t1, unsigned long long*
   }
   if (blocks < 1) blocks = 1;
   cudaEvent_t ev = nullptr;
-  const bool tr = traced && trace_on();
+  const bool tr = traced && trace_on("census_TXb");
   if (tr) trace_begin(s, &ev);
   k_census_txw<kExact, kBatched><<<(unsigned)blocks, CENSUS_THREADS, 0, s>>>(
       g->view(), t0, t1, lut, (int)T.lut.size(), T.ncls, num_graphs(g), sub ? 1 : 0, hist);

@@ -389,7 +389,9 @@ __device__ __forceinline__ bool has_quad(const DevGraph& g, int32_t a, int32_t b
 }
 
 // ------------------------------------------------------------------ tracing (trace.cu)
-bool trace_on();
+// Whether spans named `name` are traced now: tracing is on and no filter
+// (hm_trace_only) excludes the name.
+bool trace_on(const char* name);
 void trace_begin(cudaStream_t s, cudaEvent_t* a);
 void trace_end(const char* name, cudaStream_t s, cudaEvent_t a);
 
@@ -400,7 +402,7 @@ struct TraceSpan {
   cudaStream_t s;
   cudaEvent_t a = nullptr;
   TraceSpan(const char* n, cudaStream_t st) : name(n), s(st) {
-    if (trace_on()) trace_begin(s, &a);
+    if (trace_on(name)) trace_begin(s, &a);
   }
   void end() {
     if (a) {

@@ -423,7 +423,7 @@ void launch_sample(const hm_graph* g, const F& f, const uint64_t* ws, int64_t A,
   const ClassTables& T = class_tables(order);
   const uint8_t* lut = device_lut(order);
   cudaEvent_t ev = nullptr;
-  const bool tr = trace_on();
+  const bool tr = trace_on(F::kName);
   if (tr) trace_begin(s, &ev);
   if (weighted) {
     k_sample<F, true><<<sample_blocks((const void*)k_sample<F, true>, total), SAMPLE_THREADS, 0,

@@ -456,11 +456,30 @@ __global__ void __launch_bounds__(PLACE_T) k_sort_place(const Batch B, const Gri
   const JobDev& J = B.j[G.job[blockIdx.x]];
   const int n = (int)J.n;
   const bool has_b = J.b[0] != nullptr;
-  // ranks are a permutation of [0, n) (each counts fewer than n keys)
-  for (int k = threadIdx.x; k < n; k += PLACE_T) {
-    const uint32_t r = J.rank[k];
-    ka_s[r] = J.a[0][k];
-    kb_s[r] = has_b ? J.b[0][k] : 0;
+  // ranks are a permutation of [0, n) (each counts fewer than n keys); a
+  // thread's (at most 8) ranks and keys are loaded before any is stored, so
+  // their loads overlap
+  {
+    constexpr int PER = (int)(SMALL_KEYS / PLACE_T);
+    uint32_t r[PER];
+    uint64_t va[PER], vb[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int k = threadIdx.x + u * PLACE_T;
+      if (k < n) {
+        r[u] = J.rank[k];
+        va[u] = J.a[0][k];
+        vb[u] = has_b ? J.b[0][k] : 0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int k = threadIdx.x + u * PLACE_T;
+      if (k < n) {
+        ka_s[r[u]] = va[u];
+        kb_s[r[u]] = vb[u];
+      }
+    }
   }
   __syncthreads();
   if (!J.unique) {

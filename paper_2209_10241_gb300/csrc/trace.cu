@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cstring>
 #include <mutex>
+#include <string>
 
 #include "hm_internal.cuh"
 
@@ -36,7 +37,13 @@ cudaEvent_t take_event() {
 
 }  // namespace
 
-bool trace_on() { return g_on; }
+std::string g_only;  // traced span name; empty = every span
+
+bool trace_on(const char* name) {
+  if (!g_on) return false;
+  std::lock_guard<std::mutex> lock(g_mu);
+  return g_only.empty() || (name && g_only == name);
+}
 
 static std::atomic<uint64_t> g_launches{0};
 uint64_t launch_count_add(uint64_t n) { return g_launches.fetch_add(n) + n; }
@@ -63,6 +70,13 @@ hm_status hm_trace_enable(int on) {
   return hm::guarded([&] {
     std::lock_guard<std::mutex> lock(hm::g_mu);
     hm::g_on = on != 0;
+  });
+}
+
+hm_status hm_trace_only(const char* name) {
+  return hm::guarded([&] {
+    std::lock_guard<std::mutex> lock(hm::g_mu);
+    hm::g_only = name ? name : "";
   });
 }
 

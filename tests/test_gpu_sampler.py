@@ -95,6 +95,21 @@ def test_default_split_and_errors(hm):
     assert est.cpu().numpy().tobytes() == oest.tobytes()
 
 
+def test_trace_filter_keeps_one_kernel(hm):
+    g = hm.from_host(synth.workload("uniform-200"), 4)
+    hm.trace_read()
+    hm.trace_only("census_Q")
+    hm.trace_enable(True)
+    try:
+        hm.count_exact(g, 4)
+        torch.cuda.synchronize()
+    finally:
+        hm.trace_enable(False)
+        hm.trace_only(None)
+    names = [name for name, _ in hm.trace_read()]
+    assert names and set(names) == {"census_Q"}
+
+
 def test_launch_counter_counts_library_kernels(hm):
     h = synth.workload("uniform-200")
     before = hm.launch_count()
