@@ -390,6 +390,83 @@ __global__ void k_ws_all(const int64_t* __restrict__ off2, const int64_t* __rest
   }
 }
 
+// TX on graphs with node signatures (no bitmaps), one warp per 3-hyperedge
+// e = {a, b, c}. Most candidates d of a member x come from a pair {x, d} and
+// are "plain": the signatures prove that d forms no pair with the other two
+// members, no 3-hyperedge with two members and no 4-hyperedge with e. Such a
+// candidate passes every canonical rule of FamTXT and its pattern depends only
+// on x, so the lanes read x's pair list 32 entries at a time and count the
+// plain ones with a ballot. The others (signature hits) and the candidates
+// from x's 3-hyperedges take FamTXT's exact evaluation. Same sets and masks as
+// the per-candidate kernel, without its per-candidate bookkeeping.
+__global__ void __launch_bounds__(CENSUS_THREADS)
+    k_census_txs(const DevGraph g, const uint8_t* __restrict__ lut_g, int nmask, int ncls,
+                 int sub, unsigned long long* __restrict__ hist) {
+  __shared__ unsigned long long bins[BIN_STRIDE];
+  __shared__ __align__(16) uint8_t lut[2048];
+  load_lut(lut, lut_g, nmask);
+  for (int i = threadIdx.x; i < ncls; i += blockDim.x) bins[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const FamTXT<true> fam{};
+  auto count = [&](uint32_t mask, unsigned long long n) {
+    const uint8_t c1 = lut[mask];
+    if (c1 != 0xFF) atomicAdd(&bins[c1], n);
+    if (sub) {
+      const uint8_t c2 = lut[mask & 63u];
+      if (c2 != 0xFF) atomicAdd(&bins[c2], 0ull - n);
+    }
+  };
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < g.m3; t += warps) {
+    typename FamTXT<true>::State st;
+    fam.begin(g, t, 0, st);
+    const uint32_t fixed = (st.ab ? 1u : 0u) | (st.ac ? 2u : 0u) | (st.bc ? 8u : 0u) | 64u;
+    uint64_t base = 0;  // candidate index of member `which`'s first candidate
+#pragma unroll 1
+    for (int which = 0; which < 3; ++which) {
+      const int o1 = which == 0 ? 1 : 0, o2 = which == 2 ? 1 : 2;
+      const int32_t x = st.x[which];
+      const int64_t ox = g.off2[x];
+      const int32_t d2 = st.d2[which];
+      unsigned long long plain = 0;
+      for (int32_t i0 = 0; i0 < d2; i0 += 32) {
+        const int32_t i = i0 + lane;
+        const bool valid = i < d2;
+        const int32_t d = valid ? g.adj2[ox + i] : -1;
+        const bool in_e = d == st.x[0] || d == st.x[1] || d == st.x[2];
+        const uint64_t db = sig_bit(d);
+        const bool maybe = ((st.s2[o1] | st.s2[o2]) & db) ||
+                           ((st.s3[which] & (st.s3[o1] | st.s3[o2])) & db) ||
+                           ((st.s3[o1] & st.s3[o2]) & db) || (st.s4 & db);
+        plain += __popc(__ballot_sync(0xffffffffu, valid && !in_e && !maybe));
+        if (valid && !in_e && maybe) {
+          typename FamTXT<true>::State s2 = st;
+          s2.r = base + (uint64_t)i;
+          uint32_t mask = 0;
+          int32_t nd[4];
+          if (fam.item(g, t, s2, mask, nd)) count(mask, 1ull);
+        }
+      }
+      if (plain && lane == 0)
+        count(fixed | (which == 0 ? 4u : which == 1 ? 16u : 32u), plain);
+      // candidates from x's 3-hyperedges
+      const uint64_t d3 = st.w[which] - (uint64_t)d2;
+      for (uint64_t j = lane; j < d3; j += 32) {
+        typename FamTXT<true>::State s2 = st;
+        s2.r = base + (uint64_t)d2 + j;
+        uint32_t mask = 0;
+        int32_t nd[4];
+        if (fam.item(g, t, s2, mask, nd)) count(mask, 1ull);
+      }
+      base += st.w[which];
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < ncls; i += blockDim.x)
+    if (bins[i]) atomicAdd(&hist[i], bins[i]);
+}
+
 unsigned grid1d(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b < 1) b = 1;
@@ -735,6 +812,23 @@ void launch_txw(const hm_graph* g, uint64_t b, uint64_t e, unsigned long long* h
 }
 
 // sub: the set's pair pattern is subtracted too (graphlet census, TX only).
+// TX of a whole graph with node signatures: k_census_txs.
+void launch_txs(const hm_graph* g, unsigned long long* hist, cudaStream_t s, bool traced,
+                bool sub) {
+  if (g->counts[3] == 0) return;
+  const ClassTables& T = class_tables(4);
+  const uint8_t* lut = device_lut(4);
+  const int64_t want = (g->counts[3] + CENSUS_THREADS / 32 - 1) / (CENSUS_THREADS / 32);
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, 152 * 8));
+  cudaEvent_t ev = nullptr;
+  const bool tr = traced && trace_on("census_TX");
+  if (tr) trace_begin(s, &ev);
+  k_census_txs<<<blocks, CENSUS_THREADS, 0, s>>>(g->view(), lut, (int)T.lut.size(), T.ncls,
+                                                  sub ? 1 : 0, hist);
+  HM_KCHECK();
+  if (tr) trace_end("census_TX", s, ev);
+}
+
 void launch_one(const hm_graph* g, char fam, bool bits, int chunk, int order,
                 unsigned long long* hist, cudaStream_t s, uint64_t b = 0, uint64_t e = ~0ull,
                 bool traced = true, bool sub = false) {
@@ -766,6 +860,8 @@ void launch_one(const hm_graph* g, char fam, bool bits, int chunk, int order,
     default:
       if (bits) {
         launch_txw(g, b, e, hist, s, traced, sub);
+      } else if (g->sig && !g->block && b == 0 && e == ~0ull && !std::getenv("HM_TX_PER_CANDIDATE")) {
+        launch_txs(g, hist, s, traced, sub);
       } else {
         launch_family(g, FamTX{}, &g->TX, g->TX.total, order, hist, s, chunk, b, e, traced,
                       sub ? 1 : 0);
@@ -911,7 +1007,9 @@ void tune_census(hm_graph* g, int order, cudaStream_t s) {
       fams.push_back({'S', &g->S, g->bits2 ? &g->Sb : nullptr, {}});
       fams.push_back({'P', &g->P, g->bits2 ? &g->Pb : nullptr, {}});
     }
-    fams.push_back({'X', &g->TX, g->bits2 ? &g->TXb : nullptr, {}});
+    // with node signatures TX runs k_census_txs, which has no schedule
+    if (!(g->sig && !g->block && !std::getenv("HM_TX_PER_CANDIDATE")))
+      fams.push_back({'X', &g->TX, g->bits2 ? &g->TXb : nullptr, {}});
   }
   // slice boundaries in both spaces (bt = pc where there is no bit-sliced
   // variant), read back in one copy

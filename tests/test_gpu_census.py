@@ -31,8 +31,9 @@ def _set_mode(monkeypatch, mode):
     exact 3-hyperedge rows; sliced_filter: bit-sliced with the co-occurrence
     filter and exact probes of the risky candidates; tuned: the library's
     defaults, schedules picked by the autotuner; chunk8 / chunk32: hash
-    probes with 8 / 32 candidates per lane on every per-candidate family;
-    graphlets*: pairs-only sets from graphlet identities, with the bit-sliced
+    probes with 8 / 32 candidates per lane on every per-candidate family
+    (chunk8 with TX per candidate too, else TX goes by 3-hyperedge with node
+    signatures); graphlets*: pairs-only sets from graphlet identities, with the bit-sliced
     TX family on exact rows / on the co-occurrence filter (and a warp per
     pair on short rows) / per candidate;
     graphlets_hash: the same without pair bitmaps (hash probes, 4-cycles by
@@ -40,7 +41,8 @@ def _set_mode(monkeypatch, mode):
     4-cycle pass bounded at 4 paths, so that small graphs' nodes reach the
     sort-based tier too, and the per-node sums taken over the whole grid."""
     for var in ("HM_PAIR_BITMAP", "HM_DENSE_FAMILIES", "HM_TRIPLE_ROWS", "HM_AUTOTUNE",
-                "HM_CENSUS_CHUNK", "HM_GRAPHLETS", "HM_C4_UB", "HM_GL_NODE_SUMS", "HM_GL_WIDE"):
+                "HM_CENSUS_CHUNK", "HM_GRAPHLETS", "HM_C4_UB", "HM_GL_NODE_SUMS", "HM_GL_WIDE",
+                "HM_TX_PER_CANDIDATE"):
         monkeypatch.delenv(var, raising=False)
     if mode == "tuned":
         return
@@ -64,6 +66,8 @@ def _set_mode(monkeypatch, mode):
     if mode.startswith("chunk"):
         monkeypatch.setenv("HM_PAIR_BITMAP", "0")
         monkeypatch.setenv("HM_CENSUS_CHUNK", mode[5:])
+        if mode == "chunk8":
+            monkeypatch.setenv("HM_TX_PER_CANDIDATE", "1")
         return
     monkeypatch.setenv("HM_PAIR_BITMAP", "0" if mode == "hash" else "1")
     monkeypatch.setenv("HM_DENSE_FAMILIES", "1" if mode.startswith("sliced") else "0")
