@@ -390,15 +390,37 @@ __global__ void k_ws_all(const int64_t* __restrict__ off2, const int64_t* __rest
   }
 }
 
-// TX on graphs with node signatures (no bitmaps), one warp per 3-hyperedge
-// e = {a, b, c}. Most candidates d of a member x come from a pair {x, d} and
-// are "plain": the signatures prove that d forms no pair with the other two
-// members, no 3-hyperedge with two members and no 4-hyperedge with e. Such a
-// candidate passes every canonical rule of FamTXT and its pattern depends only
-// on x, so the lanes read x's pair list 32 entries at a time and count the
-// plain ones with a ballot. The others (signature hits) and the candidates
-// from x's 3-hyperedges take FamTXT's exact evaluation. Same sets and masks as
-// the per-candidate kernel, without its per-candidate bookkeeping.
+// x in the sorted range a[lo, hi)?
+__device__ __forceinline__ bool in_sorted(const int32_t* __restrict__ a, int64_t lo, int64_t hi,
+                                          int32_t x) {
+  int64_t l = lo, h = hi;
+  while (l < h) {
+    const int64_t mid = (l + h) >> 1;
+    if (__ldg(a + mid) < x)
+      l = mid + 1;
+    else
+      h = mid;
+  }
+  return l < hi && __ldg(a + l) == x;
+}
+
+// TX on graphs without bitmaps, one warp per 3-hyperedge e = {a, b, c}. A
+// candidate d of member x from a pair {x, d} is "plain" unless d is a pair
+// neighbour of another member, lies in a 3-hyperedge with two members, or
+// completes a 4-hyperedge with e. A plain candidate passes every canonical
+// rule of FamTXT and its pattern depends only on x, so it is counted, not
+// enumerated: plain(x) = d2(x) - (other members adjacent to x) - (specials
+// of x). The specials come from small sets, each taken once (from its first
+// source, in a fixed order, with exact membership tests):
+//   1. N(x) & N(o1), 2. N(x) & N(o2), by scanning the shorter sorted row and
+//      binary search in the longer;
+//   3-5. third nodes d in N(x) of the 3-hyperedges through (x, o1), (x, o2),
+//      (o1, o2), by scanning the shorter incidence list;
+//   6. where the members' quad signatures share a bit, the d in N(x) with
+//      that bit and an existing 4-hyperedge {a, b, c, d};
+// and each is evaluated exactly (FamTXT::evaluate). The candidates from
+// 3-hyperedges are the 3-hyperedges through two members, taken from the same
+// scans. The work per 3-hyperedge follows the shorter lists, not the hubs'.
 __global__ void __launch_bounds__(CENSUS_THREADS)
     k_census_txs(const DevGraph g, const uint8_t* __restrict__ lut_g, int nmask, int ncls,
                  int sub, unsigned long long* __restrict__ hist) {
@@ -421,45 +443,105 @@ __global__ void __launch_bounds__(CENSUS_THREADS)
   for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < g.m3; t += warps) {
     typename FamTXT<true>::State st;
     fam.begin(g, t, 0, st);
+    const int32_t m[3] = {st.x[0], st.x[1], st.x[2]};
+    int64_t o2s[3], o2e[3], o3s[3];
+    int32_t d3[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      o2s[i] = g.off2[m[i]];
+      o2e[i] = o2s[i] + st.d2[i];
+      o3s[i] = g.off3[m[i]];
+      d3[i] = (int32_t)(st.w[i] - (uint64_t)st.d2[i]);
+    }
+    const bool adjm[3][3] = {{false, st.ab, st.ac}, {st.ab, false, st.bc}, {st.ac, st.bc, false}};
     const uint32_t fixed = (st.ab ? 1u : 0u) | (st.ac ? 2u : 0u) | (st.bc ? 8u : 0u) | 64u;
-    uint64_t base = 0;  // candidate index of member `which`'s first candidate
+    auto adj = [&](int i, int32_t d) { return in_sorted(g.adj2, o2s[i], o2e[i], d); };
+    auto in_e = [&](int32_t d) { return d == m[0] || d == m[1] || d == m[2]; };
+    // third node of the 3-hyperedge th if it holds members p and q (and is not e), else -1
+    auto third = [&](int64_t th, int p, int q) -> int32_t {
+      if (th == t) return -1;
+      const int4 h = g.e3[th];
+      const bool hp = h.x == m[p] || h.y == m[p] || h.z == m[p];
+      const bool hq = h.x == m[q] || h.y == m[q] || h.z == m[q];
+      if (!hp || !hq) return -1;
+      return (h.x != m[p] && h.x != m[q]) ? h.x : (h.y != m[p] && h.y != m[q]) ? h.y : h.z;
+    };
+    uint32_t mask;
+    int32_t nd[4];
+    // candidates from 3-hyperedges through members j < k (for x = m[j])
 #pragma unroll 1
-    for (int which = 0; which < 3; ++which) {
-      const int o1 = which == 0 ? 1 : 0, o2 = which == 2 ? 1 : 2;
-      const int32_t x = st.x[which];
-      const int64_t ox = g.off2[x];
-      const int32_t d2 = st.d2[which];
-      unsigned long long plain = 0;
-      for (int32_t i0 = 0; i0 < d2; i0 += 32) {
-        const int32_t i = i0 + lane;
-        const bool valid = i < d2;
-        const int32_t d = valid ? g.adj2[ox + i] : -1;
-        const bool in_e = d == st.x[0] || d == st.x[1] || d == st.x[2];
-        const uint64_t db = sig_bit(d);
-        const bool maybe = ((st.s2[o1] | st.s2[o2]) & db) ||
-                           ((st.s3[which] & (st.s3[o1] | st.s3[o2])) & db) ||
-                           ((st.s3[o1] & st.s3[o2]) & db) || (st.s4 & db);
-        plain += __popc(__ballot_sync(0xffffffffu, valid && !in_e && !maybe));
-        if (valid && !in_e && maybe) {
-          typename FamTXT<true>::State s2 = st;
-          s2.r = base + (uint64_t)i;
-          uint32_t mask = 0;
-          int32_t nd[4];
-          if (fam.item(g, t, s2, mask, nd)) count(mask, 1ull);
+    for (int pr = 0; pr < 3; ++pr) {
+      const int j = pr == 2 ? 1 : 0, k = pr == 0 ? 1 : 2;
+      const int sm = d3[j] <= d3[k] ? j : k;
+      for (int32_t idx = lane; idx < d3[sm]; idx += 32) {
+        const int64_t th = g.inc3[o3s[sm] + idx];
+        const int32_t d = third(th, j, k);
+        if (d < 0 || in_e(d)) continue;
+        const int4 h = g.e3[th];
+        if (fam.evaluate(g, st, j, d, false, make_tri(h.x, h.y, h.z), mask, nd)) count(mask, 1ull);
+      }
+    }
+    // pair candidates, member by member
+#pragma unroll 1
+    for (int i = 0; i < 3; ++i) {
+      const int o1 = i == 0 ? 1 : 0, o2 = i == 2 ? 1 : 2;
+      unsigned long long special = 0;
+      auto take = [&](bool is_new, int32_t d) {
+        special += __popc(__ballot_sync(__activemask(), is_new));
+        if (is_new && fam.evaluate(g, st, i, d, true, Tri{0, 0}, mask, nd)) count(mask, 1ull);
+      };
+      // 1-2: shared pair neighbours
+#pragma unroll 1
+      for (int src = 0; src < 2; ++src) {
+        const int o = src == 0 ? o1 : o2;
+        const int sm = st.d2[i] <= st.d2[o] ? i : o, lg = sm == i ? o : i;
+        for (int32_t i0 = 0; i0 < st.d2[sm]; i0 += 32) {
+          const int32_t idx = i0 + lane;
+          bool is_new = false;
+          int32_t d = -1;
+          if (idx < st.d2[sm]) {
+            d = g.adj2[o2s[sm] + idx];
+            is_new = !in_e(d) && adj(lg, d) && (src == 0 || !adj(o1, d));
+          }
+          take(is_new, d);
         }
       }
-      if (plain && lane == 0)
-        count(fixed | (which == 0 ? 4u : which == 1 ? 16u : 32u), plain);
-      // candidates from x's 3-hyperedges
-      const uint64_t d3 = st.w[which] - (uint64_t)d2;
-      for (uint64_t j = lane; j < d3; j += 32) {
-        typename FamTXT<true>::State s2 = st;
-        s2.r = base + (uint64_t)d2 + j;
-        uint32_t mask = 0;
-        int32_t nd[4];
-        if (fam.item(g, t, s2, mask, nd)) count(mask, 1ull);
+      // 3-5: third nodes of 3-hyperedges through (x, o1), (x, o2), (o1, o2)
+#pragma unroll 1
+      for (int src = 0; src < 3; ++src) {
+        const int p = src == 2 ? o1 : i, q = src == 0 ? o1 : o2;
+        const int sm = d3[p] <= d3[q] ? p : q;
+        for (int32_t i0 = 0; i0 < d3[sm]; i0 += 32) {
+          const int32_t idx = i0 + lane;
+          bool is_new = false;
+          int32_t d = -1;
+          if (idx < d3[sm]) {
+            d = third(g.inc3[o3s[sm] + idx], p, q);
+            is_new = d >= 0 && !in_e(d) && adj(i, d) && !adj(o1, d) && !adj(o2, d) &&
+                     (src == 0 || !has_triple(g, m[i], m[o1], d)) &&
+                     (src <= 1 || !has_triple(g, m[i], m[o2], d));
+          }
+          take(is_new, d);
+        }
       }
-      base += st.w[which];
+      // 6: 4-hyperedges {a, b, c, d}
+      if (st.s4) {
+        for (int32_t i0 = 0; i0 < st.d2[i]; i0 += 32) {
+          const int32_t idx = i0 + lane;
+          bool is_new = false;
+          int32_t d = -1;
+          if (idx < st.d2[i]) {
+            d = g.adj2[o2s[i] + idx];
+            is_new = (st.s4 & sig_bit(d)) && !in_e(d) && !adj(o1, d) && !adj(o2, d) &&
+                     !has_triple(g, m[i], m[o1], d) && !has_triple(g, m[i], m[o2], d) &&
+                     !has_triple(g, m[o1], m[o2], d) && has_quad(g, m[0], m[1], m[2], d);
+          }
+          take(is_new, d);
+        }
+      }
+      const unsigned long long others = (adjm[i][o1] ? 1 : 0) + (adjm[i][o2] ? 1 : 0);
+      const unsigned long long plain = (unsigned long long)st.d2[i] - others - special;
+      if (plain && lane == 0) count(fixed | (i == 0 ? 4u : i == 1 ? 16u : 32u), plain);
     }
   }
   __syncthreads();

@@ -324,6 +324,14 @@ struct FamTXT {
       hpair = false;
       htri = make_tri(h.x, h.y, h.z);
     }
+    return evaluate(g, s, which, d, hpair, htri, mask, nd);
+  }
+  // The candidate {a, b, c, d} generated from member `which` by the pair
+  // {x, d} (hpair) or the 3-hyperedge htri: the canonical rules and its mask.
+  __device__ bool evaluate(const DevGraph& g, const State& s, int which, int32_t d, bool hpair,
+                           Tri htri, uint32_t& mask, int32_t (&nd)[4]) const {
+    const int32_t a = s.x[0], b = s.x[1], c = s.x[2];
+    const int32_t x = s.x[which];
     // h must be the smallest hyperedge of the set containing d. A pair
     // hyperedge h = {x, d} is known to exist; other probes run only where
     // the members' signatures hold d's bit.
