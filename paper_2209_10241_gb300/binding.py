@@ -131,10 +131,23 @@ class Graph:
     def __init__(self, handle, kmax: int):
         self._h = handle
         self.kmax = kmax
-        counts = (ctypes.c_int64 * 8)()
-        _check(load().hm_graph_info(self._h, counts))
-        self.counts = list(counts)
-        self.num_nodes = self.counts[0]
+        self._counts = None
+
+    @property
+    def counts(self):
+        """[nodes, input hyperedges, |E_2|, |E_3|, |E_4|, oversized, 0, 0]
+        (hm_graph_info, read on first use)."""
+        if self._counts is None:
+            if not getattr(self, "_h", None):
+                raise RuntimeError("graph already freed")
+            counts = (ctypes.c_int64 * 8)()
+            _check(load().hm_graph_info(self._h, counts))
+            self._counts = list(counts)
+        return self._counts
+
+    @property
+    def num_nodes(self):
+        return self.counts[0]
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -142,6 +155,9 @@ class Graph:
             self._h = None
 
     def free(self):
+        """Releases the device structures; the counts stay readable."""
+        if getattr(self, "_h", None) and self._counts is None:
+            self.counts
         self.__del__()
 
     def count(self, s: int) -> int:
