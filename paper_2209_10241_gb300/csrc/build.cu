@@ -795,7 +795,7 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
 }
 
 // Freed memory stays in the device pool for the next graph instead of going
-// back to the driver (process-local setting of this device's default pool).
+// back to the system (a process-local setting of this device's default pool).
 void keep_pool_memory() {
   static bool done[64] = {false};
   int dev = 0;
