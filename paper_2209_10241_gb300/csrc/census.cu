@@ -455,7 +455,12 @@ __global__ void __launch_bounds__(CENSUS_THREADS)
     }
     const bool adjm[3][3] = {{false, st.ab, st.ac}, {st.ab, false, st.bc}, {st.ac, st.bc, false}};
     const uint32_t fixed = (st.ab ? 1u : 0u) | (st.ac ? 2u : 0u) | (st.bc ? 8u : 0u) | 64u;
-    auto adj = [&](int i, int32_t d) { return in_sorted(g.adj2, o2s[i], o2e[i], d); };
+    // d a pair neighbour of member i: the signature word rules most d out
+    // before the binary search (ncu: the searches made this kernel
+    // instruction-bound, ~10k warp instructions per 3-hyperedge)
+    auto adj = [&](int i, int32_t d) {
+      return (st.s2[i] & sig_bit(d)) && in_sorted(g.adj2, o2s[i], o2e[i], d);
+    };
     auto in_e = [&](int32_t d) { return d == m[0] || d == m[1] || d == m[2]; };
     // third node of the 3-hyperedge th if it holds members p and q (and is not e), else -1
     auto third = [&](int64_t th, int p, int q) -> int32_t {
