@@ -300,6 +300,30 @@ __device__ int32_t find_pos(const int32_t* __restrict__ a, int64_t lo, int64_t h
   return (int32_t)(l - lo);
 }
 
+// Pair positions read off the bitmap rows: the position of v in u's row is
+// the number of u's neighbours below v, a popcount of the row's words below v
+// (graph-local columns), so no CSR is needed and this runs beside its chain.
+__global__ void k_pairpos_bits(const uint32_t* __restrict__ bits, int32_t bw, int32_t block,
+                               uint64_t inv, const uint64_t* __restrict__ e2, int64_t m,
+                               int2* __restrict__ pos) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = (int32_t)(e2[p] >> 32), v = (int32_t)(e2[p] & 0xFFFFFFFFull);
+    const int32_t base = block ? (int32_t)__umul64hi((uint64_t)(uint32_t)u, inv) * block : 0;
+    int32_t r[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const uint32_t* row = bits + (size_t)(k == 0 ? u : v) * bw;
+      const int32_t c = (k == 0 ? v : u) - base;
+      int32_t cnt = 0;
+      for (int32_t w = 0; w < (c >> 5); ++w) cnt += __popc(__ldg(row + w));
+      if (c & 31) cnt += __popc(__ldg(row + (c >> 5)) & ((1u << (c & 31)) - 1u));
+      r[k] = cnt;
+    }
+    pos[p] = make_int2(r[0], r[1]);
+  }
+}
+
 __global__ void k_pairpos(const uint64_t* __restrict__ e2, int64_t m, const int64_t* __restrict__ off2,
                           const int32_t* __restrict__ adj2, int2* __restrict__ pos) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m;
@@ -753,7 +777,13 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     }
     if (!bitmaps) csr_offsets(pkeys, 2 * m2, b, n, g->off2, f[0]);
     if (m2) {
-      k_pairpos<<<grid1d(m2), T256, 0, f[0]>>>(g->e2, m2, g->off2, g->adj2, g->pairpos);
+      if (bitmaps) {  // positions from the rows, beside the hash inserts
+        const hm::DevGraph gv = g->view();
+        k_pairpos_bits<<<grid1d(m2), T256, 0, s>>>(g->bits2, g->bwords, gv.block, gv.block_inv,
+                                                    g->e2, m2, g->pairpos);
+      } else {
+        k_pairpos<<<grid1d(m2), T256, 0, f[0]>>>(g->e2, m2, g->off2, g->adj2, g->pairpos);
+      }
       HM_KCHECK();
     }
     if (!bitmaps) {  // with bitmaps k_bits_degree took the maximum
