@@ -455,9 +455,8 @@ __global__ void __launch_bounds__(CENSUS_THREADS)
     }
     const bool adjm[3][3] = {{false, st.ab, st.ac}, {st.ab, false, st.bc}, {st.ac, st.bc, false}};
     const uint32_t fixed = (st.ab ? 1u : 0u) | (st.ac ? 2u : 0u) | (st.bc ? 8u : 0u) | 64u;
-    // d a pair neighbour of member i: the signature word rules most d out
-    // before the binary search (ncu: the searches made this kernel
-    // instruction-bound, ~10k warp instructions per 3-hyperedge)
+    // d a pair neighbour of member i: the signature word rules d out before
+    // the binary search wherever i's word lacks d's bit
     auto adj = [&](int i, int32_t d) {
       return (st.s2[i] & sig_bit(d)) && in_sorted(g.adj2, o2s[i], o2e[i], d);
     };
