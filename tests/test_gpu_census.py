@@ -247,3 +247,23 @@ def test_class_table_matches_oracle(hm, k):
         assert hm.class_info(k, c) == (int(canon[c]), int(mc[c]), int(cm[c]))
     for mask in range(1 << (4 if k == 3 else 11)):
         assert hm.class_of_mask(k, mask) == oracle.class_of(k, mask)
+
+
+def test_full_size_coauthorship_paths_agree(hm, monkeypatch):
+    # at full size (10^6 nodes, 2.10^6 hyperedges) the oracle is too slow for
+    # the whole census, so two independent GPU paths must agree bit for bit:
+    # the graphlet identities with hash probes against the per-candidate S/P
+    # enumeration (each on its own graph build)
+    h = synth.workload("coauth-1m")
+    hists = []
+    for graphlets in ("1", "0"):
+        for var in ("HM_PAIR_BITMAP", "HM_DENSE_FAMILIES", "HM_TRIPLE_ROWS", "HM_CENSUS_CHUNK",
+                    "HM_C4_UB", "HM_GL_NODE_SUMS", "HM_GL_WIDE", "HM_TX_PER_CANDIDATE"):
+            monkeypatch.delenv(var, raising=False)
+        monkeypatch.setenv("HM_GRAPHLETS", graphlets)
+        monkeypatch.setenv("HM_AUTOTUNE", "0")
+        g = hm.from_host(h, 4)
+        hists.append(hm.count_exact(g, 4).cpu().numpy().astype(np.uint64))
+        g.free()
+    assert hists[0].sum() > 0
+    assert (hists[0] == hists[1]).all()
