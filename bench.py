@@ -1,23 +1,31 @@
-"""Benchmark: exact order-4 higher-order motif census on a face-to-face-shaped hypergraph.
+"""Benchmark: exact order-4 higher-order motif census on a co-authorship-shaped hypergraph.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload coauth-1m|f2f-330] [--only ...]
 
 A step is one pass of the whole exact path over the resident hyperedge list:
 device ingest (normalise, deduplicate, hash sets, CSR; hm_build) and the
 order-4 census (work spaces + every candidate family; hm_count_exact). The
 metric is connected 4-node sets counted per second (the histogram total over
-the step time). Inputs are synthetic (the paper's datasets are not
-available): 330 nodes, 20,000 distinct hyperedges of sizes 2-5, power-law
-node activity. L2 is flushed (256 MiB write) before every timed step.
+the step time). The headline workload is the largest exact order-4 case that
+fits one GPU: 10^6 nodes and 2*10^6 distinct hyperedges of sizes 2-25
+(truncated power law, exponent 2.5), power-law node activity (exponent 2.2),
+shaped like the paper's co-authorship datasets, which are not available here.
+L2 is flushed (256 MiB write) before every timed step.
+
+Beside the headline, the same line carries the face-to-face-shaped exact
+census (330 nodes, 20,000 hyperedges), the null-model batch and the sampler,
+each with the oracle timed on a bounded sample of its workload.
 
 Under torchrun each rank counts its own replica (weak scaling); rank 0 prints
-one JSON line with the max time over ranks. `--impl reference` times the
-CPU oracle on the host cores on a bounded sample of the same workload.
+one JSON line with the max time over ranks. `--impl reference` times the CPU
+oracle on the host cores on bounded samples of the same workload.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -29,15 +37,33 @@ sys.path.insert(0, ROOT)
 
 METRIC = "order-4 census: connected 4-node sets counted per second"
 UNIT = "sets/s"
-WORKLOAD = "f2f-330"
+WORKLOAD = "coauth-1m"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
-# Roofline of the census kernels. Their tables are L2/L1-resident on this
-# workload (ncu: under 2 MB of DRAM traffic per launch), so they are bound by
-# the integer/logic (ALU) pipe: peak = SMs x 64 int32 lanes per clock x SM
-# clock. Achieved = the algorithmic 32-bit word operations of one launch /
-# event-timed launch duration. The operations are what each method needs,
-# counted from the workload, independent of how lanes are mapped:
+# HBM roofline of the sparse census kernels (no dense bitmaps: every fill-in
+# test is a probe into hash tables of packed hyperedge keys). Algorithmic bytes
+# per unit = the probes one candidate needs x one 32-byte sector:
+#   TX candidate (a 3-hyperedge e, a member x, a hyperedge h of size <= 3
+#     through x adding one node d): 9 probes -> 288 B;
+#   Q candidate (a 4-hyperedge): its 10 proper sub-tuples of size 2-3 -> 320 B.
+# The TX kernel (k_census_txs) skips most of these probes legitimately: a
+# candidate whose fourth node shares no pair, 3-hyperedge or 4-hyperedge with
+# the other members (proved from node signatures and list intersections) is
+# counted in bulk by the class of its generating member, with no probe at all.
+# So `frac` is the method's per-candidate byte demand served per second, and
+# can exceed the copy bandwidth; the DRAM bytes the kernel really moved are
+# `traffic` (ncu, one capture of the same workload).
+# kernel -> (unit, bytes per unit, work_totals key, DRAM bytes per launch or None)
+ROOFLINE_HBM = {
+    "census_TX": ("TX candidate", 288, "census_TX", None),
+    "census_Q": ("4-hyperedge", 320, "census_Q", None),
+}
+
+# ALU roofline of the dense (bitmap) census kernels, for the face-to-face row:
+# their tables are L2/L1-resident (ncu: under 2 MB of DRAM per launch), so they
+# are bound by the integer/logic pipe: peak = SMs x 64 int32 lanes per clock x
+# SM clock. Achieved = algorithmic 32-bit word operations of one launch /
+# event-timed launch duration:
 #   census_gl_edges (per pair u < v of E_2): t(e) = AND, popcount and add over
 #     the bw words of the two rows (3 bw), plus, for every common neighbour
 #     w > v, AND, AND, popcount, add over the bw - w/32 words from w's word on;
@@ -47,12 +73,10 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 #   census_TXb (per item = 3-hyperedge x group of 4 row words): per word, 9
 #     row words combined into candidate / triple / risky masks (8 ops) and 7
 #     class counts of 5 ops (three masks, popcount, add) = 43 ops.
-SMS = 152
 ALU_LANES_PER_SM_CLK = 64
 # kernel -> (unit, algorithmic ops per unit or None when counted from the
-# graph, DRAM bytes per launch from ncu on this workload or None)
-# (traffic = dram__bytes_read.sum + dram__bytes_write.sum of one capture)
-ROOFLINE = {
+# graph, DRAM bytes per launch from ncu on the face-to-face workload)
+ROOFLINE_ALU = {
     "census_gl_edges": ("pair", None, 145_000),
     "census_gl_pairs": ("node pair", None, 26_000),
     "census_TXb": ("item", 4 * 43, 1_653_000),
@@ -79,18 +103,37 @@ def graphlet_pair_ops(e2, n: int, bw: int) -> int:
 
 
 def algorithmic_ops(kernel: str, units, n: int, e2):
-    """(ops per launch, ops per unit) of a census kernel on the bench graph, or
-    (None, None) for a kernel without a count."""
+    """(ops per launch, ops per unit) of a dense census kernel on a one-graph
+    workload, or (None, None) for a kernel without a count."""
     bw = ((n + 127) // 128) * 4
     if kernel == "census_gl_edges":
         ops = graphlet_pair_ops(e2, n, bw)
     elif kernel == "census_gl_pairs":
         ops = 3 * bw * units
-    elif kernel in ROOFLINE and ROOFLINE[kernel][1] is not None and units:
-        ops = ROOFLINE[kernel][1] * units
+    elif kernel in ROOFLINE_ALU and ROOFLINE_ALU[kernel][1] is not None and units:
+        ops = ROOFLINE_ALU[kernel][1] * units
     else:
         return None, None
     return ops, (ops / units if units else None)
+
+
+def hbm_roofline(kernel: str, totals: dict, avg_launch_s: float, peak_gbs: float, src: str):
+    """Roofline object of a sparse census kernel: algorithmic bytes per launch
+    (units x bytes per unit) / average launch time, against the measured copy
+    bandwidth; None fields for a kernel without a byte model."""
+    if kernel not in ROOFLINE_HBM or not avg_launch_s:
+        return {"kernel": kernel, "bound": "hbm", "achieved": None, "peak": peak_gbs,
+                "unit": "GB/s", "frac": None, "traffic": None}
+    unit, per, key, traffic = ROOFLINE_HBM[kernel]
+    units = int(totals.get(key) or 0)
+    achieved = units * per / avg_launch_s / 1e9
+    return {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": peak_gbs,
+            "unit": "GB/s", "frac": achieved / peak_gbs, "traffic": traffic,
+            "units_per_launch": units, "unit_kind": unit, "bytes_per_unit": per,
+            "launch_ms": avg_launch_s * 1e3,
+            "peak_source": f"hbm_gbs {src} (copy bandwidth)",
+            "reading": "per-candidate probe bytes of the method (32 B sector per probe); "
+                       "the kernel counts most candidates in bulk without probing"}
 
 
 def max_over_ranks(x: float, device: str = "cuda") -> float:
@@ -124,6 +167,11 @@ def _peaks():
             return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _sm_count() -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
 
 
 class Clocks:
@@ -180,11 +228,97 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- oracle samples
+def _oracle_roots_child(members, offsets, num_nodes, order, threads, start, target_s, conn):
+    """Spawned child: the oracle's census over ESU root windows [lo, hi), from
+    `start` downwards, each window sized for about target_s seconds; sends
+    ("chunk", lo, hi, sets, seconds) after each window."""
+    import oracle
+    g = oracle.Graph(members, offsets, num_nodes, 4)
+    conn.send(("ready",))
+    hi, chunk = int(start), max(1, threads // 2)
+    while hi > 0:
+        lo = max(0, hi - chunk)
+        t0 = time.perf_counter()
+        hist, _ = g.census(order, threads=threads, roots=(lo, hi))
+        dt = time.perf_counter() - t0
+        conn.send(("chunk", lo, hi, int(hist.sum()), dt))
+        grow = target_s / max(dt, 1e-3)
+        chunk = max(1, int((hi - lo) * min(2.0, max(0.5, grow))))
+        hi = lo
+    conn.send(("done",))
+
+
+class OracleRoots:
+    """The oracle (plain ESU + fill-in, as it stands) on ESU root windows of a
+    workload, run in a spawned child process that is stopped when the budget
+    ends: only windows that completed count, so one heavy root cannot hold the
+    run. ESU root v enumerates the connected sets whose smallest id is v; ids
+    are a seeded permutation of the generator's activity ranks, and windows
+    start at the middle id (roots above it see half their neighbourhood on
+    average) and move downwards."""
+
+    def __init__(self, h, order: int, target_s: float = 1.0, start=None):
+        self.threads = os.cpu_count() or 1
+        self.order = order
+        self.n = h.num_nodes
+        ctx = mp.get_context("spawn")
+        self.conn, child = ctx.Pipe(duplex=False)
+        st = self.n // 2 if start is None else start
+        self.start = st
+        self.proc = ctx.Process(target=_oracle_roots_child,
+                                args=(h.members, h.offsets, h.num_nodes, order, self.threads,
+                                      st, target_s, child), daemon=True)
+        self.proc.start()
+        child.close()
+        self.lo = st
+        if not self.conn.poll(600) or self.conn.recv()[0] != "ready":
+            raise RuntimeError("oracle child did not start")
+
+    def run(self, budget_s: float, first_wait_s: float = None):
+        """Windows completed within budget_s (waiting up to first_wait_s for the
+        first one): (sets, seconds, roots)."""
+        sets, secs, roots = 0, 0.0, 0
+        deadline = time.monotonic() + budget_s
+        hard = time.monotonic() + (first_wait_s or budget_s)
+        while True:
+            left = (deadline if roots else max(deadline, hard)) - time.monotonic()
+            if left <= 0 or not self.conn.poll(left):
+                break
+            msg = self.conn.recv()
+            if msg[0] != "chunk":
+                break
+            _, lo, hi, s, dt = msg
+            sets += s
+            secs += dt
+            roots += hi - lo
+            self.lo = lo
+        return sets, secs, roots
+
+    def close(self):
+        if self.proc.is_alive():
+            self.proc.kill()
+        self.proc.join(5)
+
+
+def cpu_baseline(h, order: int, name: str, budget_s: float = 20.0):
+    """The oracle on a bounded, time-boxed sample of ESU roots of the workload."""
+    orc = OracleRoots(h, order)
+    try:
+        sets, secs, roots = orc.run(budget_s, first_wait_s=4 * budget_s)
+    finally:
+        orc.close()
+    return {"value": (sets / secs) if secs else None, "unit": UNIT, "cores": orc.threads,
+            "kind": "oracle",
+            "sample": f"{name} order-{order}: ESU roots [{orc.lo}, {orc.start}) of {h.num_nodes} "
+                      f"(middle id downwards; {sets} connected sets in {secs:.1f} s of completed "
+                      f"windows, {budget_s:.0f} s budget)"}
+
+
 class _Chunks:
-    """Sizes a sample taken in chunks of units that may grow heavier (ESU roots
-    towards the most active nodes): each chunk at most doubles, and is cut to
-    what the budget left allows at the last cost per unit times its last
-    growth; 0 means stop."""
+    """Sizes a sample taken in chunks of units that may grow heavier: each chunk
+    at most doubles, and is cut to what the budget left allows at the last cost
+    per unit times its last growth; 0 means stop."""
 
     def __init__(self, first, smallest, budget_s):
         self.next, self.smallest, self.budget = first, smallest, budget_s
@@ -200,29 +334,65 @@ class _Chunks:
         return self.next
 
 
-def cpu_baseline(h, order: int, budget_s: float = 15.0):
-    """The oracle (plain ESU + fill-in) on a bounded sample of ESU roots."""
+def cpu_baseline_rows(budget_s: float = 8.0):
+    """The oracle beside the f2f, sampler and null-batch rows, each on a bounded sample."""
     import oracle
+    from paper_2209_10241_gb300 import synth
     threads = os.cpu_count() or 1
+    out = {}
+    # the face-to-face exact census over ESU roots from the largest id down
+    h = synth.workload("f2f-330")
     g = oracle.Graph.from_hypergraph(h, 4)
-    # ESU root v enumerates the sets whose smallest id is v; the generator's
-    # low ids are its most active nodes, so the light roots are the top ids and
-    # the sample grows downwards from the largest id, in budget-sized chunks
     lo, sets = h.num_nodes, 0
     ch = _Chunks(max(threads, 8), threads, budget_s)
     while ch.next and lo > 0:
         new_lo = max(0, lo - ch.next)
         t0 = time.perf_counter()
-        hist, _ = g.census(order, threads=threads, roots=(new_lo, lo))
+        hist, _ = g.census(4, threads=threads, roots=(new_lo, lo))
         ch.done(lo - new_lo, time.perf_counter() - t0)
         sets += int(hist.sum())
         lo = new_lo
-    t_used = ch.used
-    return {"value": sets / t_used, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{WORKLOAD} order-{order}: ESU roots [{lo}, {h.num_nodes}) of "
-                      f"{h.num_nodes} ({sets} connected sets in {t_used:.1f} s)"}
+    out["f2f_330"] = {"value": sets / ch.used, "unit": UNIT, "cores": threads, "kind": "oracle",
+                      "sample": f"f2f-330 order-4: ESU roots [{lo}, {h.num_nodes}) of "
+                                f"{h.num_nodes} ({sets} connected sets in {ch.used:.1f} s)"}
+    # Alg. 4 as the oracle runs it, sample by sample (single-threaded)
+    h = synth.workload("comm-5m", seed=9, scale=0.004)
+    g = oracle.Graph.from_hypergraph(h, 4)
+    draws = 0
+    ch = _Chunks(60, 60, budget_s)
+    while ch.next and draws < 1_000_000:
+        S = ch.next
+        split = {2: S // 6, 4: S // 3}
+        split[3] = S - split[2] - split[4]
+        t0 = time.perf_counter()
+        g.sample(4, split, seed=100 + draws)
+        ch.done(S, time.perf_counter() - t0)
+        draws += S
+    out["sampler"] = {"value": draws / ch.used, "unit": "draws/s", "cores": 1, "kind": "oracle",
+                      "sample": f"Alg. 4 on the comm-5m generator at scale 0.004 "
+                                f"({draws} draws in {ch.used:.1f} s)"}
+    # one stub-shuffled null model of the smallest base, over a bounded set of ESU roots
+    b = synth.null_base(NULL_BASES[0], seed=100)
+    mem = oracle.stub_shuffle(b.members, b.offsets, seed=1, model=0)
+    gm = oracle.Graph(mem, b.offsets, b.num_nodes, 4)
+    lo, sets = b.num_nodes, 0
+    ch = _Chunks(max(threads, 8), threads, budget_s)
+    while ch.next and lo > 0:
+        new_lo = max(0, lo - ch.next)
+        t0 = time.perf_counter()
+        hist, _ = gm.census(4, threads=threads, roots=(new_lo, lo))
+        ch.done(lo - new_lo, time.perf_counter() - t0)
+        sets += int(hist.sum())
+        lo = new_lo
+    out["null_batch"] = {"value": sets / ch.used, "unit": UNIT, "cores": threads,
+                         "kind": "oracle",
+                         "sample": f"stub shuffle 0 of the {NULL_BASES[0]}-hyperedge base: ESU "
+                                   f"roots [{lo}, {b.num_nodes}) of {b.num_nodes} ({sets} sets "
+                                   f"in {ch.used:.1f} s)"}
+    return out
 
 
+# ---------------------------------------------------------------- GPU measurements
 def _event_ms(fn, stream):
     import torch
     e0 = torch.cuda.Event(enable_timing=True)
@@ -235,58 +405,212 @@ def _event_ms(fn, stream):
     return e0.elapsed_time(e1), out
 
 
-def measure_sampler(hm, stream, scale=0.004, budgets=(12_000, 60_000, 300_000), seeds=5):
+def measure_exact(hm, h, order, steps, warmup, stream, flush, barrier=None, clocks=None):
+    """Build + census steps on the resident hyperedge list of h.
+
+    Warm-up steps after the first (which also tunes the census schedules) are
+    fully traced: the kernels' shares and the ingest phases come from there,
+    and the dominant kernel is the one traced in the timed steps (two events
+    per launch, on its launching stream)."""
+    import torch
+    mem = torch.from_numpy(h.members).cuda()
+    off = torch.from_numpy(h.offsets).cuda()
+    n = h.num_nodes
+    hist = torch.empty(hm.num_classes(order), dtype=torch.int64, device="cuda")
+
+    def step():
+        g = hm.build(mem, off, n, order)
+        hm.count_exact(g, order, out=hist)
+        return g
+
+    g = None
+    for i in range(warmup):
+        if i == 1:
+            torch.cuda.synchronize()
+            hm.trace_read()
+            hm.trace_enable(True)
+        if g is not None:
+            g.free()
+        g = step()
+    torch.cuda.synchronize()
+    hm.trace_enable(False)
+    per, phases = {}, {}
+    for name, ms in hm.trace_read():
+        c = (phases if name.startswith("ingest_") else per).setdefault(name, [0, 0.0])
+        c[0] += 1
+        c[1] += ms
+    dom = max(per, key=lambda k: per[k][1])
+    totals = hm.work_totals(g, order)
+    g_counts = [int(x) for x in g.counts]
+    e2 = g.edges(2).cpu().numpy() if n <= 4096 else None
+    g.free()
+    torch.cuda.synchronize()
+    sets_per_step = int(hist.sum().item())
+
+    hm.trace_only(dom)
+    hm.trace_enable(True)
+    launches0 = hm.launch_count()
+    total_ms = 0.0
+    ctx = clocks if clocks is not None else _NullCtx()
+    with ctx:
+        if barrier:
+            barrier()
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g = step()
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            g.free()
+        if barrier:
+            barrier()
+        torch.cuda.synchronize()
+    hm.trace_enable(False)
+    hm.trace_only(None)
+    gpu_launches = hm.launch_count() - launches0
+    trace = hm.trace_read()
+    assert int(hist.sum().item()) == sets_per_step
+    dom_launches = sum(1 for name, _ in trace if name == dom)
+    dom_ms = sum(ms for name, ms in trace if name == dom)
+    return {"total_ms": total_ms, "sets_per_step": sets_per_step, "totals": totals,
+            "graph_counts": g_counts, "e2": e2, "dominant": dom,
+            "dom_avg_s": (dom_ms / dom_launches / 1e3) if dom_launches else None,
+            "gpu_launches": gpu_launches,
+            "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4),
+                            "share": round(v[1] / sum(x[1] for x in per.values()), 4)}
+                        for k, v in sorted(per.items(), key=lambda kv: -kv[1][1])},
+            "ingest_ms_per_step": {k: round(v[1] / v[0], 4) for k, v in phases.items()},
+            "hist": hist.cpu()}
+
+
+class _NullCtx:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+    def summary(self):
+        return None
+
+
+def measure_e2e(hm, h, order, steps, stream, flush, barrier=None):
+    """hm_count_exact_host from pinned host buffers: the copies of the hyperedge
+    list in and of the histogram out are inside every timed step."""
+    import torch
+    hmem = torch.from_numpy(h.members).pin_memory()
+    hoff = torch.from_numpy(h.offsets).pin_memory()
+    hout = torch.empty(hm.num_classes(order), dtype=torch.int64).pin_memory()
+    for _ in range(2):
+        hm.count_exact_host(hmem, hoff, h.num_nodes, order, out=hout)
+    if barrier:
+        barrier()
+    e2e_ms = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hm.count_exact_host(hmem, hoff, h.num_nodes, order, out=hout)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    return e2e_ms, int(hout.sum().item()), int(h.members.nbytes + h.offsets.nbytes), \
+        hout.numel() * 8
+
+
+def small_exact_row(hm, stream, flush, order=4, steps=20, warmup=5):
+    """The face-to-face-shaped exact census (330 nodes, 20,000 hyperedges), with
+    the ALU roofline of its dominant dense kernel."""
+    from paper_2209_10241_gb300 import synth
+    h = synth.workload("f2f-330")
+    r = measure_exact(hm, h, order, steps, warmup, stream, flush)
+    peaks, src = _peaks()
+    sms = _sm_count()
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    dom = r["dominant"]
+    unit, _, traffic = ROOFLINE_ALU.get(dom, ("item", None, None))
+    units = r["totals"].get(dom) or {"census_gl_edges": r["graph_counts"][2],
+                                     "census_gl_pairs": h.num_nodes * (h.num_nodes - 1) // 2
+                                     }.get(dom)
+    ops, per_unit = algorithmic_ops(dom, units, h.num_nodes, r["e2"])
+    peak = sms * ALU_LANES_PER_SM_CLK * mhz * 1e6 / 1e12
+    ach = (ops / r["dom_avg_s"] / 1e12) if ops and r["dom_avg_s"] else None
+    ms = r["total_ms"] / steps
+    return {"workload": "f2f-330", "nodes": h.num_nodes, "hyperedges": h.num_hyperedges,
+            "ms_per_step": ms, "sets_per_step": r["sets_per_step"],
+            "sets_per_s": r["sets_per_step"] / (ms / 1e3), "kernels": r["kernels"],
+            "ingest_ms_per_step": r["ingest_ms_per_step"],
+            "roofline": {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak,
+                         "unit": "Tops/s (algorithmic int32 word-ops)",
+                         "frac": (ach / peak) if ach else None, "traffic": traffic,
+                         "units_per_launch": units, "unit_kind": unit, "ops_per_unit": per_unit,
+                         "launch_ms": (r["dom_avg_s"] or 0) * 1e3,
+                         "peak_source": f"{sms} SMs x {ALU_LANES_PER_SM_CLK} lanes x {mhz:.0f} "
+                                        f"MHz (maximum SM clock, {src})"}}
+
+
+def mre(est, T, mask):
+    """Mean relative error of estimates over the classes in mask."""
+    import numpy as np
+    return float(np.mean(np.abs(est[mask] - T[mask]) / T[mask])) if mask.any() else None
+
+
+def measure_sampler(hm, stream, scale=0.004,
+                    budgets=(12_000, 60_000, 300_000, 1_500_000), seeds=5):
     """Alg. 4 with uniform and learned proposals: relative error vs GPU time.
 
     Communication-shaped graph (comm-5m generator at `scale`); the proposal is
     trained on a separate instance of the same generator from exact
-    per-hyperedge contributions; "learned" weights draws by t_e / sqrt(cost_e)
-    (beta = 1/2, error per unit of GPU time), "learned_per_draw" by t_e
-    (beta = 0); error = mean over classes with T_c >= 100 of |T^_c - T_c| / T_c
-    against the exact census, averaged over seeds.
+    per-hyperedge contributions (hm_proposal_train); "learned" weights draws
+    by t_e / sqrt(cost_e) (beta = 1/2, error per unit of GPU time). The
+    learned rows' GPU time includes the proposal weights (features, MLP
+    inference, integer weights: hm_proposal_weights). Error = mean over
+    classes of |T^_c - T_c| / T_c against the exact census, over classes with
+    T_c > 0 (primary), T_c >= 100 and T_c >= 1000, averaged over seeds.
     """
     import numpy as np
-    import torch
     from paper_2209_10241_gb300 import synth
     k = 4
     tr = synth.workload("comm-5m", seed=7, scale=scale)
     gt = hm.from_host(tr, 4)
-    t_train = time.perf_counter()
-    contrib = hm.contributions(gt, k)
-    exact_t = hm.count_exact(gt, k)
-    tgt = hm.proposal_targets(gt, k, contrib, exact_t, eps=1e-9)
-    feat = hm.features(gt, k)
-    params = torch.from_numpy(synth.mlp_init_params(1)).cuda()
-    losses = hm.mlp_train(params, feat, tgt, epochs=300, batch=4096, lr=1e-3, seed=3)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t_train
+    train_ms, prop = _event_ms(lambda: hm.proposal_train(gt, k, seed=3, epochs=300,
+                                                         batch=4096, lr=1e-3), stream)
     h = synth.workload("comm-5m", seed=9, scale=scale)
     g = hm.from_host(h, 4)
     exact_ms, T = _event_ms(lambda: hm.count_exact(g, k), stream)
     T = T.cpu().numpy().astype(np.float64)
-    big = T >= 100
-    q_ms, q = _event_ms(lambda: hm.proposal_weights(g, k, params, lam=0.1, beta=0.5), stream)
-    q0 = hm.proposal_weights(g, k, params, lam=0.1, beta=0.0)
+    masks = {"T>0": T > 0, "T>=100": T >= 100, "T>=1000": T >= 1000}
+    q_ms, q = _event_ms(lambda: hm.proposal_q(prop, g, lam=0.1, beta=0.5), stream)
     rows = []
     for S in budgets:
         split = {2: S // 6, 4: S // 3}
         split[3] = S - split[2] - split[4]
         rec = {"S": S}
-        for name, qq in (("uniform", None), ("learned", q), ("learned_per_draw", q0)):
-            ms, errs = [], []
+        for name, qq in (("uniform", None), ("learned", q)):
+            ms, errs = [], {m: [] for m in masks}
             for r in range(seeds):
                 t, (est, _) = _event_ms(lambda: hm.count_sampled(g, k, samples=split,
                                                                  seed=100 + r, q=qq), stream)
                 e = est.cpu().numpy()
-                ms.append(t)
-                errs.append(float(np.mean(np.abs(e[big] - T[big]) / T[big])))
-            rec[name] = {"ms": float(np.median(ms)), "mre": float(np.mean(errs))}
+                ms.append(t + (q_ms if qq is not None else 0.0))
+                for m, mk in masks.items():
+                    errs[m].append(mre(e, T, mk))
+            rec[name] = {"gpu_ms": float(np.median(ms)),
+                         **{f"mre_{m}": float(np.mean(v)) for m, v in errs.items()}}
         rows.append(rec)
     return {"workload": f"comm-5m generator at scale {scale}: {h.num_nodes} nodes, "
                         f"{h.num_hyperedges} hyperedges", "order": k,
-            "classes_T_ge_100": int(big.sum()), "exact_census_ms": exact_ms,
-            "proposal_weights_ms": q_ms, "train_s": train_s,
-            "train_loss_first_last": [losses[0], losses[-1]], "by_budget": rows}
+            "classes": {m: int(mk.sum()) for m, mk in masks.items()},
+            "exact_census_ms": exact_ms, "proposal_weights_ms": q_ms,
+            "learned_gpu_ms_includes": "proposal weights (features, MLP inference, integer q)",
+            "train_ms": train_ms, "train_on": f"{tr.num_hyperedges} hyperedges (seed 7)",
+            "by_budget": rows}
 
 
 NULL_BASES = (50_000, 69_000, 97_000, 134_000, 186_000, 259_000, 360_000, 500_000)
@@ -313,27 +637,20 @@ def measure_sampler_full(hm, stream, budgets=(100_000, 1_000_000, 10_000_000), s
     0.05, another seed); error against the exact census of the full graph. A
     budget whose single run exceeds run_limit_s ends the sweep."""
     import numpy as np
-    import torch
     from paper_2209_10241_gb300 import synth
     k = 4
     t0 = time.perf_counter()
     tr = synth.workload("comm-5m", seed=7, scale=0.05)
     gt = hm.from_host(tr, 4)
-    contrib = hm.contributions(gt, k)
-    exact_t = hm.count_exact(gt, k)
-    tgt = hm.proposal_targets(gt, k, contrib, exact_t, eps=1e-9)
-    feat = hm.features(gt, k)
-    params = torch.from_numpy(synth.mlp_init_params(1)).cuda()
-    losses = hm.mlp_train(params, feat, tgt, epochs=300, batch=8192, lr=1e-3, seed=3)
-    torch.cuda.synchronize()
+    prop = hm.proposal_train(gt, k, seed=3, epochs=300, batch=8192, lr=1e-3)
     train_s = time.perf_counter() - t0
-    del contrib, feat, tgt, gt
+    del gt
     h = synth.workload("comm-5m", seed=0)
     g = hm.from_host(h, 4)
     exact_ms, T = _event_ms(lambda: hm.count_exact(g, k), stream)
     T = T.cpu().numpy().astype(np.float64)
-    q_ms, q = _event_ms(lambda: hm.proposal_weights(g, k, params, lam=0.1, beta=0.5), stream)
-    masks = {"T>=100": T >= 100, "T>=1000": T >= 1000}
+    q_ms, q = _event_ms(lambda: hm.proposal_q(prop, g, lam=0.1, beta=0.5), stream)
+    masks = {"T>0": T > 0, "T>=100": T >= 100, "T>=1000": T >= 1000}
     rows = []
     for S in budgets:
         split = {2: S // 6, 4: S // 3}
@@ -346,13 +663,13 @@ def measure_sampler_full(hm, stream, budgets=(100_000, 1_000_000, 10_000_000), s
                 t, (est, _) = _event_ms(lambda: hm.count_sampled(g, k, samples=split,
                                                                  seed=100 + r, q=qq), stream)
                 e = est.cpu().numpy()
-                ms.append(t)
-                for m, big in masks.items():
-                    errs[m].append(float(np.mean(np.abs(e[big] - T[big]) / T[big])))
+                ms.append(t + (q_ms if qq is not None else 0.0))
+                for m, mk in masks.items():
+                    errs[m].append(mre(e, T, mk))
                 if t > run_limit_s * 1e3:
                     slow = True
                     break
-            rec[name] = {"ms": float(np.median(ms)), "runs": len(ms),
+            rec[name] = {"gpu_ms": float(np.median(ms)), "runs": len(ms),
                          **{f"mre_{m}": float(np.mean(v)) for m, v in errs.items()}}
         rows.append(rec)
         if slow:
@@ -360,17 +677,16 @@ def measure_sampler_full(hm, stream, budgets=(100_000, 1_000_000, 10_000_000), s
     return {"workload": f"comm-5m generator, full size: {h.num_nodes} nodes, "
                         f"{h.num_hyperedges} hyperedges; proposal trained on {tr.num_hyperedges} "
                         f"hyperedges (scale 0.05, seed 7)", "order": k,
-            "classes_T_ge_100": int(masks["T>=100"].sum()),
-            "classes_T_ge_1000": int(masks["T>=1000"].sum()), "exact_census_ms": exact_ms,
-            "proposal_weights_ms": q_ms, "train_s": train_s,
-            "train_loss_first_last": [losses[0], losses[-1]], "by_budget": rows}
+            "classes": {m: int(mk.sum()) for m, mk in masks.items()},
+            "exact_census_ms": exact_ms, "proposal_weights_ms": q_ms, "train_s": train_s,
+            "by_budget": rows}
 
 
-def measure_large(hm, stream, names=("coauth-1m", "comm-5m")):
-    """Exact order-4 census of the full-size co-authorship- and communication-
-    shaped workloads: device ingest + census, event-timed once each (the
-    census of one of them runs for seconds, so there is no L2 effect to
-    flush). Not part of the default run: generating comm-5m takes ~1.5 min."""
+def measure_large(hm, stream, names=("comm-5m",), scale=1.0):
+    """Exact order-4 census of the full-size communication-shaped workload (or
+    another named one): device ingest + census, event-timed once each, with
+    the library's trace spans. Not part of the default run: generating comm-5m
+    takes ~1.5 min."""
     import torch
     from paper_2209_10241_gb300 import synth
     out = {}
@@ -382,7 +698,7 @@ def measure_large(hm, stream, names=("coauth-1m", "comm-5m")):
     torch.cuda.synchronize()
     for name in names:
         t0 = time.perf_counter()
-        h = synth.workload(name)
+        h = synth.workload(name, scale=scale)
         gen_s = time.perf_counter() - t0
         mem = torch.from_numpy(h.members).cuda()
         off = torch.from_numpy(h.offsets).cuda()
@@ -397,7 +713,7 @@ def measure_large(hm, stream, names=("coauth-1m", "comm-5m")):
             spans[span] = round(spans.get(span, 0.0) + ms, 4)
         totals = hm.work_totals(g, 4)
         sets = int(hist.sum().item())
-        out[name] = {"nodes": h.num_nodes, "hyperedges": h.num_hyperedges,
+        out[name] = {"nodes": h.num_nodes, "hyperedges": h.num_hyperedges, "scale": scale,
                      "graph_counts": [int(x) for x in g.counts],
                      "generate_s": gen_s, "build_ms": build_ms, "census_ms": census_ms,
                      "sets": sets, "sets_per_s": sets / ((build_ms + census_ms) / 1e3),
@@ -408,77 +724,45 @@ def measure_large(hm, stream, names=("coauth-1m", "comm-5m")):
     return out
 
 
-def cpu_baseline_rows(budget_s: float = 8.0):
-    """The oracle beside the sampler and null-batch rows, each on a bounded sample."""
-    import oracle
-    from paper_2209_10241_gb300 import synth
-    threads = os.cpu_count() or 1
-    out = {}
-    # Alg. 4 as the oracle runs it, sample by sample (single-threaded)
-    h = synth.workload("comm-5m", seed=9, scale=0.004)
-    g = oracle.Graph.from_hypergraph(h, 4)
-    draws = 0
-    ch = _Chunks(60, 60, budget_s)
-    while ch.next and draws < 1_000_000:
-        S = ch.next
-        split = {2: S // 6, 4: S // 3}
-        split[3] = S - split[2] - split[4]
-        t0 = time.perf_counter()
-        g.sample(4, split, seed=100 + draws)
-        ch.done(S, time.perf_counter() - t0)
-        draws += S
-    t_used = ch.used
-    out["sampler"] = {"value": draws / t_used, "unit": "draws/s", "cores": 1, "kind": "oracle",
-                      "sample": f"Alg. 4 on the comm-5m generator at scale 0.004 "
-                                f"({draws} draws in {t_used:.1f} s)"}
-    # one stub-shuffled null model of the smallest base, over a bounded set of ESU roots
-    b = synth.null_base(NULL_BASES[0], seed=100)
-    mem = oracle.stub_shuffle(b.members, b.offsets, seed=1, model=0)
-    gm = oracle.Graph(mem, b.offsets, b.num_nodes, 4)
-    # ESU root v enumerates the sets whose smallest id is v: the top ids are the
-    # light roots, so the sample grows downwards from the largest id
-    lo, sets = b.num_nodes, 0
-    ch = _Chunks(max(threads, 8), threads, budget_s)
-    while ch.next and lo > 0:
-        new_lo = max(0, lo - ch.next)
-        t0 = time.perf_counter()
-        hist, _ = gm.census(4, threads=threads, roots=(new_lo, lo))
-        ch.done(lo - new_lo, time.perf_counter() - t0)
-        sets += int(hist.sum())
-        lo = new_lo
-    t_used = ch.used
-    out["null_batch"] = {"value": sets / t_used, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"stub shuffle 0 of the {NULL_BASES[0]}-hyperedge base: ESU "
-                                   f"roots [{lo}, {b.num_nodes}) of {b.num_nodes} ({sets} sets "
-                                   f"in {t_used:.1f} s)"}
-    return out
-
-
+# ---------------------------------------------------------------- reference arm
 def run_reference(args, rank: int):
+    """The oracle as it stands on the host cores: each step a time-boxed
+    sample of ESU root windows of the headline workload (windows continue
+    downwards from step to step)."""
     if rank != 0:
         return
     from paper_2209_10241_gb300 import synth
-    h = synth.workload(WORKLOAD)
-    times = []
-    per_step_budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
-    for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(h, args.order, budget_s=per_step_budget)
-        if i >= args.warmup:
-            times.append(cb["value"])
-    value = statistics.median(times)
-    cb["value"] = value
+    h = synth.workload(args.workload)
+    per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    orc = OracleRoots(h, args.order, target_s=min(1.0, per_step / 2))
+    vals, sets_all, secs_all = [], 0, 0.0
+    try:
+        for i in range(args.warmup + args.steps):
+            sets, secs, _ = orc.run(per_step, first_wait_s=10 * per_step)
+            if i >= args.warmup and secs > 0:
+                vals.append(sets / secs)
+                sets_all += sets
+                secs_all += secs
+    finally:
+        orc.close()
+    value = statistics.median(vals) if vals else None
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "order": args.order, "nodes": 330,
-                   "hyperedges": 20000},
-        "cpu_baseline": cb,
+        "config": {"workload": args.workload, "order": args.order, "nodes": h.num_nodes,
+                   "hyperedges": h.num_hyperedges},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.threads, "kind": "oracle",
+                         "sample": f"{args.workload} order-{args.order}: per step, the ESU root "
+                                   f"windows completed in {per_step:.1f} s, from id "
+                                   f"{orc.start} downwards (reached {orc.lo}); "
+                                   f"{sets_all} sets in {secs_all:.1f} s over the timed steps"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
+# ---------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -486,11 +770,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--order", type=int, default=4)
+    ap.add_argument("--workload", default=WORKLOAD, choices=["coauth-1m", "f2f-330"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the sampler and null-batch measurements")
-    ap.add_argument("--only", choices=["sampler", "null", "large", "sampler-full"], default=None,
-                    help="run one of the extra measurements alone (for profiling)")
+                    help="skip the face-to-face, sampler and null-batch rows")
+    ap.add_argument("--only", choices=["sampler", "null", "large", "sampler-full", "f2f"],
+                    default=None, help="run one of the extra measurements alone (for profiling)")
+    ap.add_argument("--large", default="comm-5m",
+                    help="workload of --only large (comm-5m or coauth-1m)")
+    ap.add_argument("--scale", type=float, default=1.0, help="scale of --only large")
     ap.add_argument("--null-bases", type=int, default=8,
                     help="number of null-model bases (log-spaced 50k-500k hyperedges)")
     args = ap.parse_args()
@@ -508,115 +796,40 @@ def main():
     from paper_2209_10241_gb300 import synth
 
     torch.cuda.set_device(local)
+    hm.load()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     if args.only:
-        hm.load()
-        stream = torch.cuda.current_stream()
         if args.only == "sampler":
             res = measure_sampler(hm, stream)
         elif args.only == "null":
             res = measure_null(hm, stream, hyperedges=NULL_BASES[:args.null_bases])
         elif args.only == "sampler-full":
             res = measure_sampler_full(hm, stream)
+        elif args.only == "f2f":
+            res = small_exact_row(hm, stream, flush, args.order, args.steps, args.warmup)
         else:
-            res = measure_large(hm, stream)
+            res = measure_large(hm, stream, names=(args.large,), scale=args.scale)
         print(json.dumps({"only": args.only, **res}), flush=True)
         return
     if world > 1:
         dist.init_process_group("nccl")
-    hm.load()
-    h = synth.workload(WORKLOAD)
-    mem = torch.from_numpy(h.members).cuda()
-    off = torch.from_numpy(h.offsets).cuda()
-    n = h.num_nodes
-    ncls = hm.num_classes(args.order)
-    hist = torch.empty(ncls, dtype=torch.int64, device="cuda")
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    def step():
-        g = hm.build(mem, off, n, args.order)
-        hm.count_exact(g, args.order, out=hist)
-        return g
-
-    # warm-up; every step after the first (which also tunes the census
-    # schedules) fully traced: the kernels' shares and the ingest phases come
-    # from here, and the dominant kernel is the one traced in the timed region
-    for i in range(args.warmup):
-        if i == 1:
-            torch.cuda.synchronize()
-            hm.trace_read()
-            hm.trace_enable(True)
-        if i < args.warmup - 1:
-            step().free()
-        else:
-            g = step()
-    torch.cuda.synchronize()
-    hm.trace_enable(False)
-    per, phases = {}, {}
-    for name, ms in hm.trace_read():
-        c = (phases if name.startswith("ingest_") else per).setdefault(name, [0, 0.0])
-        c[0] += 1
-        c[1] += ms
-    dom = max(per, key=lambda k: per[k][1])
-    totals = hm.work_totals(g, args.order)
-    g_counts = list(g.counts)
-    e2_host = g.edges(2).cpu().numpy()
-    g.free()
-    torch.cuda.synchronize()
-    sets_per_step = int(hist.sum().item())
+    h = synth.workload(args.workload)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    # device-resident timed region; only the dominant kernel's launches are
-    # bracketed by events (two per launch), so the trace adds ~3 us per step
-    hm.trace_only(dom)
-    hm.trace_enable(True)
-    launches0 = hm.launch_count()
-    total_ms = 0.0
-    with Clocks(local) as clk:
-        barrier()
-        for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            g = step()
-            e1.record(stream)
-            e1.synchronize()
-            total_ms += e0.elapsed_time(e1)
-            g.free()
-        barrier()
-    hm.trace_enable(False)
-    hm.trace_only(None)
-    gpu_launches = hm.launch_count() - launches0
-    trace = hm.trace_read()
-    assert int(hist.sum().item()) == sets_per_step
-    total_ms = max_over_ranks(total_ms)
+    clk = Clocks(local)
+    r = measure_exact(hm, h, args.order, args.steps, args.warmup, stream, flush, barrier, clk)
+    total_ms = max_over_ranks(r["total_ms"])
     ms_per_step = total_ms / args.steps
+    sets_per_step = r["sets_per_step"]
     value = whole_job_rate(sets_per_step, args.steps, world, total_ms)
-
-    # end-to-end through the C ABI with host buffers
-    hmem = torch.from_numpy(h.members).pin_memory()
-    hoff = torch.from_numpy(h.offsets).pin_memory()
-    hout = torch.empty(ncls, dtype=torch.int64).pin_memory()
-    for _ in range(2):
-        hm.count_exact_host(hmem, hoff, n, args.order, out=hout)
-    barrier()
-    e2e_ms = 0.0
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        hm.count_exact_host(hmem, hoff, n, args.order, out=hout)
-        e1.record(stream)
-        e1.synchronize()
-        e2e_ms += e0.elapsed_time(e1)
-    assert int(hout.sum().item()) == sets_per_step
+    e2e_ms, e2e_sets, h2d, d2h = measure_e2e(hm, h, args.order, args.steps, stream, flush,
+                                             barrier)
+    assert e2e_sets == sets_per_step
     e2e_ms = max_over_ranks(e2e_ms)
     e2e_value = whole_job_rate(sets_per_step, args.steps, world, e2e_ms)
 
@@ -626,53 +839,35 @@ def main():
             dist.destroy_process_group()
         return
 
-    # the dominant kernel's launches in the timed region (events on the
-    # launching stream)
-    dom_launches = sum(1 for name, _ in trace if name == dom)
-    dom_ms = sum(ms for name, ms in trace if name == dom)
-    avg_s = dom_ms / dom_launches / 1e3
     peaks, src = _peaks()
-    clocks = clk.summary()
-    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    unit, _, traffic = ROOFLINE.get(dom, ("item", None, None))
-    units = totals.get(dom) or {"census_gl_edges": g_counts[2],
-                                "census_gl_pairs": n * (n - 1) // 2}.get(dom)
-    ops, ops_per_unit = algorithmic_ops(dom, units, n, e2_host)
-    peak_tops = SMS * ALU_LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e12
-    achieved = (ops / avg_s / 1e12) if ops else None
-    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak_tops,
-                "unit": "Tops/s (algorithmic int32 word-ops)",
-                "frac": (achieved / peak_tops) if achieved else None, "traffic": traffic,
-                "units_per_launch": units, "unit_kind": unit, "ops_per_unit": ops_per_unit,
-                "launch_ms": avg_s * 1e3,
-                "peak_source": f"{SMS} SMs x {ALU_LANES_PER_SM_CLK} lanes x {sm_mhz:.0f} MHz "
-                               f"(sampled clock; HBM {peaks['hbm_gbs']} GB/s {src}, unused)"}
+    roofline = hbm_roofline(r["dominant"], r["totals"], r["dom_avg_s"], peaks["hbm_gbs"], src)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "order": args.order, "nodes": n,
-                   "hyperedges": h.num_hyperedges, "l2": "flushed (256 MiB write) before each step",
+        "config": {"workload": args.workload, "order": args.order, "nodes": h.num_nodes,
+                   "hyperedges": h.num_hyperedges,
+                   "l2": "flushed (256 MiB write) before each step",
                    "parallelism": f"replicas x{world}"},
         "sets_per_step": sets_per_step,
-        "candidates_per_step": totals,
+        "graph_counts": r["graph_counts"],
+        "candidates_per_step": r["totals"],
         "kernels_from": "warm-up steps after the first (every kernel traced)",
-        "kernels": {k: {"launches": v[0], "ms_total": round(v[1], 4),
-                        "share": round(v[1] / sum(x[1] for x in per.values()), 4)}
-                    for k, v in sorted(per.items(), key=lambda kv: -kv[1][1])},
-        "ingest_ms_per_step": {k: round(v[1] / v[0], 4) for k, v in phases.items()},
+        "kernels": r["kernels"],
+        "ingest_ms_per_step": r["ingest_ms_per_step"],
         "roofline": roofline,
-        "clocks": clocks,
-        "gpu_launches": gpu_launches,
-        "e2e": {"value": e2e_value, "unit": UNIT,
-                "h2d_bytes_per_step": int(h.members.nbytes + h.offsets.nbytes),
-                "d2h_bytes_per_step": ncls * 8},
+        "clocks": clk.summary(),
+        "gpu_launches": r["gpu_launches"],
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
     }
     if world == 1 and not args.no_extras:
+        if args.workload != "f2f-330":
+            line["f2f_330"] = small_exact_row(hm, stream, flush, args.order)
         line["sampler"] = measure_sampler(hm, stream)
         line["null_batch"] = measure_null(hm, stream, hyperedges=NULL_BASES[:args.null_bases])
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(h, args.order)
+        line["cpu_baseline"] = cpu_baseline(h, args.order, args.workload)
         if not args.no_extras:
             line["cpu_baseline"]["rows"] = cpu_baseline_rows()
     print(json.dumps(line), flush=True)

@@ -39,6 +39,7 @@ extern "C" {
 #endif
 
 typedef struct hm_graph hm_graph;
+typedef struct hm_proposal hm_proposal;
 typedef int hm_status;
 
 enum {
@@ -89,8 +90,10 @@ hm_status hm_class_of_mask(int order, uint32_t mask, int32_t* cls);
  * set). Hyperedges with more than max_order distinct members cannot lie in a
  * max_order-node set (Def. 2), so they are only counted (hm_graph_info).
  * Synchronous on `stream`. Errors: HM_EINVAL (bad sizes, a member outside
- * [0, num_nodes), offsets not monotone), HM_ENOMEM, HM_ECUDA. On success *out
- * owns device memory until hm_free.
+ * [0, num_nodes), offsets not monotone), HM_ENOMEM, HM_ECUDA, HM_ETABLEFULL (a
+ * hash set could not hold its keys: only when the HM_TABLE_CAP test hook
+ * forces tables smaller than their key sets), HM_ETIMEOUT (a bounded wait of
+ * the sort gave up). On success *out owns device memory until hm_free.
  */
 hm_status hm_build(const int32_t* d_members, const int64_t* d_offsets, int64_t num_hyperedges,
                    int32_t num_nodes, int max_order, void* stream, hm_graph** out);
@@ -197,6 +200,17 @@ hm_status hm_trace_enable(int on);
 /* Restricts the trace to spans named `name` (NULL or "" = every span), so
  * that a timed run pays for the events of one kernel only. */
 hm_status hm_trace_only(const char* name);
+/*
+ * Self-test of the bounded device-side waits (no counterpart in the paper;
+ * instrumentation). Runs the radix sort's decoupled look-back, in both its
+ * thread and warp forms, against a status word that no tile ever publishes:
+ * each wait gives up after its poll limit (2^20 polls, about a second), and
+ * the call returns HM_ETIMEOUT through the same path as any entry point whose
+ * wait gave up, with the device left usable. Returns HM_EINVAL if no wait
+ * gave up. Synchronous.
+ */
+hm_status hm_selftest_wait(void* stream);
+
 /* Number of kernels the library has launched in this process (instrumentation). */
 uint64_t hm_launch_count(void);
 hm_status hm_trace_read(int max_entries, char* names, int name_len, float* ms, int* count);
@@ -273,9 +287,9 @@ hm_status hm_proposal_targets(hm_graph* g, int order, const uint32_t* d_contrib,
                               void* stream);
 
 /*
- * Integer proposal for hm_count_sampled: within stratum s, with
- * z_e = f(x_e) - beta * log1p(cost_e), cost_e = the number of sets a draw of
- * e enumerates (feature 9), w_e = exp(z_e - max_s z),
+ * Integer proposal for hm_count_sampled from explicit MLP parameters: within
+ * stratum s, with z_e = f(x_e) - beta * log1p(cost_e), cost_e = the number of
+ * sets a draw of e enumerates (feature 9), w_e = exp(z_e - max_s z),
  * p_e = (1 - lambda) w_e / sum_s w + lambda / |E_s| (0 < lambda <= 1 keeps
  * every p_e > 0), and d_q[row] = min(2^32 - 1, 1 + floor(p_e * |E_s| * 1024))
  * (device uint32). beta in [0, 1]: 0 minimises the variance per draw, 1/2
@@ -283,8 +297,50 @@ hm_status hm_proposal_targets(hm_graph* g, int order, const uint32_t* d_contrib,
  * to t_e / sqrt(cost_e)). Reductions run in a fixed order: q is
  * reproducible. Synchronous.
  */
-hm_status hm_proposal_weights(hm_graph* g, int order, const float* d_params, float lambda,
-                              float beta, uint32_t* d_q, void* stream);
+hm_status hm_proposal_weights_params(hm_graph* g, int order, const float* d_params,
+                                     float lambda, float beta, uint32_t* d_q, void* stream);
+
+/*
+ * He-uniform initial MLP parameters (device float[hm_mlp_num_params()]):
+ * weight i = (2u - 1) * sqrt(6 / fan_in) with u = (v >> 11) * 2^-53 and v the
+ * 64-bit Philox4x32-10 value of key = seed, counter (i, 0, 0, 0x494E4954),
+ * computed in double and rounded to float; biases 0. Enqueued on `stream`.
+ */
+hm_status hm_mlp_init(float* d_params, uint64_t seed, void* stream);
+
+/*
+ * Train the learned proposal of Alg. 4's sampler on `train` (typically a
+ * subsample of, or a graph shaped like, the hypergraph to be sampled), all
+ * on the device: exact per-hyperedge contributions (hm_contributions) and
+ * the exact census (hm_count_exact) give the targets (hm_proposal_targets,
+ * eps = 1e-9), hm_features gives the inputs, the parameters start from
+ * hm_mlp_init(seed) and train by hm_mlp_train(epochs, batch, lr, seed).
+ * Bit for bit the same as that chain of calls. h_loss: host float[epochs]
+ * (may be NULL), each epoch's mean loss. Synchronous. On success *out owns a
+ * small device buffer until hm_proposal_free. Errors: HM_EINVAL (bad
+ * arguments), HM_EUNSUPPORTED (order > the graph's max_order), HM_ENOMEM,
+ * HM_ECUDA, HM_ETIMEOUT.
+ */
+hm_status hm_proposal_train(hm_graph* train, int order, uint64_t seed, int epochs, int64_t batch,
+                            float lr, float* h_loss, void* stream, hm_proposal** out);
+
+/* Copy a trained proposal's MLP parameters to d_params (device
+ * float[hm_mlp_num_params()]); enqueued on `stream`. */
+hm_status hm_proposal_params(const hm_proposal* p, float* d_params, void* stream);
+
+/* Order a proposal was trained at (-1 for NULL). */
+int hm_proposal_order(const hm_proposal* p);
+
+/*
+ * Integer proposal q for hm_count_sampled on graph g (any graph built with
+ * max_order >= the proposal's order), as hm_proposal_weights_params with the
+ * proposal's trained parameters and order. Synchronous.
+ */
+hm_status hm_proposal_weights(const hm_proposal* p, hm_graph* g, float lambda, float beta,
+                              uint32_t* d_q, void* stream);
+
+/* Release a proposal. NULL is allowed. */
+void hm_proposal_free(hm_proposal* p);
 
 /*
  * Null-model batch: the counting step repeated on randomised hypergraphs
@@ -316,23 +372,29 @@ hm_status hm_count_null_batch(int num_bases, const int32_t* d_members, const int
 
 /*
  * hm_count_sampled without any device allocation (the paper has no
- * counterpart; this serves callers that cannot allocate device memory while
- * they count -- e.g. code running in a host callback or a latency-critical
- * loop where cudaMalloc/cudaFree may block or synchronise the device, or
- * applications that reserve all device memory up front). Same arguments,
+ * counterpart). It serves callers that cannot allocate device memory while
+ * they count: applications that reserve the GPU's memory up front (a serving
+ * process with a fixed budget, or one where another framework's caching
+ * allocator holds the rest), and latency-critical loops where
+ * cudaMalloc/cudaFree may block or synchronise the device. Same arguments,
  * results and errors as hm_count_sampled, bit for bit.
  *   - Every temporary lives in one static device array of 32 MiB inside
  *     libhm.so, which each GPU that loads the library holds until the
  *     process exits. Requests whose temporaries cannot fit are rejected with
  *     HM_EINVAL and a message naming the limit: with weights d_q, each
  *     stratum needs about 16 * |E_s| bytes; at order 4 one draw of a pair
- *     needs about 64 * (max pair degree) bytes.
+ *     needs about 64 * (max pair degree) bytes. Larger sample counts are
+ *     taken in several batches.
  *   - The first call on a device (with that device current) resolves the
  *     array's device address and copies the class tables; make that first
  *     call before any stream capture.
  *   - All calls on a device share the array: calls that overlap on the GPU
  *     (other streams, other host threads) race and must be serialised by the
- *     caller. The call synchronises `stream` between sample batches.
+ *     caller.
+ *   - The call synchronises `stream` and reads sizes back to the host
+ *     between sample batches, so it is made from ordinary host code; it
+ *     cannot be called from a stream callback (host function), where CUDA
+ *     calls are not allowed.
  *   - The graph must have been built by hm_build (which allocates).
  */
 hm_status hm_count_sampled_noalloc(hm_graph* g, int order, const uint64_t* samples_per_size,

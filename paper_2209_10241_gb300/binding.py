@@ -54,14 +54,23 @@ _SIGS = {
     "hm_mlp_train": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
                                     ctypes.c_float, ctypes.c_uint64, _vp, _vp]),
     "hm_proposal_targets": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_float, _vp, _vp]),
-    "hm_proposal_weights": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_float,
-                                           ctypes.c_float, _vp, _vp]),
+    "hm_proposal_weights_params": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_float,
+                                                  ctypes.c_float, _vp, _vp]),
+    "hm_mlp_init": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp]),
+    "hm_proposal_train": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                                         ctypes.c_int64, ctypes.c_float, _vp, _vp,
+                                         ctypes.POINTER(_vp)]),
+    "hm_proposal_params": (ctypes.c_int, [_vp, _vp, _vp]),
+    "hm_proposal_order": (ctypes.c_int, [_vp]),
+    "hm_proposal_weights": (ctypes.c_int, [_vp, _vp, ctypes.c_float, ctypes.c_float, _vp, _vp]),
+    "hm_proposal_free": (None, [_vp]),
     "hm_count_exact_host": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int,
                                            _vp, _vp]),
     "hm_work_totals": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "hm_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "hm_trace_only": (ctypes.c_int, [ctypes.c_char_p]),
     "hm_launch_count": (ctypes.c_uint64, []),
+    "hm_selftest_wait": (ctypes.c_int, [_vp]),
     "hm_trace_read": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]),
     "hm_free": (None, [_vp]),
 }
@@ -296,6 +305,11 @@ def work_totals(g: Graph, order: int, stream=None) -> dict:
     return {name: int(arr[i]) for i, name in enumerate(FAMILIES[order])}
 
 
+def selftest_wait(stream=None):
+    """hm_selftest_wait: raises HMError (HM_ETIMEOUT when the bounded waits work)."""
+    _check(load().hm_selftest_wait(_stream(stream)))
+
+
 def launch_count() -> int:
     """Kernels launched by libhm.so so far in this process."""
     return int(load().hm_launch_count())
@@ -366,8 +380,65 @@ def proposal_targets(g: Graph, order: int, contrib: torch.Tensor, exact: torch.T
 
 def proposal_weights(g: Graph, order: int, params: torch.Tensor, lam: float = 0.1,
                      beta: float = 0.0, stream=None) -> torch.Tensor:
-    """Integer proposal q (int32 tensor holding uint32) for hm_count_sampled."""
+    """hm_proposal_weights_params: integer proposal q (int32 tensor holding
+    uint32) for hm_count_sampled from explicit MLP parameters."""
     q = torch.empty(_rows(g, order), dtype=torch.int32, device="cuda")
-    _check(load().hm_proposal_weights(g._h, order, _dptr(params), float(lam), float(beta),
-                                      _dptr(q), _stream(stream)))
+    _check(load().hm_proposal_weights_params(g._h, order, _dptr(params), float(lam),
+                                             float(beta), _dptr(q), _stream(stream)))
+    return q
+
+
+def mlp_init(seed: int, stream=None) -> torch.Tensor:
+    """hm_mlp_init: He-uniform initial parameters from Philox(seed)."""
+    p = torch.empty(mlp_num_params(), dtype=torch.float32, device="cuda")
+    _check(load().hm_mlp_init(_dptr(p), int(seed) & (2**64 - 1), _stream(stream)))
+    return p
+
+
+class Proposal:
+    """Owning handle of a trained proposal (hm_proposal)."""
+
+    def __init__(self, handle, losses):
+        self._h = handle
+        self.losses = losses
+
+    @property
+    def order(self) -> int:
+        return int(load().hm_proposal_order(self._h))
+
+    def params(self, stream=None) -> torch.Tensor:
+        out = torch.empty(mlp_num_params(), dtype=torch.float32, device="cuda")
+        _check(load().hm_proposal_params(self._h, _dptr(out), _stream(stream)))
+        return out
+
+    def free(self):
+        if self._h:
+            load().hm_proposal_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def proposal_train(train: Graph, order: int, seed: int = 0, epochs: int = 300,
+                   batch: int = 8192, lr: float = 1e-3, stream=None) -> Proposal:
+    """hm_proposal_train on a built graph; returns the Proposal handle (with the
+    per-epoch mean losses in .losses)."""
+    losses = (ctypes.c_float * max(1, epochs))()
+    h = _vp()
+    _check(load().hm_proposal_train(train._h, order, int(seed) & (2**64 - 1), int(epochs),
+                                    int(batch), float(lr), losses, _stream(stream),
+                                    ctypes.byref(h)))
+    return Proposal(h, [float(losses[i]) for i in range(epochs)])
+
+
+def proposal_q(p: Proposal, g: Graph, lam: float = 0.1, beta: float = 0.0,
+               stream=None) -> torch.Tensor:
+    """hm_proposal_weights: integer proposal q of graph g from a trained proposal."""
+    q = torch.empty(_rows(g, p.order), dtype=torch.int32, device="cuda")
+    _check(load().hm_proposal_weights(p._h, g._h, float(lam), float(beta), _dptr(q),
+                                      _stream(stream)))
     return q

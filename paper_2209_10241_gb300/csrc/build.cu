@@ -470,8 +470,18 @@ __global__ void k_edges_out(const uint64_t* __restrict__ e2, const int4* __restr
   }
 }
 
+// Slots of an open-addressing table for m keys: the power of two >= 2m (load
+// <= 1/2). HM_TABLE_CAP=c (a test hook) forces c slots (rounded up to a
+// power of two, at least 16) whatever m: a table smaller than its key set
+// fills up, every insertion and probe still ends after one pass over the
+// slots, and hm_build returns HM_ETABLEFULL.
 uint64_t table_capacity(int64_t m) {
   uint64_t c = 16;
+  if (const char* env = std::getenv("HM_TABLE_CAP")) {
+    const long long want = std::atoll(env);
+    while ((long long)c < want && c < (1ull << 40)) c <<= 1;
+    return c;
+  }
   while (c < (uint64_t)(2 * m)) c <<= 1;
   return c;
 }

@@ -24,6 +24,9 @@
 namespace hm {
 
 void features(const hm_graph* g, int order, float* d_feat, cudaStream_t s);
+void contributions(hm_graph* g, int order, uint32_t* d_contrib, cudaStream_t s);
+void prepare_census(hm_graph* g, int order, cudaStream_t s);
+void launch_census(const hm_graph* g, int order, unsigned long long* hist, cudaStream_t s);
 void mlp_forward(const float* params, const float* X, int64_t n, float* y, cudaStream_t s);
 void mlp_backward(const float* params, const float* X, const float* target, int64_t n,
                   float* grad, float* loss_sum, void* scratch, cudaStream_t s);
@@ -154,7 +157,34 @@ __global__ void k_gather_rows(const float* __restrict__ X, const float* __restri
   }
 }
 
+// He-uniform initial weights from Philox4x32-10 (key = seed, counter =
+// (parameter index, 0, 0, "INIT")): u = (value >> 11) 2^-53 in [0, 1), and
+// weight = (2u - 1) sqrt(6 / fan_in) in double, rounded once to float; the
+// biases start at 0. Layout as in mlp.cu: W1[16][64] | b1[64] | W2[64][64] |
+// b2[64] | w3[64] | b3.
+__global__ void k_mlp_init(float* __restrict__ p, uint64_t seed) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 5313) return;
+  double fan = 0.0;
+  if (i < 1024) fan = 16.0;
+  else if (i >= 1088 && i < 5184) fan = 64.0;
+  else if (i >= 5248 && i < 5312) fan = 64.0;
+  if (fan == 0.0) {
+    p[i] = 0.f;
+    return;
+  }
+  const uint64_t v = philox_draw64(seed, (uint64_t)i, 0u, 0x494E4954u);  // "INIT"
+  const double u = (double)(v >> 11) * 0x1.0p-53;
+  p[i] = (float)((2.0 * u - 1.0) * sqrt(6.0 / fan));
+}
+
 }  // namespace
+
+void mlp_init(float* params, uint64_t seed, cudaStream_t s) {
+  HM_CHECK(mlp_num_params() == 5313, HM_EINVAL, "parameter layout changed");
+  k_mlp_init<<<(5313 + 255) / 256, 256, 0, s>>>(params, seed);
+  HM_KCHECK();
+}
 
 void proposal_targets(const hm_graph* g, int order, const uint32_t* contrib,
                       const uint64_t* exact_hist, float eps, float* out, cudaStream_t s) {
@@ -247,7 +277,115 @@ void mlp_train(float* params, const float* X, const float* target, int64_t n, in
 
 }  // namespace hm
 
+// A trained proposal: the MLP parameters and the order it was trained at.
+struct hm_proposal {
+  int device = 0;
+  int order = 4;
+  float* params = nullptr;  // device float[5313]
+};
+
+namespace hm {
+
+// Alg. 4's proposal trained inside the library: exact per-hyperedge
+// contributions and the exact census of the training graph give the targets,
+// the features are the inputs, the weights start from mlp_init(seed) and train
+// with mlp_train(seed).
+void proposal_train(hm_graph* g, int order, uint64_t seed, int epochs, int64_t batch, float lr,
+                    float* h_loss, cudaStream_t s, hm_proposal* p) {
+  int64_t rows = 0;
+  for (int k = 2; k <= order; ++k) rows += g->counts[k];
+  const ClassTables& T = class_tables(order);
+  mlp_init(p->params, seed, s);
+  if (rows == 0) {
+    for (int e = 0; h_loss && e < epochs; ++e) h_loss[e] = 0.f;
+    HM_CUDA(cudaStreamSynchronize(s));
+    return;
+  }
+  DBuf<float> feat(rows * 16, s), tgt(rows, s);
+  {
+    DBuf<uint32_t> contrib((size_t)rows * T.ncls, s);
+    DBuf<unsigned long long> exact(T.ncls, s);
+    contributions(g, order, contrib.p, s);
+    prepare_census(g, order, s);
+    HM_CUDA(cudaMemsetAsync(exact.p, 0, sizeof(unsigned long long) * T.ncls, s));
+    launch_census(g, order, exact.p, s);
+    proposal_targets(g, order, contrib.p, (const uint64_t*)exact.p, 1e-9f, tgt.p, s);
+  }
+  features(g, order, feat.p, s);
+  mlp_train(p->params, feat.p, tgt.p, rows, epochs, batch, lr, seed, h_loss, s);
+}
+
+}  // namespace hm
+
 extern "C" {
+
+hm_status hm_mlp_init(float* d_params, uint64_t seed, void* stream) {
+  return hm::guarded([&] {
+    HM_CHECK(d_params != nullptr, HM_EINVAL, "NULL parameters");
+    hm::mlp_init(d_params, seed, (cudaStream_t)stream);
+  });
+}
+
+hm_status hm_proposal_train(hm_graph* train, int order, uint64_t seed, int epochs, int64_t batch,
+                            float lr, float* h_loss, void* stream, hm_proposal** out) {
+  hm_proposal* p = nullptr;
+  hm_status st = hm::guarded([&] {
+    HM_CHECK(train != nullptr && out != nullptr, HM_EINVAL, "NULL argument");
+    HM_CHECK(order == 3 || order == 4, HM_EINVAL, "order must be 3 or 4");
+    HM_CHECK(order <= train->kmax, HM_EUNSUPPORTED, "order exceeds the graph's max_order");
+    HM_CHECK(epochs >= 1 && batch >= 1, HM_EINVAL, "epochs and batch must be >= 1");
+    HM_CHECK(lr > 0.f, HM_EINVAL, "learning rate must be > 0");
+    int dev = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    HM_CHECK(dev == train->device, HM_EINVAL, "graph was built on another device");
+    cudaStream_t s = (cudaStream_t)stream;
+    p = new hm_proposal();
+    p->device = dev;
+    p->order = order;
+    HM_CUDA(cudaMalloc((void**)&p->params, sizeof(float) * hm::mlp_num_params()));
+    hm::proposal_train(train, order, seed, epochs, batch, lr, h_loss, s, p);
+  });
+  if (st != HM_OK) {
+    if (p) {
+      if (p->params) cudaFree(p->params);
+      delete p;
+    }
+    return st;
+  }
+  *out = p;
+  return HM_OK;
+}
+
+hm_status hm_proposal_params(const hm_proposal* p, float* d_params, void* stream) {
+  return hm::guarded([&] {
+    HM_CHECK(p && d_params, HM_EINVAL, "NULL argument");
+    HM_CUDA(cudaMemcpyAsync(d_params, p->params, sizeof(float) * hm::mlp_num_params(),
+                            cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  });
+}
+
+int hm_proposal_order(const hm_proposal* p) { return p ? p->order : -1; }
+
+hm_status hm_proposal_weights(const hm_proposal* p, hm_graph* g, float lambda, float beta,
+                              uint32_t* d_q, void* stream) {
+  return hm::guarded([&] {
+    HM_CHECK(p && g && d_q, HM_EINVAL, "NULL argument");
+    HM_CHECK(p->order <= g->kmax, HM_EUNSUPPORTED, "proposal order exceeds the graph's max_order");
+    HM_CHECK(lambda > 0.f && lambda <= 1.f, HM_EINVAL, "lambda must be in (0, 1]");
+    HM_CHECK(beta >= 0.f && beta <= 1.f, HM_EINVAL, "beta must be in [0, 1]");
+    int dev = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    HM_CHECK(dev == g->device && dev == p->device, HM_EINVAL,
+             "graph or proposal lives on another device");
+    hm::proposal_weights(g, p->order, p->params, lambda, beta, d_q, (cudaStream_t)stream);
+  });
+}
+
+void hm_proposal_free(hm_proposal* p) {
+  if (!p) return;
+  if (p->params) cudaFree(p->params);
+  delete p;
+}
 
 hm_status hm_proposal_targets(hm_graph* g, int order, const uint32_t* d_contrib,
                               const uint64_t* d_exact_hist, float eps, float* d_target,
@@ -261,8 +399,8 @@ hm_status hm_proposal_targets(hm_graph* g, int order, const uint32_t* d_contrib,
   });
 }
 
-hm_status hm_proposal_weights(hm_graph* g, int order, const float* d_params, float lambda,
-                              float beta, uint32_t* d_q, void* stream) {
+hm_status hm_proposal_weights_params(hm_graph* g, int order, const float* d_params,
+                                     float lambda, float beta, uint32_t* d_q, void* stream) {
   return hm::guarded([&] {
     HM_CHECK(g && d_params && d_q, HM_EINVAL, "NULL argument");
     HM_CHECK(order == 3 || order == 4, HM_EINVAL, "order must be 3 or 4");

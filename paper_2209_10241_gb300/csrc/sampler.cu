@@ -553,12 +553,15 @@ void count_sampled(hm_graph* g, int order, const uint64_t* S, uint64_t seed, con
 }
 
 // ================================================================ allocation-free variant
-// Some callers cannot allocate device memory while they count: code running
-// inside a host callback or a real-time loop where cudaMalloc may block or
-// synchronise the device, or applications whose memory is fully reserved up
-// front. hm_count_sampled_noalloc serves them: every temporary lives in one
-// file-scope device array of NOALLOC_BYTES, held by each GPU that loads the
-// library until the process exits.
+// Some callers cannot allocate device memory while they count: applications
+// that reserve the GPU's memory up front (a serving process with a fixed
+// memory budget, or one whose other framework's caching allocator holds the
+// rest), and latency-critical loops where cudaMalloc/cudaFree may block or
+// synchronise the device. hm_count_sampled_noalloc serves them: every
+// temporary lives in one file-scope device array of NOALLOC_BYTES, held by
+// each GPU that loads the library until the process exits. The call itself
+// synchronises its stream and reads values back to the host between batches,
+// so it is made from ordinary host code, not from a stream callback.
 namespace {
 
 constexpr size_t NOALLOC_BYTES = (size_t)32 << 20;
@@ -709,12 +712,14 @@ void count_sampled_noalloc(hm_graph* g, int order, const uint64_t* S, uint64_t s
   HM_CUDA(cudaMemcpyAsync(Q, hostQ, sizeof hostQ, cudaMemcpyHostToDevice, st));
   int* bad = ar.take<int>(1);
   const bool weighted = d_q != nullptr;
-  // worst-case bytes of one draw: per-draw arrays, scan temporaries, and (order 4,
-  // pair strata) up to 2 * max pair degree second-level entries of 24 bytes
-  const size_t per_draw = 6 * 8 + 8 + (order == 4 ? (size_t)2 * (size_t)g->max_d2 * 32 : 0);
   int64_t qoff = 0;
   for (int s = 2; s <= order; ++s) {
     const int64_t len = g->counts[s];
+    // worst-case bytes of one draw: per-draw arrays and scan temporaries, plus,
+    // for the pair stratum at order 4 (the only one that builds second-level
+    // entries), up to 2 * max pair degree entries of 24 bytes
+    const size_t per_draw =
+        6 * 8 + 8 + (order == 4 && s == 2 ? (size_t)2 * (size_t)g->max_d2 * 32 : 0);
     const size_t mark = ar.used;
     uint64_t* P = nullptr;
     if (weighted && len > 0) {

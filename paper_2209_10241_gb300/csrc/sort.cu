@@ -756,6 +756,36 @@ void sort_batch(const SortJob* jobs, int njobs, cudaStream_t s, unsigned char* e
   }
 }
 
+namespace {
+
+// Self-test of the bounded waits: the last of `tiles` tiles looks back over
+// the others, one of which (tile 0) never publishes, with both look-back
+// forms; each wait gives up after SPIN_LIMIT polls and counts a timeout.
+__global__ void k_wait_selftest(const uint64_t* status, int64_t tiles, uint64_t* out) {
+  if (threadIdx.x == 0) out[0] = look_back(status, tiles - 1, 1, 0);
+  __syncwarp();
+  const uint64_t v = look_back_warp(status, tiles - 1);
+  if (threadIdx.x == 0) out[1] = v;
+}
+
+}  // namespace
+
+void wait_selftest(cudaStream_t s) {
+  constexpr int64_t tiles = 4;
+  DBuf<uint64_t> buf(tiles + 2, s);
+  std::vector<uint64_t> h(tiles + 2, 0);
+  for (int64_t t = 1; t < tiles; ++t) h[t] = ST_AGG | 1;  // tiles 1..3 publish an aggregate
+  HM_CUDA(cudaMemcpyAsync(buf.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice, s));
+  k_wait_selftest<<<1, 32, 0, s>>>(buf.p, tiles, buf.p + tiles);
+  HM_KCHECK();
+  unsigned* timeouts = (unsigned*)(pinned_words() + 80);
+  *timeouts = 0;
+  wait_timeouts_async(timeouts, s);
+  HM_CUDA(cudaStreamSynchronize(s));
+  wait_timeouts_check(*timeouts, s);
+  HM_CHECK(false, HM_EINVAL, "bounded wait self-test: no wait gave up");
+}
+
 void wait_timeouts_async(unsigned* h_count, cudaStream_t s) {
   HM_CUDA(cudaMemcpyFromSymbolAsync(h_count, g_wait_timeouts, sizeof(unsigned), 0,
                                     cudaMemcpyDeviceToHost, s));
@@ -942,3 +972,7 @@ void scan_batch_inplace(const ScanJob* jobs, int njobs, cudaStream_t s, unsigned
 }
 
 }  // namespace hm
+
+extern "C" hm_status hm_selftest_wait(void* stream) {
+  return hm::guarded([&] { hm::wait_selftest((cudaStream_t)stream); });
+}

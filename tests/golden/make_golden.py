@@ -27,6 +27,17 @@ CASES = {
     "uniform-200": ("uniform-200", 0, 1.0, (3, 4)),
     "f2f-330": ("f2f-330", 0, 1.0, (3, 4)),
     "coauth-1m-s001": ("coauth-1m", 0, 0.01, (3, 4)),
+    "coauth-1m-s005": ("coauth-1m", 0, 0.05, (3, 4)),
+    "comm-5m-s001": ("comm-5m", 0, 0.01, (3, 4)),
+}
+
+# Stub-shuffled null models (Sec. 6.3) of the smallest null-batch base:
+# name: (base hyperedges, base seed, shuffle seed, model index, orders). Model
+# t of a batch with shuffle seed s is oracle.stub_shuffle(base, seed=s,
+# model=t), normalised and counted like any input.
+NULL_CASES = {
+    "null-50k-m0": (50_000, 100, 1, 0, (3, 4)),
+    "null-50k-m1": (50_000, 100, 1, 1, (3, 4)),
 }
 
 
@@ -39,11 +50,20 @@ def input_digest(h) -> str:
 
 
 def make(name: str, threads: int) -> dict:
-    wl, seed, scale, orders = CASES[name]
-    h = synth.workload(wl, seed=seed, scale=scale)
-    g = oracle.Graph.from_hypergraph(h, 4)
+    if name in NULL_CASES:
+        H, base_seed, null_seed, model, orders = NULL_CASES[name]
+        h = synth.null_base(H, seed=base_seed)
+        shuffled = oracle.stub_shuffle(h.members, h.offsets, seed=null_seed, model=model)
+        g = oracle.Graph(shuffled, h.offsets, h.num_nodes, 4)
+        head = {"case": name, "workload": "null_base", "base_hyperedges": H,
+                "base_seed": base_seed, "null_seed": null_seed, "model": model}
+    else:
+        wl, seed, scale, orders = CASES[name]
+        h = synth.workload(wl, seed=seed, scale=scale)
+        g = oracle.Graph.from_hypergraph(h, 4)
+        head = {"case": name, "workload": wl, "seed": seed, "scale": scale}
     rec = {
-        "case": name, "workload": wl, "seed": seed, "scale": scale,
+        **head,
         "num_nodes": h.num_nodes, "num_hyperedges": h.num_hyperedges,
         "input_sha256": input_digest(h),
         "distinct_per_size": {str(s): g.count(s) for s in (2, 3, 4)},
@@ -63,7 +83,7 @@ def make(name: str, threads: int) -> dict:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--threads", type=int, default=os.cpu_count() or 1)
-    ap.add_argument("names", nargs="*", default=list(CASES))
+    ap.add_argument("names", nargs="*", default=list(CASES) + list(NULL_CASES))
     a = ap.parse_args()
     for name in a.names:
         rec = make(name, a.threads)

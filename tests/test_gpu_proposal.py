@@ -4,11 +4,12 @@
   countmax_c * T_c (full-sweep identity);
 * features equal the CPU reference (float32 vs float64: rtol 1e-5);
 * the tensor-core MLP forward and backward equal the float64 reference with
-  the same bf16 rounding points: the remaining differences come from fp32 vs
-  fp64 accumulation (~1e-6 relative) and from rare bf16 rounding flips that
-  this causes (one bf16 ulp, 2^-8 relative, on few elements), so outputs are
-  compared at 2e-3 relative to their scale and gradients at 5e-3 of their
-  largest magnitude;
+  the same bf16 rounding points, every output and every gradient element
+  within its own bound (tests/mlp_bounds.py: float32 accumulation error on
+  the sum of |terms|, plus the proven effect of the bf16 roundings that can
+  flip), so a small entry cannot be wrong and pass;
+* hm_proposal_train equals the chain of calls it wraps bit for bit, and its
+  initial weights are the Philox He-uniform draws hm.h states;
 * one Adam step equals the reference update;
 * training lowers the loss, and the learned proposal's estimates are unbiased
   and bit-exact with the oracle given the same q;
@@ -25,6 +26,7 @@ import oracle
 from oracle import features as F
 from oracle import mlp
 from paper_2209_10241_gb300 import synth
+from tests import mlp_bounds
 
 pytestmark = pytest.mark.gpu
 
@@ -64,22 +66,31 @@ def _mlp_data(n, seed):
     return X, t
 
 
+@pytest.mark.parametrize("biases", [False, True])
 @pytest.mark.parametrize("n", [1, 17, 1000, 33333])
-def test_mlp_forward_backward_match_reference(hm, n):
-    p = mlp.init_params(5)
+def test_mlp_forward_backward_match_reference(hm, n, biases):
+    p = mlp.init_params(5).copy()
+    if biases:  # the initial biases are 0: give them values too
+        st = synth.Stream(n, 31)
+        for lo, hi in ((mlp.P_B1, mlp.P_W2), (mlp.P_B2, mlp.P_W3), (mlp.P_B3, mlp.NPARAM)):
+            u = (st.u64(hi - lo) >> np.uint64(40)).astype(np.float64) / 2 ** 24
+            p[lo:hi] = (u - 0.5).astype(np.float32)
     X, t = _mlp_data(n, n)
     dp, dX, dt = (torch.from_numpy(a).cuda() for a in (p, X, t))
+    yr, yb, gr, gb, L, Lb = mlp_bounds.bounds(p, X, t)
+    # the bounds' reference is the plain float64 reference network
+    yr2, _ = mlp.forward(p.astype(np.float64), X.astype(np.float64))
+    assert np.array_equal(yr, yr2)
+    assert np.allclose(gr, mlp.backward(p.astype(np.float64), X.astype(np.float64),
+                                        t.astype(np.float64)), rtol=1e-12, atol=0)
     y = hm.mlp_forward(dp, dX).cpu().numpy().astype(np.float64)
-    yr, _ = mlp.forward(p.astype(np.float64), X.astype(np.float64))
-    assert np.allclose(y, yr, rtol=0, atol=2e-3 * max(1.0, np.abs(yr).max()))
+    bad = np.abs(y - yr) > yb
+    assert not bad.any(), (np.where(bad)[0][:5], (np.abs(y - yr) / yb)[bad][:5])
     grad, loss = hm.mlp_backward(dp, dX, dt)
-    gr = mlp.backward(p.astype(np.float64), X.astype(np.float64), t.astype(np.float64))
     g = grad.cpu().numpy().astype(np.float64)
-    for lo, hi in [(mlp.P_W1, mlp.P_B1), (mlp.P_B1, mlp.P_W2), (mlp.P_W2, mlp.P_B2),
-                   (mlp.P_B2, mlp.P_W3), (mlp.P_W3, mlp.P_B3), (mlp.P_B3, mlp.NPARAM)]:
-        scale = max(1e-12, np.abs(gr[lo:hi]).max())
-        assert np.abs(g[lo:hi] - gr[lo:hi]).max() <= 5e-3 * scale, (lo, hi)
-    assert abs(loss.item() - ((yr - t) ** 2).sum()) <= 1e-3 * max(1.0, ((yr - t) ** 2).sum())
+    bad = np.abs(g - gr) > gb
+    assert not bad.any(), (np.where(bad)[0][:5], (np.abs(g - gr) / gb)[bad][:5])
+    assert abs(loss.item() - L) <= Lb
 
 
 def test_adam_step_matches_reference(hm):
@@ -186,3 +197,53 @@ def test_learned_proposal_gains_over_uniform(hm, trained):
     mse_u = np.mean(err["uniform"])
     mse_l = np.mean(err["learned"])
     assert mse_l < 0.8 * mse_u, (mse_l, mse_u)
+
+
+def test_mlp_init_is_the_stated_philox_draw(hm):
+    seed = 0x1234_5678_9ABC
+    got = hm.mlp_init(seed).cpu().numpy()
+    want = np.zeros(mlp.NPARAM, dtype=np.float64)
+    for lo, hi, fan in ((mlp.P_W1, mlp.P_B1, 16), (mlp.P_W2, mlp.P_B2, 64),
+                        (mlp.P_W3, mlp.P_B3, 64)):
+        for i in range(lo, hi):
+            u = (oracle.draw64(seed, i, 0, 0x494E4954) >> 11) * 2.0 ** -53
+            want[i] = (2.0 * u - 1.0) * np.sqrt(6.0 / fan)
+    assert np.array_equal(got, want.astype(np.float32))
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_proposal_train_equals_the_chain(hm, k):
+    h = synth.workload("comm-5m", seed=7, scale=0.002)
+    g = hm.from_host(h, 4)
+    prop = hm.proposal_train(g, k, seed=11, epochs=6, batch=1024, lr=3e-3)
+    assert prop.order == k
+    # the five calls it wraps
+    contrib = hm.contributions(g, k)
+    exact = hm.count_exact(g, k)
+    tgt = hm.proposal_targets(g, k, contrib, exact, eps=1e-9)
+    feat = hm.features(g, k)
+    p = hm.mlp_init(11)
+    losses = hm.mlp_train(p, feat, tgt, epochs=6, batch=1024, lr=3e-3, seed=11)
+    assert torch.equal(prop.params(), p)
+    assert prop.losses == losses
+    h2 = synth.workload("comm-5m", seed=8, scale=0.002)
+    g2 = hm.from_host(h2, 4)
+    q1 = hm.proposal_q(prop, g2, lam=0.1, beta=0.5)
+    q2 = hm.proposal_weights(g2, k, p, lam=0.1, beta=0.5)
+    assert torch.equal(q1, q2)
+    prop.free()
+
+
+def test_proposal_api_errors(hm):
+    h = synth.workload("uniform-200")
+    g3 = hm.from_host(h, 3)
+    with pytest.raises(hm.HMError) as e:
+        hm.proposal_train(g3, 4, seed=1, epochs=1)
+    assert e.value.status == 6  # order above the graph's max_order
+    with pytest.raises(hm.HMError) as e:
+        hm.proposal_train(g3, 3, seed=1, epochs=0)
+    assert e.value.status == 1
+    prop = hm.proposal_train(hm.from_host(h, 4), 4, seed=1, epochs=1)
+    with pytest.raises(hm.HMError) as e:
+        hm.proposal_q(prop, g3)  # order-4 proposal on an order-3 graph
+    assert e.value.status == 6

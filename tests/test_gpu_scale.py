@@ -1,0 +1,92 @@
+"""GPU parity with the oracle at the scales the benchmark runs.
+
+Stored oracle histograms (tests/golden/, written by make_golden.py, which
+calls only oracle/) pin:
+* the co-authorship-shaped workload at 5 % scale (5*10^4 nodes, 10^5
+  hyperedges) and the communication-shaped one at 1 % scale (5*10^4 nodes,
+  10^5 hyperedges): sparse graphs without bitmaps, where the census runs the
+  sparse TX kernel, the graphlet identities by hash probes and both tiers of
+  the 4-cycle pass;
+* stub-shuffled models 0 and 1 (shuffle seed 1) of the smallest null-model
+  base (5*10^4 hyperedges, 825 nodes), which are rows 0 and 1 of the
+  benchmark's 64-model null batch: the batch is run exactly as the benchmark
+  runs it (8 bases, 8 models each, blocks of up to 8,250 nodes) and its rows
+  compared, in the default mode and with the graphlet census forced on
+  bitmap rows.
+Counts are integers and must match bit for bit.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2209_10241_gb300 import synth
+from tests.golden.make_golden import NULL_CASES, input_digest
+from tests.test_gpu_census import _set_mode
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+NULL_BASES = (50_000, 69_000, 97_000, 134_000, 186_000, 259_000, 360_000, 500_000)
+
+
+def _golden(case):
+    path = os.path.join(GOLDEN, f"census_{case}.json")
+    if not os.path.exists(path):
+        pytest.skip(f"stored oracle histogram {case} not written yet")
+    with open(path) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("case", ["coauth-1m-s005", "comm-5m-s001"])
+@pytest.mark.parametrize("k", [3, 4])
+@pytest.mark.parametrize("mode", ["tuned", "graphlets_hash", "graphlets_tiers", "chunk8"])
+def test_sparse_workloads_against_stored_oracle(hm, monkeypatch, case, k, mode):
+    _set_mode(monkeypatch, mode)
+    rec = _golden(case)
+    h = synth.workload(rec["workload"], seed=rec["seed"], scale=rec["scale"])
+    assert input_digest(h) == rec["input_sha256"], "generator drift: regenerate goldens"
+    g = hm.from_host(h, 4)
+    for s in (2, 3, 4):
+        assert g.count(s) == rec["distinct_per_size"][str(s)]
+    got = hm.count_exact(g, k).cpu().numpy().astype(np.uint64)
+    assert got.tolist() == rec["hist"][str(k)]
+
+
+@pytest.fixture(scope="module")
+def bench_bases():
+    return [synth.null_base(H, seed=100 + i) for i, H in enumerate(NULL_BASES)]
+
+
+@pytest.mark.parametrize("mode", ["default", "graphlets_bitmap"])
+@pytest.mark.parametrize("k", [3, 4])
+def test_bench_null_batch_rows_against_stored_oracle(hm, monkeypatch, bench_bases, mode, k):
+    for var in ("HM_PAIR_BITMAP", "HM_DENSE_FAMILIES", "HM_TRIPLE_ROWS", "HM_AUTOTUNE",
+                "HM_CENSUS_CHUNK", "HM_GRAPHLETS"):
+        monkeypatch.delenv(var, raising=False)
+    if mode == "graphlets_bitmap":
+        monkeypatch.setenv("HM_GRAPHLETS", "1")
+        monkeypatch.setenv("HM_PAIR_BITMAP", "1")
+        monkeypatch.setenv("HM_AUTOTUNE", "0")
+    rows = hm.null_batch(bench_bases, k, 8, seed=1).cpu().numpy().astype(np.uint64)
+    assert rows.shape == (64, hm.num_classes(k))
+    for name, (H, base_seed, null_seed, model, _) in NULL_CASES.items():
+        rec = _golden(name)
+        assert (H, base_seed, null_seed) == (NULL_BASES[0], 100, 1)
+        assert input_digest(bench_bases[0]) == rec["input_sha256"]
+        assert rows[model].tolist() == rec["hist"][str(k)], name
+
+
+def test_bench_null_batch_rows_equal_single_builds(hm, bench_bases):
+    """Rows of the largest and a middle base equal the census of the same
+    stub-shuffled model built alone (union against single-graph paths)."""
+    import torch
+    import oracle
+    rows = hm.null_batch(bench_bases, 4, 8, seed=1).cpu()
+    for b, j in ((7, 0), (7, 7), (3, 5)):
+        t = b * 8 + j
+        h = bench_bases[b]
+        mem = oracle.stub_shuffle(h.members, h.offsets, seed=1, model=t)
+        g = hm.build(torch.from_numpy(mem).cuda(), torch.from_numpy(h.offsets).cuda(),
+                     h.num_nodes, 4)
+        assert torch.equal(hm.count_exact(g, 4).cpu(), rows[t]), (b, j)

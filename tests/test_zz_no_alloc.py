@@ -1,9 +1,9 @@
 """The allocation-free sampler entry point agrees with the allocating one.
 
 hm_count_sampled_noalloc exists for callers that must not allocate device
-memory while counting (host callbacks, latency-critical loops, memory
-reserved up front); its temporaries live in a static device array inside
-libhm.so. Two calls in a row (the array keeps the previous call's contents)
+memory while counting (applications that reserve the GPU's memory up front,
+latency-critical loops where cudaMalloc may block); its temporaries live in
+a static device array inside libhm.so. Two calls in a row (the array keeps the previous call's contents)
 must each match hm_count_sampled bit for bit, the tolerance every sampler
 test uses. This file is collected last on purpose.
 """
@@ -35,6 +35,41 @@ def test_two_calls_in_a_row_match_hm_count_sampled(hm, k, weighted):
     est = torch.empty(nc, dtype=torch.float64, device="cuda")
     raw = torch.empty(2 * nc, dtype=torch.int64, device="cuda")
     for seed in (21, 22):
+        want_est, want_raw = _reference(hm, g, k, S, seed, q)
+        hm.count_sampled_noalloc(g, k, est, raw, samples=S, seed=seed, q=q)
+        assert est.cpu().numpy().tobytes() == want_est.tobytes()
+        assert (raw.cpu().numpy() == want_raw).all()
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_several_batches_per_stratum(hm, weighted):
+    # a hub with 6,000 pair neighbours: one order-4 pair draw may need
+    # ~0.38 MB of second-level entries, so the static array holds fewer than
+    # 90 pair draws at a time and 240 of them run in several batches (the
+    # arena is reset between batches, beside the weighted prefix sums)
+    hub_leaves = 6_000
+    edges = [[0, v] for v in range(1, hub_leaves + 1)]
+    st = synth.Stream(5, 9)
+    extra = 400
+    for _ in range(extra):
+        a, b, c, d = (int(x) for x in 1 + st.below(4, 300))
+        edges.append([a, b])
+        edges.append([0, a, b])
+        edges.append([a, b, c])
+        edges.append([0, a, b, c, d][:4])
+        edges.append([a, c, d])
+    h = synth.from_edges(edges, hub_leaves + 1)
+    g = hm.from_host(h, 4)
+    k = 4
+    S = {2: 240, 3: 400, 4: 200}
+    q = None
+    if weighted:
+        rows = sum(g.count(s) for s in range(2, k + 1))
+        q = torch.from_numpy((1 + synth.Stream(13, 2).below(rows, 500)).astype(np.int32)).cuda()
+    nc = hm.num_classes(k)
+    est = torch.empty(nc, dtype=torch.float64, device="cuda")
+    raw = torch.empty(2 * nc, dtype=torch.int64, device="cuda")
+    for seed in (31, 32):
         want_est, want_raw = _reference(hm, g, k, S, seed, q)
         hm.count_sampled_noalloc(g, k, est, raw, samples=S, seed=seed, q=q)
         assert est.cpu().numpy().tobytes() == want_est.tobytes()
