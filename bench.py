@@ -409,9 +409,10 @@ def measure_exact(hm, h, order, steps, warmup, stream, flush, barrier=None, cloc
     """Build + census steps on the resident hyperedge list of h.
 
     Warm-up steps after the first (which also tunes the census schedules) are
-    fully traced: the kernels' shares and the ingest phases come from there,
-    and the dominant kernel is the one traced in the timed steps (two events
-    per launch, on its launching stream)."""
+    fully traced with the forked launches run in order: the kernels' shares
+    and the ingest phases come from there, and the dominant kernel is the one
+    traced in the timed steps (two events per launch, on its launching
+    stream; those steps run the census launches concurrently, as always)."""
     import torch
     mem = torch.from_numpy(h.members).cuda()
     off = torch.from_numpy(h.offsets).cuda()
@@ -426,14 +427,18 @@ def measure_exact(hm, h, order, steps, warmup, stream, flush, barrier=None, cloc
     g = None
     for i in range(warmup):
         if i == 1:
+            # traced steps run the forked launches in order, so that each
+            # span times one kernel (as a serialised launch list does)
             torch.cuda.synchronize()
             hm.trace_read()
+            hm.serialize_launches(True)
             hm.trace_enable(True)
         if g is not None:
             g.free()
         g = step()
     torch.cuda.synchronize()
     hm.trace_enable(False)
+    hm.serialize_launches(False)
     per, phases = {}, {}
     for name, ms in hm.trace_read():
         c = (phases if name.startswith("ingest_") else per).setdefault(name, [0, 0.0])
@@ -852,7 +857,7 @@ def main():
         "sets_per_step": sets_per_step,
         "graph_counts": r["graph_counts"],
         "candidates_per_step": r["totals"],
-        "kernels_from": "warm-up steps after the first (every kernel traced)",
+        "kernels_from": "warm-up steps after the first (every kernel traced, launches in order)",
         "kernels": r["kernels"],
         "ingest_ms_per_step": r["ingest_ms_per_step"],
         "roofline": roofline,

@@ -211,6 +211,15 @@ hm_status hm_trace_only(const char* name);
  */
 hm_status hm_selftest_wait(void* stream);
 
+/*
+ * Instrumentation (no counterpart in the paper): while on != 0, work that
+ * the library would run concurrently on side streams (the census launches of
+ * one graph, the ingest's structure chains) runs in order on the calling
+ * stream instead, so that traced spans time one kernel each, as a profiler's
+ * serialised launch list does. Results are the same either way. Process-wide.
+ */
+hm_status hm_serialize_launches(int on);
+
 /* Number of kernels the library has launched in this process (instrumentation). */
 uint64_t hm_launch_count(void);
 hm_status hm_trace_read(int max_entries, char* names, int name_len, float* ms, int* count);

@@ -71,6 +71,7 @@ _SIGS = {
     "hm_trace_only": (ctypes.c_int, [ctypes.c_char_p]),
     "hm_launch_count": (ctypes.c_uint64, []),
     "hm_selftest_wait": (ctypes.c_int, [_vp]),
+    "hm_serialize_launches": (ctypes.c_int, [ctypes.c_int]),
     "hm_trace_read": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]),
     "hm_free": (None, [_vp]),
 }
@@ -308,6 +309,11 @@ def work_totals(g: Graph, order: int, stream=None) -> dict:
 def selftest_wait(stream=None):
     """hm_selftest_wait: raises HMError (HM_ETIMEOUT when the bounded waits work)."""
     _check(load().hm_selftest_wait(_stream(stream)))
+
+
+def serialize_launches(on: bool = True):
+    """hm_serialize_launches: forked work in order on the calling stream."""
+    _check(load().hm_serialize_launches(1 if on else 0))
 
 
 def launch_count() -> int:

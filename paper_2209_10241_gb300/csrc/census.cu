@@ -390,38 +390,102 @@ __global__ void k_ws_all(const int64_t* __restrict__ off2, const int64_t* __rest
   }
 }
 
-// x in the sorted range a[lo, hi)?
-__device__ __forceinline__ bool in_sorted(const int32_t* __restrict__ a, int64_t lo, int64_t hi,
-                                          int32_t x) {
-  int64_t l = lo, h = hi;
-  while (l < h) {
-    const int64_t mid = (l + h) >> 1;
-    if (__ldg(a + mid) < x)
-      l = mid + 1;
-    else
-      h = mid;
-  }
-  return l < hi && __ldg(a + l) == x;
+// TX on graphs without bitmaps, one warp per 3-hyperedge e = {a, b, c}
+// (a < b < c). A fourth node d outside e makes the 4-set V' = e + {d}; write
+// P(d) for its pairs to a, b, c, T(d) for the 3-hyperedges it forms with two
+// members, Q(d) for the 4-hyperedge e + {d}. A pair neighbour d of member x
+// is "plain" when P(d) = {x}, T(d) is empty and Q(d) is false: then V' is a
+// TX set whose pattern depends only on x, and e is its only 3-hyperedge. So
+// plain candidates are counted, not enumerated:
+//   plain(x) = d2(x) - (members adjacent to x) - (special pair neighbours of x),
+// where the special nodes of e are the d with two or more pairs to e, with a
+// 3-hyperedge through two members, or with the 4-hyperedge. They are found
+// by six scans, each node kept at its first source only:
+//   0-2. N(a) & N(b), N(a) & N(c), N(b) & N(c): the shorter of the two rows
+//        scanned, membership in the other by a signature test and a probe;
+//   3-5. the third nodes of the 3-hyperedges through (a, b), (a, c), (b, c):
+//        the shorter of the two members' incidence lists scanned;
+//   6.   where the three members' 4-hyperedge signatures share d's bit, the
+//        pair neighbours d of each member with Q(d) (others are found above).
+// Each special d gets its full P, T and Q by probes (a signature test first),
+// adds to the special count of every member it is a pair neighbour of, and is
+// counted when V' is a TX set of this anchor: no 4-hyperedge, and e the
+// smallest 3-hyperedge of V' ({a,b,d} < e iff d < c, {a,c,d} < e iff d < b,
+// {b,c,d} < e iff d < a). Every loop and member index is a compile-time
+// constant after unrolling, so the per-member state stays in registers.
+struct TxsAnchor {
+  int32_t m0, m1, m2;
+  int64_t o20, o21, o22, o30, o31, o32;
+  int32_t d20, d21, d22, d30, d31, d32;
+  uint64_t s20, s21, s22, s30, s31, s32, s4;
+  bool pab, pac, pbc;
+};
+
+template <class T>
+__device__ __forceinline__ T sel3(int i, T x0, T x1, T x2) {
+  return i == 0 ? x0 : (i == 1 ? x1 : x2);
 }
 
-// TX on graphs without bitmaps, one warp per 3-hyperedge e = {a, b, c}. A
-// candidate d of member x from a pair {x, d} is "plain" unless d is a pair
-// neighbour of another member, lies in a 3-hyperedge with two members, or
-// completes a 4-hyperedge with e. A plain candidate passes every canonical
-// rule of FamTXT and its pattern depends only on x, so it is counted, not
-// enumerated: plain(x) = d2(x) - (other members adjacent to x) - (specials
-// of x). The specials come from small sets, each taken once (from its first
-// source, in a fixed order, with exact membership tests):
-//   1. N(x) & N(o1), 2. N(x) & N(o2), by scanning the shorter sorted row and
-//      binary search in the longer;
-//   3-5. third nodes d in N(x) of the 3-hyperedges through (x, o1), (x, o2),
-//      (o1, o2), by scanning the shorter incidence list;
-//   6. where the members' quad signatures share a bit, the d in N(x) with
-//      that bit and an existing 4-hyperedge {a, b, c, d};
-// and each is evaluated exactly (FamTXT::evaluate). The candidates from
-// 3-hyperedges are the 3-hyperedges through two members, taken from the same
-// scans. The work per 3-hyperedge follows the shorter lists, not the hubs'.
-__global__ void __launch_bounds__(CENSUS_THREADS)
+struct TxsBins {
+  unsigned long long* bins;
+  const uint8_t* lut;
+  int sub;
+  __device__ void count(uint32_t mask, unsigned long long n) const {
+    const uint8_t c1 = lut[mask];
+    if (c1 != 0xFF) atomicAdd(&bins[c1], n);
+    if (sub) {
+      const uint8_t c2 = lut[mask & 63u];
+      if (c2 != 0xFF) atomicAdd(&bins[c2], 0ull - n);
+    }
+  }
+};
+
+// One candidate d of source src (0-2 pair intersections of members (0,1),
+// (0,2), (1,2); 3-5 third nodes of 3-hyperedges through the same pairs;
+// 6-8 quad scan of member src - 6); kp: pair bits known to be set. Adds to
+// the special counts sp0..sp2 and counts the set when it is a TX set of this
+// anchor.
+__device__ __forceinline__ void txs_candidate(const DevGraph& g, const TxsAnchor& A, int src,
+                                              int32_t d, uint32_t kp, const TxsBins& B,
+                                              uint32_t& sp0, uint32_t& sp1, uint32_t& sp2) {
+  const int32_t a = A.m0, b = A.m1, c = A.m2;
+  if (d == a || d == b || d == c) return;
+  const uint64_t db = sig_bit(d);
+  bool Q = false;
+  if (src >= 6) {  // quad scan: only the nodes that close the 4-hyperedge
+    Q = (A.s4 & db) && has_quad(g, a, b, c, d);
+    if (!Q) return;
+  }
+  const bool p0 = (kp & 1u) || ((A.s20 & db) && has_pair(g, a, d));
+  const bool p1 = (kp & 2u) || ((A.s21 & db) && has_pair(g, b, d));
+  const bool p2 = (kp & 4u) || ((A.s22 & db) && has_pair(g, c, d));
+  if (src == 0 && !(p0 && p1)) return;
+  if (src == 1 && (!(p0 && p2) || p1)) return;
+  if (src == 2 && (!(p1 && p2) || p0)) return;
+  const int np = (p0 ? 1 : 0) + (p1 ? 1 : 0) + (p2 ? 1 : 0);
+  if (src >= 3 && np >= 2) return;  // found by a pair intersection
+  const bool t01 = src == 3 || ((A.s30 & A.s31 & db) && has_triple(g, a, b, d));
+  if (src == 4 && t01) return;
+  const bool t02 = src == 4 || ((A.s30 & A.s32 & db) && has_triple(g, a, c, d));
+  if (src == 5 && (t01 || t02)) return;
+  const bool t12 = src == 5 || ((A.s31 & A.s32 & db) && has_triple(g, b, c, d));
+  if (src >= 6 && (t01 || t02 || t12)) return;  // found by a triple scan
+  if (src < 6) Q = (A.s4 & db) && has_quad(g, a, b, c, d);
+  sp0 += p0 ? 1u : 0u;
+  sp1 += p1 ? 1u : 0u;
+  sp2 += p2 ? 1u : 0u;
+  if (Q) return;  // family Q
+  if ((t01 && d < c) || (t02 && d < b) || (t12 && d < a)) return;  // a smaller 3-hyperedge
+  const uint32_t mask = (A.pab ? 1u : 0u) | (A.pac ? 2u : 0u) | (p0 ? 4u : 0u) |
+                        (A.pbc ? 8u : 0u) | (p1 ? 16u : 0u) | (p2 ? 32u : 0u) | 64u |
+                        (t01 ? 128u : 0u) | (t02 ? 256u : 0u) | (t12 ? 512u : 0u);
+  B.count(mask, 1ull);
+}
+
+#ifndef HM_TXS_MINBLOCKS
+#define HM_TXS_MINBLOCKS 4
+#endif
+__global__ void __launch_bounds__(CENSUS_THREADS, HM_TXS_MINBLOCKS)
     k_census_txs(const DevGraph g, const uint8_t* __restrict__ lut_g, int nmask, int ncls,
                  int sub, unsigned long long* __restrict__ hist) {
   __shared__ unsigned long long bins[BIN_STRIDE];
@@ -431,121 +495,107 @@ __global__ void __launch_bounds__(CENSUS_THREADS)
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const FamTXT<true> fam{};
-  auto count = [&](uint32_t mask, unsigned long long n) {
-    const uint8_t c1 = lut[mask];
-    if (c1 != 0xFF) atomicAdd(&bins[c1], n);
-    if (sub) {
-      const uint8_t c2 = lut[mask & 63u];
-      if (c2 != 0xFF) atomicAdd(&bins[c2], 0ull - n);
-    }
-  };
+  const TxsBins B{bins, lut, sub};
   for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < g.m3; t += warps) {
-    typename FamTXT<true>::State st;
-    fam.begin(g, t, 0, st);
-    const int32_t m[3] = {st.x[0], st.x[1], st.x[2]};
-    int64_t o2s[3], o2e[3], o3s[3];
-    int32_t d3[3];
+    TxsAnchor A;
+    const int4 e = g.e3[t];
+    A.m0 = e.x;
+    A.m1 = e.y;
+    A.m2 = e.z;
+    A.o20 = g.off2[e.x];
+    A.o21 = g.off2[e.y];
+    A.o22 = g.off2[e.z];
+    A.d20 = (int32_t)(g.off2[e.x + 1] - A.o20);
+    A.d21 = (int32_t)(g.off2[e.y + 1] - A.o21);
+    A.d22 = (int32_t)(g.off2[e.z + 1] - A.o22);
+    A.o30 = g.off3[e.x];
+    A.o31 = g.off3[e.y];
+    A.o32 = g.off3[e.z];
+    A.d30 = (int32_t)(g.off3[e.x + 1] - A.o30);
+    A.d31 = (int32_t)(g.off3[e.y + 1] - A.o31);
+    A.d32 = (int32_t)(g.off3[e.z + 1] - A.o32);
+    A.s20 = g.sig[e.x];
+    A.s21 = g.sig[e.y];
+    A.s22 = g.sig[e.z];
+    A.s30 = g.sig[(int64_t)g.n + e.x];
+    A.s31 = g.sig[(int64_t)g.n + e.y];
+    A.s32 = g.sig[(int64_t)g.n + e.z];
+    A.s4 = g.sig[2 * (int64_t)g.n + e.x] & g.sig[2 * (int64_t)g.n + e.y] &
+           g.sig[2 * (int64_t)g.n + e.z];
+    // the pairs inside e: lanes 0-2 probe, the warp shares
+    bool mine = false;
+    if (lane < 3) {  // lane 0: {a, b}, 1: {a, c}, 2: {b, c}
+      const int32_t u = lane == 2 ? e.y : e.x, v = lane == 0 ? e.y : e.z;
+      mine = ((lane == 2 ? A.s21 : A.s20) & sig_bit(v)) && has_pair(g, u, v);
+    }
+    const unsigned pb = __ballot_sync(0xffffffffu, mine);
+    A.pab = pb & 1u;
+    A.pac = pb & 2u;
+    A.pbc = pb & 4u;
+    uint32_t sp0 = 0, sp1 = 0, sp2 = 0;
+    const int nsrc = A.s4 ? 9 : 6;
+#pragma unroll 1
+    for (int src = 0; src < nsrc; ++src) {
+      // the source's list (warp-uniform): member pair (p, q) or member x
+      const int p = src < 6 ? (src % 3 == 2 ? 1 : 0) : src - 6;
+      const int q = src % 3 == 0 ? 1 : 2;
+      int64_t o;
+      int32_t len;
+      uint32_t kp = 0;
+      int32_t mp = 0, mq = 0;
+      if (src < 3) {  // the shorter of the two pair rows
+        const int32_t lp = sel3(p, A.d20, A.d21, A.d22), lq = sel3(q, A.d20, A.d21, A.d22);
+        const bool ps = lp <= lq;
+        o = ps ? sel3(p, A.o20, A.o21, A.o22) : sel3(q, A.o20, A.o21, A.o22);
+        len = ps ? lp : lq;
+        kp = 1u << (ps ? p : q);
+      } else if (src < 6) {  // the shorter of the two incidence lists
+        const int32_t lp = sel3(p, A.d30, A.d31, A.d32), lq = sel3(q, A.d30, A.d31, A.d32);
+        const bool ps = lp <= lq;
+        o = ps ? sel3(p, A.o30, A.o31, A.o32) : sel3(q, A.o30, A.o31, A.o32);
+        len = ps ? lp : lq;
+        mp = sel3(p, A.m0, A.m1, A.m2);
+        mq = sel3(q, A.m0, A.m1, A.m2);
+      } else {  // member p's pair row
+        o = sel3(p, A.o20, A.o21, A.o22);
+        len = sel3(p, A.d20, A.d21, A.d22);
+        kp = 1u << p;
+      }
+      for (int32_t i0 = 0; i0 < len; i0 += 32) {
+        const int32_t idx = i0 + lane;
+        if (idx >= len) continue;
+        int32_t d;
+        if (src < 3 || src >= 6) {
+          d = __ldg(g.adj2 + o + idx);
+        } else {
+          const int64_t th = __ldg(g.inc3 + o + idx);
+          if (th == t) continue;
+          const int4 h = g.e3[th];
+          const bool hp = h.x == mp || h.y == mp || h.z == mp;
+          const bool hq = h.x == mq || h.y == mq || h.z == mq;
+          if (!hp || !hq) continue;
+          d = (h.x != mp && h.x != mq) ? h.x : (h.y != mp && h.y != mq) ? h.y : h.z;
+        }
+        txs_candidate(g, A, src, d, kp, B, sp0, sp1, sp2);
+      }
+    }
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      o2s[i] = g.off2[m[i]];
-      o2e[i] = o2s[i] + st.d2[i];
-      o3s[i] = g.off3[m[i]];
-      d3[i] = (int32_t)(st.w[i] - (uint64_t)st.d2[i]);
+    for (int o = 16; o; o >>= 1) {
+      sp0 += __shfl_xor_sync(0xffffffffu, sp0, o);
+      sp1 += __shfl_xor_sync(0xffffffffu, sp1, o);
+      sp2 += __shfl_xor_sync(0xffffffffu, sp2, o);
     }
-    const bool adjm[3][3] = {{false, st.ab, st.ac}, {st.ab, false, st.bc}, {st.ac, st.bc, false}};
-    const uint32_t fixed = (st.ab ? 1u : 0u) | (st.ac ? 2u : 0u) | (st.bc ? 8u : 0u) | 64u;
-    // d a pair neighbour of member i: the signature word rules d out before
-    // the binary search wherever i's word lacks d's bit
-    auto adj = [&](int i, int32_t d) {
-      return (st.s2[i] & sig_bit(d)) && in_sorted(g.adj2, o2s[i], o2e[i], d);
-    };
-    auto in_e = [&](int32_t d) { return d == m[0] || d == m[1] || d == m[2]; };
-    // third node of the 3-hyperedge th if it holds members p and q (and is not e), else -1
-    auto third = [&](int64_t th, int p, int q) -> int32_t {
-      if (th == t) return -1;
-      const int4 h = g.e3[th];
-      const bool hp = h.x == m[p] || h.y == m[p] || h.z == m[p];
-      const bool hq = h.x == m[q] || h.y == m[q] || h.z == m[q];
-      if (!hp || !hq) return -1;
-      return (h.x != m[p] && h.x != m[q]) ? h.x : (h.y != m[p] && h.y != m[q]) ? h.y : h.z;
-    };
-    uint32_t mask;
-    int32_t nd[4];
-    // candidates from 3-hyperedges through members j < k (for x = m[j])
-#pragma unroll 1
-    for (int pr = 0; pr < 3; ++pr) {
-      const int j = pr == 2 ? 1 : 0, k = pr == 0 ? 1 : 2;
-      const int sm = d3[j] <= d3[k] ? j : k;
-      for (int32_t idx = lane; idx < d3[sm]; idx += 32) {
-        const int64_t th = g.inc3[o3s[sm] + idx];
-        const int32_t d = third(th, j, k);
-        if (d < 0 || in_e(d)) continue;
-        const int4 h = g.e3[th];
-        if (fam.evaluate(g, st, j, d, false, make_tri(h.x, h.y, h.z), mask, nd)) count(mask, 1ull);
-      }
-    }
-    // pair candidates, member by member
-#pragma unroll 1
-    for (int i = 0; i < 3; ++i) {
-      const int o1 = i == 0 ? 1 : 0, o2 = i == 2 ? 1 : 2;
-      unsigned long long special = 0;
-      auto take = [&](bool is_new, int32_t d) {
-        special += __popc(__ballot_sync(__activemask(), is_new));
-        if (is_new && fam.evaluate(g, st, i, d, true, Tri{0, 0}, mask, nd)) count(mask, 1ull);
-      };
-      // 1-2: shared pair neighbours
-#pragma unroll 1
-      for (int src = 0; src < 2; ++src) {
-        const int o = src == 0 ? o1 : o2;
-        const int sm = st.d2[i] <= st.d2[o] ? i : o, lg = sm == i ? o : i;
-        for (int32_t i0 = 0; i0 < st.d2[sm]; i0 += 32) {
-          const int32_t idx = i0 + lane;
-          bool is_new = false;
-          int32_t d = -1;
-          if (idx < st.d2[sm]) {
-            d = g.adj2[o2s[sm] + idx];
-            is_new = !in_e(d) && adj(lg, d) && (src == 0 || !adj(o1, d));
-          }
-          take(is_new, d);
-        }
-      }
-      // 3-5: third nodes of 3-hyperedges through (x, o1), (x, o2), (o1, o2)
-#pragma unroll 1
-      for (int src = 0; src < 3; ++src) {
-        const int p = src == 2 ? o1 : i, q = src == 0 ? o1 : o2;
-        const int sm = d3[p] <= d3[q] ? p : q;
-        for (int32_t i0 = 0; i0 < d3[sm]; i0 += 32) {
-          const int32_t idx = i0 + lane;
-          bool is_new = false;
-          int32_t d = -1;
-          if (idx < d3[sm]) {
-            d = third(g.inc3[o3s[sm] + idx], p, q);
-            is_new = d >= 0 && !in_e(d) && adj(i, d) && !adj(o1, d) && !adj(o2, d) &&
-                     (src == 0 || !has_triple(g, m[i], m[o1], d)) &&
-                     (src <= 1 || !has_triple(g, m[i], m[o2], d));
-          }
-          take(is_new, d);
-        }
-      }
-      // 6: 4-hyperedges {a, b, c, d}
-      if (st.s4) {
-        for (int32_t i0 = 0; i0 < st.d2[i]; i0 += 32) {
-          const int32_t idx = i0 + lane;
-          bool is_new = false;
-          int32_t d = -1;
-          if (idx < st.d2[i]) {
-            d = g.adj2[o2s[i] + idx];
-            is_new = (st.s4 & sig_bit(d)) && !in_e(d) && !adj(o1, d) && !adj(o2, d) &&
-                     !has_triple(g, m[i], m[o1], d) && !has_triple(g, m[i], m[o2], d) &&
-                     !has_triple(g, m[o1], m[o2], d) && has_quad(g, m[0], m[1], m[2], d);
-          }
-          take(is_new, d);
-        }
-      }
-      const unsigned long long others = (adjm[i][o1] ? 1 : 0) + (adjm[i][o2] ? 1 : 0);
-      const unsigned long long plain = (unsigned long long)st.d2[i] - others - special;
-      if (plain && lane == 0) count(fixed | (i == 0 ? 4u : i == 1 ? 16u : 32u), plain);
+    if (lane == 0) {
+      const uint32_t fixed = (A.pab ? 1u : 0u) | (A.pac ? 2u : 0u) | (A.pbc ? 8u : 0u) | 64u;
+      const unsigned long long pa =
+          (unsigned long long)A.d20 - (A.pab ? 1 : 0) - (A.pac ? 1 : 0) - sp0;
+      const unsigned long long pbn =
+          (unsigned long long)A.d21 - (A.pab ? 1 : 0) - (A.pbc ? 1 : 0) - sp1;
+      const unsigned long long pc =
+          (unsigned long long)A.d22 - (A.pac ? 1 : 0) - (A.pbc ? 1 : 0) - sp2;
+      if (pa) B.count(fixed | 4u, pa);
+      if (pbn) B.count(fixed | 16u, pbn);
+      if (pc) B.count(fixed | 32u, pc);
     }
   }
   __syncthreads();
@@ -904,8 +954,11 @@ void launch_txs(const hm_graph* g, unsigned long long* hist, cudaStream_t s, boo
   if (g->counts[3] == 0) return;
   const ClassTables& T = class_tables(4);
   const uint8_t* lut = device_lut(4);
+  // a persistent grid: the resident blocks of every SM, warps striding over E_3
+  int sms = 0, per_sm = 0;
+  resident_blocks((const void*)k_census_txs, sms, per_sm);
   const int64_t want = (g->counts[3] + CENSUS_THREADS / 32 - 1) / (CENSUS_THREADS / 32);
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, 152 * 8));
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * per_sm));
   cudaEvent_t ev = nullptr;
   const bool tr = traced && trace_on("census_TX");
   if (tr) trace_begin(s, &ev);

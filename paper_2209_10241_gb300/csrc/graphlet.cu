@@ -511,46 +511,111 @@ __global__ void __launch_bounds__(C4_WARPS * 32)
   if (lane == 0) acc.flush(agg);
 }
 
-// Sort tier, emission: one warp per node with slots [ws[x], ws[x+1]); the
-// lower-ranked neighbours y take consecutive sub-ranges of d(y) slots (a warp
-// scan per round of 32), each filled with the key of every kept z, else the
-// sentinel.
-__global__ void k_c4_emit(const DevGraph g, int bits, const uint64_t* __restrict__ ws,
-                          uint64_t* __restrict__ keys) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t x64 = gw; x64 < g.n; x64 += warps) {
-    const int32_t x = (int32_t)x64;
-    uint64_t base = ws[x];
-    if (ws[x + 1] == base) continue;
-    const int64_t ox = g.off2[x];
-    const int32_t dx = (int32_t)(g.off2[x + 1] - ox);
-    const uint64_t hi = (uint64_t)x << bits;
-    for (int32_t i0 = 0; i0 < dx; i0 += 32) {
-      const int32_t i = i0 + lane;
-      int32_t y = 0, dy = 0;
-      if (i < dx) {
-        y = g.adj2[ox + i];
-        dy = degree(g, y);
-        if (!lower_rank(dy, y, dx, x)) dy = 0;
-      }
-      uint32_t incl = (uint32_t)dy;
+// Sort tier, emission: one block per node with slots [ws[x], ws[x+1]). The
+// lower-ranked neighbours y are staged in shared memory (C4E_CAP per round)
+// with an exclusive prefix of their degrees; the block's threads then walk
+// the round's slots in order, each finding its y by binary search in the
+// prefix, so that neighbour lists are read and keys written in consecutive
+// runs. A slot holds the key of its path x - y - z when z is kept, else the
+// sentinel. The slots of a round sum the same degrees as c4_bound, so the
+// node's slots are exactly [ws[x], ws[x+1]).
+constexpr int C4E_THREADS = 512;
+constexpr int C4E_CAP = 1024;  // neighbours per round (2 per thread)
+
+__global__ void __launch_bounds__(C4E_THREADS)
+    k_c4_emit(const DevGraph g, int bits, const uint64_t* __restrict__ ws,
+              uint64_t* __restrict__ keys) {
+  __shared__ int64_t s_off[C4E_CAP];
+  __shared__ uint32_t s_pre[C4E_CAP];
+  __shared__ uint32_t s_wsum[C4E_THREADS / 32];
+  __shared__ int32_t s_heavy[C4E_THREADS];
+  __shared__ int s_nheavy;
+  __shared__ uint32_t s_total;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t c0 = (int64_t)blockIdx.x * C4E_THREADS; c0 < g.n;
+       c0 += (int64_t)gridDim.x * C4E_THREADS) {
+    if (threadIdx.x == 0) s_nheavy = 0;
+    __syncthreads();
+    const int64_t xi = c0 + threadIdx.x;
+    if (xi < g.n && ws[xi + 1] != ws[xi]) s_heavy[atomicAdd(&s_nheavy, 1)] = (int32_t)xi;
+    __syncthreads();
+    const int nh = s_nheavy;
+    for (int hh = 0; hh < nh; ++hh) {
+      const int32_t x = s_heavy[hh];
+      const int64_t ox = g.off2[x];
+      const int32_t dx = (int32_t)(g.off2[x + 1] - ox);
+      uint64_t base = ws[x];
+      const uint64_t hi = (uint64_t)x << bits;
+      for (int32_t r0 = 0; r0 < dx; r0 += C4E_CAP) {
+        const int32_t cnt = min(C4E_CAP, dx - r0);
+        uint32_t v[2];
+        int64_t o[2];
+        uint32_t tsum = 0;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-      }
-      uint64_t* out = keys + base + (incl - (uint32_t)dy);
-      if (dy) {
-        const int64_t oy = g.off2[y];
-        for (int32_t k = 0; k < dy; ++k) {
-          const int32_t z = g.adj2[oy + k];
-          const bool keep = z != x && lower_rank(degree(g, z), z, dx, x);
-          out[k] = keep ? (hi | (uint64_t)z) : C4_SENTINEL;
+        for (int q = 0; q < 2; ++q) {
+          const int32_t j = threadIdx.x * 2 + q;
+          v[q] = 0;
+          o[q] = 0;
+          if (j < cnt) {
+            const int32_t y = g.adj2[ox + r0 + j];
+            const int64_t oy = g.off2[y];
+            const int32_t dy = (int32_t)(g.off2[y + 1] - oy);
+            if (lower_rank(dy, y, dx, x)) {
+              v[q] = (uint32_t)dy;
+              o[q] = oy;
+            }
+          }
+          tsum += v[q];
         }
+        // exclusive prefix of the per-thread sums over the block
+        uint32_t incl = tsum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t u = __shfl_up_sync(0xffffffffu, incl, d);
+          if (lane >= d) incl += u;
+        }
+        if (lane == 31) s_wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+          uint32_t w = lane < C4E_THREADS / 32 ? s_wsum[lane] : 0u;
+          uint32_t wi = w;
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, wi, d);
+            if (lane >= d) wi += u;
+          }
+          if (lane < C4E_THREADS / 32) s_wsum[lane] = wi - w;
+          if (lane == 31) s_total = wi;
+        }
+        __syncthreads();
+        uint32_t ex = s_wsum[wid] + incl - tsum;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int32_t j = threadIdx.x * 2 + q;
+          if (j < cnt) {
+            s_pre[j] = ex;
+            s_off[j] = o[q];
+          }
+          ex += v[q];
+        }
+        __syncthreads();
+        const uint32_t total = s_total;
+        for (uint32_t sl = threadIdx.x; sl < total; sl += C4E_THREADS) {
+          // the last staged neighbour whose range starts at or before sl (a
+          // neighbour without slots shares its start with the next one)
+          int lo = 0, hi2 = cnt;
+          while (hi2 - lo > 1) {
+            const int mid = (lo + hi2) >> 1;
+            if (s_pre[mid] <= sl) lo = mid;
+            else hi2 = mid;
+          }
+          const int32_t z = g.adj2[s_off[lo] + (sl - s_pre[lo])];
+          const bool keep = z != x && lower_rank(degree(g, z), z, dx, x);
+          keys[base + sl] = keep ? (hi | (uint64_t)(uint32_t)z) : C4_SENTINEL;
+        }
+        base += total;
+        __syncthreads();  // the next round overwrites the staged neighbours
       }
-      base += __shfl_sync(0xffffffffu, incl, 31);
     }
   }
 }
@@ -747,25 +812,36 @@ void graphlet_edges(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
 }
 
 void graphlet_pairs(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
-  TraceSpan span("census_gl_pairs", s);
   if (!g->bits2) {
-    // warp tier over all nodes, then the sort tier over the heavy nodes
+    // warp tier over all nodes, then the sort tier over the heavy nodes (a
+    // trace span per stage)
     const uint64_t want = ((uint64_t)g->n * 32 + C4_WARPS * 32 - 1) / (C4_WARPS * 32);
     const unsigned wblocks = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, 152 * 6));
+    TraceSpan sw("census_c4_warp", s);
     k_c4_warp<<<wblocks, C4_WARPS * 32, 0, s>>>(g->view(), G.per, g->c4_warp_ub, G.agg);
     HM_KCHECK();
+    sw.end();
     const uint64_t nk = g->C4.total;
     if (nk) {
-      k_c4_emit<<<wblocks, C4_WARPS * 32, 0, s>>>(g->view(), g->bits, g->C4.ws, G.c4_keys);
+      const uint64_t eb = std::min<uint64_t>(((uint64_t)g->n + C4E_THREADS - 1) / C4E_THREADS,
+                                             152 * 4);
+      TraceSpan se("census_c4_emit", s);
+      k_c4_emit<<<(unsigned)std::max<uint64_t>(1, eb), C4E_THREADS, 0, s>>>(g->view(), g->bits,
+                                                                           g->C4.ws, G.c4_keys);
       HM_KCHECK();
+      se.end();
+      TraceSpan ss("census_c4_sort", s);
       radix_sort_u64(G.c4_keys, nullptr, (int64_t)nk, 2 * g->bits, s);
+      ss.end();
       const uint64_t rb = std::min<uint64_t>((nk + 255) / 256, 152 * 8);
+      TraceSpan sr("census_c4_runs", s);
       k_c4_runs<<<(unsigned)rb, 256, 0, s>>>(G.c4_keys, nk, g->bits, G.per, G.agg);
       HM_KCHECK();
+      sr.end();
     }
-    span.end();
     return;
   }
+  TraceSpan span("census_gl_pairs", s);
   k_graphlet_pairs<<<grid_n((uint64_t)g->n * 32), 256, 0, s>>>(g->view(), G.per, G.agg);
   HM_KCHECK();
   span.end();

@@ -2,6 +2,8 @@
 // sort (8-bit digits, warp-match ranking), unique, CSR offsets.
 #include <mutex>
 
+#include <atomic>
+
 #include "hm_internal.cuh"
 
 namespace hm {
@@ -177,7 +179,15 @@ ForkEvents& fork_events(int dev) {
 }
 }  // namespace
 
+// hm_serialize_launches: forked work runs in order on the parent stream
+std::atomic<bool> g_serial{false};
+
 Fork::Fork(cudaStream_t s, int w) : main(s), width(w < 1 ? 1 : w > kSide ? kSide : w) {
+  if (g_serial.load(std::memory_order_relaxed)) {
+    for (int i = 0; i < kSide; ++i) side[i] = main;
+    width = 0;
+    return;
+  }
   int dev = 0;
   HM_CUDA(cudaGetDevice(&dev));
   HM_CHECK(dev >= 0 && dev < 64, HM_ECUDA, "device ordinal above 63");
@@ -245,3 +255,8 @@ void csr_offsets(const uint64_t* keys, int64_t n, int shift, int32_t num_nodes, 
 }
 
 }  // namespace hm
+
+extern "C" hm_status hm_serialize_launches(int on) {
+  hm::g_serial.store(on != 0);
+  return HM_OK;
+}
