@@ -621,17 +621,63 @@ def measure_sampler(hm, stream, scale=0.004,
 NULL_BASES = (50_000, 69_000, 97_000, 134_000, 186_000, 259_000, 360_000, 500_000)
 
 
-def measure_null(hm, stream, hyperedges=NULL_BASES, models=8):
+def measure_profiles(hm, stream, cases=(("f2f-330", 1.0, (100, 250, 500, 1000)),
+                                        ("coauth-1m", 0.1, (1000, 2500, 5000, 10000))),
+                     models=10, seeds=10):
+    """Table 3's accuracy measures on the GPU: the significance profile of
+    sampled estimates (Alg. 4, default budget split) against the profile of
+    the exact counts, both against `models` stub-shuffled null models counted
+    exactly; rho, MaxAE and MAE averaged over `seeds` repetitions, with the
+    sampler's GPU time. Face-to-face-shaped (hs / ps) and co-authorship-shaped
+    (dblp / history / geology) workloads, with the paper's sample sizes for
+    each kind."""
+    import numpy as np
+    from paper_2209_10241_gb300 import synth
+    k = 4
+    out = {}
+    for name, scale, budgets in cases:
+        h = synth.workload(name, seed=0, scale=scale)
+        g = hm.from_host(h, 4)
+        hm.count_exact(g, k)  # first call: work spaces and schedules
+        exact_ms, T = _event_ms(lambda: hm.count_exact(g, k), stream)
+        null_ms, rows = _event_ms(lambda: hm.null_batch([h], k, models, seed=1), stream)
+        sp, _ = hm.significance_profile(T, rows)
+        recs = []
+        for S in budgets:
+            ms, r = [], []
+            for seed in range(seeds):
+                t, (est, _) = _event_ms(lambda: hm.count_sampled(g, k, total=S, seed=seed),
+                                        stream)
+                sp_hat, _ = hm.significance_profile(est, rows)
+                r.append(hm.profile_compare(sp_hat, sp).cpu().numpy())
+                ms.append(t)
+            r = np.array(r)
+            recs.append({"S": S, "gpu_ms": float(np.median(ms)), "rho": float(r[:, 0].mean()),
+                         "maxae": float(r[:, 1].mean()), "mae": float(r[:, 2].mean())})
+        out[f"{name}@{scale}"] = {"nodes": h.num_nodes, "hyperedges": h.num_hyperedges,
+                                  "null_models": models, "exact_census_ms": exact_ms,
+                                  "null_batch_ms": null_ms, "by_budget": recs}
+    return out
+
+
+def measure_null(hm, stream, hyperedges=NULL_BASES, models=8, sweeps=10):
     """Null-model batch: len(hyperedges) face-to-face-shaped bases x `models`
-    stub shuffles counted at order 4 (64 uneven graphs, one union per 64)."""
+    randomised copies counted at order 4 (64 uneven graphs, one union per 64):
+    stub shuffles, and configuration-model draws by `sweeps` rounds of
+    pairwise reshuffles."""
     from paper_2209_10241_gb300 import synth
     bases = [synth.null_base(H, seed=100 + i) for i, H in enumerate(hyperedges)]
     hm.null_batch(bases[:1], 4, 1, seed=1)  # warm-up
     ms, out = _event_ms(lambda: hm.null_batch(bases, 4, models, seed=1), stream)
     sets = int(out.sum().item())
+    hm.null_batch(bases[:1], 4, 1, seed=1, sweeps=sweeps)  # warm-up
+    mms, mout = _event_ms(lambda: hm.null_batch(bases, 4, models, seed=1, sweeps=sweeps), stream)
+    msets = int(mout.sum().item())
     return {"bases": [b.num_hyperedges for b in bases], "nodes": [b.num_nodes for b in bases],
             "models": len(bases) * models, "ms": ms, "sets": sets,
-            "sets_per_s": sets / (ms / 1e3)}
+            "sets_per_s": sets / (ms / 1e3),
+            "configuration_model": {"sweeps": sweeps, "ms": mms, "sets": msets,
+                                    "sets_per_s": msets / (mms / 1e3)}}
 
 
 def measure_sampler_full(hm, stream, budgets=(100_000, 1_000_000, 10_000_000), seeds=5,
@@ -779,7 +825,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the face-to-face, sampler and null-batch rows")
-    ap.add_argument("--only", choices=["sampler", "null", "large", "sampler-full", "f2f"],
+    ap.add_argument("--only", choices=["sampler", "null", "large", "sampler-full", "f2f",
+                                       "profiles"],
                     default=None, help="run one of the extra measurements alone (for profiling)")
     ap.add_argument("--large", default="comm-5m",
                     help="workload of --only large (comm-5m or coauth-1m)")
@@ -811,6 +858,8 @@ def main():
             res = measure_null(hm, stream, hyperedges=NULL_BASES[:args.null_bases])
         elif args.only == "sampler-full":
             res = measure_sampler_full(hm, stream)
+        elif args.only == "profiles":
+            res = measure_profiles(hm, stream)
         elif args.only == "f2f":
             res = small_exact_row(hm, stream, flush, args.order, args.steps, args.warmup)
         else:
@@ -871,6 +920,7 @@ def main():
             line["f2f_330"] = small_exact_row(hm, stream, flush, args.order)
         line["sampler"] = measure_sampler(hm, stream)
         line["null_batch"] = measure_null(hm, stream, hyperedges=NULL_BASES[:args.null_bases])
+        line["profiles"] = measure_profiles(hm, stream)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(h, args.order, args.workload)
         if not args.no_extras:

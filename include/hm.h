@@ -379,6 +379,89 @@ hm_status hm_count_null_batch(int num_bases, const int32_t* d_members, const int
                               int models_per_base, uint64_t seed, uint64_t* d_hists,
                               void* stream);
 
+/* ---------------------------------------------------------------- motif profiles
+ * Sec. 6.3 judges estimated counts by the motif profiles they give against a
+ * configuration-model null, next to the profiles of the exact counts (rho,
+ * MaxAE and MAE, Table 3). The profile is the one of the prior work the
+ * paper cites: for class c, with N_c the observed count and <N_c> its mean
+ * over the null models,
+ *   D_c  = (N_c - <N_c>) / (N_c + <N_c> + eps)      (eps = 4 there),
+ *   SP_c = D_c / sqrt(sum_k D_k^2)                  (zeros when D = 0).
+ * All arithmetic is IEEE double with sums in a fixed order (reproducible).
+ */
+
+/*
+ * Significance profile of one hypergraph.
+ *   d_observed   device double[num_classes]: observed counts (exact counts
+ *                through hm_counts_to_double, or hm_count_sampled estimates)
+ *   d_null_rows  device uint64[num_models * num_classes]: the null models'
+ *                exact counts, row t = model t (hm_count_null_batch layout)
+ *   d_profile    device double[num_classes]: SP, overwritten
+ *   d_abundance  device double[num_classes] or NULL: D, overwritten
+ * Enqueued on `stream`. HM_EINVAL on sizes < 1, NULL buffers or eps < 0.
+ */
+hm_status hm_significance_profile(int num_classes, const double* d_observed,
+                                  const uint64_t* d_null_rows, int num_models, double eps,
+                                  double* d_profile, double* d_abundance, void* stream);
+
+/*
+ * Agreement of an estimated profile p with the exact one q (Table 3):
+ * d_out (device double[3]) = {Pearson's rho of p and q (0 when either is
+ * constant), max_c |p_c - q_c| (MaxAE), mean_c |p_c - q_c| (MAE)}. Enqueued
+ * on `stream`.
+ */
+hm_status hm_profile_compare(int num_classes, const double* d_estimated, const double* d_exact,
+                             double* d_out, void* stream);
+
+/* d_out[i] = (double)d_counts[i] for i < n (exact below 2^53); enqueued. */
+hm_status hm_counts_to_double(const uint64_t* d_counts, int64_t n, double* d_out, void* stream);
+
+/* ---------------------------------------------------------------- configuration model
+ * The null model Sec. 6.3 samples is Chodrow's configuration model of
+ * hypergraphs. It is sampled here by its pairwise-reshuffle Markov chain: two
+ * hyperedges e, f keep their intersection and deal the rest of their
+ * members out again at random, |e| - |e n f| to e and the remainder to f.
+ * Degrees and sizes are kept, no hyperedge gets a repeated member, and the
+ * move is symmetric, so the stationary distribution is uniform over the
+ * hyperedge-labelled hypergraphs with those degrees and sizes (duplicate
+ * hyperedges allowed; the census collapses them, as for any input).
+ * Round r of `sweeps` pairs the hyperedges of a model by a random matching:
+ * hyperedge i gets the key v >> 6, v the 64-bit Philox4x32-10 value of key =
+ * seed and counter ((r << 32) | i, model << 8, 0x4D434D43), the hyperedges
+ * are sorted by (key, i) and positions 2k, 2k + 1 form pair k (an odd one
+ * out stays). In pair k, S = e's members outside f (in order), then f's
+ * outside e; step q of a partial Fisher-Yates shuffle (q < |e \ f| and
+ * q < |S| - 1) swaps S[q] with S[q + mulhi64(v_q, |S| - q)], v_q the value of
+ * counter ((r << 32) | k, (model << 8) | (q + 1), 0x4D434D43), and S returns
+ * to the same slots in order (e's first). Pairs with |S| > 255, |S| < 2 or S
+ * within one of them stay as they are. Every pair of a round moves at once
+ * (disjoint moves commute). Hyperedges must not repeat a member (HM_EINVAL).
+ */
+
+/*
+ * One configuration-model draw: d_out (device int32[d_offsets[m]]) gets the
+ * members of model `model` (< 2^24) after `sweeps` rounds started from the
+ * input (offsets unchanged). Synchronous. Errors: HM_EINVAL (bad sizes, a
+ * member outside [0, num_nodes), a repeated member), HM_ENOMEM, HM_ECUDA.
+ */
+hm_status hm_configuration_model(const int32_t* d_members, const int64_t* d_offsets,
+                                 int64_t num_hyperedges, int32_t num_nodes, uint32_t model,
+                                 int sweeps, uint64_t seed, int32_t* d_out, void* stream);
+
+/*
+ * hm_count_null_batch with configuration-model draws instead of stub
+ * shuffles: model t = b * models_per_base + j starts from base b and takes
+ * `sweeps` rounds of pairwise reshuffles (as hm_configuration_model with
+ * model = t), then is counted at `order` as by hm_count_exact. The models of
+ * a 64-model group are reshuffled together, each round one sort and one
+ * launch for the group. Same layout and errors as hm_count_null_batch, plus
+ * HM_EINVAL for a repeated member or 2^24 models or more.
+ */
+hm_status hm_count_null_batch_mcmc(int num_bases, const int32_t* d_members,
+                                   const int64_t* d_offsets, const int64_t* h_base_edges,
+                                   const int32_t* h_num_nodes, int order, int models_per_base,
+                                   int sweeps, uint64_t seed, uint64_t* d_hists, void* stream);
+
 /*
  * hm_count_sampled without any device allocation (the paper has no
  * counterpart). It serves callers that cannot allocate device memory while

@@ -62,6 +62,7 @@ def lib():
             "orc_sample_indices": (None, [vp, ctypes.c_int, u64, u64, vp, vp]),
             "orc_sample": (i64, [vp, ctypes.c_int, vp, u64, vp, vp, vp]),
             "orc_stub_shuffle": (None, [vp, vp, i64, u64, u32, vp]),
+            "orc_config_mcmc": (None, [vp, vp, i64, u64, u32, ctypes.c_int, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -185,4 +186,13 @@ def stub_shuffle(members, offsets, seed: int, model: int) -> np.ndarray:
     off = np.ascontiguousarray(offsets, dtype=np.int64)
     out = np.zeros_like(mem)
     lib().orc_stub_shuffle(_ptr(mem), _ptr(off), off.shape[0] - 1, seed, model, _ptr(out))
+    return out
+
+
+def config_mcmc(members, offsets, seed: int, model: int, sweeps: int) -> np.ndarray:
+    """Configuration-model draw by pairwise reshuffles (see orc_config_mcmc)."""
+    mem = np.ascontiguousarray(members, dtype=np.int32)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    out = np.zeros_like(mem)
+    lib().orc_config_mcmc(_ptr(mem), _ptr(off), off.shape[0] - 1, seed, model, sweeps, _ptr(out))
     return out

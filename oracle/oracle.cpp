@@ -619,4 +619,61 @@ void orc_stub_shuffle(const int32_t* members, const int64_t* offsets, int64_t m,
   for (int64_t i = 0; i < M; ++i) out_members[i] = members[key[i].second];
 }
 
+// Configuration model of hypergraphs (the null model Sec. 6.3 cites, by
+// Chodrow), sampled by its pairwise-reshuffle Markov chain: two hyperedges e,
+// f keep their intersection and deal the remaining members of both out again
+// at random, |e| - |e n f| to e and the rest to f, which keeps every degree
+// and size. Round r (of `sweeps`) pairs the hyperedges by a random matching:
+// hyperedge i gets the key draw64(seed, (r << 32) | i, model << 8, TAG_MCMC)
+// >> 6, the hyperedges are sorted by (key, i), and positions 2k and 2k + 1
+// form pair k (an odd one out stays). In pair k the re-dealt members are S =
+// e's members outside f (in order) then f's outside e, with their slots;
+// Fisher-Yates steps q = 0, 1, ... while q < |e \ f| and q < |S| - 1 swap S[q]
+// with S[q + mulhi64(draw64(seed, (r << 32) | k, (model << 8) | (q + 1),
+// TAG_MCMC), |S| - q)], and S goes back to the slots in order. Pairs whose S
+// has more than 255 members, fewer than 2, or lies wholly in e or in f stay
+// as they are. out_members has offsets[m] entries; the offsets stay the same.
+void orc_config_mcmc(const int32_t* members, const int64_t* offsets, int64_t m, uint64_t seed,
+                     uint32_t model, int sweeps, int32_t* out_members) {
+  const uint32_t TAG_MCMC = 0x4D434D43u;  // "MCMC"
+  const int64_t M = offsets[m];
+  for (int64_t i = 0; i < M; ++i) out_members[i] = members[i];
+  for (int r = 0; r < sweeps; ++r) {
+    std::vector<std::pair<uint64_t, int64_t>> key(m);
+    for (int64_t i = 0; i < m; ++i)
+      key[i] = {draw64(seed, ((uint64_t)r << 32) | (uint64_t)i, model << 8, TAG_MCMC) >> 6, i};
+    std::sort(key.begin(), key.end());
+    for (int64_t k = 0; 2 * k + 1 < m; ++k) {
+      const int64_t e = key[2 * k].second, f = key[2 * k + 1].second;
+      std::vector<int32_t> S;
+      std::vector<int64_t> slot;
+      auto in = [&](int64_t h, int32_t v) {
+        for (int64_t j = offsets[h]; j < offsets[h + 1]; ++j)
+          if (out_members[j] == v) return true;
+        return false;
+      };
+      for (int64_t j = offsets[e]; j < offsets[e + 1]; ++j)
+        if (!in(f, out_members[j])) {
+          S.push_back(out_members[j]);
+          slot.push_back(j);
+        }
+      const int ae = (int)S.size();
+      for (int64_t j = offsets[f]; j < offsets[f + 1]; ++j)
+        if (!in(e, out_members[j])) {
+          S.push_back(out_members[j]);
+          slot.push_back(j);
+        }
+      const int ns = (int)S.size();
+      if (ns > 255 || ns < 2 || ae == 0 || ae == ns) continue;
+      for (int q = 0; q < ae && q < ns - 1; ++q) {
+        const uint64_t v =
+            draw64(seed, ((uint64_t)r << 32) | (uint64_t)k, (model << 8) | (uint32_t)(q + 1), TAG_MCMC);
+        const int j = q + (int)mulhi64(v, (uint64_t)(ns - q));
+        std::swap(S[q], S[j]);
+      }
+      for (int q = 0; q < ns; ++q) out_members[slot[q]] = S[q];
+    }
+  }
+}
+
 }  // extern "C"

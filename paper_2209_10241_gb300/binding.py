@@ -44,6 +44,12 @@ _SIGS = {
                                                 ctypes.c_uint64, _vp, _vp, _vp, _vp]),
     "hm_count_null_batch": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int,
                                            ctypes.c_int, ctypes.c_uint64, _vp, _vp]),
+    "hm_count_null_batch_mcmc": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                                _vp, _vp]),
+    "hm_configuration_model": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32,
+                                              ctypes.c_uint32, ctypes.c_int, ctypes.c_uint64,
+                                              _vp, _vp]),
     "hm_contributions": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "hm_features": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "hm_mlp_num_params": (ctypes.c_int, []),
@@ -72,6 +78,10 @@ _SIGS = {
     "hm_launch_count": (ctypes.c_uint64, []),
     "hm_selftest_wait": (ctypes.c_int, [_vp]),
     "hm_serialize_launches": (ctypes.c_int, [ctypes.c_int]),
+    "hm_significance_profile": (ctypes.c_int, [ctypes.c_int, _vp, _vp, ctypes.c_int,
+                                               ctypes.c_double, _vp, _vp, _vp]),
+    "hm_profile_compare": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _vp, _vp]),
+    "hm_counts_to_double": (ctypes.c_int, [_vp, ctypes.c_int64, _vp, _vp]),
     "hm_trace_read": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.c_int, _vp, _vp]),
     "hm_free": (None, [_vp]),
 }
@@ -233,9 +243,12 @@ def count_sampled_noalloc(g: Graph, order: int, est: torch.Tensor, raw: torch.Te
     return est, raw
 
 
-def null_batch(bases, order: int, models_per_base: int, seed: int, stream=None) -> torch.Tensor:
-    """hm_count_null_batch over host hypergraphs (synth.Hypergraph); returns an
-    int64 device tensor [len(bases) * models_per_base, ncls] of uint64 counts."""
+def null_batch(bases, order: int, models_per_base: int, seed: int, stream=None,
+               sweeps: int = None) -> torch.Tensor:
+    """hm_count_null_batch (stub shuffling), or hm_count_null_batch_mcmc when
+    `sweeps` is given (the configuration model by pairwise reshuffles), over
+    host hypergraphs (synth.Hypergraph); returns an int64 device tensor
+    [len(bases) * models_per_base, ncls] of uint64 counts."""
     import numpy as np
     mem = np.concatenate([b.members for b in bases]) if bases else np.zeros(0, np.int32)
     offs, edges, shift = [np.zeros(1, np.int64)], [0], 0
@@ -250,9 +263,26 @@ def null_batch(bases, order: int, models_per_base: int, seed: int, stream=None) 
     hn = (ctypes.c_int32 * len(bases))(*[b.num_nodes for b in bases])
     nc = num_classes(order)
     out = torch.empty((len(bases) * models_per_base, max(1, nc)), dtype=torch.int64, device="cuda")
-    _check(load().hm_count_null_batch(len(bases), _dptr(dmem), _dptr(doff), hedges, hn, order,
-                                      models_per_base, int(seed) & (2**64 - 1), _dptr(out),
-                                      _stream(stream)))
+    if sweeps is None:
+        _check(load().hm_count_null_batch(len(bases), _dptr(dmem), _dptr(doff), hedges, hn,
+                                          order, models_per_base, int(seed) & (2**64 - 1),
+                                          _dptr(out), _stream(stream)))
+    else:
+        _check(load().hm_count_null_batch_mcmc(len(bases), _dptr(dmem), _dptr(doff), hedges, hn,
+                                               order, models_per_base, int(sweeps),
+                                               int(seed) & (2**64 - 1), _dptr(out),
+                                               _stream(stream)))
+    return out
+
+
+def configuration_model(members: torch.Tensor, offsets: torch.Tensor, num_nodes: int,
+                        model: int, sweeps: int, seed: int, stream=None) -> torch.Tensor:
+    """hm_configuration_model: one draw's members (int32 device tensor, the
+    offsets stay those of the input)."""
+    out = torch.empty_like(members)
+    _check(load().hm_configuration_model(_dptr(members), _dptr(offsets), offsets.numel() - 1,
+                                         int(num_nodes), int(model), int(sweeps),
+                                         int(seed) & (2**64 - 1), _dptr(out), _stream(stream)))
     return out
 
 
@@ -448,3 +478,34 @@ def proposal_q(p: Proposal, g: Graph, lam: float = 0.1, beta: float = 0.0,
     _check(load().hm_proposal_weights(p._h, g._h, float(lam), float(beta), _dptr(q),
                                       _stream(stream)))
     return q
+
+
+def counts_to_double(counts: torch.Tensor, stream=None) -> torch.Tensor:
+    """hm_counts_to_double on a device tensor of uint64 counts (held as int64)."""
+    out = torch.empty(counts.numel(), dtype=torch.float64, device="cuda")
+    _check(load().hm_counts_to_double(_dptr(counts), counts.numel(), _dptr(out),
+                                      _stream(stream)))
+    return out
+
+
+def significance_profile(observed: torch.Tensor, null_rows: torch.Tensor, eps: float = 4.0,
+                         stream=None):
+    """hm_significance_profile: (profile, abundance) float64 device tensors.
+    observed: float64 [C] (or int64 counts, converted on the device);
+    null_rows: int64 [M, C] holding uint64 counts."""
+    if observed.dtype != torch.float64:
+        observed = counts_to_double(observed, stream)
+    M, C = null_rows.shape
+    prof = torch.empty(C, dtype=torch.float64, device="cuda")
+    ab = torch.empty(C, dtype=torch.float64, device="cuda")
+    _check(load().hm_significance_profile(int(C), _dptr(observed), _dptr(null_rows), int(M),
+                                          float(eps), _dptr(prof), _dptr(ab), _stream(stream)))
+    return prof, ab
+
+
+def profile_compare(estimated: torch.Tensor, exact: torch.Tensor, stream=None) -> torch.Tensor:
+    """hm_profile_compare: float64 device tensor (rho, MaxAE, MAE)."""
+    out = torch.empty(3, dtype=torch.float64, device="cuda")
+    _check(load().hm_profile_compare(int(exact.numel()), _dptr(estimated), _dptr(exact),
+                                     _dptr(out), _stream(stream)))
+    return out
