@@ -53,9 +53,10 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # So `frac` is the method's per-candidate byte demand served per second, and
 # can exceed the copy bandwidth; the DRAM bytes the kernel really moved are
 # `traffic` (ncu, one capture of the same workload).
-# kernel -> (unit, bytes per unit, work_totals key, DRAM bytes per launch or None)
+# kernel -> (unit, bytes per unit, work_totals key, DRAM bytes per launch from
+# one ncu capture of the headline workload, or None)
 ROOFLINE_HBM = {
-    "census_TX": ("TX candidate", 288, "census_TX", None),
+    "census_TX": ("TX candidate", 288, "census_TX", 504_759_552 + 14_063_104),
     "census_Q": ("4-hyperedge", 320, "census_Q", None),
 }
 
