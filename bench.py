@@ -622,6 +622,47 @@ def measure_sampler(hm, stream, scale=0.004,
 NULL_BASES = (50_000, 69_000, 97_000, 134_000, 186_000, 259_000, 360_000, 500_000)
 
 
+def measure_baseline(hm, stream, cases=(("f2f-330", 1.0, (3, 4)), ("coauth-1m", 0.01, (3, 4)),
+                                        ("coauth-1m", 1.0, (3,)))):
+    """Table 2 on the GPU: the exact census by the efficient path (hm_build +
+    hm_count_exact, "Eff") against Alg. 1 (projection + enumeration of its
+    connected k-node subgraphs + fill-in, hm_count_exact_baseline, "Base"),
+    both from the resident hyperedge list, event-timed once each (Eff after
+    one untimed run on the same graph, which tunes its schedules; Base after a
+    warm-up on a small graph). Full-size co-authorship at order 4 is left out:
+    its projection has ~4.5e13 connected 4-node subgraphs."""
+    import torch
+    from paper_2209_10241_gb300 import synth
+    small = synth.workload("uniform-200")
+    sm, so = torch.from_numpy(small.members).cuda(), torch.from_numpy(small.offsets).cuda()
+    for k in (3, 4):
+        hm.count_exact_baseline(sm, so, small.num_nodes, k)
+        hm.count_exact(hm.build(sm, so, small.num_nodes, k), k)
+    out = {}
+    for name, scale, orders in cases:
+        h = synth.workload(name, seed=0, scale=scale)
+        mem = torch.from_numpy(h.members).cuda()
+        off = torch.from_numpy(h.offsets).cuda()
+        rec = {"nodes": h.num_nodes, "hyperedges": h.num_hyperedges}
+        for k in orders:
+            def eff():
+                g = hm.build(mem, off, h.num_nodes, k)
+                r = hm.count_exact(g, k)
+                return g, r
+            g, _ = eff()  # the shape's work spaces and schedules, once
+            g.free()
+            eff_ms, (g, he) = _event_ms(eff, stream)
+            g.free()
+            base_ms, (hb, cand, npairs) = _event_ms(
+                lambda: hm.count_exact_baseline(mem, off, h.num_nodes, k), stream)
+            assert torch.equal(he, hb)
+            rec[f"order{k}"] = {"eff_ms": eff_ms, "base_ms": base_ms, "sets": int(he.sum().item()),
+                                "base_candidates": cand, "projection_pairs": npairs,
+                                "base_over_eff": base_ms / eff_ms}
+        out[f"{name}@{scale}"] = rec
+    return out
+
+
 def measure_profiles(hm, stream, cases=(("f2f-330", 1.0, (100, 250, 500, 1000)),
                                         ("coauth-1m", 0.1, (1000, 2500, 5000, 10000))),
                      models=10, seeds=10):
@@ -827,7 +868,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the face-to-face, sampler and null-batch rows")
     ap.add_argument("--only", choices=["sampler", "null", "large", "sampler-full", "f2f",
-                                       "profiles"],
+                                       "profiles", "baseline"],
                     default=None, help="run one of the extra measurements alone (for profiling)")
     ap.add_argument("--large", default="comm-5m",
                     help="workload of --only large (comm-5m or coauth-1m)")
@@ -859,6 +900,8 @@ def main():
             res = measure_null(hm, stream, hyperedges=NULL_BASES[:args.null_bases])
         elif args.only == "sampler-full":
             res = measure_sampler_full(hm, stream)
+        elif args.only == "baseline":
+            res = measure_baseline(hm, stream)
         elif args.only == "profiles":
             res = measure_profiles(hm, stream)
         elif args.only == "f2f":
@@ -922,6 +965,7 @@ def main():
         line["sampler"] = measure_sampler(hm, stream)
         line["null_batch"] = measure_null(hm, stream, hyperedges=NULL_BASES[:args.null_bases])
         line["profiles"] = measure_profiles(hm, stream)
+        line["baseline"] = measure_baseline(hm, stream)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(h, args.order, args.workload)
         if not args.no_extras:

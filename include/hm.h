@@ -188,6 +188,28 @@ hm_status hm_count_exact_host(const int32_t* h_members, const int64_t* h_offsets
                               uint64_t* h_hist, void* stream);
 
 /*
+ * The baseline of Sec. 4.1 (Alg. 1), for comparison with hm_count_exact
+ * (Table 2): the hypergraph is projected onto a graph (two nodes joined when
+ * they share a hyperedge of ANY size), every connected `order`-node subgraph
+ * of the projection is enumerated once (wedges and triangles; stars, paths
+ * and 4-cycles, by the canonical rules of simple graphs), filled in against
+ * the hypergraph (Sec. 4.3) and counted by class when the sub-hypergraph it
+ * induces is connected (Fig. 2 shows why it may not be). d_hist equals
+ * hm_count_exact's; the extra work is the point of the comparison.
+ *   d_members, d_offsets  as for hm_build (device)
+ *   d_hist                device uint64[hm_num_classes(order)], overwritten
+ *   h_info                host uint64[2] or NULL: {candidate sets generated
+ *                         (sum_v C(d(v), 2) for order 3, sum_v C(d(v), 3) +
+ *                         sum_{uv} (d(u) - 1)(d(v) - 1) for order 4, d the
+ *                         projection degree), distinct projection pairs}
+ * Builds the hypergraph and the projection inside the call, synchronous.
+ * Errors as hm_build; HM_EINVAL if the projection has 2^31 pairs or more.
+ */
+hm_status hm_count_exact_baseline(const int32_t* d_members, const int64_t* d_offsets,
+                                  int64_t num_hyperedges, int32_t num_nodes, int order,
+                                  uint64_t* d_hist, uint64_t* h_info, void* stream);
+
+/*
  * Kernel timing trace (no counterpart in the paper; instrumentation). While
  * enabled, every census kernel launch, and each phase of hm_build's ingest
  * (entries named "ingest_*", several launches each), is bracketed by CUDA

@@ -73,6 +73,8 @@ _SIGS = {
     "hm_count_exact_host": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int,
                                            _vp, _vp]),
     "hm_work_totals": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "hm_count_exact_baseline": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32,
+                                               ctypes.c_int, _vp, _vp, _vp]),
     "hm_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "hm_trace_only": (ctypes.c_int, [ctypes.c_char_p]),
     "hm_launch_count": (ctypes.c_uint64, []),
@@ -509,3 +511,16 @@ def profile_compare(estimated: torch.Tensor, exact: torch.Tensor, stream=None) -
     _check(load().hm_profile_compare(int(exact.numel()), _dptr(estimated), _dptr(exact),
                                      _dptr(out), _stream(stream)))
     return out
+
+
+def count_exact_baseline(members: torch.Tensor, offsets: torch.Tensor, num_nodes: int,
+                         order: int, stream=None):
+    """hm_count_exact_baseline (Alg. 1 on the GPU): (hist int64 device tensor,
+    candidates generated, distinct projection pairs)."""
+    nc = num_classes(order)
+    out = torch.empty(nc, dtype=torch.int64, device="cuda")
+    info = (ctypes.c_uint64 * 2)()
+    _check(load().hm_count_exact_baseline(_dptr(members), _dptr(offsets), offsets.numel() - 1,
+                                          int(num_nodes), int(order), _dptr(out), info,
+                                          _stream(stream)))
+    return out, int(info[0]), int(info[1])

@@ -38,6 +38,7 @@
 #include <mutex>
 #include <string>
 
+#include "baseline.cuh"
 #include "families.cuh"
 
 namespace hm {
@@ -1044,6 +1045,23 @@ void launch_census(const hm_graph* g, int order, unsigned long long* hist, cudaS
       launch_one(g, 'P', g->usePb, pick(g->chunkP), 4, hist, s);
     }
   }
+}
+
+// Alg. 1 on the projection graph p, with fill-in against the hypergraph h:
+// the connected k-sets of p (wedges and triangles for k = 3; stars, paths and
+// 4-cycles for k = 4), each counted by the class of the sub-hypergraph of h it
+// induces when that is connected. Returns the candidates generated.
+uint64_t launch_baseline(hm_graph* p, const hm_graph* h, int order, unsigned long long* hist,
+                         cudaStream_t s) {
+  if (order == 3) {
+    ensure_spaces(p, {{&p->W, 'W'}}, s);
+    launch_family(p, base::BaseW{h->view()}, &p->W, p->W.total, 3, hist, s);
+    return p->W.total;
+  }
+  ensure_spaces(p, {{&p->S, 'S'}, {&p->P, 'P'}}, s);
+  launch_family(p, base::BaseS{h->view()}, &p->S, p->S.total, 4, hist, s);
+  launch_family(p, base::BaseP{h->view()}, &p->P, p->P.total, 4, hist, s);
+  return p->S.total + p->P.total;
 }
 
 // ------------------------------------------------------------------ autotuner
