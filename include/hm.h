@@ -401,6 +401,40 @@ hm_status hm_count_null_batch(int num_bases, const int32_t* d_members, const int
                               int models_per_base, uint64_t seed, uint64_t* d_hists,
                               void* stream);
 
+/* ---------------------------------------------------------------- order 5
+ * Alg. 4 at order 5 (Sec. 6.4). A 5-node pattern is a 26-bit mask over the
+ * subsets of its five sorted positions with 2..5 members, by size and then
+ * lexicographically: bits 0-9 {01,02,03,04,12,13,14,23,24,34}, bits 10-19
+ * the triples {012,...,234}, bits 20-24 the quads {0123,...,1234}, bit 25
+ * {01234}. A class is its canonical mask: the minimum over the 120
+ * relabelings (Def. 3); there is no class table.
+ *
+ * Draw t of stratum s (s = 2..5) is hyperedge mulhi64(v, |E_s|) of E_s
+ * (distinct hyperedges with s distinct members, ascending), v the 64-bit
+ * Philox4x32-10 value of key = seed, counter (t lo, t hi, s, 0x53414D50). The
+ * sets counted for it are the 5-node V' containing it whose H[V'] is
+ * connected and whose largest hyperedges have s members; n_c counts them
+ * over all draws, and the estimate of class c is
+ * (n_c * |E_m|) / (S_m * countmax_c) in IEEE double in this order, m and
+ * countmax_c the size and number of c's largest hyperedges.
+ *   samples_per_size  host uint64[6], entry s = S_s (s = 2..5); NULL: split
+ *                     total_samples as S_2 = floor(S/8), S_3 = floor(3S/8),
+ *                     S_4 = floor(S/4), S_5 = S - S_2 - S_3 - S_4
+ *   d_masks, d_raw, d_est  device uint32 / uint64 / double[capacity]: the
+ *                     classes met, ascending by canonical mask (the first
+ *                     `capacity` of them), with n_c and the estimate
+ *   *h_num_classes    the number of classes met (may exceed capacity)
+ * Builds its structures from the hyperedge list inside the call (uniform
+ * draws only), uses a 512 MiB histogram, synchronous. Errors: HM_EINVAL (bad
+ * sizes, a stratum with |E_s| > 0 and S_s == 0), HM_EUNSUPPORTED (node ids of
+ * 2^25 or more), HM_ENOMEM, HM_ECUDA.
+ */
+hm_status hm_count_sampled5(const int32_t* d_members, const int64_t* d_offsets,
+                            int64_t num_hyperedges, int32_t num_nodes,
+                            const uint64_t* samples_per_size, uint64_t total_samples,
+                            uint64_t seed, uint32_t* d_masks, uint64_t* d_raw, double* d_est,
+                            int64_t capacity, int64_t* h_num_classes, void* stream);
+
 /* ---------------------------------------------------------------- motif profiles
  * Sec. 6.3 judges estimated counts by the motif profiles they give against a
  * configuration-model null, next to the profiles of the exact counts (rho,

@@ -63,6 +63,10 @@ def lib():
             "orc_sample": (i64, [vp, ctypes.c_int, vp, u64, vp, vp, vp]),
             "orc_stub_shuffle": (None, [vp, vp, i64, u64, u32, vp]),
             "orc_config_mcmc": (None, [vp, vp, i64, u64, u32, ctypes.c_int, vp]),
+            "orc_sample5": (i64, [vp, vp, i64, i32, vp, u64, i64, vp, vp, vp]),
+            "orc_sweep5": (i64, [vp, vp, i64, i32, i64, vp, vp]),
+            "orc_canonical5": (u32, [u32]),
+            "orc_connected5": (ctypes.c_int, [u32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -196,3 +200,39 @@ def config_mcmc(members, offsets, seed: int, model: int, sweeps: int) -> np.ndar
     out = np.zeros_like(mem)
     lib().orc_config_mcmc(_ptr(mem), _ptr(off), off.shape[0] - 1, seed, model, sweeps, _ptr(out))
     return out
+
+
+def sample5(members, offsets, num_nodes: int, samples, seed: int, cap: int = 1 << 20):
+    """Alg. 4 at order 5 (see orc_sample5): (canonical masks, raw counts, estimates)."""
+    mem = np.ascontiguousarray(members, dtype=np.int32)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    S = np.zeros(6, dtype=np.uint64)
+    for s in range(2, 6):
+        S[s] = samples[s]
+    masks = np.zeros(cap, dtype=np.uint32)
+    raw = np.zeros(cap, dtype=np.uint64)
+    est = np.zeros(cap, dtype=np.float64)
+    nc = lib().orc_sample5(_ptr(mem), _ptr(off), off.shape[0] - 1, int(num_nodes), _ptr(S), seed,
+                           cap, _ptr(masks), _ptr(raw), _ptr(est))
+    nc = min(int(nc), cap)
+    return masks[:nc], raw[:nc], est[:nc]
+
+
+def sweep5(members, offsets, num_nodes: int, cap: int = 1 << 20):
+    """Every hyperedge once (see orc_sweep5): (canonical masks, sums)."""
+    mem = np.ascontiguousarray(members, dtype=np.int32)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    masks = np.zeros(cap, dtype=np.uint32)
+    sums = np.zeros(cap, dtype=np.uint64)
+    nc = lib().orc_sweep5(_ptr(mem), _ptr(off), off.shape[0] - 1, int(num_nodes), cap,
+                          _ptr(masks), _ptr(sums))
+    nc = min(int(nc), cap)
+    return masks[:nc], sums[:nc]
+
+
+def canonical5(mask: int) -> int:
+    return int(lib().orc_canonical5(mask))
+
+
+def connected5(mask: int) -> bool:
+    return bool(lib().orc_connected5(mask))

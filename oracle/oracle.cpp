@@ -39,6 +39,7 @@
 #include <atomic>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <set>
 #include <thread>
 #include <unordered_map>
@@ -676,4 +677,250 @@ void orc_config_mcmc(const int32_t* members, const int64_t* offsets, int64_t m, 
   }
 }
 
+
+// ---------------------------------------------------------------- order 5 (Sec. 6.4)
+// Alg. 4 at order 5. A 5-node pattern is a 26-bit mask over the subsets of
+// its 5 sorted positions with 2..5 members (by size, then lexicographic: bits
+// 0-9 pairs 01..34, 10-19 triples 012..234, 20-24 quads 0123..1234, 25 the
+// five). There is no class table: a class is its canonical mask, the minimum
+// over the 120 relabelings. For a drawn hyperedge e, the sets counted are the
+// 5-node V' containing e whose H[V'] is connected and whose largest
+// hyperedges have |e| members; every such V' is connected in the projection
+// of the hyperedges of size <= |e| (the only hyperedges inside it), so it can
+// be grown from e by adding projection neighbours one at a time, and the
+// oracle tries every set grown that way. Draw t of stratum s is hyperedge
+// mulhi64(draw64(seed, t, s, "SAMP"), |E_s|) of E_s (ascending tuples).
+namespace o5 {
+
+struct Sub5 {
+  uint32_t nodes[26];  // node bitmask of subset b
+  int size[26];
+  int index_of[32];    // node bitmask -> subset index, -1 for size < 2
+  std::vector<std::array<uint8_t, 26>> perm_map;  // per relabeling: b -> image subset
+};
+
+const Sub5& sub5() {
+  static Sub5 S = [] {
+    Sub5 t;
+    for (int i = 0; i < 32; ++i) t.index_of[i] = -1;
+    int b = 0;
+    // combinations of each size in lexicographic order
+    for (int sz = 2; sz <= 5; ++sz) {
+      std::vector<int> c(sz);
+      for (int i = 0; i < sz; ++i) c[i] = i;
+      while (true) {
+        uint32_t m = 0;
+        for (int i = 0; i < sz; ++i) m |= 1u << c[i];
+        t.nodes[b] = m;
+        t.size[b] = sz;
+        t.index_of[m] = b;
+        ++b;
+        int i = sz - 1;
+        while (i >= 0 && c[i] == 5 - sz + i) --i;
+        if (i < 0) break;
+        ++c[i];
+        for (int j = i + 1; j < sz; ++j) c[j] = c[j - 1] + 1;
+      }
+    }
+    int perm[5] = {0, 1, 2, 3, 4};
+    do {
+      std::array<uint8_t, 26> pm;
+      for (int q = 0; q < 26; ++q) {
+        uint32_t img = 0;
+        for (int i = 0; i < 5; ++i)
+          if ((t.nodes[q] >> i) & 1u) img |= 1u << perm[i];
+        pm[q] = (uint8_t)t.index_of[img];
+      }
+      t.perm_map.push_back(pm);
+    } while (std::next_permutation(perm, perm + 5));
+    return t;
+  }();
+  return S;
+}
+
+uint32_t canonical5(uint32_t mask) {
+  const Sub5& S = sub5();
+  uint32_t best = mask;
+  for (const auto& pm : S.perm_map) {
+    uint32_t r = 0;
+    for (int q = 0; q < 26; ++q)
+      if ((mask >> q) & 1u) r |= 1u << pm[q];
+    best = std::min(best, r);
+  }
+  return best;
+}
+
+bool connected5(uint32_t mask) {
+  const Sub5& S = sub5();
+  int parent[5] = {0, 1, 2, 3, 4};
+  auto find = [&](int x) {
+    while (parent[x] != x) x = parent[x];
+    return x;
+  };
+  for (int q = 0; q < 26; ++q) {
+    if (!((mask >> q) & 1u)) continue;
+    int first = -1;
+    for (int i = 0; i < 5; ++i) {
+      if (!((S.nodes[q] >> i) & 1u)) continue;
+      if (first < 0) first = i;
+      else parent[find(i)] = find(first);
+    }
+  }
+  const int r = find(0);
+  for (int i = 1; i < 5; ++i)
+    if (find(i) != r) return false;
+  return true;
+}
+
+// (largest hyperedge size, how many hyperedges of that size) of a mask
+void maxcard5(uint32_t mask, int* mc, int* cm) {
+  const Sub5& S = sub5();
+  *mc = 0;
+  *cm = 0;
+  for (int q = 0; q < 26; ++q) {
+    if (!((mask >> q) & 1u)) continue;
+    if (S.size[q] > *mc) {
+      *mc = S.size[q];
+      *cm = 1;
+    } else if (S.size[q] == *mc) {
+      ++*cm;
+    }
+  }
+}
+
+struct Graph5 {
+  int32_t n = 0;
+  std::vector<std::vector<int32_t>> E[6];  // distinct sorted hyperedges of size s, ascending
+  std::set<std::vector<int32_t>> all;      // every distinct hyperedge of size 2..5
+  std::vector<std::vector<int32_t>> adj[6];  // adj[s]: projection of sizes 2..s, sorted
+};
+
+Graph5 make_graph5(const int32_t* members, const int64_t* offsets, int64_t m, int32_t n) {
+  Graph5 g;
+  g.n = n;
+  std::set<std::vector<int32_t>> bysize[6];
+  for (int64_t j = 0; j < m; ++j) {
+    std::vector<int32_t> e(members + offsets[j], members + offsets[j + 1]);
+    std::sort(e.begin(), e.end());
+    e.erase(std::unique(e.begin(), e.end()), e.end());
+    if (e.size() < 2 || e.size() > 5) continue;
+    bysize[e.size()].insert(e);
+    g.all.insert(e);
+  }
+  for (int s = 2; s <= 5; ++s) g.E[s].assign(bysize[s].begin(), bysize[s].end());
+  for (int s = 2; s <= 5; ++s) {
+    std::vector<std::set<int32_t>> nb(n);
+    for (int t = 2; t <= s; ++t)
+      for (const auto& e : g.E[t])
+        for (int32_t a : e)
+          for (int32_t b : e)
+            if (a != b) nb[a].insert(b);
+    g.adj[s].resize(n);
+    for (int v = 0; v < n; ++v) g.adj[s][v].assign(nb[v].begin(), nb[v].end());
+  }
+  return g;
+}
+
+// mask of the 5-node set (sorted nodes v[0..4])
+uint32_t fill5(const Graph5& g, const int32_t* v) {
+  const Sub5& S = sub5();
+  uint32_t mask = 0;
+  for (int q = 0; q < 26; ++q) {
+    std::vector<int32_t> t;
+    for (int i = 0; i < 5; ++i)
+      if ((S.nodes[q] >> i) & 1u) t.push_back(v[i]);
+    if (g.all.count(t)) mask |= 1u << q;
+  }
+  return mask;
+}
+
+// every counted set through hyperedge e: adds 1 to counts[canonical mask].
+// The candidate 5-sets are grown from e one node at a time, each new node a
+// projection neighbour (sizes <= |e|) of the set so far; distinct sets are
+// kept at every size, so each candidate is tried once.
+void sets_through(const Graph5& g, const std::vector<int32_t>& e,
+                  std::map<uint32_t, uint64_t>& counts) {
+  const int s = (int)e.size();
+  std::set<std::vector<int32_t>> level = {e};
+  for (int size = s; size < 5; ++size) {
+    std::set<std::vector<int32_t>> next;
+    for (const auto& cur : level)
+      for (int32_t x : cur)
+        for (int32_t y : g.adj[s][x]) {
+          if (std::binary_search(cur.begin(), cur.end(), y)) continue;
+          std::vector<int32_t> grown = cur;
+          grown.insert(std::upper_bound(grown.begin(), grown.end(), y), y);
+          next.insert(grown);
+        }
+    level.swap(next);
+  }
+  for (const auto& v : level) {
+    const uint32_t mask = fill5(g, v.data());
+    int mc, cm;
+    maxcard5(mask, &mc, &cm);
+    if (mc != s || !connected5(mask)) continue;
+    ++counts[canonical5(mask)];
+  }
+}
+
+int64_t write_out(const std::map<uint32_t, uint64_t>& counts, int64_t cap, uint32_t* masks,
+                  uint64_t* vals) {
+  int64_t i = 0;
+  for (const auto& kv : counts) {
+    if (i < cap) {
+      masks[i] = kv.first;
+      vals[i] = kv.second;
+    }
+    ++i;
+  }
+  return i;
+}
+
+}  // namespace o5
+
+// Alg. 4 at order 5 (uniform draws). S: draws per stratum, S[s] for s = 2..5.
+// Writes up to cap classes in ascending canonical mask: masks, raw counts n_c,
+// estimates (n_c |E_m|) / (S_m countmax_c) in IEEE double, m = the class's
+// largest hyperedge size. Returns the number of classes met.
+int64_t orc_sample5(const int32_t* members, const int64_t* offsets, int64_t m, int32_t n,
+                    const uint64_t* S, uint64_t seed, int64_t cap, uint32_t* masks, uint64_t* raw,
+                    double* est) {
+  const o5::Graph5 g = o5::make_graph5(members, offsets, m, n);
+  std::map<uint32_t, uint64_t> counts;
+  for (int s = 2; s <= 5; ++s) {
+    const uint64_t len = g.E[s].size();
+    if (len == 0) continue;
+    for (uint64_t t = 0; t < S[s]; ++t) {
+      const uint64_t idx = mulhi64(draw64(seed, t, (uint32_t)s, TAG_SAMPLE), len);
+      o5::sets_through(g, g.E[s][idx], counts);
+    }
+  }
+  const int64_t nc = o5::write_out(counts, cap, masks, raw);
+  int64_t i = 0;
+  for (const auto& kv : counts) {
+    if (i >= cap) break;
+    int mc, cm;
+    o5::maxcard5(kv.first, &mc, &cm);
+    const double denom = (double)S[mc] * (double)cm;
+    est[i] = S[mc] ? ((double)kv.second * (double)g.E[mc].size()) / denom : 0.0;
+    ++i;
+  }
+  return nc;
+}
+
+// Every hyperedge of size 2..5 taken once (no sampling): sum over e of the
+// counted sets through e, per canonical mask. Equals countmax_c times the
+// exact order-5 count of class c (each set is counted once per hyperedge of
+// maximum cardinality it holds).
+int64_t orc_sweep5(const int32_t* members, const int64_t* offsets, int64_t m, int32_t n,
+                   int64_t cap, uint32_t* masks, uint64_t* sums) {
+  const o5::Graph5 g = o5::make_graph5(members, offsets, m, n);
+  std::map<uint32_t, uint64_t> counts;
+  for (int s = 2; s <= 5; ++s)
+    for (const auto& e : g.E[s]) o5::sets_through(g, e, counts);
+  return o5::write_out(counts, cap, masks, sums);
+}
+
+uint32_t orc_canonical5(uint32_t mask) { return o5::canonical5(mask); }
+int orc_connected5(uint32_t mask) { return o5::connected5(mask) ? 1 : 0; }
 }  // extern "C"

@@ -75,6 +75,9 @@ _SIGS = {
     "hm_work_totals": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "hm_count_exact_baseline": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32,
                                                ctypes.c_int, _vp, _vp, _vp]),
+    "hm_count_sampled5": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp,
+                                         ctypes.c_uint64, ctypes.c_uint64, _vp, _vp, _vp,
+                                         ctypes.c_int64, _vp, _vp]),
     "hm_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "hm_trace_only": (ctypes.c_int, [ctypes.c_char_p]),
     "hm_launch_count": (ctypes.c_uint64, []),
@@ -524,3 +527,24 @@ def count_exact_baseline(members: torch.Tensor, offsets: torch.Tensor, num_nodes
                                           int(num_nodes), int(order), _dptr(out), info,
                                           _stream(stream)))
     return out, int(info[0]), int(info[1])
+
+
+def count_sampled5(members: torch.Tensor, offsets: torch.Tensor, num_nodes: int, samples=None,
+                   total: int = 0, seed: int = 0, capacity: int = 1 << 20, stream=None):
+    """hm_count_sampled5 (Alg. 4 at order 5): (canonical masks int64, raw
+    counts int64, estimates float64) device tensors of the classes met,
+    ascending by mask."""
+    arr = None
+    if samples is not None:
+        arr = (ctypes.c_uint64 * 6)(*[int(samples.get(s, 0)) if isinstance(samples, dict)
+                                      else int(samples[s]) for s in range(6)])
+    masks = torch.empty(capacity, dtype=torch.int32, device="cuda")
+    raw = torch.empty(capacity, dtype=torch.int64, device="cuda")
+    est = torch.empty(capacity, dtype=torch.float64, device="cuda")
+    nc = ctypes.c_int64()
+    _check(load().hm_count_sampled5(_dptr(members), _dptr(offsets), offsets.numel() - 1,
+                                    int(num_nodes), arr, int(total), int(seed) & (2**64 - 1),
+                                    _dptr(masks), _dptr(raw), _dptr(est), int(capacity),
+                                    ctypes.byref(nc), _stream(stream)))
+    k = min(int(nc.value), capacity)
+    return masks[:k].to(torch.int64) & 0xFFFFFFFF, raw[:k], est[:k]
