@@ -663,6 +663,42 @@ def measure_baseline(hm, stream, cases=(("f2f-330", 1.0, (3, 4)), ("coauth-1m", 
     return out
 
 
+def measure_order5(hm, stream, cases=(("f2f-330", 1.0, 5_000), ("coauth-1m", 0.01, 20_000)),
+                   models=5, sweeps=10, top=5):
+    """Sec. 6.4 on the GPU: Alg. 4 at order 5 on a face-to-face-shaped and a
+    co-authorship-shaped hypergraph (the kinds the paper mines at order 5),
+    and on `models` configuration-model draws of each (pairwise reshuffles);
+    the classes whose estimated abundance against the null is largest, with
+    the sampler's GPU time."""
+    import numpy as np
+    import torch
+    from paper_2209_10241_gb300 import synth
+    out = {}
+    for name, scale, total in cases:
+        h = synth.workload(name, seed=0, scale=scale)
+        mem = torch.from_numpy(h.members).cuda()
+        off = torch.from_numpy(h.offsets).cuda()
+        hm.count_sampled5(mem, off, h.num_nodes, total=100, seed=0)  # warm-up
+        ms, (m, r, e) = _event_ms(lambda: hm.count_sampled5(mem, off, h.num_nodes, total=total,
+                                                            seed=1), stream)
+        obs = dict(zip(m.cpu().numpy().tolist(), e.cpu().numpy().tolist()))
+        null = {k: 0.0 for k in obs}
+        for t in range(models):
+            nm = hm.configuration_model(mem, off, h.num_nodes, t, sweeps, seed=7)
+            mm, _, ee = hm.count_sampled5(nm, off, h.num_nodes, total=total, seed=2 + t)
+            for k, v in zip(mm.cpu().numpy().tolist(), ee.cpu().numpy().tolist()):
+                if k in null:
+                    null[k] += v / models
+        delta = {k: (obs[k] - null[k]) / (obs[k] + null[k] + 4.0) for k in obs}
+        best = sorted((k for k in obs if obs[k] >= 10.0), key=lambda k: -delta[k])[:top]
+        out[f"{name}@{scale}"] = {
+            "nodes": h.num_nodes, "hyperedges": h.num_hyperedges, "draws": total,
+            "gpu_ms": ms, "classes_met": len(obs), "null_models": models,
+            "over_expressed": [{"canonical_mask": int(k), "abundance": delta[k],
+                                "estimate": obs[k], "null_mean": null[k]} for k in best]}
+    return out
+
+
 def measure_profiles(hm, stream, cases=(("f2f-330", 1.0, (100, 250, 500, 1000)),
                                         ("coauth-1m", 0.1, (1000, 2500, 5000, 10000))),
                      models=10, seeds=10):
@@ -868,7 +904,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the face-to-face, sampler and null-batch rows")
     ap.add_argument("--only", choices=["sampler", "null", "large", "sampler-full", "f2f",
-                                       "profiles", "baseline"],
+                                       "profiles", "baseline", "order5"],
                     default=None, help="run one of the extra measurements alone (for profiling)")
     ap.add_argument("--large", default="comm-5m",
                     help="workload of --only large (comm-5m or coauth-1m)")
@@ -900,6 +936,8 @@ def main():
             res = measure_null(hm, stream, hyperedges=NULL_BASES[:args.null_bases])
         elif args.only == "sampler-full":
             res = measure_sampler_full(hm, stream)
+        elif args.only == "order5":
+            res = measure_order5(hm, stream)
         elif args.only == "baseline":
             res = measure_baseline(hm, stream)
         elif args.only == "profiles":
@@ -966,6 +1004,7 @@ def main():
         line["null_batch"] = measure_null(hm, stream, hyperedges=NULL_BASES[:args.null_bases])
         line["profiles"] = measure_profiles(hm, stream)
         line["baseline"] = measure_baseline(hm, stream)
+        line["order5"] = measure_order5(hm, stream)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(h, args.order, args.workload)
         if not args.no_extras:

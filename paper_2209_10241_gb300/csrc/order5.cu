@@ -17,8 +17,11 @@
 // of e by ESU with e as the seed (each connected superset once: ESU on the
 // graph with e contracted to one root), then fills each in against the
 // hypergraph, keeps it if it passes the rule and is connected, and counts
-// its canonical mask. Extension lists live in a per-warp slice of scratch;
-// a list at depth c holds at most c times the largest projection degree.
+// its canonical mask. Phase A (a warp per draw) writes each draw's root
+// extension; phase B takes one warp per (draw, first node added), so that a
+// draw at a hub spreads over many warps. Extension lists live in fixed-size
+// slots of scratch: a list at depth c holds at most c times the largest
+// projection degree.
 #include <algorithm>
 #include <vector>
 
@@ -106,7 +109,12 @@ struct Five {
   const ulonglong2* h5;  // slots (hi, lo), empty hi = ~0
   uint64_t h5_mask;
   int bits;
+  // memo of raw mask -> canonical mask (MEMO_DISCONNECTED, or MEMO_UNKNOWN
+  // before the first time a mask is met); every writer of an entry writes
+  // the same value
+  uint32_t* memo;
 };
+constexpr uint32_t MEMO_UNKNOWN = 0xFFFFFFFFu, MEMO_DISCONNECTED = 0xFFFFFFFEu;
 
 __device__ __forceinline__ bool has_quint(const Five& F, const int32_t* v) {
   if (F.m5 == 0) return false;
@@ -286,6 +294,9 @@ __device__ uint32_t evaluate5(const DevGraph& g, const Five& F, const Sub5Tables
     if (has_pair(g, w[0], w[1])) mask |= 1u << q;
   }
   if (s == 5) mask |= 1u << 25;  // the drawn hyperedge itself
+  const uint32_t known = F.memo[mask];
+  if (known == MEMO_DISCONNECTED) return NOT_COUNTED;
+  if (known != MEMO_UNKNOWN) return known;
   // connectivity over the five positions
   int parent[5] = {0, 1, 2, 3, 4};
   for (int q = 0; q < 26; ++q) {
@@ -309,7 +320,10 @@ __device__ uint32_t evaluate5(const DevGraph& g, const Five& F, const Sub5Tables
   for (int i = 1; i < 5; ++i) {
     int x = i;
     while (parent[x] != x) x = parent[x];
-    if (x != r0) return NOT_COUNTED;
+    if (x != r0) {
+      F.memo[mask] = MEMO_DISCONNECTED;
+      return NOT_COUNTED;
+    }
   }
   // canonical form: the smallest image over the 120 relabelings
   uint32_t best = mask;
@@ -322,6 +336,7 @@ __device__ uint32_t evaluate5(const DevGraph& g, const Five& F, const Sub5Tables
     }
     best = min(best, r);
   }
+  F.memo[mask] = best;
   return best;
 }
 
@@ -370,97 +385,141 @@ __device__ int32_t extend(const DevGraph& P, const int32_t* src, int32_t n, int3
   return len;
 }
 
-template <int S>
-__global__ void __launch_bounds__(O5_WARPS * 32)
-    k_sample5(const DevGraph g, const DevGraph P, const Five F, const Sub5Tables* __restrict__ Tg,
-              uint64_t seed, uint64_t draws, int64_t len_s, int64_t cap,
-              int32_t* __restrict__ arena, unsigned long long* __restrict__ hist) {
-  __shared__ Sub5Tables T;
+__device__ __forceinline__ void load_tables(Sub5Tables& T, const Sub5Tables* __restrict__ Tg) {
   for (int i = threadIdx.x; i < (int)sizeof(Sub5Tables); i += blockDim.x)
     reinterpret_cast<uint8_t*>(&T)[i] = reinterpret_cast<const uint8_t*>(Tg)[i];
   __syncthreads();
+}
+
+// members of draw t of stratum S
+template <int S>
+__device__ __forceinline__ void drawn(const DevGraph& g, const Five& F, uint64_t seed, int64_t t,
+                                      int64_t len_s, int32_t* sub) {
+  const uint64_t idx =
+      __umul64hi(philox_draw64(seed, (uint64_t)t, (uint32_t)S, TAG_SAMPLE5), (uint64_t)len_s);
+  if (S == 2) {
+    const uint64_t p = g.e2[idx];
+    sub[0] = (int32_t)(p >> 32);
+    sub[1] = (int32_t)(p & 0xFFFFFFFFull);
+  } else if (S == 3) {
+    const int4 h = g.e3[idx];
+    sub[0] = h.x;
+    sub[1] = h.y;
+    sub[2] = h.z;
+  } else if (S == 4) {
+    const int4 h = g.e4[idx];
+    sub[0] = h.x;
+    sub[1] = h.y;
+    sub[2] = h.z;
+    sub[3] = h.w;
+  } else {
+    for (int i = 0; i < 5; ++i) sub[i] = F.e5[5 * idx + i];
+  }
+}
+
+// Evaluates V4 + {x} for every x of L[0, n) (lanes in parallel).
+__device__ __forceinline__ void finish(const DevGraph& g, const Five& F, const Sub5Tables& T,
+                                       int S, const int32_t* L, int32_t n, const int32_t* v4,
+                                       unsigned long long* hist) {
+  const int lane = threadIdx.x & 31;
+  for (int32_t i = lane; i - lane < n; i += 32) {
+    uint32_t key = NOT_COUNTED;
+    if (i < n) key = evaluate5(g, F, T, S, v4[0], v4[1], v4[2], v4[3], L[i]);
+    count5(key, hist);
+  }
+}
+
+// Phase A, one warp per draw: stratum 5 draws are evaluated; stratum 4
+// draws enumerate their root extension at once; strata 2 and 3 write their
+// root extension L0 (the seed's projection neighbours outside it, each once,
+// from its first member in order) to slot t of `roots` (cap0 entries) and
+// its length to n0[t].
+template <int S>
+__global__ void __launch_bounds__(O5_WARPS * 32)
+    k_roots5(const DevGraph g, const DevGraph P, const Five F, const Sub5Tables* __restrict__ Tg,
+             uint64_t seed, int64_t t0, int64_t draws, int64_t len_s, int64_t cap0,
+             int32_t* __restrict__ roots, int32_t* __restrict__ n0, unsigned long long* hist) {
+  __shared__ Sub5Tables T;
+  load_tables(T, Tg);
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  int32_t* L0 = arena + gw * 3 * cap;  // extension lists of the three depths
-  int32_t* L1 = L0 + cap;
-  int32_t* L2 = L1 + cap;
-  for (int64_t t = gw; t < (int64_t)draws; t += nw) {
-    const uint64_t idx =
-        __umul64hi(philox_draw64(seed, (uint64_t)t, (uint32_t)S, TAG_SAMPLE5), (uint64_t)len_s);
+  for (int64_t d = gw; d < draws; d += nw) {
     int32_t sub[5];
-    if (S == 2) {
-      const uint64_t p = g.e2[idx];
-      sub[0] = (int32_t)(p >> 32);
-      sub[1] = (int32_t)(p & 0xFFFFFFFFull);
-    } else if (S == 3) {
-      const int4 h = g.e3[idx];
-      sub[0] = h.x;
-      sub[1] = h.y;
-      sub[2] = h.z;
-    } else if (S == 4) {
-      const int4 h = g.e4[idx];
-      sub[0] = h.x;
-      sub[1] = h.y;
-      sub[2] = h.z;
-      sub[3] = h.w;
-    } else {
-      for (int i = 0; i < 5; ++i) sub[i] = F.e5[5 * idx + i];
-    }
+    drawn<S>(g, F, seed, t0 + d, len_s, sub);
     if (S == 5) {
       const uint32_t key =
           lane == 0 ? evaluate5(g, F, T, 5, sub[0], sub[1], sub[2], sub[3], sub[4]) : NOT_COUNTED;
       count5(key, hist);
       continue;
     }
-    // root extension: the neighbours (in P) of the seed's members outside
-    // it, each once (from its first member in order)
-    int32_t n0 = 0;
+    int32_t* L0 = roots + d * cap0;
+    int32_t n = 0;
     for (int m = 0; m < S; ++m) {
       const int64_t o = P.off2[sub[m]];
-      const int32_t d = (int32_t)(P.off2[sub[m] + 1] - o);
-      for (int32_t i0 = 0; i0 < d; i0 += 32) {
+      const int32_t dg = (int32_t)(P.off2[sub[m] + 1] - o);
+      for (int32_t i0 = 0; i0 < dg; i0 += 32) {
         const int32_t i = i0 + lane;
         int32_t u = 0;
         bool take = false;
-        if (i < d) {
+        if (i < dg) {
           u = P.adj2[o + i];
           take = true;
           for (int j = 0; j < S; ++j) take &= u != sub[j];
           for (int j = 0; j < m; ++j) take &= !has_pair(P, u, sub[j]);
         }
-        warp_append(take, u, L0, n0);
+        warp_append(take, u, L0, n);
       }
     }
     __syncwarp();
-    // depth by depth down to four nodes, then every fifth node at once
-    auto finish = [&](const int32_t* L, int32_t n, const int32_t* v4) {
-      for (int32_t i = lane; i - lane < n; i += 32) {
-        uint32_t key = NOT_COUNTED;
-        if (i < n) key = evaluate5(g, F, T, S, v4[0], v4[1], v4[2], v4[3], L[i]);
-        count5(key, hist);
-      }
-    };
     if (S == 4) {
-      finish(L0, n0, sub);
-    } else if (S == 3) {
-      for (int32_t i = 0; i < n0; ++i) {
-        const int32_t w = L0[i];
-        const int32_t n1 = extend(P, L0, n0, i + 1, w, sub, 3, L1);
-        sub[3] = w;
-        finish(L1, n1, sub);
-      }
+      finish(g, F, T, 4, L0, n, sub, hist);
+    } else if (lane == 0) {
+      n0[d] = n;
+    }
+  }
+}
+
+// Phase B, one warp per item (draw d, position i of its root extension): the
+// first node added is w = L0[i]; the ESU subtree under it is enumerated
+// here (strata 2 and 3).
+template <int S>
+__global__ void __launch_bounds__(O5_WARPS * 32)
+    k_items5(const DevGraph g, const DevGraph P, const Five F, const Sub5Tables* __restrict__ Tg,
+             uint64_t seed, int64_t t0, int64_t draws, int64_t len_s, int64_t cap0, int64_t cap,
+             const int32_t* __restrict__ roots, const int32_t* __restrict__ n0,
+             const uint64_t* __restrict__ item0, uint64_t items, int32_t* __restrict__ arena,
+             unsigned long long* hist) {
+  __shared__ Sub5Tables T;
+  load_tables(T, Tg);
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int32_t* L1 = arena + gw * 2 * cap;
+  int32_t* L2 = L1 + cap;
+  for (uint64_t it = (uint64_t)gw; it < items; it += (uint64_t)nw) {
+    int64_t lo = 0, hi = draws;  // the draw: last d with item0[d] <= it
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (item0[mid] <= it) lo = mid;
+      else hi = mid;
+    }
+    const int64_t d = lo;
+    const int32_t i = (int32_t)(it - item0[d]);
+    const int32_t* L0 = roots + d * cap0;
+    const int32_t nd0 = n0[d];
+    int32_t sub[5];
+    drawn<S>(g, F, seed, t0 + d, len_s, sub);
+    const int32_t w = L0[i];
+    const int32_t n1 = extend(P, L0, nd0, i + 1, w, sub, S, L1);
+    sub[S] = w;
+    if (S == 3) {
+      finish(g, F, T, 3, L1, n1, sub, hist);
     } else {  // S == 2
-      for (int32_t i = 0; i < n0; ++i) {
-        const int32_t w = L0[i];
-        const int32_t n1 = extend(P, L0, n0, i + 1, w, sub, 2, L1);
-        sub[2] = w;
-        for (int32_t j = 0; j < n1; ++j) {
-          const int32_t w2 = L1[j];
-          const int32_t n2 = extend(P, L1, n1, j + 1, w2, sub, 3, L2);
-          sub[3] = w2;
-          finish(L2, n2, sub);
-        }
+      for (int32_t j = 0; j < n1; ++j) {
+        const int32_t w2 = L1[j];
+        const int32_t n2 = extend(P, L1, n1, j + 1, w2, sub, 3, L2);
+        sub[3] = w2;
+        finish(g, F, T, 2, L2, n2, sub, hist);
       }
     }
   }
@@ -533,6 +592,12 @@ __global__ void k_h5_emit(const unsigned long long* __restrict__ hist,
   }
 }
 
+__global__ void k_widen32(const int32_t* __restrict__ in, int64_t n, uint64_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (uint64_t)(uint32_t)in[i];
+}
+
 unsigned grid_n(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b < 1) b = 1;
@@ -592,7 +657,9 @@ int64_t count_sampled5(const int32_t* d_members, const int64_t* d_offsets, int64
         HM_KCHECK();
       }
     }
-    const Five F{e5.p, m5, h5.p, h5_mask, b};
+    DBuf<uint32_t> memo(H5_SIZE, s);
+    HM_CUDA(cudaMemsetAsync(memo.p, 0xFF, H5_SIZE * sizeof(uint32_t), s));
+    const Five F{e5.p, m5, h5.p, h5_mask, b, memo.p};
     const int64_t lens[6] = {0, 0, g->counts[2], g->counts[3], g->counts[4], m5};
     for (int st = 2; st <= 5; ++st)
       HM_CHECK(lens[st] == 0 || S[st] > 0, HM_EINVAL,
@@ -625,32 +692,60 @@ int64_t count_sampled5(const int32_t* d_members, const int64_t* d_offsets, int64
     for (int st = 2; st <= 5; ++st) {
       if (S[st] == 0 || lens[st] == 0) continue;
       const hm_graph* P = st == 2 ? g : (st == 5 ? g : proj[st]);
-      // a list at depth c holds at most c * (largest degree of P) entries
-      const int64_t cap = 4 * (int64_t)std::max(1, P->max_d2) + 32;
-      const int64_t want_blocks = ((int64_t)S[st] + O5_WARPS - 1) / O5_WARPS;
-      const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(want_blocks, (int64_t)sms * 4));
-      const int64_t warps = blocks * O5_WARPS;
-      DBuf<int32_t> arena(st == 5 ? 1 : (size_t)(warps * 3 * cap), s);
+      const int64_t maxdeg = std::max(1, P->max_d2);
+      // lists at depth c hold at most c * maxdeg entries (c <= 4)
+      const int64_t cap0 = (int64_t)st * maxdeg + 32, cap = 4 * maxdeg + 32;
       const DevGraph gv = g->view(), pv = P->view();
-      switch (st) {
-        case 2:
-          k_sample5<2><<<(unsigned)blocks, O5_WARPS * 32, 0, s>>>(
-              gv, pv, F, tables.p, seed, S[st], lens[st], cap, arena.p, hist.p);
-          break;
-        case 3:
-          k_sample5<3><<<(unsigned)blocks, O5_WARPS * 32, 0, s>>>(
-              gv, pv, F, tables.p, seed, S[st], lens[st], cap, arena.p, hist.p);
-          break;
-        case 4:
-          k_sample5<4><<<(unsigned)blocks, O5_WARPS * 32, 0, s>>>(
-              gv, pv, F, tables.p, seed, S[st], lens[st], cap, arena.p, hist.p);
-          break;
-        default:
-          k_sample5<5><<<(unsigned)blocks, O5_WARPS * 32, 0, s>>>(
-              gv, pv, F, tables.p, seed, S[st], lens[st], cap, arena.p, hist.p);
-          break;
+      // draws in batches whose root lists take at most ~256 MB
+      const int64_t per = std::max<int64_t>(1, std::min<int64_t>((int64_t)S[st],
+                                                                 (64ll << 20) / cap0));
+      for (int64_t t0 = 0; t0 < (int64_t)S[st]; t0 += per) {
+        const int64_t nd = std::min<int64_t>(per, (int64_t)S[st] - t0);
+        const int64_t rblocks =
+            std::max<int64_t>(1, std::min<int64_t>((nd + O5_WARPS - 1) / O5_WARPS, (int64_t)sms * 8));
+        DBuf<int32_t> roots(st <= 4 ? (size_t)(nd * cap0) : 1, s), n0(nd + 1, s);
+        switch (st) {
+          case 2:
+            k_roots5<2><<<(unsigned)rblocks, O5_WARPS * 32, 0, s>>>(
+                gv, pv, F, tables.p, seed, t0, nd, lens[st], cap0, roots.p, n0.p, hist.p);
+            break;
+          case 3:
+            k_roots5<3><<<(unsigned)rblocks, O5_WARPS * 32, 0, s>>>(
+                gv, pv, F, tables.p, seed, t0, nd, lens[st], cap0, roots.p, n0.p, hist.p);
+            break;
+          case 4:
+            k_roots5<4><<<(unsigned)rblocks, O5_WARPS * 32, 0, s>>>(
+                gv, pv, F, tables.p, seed, t0, nd, lens[st], cap0, roots.p, n0.p, hist.p);
+            break;
+          default:
+            k_roots5<5><<<(unsigned)rblocks, O5_WARPS * 32, 0, s>>>(
+                gv, pv, F, tables.p, seed, t0, nd, lens[st], cap0, roots.p, n0.p, hist.p);
+            break;
+        }
+        HM_KCHECK();
+        if (st >= 4) continue;
+        // items (draw, first added node): prefix of the root list lengths
+        DBuf<uint64_t> n64(nd + 1, s), item0(nd + 1, s);
+        k_widen32<<<grid_n(nd), 256, 0, s>>>(n0.p, nd, n64.p);
+        HM_KCHECK();
+        scan_exclusive_u64(n64.p, item0.p, nd, s);
+        uint64_t items = 0;
+        HM_CUDA(cudaMemcpyAsync(&items, item0.p + nd, sizeof items, cudaMemcpyDeviceToHost, s));
+        HM_CUDA(cudaStreamSynchronize(s));
+        if (items == 0) continue;
+        const int64_t iblocks = std::max<int64_t>(
+            1, std::min<int64_t>(((int64_t)items + O5_WARPS - 1) / O5_WARPS, (int64_t)sms * 8));
+        DBuf<int32_t> arena((size_t)(iblocks * O5_WARPS * 2 * cap), s);
+        if (st == 2)
+          k_items5<2><<<(unsigned)iblocks, O5_WARPS * 32, 0, s>>>(
+              gv, pv, F, tables.p, seed, t0, nd, lens[st], cap0, cap, roots.p, n0.p, item0.p,
+              items, arena.p, hist.p);
+        else
+          k_items5<3><<<(unsigned)iblocks, O5_WARPS * 32, 0, s>>>(
+              gv, pv, F, tables.p, seed, t0, nd, lens[st], cap0, cap, roots.p, n0.p, item0.p,
+              items, arena.p, hist.p);
+        HM_KCHECK();
       }
-      HM_KCHECK();
     }
     // the classes met, ascending, with their estimates
     const int64_t nch = H5_SIZE / H5_CHUNK;
