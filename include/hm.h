@@ -223,6 +223,20 @@ hm_status hm_trace_enable(int on);
  * that a timed run pays for the events of one kernel only. */
 hm_status hm_trace_only(const char* name);
 /*
+ * Debug check of canonical generation (no counterpart in the paper; the
+ * paper dedupes with a visited set, this library by rules that accept each
+ * connected set in exactly one family and anchor). Runs the per-candidate
+ * families (T3 and W at order 3; Q, TX, S and P at order 4) over the whole
+ * graph, emits every connected set they accept as its sorted nodes packed
+ * into one 64-bit key, radix-sorts the keys and counts repeats: h_out (host
+ * uint64[2]) = {sets emitted, keys equal to their predecessor}. A correct
+ * census has 0 repeats and as many sets as hm_count_exact's total. Needs
+ * order * (bits per node id) <= 64 (HM_EUNSUPPORTED otherwise) and 8 bytes per
+ * set of device memory. Synchronous.
+ */
+hm_status hm_debug_canonical_check(hm_graph* g, int order, uint64_t* h_out, void* stream);
+
+/*
  * Self-test of the bounded device-side waits (no counterpart in the paper;
  * instrumentation). Runs the radix sort's decoupled look-back, in both its
  * thread and warp forms, against a status word that no tile ever publishes:

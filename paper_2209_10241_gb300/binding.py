@@ -82,6 +82,7 @@ _SIGS = {
     "hm_trace_only": (ctypes.c_int, [ctypes.c_char_p]),
     "hm_launch_count": (ctypes.c_uint64, []),
     "hm_selftest_wait": (ctypes.c_int, [_vp]),
+    "hm_debug_canonical_check": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "hm_serialize_launches": (ctypes.c_int, [ctypes.c_int]),
     "hm_significance_profile": (ctypes.c_int, [ctypes.c_int, _vp, _vp, ctypes.c_int,
                                                ctypes.c_double, _vp, _vp, _vp]),
@@ -548,3 +549,10 @@ def count_sampled5(members: torch.Tensor, offsets: torch.Tensor, num_nodes: int,
                                     ctypes.byref(nc), _stream(stream)))
     k = min(int(nc.value), capacity)
     return masks[:k].to(torch.int64) & 0xFFFFFFFF, raw[:k], est[:k]
+
+
+def debug_canonical_check(g: Graph, order: int, stream=None):
+    """hm_debug_canonical_check: (sets emitted, repeated keys)."""
+    out = (ctypes.c_uint64 * 2)()
+    _check(load().hm_debug_canonical_check(g._h, order, out, _stream(stream)))
+    return int(out[0]), int(out[1])

@@ -1047,6 +1047,118 @@ void launch_census(const hm_graph* g, int order, unsigned long long* hist, cudaS
   }
 }
 
+// ------------------------------------------------------------------ generation check
+namespace {
+
+// Every connected set a per-candidate family accepts, as its sorted nodes
+// packed into one key (bits per node, most significant first); count holds
+// the number of sets, keys the first cap of them.
+template <class F>
+__global__ void k_emit_keys(const DevGraph g, const F fam, const uint64_t* __restrict__ ws,
+                            int64_t A, uint64_t total, const uint8_t* __restrict__ lut, int k,
+                            int bits, unsigned long long* __restrict__ count,
+                            uint64_t* __restrict__ keys, uint64_t cap) {
+  for (uint64_t gi = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; gi < total;
+       gi += (uint64_t)gridDim.x * blockDim.x) {
+    typename F::State st;
+    uint32_t mask = 0;
+    int32_t nd[4];
+    bool ok;
+    if (F::kDirect) {
+      ok = fam.item(g, (int64_t)gi, st, mask, nd);
+    } else {
+      const int64_t a = anchor_of(ws, A, gi);
+      fam.begin(g, a, gi - ws[a], st);
+      ok = fam.item(g, a, st, mask, nd);
+    }
+    if (!ok || lut[mask] == 0xFF) continue;
+    for (int i = 1; i < k; ++i) {  // insertion sort of the k nodes
+      const int32_t x = nd[i];
+      int j = i - 1;
+      while (j >= 0 && nd[j] > x) {
+        nd[j + 1] = nd[j];
+        --j;
+      }
+      nd[j + 1] = x;
+    }
+    uint64_t key = 0;
+    for (int i = 0; i < k; ++i) key = (key << bits) | (uint64_t)(uint32_t)nd[i];
+    const unsigned long long at = atomicAdd(count, 1ull);
+    if (at < cap) keys[at] = key;
+  }
+}
+
+__global__ void k_count_dups(const uint64_t* __restrict__ keys, uint64_t n,
+                             unsigned long long* __restrict__ dups) {
+  unsigned long long mine = 0;
+  for (uint64_t i = 1 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    mine += keys[i] == keys[i - 1] ? 1ull : 0ull;
+  if (mine) atomicAdd(dups, mine);
+}
+
+template <class F>
+void emit_keys(const hm_graph* g, const F& fam, const hm_graph::Space* sp, uint64_t total,
+               int order, unsigned long long* count, uint64_t* keys, uint64_t cap,
+               cudaStream_t s) {
+  if (total == 0) return;
+  const uint64_t blocks = std::min<uint64_t>((total + 255) / 256, 152 * 16);
+  k_emit_keys<F><<<(unsigned)blocks, 256, 0, s>>>(g->view(), fam, sp ? sp->ws : nullptr,
+                                                  sp ? sp->anchors : 0, total, device_lut(order),
+                                                  order, g->bits, count, keys, cap);
+  HM_KCHECK();
+}
+
+void emit_all(hm_graph* g, int order, unsigned long long* count, uint64_t* keys, uint64_t cap,
+              cudaStream_t s) {
+  if (order == 3) {
+    emit_keys(g, FamT3{}, nullptr, (uint64_t)g->counts[3], 3, count, keys, cap, s);
+    emit_keys(g, FamW{}, &g->W, g->W.total, 3, count, keys, cap, s);
+  } else {
+    emit_keys(g, FamQ{}, nullptr, (uint64_t)g->counts[4], 4, count, keys, cap, s);
+    emit_keys(g, FamTX{}, &g->TX, g->TX.total, 4, count, keys, cap, s);
+    emit_keys(g, FamS{}, &g->S, g->S.total, 4, count, keys, cap, s);
+    emit_keys(g, FamP{}, &g->P, g->P.total, 4, count, keys, cap, s);
+  }
+}
+
+}  // namespace
+
+// The per-candidate families' canonical generation checked directly: every
+// accepted connected set emitted as a key, the keys radix-sorted, repeats
+// counted. out = {sets, repeated keys}.
+void debug_canonical(hm_graph* g, int order, uint64_t* out, cudaStream_t s) {
+  HM_CHECK(order * g->bits <= 64, HM_EUNSUPPORTED, "node ids too wide for one 64-bit key");
+  HM_CHECK(g->block == 0, HM_EUNSUPPORTED, "not available for a union of graphs");
+  ensure_spaces(g, order == 3 ? std::vector<std::pair<hm_graph::Space*, char>>{{&g->W, 'W'}}
+                              : std::vector<std::pair<hm_graph::Space*, char>>{
+                                    {&g->S, 'S'}, {&g->P, 'P'}, {&g->TX, 'X'}},
+                s);
+  DBuf<unsigned long long> cnt(2, s);
+  HM_CUDA(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(unsigned long long), s));
+  emit_all(g, order, cnt.p, nullptr, 0, s);  // count only
+  unsigned long long n = 0;
+  HM_CUDA(cudaMemcpyAsync(&n, cnt.p, sizeof n, cudaMemcpyDeviceToHost, s));
+  HM_CUDA(cudaStreamSynchronize(s));
+  DBuf<uint64_t> keys(n ? n : 1, s);
+  HM_CUDA(cudaMemsetAsync(cnt.p, 0, 2 * sizeof(unsigned long long), s));
+  emit_all(g, order, cnt.p, keys.p, n, s);
+  if (n > 1) {
+    radix_sort_u64(keys.p, nullptr, (int64_t)n, order * g->bits, s);
+    k_count_dups<<<(unsigned)std::min<uint64_t>((n + 255) / 256, 152 * 8), 256, 0, s>>>(
+        keys.p, n, cnt.p + 1);
+    HM_KCHECK();
+  }
+  unsigned long long h[2] = {0, 0};
+  HM_CUDA(cudaMemcpyAsync(h, cnt.p, sizeof h, cudaMemcpyDeviceToHost, s));
+  unsigned timeouts = 0;
+  wait_timeouts_async(&timeouts, s);
+  HM_CUDA(cudaStreamSynchronize(s));
+  wait_timeouts_check(timeouts, s);
+  out[0] = h[0];
+  out[1] = h[1];
+}
+
 // Alg. 1 on the projection graph p, with fill-in against the hypergraph h:
 // the connected k-sets of p (wedges and triangles for k = 3; stars, paths and
 // 4-cycles for k = 4), each counted by the class of the sub-hypergraph of h it
@@ -1386,5 +1498,15 @@ extern "C" hm_status hm_work_totals(hm_graph* g, int order, uint64_t* totals, vo
       totals[8] = g->TXb.total;
       totals[9] = g->useTXb ? 1 : 0;
     }
+  });
+}
+
+extern "C" hm_status hm_debug_canonical_check(hm_graph* g, int order, uint64_t* h_out,
+                                              void* stream) {
+  return hm::guarded([&] {
+    HM_CHECK(g && h_out, HM_EINVAL, "NULL argument");
+    HM_CHECK(order == 3 || order == 4, HM_EINVAL, "order must be 3 or 4");
+    HM_CHECK(order <= g->kmax, HM_EUNSUPPORTED, "order exceeds the graph's max_order");
+    hm::debug_canonical(g, order, h_out, (cudaStream_t)stream);
   });
 }
