@@ -486,18 +486,29 @@ __device__ __forceinline__ void txs_candidate(const DevGraph& g, const TxsAnchor
 #ifndef HM_TXS_MINBLOCKS
 #define HM_TXS_MINBLOCKS 4
 #endif
+// G lanes per 3-hyperedge (32: a warp; 8: four 3-hyperedges per warp, for
+// those whose lists are all short). The 3-hyperedges are list[0, *count), or
+// all of E_3 when list is null. The only cross-lane operations (the pairs
+// inside e, the special-count sums) stay within a group.
+template <int G>
 __global__ void __launch_bounds__(CENSUS_THREADS, HM_TXS_MINBLOCKS)
-    k_census_txs(const DevGraph g, const uint8_t* __restrict__ lut_g, int nmask, int ncls,
-                 int sub, unsigned long long* __restrict__ hist) {
+    k_census_txs(const DevGraph g, const int32_t* __restrict__ list,
+                 const unsigned int* __restrict__ count, const uint8_t* __restrict__ lut_g,
+                 int nmask, int ncls, int sub, unsigned long long* __restrict__ hist) {
   __shared__ unsigned long long bins[BIN_STRIDE];
   __shared__ __align__(16) uint8_t lut[2048];
   load_lut(lut, lut_g, nmask);
   for (int i = threadIdx.x; i < ncls; i += blockDim.x) bins[i] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int glane = lane % G, gbase = lane - glane;
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
+  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int64_t total = list ? (int64_t)*count : g.m3;
   const TxsBins B{bins, lut, sub};
-  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < g.m3; t += warps) {
+  for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; it < total;
+       it += groups) {
+    const int64_t t = list ? (int64_t)list[it] : it;
     TxsAnchor A;
     const int4 e = g.e3[t];
     A.m0 = e.x;
@@ -523,13 +534,13 @@ __global__ void __launch_bounds__(CENSUS_THREADS, HM_TXS_MINBLOCKS)
     A.s32 = g.sig[(int64_t)g.n + e.z];
     A.s4 = g.sig[2 * (int64_t)g.n + e.x] & g.sig[2 * (int64_t)g.n + e.y] &
            g.sig[2 * (int64_t)g.n + e.z];
-    // the pairs inside e: lanes 0-2 probe, the warp shares
+    // the pairs inside e: group lanes 0-2 probe, the group shares
     bool mine = false;
-    if (lane < 3) {  // lane 0: {a, b}, 1: {a, c}, 2: {b, c}
-      const int32_t u = lane == 2 ? e.y : e.x, v = lane == 0 ? e.y : e.z;
-      mine = ((lane == 2 ? A.s21 : A.s20) & sig_bit(v)) && has_pair(g, u, v);
+    if (glane < 3) {  // lane 0: {a, b}, 1: {a, c}, 2: {b, c}
+      const int32_t u = glane == 2 ? e.y : e.x, v = glane == 0 ? e.y : e.z;
+      mine = ((glane == 2 ? A.s21 : A.s20) & sig_bit(v)) && has_pair(g, u, v);
     }
-    const unsigned pb = __ballot_sync(0xffffffffu, mine);
+    const unsigned pb = (__ballot_sync(gmask, mine) >> gbase) & 7u;
     A.pab = pb & 1u;
     A.pac = pb & 2u;
     A.pbc = pb & 4u;
@@ -537,7 +548,7 @@ __global__ void __launch_bounds__(CENSUS_THREADS, HM_TXS_MINBLOCKS)
     const int nsrc = A.s4 ? 9 : 6;
 #pragma unroll 1
     for (int src = 0; src < nsrc; ++src) {
-      // the source's list (warp-uniform): member pair (p, q) or member x
+      // the source's list (group-uniform): member pair (p, q) or member x
       const int p = src < 6 ? (src % 3 == 2 ? 1 : 0) : src - 6;
       const int q = src % 3 == 0 ? 1 : 2;
       int64_t o;
@@ -562,8 +573,8 @@ __global__ void __launch_bounds__(CENSUS_THREADS, HM_TXS_MINBLOCKS)
         len = sel3(p, A.d20, A.d21, A.d22);
         kp = 1u << p;
       }
-      for (int32_t i0 = 0; i0 < len; i0 += 32) {
-        const int32_t idx = i0 + lane;
+      for (int32_t i0 = 0; i0 < len; i0 += G) {
+        const int32_t idx = i0 + glane;
         if (idx >= len) continue;
         int32_t d;
         if (src < 3 || src >= 6) {
@@ -581,12 +592,12 @@ __global__ void __launch_bounds__(CENSUS_THREADS, HM_TXS_MINBLOCKS)
       }
     }
 #pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      sp0 += __shfl_xor_sync(0xffffffffu, sp0, o);
-      sp1 += __shfl_xor_sync(0xffffffffu, sp1, o);
-      sp2 += __shfl_xor_sync(0xffffffffu, sp2, o);
+    for (int o = G / 2; o; o >>= 1) {
+      sp0 += __shfl_xor_sync(gmask, sp0, o);
+      sp1 += __shfl_xor_sync(gmask, sp1, o);
+      sp2 += __shfl_xor_sync(gmask, sp2, o);
     }
-    if (lane == 0) {
+    if (glane == 0) {
       const uint32_t fixed = (A.pab ? 1u : 0u) | (A.pac ? 2u : 0u) | (A.pbc ? 8u : 0u) | 64u;
       const unsigned long long pa =
           (unsigned long long)A.d20 - (A.pab ? 1 : 0) - (A.pac ? 1 : 0) - sp0;
@@ -602,6 +613,53 @@ __global__ void __launch_bounds__(CENSUS_THREADS, HM_TXS_MINBLOCKS)
   __syncthreads();
   for (int i = threadIdx.x; i < ncls; i += blockDim.x)
     if (bins[i]) atomicAdd(&hist[i], bins[i]);
+}
+
+// Splits E_3 for k_census_txs: a 3-hyperedge whose every scanned list (the
+// shorter row and the shorter incidence list of each member pair, and each
+// member's row where the 4-hyperedge signatures meet) has at most
+// TXS_SMALL entries goes to the 8-lane list, the others to the warp list.
+#ifndef HM_TXS_SMALL
+#define HM_TXS_SMALL 32
+#endif
+constexpr int TXS_SMALL = HM_TXS_SMALL;
+__global__ void k_txs_split(const DevGraph g, int32_t* __restrict__ small,
+                            int32_t* __restrict__ large, unsigned int* __restrict__ counts) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n = (g.m3 + 31) / 32 * 32;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    bool valid = t < g.m3, is_small = false;
+    if (valid) {
+      const int4 e = g.e3[t];
+      const int32_t m[3] = {e.x, e.y, e.z};
+      int32_t d2[3], d3[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        d2[j] = (int32_t)(g.off2[m[j] + 1] - g.off2[m[j]]);
+        d3[j] = (int32_t)(g.off3[m[j] + 1] - g.off3[m[j]]);
+      }
+      int32_t mx = max(max(min(d2[0], d2[1]), min(d2[0], d2[2])), min(d2[1], d2[2]));
+      mx = max(mx, max(max(min(d3[0], d3[1]), min(d3[0], d3[2])), min(d3[1], d3[2])));
+      const uint64_t s4 = g.sig[2 * (int64_t)g.n + e.x] & g.sig[2 * (int64_t)g.n + e.y] &
+                          g.sig[2 * (int64_t)g.n + e.z];
+      if (s4) mx = max(mx, max(d2[0], max(d2[1], d2[2])));
+      is_small = mx <= TXS_SMALL;
+    }
+    // warp-aggregated appends
+    const unsigned bs = __ballot_sync(0xffffffffu, valid && is_small);
+    const unsigned bl = __ballot_sync(0xffffffffu, valid && !is_small);
+    unsigned int base_s = 0, base_l = 0;
+    if (lane == 0) {
+      if (bs) base_s = atomicAdd(&counts[0], (unsigned)__popc(bs));
+      if (bl) base_l = atomicAdd(&counts[1], (unsigned)__popc(bl));
+    }
+    base_s = __shfl_sync(0xffffffffu, base_s, 0);
+    base_l = __shfl_sync(0xffffffffu, base_l, 0);
+    const unsigned below = (1u << lane) - 1u;
+    if (valid && is_small) small[base_s + __popc(bs & below)] = (int32_t)t;
+    if (valid && !is_small) large[base_l + __popc(bl & below)] = (int32_t)t;
+  }
 }
 
 unsigned grid1d(int64_t n) {
@@ -955,16 +1013,32 @@ void launch_txs(const hm_graph* g, unsigned long long* hist, cudaStream_t s, boo
   if (g->counts[3] == 0) return;
   const ClassTables& T = class_tables(4);
   const uint8_t* lut = device_lut(4);
-  // a persistent grid: the resident blocks of every SM, warps striding over E_3
-  int sms = 0, per_sm = 0;
-  resident_blocks((const void*)k_census_txs, sms, per_sm);
-  const int64_t want = (g->counts[3] + CENSUS_THREADS / 32 - 1) / (CENSUS_THREADS / 32);
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * per_sm));
+  // 3-hyperedges with short lists go four to a warp, the rest a warp each;
+  // persistent grids (every SM's resident blocks) read their list lengths on
+  // the device
+  const int64_t m3 = g->counts[3];
+  DBuf<unsigned char> buf(((size_t)2 * m3 * 4 + 255) / 256 * 256 + 256, s);
+  int32_t* small = reinterpret_cast<int32_t*>(buf.p);
+  int32_t* large = small + m3;
+  unsigned int* counts = reinterpret_cast<unsigned int*>(buf.p + ((size_t)2 * m3 * 4 + 255) / 256 * 256);
   cudaEvent_t ev = nullptr;
   const bool tr = traced && trace_on("census_TX");
   if (tr) trace_begin(s, &ev);
-  k_census_txs<<<blocks, CENSUS_THREADS, 0, s>>>(g->view(), lut, (int)T.lut.size(), T.ncls,
-                                                  sub ? 1 : 0, hist);
+  HM_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned int), s));
+  k_txs_split<<<grid1d(m3), 256, 0, s>>>(g->view(), small, large, counts);
+  HM_KCHECK();
+  int sms = 0, per32 = 0, per8 = 0;
+  resident_blocks((const void*)k_census_txs<32>, sms, per32);
+  resident_blocks((const void*)k_census_txs<8>, sms, per8);
+  const int64_t want32 = (m3 + CENSUS_THREADS / 32 - 1) / (CENSUS_THREADS / 32);
+  const int64_t want8 = (m3 + CENSUS_THREADS / 8 - 1) / (CENSUS_THREADS / 8);
+  const int b32 = (int)std::max<int64_t>(1, std::min<int64_t>(want32, (int64_t)sms * per32));
+  const int b8 = (int)std::max<int64_t>(1, std::min<int64_t>(want8, (int64_t)sms * per8));
+  k_census_txs<32><<<b32, CENSUS_THREADS, 0, s>>>(g->view(), large, counts + 1, lut,
+                                                  (int)T.lut.size(), T.ncls, sub ? 1 : 0, hist);
+  HM_KCHECK();
+  k_census_txs<8><<<b8, CENSUS_THREADS, 0, s>>>(g->view(), small, counts, lut, (int)T.lut.size(),
+                                                T.ncls, sub ? 1 : 0, hist);
   HM_KCHECK();
   if (tr) trace_end("census_TX", s, ev);
 }
