@@ -379,8 +379,15 @@ constexpr int C4_WARP_SLOTS = 512;
 constexpr uint32_t C4_WARP_UB = C4_WARP_SLOTS / 2;
 constexpr uint64_t C4_SENTINEL = ~0ull;
 
+// HM_C4_SORT=1 counts the heavy nodes' 4-cycles by sorting their path keys
+// instead of per-node tables (the tests cover both tiers).
+bool c4_sort_tier() {
+  const char* e = std::getenv("HM_C4_SORT");
+  return e && e[0] == '1';
+}
+
 // The warp tier's bound: C4_WARP_UB, or lower by HM_C4_UB (tests send small
-// graphs' nodes to the sort with it).
+// graphs' nodes to the heavy tier with it).
 uint32_t c4_warp_bound() {
   uint32_t w = C4_WARP_UB;
   if (const char* e = std::getenv("HM_C4_UB")) {
@@ -620,6 +627,146 @@ __global__ void __launch_bounds__(C4E_THREADS)
   }
 }
 
+// Table tier (the default for heavy nodes): one block per node x, paths
+// enumerated as in k_c4_emit, but each endpoint z goes into x's own
+// open-addressing table of 2 * ub(x) slots, [2 ws[x], 2 ws[x+1]) of `table`
+// (slot = (z << 32) | count, empty = all ones; a match adds 1 to the count
+// word, which never carries into z). After the block's inserts, the block
+// sums C(count, 2) over its table: the 4-cycles at x. A table holds at most
+// ub(x) keys in 2 ub(x) slots, so every probe ends.
+__global__ void __launch_bounds__(C4E_THREADS)
+    k_c4_table(const DevGraph g, const uint64_t* __restrict__ ws, int32_t nodes_per_graph,
+               unsigned long long* __restrict__ table, unsigned long long* __restrict__ agg) {
+  __shared__ int64_t s_off[C4E_CAP];
+  __shared__ uint32_t s_pre[C4E_CAP];
+  __shared__ uint32_t s_wsum[C4E_THREADS / 32];
+  __shared__ int32_t s_heavy[C4E_THREADS];
+  __shared__ int s_nheavy;
+  __shared__ uint32_t s_total;
+  __shared__ unsigned long long s_sum[C4E_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  C4Sum acc;
+  for (int64_t c0 = (int64_t)blockIdx.x * C4E_THREADS; c0 < g.n;
+       c0 += (int64_t)gridDim.x * C4E_THREADS) {
+    if (threadIdx.x == 0) s_nheavy = 0;
+    __syncthreads();
+    const int64_t xi = c0 + threadIdx.x;
+    if (xi < g.n && ws[xi + 1] != ws[xi]) s_heavy[atomicAdd(&s_nheavy, 1)] = (int32_t)xi;
+    __syncthreads();
+    const int nh = s_nheavy;
+    for (int hh = 0; hh < nh; ++hh) {
+      const int32_t x = s_heavy[hh];
+      const int64_t ox = g.off2[x];
+      const int32_t dx = (int32_t)(g.off2[x + 1] - ox);
+      const uint64_t tb = 2 * ws[x], tcap = 2 * (ws[x + 1] - ws[x]);
+      for (int32_t r0 = 0; r0 < dx; r0 += C4E_CAP) {
+        const int32_t cnt = min(C4E_CAP, dx - r0);
+        uint32_t v[2];
+        int64_t o[2];
+        uint32_t tsum = 0;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int32_t j = threadIdx.x * 2 + q;
+          v[q] = 0;
+          o[q] = 0;
+          if (j < cnt) {
+            const int32_t y = g.adj2[ox + r0 + j];
+            const int64_t oy = g.off2[y];
+            const int32_t dy = (int32_t)(g.off2[y + 1] - oy);
+            if (lower_rank(dy, y, dx, x)) {
+              v[q] = (uint32_t)dy;
+              o[q] = oy;
+            }
+          }
+          tsum += v[q];
+        }
+        uint32_t incl = tsum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t u = __shfl_up_sync(0xffffffffu, incl, d);
+          if (lane >= d) incl += u;
+        }
+        if (lane == 31) s_wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+          uint32_t w = lane < C4E_THREADS / 32 ? s_wsum[lane] : 0u;
+          uint32_t wi = w;
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, wi, d);
+            if (lane >= d) wi += u;
+          }
+          if (lane < C4E_THREADS / 32) s_wsum[lane] = wi - w;
+          if (lane == 31) s_total = wi;
+        }
+        __syncthreads();
+        uint32_t ex = s_wsum[wid] + incl - tsum;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int32_t j = threadIdx.x * 2 + q;
+          if (j < cnt) {
+            s_pre[j] = ex;
+            s_off[j] = o[q];
+          }
+          ex += v[q];
+        }
+        __syncthreads();
+        const uint32_t total = s_total;
+        for (uint32_t sl = threadIdx.x; sl < total; sl += C4E_THREADS) {
+          int lo = 0, hi2 = cnt;
+          while (hi2 - lo > 1) {
+            const int mid = (lo + hi2) >> 1;
+            if (s_pre[mid] <= sl) lo = mid;
+            else hi2 = mid;
+          }
+          const int32_t z = g.adj2[s_off[lo] + (sl - s_pre[lo])];
+          if (z == x || !lower_rank(degree(g, z), z, dx, x)) continue;
+          const unsigned long long key = (unsigned long long)(uint32_t)z << 32;
+          uint64_t slot = __umul64hi(mix64((uint64_t)(uint32_t)z), tcap);
+          for (uint64_t it = 0; it < tcap; ++it) {
+            unsigned long long* p = table + tb + slot;
+            const unsigned long long cur = *p;
+            if (cur == ~0ull) {
+              const unsigned long long prev = atomicCAS(p, ~0ull, key | 1ull);
+              if (prev == ~0ull) break;
+              if ((prev >> 32) == (uint32_t)z) {
+                atomicAdd(p, 1ull);
+                break;
+              }
+            } else if ((cur >> 32) == (uint32_t)z) {
+              atomicAdd(p, 1ull);
+              break;
+            }
+            if (++slot == tcap) slot = 0;
+          }
+        }
+        __syncthreads();  // the next round overwrites the staged neighbours
+      }
+      // the block's inserts are done (the barrier above): sum C(c, 2) over
+      // x's table, read from L2 where the atomics landed
+      unsigned long long sum = 0;
+      for (uint64_t sl = threadIdx.x; sl < tcap; sl += C4E_THREADS) {
+        const unsigned long long v2 = __ldcg(table + tb + sl);
+        if (v2 != ~0ull) {
+          const unsigned long long c = v2 & 0xFFFFFFFFull;
+          sum += c * (c - 1) / 2;
+        }
+      }
+#pragma unroll
+      for (int o2 = 16; o2; o2 >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
+      if (lane == 0) s_sum[wid] = sum;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < C4E_THREADS / 32; ++w) t += s_sum[w];
+        acc.add(agg, x / nodes_per_graph, t);
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) acc.flush(agg);
+}
+
 // Sort tier, counting: each run of c equal keys (c paths from x to one z)
 // closes C(c, 2) 4-cycles at x.
 __global__ void k_c4_runs(const uint64_t* __restrict__ keys, uint64_t nkeys, int bits,
@@ -767,7 +914,8 @@ void graphlet_prepare(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
     // the sort tier's path keys, then the per-warp pair lists
     G.cap = std::max<int64_t>(1, g->max_d2);
     HM_CHECK(g->C4.ready, HM_EINVAL, "4-cycle paths not sized");
-    keyb = ((size_t)g->C4.total * 8 + 255) & ~(size_t)255;
+    // path keys for the sort (HM_C4_SORT=1), else a table of 2 slots per path
+    keyb = ((size_t)g->C4.total * (c4_sort_tier() ? 8 : 16) + 255) & ~(size_t)255;
     extra = keyb + (size_t)SPARSE_EDGE_BLOCKS * SPARSE_WARPS * G.cap * 4;
   }
   G.buf.alloc(zero + extra, s);
@@ -822,7 +970,16 @@ void graphlet_pairs(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
     HM_KCHECK();
     sw.end();
     const uint64_t nk = g->C4.total;
-    if (nk) {
+    if (nk && !c4_sort_tier()) {
+      const uint64_t eb = std::min<uint64_t>(((uint64_t)g->n + C4E_THREADS - 1) / C4E_THREADS,
+                                             152 * 4);
+      TraceSpan st("census_c4_table", s);
+      HM_CUDA(cudaMemsetAsync(G.c4_keys, 0xFF, 2 * nk * sizeof(uint64_t), s));
+      k_c4_table<<<(unsigned)std::max<uint64_t>(1, eb), C4E_THREADS, 0, s>>>(
+          g->view(), g->C4.ws, G.per, (unsigned long long*)G.c4_keys, G.agg);
+      HM_KCHECK();
+      st.end();
+    } else if (nk) {
       const uint64_t eb = std::min<uint64_t>(((uint64_t)g->n + C4E_THREADS - 1) / C4E_THREADS,
                                              152 * 4);
       TraceSpan se("census_c4_emit", s);

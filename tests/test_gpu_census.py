@@ -22,7 +22,8 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 MODES = ["hash", "bitmap", "sliced", "sliced_filter", "tuned", "chunk8", "chunk32", "graphlets",
-         "graphlets_filter", "graphlets_pc", "graphlets_hash", "graphlets_tiers"]
+         "graphlets_filter", "graphlets_pc", "graphlets_hash", "graphlets_tiers",
+         "graphlets_sort"]
 
 
 def _set_mode(monkeypatch, mode):
@@ -39,20 +40,24 @@ def _set_mode(monkeypatch, mode):
     graphlets_hash: the same without pair bitmaps (hash probes, 4-cycles by
     degree order); graphlets_tiers: graphlets_hash with the warp tier of the
     4-cycle pass bounded at 4 paths, so that small graphs' nodes reach the
-    sort-based tier too, and the per-node sums taken over the whole grid."""
+    per-node table tier too, and the per-node sums taken over the whole
+    grid; graphlets_sort: graphlets_tiers with the heavy nodes' 4-cycles
+    counted by sorting their path keys instead of per-node tables."""
     for var in ("HM_PAIR_BITMAP", "HM_DENSE_FAMILIES", "HM_TRIPLE_ROWS", "HM_AUTOTUNE",
                 "HM_CENSUS_CHUNK", "HM_GRAPHLETS", "HM_C4_UB", "HM_GL_NODE_SUMS", "HM_GL_WIDE",
-                "HM_TX_PER_CANDIDATE"):
+                "HM_TX_PER_CANDIDATE", "HM_C4_SORT"):
         monkeypatch.delenv(var, raising=False)
     if mode == "tuned":
         return
-    if mode in ("graphlets_hash", "graphlets_tiers"):
+    if mode in ("graphlets_hash", "graphlets_tiers", "graphlets_sort"):
         monkeypatch.setenv("HM_PAIR_BITMAP", "0")
         monkeypatch.setenv("HM_GRAPHLETS", "1")
         monkeypatch.setenv("HM_AUTOTUNE", "0")
-        if mode == "graphlets_tiers":
+        if mode != "graphlets_hash":
             monkeypatch.setenv("HM_C4_UB", "4")
             monkeypatch.setenv("HM_GL_NODE_SUMS", "1")
+        if mode == "graphlets_sort":
+            monkeypatch.setenv("HM_C4_SORT", "1")
         return
     if mode.startswith("graphlets"):
         monkeypatch.setenv("HM_PAIR_BITMAP", "1")
@@ -258,7 +263,8 @@ def test_full_size_coauthorship_paths_agree(hm, monkeypatch):
     hists = []
     for graphlets in ("1", "0"):
         for var in ("HM_PAIR_BITMAP", "HM_DENSE_FAMILIES", "HM_TRIPLE_ROWS", "HM_CENSUS_CHUNK",
-                    "HM_C4_UB", "HM_GL_NODE_SUMS", "HM_GL_WIDE", "HM_TX_PER_CANDIDATE"):
+                    "HM_C4_UB", "HM_GL_NODE_SUMS", "HM_GL_WIDE", "HM_TX_PER_CANDIDATE",
+                    "HM_C4_SORT"):
             monkeypatch.delenv(var, raising=False)
         monkeypatch.setenv("HM_GRAPHLETS", graphlets)
         monkeypatch.setenv("HM_AUTOTUNE", "0")

@@ -40,7 +40,8 @@ def _golden(case):
 
 @pytest.mark.parametrize("case", ["coauth-1m-s005", "comm-5m-s001"])
 @pytest.mark.parametrize("k", [3, 4])
-@pytest.mark.parametrize("mode", ["tuned", "graphlets_hash", "graphlets_tiers", "chunk8"])
+@pytest.mark.parametrize("mode", ["tuned", "graphlets_hash", "graphlets_tiers", "graphlets_sort",
+                                  "chunk8"])
 def test_sparse_workloads_against_stored_oracle(hm, monkeypatch, case, k, mode):
     _set_mode(monkeypatch, mode)
     rec = _golden(case)
