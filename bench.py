@@ -54,9 +54,13 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # can exceed the copy bandwidth; the DRAM bytes the kernel really moved are
 # `traffic` (ncu, one capture of the same workload).
 # kernel -> (unit, bytes per unit, work_totals key, DRAM bytes per launch from
-# one ncu capture of the headline workload, or None)
+# one ncu capture of the headline workload, or None). The census_TX span is
+# the sparse TX pass: the split and its two kernels (k_census_txs<32> on
+# 3-hyperedges with a long list, <8> on the rest); its traffic is the sum of
+# the two kernels' read + write bytes.
 ROOFLINE_HBM = {
-    "census_TX": ("TX candidate", 288, "census_TX", 504_759_552 + 14_063_104),
+    "census_TX": ("TX candidate", 288, "census_TX",
+                  194_833_152 + 14_434_560 + 155_997_696 + 4_086_784),
     "census_Q": ("4-hyperedge", 320, "census_Q", None),
 }
 

@@ -371,10 +371,14 @@ __global__ void __launch_bounds__(SPARSE_WARPS * 32)
 // a communication-shaped graph 1 % of the nodes hold 84 % of 2.2e8 paths, the
 // largest 3.6e5), so:
 //   ub <= warp bound: one warp per node counts in a shared-memory hash;
-//   above: the node's paths are written as keys (x << bits) | z into its
-//   slots (a prefix sum of the bounds, computed at build time; unused slots
-//   hold a sentinel), sorted, and each run of c equal keys adds C(c, 2).
-constexpr int C4_WARPS = 8;
+//   above: the node owns ub slots of one path space (a prefix sum of the
+//   bounds, computed at build time) and a table of 2 ub slots in global
+//   memory; blocks take equal pieces of the path space and insert their
+//   paths' endpoints into the owners' tables, then one pass adds C(c, 2)
+//   over the tables. (HM_C4_SORT=1 instead writes each path as a key
+//   (x << bits) | z into its slot, unused slots a sentinel, sorts the keys
+//   and adds C(c, 2) per run of c equal keys.)
+constexpr int C4_WARPS = 4;
 constexpr int C4_WARP_SLOTS = 512;
 constexpr uint32_t C4_WARP_UB = C4_WARP_SLOTS / 2;
 constexpr uint64_t C4_SENTINEL = ~0ull;
@@ -455,9 +459,11 @@ __device__ __forceinline__ uint64_t c4_bound(const DevGraph& g, int32_t x, int64
   return ub;
 }
 
-// Per node: its bound when above the warp tier's (its slots for the sort),
-// else 0. One warp per node.
-__global__ void k_c4_bound(const DevGraph g, uint32_t warp_ub, uint64_t* __restrict__ out) {
+// Per node: its bound when above the warp tier's bound (its slots of the
+// heavy tier), else 0; and into light, its bound when in [2, warp_ub], else
+// 0. One warp per node.
+__global__ void k_c4_bound(const DevGraph g, uint32_t warp_ub, uint64_t* __restrict__ out,
+                           uint16_t* __restrict__ light) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -465,44 +471,86 @@ __global__ void k_c4_bound(const DevGraph g, uint32_t warp_ub, uint64_t* __restr
     const int32_t x = (int32_t)x64;
     const int64_t ox = g.off2[x];
     const uint64_t ub = c4_bound(g, x, ox, (int32_t)(g.off2[x + 1] - ox));
-    if (lane == 0) out[x] = ub > warp_ub ? ub : 0;
+    if (lane == 0) {
+      out[x] = ub > warp_ub ? ub : 0;
+      light[x] = (ub >= 2 && ub <= warp_ub) ? (uint16_t)ub : (uint16_t)0;
+    }
   }
 }
 
-// Warp tier: one warp per node with a bound in [2, warp_ub].
+// Warp tier: the nodes with a bound ub in [2, warp_ub] (light[x] = ub, else
+// 0), one warp per node. A warp reads the bounds of 32 consecutive nodes and
+// takes its active ones in turn. It stages x's lower-ranked neighbours y (at
+// most ub of them, each with d(y) >= 1) with the exclusive prefix of their
+// degrees, then its lanes take the ub paths in turn (lane l the paths l,
+// l + 32, ...), each finding its y by binary search in the prefix, so that a
+// lane's work is ub / 32 paths whatever the degrees.
 __global__ void __launch_bounds__(C4_WARPS * 32)
-    k_c4_warp(const DevGraph g, int32_t nodes_per_graph, uint32_t warp_ub,
+    k_c4_warp(const DevGraph g, const uint16_t* __restrict__ light, int32_t nodes_per_graph,
               unsigned long long* __restrict__ agg) {
   __shared__ int32_t keys_s[C4_WARPS][C4_WARP_SLOTS];
   __shared__ uint32_t cnt_s[C4_WARPS][C4_WARP_SLOTS];
+  __shared__ int64_t off_s[C4_WARPS][C4_WARP_UB];
+  __shared__ uint32_t pre_s[C4_WARPS][C4_WARP_UB];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int32_t* keys = keys_s[wid];
   uint32_t* cnt = cnt_s[wid];
+  int64_t* soff = off_s[wid];
+  uint32_t* spre = pre_s[wid];
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   C4Sum acc;
-  for (int64_t x64 = gw; x64 < g.n; x64 += warps) {
-    const int32_t x = (int32_t)x64;
+  for (int64_t c0 = gw * 32; c0 < g.n; c0 += warps * 32) {
+   const uint32_t mine = c0 + lane < g.n ? light[c0 + lane] : 0u;
+   unsigned act = __ballot_sync(0xffffffffu, mine != 0);
+   while (act) {
+    const int src = __ffs(act) - 1;
+    act &= act - 1;
+    const int32_t x = (int32_t)(c0 + src);
+    const uint32_t ub = __shfl_sync(0xffffffffu, mine, src);
     const int64_t ox = g.off2[x];
     const int32_t dx = (int32_t)(g.off2[x + 1] - ox);
-    const uint64_t ub = c4_bound(g, x, ox, dx);
-    if (ub < 2 || ub > warp_ub) continue;  // no 4-cycle at x / counted by sort
-    const int lg = c4_lg((uint32_t)ub);
+    const int lg = c4_lg(ub);
     for (int i = lane; i < (1 << lg); i += 32) {
       keys[i] = -1;
       cnt[i] = 0;
     }
-    __syncwarp();
-    for (int32_t i = lane; i < dx; i += 32) {
-      const int32_t y = g.adj2[ox + i];
-      const int32_t dy = degree(g, y);
-      if (!lower_rank(dy, y, dx, x)) continue;
-      const int64_t oy = g.off2[y];
-      for (int32_t k = 0; k < dy; ++k) {
-        const int32_t z = g.adj2[oy + k];
-        if (z == x) continue;
-        if (lower_rank(degree(g, z), z, dx, x)) c4_insert(keys, cnt, lg, z);
+    uint32_t m = 0, run = 0;  // staged neighbours, their degree sum (warp-uniform)
+    for (int32_t i0 = 0; i0 < dx; i0 += 32) {
+      const int32_t i = i0 + lane;
+      uint32_t v = 0;
+      int64_t oy = 0;
+      if (i < dx) {
+        const int32_t y = g.adj2[ox + i];
+        oy = g.off2[y];
+        const int32_t dy = (int32_t)(g.off2[y + 1] - oy);
+        if (lower_rank(dy, y, dx, x)) v = (uint32_t)dy;
       }
+      const unsigned b = __ballot_sync(0xffffffffu, v != 0);
+      uint32_t incl = v;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += u;
+      }
+      if (v) {
+        const uint32_t at = m + __popc(b & ((1u << lane) - 1u));
+        soff[at] = oy;
+        spre[at] = run + incl - v;
+      }
+      m += __popc(b);
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncwarp();
+    for (uint32_t sl = lane; sl < run; sl += 32) {
+      uint32_t lo = 0, hi = m;
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (spre[mid] <= sl) lo = mid;
+        else hi = mid;
+      }
+      const int32_t z = g.adj2[soff[lo] + (sl - spre[lo])];
+      if (z != x && lower_rank(degree(g, z), z, dx, x)) c4_insert(keys, cnt, lg, z);
     }
     __syncwarp();
     uint64_t sum = 0;
@@ -514,6 +562,7 @@ __global__ void __launch_bounds__(C4_WARPS * 32)
     for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if (lane == 0) acc.add(agg, x / nodes_per_graph, sum);
     __syncwarp();
+   }
   }
   if (lane == 0) acc.flush(agg);
 }
@@ -627,39 +676,64 @@ __global__ void __launch_bounds__(C4E_THREADS)
   }
 }
 
-// Table tier (the default for heavy nodes): one block per node x, paths
-// enumerated as in k_c4_emit, but each endpoint z goes into x's own
-// open-addressing table of 2 * ub(x) slots, [2 ws[x], 2 ws[x+1]) of `table`
-// (slot = (z << 32) | count, empty = all ones; a match adds 1 to the count
-// word, which never carries into z). After the block's inserts, the block
-// sums C(count, 2) over its table: the 4-cycles at x. A table holds at most
-// ub(x) keys in 2 ub(x) slots, so every probe ends.
+// Table tier (the default for heavy nodes). Node x's paths own the slots
+// [ws[x], ws[x+1]) of one path space, which is cut into pieces of C4T_PIECE
+// consecutive slots, one block per piece, so that a node with many paths is
+// spread over many blocks and every block has the same work. For each node
+// its piece overlaps, the block stages x's lower-ranked neighbours (rounds of
+// C4E_CAP, degree prefix as in k_c4_emit), walks the overlapped slots and
+// puts each kept endpoint z into x's open-addressing table of 2 (ws[x+1] -
+// ws[x]) slots at [2 ws[x], 2 ws[x+1]) (slot = (z << 32) | count, empty = all
+// ones; a match adds 1 to the count word, which never carries into z). A
+// table holds at most ws[x+1] - ws[x] keys in twice as many slots, so every
+// probe ends. k_c4_sum then adds C(count, 2) over all tables.
+constexpr uint32_t C4T_PIECE = 4096;
+
+// The node x with ws[x] <= pos < ws[x + 1] (ws is nondecreasing, ws[0] = 0 <=
+// pos < ws[n]), by a 32-way search of one warp; every lane returns it.
+__device__ __forceinline__ int64_t c4_owner(const uint64_t* __restrict__ ws, int64_t n,
+                                            uint64_t pos) {
+  const int lane = threadIdx.x & 31;
+  int64_t lo = 0, hi = n;  // ws[lo] <= pos < ws[hi]
+  while (hi - lo > 1) {
+    const int64_t step = (hi - lo + 31) / 32;
+    const int64_t idx = min(lo + lane * step, hi);
+    const unsigned ok = __ballot_sync(0xffffffffu, ws[idx] <= pos);  // lane 0 always
+    const int l = 31 - __clz(ok);
+    const int64_t nlo = lo + l * step;
+    hi = min(nlo + step, hi);
+    lo = nlo;
+  }
+  return lo;
+}
+
 __global__ void __launch_bounds__(C4E_THREADS)
-    k_c4_table(const DevGraph g, const uint64_t* __restrict__ ws, int32_t nodes_per_graph,
-               unsigned long long* __restrict__ table, unsigned long long* __restrict__ agg) {
+    k_c4_table(const DevGraph g, const uint64_t* __restrict__ ws, uint64_t total,
+               unsigned long long* __restrict__ table) {
   __shared__ int64_t s_off[C4E_CAP];
   __shared__ uint32_t s_pre[C4E_CAP];
   __shared__ uint32_t s_wsum[C4E_THREADS / 32];
-  __shared__ int32_t s_heavy[C4E_THREADS];
-  __shared__ int s_nheavy;
   __shared__ uint32_t s_total;
-  __shared__ unsigned long long s_sum[C4E_THREADS / 32];
+  __shared__ int64_t s_x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  C4Sum acc;
-  for (int64_t c0 = (int64_t)blockIdx.x * C4E_THREADS; c0 < g.n;
-       c0 += (int64_t)gridDim.x * C4E_THREADS) {
-    if (threadIdx.x == 0) s_nheavy = 0;
-    __syncthreads();
-    const int64_t xi = c0 + threadIdx.x;
-    if (xi < g.n && ws[xi + 1] != ws[xi]) s_heavy[atomicAdd(&s_nheavy, 1)] = (int32_t)xi;
-    __syncthreads();
-    const int nh = s_nheavy;
-    for (int hh = 0; hh < nh; ++hh) {
-      const int32_t x = s_heavy[hh];
+  for (uint64_t p0 = (uint64_t)blockIdx.x * C4T_PIECE; p0 < total;
+       p0 += (uint64_t)gridDim.x * C4T_PIECE) {
+    const uint64_t p1 = min(p0 + (uint64_t)C4T_PIECE, total);
+    uint64_t pos = p0;
+    while (pos < p1) {
+      if (wid == 0) {
+        const int64_t xo = c4_owner(ws, g.n, pos);
+        if (lane == 0) s_x = xo;
+      }
+      __syncthreads();
+      const int32_t x = (int32_t)s_x;
+      const uint64_t wx = ws[x], wx1 = ws[x + 1];
+      const uint64_t a = pos - wx, e = min(p1, wx1) - wx;  // x's local slots [a, e)
       const int64_t ox = g.off2[x];
       const int32_t dx = (int32_t)(g.off2[x + 1] - ox);
-      const uint64_t tb = 2 * ws[x], tcap = 2 * (ws[x + 1] - ws[x]);
-      for (int32_t r0 = 0; r0 < dx; r0 += C4E_CAP) {
+      const uint64_t tb = 2 * wx, tcap = 2 * (wx1 - wx);
+      uint64_t base = 0;  // local slot of the round's first path
+      for (int32_t r0 = 0; r0 < dx && base < e; r0 += C4E_CAP) {
         const int32_t cnt = min(C4E_CAP, dx - r0);
         uint32_t v[2];
         int64_t o[2];
@@ -711,60 +785,61 @@ __global__ void __launch_bounds__(C4E_THREADS)
           ex += v[q];
         }
         __syncthreads();
-        const uint32_t total = s_total;
-        for (uint32_t sl = threadIdx.x; sl < total; sl += C4E_THREADS) {
+        const uint64_t rt = s_total;
+        // the round's slots [base, base + rt) cut to [a, e)
+        const uint64_t lo_s = a > base ? a - base : 0;
+        const uint64_t hi_s = min(e, base + rt) > base ? min(e, base + rt) - base : 0;
+        for (uint64_t sl = lo_s + threadIdx.x; sl < hi_s; sl += C4E_THREADS) {
           int lo = 0, hi2 = cnt;
           while (hi2 - lo > 1) {
             const int mid = (lo + hi2) >> 1;
-            if (s_pre[mid] <= sl) lo = mid;
+            if (s_pre[mid] <= (uint32_t)sl) lo = mid;
             else hi2 = mid;
           }
-          const int32_t z = g.adj2[s_off[lo] + (sl - s_pre[lo])];
+          const int32_t z = g.adj2[s_off[lo] + ((uint32_t)sl - s_pre[lo])];
           if (z == x || !lower_rank(degree(g, z), z, dx, x)) continue;
           const unsigned long long key = (unsigned long long)(uint32_t)z << 32;
           uint64_t slot = __umul64hi(mix64((uint64_t)(uint32_t)z), tcap);
           for (uint64_t it = 0; it < tcap; ++it) {
             unsigned long long* p = table + tb + slot;
-            const unsigned long long cur = *p;
-            if (cur == ~0ull) {
-              const unsigned long long prev = atomicCAS(p, ~0ull, key | 1ull);
-              if (prev == ~0ull) break;
-              if ((prev >> 32) == (uint32_t)z) {
-                atomicAdd(p, 1ull);
-                break;
-              }
-            } else if ((cur >> 32) == (uint32_t)z) {
+            const unsigned long long prev = atomicCAS(p, ~0ull, key | 1ull);
+            if (prev == ~0ull) break;
+            if ((prev >> 32) == (uint32_t)z) {
               atomicAdd(p, 1ull);
               break;
             }
             if (++slot == tcap) slot = 0;
           }
         }
+        base += rt;
         __syncthreads();  // the next round overwrites the staged neighbours
       }
-      // the block's inserts are done (the barrier above): sum C(c, 2) over
-      // x's table, read from L2 where the atomics landed
-      unsigned long long sum = 0;
-      for (uint64_t sl = threadIdx.x; sl < tcap; sl += C4E_THREADS) {
-        const unsigned long long v2 = __ldcg(table + tb + sl);
-        if (v2 != ~0ull) {
-          const unsigned long long c = v2 & 0xFFFFFFFFull;
-          sum += c * (c - 1) / 2;
-        }
-      }
-#pragma unroll
-      for (int o2 = 16; o2; o2 >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
-      if (lane == 0) s_sum[wid] = sum;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-        for (int w = 0; w < C4E_THREADS / 32; ++w) t += s_sum[w];
-        acc.add(agg, x / nodes_per_graph, t);
-      }
-      __syncthreads();
+      pos = wx + e;
     }
   }
-  if (threadIdx.x == 0) acc.flush(agg);
+}
+
+// C(count, 2) over every table slot; a slot's graph is that of its z.
+__global__ void k_c4_sum(const unsigned long long* __restrict__ table, uint64_t nslots,
+                         int32_t nodes_per_graph, unsigned long long* __restrict__ agg) {
+  C4Sum acc;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nslots;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const unsigned long long v = table[i];
+    if (v == ~0ull) continue;
+    const uint64_t c = v & 0xFFFFFFFFull;
+    if (c > 1) acc.add(agg, (int64_t)(v >> 32) / nodes_per_graph, c * (c - 1) / 2);
+  }
+  const int lane = threadIdx.x & 31;
+  const int64_t g0 = __shfl_sync(0xffffffffu, acc.gcur, 0);
+  if (__all_sync(0xffffffffu, acc.gcur == g0 || acc.gcur < 0 || acc.s == 0)) {
+    uint64_t sum = acc.s;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0 && g0 >= 0 && sum) atomicAdd(&agg[g0 * NAGG + 6], (unsigned long long)(2 * sum));
+  } else {
+    acc.flush(agg);
+  }
 }
 
 // Sort tier, counting: each run of c equal keys (c paths from x to one z)
@@ -930,9 +1005,13 @@ void graphlet_prepare(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
 
 void c4_bounds(hm_graph* g, uint64_t* out, cudaStream_t s) {
   g->c4_warp_ub = c4_warp_bound();
+  if (!g->c4_light) {
+    g->c4_light = dalloc<uint16_t>((size_t)g->n, s);
+    g->owned.push_back(g->c4_light);
+  }
   const uint64_t want = ((uint64_t)g->n * 32 + 255) / 256;
   k_c4_bound<<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, 152 * 8)), 256, 0, s>>>(
-      g->view(), g->c4_warp_ub, out);
+      g->view(), g->c4_warp_ub, out, g->c4_light);
   HM_KCHECK();
 }
 
@@ -961,22 +1040,24 @@ void graphlet_edges(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
 
 void graphlet_pairs(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
   if (!g->bits2) {
-    // warp tier over all nodes, then the sort tier over the heavy nodes (a
+    // warp tier over all nodes, then the heavy tier over the heavy nodes (a
     // trace span per stage)
-    const uint64_t want = ((uint64_t)g->n * 32 + C4_WARPS * 32 - 1) / (C4_WARPS * 32);
-    const unsigned wblocks = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, 152 * 6));
+    const uint64_t want = ((uint64_t)g->n + C4_WARPS * 32 - 1) / (C4_WARPS * 32);
+    const unsigned wblocks = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, 152 * 7));
     TraceSpan sw("census_c4_warp", s);
-    k_c4_warp<<<wblocks, C4_WARPS * 32, 0, s>>>(g->view(), G.per, g->c4_warp_ub, G.agg);
+    k_c4_warp<<<wblocks, C4_WARPS * 32, 0, s>>>(g->view(), g->c4_light, G.per, G.agg);
     HM_KCHECK();
     sw.end();
     const uint64_t nk = g->C4.total;
     if (nk && !c4_sort_tier()) {
-      const uint64_t eb = std::min<uint64_t>(((uint64_t)g->n + C4E_THREADS - 1) / C4E_THREADS,
-                                             152 * 4);
       TraceSpan st("census_c4_table", s);
-      HM_CUDA(cudaMemsetAsync(G.c4_keys, 0xFF, 2 * nk * sizeof(uint64_t), s));
-      k_c4_table<<<(unsigned)std::max<uint64_t>(1, eb), C4E_THREADS, 0, s>>>(
-          g->view(), g->C4.ws, G.per, (unsigned long long*)G.c4_keys, G.agg);
+      unsigned long long* tab = reinterpret_cast<unsigned long long*>(G.c4_keys);
+      HM_CUDA(cudaMemsetAsync(tab, 0xFF, 2 * nk * sizeof(uint64_t), s));
+      const uint64_t pieces = (nk + C4T_PIECE - 1) / C4T_PIECE;
+      k_c4_table<<<(unsigned)std::min<uint64_t>(pieces, 1u << 30), C4E_THREADS, 0, s>>>(
+          g->view(), g->C4.ws, nk, tab);
+      HM_KCHECK();
+      k_c4_sum<<<grid_n(2 * nk), 256, 0, s>>>(tab, 2 * nk, G.per, G.agg);
       HM_KCHECK();
       st.end();
     } else if (nk) {

@@ -452,15 +452,17 @@ struct GraphletScratch {
   int ngraphs = 1;
   int32_t per = 0;
   // graphs without pair bitmaps: per-warp lists of common neighbours (cap
-  // entries each); the paths of the nodes whose 4-cycles are counted by sort
+  // entries each); the heavy tier's tables (2 C4.total slots), or with
+  // HM_C4_SORT=1 its path keys (C4.total)
   int32_t* lists = nullptr;
   int64_t cap = 0;
-  uint64_t* c4_keys = nullptr;  // the heavy nodes' 4-cycle paths (C4.total keys)
+  uint64_t* c4_keys = nullptr;
 };
 void graphlet_prepare(const hm_graph* g, GraphletScratch& G, cudaStream_t s);
-// Per node of a graph without pair bitmaps, the 4-cycle paths it emits for
-// counting by sort: its path bound when above the warp tier's, else 0.
-// The bound in force is kept in the graph (the census splits the nodes by it).
+// Per node of a graph without pair bitmaps, the 4-cycle paths of the heavy
+// tier: its path bound when above the warp tier's, else 0; the warp tier's
+// bounds go to g->c4_light. The bound in force is kept in the graph (the
+// census splits the nodes by it).
 void c4_bounds(hm_graph* g, uint64_t* out, cudaStream_t s);
 void graphlet_edges(const hm_graph* g, GraphletScratch& G, cudaStream_t s);
 void graphlet_pairs(const hm_graph* g, GraphletScratch& G, cudaStream_t s);
@@ -515,11 +517,12 @@ struct hm_graph {
   Space Wb, Sb, Pb;
   // bit-sliced TX: items are (3-hyperedge, 4-word group of the rows)
   Space TXb;
-  // graphs without pair bitmaps: per node, the 4-cycle paths it emits for
-  // counting by sort (its path bound when above the warp tier's bound
-  // c4_warp_ub, else 0)
+  // graphs without pair bitmaps: per node, the 4-cycle paths of the heavy
+  // tier (its path bound when above the warp tier's bound c4_warp_ub, else 0)
   Space C4;
   uint32_t c4_warp_ub = 0;
+  // per node, its path bound when in [2, c4_warp_ub] (the warp tier's nodes), else 0
+  uint16_t* c4_light = nullptr;
   bool useWb = false, useSb = false, usePb = false, useTXb = false;
   // order 4: pairs-only sets from graphlet identities instead of S and P
   bool useGL = false;
