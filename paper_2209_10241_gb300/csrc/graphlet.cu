@@ -309,57 +309,233 @@ __global__ void k_graphlet_pairs(const DevGraph g, int32_t nodes_per_graph,
   }
 }
 
-// Graphs without pair bitmaps. One warp per pair (u < v): t(e) by hash probes
-// of the shorter adjacency list against the other endpoint; the common
-// neighbours w > v, in ascending order, go to the warp's list (capacity = the
-// largest pair degree) and every pair of them that is itself a pair closes a
-// 4-clique with u and v.
+// Graphs without pair bitmaps: the pair sums from the triangles and 4-cliques,
+// each found once at its lowest-ranked node u (rank = (degree, id), as in the
+// 4-cycle pass) among u's neighbours of higher rank, out(u): a triangle is a
+// pair of out(u) that is itself a pair, a 4-clique a triple of out(u) whose
+// three pairs are pairs. Ranked this way out(u) is short (at most
+// sqrt(2 m2)), so this probes far fewer pairs than intersecting the two
+// neighbour lists of every pair. A triangle adds 1 to t(e) of its three
+// pairs (a counter per slot of the pair hash set, tslot) and 2 to tnode of
+// its three nodes; every pair (u, v), v in out(u), adds (d(u) - 1)(d(v) - 1)
+// once; k_graphlet_tslots then sums C(t(e), 2) over the slots.
+//   d(u) <= GLT_SMALL: a lane per node, out(u) in shared memory, and the
+//   pairs of the warp's 32 nodes spread over its lanes;
+//   larger: the whole warp per node, out(u) in the warp's global list
+//   (capacity = the largest degree); 4-cliques from adjacency rows of out(u)
+//   in shared memory when |out(u)| <= GLT_ROWS, else by probing each
+//   triangle's later members of out(u).
+// rank order of the sparse passes: (degree, id)
+__device__ __forceinline__ bool lower_rank(int32_t dz, int32_t z, int32_t dx, int32_t x) {
+  return dz < dx || (dz == dx && z < x);
+}
+
+constexpr int GLT_SMALL = 8;
+constexpr int GLT_ROWS = 128;
+constexpr int GLT_WORDS = GLT_ROWS / 32;
+
+__device__ __forceinline__ int64_t pair_slot(const DevGraph& g, int32_t a, int32_t b) {
+  const uint64_t key = pair_key(a, b);
+  uint64_t slot = hash_pair(key) & g.h2_mask;
+  for (uint64_t it = 0; it <= g.h2_mask; ++it) {
+    const uint64_t v = __ldg(g.h2 + slot);
+    if (v == key) return (int64_t)slot;
+    if (v == EMPTY64) return -1;
+    slot = (slot + 1) & g.h2_mask;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ void pair_sums_put(PairSums& P, unsigned long long* agg, int32_t gi,
+                                              int i, uint64_t x) {
+  if (gi != P.gi) {
+    pair_sums_flush(agg, P);
+    P = PairSums{};
+    P.gi = gi;
+  }
+  P.v[i] += x;
+}
+
+// Triangle {u, v, w} found at u; s_vw is the slot of the pair (v, w).
+__device__ __forceinline__ void triangle_at(const DevGraph& g, uint32_t* tslot, uint32_t* tnode,
+                                            int32_t u, int32_t v, int32_t w, int64_t s_vw) {
+  atomicAdd(&tslot[s_vw], 1u);
+  const int64_t s_uv = pair_slot(g, u, v), s_uw = pair_slot(g, u, w);
+  if (s_uv >= 0) atomicAdd(&tslot[s_uv], 1u);
+  if (s_uw >= 0) atomicAdd(&tslot[s_uw], 1u);
+  atomicAdd(&tnode[u], 2u);
+  atomicAdd(&tnode[v], 2u);
+  atomicAdd(&tnode[w], 2u);
+}
+
 __global__ void __launch_bounds__(SPARSE_WARPS * 32)
-    k_graphlet_edges_sparse(const DevGraph g, int32_t* __restrict__ lists, int64_t cap,
-                                        uint32_t* __restrict__ tnode,
-                                        unsigned long long* __restrict__ agg) {
-  const int lane = threadIdx.x & 31;
+    k_graphlet_tri(const DevGraph g, int32_t* __restrict__ lists, int64_t cap,
+                   uint32_t* __restrict__ tslot, uint32_t* __restrict__ tnode,
+                   unsigned long long* __restrict__ agg) {
+  __shared__ int32_t out_s[SPARSE_WARPS][32][GLT_SMALL];
+  __shared__ uint32_t adj_s[SPARSE_WARPS][32][GLT_SMALL];
+  __shared__ uint32_t pre_s[SPARSE_WARPS][32];
+  __shared__ uint32_t row_s[SPARSE_WARPS][GLT_ROWS][GLT_WORDS];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   int32_t* list = lists + gw * cap;
+  int32_t(*outl)[GLT_SMALL] = out_s[wid];
+  uint32_t(*adjm)[GLT_SMALL] = adj_s[wid];
+  uint32_t* pre = pre_s[wid];
+  uint32_t(*row)[GLT_WORDS] = row_s[wid];
   PairSums P;
-  for (int64_t p = gw; p < g.m2; p += warps) {
-    const int32_t u = (int32_t)(g.e2[p] >> 32), v = (int32_t)(g.e2[p] & 0xFFFFFFFFull);
-    const int32_t du = degree(g, u), dv = degree(g, v);
-    const int32_t a = du <= dv ? u : v, b = du <= dv ? v : u, da = du <= dv ? du : dv;
-    const int64_t oa = g.off2[a];
-    uint32_t t = 0;
-    int count = 0;
-    for (int32_t i0 = 0; i0 < da; i0 += 32) {
-      const int32_t i = i0 + lane;
-      const int32_t w = i < da ? g.adj2[oa + i] : -1;
-      const bool common = w >= 0 && w != b && has_pair(g, b, w);
-      t += common ? 1u : 0u;
-      const bool keep = common && w > v;
-      const unsigned bal = __ballot_sync(0xffffffffu, keep);
-      if (keep) list[count + __popc(bal & lt)] = w;
-      count += __popc(bal);
+  for (int64_t c0 = gw * 32; c0 < g.n; c0 += warps * 32) {
+    const int64_t ul = c0 + lane;
+    const int32_t u = (int32_t)ul;
+    int32_t du = 0;
+    int64_t ou = 0;
+    if (ul < g.n) {
+      ou = g.off2[u];
+      du = (int32_t)(g.off2[u + 1] - ou);
     }
-    __syncwarp();
-    uint64_t k4 = 0;
-    for (int i = lane; i < count; i += 32) {
-      const int32_t wi = list[i];
-      for (int j = i + 1; j < count; ++j) k4 += has_pair(g, wi, list[j]) ? 1u : 0u;
+    const bool small = du <= GLT_SMALL;
+    int k = 0;
+    if (small) {
+      const int32_t gu = du ? graph_of(g, u) : 0;
+      for (int i = 0; i < du; ++i) {
+        const int32_t y = g.adj2[ou + i];
+        const int32_t dy = degree(g, y);
+        if (lower_rank(du, u, dy, y)) {
+          pair_sums_put(P, agg, gu, 0, (uint64_t)(du - 1) * (uint64_t)(dy - 1));
+          outl[lane][k] = y;
+          adjm[lane][k] = 0u;
+          ++k;
+        }
+      }
     }
-    __syncwarp();
+    // the pairs of the small nodes' out-lists, spread over the lanes
+    const uint32_t np = (uint32_t)(k * (k - 1) / 2);
+    uint32_t incl = np;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      t += __shfl_xor_sync(0xffffffffu, t, o);
-      k4 += __shfl_xor_sync(0xffffffffu, k4, o);
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
     }
-    if (lane == 0) {
-      atomicAdd(&tnode[u], t);
-      atomicAdd(&tnode[v], t);
-      pair_sums_add(P, agg, graph_of(g, u), (uint64_t)du, (uint64_t)dv, t, k4);
+    pre[lane] = incl - np;
+    const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+    __syncwarp();
+    for (uint32_t p = lane; p < tot; p += 32) {
+      int lo = 0, hi = 32;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= p) lo = mid;
+        else hi = mid;
+      }
+      uint32_t i, j;
+      fam::unrank2(p - pre[lo], i, j);
+      const int32_t v = outl[lo][i], w = outl[lo][j];
+      const int64_t s_vw = pair_slot(g, v, w);
+      if (s_vw < 0) continue;
+      const int32_t uo = (int32_t)(c0 + lo);
+      triangle_at(g, tslot, tnode, uo, v, w, s_vw);
+      pair_sums_put(P, agg, graph_of(g, uo), 1, 3);
+      atomicOr(&adjm[lo][i], 1u << j);
+      atomicOr(&adjm[lo][j], 1u << i);
+    }
+    __syncwarp();
+    if (k >= 3) {  // 4-cliques at a small node: i < j < l, all three pairs present
+      uint64_t k4 = 0;
+      for (int i = 0; i < k; ++i) {
+        uint32_t mi = adjm[lane][i] & ~((2u << i) - 1u);
+        while (mi) {
+          const int j = __ffs(mi) - 1;
+          mi &= mi - 1;
+          k4 += __popc(adjm[lane][i] & adjm[lane][j] & ~((2u << j) - 1u));
+        }
+      }
+      if (k4) pair_sums_put(P, agg, graph_of(g, u), 3, k4);
+    }
+    __syncwarp();
+    // the other nodes, one at a time with the whole warp
+    unsigned bigs = __ballot_sync(0xffffffffu, !small);
+    while (bigs) {
+      const int src = __ffs(bigs) - 1;
+      bigs &= bigs - 1;
+      const int32_t x = (int32_t)(c0 + src);
+      const int32_t dx = __shfl_sync(0xffffffffu, du, src);
+      const int64_t ox = __shfl_sync(0xffffffffu, ou, src);
+      const int32_t gx = graph_of(g, x);
+      int kx = 0;
+      for (int32_t i0 = 0; i0 < dx; i0 += 32) {
+        const int32_t i = i0 + lane;
+        int32_t y = 0;
+        bool higher = false;
+        if (i < dx) {
+          y = g.adj2[ox + i];
+          const int32_t dy = degree(g, y);
+          higher = lower_rank(dx, x, dy, y);
+          if (higher) pair_sums_put(P, agg, gx, 0, (uint64_t)(dx - 1) * (uint64_t)(dy - 1));
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, higher);
+        if (higher) list[kx + __popc(b & lt)] = y;
+        kx += __popc(b);
+      }
+      const bool rows = kx <= GLT_ROWS;
+      if (rows)
+        for (int r = lane; r < kx * GLT_WORDS; r += 32) row[r / GLT_WORDS][r % GLT_WORDS] = 0u;
+      __syncwarp();
+      const uint64_t npx = (uint64_t)kx * (uint64_t)(kx - 1) / 2;
+      for (uint64_t p = lane; p < npx; p += 32) {
+        uint32_t i, j;
+        fam::unrank2(p, i, j);
+        const int32_t v = list[i], w = list[j];
+        const int64_t s_vw = pair_slot(g, v, w);
+        if (s_vw < 0) continue;
+        triangle_at(g, tslot, tnode, x, v, w, s_vw);
+        pair_sums_put(P, agg, gx, 1, 3);
+        if (rows) {
+          atomicOr(&row[i][j >> 5], 1u << (j & 31));
+          atomicOr(&row[j][i >> 5], 1u << (i & 31));
+        } else {
+          uint64_t k4 = 0;
+          for (int l = (int)j + 1; l < kx; ++l) {
+            const int32_t z = list[l];
+            if (has_pair(g, v, z) && has_pair(g, w, z)) ++k4;
+          }
+          if (k4) pair_sums_put(P, agg, gx, 3, k4);
+        }
+      }
+      __syncwarp();
+      if (rows && kx >= 3) {
+        uint64_t k4 = 0;
+        for (uint64_t p = lane; p < npx; p += 32) {
+          uint32_t i, j;
+          fam::unrank2(p, i, j);
+          if (!((row[i][j >> 5] >> (j & 31)) & 1u)) continue;
+          for (uint32_t wd = j >> 5; wd < GLT_WORDS; ++wd) {
+            uint32_t m = row[i][wd] & row[j][wd];
+            if (wd == (j >> 5)) m &= ~((2u << (j & 31)) - 1u);
+            k4 += __popc(m);
+          }
+        }
+        if (k4) pair_sums_put(P, agg, gx, 3, k4);
+      }
+      __syncwarp();
     }
   }
-  pair_sums_block<SPARSE_WARPS>(P, agg);
+  pair_sums_groups<SPARSE_WARPS * 32>(P, threadIdx.x, true, agg);
+}
+
+// C(t(e), 2) over the slots of the pair hash set, into the pair's graph.
+__global__ void k_graphlet_tslots(const DevGraph g, const uint32_t* __restrict__ tslot,
+                                  unsigned long long* __restrict__ agg) {
+  PairSums P;
+  const uint64_t slots = g.h2_mask + 1;
+  for (uint64_t sl = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; sl < slots;
+       sl += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t t = tslot[sl];
+    if (t < 2) continue;
+    const int32_t a = (int32_t)(__ldg(g.h2 + sl) >> 32);
+    pair_sums_put(P, agg, graph_of(g, a), 2, t * (t - 1) / 2);
+  }
+  pair_sums_flush(agg, P);
 }
 
 // 4-cycles of graphs without pair bitmaps, each at its highest-ranked node x
@@ -401,9 +577,6 @@ uint32_t c4_warp_bound() {
   return w;
 }
 
-__device__ __forceinline__ bool lower_rank(int32_t dz, int32_t z, int32_t dx, int32_t x) {
-  return dz < dx || (dz == dx && z < x);
-}
 
 // Counts z in a table of 2^lg slots (keys -1 = empty). Every table holds
 // fewer distinct keys than slots, so a probe always ends; the bound on the
@@ -983,7 +1156,9 @@ void graphlet_prepare(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
   G.per = g->block ? g->block : g->n;
   const size_t tb = ((size_t)g->n * 4 + 255) & ~(size_t)255;
   const size_t ab = ((size_t)G.ngraphs * NAGG * 8 + 255) & ~(size_t)255;
-  size_t zero = tb + ab, extra = 0;
+  // graphs without pair bitmaps: a triangle counter per slot of the pair hash set
+  const size_t sb = g->bits2 || !g->counts[2] ? 0 : ((size_t)(g->h2_mask + 1) * 4 + 255) & ~(size_t)255;
+  size_t zero = tb + ab + sb, extra = 0;
   size_t keyb = 0;
   if (!g->bits2) {
     // the sort tier's path keys, then the per-warp pair lists
@@ -996,6 +1171,7 @@ void graphlet_prepare(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
   G.buf.alloc(zero + extra, s);
   G.tnode = reinterpret_cast<uint32_t*>(G.buf.p);
   G.agg = reinterpret_cast<unsigned long long*>(G.buf.p + tb);
+  G.tslot = sb ? reinterpret_cast<uint32_t*>(G.buf.p + tb + ab) : nullptr;
   if (!g->bits2) {
     G.c4_keys = g->C4.total ? reinterpret_cast<uint64_t*>(G.buf.p + zero) : nullptr;
     G.lists = reinterpret_cast<int32_t*>(G.buf.p + zero + keyb);
@@ -1019,9 +1195,13 @@ void graphlet_edges(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
   if (g->counts[2] == 0) return;
   TraceSpan span("census_gl_edges", s);
   if (!g->bits2) {
-    const uint64_t want = ((uint64_t)g->counts[2] * 32 + 255) / 256;
+    // 32 nodes per warp
+    const uint64_t want = ((uint64_t)g->n + SPARSE_WARPS * 32 - 1) / (SPARSE_WARPS * 32);
     const unsigned blocks = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, SPARSE_EDGE_BLOCKS));
-    k_graphlet_edges_sparse<<<blocks, SPARSE_WARPS * 32, 0, s>>>(g->view(), G.lists, G.cap, G.tnode, G.agg);
+    k_graphlet_tri<<<blocks, SPARSE_WARPS * 32, 0, s>>>(g->view(), G.lists, G.cap, G.tslot,
+                                                       G.tnode, G.agg);
+    HM_KCHECK();
+    k_graphlet_tslots<<<grid_n(g->h2_mask + 1), 256, 0, s>>>(g->view(), G.tslot, G.agg);
     HM_KCHECK();
     span.end();
     return;

@@ -449,6 +449,7 @@ struct GraphletScratch {
   DBuf<unsigned char> buf;
   uint32_t* tnode = nullptr;
   unsigned long long* agg = nullptr;
+  uint32_t* tslot = nullptr;  // graphs without pair bitmaps: triangles per pair-set slot
   int ngraphs = 1;
   int32_t per = 0;
   // graphs without pair bitmaps: per-warp lists of common neighbours (cap
