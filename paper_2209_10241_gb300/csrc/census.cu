@@ -405,8 +405,11 @@ __global__ void k_ws_all(const int64_t* __restrict__ off2, const int64_t* __rest
 //   0-2. N(a) & N(b), N(a) & N(c), N(b) & N(c): the shorter of the two rows
 //        scanned, membership in the other by a signature test and a probe;
 //   3-5. the third nodes of the 3-hyperedges through (a, b), (a, c), (b, c):
-//        the shorter of the two members' incidence lists scanned;
-//   6.   where the three members' 4-hyperedge signatures share d's bit, the
+//        the shorter of the two members' incidence lists scanned, for the
+//        member pairs that lie in another 3-hyperedge too (the others have
+//        none);
+//   6.   where the three members' 4-hyperedge signatures share a bit and a
+//        Bloom filter of the 4-hyperedges' 3-subsets does not rule e out, the
 //        pair neighbours d of each member with Q(d) (others are found above).
 // Each special d gets its full P, T and Q by probes (a signature test first),
 // adds to the special count of every member it is a pair neighbour of, and is
@@ -493,7 +496,8 @@ __device__ __forceinline__ void txs_candidate(const DevGraph& g, const TxsAnchor
 template <int G>
 __global__ void __launch_bounds__(CENSUS_THREADS, HM_TXS_MINBLOCKS)
     k_census_txs(const DevGraph g, const int32_t* __restrict__ list,
-                 const unsigned int* __restrict__ count, const uint8_t* __restrict__ lut_g,
+                 const unsigned int* __restrict__ count, const uint8_t* __restrict__ share,
+                 const uint8_t* __restrict__ lut_g,
                  int nmask, int ncls, int sub, unsigned long long* __restrict__ hist) {
   __shared__ unsigned long long bins[BIN_STRIDE];
   __shared__ __align__(16) uint8_t lut[2048];
@@ -545,9 +549,12 @@ __global__ void __launch_bounds__(CENSUS_THREADS, HM_TXS_MINBLOCKS)
     A.pac = pb & 2u;
     A.pbc = pb & 4u;
     uint32_t sp0 = 0, sp1 = 0, sp2 = 0;
-    const int nsrc = A.s4 ? 9 : 6;
+    const uint32_t shared = share[t];
+    const int nsrc = (shared & 8u) ? 9 : 6;
 #pragma unroll 1
     for (int src = 0; src < nsrc; ++src) {
+      // a member pair inside no other 3-hyperedge has no third node to scan for
+      if (src >= 3 && src < 6 && !((shared >> (src - 3)) & 1u)) continue;
       // the source's list (group-uniform): member pair (p, q) or member x
       const int p = src < 6 ? (src % 3 == 2 ? 1 : 0) : src - 6;
       const int q = src % 3 == 0 ? 1 : 2;
@@ -615,16 +622,94 @@ __global__ void __launch_bounds__(CENSUS_THREADS, HM_TXS_MINBLOCKS)
     if (bins[i]) atomicAdd(&hist[i], bins[i]);
 }
 
+// The member pairs of the 3-hyperedges: an open-addressing set of pair keys
+// whose top bit (free: node ids are below 2^31) marks a pair inside two or
+// more 3-hyperedges. A pair inside e only has third nodes other than e's to
+// scan for (sources 3-5 of k_census_txs) when it is so marked, and few are.
+constexpr uint64_t TP_SHARED = 1ull << 63;
+
+__device__ __forceinline__ void tp_insert(unsigned long long* tab, uint64_t mask, uint64_t key) {
+  uint64_t slot = hash_pair(key) & mask;
+  for (uint64_t it = 0; it <= mask; ++it) {
+    const unsigned long long prev = atomicCAS(tab + slot, EMPTY64, key);
+    if (prev == EMPTY64) return;
+    if ((prev & ~TP_SHARED) == key) {
+      if (!(prev & TP_SHARED)) atomicOr(tab + slot, TP_SHARED);
+      return;
+    }
+    slot = (slot + 1) & mask;
+  }
+}
+
+// Whether the pair lies in two or more 3-hyperedges (true when it is not
+// found, which cannot happen for a member pair: scanning is always safe).
+__device__ __forceinline__ bool tp_shared(const unsigned long long* tab, uint64_t mask,
+                                          uint64_t key) {
+  uint64_t slot = hash_pair(key) & mask;
+  for (uint64_t it = 0; it <= mask; ++it) {
+    const unsigned long long v = tab[slot];
+    if ((v & ~TP_SHARED) == key) return (v & TP_SHARED) != 0;
+    if (v == EMPTY64) return true;
+    slot = (slot + 1) & mask;
+  }
+  return true;
+}
+
+// A Bloom filter of the 3-subsets of the 4-hyperedges (two bits of a
+// nbits-bit array per subset, nbits a power of two): a clear bit proves that
+// no 4-hyperedge contains the 3-hyperedge, so that it has no quad scan.
+__device__ __forceinline__ uint64_t tq_hash(int32_t a, int32_t b, int32_t c) {
+  return hash_tuple(a, b, c, -1);
+}
+
+__global__ void k_tq_bloom(const DevGraph g, uint32_t* __restrict__ bloom, uint32_t nbits) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.m4;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int4 e = g.e4[t];  // a < b < c < d
+    const int32_t m[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+    for (int skip = 0; skip < 4; ++skip) {
+      int32_t k3[3];
+      int j = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (i != skip) k3[j++] = m[i];
+      const uint64_t h = tq_hash(k3[0], k3[1], k3[2]);
+      const uint32_t b0 = (uint32_t)h & (nbits - 1u), b1 = (uint32_t)(h >> 32) & (nbits - 1u);
+      atomicOr(&bloom[b0 >> 5], 1u << (b0 & 31));
+      atomicOr(&bloom[b1 >> 5], 1u << (b1 & 31));
+    }
+  }
+}
+
+__global__ void k_tp_insert(const DevGraph g, unsigned long long* __restrict__ tab,
+                            uint64_t mask) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.m3;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int4 e = g.e3[t];
+    tp_insert(tab, mask, pair_key(e.x, e.y));
+    tp_insert(tab, mask, pair_key(e.x, e.z));
+    tp_insert(tab, mask, pair_key(e.y, e.z));
+  }
+}
+
 // Splits E_3 for k_census_txs: a 3-hyperedge whose every scanned list (the
-// shorter row and the shorter incidence list of each member pair, and each
-// member's row where the 4-hyperedge signatures meet) has at most
-// TXS_SMALL entries goes to the 8-lane list, the others to the warp list.
+// shorter row of each member pair, the shorter incidence list of each member
+// pair that lies in another 3-hyperedge too, and each member's row where the
+// 4-hyperedge signatures meet) has at most TXS_SMALL entries goes to the
+// 8-lane list, the others to the warp list. share[t] gets the member pairs
+// that lie in another 3-hyperedge (bit 0: (a, b), 1: (a, c), 2: (b, c)) and
+// bit 3 when the quad scans run: the members' 4-hyperedge signatures meet and
+// the Bloom filter does not rule out a 4-hyperedge containing e.
 #ifndef HM_TXS_SMALL
 #define HM_TXS_SMALL 32
 #endif
 constexpr int TXS_SMALL = HM_TXS_SMALL;
-__global__ void k_txs_split(const DevGraph g, int32_t* __restrict__ small,
-                            int32_t* __restrict__ large, unsigned int* __restrict__ counts) {
+__global__ void k_txs_split(const DevGraph g, const unsigned long long* __restrict__ tab,
+                            uint64_t mask, const uint32_t* __restrict__ bloom, uint32_t nbits,
+                            uint8_t* __restrict__ share,
+                            int32_t* __restrict__ small, int32_t* __restrict__ large,
+                            unsigned int* __restrict__ counts) {
   const int lane = threadIdx.x & 31;
   const int64_t n = (g.m3 + 31) / 32 * 32;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
@@ -639,11 +724,23 @@ __global__ void k_txs_split(const DevGraph g, int32_t* __restrict__ small,
         d2[j] = (int32_t)(g.off2[m[j] + 1] - g.off2[m[j]]);
         d3[j] = (int32_t)(g.off3[m[j] + 1] - g.off3[m[j]]);
       }
-      int32_t mx = max(max(min(d2[0], d2[1]), min(d2[0], d2[2])), min(d2[1], d2[2]));
-      mx = max(mx, max(max(min(d3[0], d3[1]), min(d3[0], d3[2])), min(d3[1], d3[2])));
+      const bool s01 = tp_shared(tab, mask, pair_key(e.x, e.y));
+      const bool s02 = tp_shared(tab, mask, pair_key(e.x, e.z));
+      const bool s12 = tp_shared(tab, mask, pair_key(e.y, e.z));
       const uint64_t s4 = g.sig[2 * (int64_t)g.n + e.x] & g.sig[2 * (int64_t)g.n + e.y] &
                           g.sig[2 * (int64_t)g.n + e.z];
-      if (s4) mx = max(mx, max(d2[0], max(d2[1], d2[2])));
+      bool quad = s4 != 0;
+      if (quad) {
+        const uint64_t h = tq_hash(e.x, e.y, e.z);
+        const uint32_t b0 = (uint32_t)h & (nbits - 1u), b1 = (uint32_t)(h >> 32) & (nbits - 1u);
+        quad = ((bloom[b0 >> 5] >> (b0 & 31)) & 1u) && ((bloom[b1 >> 5] >> (b1 & 31)) & 1u);
+      }
+      share[t] = (uint8_t)((s01 ? 1u : 0u) | (s02 ? 2u : 0u) | (s12 ? 4u : 0u) | (quad ? 8u : 0u));
+      int32_t mx = max(max(min(d2[0], d2[1]), min(d2[0], d2[2])), min(d2[1], d2[2]));
+      if (s01) mx = max(mx, min(d3[0], d3[1]));
+      if (s02) mx = max(mx, min(d3[0], d3[2]));
+      if (s12) mx = max(mx, min(d3[1], d3[2]));
+      if (quad) mx = max(mx, max(d2[0], max(d2[1], d2[2])));
       is_small = mx <= TXS_SMALL;
     }
     // warp-aggregated appends
@@ -1017,15 +1114,36 @@ void launch_txs(const hm_graph* g, unsigned long long* hist, cudaStream_t s, boo
   // persistent grids (every SM's resident blocks) read their list lengths on
   // the device
   const int64_t m3 = g->counts[3];
-  DBuf<unsigned char> buf(((size_t)2 * m3 * 4 + 255) / 256 * 256 + 256, s);
+  // the member-pair set: a power of two >= 2 x (3 m3) slots, so it never fills
+  uint64_t tcap = 16;
+  while (tcap < (uint64_t)(6 * m3)) tcap <<= 1;
+  const size_t lb = ((size_t)2 * m3 * 4 + 255) / 256 * 256;
+  const size_t shb = ((size_t)m3 + 255) / 256 * 256;
+  // the quad Bloom filter: a power of two >= 32 bits per 4-hyperedge (8 per 3-subset)
+  uint32_t nbits = 1024;
+  while ((uint64_t)nbits < 32ull * (uint64_t)g->counts[4] && nbits < (1u << 31)) nbits <<= 1;
+  const size_t bb = (size_t)nbits / 8;
+  DBuf<unsigned char> buf(lb + 256 + shb + (size_t)tcap * 8 + bb, s);
   int32_t* small = reinterpret_cast<int32_t*>(buf.p);
   int32_t* large = small + m3;
-  unsigned int* counts = reinterpret_cast<unsigned int*>(buf.p + ((size_t)2 * m3 * 4 + 255) / 256 * 256);
+  unsigned int* counts = reinterpret_cast<unsigned int*>(buf.p + lb);
+  uint8_t* share = buf.p + lb + 256;
+  unsigned long long* tab = reinterpret_cast<unsigned long long*>(buf.p + lb + 256 + shb);
+  uint32_t* bloom = reinterpret_cast<uint32_t*>(buf.p + lb + 256 + shb + (size_t)tcap * 8);
   cudaEvent_t ev = nullptr;
   const bool tr = traced && trace_on("census_TX");
   if (tr) trace_begin(s, &ev);
   HM_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned int), s));
-  k_txs_split<<<grid1d(m3), 256, 0, s>>>(g->view(), small, large, counts);
+  HM_CUDA(cudaMemsetAsync(tab, 0xFF, (size_t)tcap * 8, s));
+  HM_CUDA(cudaMemsetAsync(bloom, 0, bb, s));
+  k_tp_insert<<<grid1d(m3), 256, 0, s>>>(g->view(), tab, tcap - 1);
+  HM_KCHECK();
+  if (g->counts[4]) {
+    k_tq_bloom<<<grid1d(g->counts[4]), 256, 0, s>>>(g->view(), bloom, nbits);
+    HM_KCHECK();
+  }
+  k_txs_split<<<grid1d(m3), 256, 0, s>>>(g->view(), tab, tcap - 1, bloom, nbits, share, small,
+                                         large, counts);
   HM_KCHECK();
   int sms = 0, per32 = 0, per8 = 0;
   resident_blocks((const void*)k_census_txs<32>, sms, per32);
@@ -1034,11 +1152,11 @@ void launch_txs(const hm_graph* g, unsigned long long* hist, cudaStream_t s, boo
   const int64_t want8 = (m3 + CENSUS_THREADS / 8 - 1) / (CENSUS_THREADS / 8);
   const int b32 = (int)std::max<int64_t>(1, std::min<int64_t>(want32, (int64_t)sms * per32));
   const int b8 = (int)std::max<int64_t>(1, std::min<int64_t>(want8, (int64_t)sms * per8));
-  k_census_txs<32><<<b32, CENSUS_THREADS, 0, s>>>(g->view(), large, counts + 1, lut,
+  k_census_txs<32><<<b32, CENSUS_THREADS, 0, s>>>(g->view(), large, counts + 1, share, lut,
                                                   (int)T.lut.size(), T.ncls, sub ? 1 : 0, hist);
   HM_KCHECK();
-  k_census_txs<8><<<b8, CENSUS_THREADS, 0, s>>>(g->view(), small, counts, lut, (int)T.lut.size(),
-                                                T.ncls, sub ? 1 : 0, hist);
+  k_census_txs<8><<<b8, CENSUS_THREADS, 0, s>>>(g->view(), small, counts, share, lut,
+                                                (int)T.lut.size(), T.ncls, sub ? 1 : 0, hist);
   HM_KCHECK();
   if (tr) trace_end("census_TX", s, ev);
 }
