@@ -367,7 +367,7 @@ __global__ void k_ws_all(const int64_t* __restrict__ off2, const int64_t* __rest
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < maxA;
        i += (int64_t)gridDim.x * blockDim.x) {
     for (int k = 0; k < W.nj; ++k) {
-      if (i >= W.A[k] || W.fam[k] == 'c') continue;  // 'c': c4_bounds
+      if (i >= W.A[k] || W.fam[k] == 'c' || W.fam[k] == 'o') continue;  // c4_bounds, out_lists
       const char f = W.fam[k];
       uint64_t v = 0;
       if (f == 'W' || f == 'S' || f == 'w' || f == 's') {
@@ -402,8 +402,16 @@ __global__ void k_ws_all(const int64_t* __restrict__ off2, const int64_t* __rest
 // where the special nodes of e are the d with two or more pairs to e, with a
 // 3-hyperedge through two members, or with the 4-hyperedge. They are found
 // by six scans, each node kept at its first source only:
-//   0-2. N(a) & N(b), N(a) & N(c), N(b) & N(c): the shorter of the two rows
-//        scanned, membership in the other by a signature test and a probe;
+//   0-2. N(a) & N(b), N(a) & N(c), N(b) & N(c). With nodes ranked by
+//        (degree, id), a common neighbour d of p and q is either above the
+//        lower-ranked of the two, r, and so in r's out-list (its neighbours
+//        of higher rank), or below both, and then the lowest node of the
+//        wedge p - d - q: those come as wedge records, made once per graph
+//        from every pair of every out-list that is the member pair of exactly
+//        one 3-hyperedge. So r's out-list is scanned, membership in the other
+//        row by a signature test and a probe, and the records are read; a
+//        member pair inside two or more 3-hyperedges has no records, and its
+//        shorter row is scanned whole instead;
 //   3-5. the third nodes of the 3-hyperedges through (a, b), (a, c), (b, c):
 //        the shorter of the two members' incidence lists scanned, for the
 //        member pairs that lie in another 3-hyperedge too (the others have
@@ -415,12 +423,15 @@ __global__ void k_ws_all(const int64_t* __restrict__ off2, const int64_t* __rest
 // adds to the special count of every member it is a pair neighbour of, and is
 // counted when V' is a TX set of this anchor: no 4-hyperedge, and e the
 // smallest 3-hyperedge of V' ({a,b,d} < e iff d < c, {a,c,d} < e iff d < b,
-// {b,c,d} < e iff d < a). Every loop and member index is a compile-time
-// constant after unrolling, so the per-member state stays in registers.
+// {b,c,d} < e iff d < a). The three pair sources and the records form one
+// index space over the group's lanes, so that short lists take one round;
+// member indices are three-way selects, so the per-member state stays in
+// registers, and all sources share one call site of the candidate code.
 struct TxsAnchor {
   int32_t m0, m1, m2;
-  int64_t o20, o21, o22, o30, o31, o32;
-  int32_t d20, d21, d22, d30, d31, d32;
+  int32_t od0, od1, od2;  // out-list lengths
+  int64_t o20, o21, o22;
+  int32_t d20, d21, d22;
   uint64_t s20, s21, s22, s30, s31, s32, s4;
   bool pab, pac, pbc;
 };
@@ -486,6 +497,26 @@ __device__ __forceinline__ void txs_candidate(const DevGraph& g, const TxsAnchor
   B.count(mask, 1ull);
 }
 
+// The list of pair source j (member pair (p, q): 0 (a, b), 1 (a, c), 2 (b, c)):
+// for a pair inside another 3-hyperedge too, the shorter of the two rows;
+// else the out-list of the lower-ranked member (the wedges below both come as
+// records). kp: the member known to be adjacent.
+__device__ __forceinline__ void txs_pair_list(const TxsAnchor& A, uint32_t shared, int j,
+                                              int64_t& o, int32_t& len, uint32_t& kp,
+                                              bool& out) {
+  const int p = j == 2 ? 1 : 0, q = j == 0 ? 1 : 2;
+  const int32_t lp = sel3(p, A.d20, A.d21, A.d22), lq = sel3(q, A.d20, A.d21, A.d22);
+  int r;
+  out = !((shared >> j) & 1u);
+  if (out)
+    r = (lp < lq || (lp == lq && sel3(p, A.m0, A.m1, A.m2) < sel3(q, A.m0, A.m1, A.m2))) ? p : q;
+  else
+    r = lp <= lq ? p : q;
+  o = sel3(r, A.o20, A.o21, A.o22);
+  len = out ? sel3(r, A.od0, A.od1, A.od2) : sel3(r, A.d20, A.d21, A.d22);
+  kp = 1u << r;
+}
+
 #ifndef HM_TXS_MINBLOCKS
 #define HM_TXS_MINBLOCKS 4
 #endif
@@ -497,7 +528,9 @@ template <int G>
 __global__ void __launch_bounds__(CENSUS_THREADS, HM_TXS_MINBLOCKS)
     k_census_txs(const DevGraph g, const int32_t* __restrict__ list,
                  const unsigned int* __restrict__ count, const uint8_t* __restrict__ share,
-                 const uint8_t* __restrict__ lut_g,
+                 const int32_t* __restrict__ out_deg, const int32_t* __restrict__ out_adj,
+                 const uint64_t* __restrict__ rec, const int64_t* __restrict__ rs,
+                 const int64_t* __restrict__ re, const uint8_t* __restrict__ lut_g,
                  int nmask, int ncls, int sub, unsigned long long* __restrict__ hist) {
   __shared__ unsigned long long bins[BIN_STRIDE];
   __shared__ __align__(16) uint8_t lut[2048];
@@ -518,18 +551,15 @@ __global__ void __launch_bounds__(CENSUS_THREADS, HM_TXS_MINBLOCKS)
     A.m0 = e.x;
     A.m1 = e.y;
     A.m2 = e.z;
+    A.od0 = out_deg[e.x];
+    A.od1 = out_deg[e.y];
+    A.od2 = out_deg[e.z];
     A.o20 = g.off2[e.x];
     A.o21 = g.off2[e.y];
     A.o22 = g.off2[e.z];
     A.d20 = (int32_t)(g.off2[e.x + 1] - A.o20);
     A.d21 = (int32_t)(g.off2[e.y + 1] - A.o21);
     A.d22 = (int32_t)(g.off2[e.z + 1] - A.o22);
-    A.o30 = g.off3[e.x];
-    A.o31 = g.off3[e.y];
-    A.o32 = g.off3[e.z];
-    A.d30 = (int32_t)(g.off3[e.x + 1] - A.o30);
-    A.d31 = (int32_t)(g.off3[e.y + 1] - A.o31);
-    A.d32 = (int32_t)(g.off3[e.z + 1] - A.o32);
     A.s20 = g.sig[e.x];
     A.s21 = g.sig[e.y];
     A.s22 = g.sig[e.z];
@@ -550,43 +580,66 @@ __global__ void __launch_bounds__(CENSUS_THREADS, HM_TXS_MINBLOCKS)
     A.pbc = pb & 4u;
     uint32_t sp0 = 0, sp1 = 0, sp2 = 0;
     const uint32_t shared = share[t];
-    const int nsrc = (shared & 8u) ? 9 : 6;
+    const int64_t r0 = rs[t];
+    const int32_t lr = (int32_t)(re[t] - r0 < 0x7FFFFFFF ? re[t] - r0 : 0x7FFFFFFF);
+    int32_t l0, l1, l2;
+    {
+      int64_t o;
+      uint32_t kp;
+      bool out;
+      txs_pair_list(A, shared, 0, o, l0, kp, out);
+      txs_pair_list(A, shared, 1, o, l1, kp, out);
+      txs_pair_list(A, shared, 2, o, l2, kp, out);
+    }
+    // Segment 0: the three pair sources and the wedge records, one index
+    // space over the group's lanes (most lists are short); 1-3: the third
+    // nodes of a member pair inside another 3-hyperedge (sources 3-5); 4-6:
+    // the quad scans (sources 6-8) where the filters allow.
 #pragma unroll 1
-    for (int src = 0; src < nsrc; ++src) {
-      // a member pair inside no other 3-hyperedge has no third node to scan for
-      if (src >= 3 && src < 6 && !((shared >> (src - 3)) & 1u)) continue;
-      // the source's list (group-uniform): member pair (p, q) or member x
+    for (int seg = 0; seg < 7; ++seg) {
+      if (seg >= 1 && seg <= 3 && !((shared >> (seg - 1)) & 1u)) continue;
+      if (seg >= 4 && !(shared & 8u)) continue;
+      const int src = seg + 2;  // sources 3-8
       const int p = src < 6 ? (src % 3 == 2 ? 1 : 0) : src - 6;
       const int q = src % 3 == 0 ? 1 : 2;
-      int64_t o;
+      int64_t o = 0;
       int32_t len;
-      uint32_t kp = 0;
       int32_t mp = 0, mq = 0;
-      if (src < 3) {  // the shorter of the two pair rows
-        const int32_t lp = sel3(p, A.d20, A.d21, A.d22), lq = sel3(q, A.d20, A.d21, A.d22);
-        const bool ps = lp <= lq;
-        o = ps ? sel3(p, A.o20, A.o21, A.o22) : sel3(q, A.o20, A.o21, A.o22);
-        len = ps ? lp : lq;
-        kp = 1u << (ps ? p : q);
-      } else if (src < 6) {  // the shorter of the two incidence lists
-        const int32_t lp = sel3(p, A.d30, A.d31, A.d32), lq = sel3(q, A.d30, A.d31, A.d32);
-        const bool ps = lp <= lq;
-        o = ps ? sel3(p, A.o30, A.o31, A.o32) : sel3(q, A.o30, A.o31, A.o32);
-        len = ps ? lp : lq;
+      if (seg == 0) {
+        len = l0 + l1 + l2 + lr;
+      } else if (seg <= 3) {  // the shorter of the two incidence lists
         mp = sel3(p, A.m0, A.m1, A.m2);
         mq = sel3(q, A.m0, A.m1, A.m2);
+        const int64_t op = g.off3[mp], oq = g.off3[mq];
+        const int32_t lp = (int32_t)(g.off3[mp + 1] - op), lq = (int32_t)(g.off3[mq + 1] - oq);
+        o = lp <= lq ? op : oq;
+        len = lp <= lq ? lp : lq;
       } else {  // member p's pair row
         o = sel3(p, A.o20, A.o21, A.o22);
         len = sel3(p, A.d20, A.d21, A.d22);
-        kp = 1u << p;
       }
       for (int32_t i0 = 0; i0 < len; i0 += G) {
-        const int32_t idx = i0 + glane;
+        int32_t idx = i0 + glane;
         if (idx >= len) continue;
         int32_t d;
-        if (src < 3 || src >= 6) {
-          d = __ldg(g.adj2 + o + idx);
-        } else {
+        int csrc = src;
+        uint32_t kpx = 1u << p;
+        if (seg == 0) {
+          if (idx < l0 + l1 + l2) {
+            csrc = idx < l0 ? 0 : (idx < l0 + l1 ? 1 : 2);
+            idx -= csrc == 0 ? 0 : (csrc == 1 ? l0 : l0 + l1);
+            int64_t ol;
+            int32_t ll;
+            bool out;
+            txs_pair_list(A, shared, csrc, ol, ll, kpx, out);
+            d = __ldg((out ? out_adj : g.adj2) + ol + idx);
+          } else {  // a wedge record: d adjacent to both members of pair csrc
+            const uint64_t r = __ldg(rec + r0 + (idx - l0 - l1 - l2));
+            d = (int32_t)(r >> 33);
+            csrc = (int)((r >> 31) & 3u);
+            kpx = csrc == 0 ? 3u : (csrc == 1 ? 5u : 6u);
+          }
+        } else if (seg <= 3) {
           const int64_t th = __ldg(g.inc3 + o + idx);
           if (th == t) continue;
           const int4 h = g.e3[th];
@@ -594,8 +647,11 @@ __global__ void __launch_bounds__(CENSUS_THREADS, HM_TXS_MINBLOCKS)
           const bool hq = h.x == mq || h.y == mq || h.z == mq;
           if (!hp || !hq) continue;
           d = (h.x != mp && h.x != mq) ? h.x : (h.y != mp && h.y != mq) ? h.y : h.z;
+          kpx = 0;
+        } else {
+          d = __ldg(g.adj2 + o + idx);
         }
-        txs_candidate(g, A, src, d, kp, B, sp0, sp1, sp2);
+        txs_candidate(g, A, csrc, d, kpx, B, sp0, sp1, sp2);
       }
     }
 #pragma unroll
@@ -628,17 +684,34 @@ __global__ void __launch_bounds__(CENSUS_THREADS, HM_TXS_MINBLOCKS)
 // scan for (sources 3-5 of k_census_txs) when it is so marked, and few are.
 constexpr uint64_t TP_SHARED = 1ull << 63;
 
-__device__ __forceinline__ void tp_insert(unsigned long long* tab, uint64_t mask, uint64_t key) {
+__device__ __forceinline__ void tp_insert(unsigned long long* tab, int32_t* val, uint64_t mask,
+                                          uint64_t key, int32_t v) {
   uint64_t slot = hash_pair(key) & mask;
   for (uint64_t it = 0; it <= mask; ++it) {
     const unsigned long long prev = atomicCAS(tab + slot, EMPTY64, key);
-    if (prev == EMPTY64) return;
+    if (prev == EMPTY64) {
+      val[slot] = v;
+      return;
+    }
     if ((prev & ~TP_SHARED) == key) {
       if (!(prev & TP_SHARED)) atomicOr(tab + slot, TP_SHARED);
       return;
     }
     slot = (slot + 1) & mask;
   }
+}
+
+// The slot of a pair of the set, or -1.
+__device__ __forceinline__ int64_t tp_find(const unsigned long long* tab, uint64_t mask,
+                                           uint64_t key) {
+  uint64_t slot = hash_pair(key) & mask;
+  for (uint64_t it = 0; it <= mask; ++it) {
+    const unsigned long long v = tab[slot];
+    if ((v & ~TP_SHARED) == key) return (int64_t)slot;
+    if (v == EMPTY64) return -1;
+    slot = (slot + 1) & mask;
+  }
+  return -1;
 }
 
 // Whether the pair lies in two or more 3-hyperedges (true when it is not
@@ -682,22 +755,96 @@ __global__ void k_tq_bloom(const DevGraph g, uint32_t* __restrict__ bloom, uint3
   }
 }
 
+// The value of a pair is 4 t + j for the first 3-hyperedge t inserting it, j
+// its member pair (0: (a, b), 1: (a, c), 2: (b, c)); it is read only for
+// unflagged pairs, which have one 3-hyperedge.
 __global__ void k_tp_insert(const DevGraph g, unsigned long long* __restrict__ tab,
-                            uint64_t mask) {
+                            int32_t* __restrict__ val, uint64_t mask) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < g.m3;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int4 e = g.e3[t];
-    tp_insert(tab, mask, pair_key(e.x, e.y));
-    tp_insert(tab, mask, pair_key(e.x, e.z));
-    tp_insert(tab, mask, pair_key(e.y, e.z));
+    tp_insert(tab, val, mask, pair_key(e.x, e.y), (int32_t)(4 * t + 0));
+    tp_insert(tab, val, mask, pair_key(e.x, e.z), (int32_t)(4 * t + 1));
+    tp_insert(tab, val, mask, pair_key(e.y, e.z), (int32_t)(4 * t + 2));
   }
 }
 
-// Splits E_3 for k_census_txs: a 3-hyperedge whose every scanned list (the
-// shorter row of each member pair, the shorter incidence list of each member
-// pair that lies in another 3-hyperedge too, and each member's row where the
-// 4-hyperedge signatures meet) has at most TXS_SMALL entries goes to the
-// 8-lane list, the others to the warp list. share[t] gets the member pairs
+// Wedge records: a common pair neighbour d of a member pair (p, q) that is
+// ranked below both is the lowest node of the wedge p - d - q, so p and q
+// both lie in out(d). Item k of the TXO space (node d, pair (i, j) of its
+// out-list) writes record k: (d << 33) | (j << 31) | t when the pair is the
+// member pair j of exactly one 3-hyperedge t (an unflagged pair of the set),
+// else REC_NONE. A warp takes 32 consecutive nodes and spreads their pairs
+// over its lanes.
+constexpr uint64_t REC_NONE = ~0ull;
+constexpr uint64_t REC_T = (1ull << 31) - 1;
+__global__ void __launch_bounds__(256)
+    k_txs_wedges(const DevGraph g, const int32_t* __restrict__ out_deg,
+                 const int32_t* __restrict__ out_adj, const uint64_t* __restrict__ ws,
+                 const unsigned long long* __restrict__ tab, const int32_t* __restrict__ val,
+                 uint64_t mask, uint64_t* __restrict__ rec) {
+  __shared__ uint64_t pre_s[8][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint64_t* pre = pre_s[wid];
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c0 = gw * 32; c0 < g.n; c0 += warps * 32) {
+    const int64_t dl = c0 + lane;
+    const uint64_t k = dl < g.n ? (uint64_t)out_deg[dl] : 0;
+    const uint64_t np = k * (k - (k > 0 ? 1 : 0)) / 2;
+    uint64_t incl = np;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    pre[lane] = incl - np;
+    const uint64_t tot = __shfl_sync(0xffffffffu, incl, 31);
+    const uint64_t base = ws[c0];
+    __syncwarp();
+    for (uint64_t p = lane; p < tot; p += 32) {
+      int lo = 0, hi = 32;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= p) lo = mid;
+        else hi = mid;
+      }
+      const int32_t d = (int32_t)(c0 + lo);
+      uint32_t i, j;
+      unrank2(p - pre[lo], i, j);
+      const int64_t od = g.off2[d];
+      const int32_t x = out_adj[od + i], y = out_adj[od + j];
+      uint64_t r = REC_NONE;
+      const int64_t sl = tp_find(tab, mask, pair_key(x, y));
+      if (sl >= 0 && !(tab[sl] & TP_SHARED)) {
+        const uint32_t v = (uint32_t)val[sl];
+        r = ((uint64_t)(uint32_t)d << 33) | ((uint64_t)(v & 3u) << 31) | (uint64_t)(v >> 2);
+      }
+      rec[base + p] = r;
+    }
+    __syncwarp();
+  }
+}
+
+// After the records are sorted by t: 3-hyperedge t's records are [rs[t], re[t]).
+__global__ void k_txs_runs(const uint64_t* __restrict__ rec, uint64_t nrec,
+                           int64_t* __restrict__ rs, int64_t* __restrict__ re) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nrec;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t r = rec[i];
+    if (r == REC_NONE) continue;
+    const uint64_t t = r & REC_T;
+    if (i == 0 || (rec[i - 1] & REC_T) != t) rs[t] = (int64_t)i;
+    if (i + 1 == nrec || (rec[i + 1] & REC_T) != t) re[t] = (int64_t)(i + 1);
+  }
+}
+
+// Splits E_3 for k_census_txs: a 3-hyperedge whose every scanned list (per
+// member pair, the out-list of its lower-ranked member or, for a pair inside
+// another 3-hyperedge too, the shorter row and the shorter incidence list;
+// its wedge records; each member's row where the 4-hyperedge signatures
+// meet) has at most TXS_SMALL entries goes to the 8-lane list, the others to
+// the warp list. share[t] gets the member pairs
 // that lie in another 3-hyperedge (bit 0: (a, b), 1: (a, c), 2: (b, c)) and
 // bit 3 when the quad scans run: the members' 4-hyperedge signatures meet and
 // the Bloom filter does not rule out a 4-hyperedge containing e.
@@ -707,7 +854,8 @@ __global__ void k_tp_insert(const DevGraph g, unsigned long long* __restrict__ t
 constexpr int TXS_SMALL = HM_TXS_SMALL;
 __global__ void k_txs_split(const DevGraph g, const unsigned long long* __restrict__ tab,
                             uint64_t mask, const uint32_t* __restrict__ bloom, uint32_t nbits,
-                            uint8_t* __restrict__ share,
+                            const int32_t* __restrict__ out_deg, const int64_t* __restrict__ rs,
+                            const int64_t* __restrict__ re, uint8_t* __restrict__ share,
                             int32_t* __restrict__ small, int32_t* __restrict__ large,
                             unsigned int* __restrict__ counts) {
   const int lane = threadIdx.x & 31;
@@ -736,10 +884,14 @@ __global__ void k_txs_split(const DevGraph g, const unsigned long long* __restri
         quad = ((bloom[b0 >> 5] >> (b0 & 31)) & 1u) && ((bloom[b1 >> 5] >> (b1 & 31)) & 1u);
       }
       share[t] = (uint8_t)((s01 ? 1u : 0u) | (s02 ? 2u : 0u) | (s12 ? 4u : 0u) | (quad ? 8u : 0u));
-      int32_t mx = max(max(min(d2[0], d2[1]), min(d2[0], d2[2])), min(d2[1], d2[2]));
-      if (s01) mx = max(mx, min(d3[0], d3[1]));
-      if (s02) mx = max(mx, min(d3[0], d3[2]));
-      if (s12) mx = max(mx, min(d3[1], d3[2]));
+      // per member pair: the out-list of its lower-ranked member, or for a
+      // shared pair the shorter row and the shorter incidence list
+      auto low = [&](int i, int j) { return d2[i] < d2[j] || (d2[i] == d2[j] && m[i] < m[j]) ? i : j; };
+      const int64_t nr = re[t] - rs[t];
+      int32_t mx = (int32_t)(nr < (1 << 30) ? nr : (1 << 30));
+      mx = max(mx, s01 ? max(min(d2[0], d2[1]), min(d3[0], d3[1])) : out_deg[m[low(0, 1)]]);
+      mx = max(mx, s02 ? max(min(d2[0], d2[2]), min(d3[0], d3[2])) : out_deg[m[low(0, 2)]]);
+      mx = max(mx, s12 ? max(min(d2[1], d2[2]), min(d3[1], d3[2])) : out_deg[m[low(1, 2)]]);
       if (quad) mx = max(mx, max(d2[0], max(d2[1], d2[2])));
       is_small = mx <= TXS_SMALL;
     }
@@ -766,7 +918,49 @@ unsigned grid1d(int64_t n) {
   return (unsigned)b;
 }
 
+// Out-lists: each pair (u, v) goes to the out-list of its lower-ranked end
+// (rank = (degree, id)), at that node's next free slot.
+__global__ void k_out_fill(const DevGraph g, int32_t* __restrict__ out_deg,
+                           int32_t* __restrict__ out_adj) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < g.m2;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t e = g.e2[p];
+    const int32_t u = (int32_t)(e >> 32), v = (int32_t)(e & 0xFFFFFFFFull);
+    const int32_t du = (int32_t)(g.off2[u + 1] - g.off2[u]);
+    const int32_t dv = (int32_t)(g.off2[v + 1] - g.off2[v]);
+    const bool u_low = du < dv || (du == dv && u < v);
+    const int32_t lo = u_low ? u : v, hi = u_low ? v : u;
+    const int32_t at = atomicAdd(&out_deg[lo], 1);
+    out_adj[g.off2[lo] + at] = hi;
+  }
+}
+
+__global__ void k_out_pairs(const int32_t* __restrict__ out_deg, int64_t n,
+                            uint64_t* __restrict__ out) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = (uint64_t)out_deg[v];
+    out[v] = k * (k - (k > 0 ? 1 : 0)) / 2;
+  }
+}
+
 }  // namespace
+
+void out_lists(hm_graph* g, uint64_t* out, cudaStream_t s) {
+  if (!g->out_deg) {
+    g->out_deg = dalloc<int32_t>((size_t)g->n, s);
+    g->owned.push_back(g->out_deg);
+    g->out_adj = dalloc<int32_t>(std::max<size_t>(1, (size_t)2 * g->counts[2]), s);
+    g->owned.push_back(g->out_adj);
+  }
+  HM_CUDA(cudaMemsetAsync(g->out_deg, 0, (size_t)g->n * sizeof(int32_t), s));
+  if (g->counts[2]) {
+    k_out_fill<<<grid1d(g->counts[2]), 256, 0, s>>>(g->view(), g->out_deg, g->out_adj);
+    HM_KCHECK();
+  }
+  k_out_pairs<<<grid1d(g->n), 256, 0, s>>>(g->out_deg, g->n, out);
+  HM_KCHECK();
+}
 
 // Prefix sums of the candidates per anchor for every family in `todo` that is
 // not ready: enqueued on s (one temporary for all families), with the totals
@@ -792,7 +986,7 @@ void spaces_enqueue(hm_graph* g, const std::vector<std::pair<hm_graph::Space*, c
   for (int i = 0; i < nj; ++i) {
     const char fam = P.need[i].second;
     int64_t a = 0;
-    if (fam == 'W' || fam == 'S' || fam == 'w' || fam == 's' || fam == 'c') a = g->n;
+    if (fam == 'W' || fam == 'S' || fam == 'w' || fam == 's' || fam == 'c' || fam == 'o') a = g->n;
     if (fam == 'P' || fam == 'p') a = g->counts[2];
     if (fam == 'X' || fam == 'x') a = g->kmax >= 3 ? g->counts[3] : 0;
     W.fam[i] = fam;
@@ -825,6 +1019,8 @@ void spaces_enqueue(hm_graph* g, const std::vector<std::pair<hm_graph::Space*, c
     }
     for (int i = 0; i < nj; ++i)
       if (W.fam[i] == 'c' && W.A[i] > 0) c4_bounds(g, W.out[i], s);
+    for (int i = 0; i < nj; ++i)
+      if (W.fam[i] == 'o' && W.A[i] > 0) out_lists(g, W.out[i], s);
     scan_batch_inplace(jobs, nj, s, scan_bytes ? base : nullptr, true);
     P.h = pinned_words() + 64;
     HM_CUDA(cudaMemcpyAsync(P.h, totals, nj * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
@@ -1012,6 +1208,8 @@ std::vector<std::pair<hm_graph::Space*, char>> census_spaces(hm_graph* g, int or
   }
   if (g->bits2)
     return {{&g->S, 'S'}, {&g->P, 'P'}, {&g->TX, 'X'}, {&g->Sb, 's'}, {&g->Pb, 'p'}, {&g->TXb, 'x'}};
+  if (g->sig && !g->block)
+    return {{&g->S, 'S'}, {&g->P, 'P'}, {&g->TX, 'X'}, {&g->C4, 'c'}, {&g->TXO, 'o'}};
   return {{&g->S, 'S'}, {&g->P, 'P'}, {&g->TX, 'X'}, {&g->C4, 'c'}};
 }
 
@@ -1114,36 +1312,64 @@ void launch_txs(const hm_graph* g, unsigned long long* hist, cudaStream_t s, boo
   // persistent grids (every SM's resident blocks) read their list lengths on
   // the device
   const int64_t m3 = g->counts[3];
+  HM_CHECK(m3 < (1ll << 29), HM_EUNSUPPORTED, "2^29 or more 3-hyperedges on the sparse TX path");
+  HM_CHECK(g->TXO.ready && g->out_deg, HM_EINVAL, "out-lists not built");
   // the member-pair set: a power of two >= 2 x (3 m3) slots, so it never fills
   uint64_t tcap = 16;
   while (tcap < (uint64_t)(6 * m3)) tcap <<= 1;
-  const size_t lb = ((size_t)2 * m3 * 4 + 255) / 256 * 256;
-  const size_t shb = ((size_t)m3 + 255) / 256 * 256;
   // the quad Bloom filter: a power of two >= 32 bits per 4-hyperedge (8 per 3-subset)
   uint32_t nbits = 1024;
   while ((uint64_t)nbits < 32ull * (uint64_t)g->counts[4] && nbits < (1u << 31)) nbits <<= 1;
-  const size_t bb = (size_t)nbits / 8;
-  DBuf<unsigned char> buf(lb + 256 + shb + (size_t)tcap * 8 + bb, s);
-  int32_t* small = reinterpret_cast<int32_t*>(buf.p);
+  const uint64_t nrec = g->TXO.total;  // wedge records, one per pair of an out-list
+  size_t at = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = at;
+    at += (bytes + 255) / 256 * 256;
+    return o;
+  };
+  const size_t o_lists = take((size_t)2 * m3 * 4), o_counts = take(8), o_share = take((size_t)m3),
+               o_tab = take((size_t)tcap * 8), o_val = take((size_t)tcap * 4),
+               o_bloom = take((size_t)nbits / 8), o_runs = take((size_t)2 * m3 * 8),
+               o_rec = take((size_t)std::max<uint64_t>(1, nrec) * 8);
+  DBuf<unsigned char> buf(at, s);
+  int32_t* small = reinterpret_cast<int32_t*>(buf.p + o_lists);
   int32_t* large = small + m3;
-  unsigned int* counts = reinterpret_cast<unsigned int*>(buf.p + lb);
-  uint8_t* share = buf.p + lb + 256;
-  unsigned long long* tab = reinterpret_cast<unsigned long long*>(buf.p + lb + 256 + shb);
-  uint32_t* bloom = reinterpret_cast<uint32_t*>(buf.p + lb + 256 + shb + (size_t)tcap * 8);
+  unsigned int* counts = reinterpret_cast<unsigned int*>(buf.p + o_counts);
+  uint8_t* share = buf.p + o_share;
+  unsigned long long* tab = reinterpret_cast<unsigned long long*>(buf.p + o_tab);
+  int32_t* tval = reinterpret_cast<int32_t*>(buf.p + o_val);
+  uint32_t* bloom = reinterpret_cast<uint32_t*>(buf.p + o_bloom);
+  int64_t* rs = reinterpret_cast<int64_t*>(buf.p + o_runs);
+  int64_t* re = rs + m3;
+  uint64_t* rec = reinterpret_cast<uint64_t*>(buf.p + o_rec);
   cudaEvent_t ev = nullptr;
   const bool tr = traced && trace_on("census_TX");
   if (tr) trace_begin(s, &ev);
   HM_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned int), s));
   HM_CUDA(cudaMemsetAsync(tab, 0xFF, (size_t)tcap * 8, s));
-  HM_CUDA(cudaMemsetAsync(bloom, 0, bb, s));
-  k_tp_insert<<<grid1d(m3), 256, 0, s>>>(g->view(), tab, tcap - 1);
+  HM_CUDA(cudaMemsetAsync(bloom, 0, (size_t)nbits / 8, s));
+  HM_CUDA(cudaMemsetAsync(rs, 0, (size_t)2 * m3 * 8, s));
+  k_tp_insert<<<grid1d(m3), 256, 0, s>>>(g->view(), tab, tval, tcap - 1);
   HM_KCHECK();
   if (g->counts[4]) {
     k_tq_bloom<<<grid1d(g->counts[4]), 256, 0, s>>>(g->view(), bloom, nbits);
     HM_KCHECK();
   }
-  k_txs_split<<<grid1d(m3), 256, 0, s>>>(g->view(), tab, tcap - 1, bloom, nbits, share, small,
-                                         large, counts);
+  if (nrec) {
+    // records by 3-hyperedge: a stable sort on the low bits that hold t
+    // (2^ebits > m3, so the sentinels sort last)
+    int ebits = 1;
+    while ((1ll << ebits) <= m3) ++ebits;
+    const uint64_t want = ((uint64_t)g->n + 255) / 256;
+    k_txs_wedges<<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, 152 * 8)), 256, 0, s>>>(
+        g->view(), g->out_deg, g->out_adj, g->TXO.ws, tab, tval, tcap - 1, rec);
+    HM_KCHECK();
+    radix_sort_u64(rec, nullptr, (int64_t)nrec, ebits, s);
+    k_txs_runs<<<grid1d((int64_t)nrec), 256, 0, s>>>(rec, nrec, rs, re);
+    HM_KCHECK();
+  }
+  k_txs_split<<<grid1d(m3), 256, 0, s>>>(g->view(), tab, tcap - 1, bloom, nbits, g->out_deg, rs,
+                                         re, share, small, large, counts);
   HM_KCHECK();
   int sms = 0, per32 = 0, per8 = 0;
   resident_blocks((const void*)k_census_txs<32>, sms, per32);
@@ -1152,11 +1378,13 @@ void launch_txs(const hm_graph* g, unsigned long long* hist, cudaStream_t s, boo
   const int64_t want8 = (m3 + CENSUS_THREADS / 8 - 1) / (CENSUS_THREADS / 8);
   const int b32 = (int)std::max<int64_t>(1, std::min<int64_t>(want32, (int64_t)sms * per32));
   const int b8 = (int)std::max<int64_t>(1, std::min<int64_t>(want8, (int64_t)sms * per8));
-  k_census_txs<32><<<b32, CENSUS_THREADS, 0, s>>>(g->view(), large, counts + 1, share, lut,
+  k_census_txs<32><<<b32, CENSUS_THREADS, 0, s>>>(g->view(), large, counts + 1, share,
+                                                  g->out_deg, g->out_adj, rec, rs, re, lut,
                                                   (int)T.lut.size(), T.ncls, sub ? 1 : 0, hist);
   HM_KCHECK();
-  k_census_txs<8><<<b8, CENSUS_THREADS, 0, s>>>(g->view(), small, counts, share, lut,
-                                                (int)T.lut.size(), T.ncls, sub ? 1 : 0, hist);
+  k_census_txs<8><<<b8, CENSUS_THREADS, 0, s>>>(g->view(), small, counts, share, g->out_deg,
+                                                g->out_adj, rec, rs, re, lut, (int)T.lut.size(),
+                                                T.ncls, sub ? 1 : 0, hist);
   HM_KCHECK();
   if (tr) trace_end("census_TX", s, ev);
 }

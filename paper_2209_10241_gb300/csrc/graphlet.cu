@@ -617,6 +617,48 @@ struct C4Sum {
   }
 };
 
+// End of a kernel: every thread's C4Sum into agg with one atomic per block and
+// graph run. A warp whose lanes all hold one graph (or nothing) is summed by
+// shuffles; the warps' sums meet in shared memory and thread 0 adds runs of
+// one graph. A warp that straddles graphs flushes lane by lane. All threads
+// of the block (NW warps) call it.
+template <int NW>
+__device__ __forceinline__ void c4_flush_block(C4Sum& acc, unsigned long long* agg) {
+  __shared__ int64_t g_s[NW];
+  __shared__ unsigned long long v_s[NW];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const bool has = acc.gcur >= 0 && acc.s != 0;
+  const unsigned any = __ballot_sync(0xffffffffu, has);
+  const int64_t gref = any ? __shfl_sync(0xffffffffu, acc.gcur, __ffs(any) - 1) : -1;
+  if (__all_sync(0xffffffffu, !has || acc.gcur == gref)) {
+    unsigned long long v = has ? acc.s : 0ull;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) {
+      g_s[wid] = gref;
+      v_s[wid] = v;
+    }
+  } else {
+    acc.flush(agg);
+    if (lane == 0) g_s[wid] = -1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t gc = -1;
+    unsigned long long sum = 0;
+    for (int w = 0; w < NW; ++w) {
+      if (g_s[w] < 0 || v_s[w] == 0) continue;
+      if (g_s[w] != gc) {
+        if (gc >= 0 && sum) atomicAdd(&agg[gc * NAGG + 6], 2 * sum);
+        gc = g_s[w];
+        sum = 0;
+      }
+      sum += v_s[w];
+    }
+    if (gc >= 0 && sum) atomicAdd(&agg[gc * NAGG + 6], 2 * sum);
+  }
+}
+
 // Path bound of x over its lower-ranked neighbours, summed over the warp
 // (every lane gets it).
 __device__ __forceinline__ uint64_t c4_bound(const DevGraph& g, int32_t x, int64_t ox, int32_t dx) {
@@ -637,16 +679,42 @@ __device__ __forceinline__ uint64_t c4_bound(const DevGraph& g, int32_t x, int64
 // 0. One warp per node.
 __global__ void k_c4_bound(const DevGraph g, uint32_t warp_ub, uint64_t* __restrict__ out,
                            uint16_t* __restrict__ light) {
+  // a warp takes 32 consecutive nodes: those of degree <= 8 a lane each, the
+  // others in turn with the whole warp
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t x64 = gw; x64 < g.n; x64 += warps) {
-    const int32_t x = (int32_t)x64;
-    const int64_t ox = g.off2[x];
-    const uint64_t ub = c4_bound(g, x, ox, (int32_t)(g.off2[x + 1] - ox));
-    if (lane == 0) {
+  for (int64_t c0 = gw * 32; c0 < g.n; c0 += warps * 32) {
+    const int64_t xl = c0 + lane;
+    int64_t ox = 0;
+    int32_t dx = 0;
+    if (xl < g.n) {
+      ox = g.off2[xl];
+      dx = (int32_t)(g.off2[xl + 1] - ox);
+    }
+    const bool small = dx <= 8;
+    if (small && xl < g.n) {
+      const int32_t x = (int32_t)xl;
+      uint64_t ub = 0;
+      for (int32_t i = 0; i < dx; ++i) {
+        const int32_t y = g.adj2[ox + i];
+        const int32_t dy = degree(g, y);
+        if (lower_rank(dy, y, dx, x)) ub += (uint64_t)dy;
+      }
       out[x] = ub > warp_ub ? ub : 0;
       light[x] = (ub >= 2 && ub <= warp_ub) ? (uint16_t)ub : (uint16_t)0;
+    }
+    unsigned bigs = __ballot_sync(0xffffffffu, !small);
+    while (bigs) {
+      const int src = __ffs(bigs) - 1;
+      bigs &= bigs - 1;
+      const int32_t x = (int32_t)(c0 + src);
+      const uint64_t ub = c4_bound(g, x, __shfl_sync(0xffffffffu, ox, src),
+                                   __shfl_sync(0xffffffffu, dx, src));
+      if (lane == 0) {
+        out[x] = ub > warp_ub ? ub : 0;
+        light[x] = (ub >= 2 && ub <= warp_ub) ? (uint16_t)ub : (uint16_t)0;
+      }
     }
   }
 }
@@ -737,7 +805,7 @@ __global__ void __launch_bounds__(C4_WARPS * 32)
     __syncwarp();
    }
   }
-  if (lane == 0) acc.flush(agg);
+  c4_flush_block<C4_WARPS>(acc, agg);
 }
 
 // Sort tier, emission: one block per node with slots [ws[x], ws[x+1]). The
@@ -993,8 +1061,9 @@ __global__ void __launch_bounds__(C4E_THREADS)
 }
 
 // C(count, 2) over every table slot; a slot's graph is that of its z.
-__global__ void k_c4_sum(const unsigned long long* __restrict__ table, uint64_t nslots,
-                         int32_t nodes_per_graph, unsigned long long* __restrict__ agg) {
+__global__ void __launch_bounds__(256)
+    k_c4_sum(const unsigned long long* __restrict__ table, uint64_t nslots,
+             int32_t nodes_per_graph, unsigned long long* __restrict__ agg) {
   C4Sum acc;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nslots;
        i += (uint64_t)gridDim.x * blockDim.x) {
@@ -1003,16 +1072,7 @@ __global__ void k_c4_sum(const unsigned long long* __restrict__ table, uint64_t 
     const uint64_t c = v & 0xFFFFFFFFull;
     if (c > 1) acc.add(agg, (int64_t)(v >> 32) / nodes_per_graph, c * (c - 1) / 2);
   }
-  const int lane = threadIdx.x & 31;
-  const int64_t g0 = __shfl_sync(0xffffffffu, acc.gcur, 0);
-  if (__all_sync(0xffffffffu, acc.gcur == g0 || acc.gcur < 0 || acc.s == 0)) {
-    uint64_t sum = acc.s;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0 && g0 >= 0 && sum) atomicAdd(&agg[g0 * NAGG + 6], (unsigned long long)(2 * sum));
-  } else {
-    acc.flush(agg);
-  }
+  c4_flush_block<8>(acc, agg);
 }
 
 // Sort tier, counting: each run of c equal keys (c paths from x to one z)
@@ -1185,7 +1245,7 @@ void c4_bounds(hm_graph* g, uint64_t* out, cudaStream_t s) {
     g->c4_light = dalloc<uint16_t>((size_t)g->n, s);
     g->owned.push_back(g->c4_light);
   }
-  const uint64_t want = ((uint64_t)g->n * 32 + 255) / 256;
+  const uint64_t want = ((uint64_t)g->n + 255) / 256;  // 32 nodes per warp
   k_c4_bound<<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, 152 * 8)), 256, 0, s>>>(
       g->view(), g->c4_warp_ub, out, g->c4_light);
   HM_KCHECK();
@@ -1237,7 +1297,7 @@ void graphlet_pairs(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
       k_c4_table<<<(unsigned)std::min<uint64_t>(pieces, 1u << 30), C4E_THREADS, 0, s>>>(
           g->view(), g->C4.ws, nk, tab);
       HM_KCHECK();
-      k_c4_sum<<<grid_n(2 * nk), 256, 0, s>>>(tab, 2 * nk, G.per, G.agg);
+      k_c4_sum<<<std::min<unsigned>(grid_n(2 * nk), 152 * 8), 256, 0, s>>>(tab, 2 * nk, G.per, G.agg);
       HM_KCHECK();
       st.end();
     } else if (nk) {

@@ -465,6 +465,9 @@ void graphlet_prepare(const hm_graph* g, GraphletScratch& G, cudaStream_t s);
 // bounds go to g->c4_light. The bound in force is kept in the graph (the
 // census splits the nodes by it).
 void c4_bounds(hm_graph* g, uint64_t* out, cudaStream_t s);
+// census.cu: the out-lists of a graph with node signatures (g->out_deg,
+// g->out_adj) and, per node, C(out_deg, 2) into out.
+void out_lists(hm_graph* g, uint64_t* out, cudaStream_t s);
 void graphlet_edges(const hm_graph* g, GraphletScratch& G, cudaStream_t s);
 void graphlet_pairs(const hm_graph* g, GraphletScratch& G, cudaStream_t s);
 void graphlet_finish(const hm_graph* g, GraphletScratch& G, unsigned long long* hist,
@@ -524,6 +527,13 @@ struct hm_graph {
   uint32_t c4_warp_ub = 0;
   // per node, its path bound when in [2, c4_warp_ub] (the warp tier's nodes), else 0
   uint16_t* c4_light = nullptr;
+  // graphs with node signatures (one graph): per node v its pair neighbours
+  // of higher rank (rank = (degree, id)), out_deg[v] of them, in any order at
+  // out_adj[off2[v] ...]; TXO: per node C(out_deg, 2), the pairs of its
+  // out-list, the index space of the sparse TX pass's wedge records
+  Space TXO;
+  int32_t* out_deg = nullptr;
+  int32_t* out_adj = nullptr;
   bool useWb = false, useSb = false, usePb = false, useTXb = false;
   // order 4: pairs-only sets from graphlet identities instead of S and P
   bool useGL = false;
