@@ -235,6 +235,13 @@ def test_abi_errors(hm):
     with pytest.raises(hm.HMError) as e:
         hm.from_host(h, 4)
     assert e.value.status == 1
+    # an out-of-range member after the fifth distinct one (past where the
+    # normalisation stops reading a hyperedge) and a negative one
+    for bad in (9, -1):
+        h = synth.from_edges([[0, 1], [0, 1, 2, 3, 4, 5, bad]], 8)
+        with pytest.raises(hm.HMError) as e:
+            hm.from_host(h, 4)
+        assert e.value.status == 1
     g = hm.from_host(synth.from_edges([[0, 1], [1, 2]], 3), 3)
     with pytest.raises(hm.HMError) as e:
         hm.count_exact(g, 4)
