@@ -520,32 +520,70 @@ __device__ __forceinline__ void txs_pair_list(const TxsAnchor& A, uint32_t share
 #ifndef HM_TXS_MINBLOCKS
 #define HM_TXS_MINBLOCKS 4
 #endif
-// G lanes per 3-hyperedge (32: a warp; 8: four 3-hyperedges per warp, for
-// those whose lists are all short). The 3-hyperedges are list[0, *count), or
-// all of E_3 when list is null. The only cross-lane operations (the pairs
+// One persistent kernel over two lists of 3-hyperedges: the warp list (a warp
+// per 3-hyperedge) and the short list (8 lanes per 3-hyperedge, four per
+// warp, for those whose lists are all short). Warps take work from two
+// counters: one 3-hyperedge of the warp list at a time, then chunks of
+// TXS_CHUNK of the short list, so that warps done with the long 3-hyperedges
+// (few, taken first) go on to short ones and no long one is left for the
+// end. G, the lanes per 3-hyperedge, is a run-time value (32 or 8), so one
+// copy of the code serves both. The only cross-lane operations (the pairs
 // inside e, the special-count sums) stay within a group.
-template <int G>
+constexpr uint32_t TXS_CHUNK = 32;
 __global__ void __launch_bounds__(CENSUS_THREADS, HM_TXS_MINBLOCKS)
-    k_census_txs(const DevGraph g, const int32_t* __restrict__ list,
-                 const unsigned int* __restrict__ count, const uint8_t* __restrict__ share,
-                 const int32_t* __restrict__ out_deg, const int32_t* __restrict__ out_adj,
-                 const uint64_t* __restrict__ rec, const int64_t* __restrict__ rs,
-                 const int64_t* __restrict__ re, const uint8_t* __restrict__ lut_g,
-                 int nmask, int ncls, int sub, unsigned long long* __restrict__ hist) {
+    k_census_txs(const DevGraph g, const int32_t* __restrict__ large,
+                 const int32_t* __restrict__ small, unsigned int* __restrict__ counts,
+                 const uint8_t* __restrict__ share, const int32_t* __restrict__ out_deg,
+                 const int32_t* __restrict__ out_adj, const uint64_t* __restrict__ rec,
+                 const int64_t* __restrict__ rs, const int64_t* __restrict__ re,
+                 const uint8_t* __restrict__ lut_g, int nmask, int ncls, int sub,
+                 unsigned long long* __restrict__ hist) {
   __shared__ unsigned long long bins[BIN_STRIDE];
   __shared__ __align__(16) uint8_t lut[2048];
   load_lut(lut, lut_g, nmask);
   for (int i = threadIdx.x; i < ncls; i += blockDim.x) bins[i] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int glane = lane % G, gbase = lane - glane;
-  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << gbase);
-  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
-  const int64_t total = list ? (int64_t)*count : g.m3;
   const TxsBins B{bins, lut, sub};
-  for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; it < total;
-       it += groups) {
-    const int64_t t = list ? (int64_t)list[it] : it;
+  // counts: [0] short list size, [1] warp list size, [2] / [3] their work counters
+  const uint32_t nsmall = counts[0], nlarge = counts[1];
+  uint32_t base = 0, rounds = 0;
+  int G = 32;
+  bool large_done = false;
+  for (;;) {
+    if (rounds == 0) {  // the warp's next piece of work (warp-uniform)
+      uint32_t got = 0;
+      if (!large_done) {
+        if (lane == 0) got = atomicAdd(&counts[3], 1u);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (got < nlarge) {
+          base = got;
+          rounds = 1;
+          G = 32;
+        } else {
+          large_done = true;
+        }
+      }
+      if (large_done) {
+        if (lane == 0) got = atomicAdd(&counts[2], TXS_CHUNK);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (got >= nsmall) break;
+        base = got;
+        rounds = TXS_CHUNK / 4;
+        G = 8;
+      }
+    }
+    const int glane = lane & (G - 1), gbase = lane - glane;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (0xFFu << gbase);
+    int64_t t = -1;
+    if (G == 32) {
+      t = large[base];
+    } else {
+      const uint32_t idx = base + (TXS_CHUNK / 4 - rounds) * 4 + (uint32_t)(lane >> 3);
+      if (idx < nsmall) t = small[idx];
+    }
+    --rounds;
+    if (t < 0) continue;  // a group with no 3-hyperedge this round
     TxsAnchor A;
     const int4 e = g.e3[t];
     A.m0 = e.x;
@@ -654,7 +692,6 @@ __global__ void __launch_bounds__(CENSUS_THREADS, HM_TXS_MINBLOCKS)
         txs_candidate(g, A, csrc, d, kpx, B, sp0, sp1, sp2);
       }
     }
-#pragma unroll
     for (int o = G / 2; o; o >>= 1) {
       sp0 += __shfl_xor_sync(gmask, sp0, o);
       sp1 += __shfl_xor_sync(gmask, sp1, o);
@@ -1308,9 +1345,9 @@ void launch_txs(const hm_graph* g, unsigned long long* hist, cudaStream_t s, boo
   if (g->counts[3] == 0) return;
   const ClassTables& T = class_tables(4);
   const uint8_t* lut = device_lut(4);
-  // 3-hyperedges with short lists go four to a warp, the rest a warp each;
-  // persistent grids (every SM's resident blocks) read their list lengths on
-  // the device
+  // 3-hyperedges with short lists go four to a warp, the rest a warp each,
+  // in one persistent grid (every SM's resident blocks) that reads the list
+  // lengths on the device
   const int64_t m3 = g->counts[3];
   HM_CHECK(m3 < (1ll << 29), HM_EUNSUPPORTED, "2^29 or more 3-hyperedges on the sparse TX path");
   HM_CHECK(g->TXO.ready && g->out_deg, HM_EINVAL, "out-lists not built");
@@ -1327,7 +1364,7 @@ void launch_txs(const hm_graph* g, unsigned long long* hist, cudaStream_t s, boo
     at += (bytes + 255) / 256 * 256;
     return o;
   };
-  const size_t o_lists = take((size_t)2 * m3 * 4), o_counts = take(8), o_share = take((size_t)m3),
+  const size_t o_lists = take((size_t)2 * m3 * 4), o_counts = take(16), o_share = take((size_t)m3),
                o_tab = take((size_t)tcap * 8), o_val = take((size_t)tcap * 4),
                o_bloom = take((size_t)nbits / 8), o_runs = take((size_t)2 * m3 * 8),
                o_rec = take((size_t)std::max<uint64_t>(1, nrec) * 8);
@@ -1345,7 +1382,7 @@ void launch_txs(const hm_graph* g, unsigned long long* hist, cudaStream_t s, boo
   cudaEvent_t ev = nullptr;
   const bool tr = traced && trace_on("census_TX");
   if (tr) trace_begin(s, &ev);
-  HM_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned int), s));
+  HM_CUDA(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned int), s));
   HM_CUDA(cudaMemsetAsync(tab, 0xFF, (size_t)tcap * 8, s));
   HM_CUDA(cudaMemsetAsync(bloom, 0, (size_t)nbits / 8, s));
   HM_CUDA(cudaMemsetAsync(rs, 0, (size_t)2 * m3 * 8, s));
@@ -1371,20 +1408,13 @@ void launch_txs(const hm_graph* g, unsigned long long* hist, cudaStream_t s, boo
   k_txs_split<<<grid1d(m3), 256, 0, s>>>(g->view(), tab, tcap - 1, bloom, nbits, g->out_deg, rs,
                                          re, share, small, large, counts);
   HM_KCHECK();
-  int sms = 0, per32 = 0, per8 = 0;
-  resident_blocks((const void*)k_census_txs<32>, sms, per32);
-  resident_blocks((const void*)k_census_txs<8>, sms, per8);
-  const int64_t want32 = (m3 + CENSUS_THREADS / 32 - 1) / (CENSUS_THREADS / 32);
-  const int64_t want8 = (m3 + CENSUS_THREADS / 8 - 1) / (CENSUS_THREADS / 8);
-  const int b32 = (int)std::max<int64_t>(1, std::min<int64_t>(want32, (int64_t)sms * per32));
-  const int b8 = (int)std::max<int64_t>(1, std::min<int64_t>(want8, (int64_t)sms * per8));
-  k_census_txs<32><<<b32, CENSUS_THREADS, 0, s>>>(g->view(), large, counts + 1, share,
-                                                  g->out_deg, g->out_adj, rec, rs, re, lut,
-                                                  (int)T.lut.size(), T.ncls, sub ? 1 : 0, hist);
-  HM_KCHECK();
-  k_census_txs<8><<<b8, CENSUS_THREADS, 0, s>>>(g->view(), small, counts, share, g->out_deg,
-                                                g->out_adj, rec, rs, re, lut, (int)T.lut.size(),
-                                                T.ncls, sub ? 1 : 0, hist);
+  int sms = 0, per = 0;
+  resident_blocks((const void*)k_census_txs, sms, per);
+  const int64_t want = (m3 + CENSUS_THREADS / 8 - 1) / (CENSUS_THREADS / 8);
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * per));
+  k_census_txs<<<blocks, CENSUS_THREADS, 0, s>>>(g->view(), large, small, counts, share,
+                                                 g->out_deg, g->out_adj, rec, rs, re, lut,
+                                                 (int)T.lut.size(), T.ncls, sub ? 1 : 0, hist);
   HM_KCHECK();
   if (tr) trace_end("census_TX", s, ev);
 }
