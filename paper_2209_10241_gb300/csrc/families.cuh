@@ -18,7 +18,10 @@ __host__ __device__ __forceinline__ uint64_t choose3(uint64_t x) {
 
 // r = C(j,2) + i with 0 <= i < j
 __device__ __forceinline__ void unrank2(uint64_t r, uint32_t& i, uint32_t& j) {
-  uint64_t jj = (uint64_t)((1.0 + sqrt(1.0 + 8.0 * (double)r)) * 0.5);
+  // the estimate is corrected exactly below; single precision is close
+  // enough for r < 2^22 and much cheaper than double on this part
+  uint64_t jj = r < (1ull << 22) ? (uint64_t)((1.0f + sqrtf(1.0f + 8.0f * (float)r)) * 0.5f)
+                                 : (uint64_t)((1.0 + sqrt(1.0 + 8.0 * (double)r)) * 0.5);
   if (jj < 1) jj = 1;
   while (choose2(jj) > r) --jj;
   while (choose2(jj + 1) <= r) ++jj;
@@ -28,7 +31,8 @@ __device__ __forceinline__ void unrank2(uint64_t r, uint32_t& i, uint32_t& j) {
 
 // r = C(l,3) + C(j,2) + i with 0 <= i < j < l
 __device__ __forceinline__ void unrank3(uint64_t r, uint32_t& i, uint32_t& j, uint32_t& l) {
-  uint64_t ll = (uint64_t)cbrt(6.0 * (double)r) + 1;
+  uint64_t ll = r < (1ull << 20) ? (uint64_t)cbrtf(6.0f * (float)r) + 1
+                                 : (uint64_t)cbrt(6.0 * (double)r) + 1;
   if (ll < 2) ll = 2;
   while (choose3(ll) > r) --ll;
   while (choose3(ll + 1) <= r) ++ll;
