@@ -55,13 +55,17 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # `traffic` (ncu, one capture of the same workload).
 # kernel -> (unit, bytes per unit, work_totals key, DRAM bytes per launch from
 # one ncu capture of the headline workload, or None). The census_TX span is
-# the sparse TX pass: the split and its two kernels (k_census_txs<32> on
-# 3-hyperedges with a long list, <8> on the rest); its traffic is the sum of
-# the two kernels' read + write bytes.
+# the TX kernel alone (k_census_txs, one persistent launch); its preparation
+# (member-pair set, quad filter, wedge records, split) is the census_TX_prep
+# span.
 ROOFLINE_HBM = {
-    "census_TX": ("TX candidate", 288, "census_TX",
-                  194_833_152 + 14_434_560 + 155_997_696 + 4_086_784),
+    "census_TX": ("TX candidate", 288, "census_TX", 231_894_528 + 13_131_776),
     "census_Q": ("4-hyperedge", 320, "census_Q", None),
+}
+# ncu evidence beside the byte model (same capture as the traffic above):
+# L2 sectors per launch and the launch's serialised duration.
+ROOFLINE_NCU = {
+    "census_TX": {"kernel": "k_census_txs", "lts_t_sectors": 35_297_158, "ncu_us": 414.9},
 }
 
 # ALU roofline of the dense (bitmap) census kernels, for the face-to-face row:
@@ -138,7 +142,11 @@ def hbm_roofline(kernel: str, totals: dict, avg_launch_s: float, peak_gbs: float
             "launch_ms": avg_launch_s * 1e3,
             "peak_source": f"hbm_gbs {src} (copy bandwidth)",
             "reading": "per-candidate probe bytes of the method (32 B sector per probe); "
-                       "the kernel counts most candidates in bulk without probing"}
+                       "the kernel counts most candidates in bulk without probing",
+            **({"dram_gbs_from_traffic": traffic / avg_launch_s / 1e9,
+                "dram_frac_from_traffic": traffic / avg_launch_s / 1e9 / peak_gbs}
+               if traffic else {}),
+            **({"ncu": ROOFLINE_NCU[kernel]} if kernel in ROOFLINE_NCU else {})}
 
 
 def max_over_ranks(x: float, device: str = "cuda") -> float:

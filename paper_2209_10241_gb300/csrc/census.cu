@@ -1379,9 +1379,11 @@ void launch_txs(const hm_graph* g, unsigned long long* hist, cudaStream_t s, boo
   int64_t* rs = reinterpret_cast<int64_t*>(buf.p + o_runs);
   int64_t* re = rs + m3;
   uint64_t* rec = reinterpret_cast<uint64_t*>(buf.p + o_rec);
+  // two trace spans: the preparation (member-pair set, quad filter, wedge
+  // records and their sort, the split) and the TX kernel itself
   cudaEvent_t ev = nullptr;
-  const bool tr = traced && trace_on("census_TX");
-  if (tr) trace_begin(s, &ev);
+  const bool trp = traced && trace_on("census_TX_prep");
+  if (trp) trace_begin(s, &ev);
   HM_CUDA(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned int), s));
   HM_CUDA(cudaMemsetAsync(tab, 0xFF, (size_t)tcap * 8, s));
   HM_CUDA(cudaMemsetAsync(bloom, 0, (size_t)nbits / 8, s));
@@ -1408,6 +1410,9 @@ void launch_txs(const hm_graph* g, unsigned long long* hist, cudaStream_t s, boo
   k_txs_split<<<grid1d(m3), 256, 0, s>>>(g->view(), tab, tcap - 1, bloom, nbits, g->out_deg, rs,
                                          re, share, small, large, counts);
   HM_KCHECK();
+  if (trp) trace_end("census_TX_prep", s, ev);
+  const bool tr = traced && trace_on("census_TX");
+  if (tr) trace_begin(s, &ev);
   int sms = 0, per = 0;
   resident_blocks((const void*)k_census_txs, sms, per);
   const int64_t want = (m3 + CENSUS_THREADS / 8 - 1) / (CENSUS_THREADS / 8);
