@@ -54,44 +54,71 @@ __device__ __forceinline__ void set_bit(const BitsOut& o, uint32_t* bm, int32_t 
   atomicOr(bm + (size_t)a * o.bw + (c >> 5), 1u << (c & 31));
 }
 
-// Slot of this lane in counter cnt[size]: the lanes of the warp that reach
-// this point with the same size share one atomic (tens of thousands of
-// same-address atomics otherwise serialise in L2).
-__device__ __forceinline__ unsigned long long agg_slot(unsigned long long* cnt, int size) {
-  const unsigned am = __activemask();
-  const unsigned peers = __match_any_sync(am, size);
-  const int leader = __ffs(peers) - 1, lane = threadIdx.x & 31;
-  unsigned long long base = 0;
-  if (lane == leader) base = atomicAdd(&cnt[size], (unsigned long long)__popc(peers));
-  base = __shfl_sync(peers, base, leader);
-  return base + (unsigned long long)__popc(peers & ((1u << lane) - 1u));
-}
+// Normalisation: hyperedge j's members (sorted, repeats collapsed) as long as
+// it has at most kmax distinct members; hyperedges with more are only counted
+// (size kmax + 1). MODE 0 only counts per size; MODE 1 emits the packed sort
+// key of each kept hyperedge of size >= 2 (members concatenated with b bits
+// each, most significant first); MODE 2 sets the bitmap bits of each kept
+// hyperedge instead (pairs, co-occurrence, exact triple rows) and emits sort
+// keys only for 3- and 4-hyperedges.
+//
+// A block takes NORM_ITEMS * 256 consecutive hyperedges, each warp 32 *
+// NORM_ITEMS of them, whose members are one contiguous range of the input:
+// the warp stages up to NORM_STAGE of them in shared memory with coalesced
+// loads (the rest are read directly), then each lane normalises NORM_ITEMS
+// hyperedges. Output slots come from per-block counts in shared memory and
+// one global atomic per size per block: same-address atomics serialise in
+// L2, so one per warp and size (a quarter of a million on 2M hyperedges) cost
+// more than the rest of the kernel.
+constexpr int NORM_THREADS = 256;
+constexpr int NORM_ITEMS = 4;
+constexpr int NORM_STAGE = 1024;  // staged members per warp (4 KB)
+constexpr int64_t NORM_TILE = (int64_t)NORM_THREADS * NORM_ITEMS;
 
-// One thread per input hyperedge: the set of its members (sorted, repeats
-// collapsed) as long as it has at most kmax distinct members. MODE 0 only
-// counts per size; MODE 1 emits the packed sort key of each kept hyperedge
-// (members concatenated with b bits each, most significant first); MODE 2
-// sets the bitmap bits of each kept hyperedge instead (pairs, co-occurrence,
-// exact triple rows) and emits sort keys only for 3- and 4-hyperedges.
+unsigned norm_grid(int64_t m) { return (unsigned)((m + NORM_TILE - 1) / NORM_TILE); }
+
 template <int MODE>
-__global__ void k_normalize(const int32_t* __restrict__ mem, const int64_t* __restrict__ off,
-                            int64_t m, int32_t n, int kmax, int b,
-                            unsigned long long* __restrict__ cnt, int* __restrict__ err,
-                            uint64_t* __restrict__ c2, uint64_t* __restrict__ c3hi,
-                            uint64_t* __restrict__ c3lo, uint64_t* __restrict__ c4hi,
-                            uint64_t* __restrict__ c4lo, const BitsOut bo) {
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
-       j += (int64_t)gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(NORM_THREADS)
+    k_normalize(const int32_t* __restrict__ mem, const int64_t* __restrict__ off, int64_t m,
+                int32_t n, int kmax, int b, unsigned long long* __restrict__ cnt,
+                int* __restrict__ err, uint64_t* __restrict__ c2, uint64_t* __restrict__ c3hi,
+                uint64_t* __restrict__ c3lo, uint64_t* __restrict__ c4hi,
+                uint64_t* __restrict__ c4lo, const BitsOut bo) {
+  __shared__ int32_t stage[NORM_THREADS / 32][NORM_STAGE];
+  __shared__ unsigned int scnt[8];
+  __shared__ unsigned long long sbase[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x < 8) scnt[threadIdx.x] = 0;
+  const int64_t w0 = (int64_t)blockIdx.x * NORM_TILE + (int64_t)warp * 32 * NORM_ITEMS;
+  const int64_t wend = min(w0 + 32 * NORM_ITEMS, m);
+  // the warp's member range, clamped to the input (offsets[m] members)
+  int64_t lo = 0, len = 0;
+  if (w0 < m) {
+    lo = off[w0];
+    const int64_t hi = min(off[wend], off[m]);
+    if (lo >= 0 && hi > lo) len = min(hi - lo, (int64_t)NORM_STAGE);
+  }
+  for (int64_t i = lane; i < len; i += 32) stage[warp][i] = mem[lo + i];
+  __syncwarp();
+  int32_t v[NORM_ITEMS][5];
+  int sz[NORM_ITEMS];  // 0: nothing to count or emit
+#pragma unroll
+  for (int it = 0; it < NORM_ITEMS; ++it) {
+    const int64_t j = w0 + it * 32 + lane;
+    sz[it] = 0;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) v[it][i] = 0;
+    if (j >= m) continue;
     const int64_t s0 = off[j], s1 = off[j + 1];
     if (s1 < s0 || s0 < 0) {
       atomicOr(err, ERR_OFFSETS);
       continue;
     }
-    int32_t v[5] = {0, 0, 0, 0, 0};
     int cntd = 0;
     bool big = false, bad = false;
     for (int64_t p = s0; p < s1; ++p) {
-      const int32_t x = mem[p];
+      const int64_t q = p - lo;
+      const int32_t x = (q >= 0 && q < len) ? stage[warp][q] : mem[p];
       if (x < 0 || x >= n) {
         bad = true;
         continue;
@@ -101,16 +128,16 @@ __global__ void k_normalize(const int32_t* __restrict__ mem, const int64_t* __re
       int pos = 0;
 #pragma unroll
       for (int i = 0; i < 5; ++i) {
-        present |= (i < cntd && v[i] == x);
-        pos += (i < cntd && v[i] < x) ? 1 : 0;
+        present |= (i < cntd && v[it][i] == x);
+        pos += (i < cntd && v[it][i] < x) ? 1 : 0;
       }
       if (present) continue;
 #pragma unroll
       for (int i = 4; i > 0; --i)
-        if (i > pos && i <= cntd) v[i] = v[i - 1];
+        if (i > pos && i <= cntd) v[it][i] = v[it][i - 1];
 #pragma unroll
       for (int i = 0; i < 5; ++i)
-        if (i == pos) v[i] = x;
+        if (i == pos) v[it][i] = x;
       ++cntd;
       if (cntd > kmax) big = true;
     }
@@ -119,40 +146,68 @@ __global__ void k_normalize(const int32_t* __restrict__ mem, const int64_t* __re
       continue;
     }
     if (big) {
-      if (MODE == 0) agg_slot(cnt, kmax + 1);
+      if (MODE == 0) sz[it] = kmax + 1;
       continue;
     }
     if (cntd < 2) continue;
     if (MODE == 2) {
-      for (int i = 0; i < cntd; ++i)
-        for (int j = 0; j < cntd; ++j)
-          if (i != j)
-            set_bit(bo, cntd == 2 ? bo.bits2 : cntd == 3 ? bo.bits3 : bo.bits4, v[i], v[j]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (i < cntd && k < cntd && i != k)
+            set_bit(bo, cntd == 2 ? bo.bits2 : cntd == 3 ? bo.bits3 : bo.bits4, v[it][i],
+                    v[it][k]);
       if (cntd == 3 && bo.tri3) {
+#pragma unroll
         for (int i = 0; i < 3; ++i)
-          for (int j = 0; j < 3; ++j) {
-            if (i == j) continue;
-            const int32_t c = v[3 - i - j];
-            atomicOr(bo.tri3 + ((size_t)v[i] * bo.n + v[j]) * bo.bw + (c >> 5), 1u << (c & 31));
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            if (i == k) continue;
+            const int32_t c = v[it][3 - i - k];
+            atomicOr(bo.tri3 + ((size_t)v[it][i] * bo.n + v[it][k]) * bo.bw + (c >> 5),
+                     1u << (c & 31));
           }
       }
       if (cntd == 2) continue;
     }
-    const unsigned long long slot = agg_slot(cnt, cntd);
-    if (MODE >= 1) {
-      unsigned __int128 key = 0;
+    sz[it] = cntd;
+  }
+  __syncthreads();  // scnt zeroed
+  // slots: lanes with the same size share one shared-memory atomic per item
+  unsigned loc[NORM_ITEMS];
+  const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (i < cntd) key = (key << b) | (uint32_t)v[i];
-      if (cntd == 2) {
-        c2[slot] = (uint64_t)key;
-      } else if (cntd == 3) {
-        c3lo[slot] = (uint64_t)key;
-        c3hi[slot] = (uint64_t)(key >> 64);
-      } else {
-        c4lo[slot] = (uint64_t)key;
-        c4hi[slot] = (uint64_t)(key >> 64);
-      }
+  for (int it = 0; it < NORM_ITEMS; ++it) {
+    const unsigned peers = __match_any_sync(0xffffffffu, sz[it]);
+    const int leader = __ffs(peers) - 1;
+    unsigned base = 0;
+    if (sz[it] && lane == leader) base = atomicAdd(&scnt[sz[it]], (unsigned)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    loc[it] = base + (unsigned)__popc(peers & lt);
+  }
+  __syncthreads();
+  if (threadIdx.x < 8 && scnt[threadIdx.x])
+    sbase[threadIdx.x] = atomicAdd(&cnt[threadIdx.x], (unsigned long long)scnt[threadIdx.x]);
+  if (MODE == 0) return;
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < NORM_ITEMS; ++it) {
+    const int cntd = sz[it];
+    if (!cntd) continue;
+    const unsigned long long slot = sbase[cntd] + loc[it];
+    unsigned __int128 key = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (i < cntd) key = (key << b) | (uint32_t)v[it][i];
+    if (cntd == 2) {
+      c2[slot] = (uint64_t)key;
+    } else if (cntd == 3) {
+      c3lo[slot] = (uint64_t)key;
+      c3hi[slot] = (uint64_t)(key >> 64);
+    } else {
+      c4lo[slot] = (uint64_t)key;
+      c4hi[slot] = (uint64_t)(key >> 64);
     }
   }
 }
@@ -535,7 +590,7 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   unsigned long long* cnt2 = counters.p + 8;
   int* err_p = reinterpret_cast<int*>(counters.p + 16);
   if (m > 0) {
-    k_normalize<0><<<grid1d(m), T256, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt, err_p,
+    k_normalize<0><<<norm_grid(m), NORM_THREADS, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt, err_p,
                                               nullptr, nullptr, nullptr, nullptr, nullptr,
                                               BitsOut{});
     HM_KCHECK();
@@ -652,10 +707,10 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     uint64_t *c2, *c3hi, *c3lo, *c4hi, *c4lo;
     std::tie(c2, c3hi, c3lo, c4hi, c4lo) = keyp;
     if (bitmaps)
-      k_normalize<2><<<grid1d(m), T256, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt2, err_p,
+      k_normalize<2><<<norm_grid(m), NORM_THREADS, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt2, err_p,
                                                 c2, c3hi, c3lo, c4hi, c4lo, bo);
     else
-      k_normalize<1><<<grid1d(m), T256, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt2, err_p,
+      k_normalize<1><<<norm_grid(m), NORM_THREADS, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt2, err_p,
                                                 c2, c3hi, c3lo, c4hi, c4lo, bo);
     HM_KCHECK();
   }

@@ -534,6 +534,10 @@ struct hm_graph {
   Space TXO;
   int32_t* out_deg = nullptr;
   int32_t* out_adj = nullptr;
+  // node -> 4-hyperedges containing it (indices into e4, any order); built
+  // by the sampler on first use at order 4
+  int64_t* off4 = nullptr;
+  int32_t* inc4 = nullptr;
   bool useWb = false, useSb = false, usePb = false, useTXb = false;
   // order 4: pairs-only sets from graphlet identities instead of S and P
   bool useGL = false;

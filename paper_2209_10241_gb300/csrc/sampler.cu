@@ -24,6 +24,8 @@
 //                pair-neighbour of c outside L1 ∪ e. Sets holding a 3- or
 //                4-hyperedge are dropped (max-cardinality rule).
 #include <cmath>
+#include <cstdlib>
+#include <functional>
 #include <mutex>
 
 #include "families.cuh"
@@ -444,6 +446,590 @@ uint64_t scan_total(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t s
   return tot;
 }
 
+// ---------------------------------------------------------------- order 4, pair stratum by types
+// For a drawn pair e = {a, b} at order 4, the sets Alg. 4 counts are the
+// 4-node sets V' containing e whose induced sub-hypergraph is connected and
+// holds no 3- or 4-hyperedge, i.e. the connected induced 4-node subgraphs of
+// the pair graph that contain the edge ab, less those holding a larger
+// hyperedge. With N_a = N2(a)\{b}, N_b = N2(b)\{a}, T = N_a ∩ N_b, A = N_a \ T
+// and B = N_b \ T (sizes sa, sb, t), every such set {a, b, c, d} is either
+//  (1) c, d both in A ∪ B ∪ T: its pattern depends only on the types of c
+//      and d and on whether cd is a pair -- C(sa+sb+t, 2) sets, counted from
+//      sa, sb, t plus one correction per pair inside A ∪ B ∪ T;
+//  (2) c in A ∪ B ∪ T and d a pair neighbour of c outside A ∪ B ∪ T ∪ {a, b}:
+//      a path (c in A or B) or a paw (c in T).
+// So instead of testing all C(sa+sb+t, 2) + Σ deg(c) candidates, each draw
+// costs one scan of the pair neighbours of every c (two membership probes per
+// neighbour); the sets that hold a 3- or 4-hyperedge all contain a 3- or
+// 4-hyperedge through a or b, so they are found from those lists and
+// subtracted (each once, by a fixed precedence among the hyperedges it
+// holds). Sums are 128-bit two's complement (a subtraction adds the negated
+// product), exact in any order, and equal the per-candidate enumeration's.
+
+enum { PP_STAR = 0, PP_PATH = 1, PP_PAW = 2, PP_C4 = 3, PP_DIAMOND = 4, PP_K4 = 5 };
+enum { TY_A = 0, TY_B = 1, TY_T = 2 };
+// one labelled pair mask of each pairs-only pattern (a = 0, b = 1, c = 2, d = 3;
+// bits ab, ac, ad, bc, bd, cd): star at a, path c-a-b-d, paw, 4-cycle, diamond, 4-clique
+constexpr int kPatternMask[6] = {7, 19, 39, 51, 31, 63};
+
+struct PairClasses {
+  int cls[6];
+};
+
+// Adds (or subtracts) w * c to the 128-bit class sum (blo, bhi)[cls].
+__device__ __forceinline__ void bins_add(unsigned long long* blo, unsigned long long* bhi, int cls,
+                                         uint64_t w, uint64_t c, bool neg) {
+  if (c == 0) return;
+  unsigned long long lo = w * c, hi = __umul64hi(w, c);
+  if (neg) {
+    hi = ~hi + (lo == 0 ? 1ull : 0ull);
+    lo = 0ull - lo;
+  }
+  const unsigned long long old = atomicAdd(&blo[cls], lo);
+  const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+  if (hi + carry) atomicAdd(&bhi[cls], hi + carry);
+}
+
+__device__ __forceinline__ void bins_flush(const unsigned long long* blo,
+                                           const unsigned long long* bhi, int ncls,
+                                           unsigned long long* raw) {
+  for (int i = threadIdx.x; i < ncls; i += blockDim.x) {
+    const unsigned long long lo = blo[i], hi = bhi[i];
+    if (lo | hi) {
+      const unsigned long long old = atomicAdd(&raw[2 * i], lo);
+      const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+      if (hi + carry) atomicAdd(&raw[2 * i + 1], hi + carry);
+    }
+  }
+}
+
+// Lanes whose update has the same key add one w x count (uniform draws: the
+// key is the class and sign; weighted: also the draw).
+template <bool kWeighted>
+__device__ __forceinline__ void bins_vote(unsigned long long* blo, unsigned long long* bhi, int cls,
+                                          bool neg, uint32_t draw, const uint64_t* wt) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long key =
+      cls < 0 ? ~0ull
+              : ((kWeighted ? (unsigned long long)draw << 9 : 0ull) |
+                 ((unsigned long long)neg << 8) | (unsigned long long)cls);
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  if (cls >= 0 && lane == __ffs(peers) - 1)
+    bins_add(blo, bhi, cls, kWeighted ? wt[draw] : 1ull, (uint64_t)__popc(peers), neg);
+}
+
+// Pair mask of {a, b, x, y} (ab present) and whether its pairs connect it.
+__device__ __forceinline__ bool pair_pattern(const DevGraph& g, int32_t a, int32_t b, int32_t x,
+                                             int32_t y, uint32_t& mask) {
+  const bool ax = has_pair(g, a, x), ay = has_pair(g, a, y), bx = has_pair(g, b, x),
+             by = has_pair(g, b, y), xy = has_pair(g, x, y);
+  mask = 1u | (ax ? 2u : 0u) | (ay ? 4u : 0u) | (bx ? 8u : 0u) | (by ? 16u : 0u) | (xy ? 32u : 0u);
+  const bool xa = ax || bx, ya = ay || by;  // x / y adjacent to {a, b}
+  return (xa || (xy && ya)) && (ya || (xy && xa));
+}
+
+// Elements of the drawn pairs' lists L1 = N2(a)\{b} ++ N2(b)\{a} (the second
+// part without N2(a)): per element (draw | type << 30, node or -1), its pair
+// degree (the neighbours stage (2) scans), and per draw the size t of T.
+__global__ void k_pair_elems(const DevGraph g, const int64_t* __restrict__ sidx,
+                             const uint64_t* __restrict__ eoff, int64_t cnt, uint64_t ne,
+                             int2* __restrict__ elems, uint64_t* __restrict__ ework,
+                             unsigned* __restrict__ tcnt) {
+  const uint64_t nchunks = (ne + CHUNK - 1) / CHUNK;
+  for (uint64_t ch = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; ch < nchunks;
+       ch += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t j0 = ch * CHUNK, j1 = min(j0 + (uint64_t)CHUNK, ne);
+    int64_t i = anchor_of(eoff, cnt, j0);
+    PairList L = pair_list(g, sidx[i]);
+    unsigned tr = 0;
+    for (uint64_t j = j0; j < j1; ++j) {
+      if (j >= eoff[i + 1]) {
+        if (tr) atomicAdd(&tcnt[i], tr);
+        tr = 0;
+        do {
+          ++i;
+        } while (eoff[i + 1] == eoff[i]);
+        L = pair_list(g, sidx[i]);
+      }
+      const uint32_t r = (uint32_t)(j - eoff[i]);
+      const int32_t c = list_elem(g, L, r);
+      uint32_t ty;
+      bool valid = true;
+      if (r < L.la) {
+        ty = has_pair(g, L.b, c) ? TY_T : TY_A;
+        tr += ty == TY_T ? 1u : 0u;
+      } else {
+        ty = TY_B;
+        valid = !has_pair(g, L.a, c);  // listed from a already (in T)
+      }
+      elems[j] = make_int2((int32_t)((uint32_t)i | (ty << 30)), valid ? c : -1);
+      ework[j] = valid ? (uint64_t)deg2(g, c) : 0ull;
+    }
+    if (tr) atomicAdd(&tcnt[i], tr);
+  }
+}
+
+// Per draw: the stage (1) sets without a pair cd (from sa, sb, t), and the
+// sizes of the stage (3) spaces: 3-hyperedges through a and b and
+// 4-hyperedges through a (xw), at most min(t3(a), t3(b)) 3-hyperedges
+// through both (gw).
+template <bool kWeighted>
+__global__ void __launch_bounds__(SAMPLE_THREADS)
+    k_pair_terms(const DevGraph g, const int64_t* __restrict__ sidx,
+                 const unsigned* __restrict__ tcnt, int64_t cnt, const uint64_t* __restrict__ wt,
+                 const int64_t* __restrict__ off4, const PairClasses pc, int ncls,
+                 unsigned long long* __restrict__ raw, uint64_t* __restrict__ xw,
+                 uint64_t* __restrict__ gw) {
+  __shared__ unsigned long long blo[176], bhi[176];
+  for (int i = threadIdx.x; i < ncls; i += blockDim.x) blo[i] = bhi[i] = 0;
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t ab = g.e2[sidx[i]];
+    const int32_t a = (int32_t)(ab >> 32), b = (int32_t)(ab & 0xFFFFFFFFull);
+    const uint64_t t = tcnt[i];
+    const uint64_t sa = (uint64_t)deg2(g, a) - 1 - t, sb = (uint64_t)deg2(g, b) - 1 - t;
+    const uint64_t w = kWeighted ? wt[i] : 1ull;
+    bins_add(blo, bhi, pc.cls[PP_STAR], w, sa * (sa - 1) / 2 + sb * (sb - 1) / 2, false);
+    bins_add(blo, bhi, pc.cls[PP_PATH], w, sa * sb, false);
+    bins_add(blo, bhi, pc.cls[PP_PAW], w, (sa + sb) * t, false);
+    bins_add(blo, bhi, pc.cls[PP_DIAMOND], w, t * (t - 1) / 2, false);
+    const uint64_t t3a = g.off3 ? (uint64_t)(g.off3[a + 1] - g.off3[a]) : 0,
+                   t3b = g.off3 ? (uint64_t)(g.off3[b + 1] - g.off3[b]) : 0,
+                   q4a = off4 ? (uint64_t)(off4[a + 1] - off4[a]) : 0;
+    xw[i] = t3a + t3b + q4a;
+    gw[i] = min(t3a, t3b);
+  }
+  __syncthreads();
+  bins_flush(blo, bhi, ncls, raw);
+}
+
+// Stage (1) corrections and stage (2): items (element c of a draw, pair
+// neighbour x of c). x outside A ∪ B ∪ T ∪ {a, b}: the set {a, b, c, x} (a
+// path, or a paw when c is in T). x in A ∪ B ∪ T: the pair cx moves the set
+// {a, b, c, x} from its pattern without cx to the one with it, counted once
+// (from the endpoint of the lower type, or the lower id within a type).
+template <bool kWeighted>
+__global__ void __launch_bounds__(SAMPLE_THREADS)
+    k_pair_bulk(const DevGraph g, const int64_t* __restrict__ sidx, const int2* __restrict__ elems,
+                const uint64_t* __restrict__ ews, int64_t ne, uint64_t total,
+                const uint64_t* __restrict__ wt, const PairClasses pc, int ncls,
+                unsigned long long* __restrict__ raw) {
+  __shared__ unsigned long long blo[176], bhi[176];
+  __shared__ int pcs[6];
+  for (int i = threadIdx.x; i < ncls; i += blockDim.x) blo[i] = bhi[i] = 0;
+  if (threadIdx.x < 6) pcs[threadIdx.x] = pc.cls[threadIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint64_t nchunks = (total + CHUNK - 1) / CHUNK;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t cb = warp * 32; cb < nchunks; cb += nwarps * 32) {
+    const uint64_t g0 = (cb + lane) * CHUNK;
+    const uint64_t g1 = min(g0 + CHUNK, total);
+    int64_t j = 0;
+    uint64_t r = 0, wa = 0;
+    int32_t a = 0, b = 0, c = 0;
+    int64_t co = 0;
+    uint32_t ty = 0, di = 0;
+    auto load = [&](int64_t jj) {
+      const int2 el = elems[jj];
+      di = (uint32_t)el.x & 0x3FFFFFFFu;
+      ty = (uint32_t)el.x >> 30;
+      c = el.y;
+      const uint64_t ab = g.e2[sidx[di]];
+      a = (int32_t)(ab >> 32);
+      b = (int32_t)(ab & 0xFFFFFFFFull);
+      co = g.off2[c];
+      wa = ews[jj + 1] - ews[jj];
+    };
+    if (g0 < total) {
+      j = anchor_of(ews, ne, g0);
+      r = g0 - ews[j];
+      load(j);
+    }
+    for (int it = 0; it < CHUNK; ++it) {
+      const uint64_t gi = g0 + it;
+      int pp = -1, pn = -1;
+      if (gi < g1) {
+        if (r == wa) {
+          do {
+            ++j;
+          } while (ews[j + 1] == ews[j]);
+          r = 0;
+          load(j);
+        }
+        const int32_t x = g.adj2[co + r];
+        ++r;
+        if (x != a && x != b) {
+          const bool inA = has_pair(g, a, x), inB = has_pair(g, b, x);
+          if (!inA && !inB) {
+            pp = ty == TY_T ? PP_PAW : PP_PATH;
+          } else {
+            const uint32_t tx = inA ? (inB ? TY_T : TY_A) : TY_B;
+            if (ty < tx || (ty == tx && c < x)) {
+              const uint32_t hi = max(ty, tx), lo = min(ty, tx);
+              if (hi == TY_T) {
+                pp = lo == TY_T ? PP_K4 : PP_DIAMOND;
+                pn = lo == TY_T ? PP_DIAMOND : PP_PAW;
+              } else if (lo == hi) {  // both in A or both in B
+                pp = PP_PAW;
+                pn = PP_STAR;
+              } else {  // one in A, one in B
+                pp = PP_C4;
+                pn = PP_PATH;
+              }
+            }
+          }
+        }
+      }
+      bins_vote<kWeighted>(blo, bhi, pp >= 0 ? pcs[pp] : -1, false, di, wt);
+      bins_vote<kWeighted>(blo, bhi, pn >= 0 ? pcs[pn] : -1, true, di, wt);
+    }
+  }
+  __syncthreads();
+  bins_flush(blo, bhi, ncls, raw);
+}
+
+// Stage (3), sets holding a larger hyperedge, each subtracted once: items
+// per draw run over the 3-hyperedges through a, then through b, then the
+// 4-hyperedges through a. A 3-hyperedge {a, b, c} goes to a list (its sets
+// are every d with {a, b, c, d} connected, handled by k_pair_g1). Otherwise
+// the hyperedge names one set {a, b, x, y}, subtracted when its pairs connect
+// it and it holds none of the hyperedges that come first: 3-hyperedges with
+// a and b, then with a, then with b, then the 4-hyperedge.
+template <bool kWeighted>
+__global__ void __launch_bounds__(SAMPLE_THREADS)
+    k_pair_excl(const DevGraph g, const int64_t* __restrict__ sidx,
+                const uint64_t* __restrict__ xs, int64_t cnt, uint64_t total,
+                const uint64_t* __restrict__ wt, const int64_t* __restrict__ off4,
+                const int32_t* __restrict__ inc4, const uint8_t* __restrict__ lut_g, int ncls,
+                unsigned long long* __restrict__ raw, int2* __restrict__ g1, uint64_t cap1,
+                unsigned long long* __restrict__ g1n) {
+  __shared__ unsigned long long blo[176], bhi[176];
+  __shared__ uint8_t lut[64];
+  for (int i = threadIdx.x; i < ncls; i += blockDim.x) blo[i] = bhi[i] = 0;
+  if (threadIdx.x < 64) lut[threadIdx.x] = lut_g[threadIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint64_t nchunks = (total + CHUNK - 1) / CHUNK;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t cb = warp * 32; cb < nchunks; cb += nwarps * 32) {
+    const uint64_t g0 = (cb + lane) * CHUNK;
+    const uint64_t g1e = min(g0 + CHUNK, total);
+    int64_t i = 0;
+    uint64_t r = 0, wa = 0, t3a = 0, t3b = 0;
+    int32_t a = 0, b = 0;
+    auto load = [&](int64_t ii) {
+      const uint64_t ab = g.e2[sidx[ii]];
+      a = (int32_t)(ab >> 32);
+      b = (int32_t)(ab & 0xFFFFFFFFull);
+      t3a = g.off3 ? (uint64_t)(g.off3[a + 1] - g.off3[a]) : 0;
+      t3b = g.off3 ? (uint64_t)(g.off3[b + 1] - g.off3[b]) : 0;
+      wa = xs[ii + 1] - xs[ii];
+    };
+    if (g0 < total) {
+      i = anchor_of(xs, cnt, g0);
+      r = g0 - xs[i];
+      load(i);
+    }
+    for (int it = 0; it < CHUNK; ++it) {
+      const uint64_t gi = g0 + it;
+      int cls = -1;
+      if (gi < g1e) {
+        if (r == wa) {
+          do {
+            ++i;
+          } while (xs[i + 1] == xs[i]);
+          r = 0;
+          load(i);
+        }
+        int32_t x = -1, y = -1;
+        bool emit = false;
+        if (r < t3a) {
+          const int4 e = g.e3[g.inc3[g.off3[a] + (int64_t)r]];
+          x = e.x == a ? e.y : e.x;
+          y = e.z == a ? e.y : e.z;
+          if (x == b || y == b) {
+            const unsigned long long slot = atomicAdd(g1n, 1ull);
+            if (slot < cap1) g1[slot] = make_int2((int32_t)i, x == b ? y : x);
+          } else {
+            emit = !has_triple(g, a, b, x) && !has_triple(g, a, b, y);
+          }
+        } else if (r < t3a + t3b) {
+          const int4 e = g.e3[g.inc3[g.off3[b] + (int64_t)(r - t3a)]];
+          x = e.x == b ? e.y : e.x;
+          y = e.z == b ? e.y : e.z;
+          emit = x != a && y != a && !has_triple(g, a, b, x) && !has_triple(g, a, b, y) &&
+                 !has_triple(g, a, x, y);
+        } else {
+          const int4 q = g.e4[inc4[off4[a] + (int64_t)(r - t3a - t3b)]];
+          const int32_t m[4] = {q.x, q.y, q.z, q.w};
+          int k = 0;
+          bool hb = false;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (m[u] == b) hb = true;
+            if (m[u] != a && m[u] != b) {
+              if (k == 0) x = m[u];
+              else y = m[u];
+              ++k;
+            }
+          }
+          emit = hb && !has_triple(g, a, b, x) && !has_triple(g, a, b, y) &&
+                 !has_triple(g, a, x, y) && !has_triple(g, b, x, y);
+        }
+        ++r;
+        uint32_t mask = 0;
+        if (emit && pair_pattern(g, a, b, x, y, mask)) cls = lut[mask];
+      }
+      bins_vote<kWeighted>(blo, bhi, cls, true, (uint32_t)i, wt);
+    }
+  }
+  __syncthreads();
+  bins_flush(blo, bhi, ncls, raw);
+}
+
+// Per listed 3-hyperedge {a, b, c}: its units, the draw's list L1 then c's
+// pair neighbours.
+__global__ void k_pair_g1_units(const DevGraph g, const int2* __restrict__ g1, int64_t n1,
+                                const uint64_t* __restrict__ eoff, uint64_t* __restrict__ uw) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n1;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int2 e = g1[k];
+    uw[k] = (eoff[e.x + 1] - eoff[e.x]) + (uint64_t)deg2(g, e.y);
+  }
+}
+
+// The sets {a, b, c, d} holding the 3-hyperedge {a, b, c}: d in L1 (an
+// element of the draw's list) or a pair neighbour of c outside L1 ∪ {a, b};
+// subtracted when connected by their pairs, unless {a, b, d} is a
+// 3-hyperedge too and d < c (the set then goes with d).
+template <bool kWeighted>
+__global__ void __launch_bounds__(SAMPLE_THREADS)
+    k_pair_g1(const DevGraph g, const int64_t* __restrict__ sidx, const int2* __restrict__ g1,
+              const uint64_t* __restrict__ us, int64_t n1, uint64_t total,
+              const uint64_t* __restrict__ eoff, const int2* __restrict__ elems,
+              const uint64_t* __restrict__ wt, const uint8_t* __restrict__ lut_g, int ncls,
+              unsigned long long* __restrict__ raw) {
+  __shared__ unsigned long long blo[176], bhi[176];
+  __shared__ uint8_t lut[64];
+  for (int i = threadIdx.x; i < ncls; i += blockDim.x) blo[i] = bhi[i] = 0;
+  if (threadIdx.x < 64) lut[threadIdx.x] = lut_g[threadIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const uint64_t nchunks = (total + CHUNK - 1) / CHUNK;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t cb = warp * 32; cb < nchunks; cb += nwarps * 32) {
+    const uint64_t g0 = (cb + lane) * CHUNK;
+    const uint64_t g1e = min(g0 + CHUNK, total);
+    int64_t k = 0;
+    uint64_t r = 0, wa = 0, l = 0, e0 = 0;
+    int32_t a = 0, b = 0, c = 0;
+    int64_t co = 0;
+    uint32_t di = 0;
+    auto load = [&](int64_t kk) {
+      const int2 e = g1[kk];
+      di = (uint32_t)e.x;
+      c = e.y;
+      const uint64_t ab = g.e2[sidx[di]];
+      a = (int32_t)(ab >> 32);
+      b = (int32_t)(ab & 0xFFFFFFFFull);
+      e0 = eoff[di];
+      l = eoff[di + 1] - e0;
+      co = g.off2[c];
+      wa = us[kk + 1] - us[kk];
+    };
+    if (g0 < total) {
+      k = anchor_of(us, n1, g0);
+      r = g0 - us[k];
+      load(k);
+    }
+    for (int it = 0; it < CHUNK; ++it) {
+      const uint64_t gi = g0 + it;
+      int cls = -1;
+      if (gi < g1e) {
+        if (r == wa) {
+          do {
+            ++k;
+          } while (us[k + 1] == us[k]);
+          r = 0;
+          load(k);
+        }
+        int32_t d;
+        bool ok;
+        if (r < l) {
+          d = elems[e0 + r].y;
+          ok = d >= 0 && d != c;
+        } else {
+          d = g.adj2[co + (int64_t)(r - l)];
+          ok = d != a && d != b && !has_pair(g, a, d) && !has_pair(g, b, d);
+        }
+        ++r;
+        if (ok && !(d < c && has_triple(g, a, b, d))) {
+          uint32_t mask = 0;
+          if (pair_pattern(g, a, b, c, d, mask)) cls = lut[mask];
+        }
+      }
+      bins_vote<kWeighted>(blo, bhi, cls, true, di, wt);
+    }
+  }
+  __syncthreads();
+  bins_flush(blo, bhi, ncls, raw);
+}
+
+__global__ void k_deg4(const int4* __restrict__ e4, int64_t m, uint64_t* __restrict__ deg) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int4 e = e4[t];
+    atomicAdd((unsigned long long*)&deg[e.x], 1ull);
+    atomicAdd((unsigned long long*)&deg[e.y], 1ull);
+    atomicAdd((unsigned long long*)&deg[e.z], 1ull);
+    atomicAdd((unsigned long long*)&deg[e.w], 1ull);
+  }
+}
+
+__global__ void k_place4(const int4* __restrict__ e4, int64_t m, const int64_t* __restrict__ off,
+                         uint32_t* __restrict__ cursor, int32_t* __restrict__ inc) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int4 e = e4[t];
+    inc[off[e.x] + atomicAdd(&cursor[e.x], 1u)] = (int32_t)t;
+    inc[off[e.y] + atomicAdd(&cursor[e.y], 1u)] = (int32_t)t;
+    inc[off[e.z] + atomicAdd(&cursor[e.z], 1u)] = (int32_t)t;
+    inc[off[e.w] + atomicAdd(&cursor[e.w], 1u)] = (int32_t)t;
+  }
+}
+
+// node -> 4-hyperedges, kept in the graph (freed with it)
+void ensure_inc4(hm_graph* g, cudaStream_t st) {
+  if (g->off4 || g->kmax < 4 || g->counts[4] == 0) return;
+  const int64_t n = g->n, m4 = g->counts[4];
+  int64_t* off4 = dalloc<int64_t>((size_t)n + 1, st);
+  g->owned.push_back(off4);
+  int32_t* inc4 = dalloc<int32_t>((size_t)4 * m4, st);
+  g->owned.push_back(inc4);
+  DBuf<uint32_t> cursor((size_t)n, st);
+  HM_CUDA(cudaMemsetAsync(off4, 0, ((size_t)n + 1) * 8, st));
+  HM_CUDA(cudaMemsetAsync(cursor.p, 0, (size_t)n * 4, st));
+  k_deg4<<<grid_n(m4), 256, 0, st>>>(g->e4, m4, reinterpret_cast<uint64_t*>(off4));
+  HM_KCHECK();
+  ScanJob oj{reinterpret_cast<uint64_t*>(off4), n, nullptr};
+  scan_batch_inplace(&oj, 1, st);
+  k_place4<<<grid_n(m4), 256, 0, st>>>(g->e4, m4, off4, cursor.p, inc4);
+  HM_KCHECK();
+  g->off4 = off4;
+  g->inc4 = inc4;
+}
+
+// The class of each pairs-only pattern (host tables).
+PairClasses pair_classes() {
+  const ClassTables& T = class_tables(4);
+  PairClasses pc;
+  for (int p = 0; p < 6; ++p) pc.cls[p] = (int)T.lut[kPatternMask[p]];
+  return pc;
+}
+
+// Whether the per-candidate enumeration (SamPA / SamPB) serves the order-4
+// pair stratum instead (HM_SAMPLE_PAIR_ENUM=1, for tests).
+bool pair_enum() {
+  const char* env = std::getenv("HM_SAMPLE_PAIR_ENUM");
+  return env && env[0] == '1';
+}
+
+template <class K>
+void launch_walk(K kernel, uint64_t total, const char* name, cudaStream_t s,
+                 const std::function<void(unsigned)>& go) {
+  if (total == 0) return;
+  cudaEvent_t ev = nullptr;
+  const bool tr = trace_on(name);
+  if (tr) trace_begin(s, &ev);
+  go((unsigned)sample_blocks((const void*)kernel, total));
+  HM_KCHECK();
+  if (tr) trace_end(name, s, ev);
+}
+
+// The pair stratum of one batch at order 4 by types (see above).
+void pair_batch_bulk(const hm_graph* g, const DrawArgs& da, const int64_t* sidx,
+                     const uint64_t* wt, const uint64_t* lsize, bool weighted,
+                     unsigned long long* raw, cudaStream_t st) {
+  const int64_t cnt = da.count;
+  const ClassTables& T = class_tables(4);
+  const uint8_t* lut = device_lut(4);
+  const PairClasses pc = pair_classes();
+  const hm::DevGraph gv = g->view();
+  DBuf<uint64_t> eoff(cnt + 1, st), xw(cnt, st), gw(cnt, st), xs(cnt + 1, st), gs(cnt + 1, st);
+  DBuf<unsigned> tcnt(cnt, st);
+  DBuf<unsigned long long> g1n(1, st);
+  HM_CUDA(cudaMemsetAsync(tcnt.p, 0, (size_t)cnt * 4, st));
+  HM_CUDA(cudaMemsetAsync(g1n.p, 0, 8, st));
+  const uint64_t ne = scan_total(lsize, eoff.p, cnt, st);
+  DBuf<int2> elems(std::max<uint64_t>(ne, 1), st);
+  DBuf<uint64_t> ework(std::max<uint64_t>(ne, 1), st), ews(ne + 1, st);
+  if (ne) {
+    const uint64_t chunks = (ne + CHUNK - 1) / CHUNK;
+    k_pair_elems<<<grid_n((int64_t)chunks), 256, 0, st>>>(gv, sidx, eoff.p, cnt, ne, elems.p,
+                                                         ework.p, tcnt.p);
+    HM_KCHECK();
+  }
+  if (weighted)
+    k_pair_terms<true><<<grid_n(cnt), SAMPLE_THREADS, 0, st>>>(gv, sidx, tcnt.p, cnt, wt, g->off4,
+                                                               pc, T.ncls, raw, xw.p, gw.p);
+  else
+    k_pair_terms<false><<<grid_n(cnt), SAMPLE_THREADS, 0, st>>>(gv, sidx, tcnt.p, cnt, wt, g->off4,
+                                                                pc, T.ncls, raw, xw.p, gw.p);
+  HM_KCHECK();
+  if (ne) {
+    const uint64_t tb = scan_total(ework.p, ews.p, (int64_t)ne, st);
+    if (weighted)
+      launch_walk(k_pair_bulk<true>, tb, "sample_pair_bulk", st, [&](unsigned blocks) {
+        k_pair_bulk<true><<<blocks, SAMPLE_THREADS, 0, st>>>(gv, sidx, elems.p, ews.p,
+                                                            (int64_t)ne, tb, wt, pc, T.ncls, raw);
+      });
+    else
+      launch_walk(k_pair_bulk<false>, tb, "sample_pair_bulk", st, [&](unsigned blocks) {
+        k_pair_bulk<false><<<blocks, SAMPLE_THREADS, 0, st>>>(gv, sidx, elems.p, ews.p,
+                                                             (int64_t)ne, tb, wt, pc, T.ncls, raw);
+      });
+  }
+  const uint64_t tx = scan_total(xw.p, xs.p, cnt, st);
+  const uint64_t cap1 = scan_total(gw.p, gs.p, cnt, st);
+  if (tx == 0) return;
+  DBuf<int2> g1(std::max<uint64_t>(cap1, 1), st);
+  if (weighted)
+    launch_walk(k_pair_excl<true>, tx, "sample_pair_excl", st, [&](unsigned blocks) {
+      k_pair_excl<true><<<blocks, SAMPLE_THREADS, 0, st>>>(gv, sidx, xs.p, cnt, tx, wt, g->off4,
+                                                          g->inc4, lut, T.ncls, raw, g1.p, cap1, g1n.p);
+    });
+  else
+    launch_walk(k_pair_excl<false>, tx, "sample_pair_excl", st, [&](unsigned blocks) {
+      k_pair_excl<false><<<blocks, SAMPLE_THREADS, 0, st>>>(gv, sidx, xs.p, cnt, tx, wt, g->off4,
+                                                           g->inc4, lut, T.ncls, raw, g1.p, cap1, g1n.p);
+    });
+  unsigned long long n1 = 0;
+  HM_CUDA(cudaMemcpyAsync(&n1, g1n.p, 8, cudaMemcpyDeviceToHost, st));
+  HM_CUDA(cudaStreamSynchronize(st));
+  HM_CHECK(n1 <= cap1, HM_EINVAL,
+           "pair stratum: more 3-hyperedges through a drawn pair than min(t3(a), t3(b))");
+  if (n1 == 0) return;
+  DBuf<uint64_t> uw(n1, st), us(n1 + 1, st);
+  k_pair_g1_units<<<grid_n((int64_t)n1), 256, 0, st>>>(gv, g1.p, (int64_t)n1, eoff.p, uw.p);
+  HM_KCHECK();
+  const uint64_t tu = scan_total(uw.p, us.p, (int64_t)n1, st);
+  if (weighted)
+    launch_walk(k_pair_g1<true>, tu, "sample_pair_g1", st, [&](unsigned blocks) {
+      k_pair_g1<true><<<blocks, SAMPLE_THREADS, 0, st>>>(gv, sidx, g1.p, us.p, (int64_t)n1, tu,
+                                                        eoff.p, elems.p, wt, lut, T.ncls, raw);
+    });
+  else
+    launch_walk(k_pair_g1<false>, tu, "sample_pair_g1", st, [&](unsigned blocks) {
+      k_pair_g1<false><<<blocks, SAMPLE_THREADS, 0, st>>>(gv, sidx, g1.p, us.p, (int64_t)n1, tu,
+                                                         eoff.p, elems.p, wt, lut, T.ncls, raw);
+    });
+}
+
 // One batch of draws of stratum s.
 void sample_batch(const hm_graph* g, int order, int s, const DrawArgs& da, bool weighted,
                   unsigned long long* raw, cudaStream_t st) {
@@ -462,6 +1048,10 @@ void sample_batch(const hm_graph* g, int order, int s, const DrawArgs& da, bool 
       f.map = sidx.p;
       launch_sample(g, f, nullptr, 0, (uint64_t)cnt, wt.p, weighted, order, raw, st);
     }
+    return;
+  }
+  if (order == 4 && s == 2 && !pair_enum()) {
+    pair_batch_bulk(g, da, sidx.p, wt.p, lsize.p, weighted, raw, st);
     return;
   }
   const uint64_t total = scan_total(work.p, ws.p, cnt, st);
@@ -493,6 +1083,7 @@ void sample_batch(const hm_graph* g, int order, int s, const DrawArgs& da, bool 
 void count_sampled(hm_graph* g, int order, const uint64_t* S, uint64_t seed, const uint32_t* d_q,
                    double* d_est, uint64_t* d_raw, cudaStream_t st) {
   const ClassTables& T = class_tables(order);
+  if (order == 4 && S[2] > 0 && !pair_enum()) ensure_inc4(g, st);
   DBuf<unsigned long long> raw_tmp(d_raw ? 0 : 2 * T.ncls, st);
   unsigned long long* raw = d_raw ? (unsigned long long*)d_raw : raw_tmp.p;
   HM_CUDA(cudaMemsetAsync(raw, 0, 2 * T.ncls * sizeof(unsigned long long), st));

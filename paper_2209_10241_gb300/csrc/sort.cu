@@ -142,7 +142,7 @@ __device__ uint64_t look_back_warp(const uint64_t* status, int64_t tile) {
 // into exclusive digit offsets (one warp per (job, pass)) and writes 0 kept
 // keys for empty unique jobs.
 __global__ void __launch_bounds__(TPB)
-    k_sort_hist(const Batch B, const Grid G, uint32_t* done) {
+    k_sort_hist(const __grid_constant__ Batch B, const __grid_constant__ Grid G, uint32_t* done) {
   __shared__ uint32_t h[SORT_MAX_PASSES][256];
   __shared__ bool last;
   if (G.nj) {
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(TPB)
 }
 
 // Pass p of every job in the grid.
-__global__ void __launch_bounds__(TPB) k_sort_pass(const Batch B, const Grid G, int p) {
+__global__ void __launch_bounds__(TPB) k_sort_pass(const __grid_constant__ Batch B, const __grid_constant__ Grid G, int p) {
   __shared__ uint32_t wcnt[TPB / 32][256];
   __shared__ uint64_t toff[256];
   __shared__ uint32_t tile_s;
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(TPB) k_sort_pass(const Batch B, const Grid G, 
 // Unique + unpack of every unique job in the grid: a key is kept when it
 // differs from its predecessor; its output position is the number of kept
 // keys before it (block scan + look-back over tiles).
-__global__ void __launch_bounds__(TPB) k_sort_unique(const Batch B, const Grid G) {
+__global__ void __launch_bounds__(TPB) k_sort_unique(const __grid_constant__ Batch B, const __grid_constant__ Grid G) {
   __shared__ uint32_t wtot[TPB / 32];
   __shared__ uint64_t tile_excl;
   __shared__ uint32_t tile_s;
@@ -391,7 +391,7 @@ __device__ __forceinline__ void rank_masks(const JobDev& J, uint64_t& ma, uint64
   }
 }
 
-__global__ void __launch_bounds__(RANK_T) k_sort_rank(const Batch B, const Grid G) {
+__global__ void __launch_bounds__(RANK_T) k_sort_rank(const __grid_constant__ Batch B, const __grid_constant__ Grid G) {
   __shared__ __align__(16) uint64_t ja[RANK_T];
   __shared__ uint64_t jb[RANK_T];
   const int e = grid_entry(G, blockIdx.x);
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(RANK_T) k_sort_rank(const Batch B, const Grid 
   }
 }
 
-__global__ void __launch_bounds__(PLACE_T) k_sort_place(const Batch B, const Grid G) {
+__global__ void __launch_bounds__(PLACE_T) k_sort_place(const __grid_constant__ Batch B, const __grid_constant__ Grid G) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* ka_s = reinterpret_cast<uint64_t*>(smem);
   uint64_t* kb_s = ka_s + SMALL_KEYS;

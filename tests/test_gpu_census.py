@@ -195,6 +195,37 @@ def test_ingest_sort_sizes(hm, monkeypatch, count, bitmap):
         assert (g.edges(s).cpu().numpy() == og.edges(s)).all()
 
 
+@pytest.mark.parametrize("bitmap", ["0", "1"])
+@pytest.mark.parametrize("m", [1, 31, 1023, 1024, 3001])
+def test_normalise_long_member_lists(hm, monkeypatch, bitmap, m):
+    # hyperedges of 2-6 members, every 13th one a long list (up to 400
+    # entries, most of them repeats of at most five distinct members, or a
+    # set of 60 distinct members): a warp's member range then exceeds what it
+    # stages in shared memory and the rest is read directly; m not a
+    # multiple of the per-block tile (ragged last block)
+    monkeypatch.setenv("HM_PAIR_BITMAP", bitmap)
+    n = 500
+    st = synth.Stream(29, m)
+    u = st.u64(8 * m).reshape(m, 8)
+    edges = []
+    for j in range(m):
+        r = u[j]
+        if j % 13 == 5:
+            base = [int(x % n) for x in r[:2 + int(r[7] % 4)]]
+            edges.append(base * (400 // len(base)))
+        elif j % 13 == 9:
+            edges.append([(int(r[0]) + 7 * i) % n for i in range(60)])
+        else:
+            edges.append([int(x % n) for x in r[:2 + int(r[6] % 5)]])
+    h = synth.from_edges(edges, n)
+    g = hm.from_host(h, 4)
+    og = oracle.Graph.from_hypergraph(h, 4)
+    for s in (2, 3, 4):
+        assert g.count(s) == og.count(s)
+        assert (g.edges(s).cpu().numpy() == og.edges(s)).all()
+    assert g.counts[5] == og.count(5)
+
+
 def test_relabel_and_duplicate_invariance(hm, pair_path):
     h = synth.workload("uniform-200")
     base = {k: _gpu_hist(hm, h, k)[0] for k in (3, 4)}

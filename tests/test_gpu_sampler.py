@@ -118,3 +118,35 @@ def test_launch_counter_counts_library_kernels(hm):
     # ingest (normalise, sort, CSR, spaces) and census launches: at least 10
     # on any path; the fused small-graph chains keep it near 16
     assert hm.launch_count() - before >= 10
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("weighted", [False, True])
+def test_pair_stratum_dense(hm, seed, weighted):
+    # many 3- and 4-hyperedges on few nodes: the pair stratum's counts by
+    # neighbour type meet every correction (3-hyperedges through both ends of
+    # the drawn pair, through one end, 4-hyperedges, sets holding several)
+    h = synth.random_tiny(16, 220, max_size=4, seed=300 + seed, dup_frac=0.1)
+    og = oracle.Graph.from_hypergraph(h, 4)
+    rows = sum(og.count(s) for s in (2, 3, 4))
+    q = (1 + synth.Stream(5, seed).below(rows, 1000)).astype(np.uint32) if weighted else None
+    _compare(hm, h, 4, {2: 3000, 3: 30, 4: 30}, seed=seed, q=q)
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_pair_stratum_types_equal_enumeration(hm, monkeypatch, weighted):
+    # a communication-shaped graph with hubs (5,000 nodes, 10,000 hyperedges):
+    # the counts by neighbour type equal the per-candidate enumeration of the
+    # pairs' sets (HM_SAMPLE_PAIR_ENUM=1) bit for bit
+    h = synth.workload("comm-5m", seed=11, scale=0.001)
+    g = hm.from_host(h, 4)
+    rows = sum(g.count(s) for s in (2, 3, 4))
+    q = None
+    if weighted:
+        q = torch.from_numpy((1 + synth.Stream(6, 1).below(rows, 1 << 20)).astype(np.int32)).cuda()
+    S = {2: 40_000, 3: 10, 4: 10}
+    est_t, raw_t = hm.count_sampled(g, 4, samples=S, seed=21, q=q)
+    monkeypatch.setenv("HM_SAMPLE_PAIR_ENUM", "1")
+    est_e, raw_e = hm.count_sampled(g, 4, samples=S, seed=21, q=q)
+    assert torch.equal(raw_t, raw_e)
+    assert est_t.cpu().numpy().tobytes() == est_e.cpu().numpy().tobytes()
