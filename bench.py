@@ -580,7 +580,7 @@ def mre(est, T, mask):
 
 
 def measure_sampler(hm, stream, scale=0.004,
-                    budgets=(12_000, 60_000, 300_000, 1_500_000), seeds=5):
+                    budgets=(12_000, 60_000, 300_000, 1_500_000, 7_500_000), seeds=5):
     """Alg. 4 with uniform and learned proposals: relative error vs GPU time.
 
     Communication-shaped graph (comm-5m generator at `scale`); the proposal is
@@ -931,6 +931,8 @@ def main():
     ap.add_argument("--large", default="comm-5m",
                     help="workload of --only large (comm-5m or coauth-1m)")
     ap.add_argument("--scale", type=float, default=1.0, help="scale of --only large")
+    ap.add_argument("--budgets", default=None,
+                    help="comma-separated draw budgets of --only sampler / sampler-full")
     ap.add_argument("--null-bases", type=int, default=8,
                     help="number of null-model bases (log-spaced 50k-500k hyperedges)")
     args = ap.parse_args()
@@ -952,12 +954,13 @@ def main():
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     if args.only:
+        budgets = tuple(int(x) for x in args.budgets.split(",")) if args.budgets else None
         if args.only == "sampler":
-            res = measure_sampler(hm, stream)
+            res = measure_sampler(hm, stream, **({"budgets": budgets} if budgets else {}))
         elif args.only == "null":
             res = measure_null(hm, stream, hyperedges=NULL_BASES[:args.null_bases])
         elif args.only == "sampler-full":
-            res = measure_sampler_full(hm, stream)
+            res = measure_sampler_full(hm, stream, **({"budgets": budgets} if budgets else {}))
         elif args.only == "order5":
             res = measure_order5(hm, stream)
         elif args.only == "baseline":
