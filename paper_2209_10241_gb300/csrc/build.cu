@@ -325,34 +325,60 @@ __global__ void k_place3(const int4* __restrict__ e3, int64_t m, const int64_t* 
   }
 }
 
-__global__ void k_directed_pairs(const uint64_t* __restrict__ e2, int64_t m, int b,
-                                 uint64_t* __restrict__ keys) {
+// Pair CSR of a graph without bitmaps, from E_2 in ascending (u, v) order. Row
+// x is [its pairs {u, x}, u < x, ascending] ++ [its pairs {x, v}, x < v,
+// ascending]; the second part is a contiguous run of E_2. Step 1, per pair p =
+// (u, v): both degrees (into the zeroed off2, scanned in place afterwards), the
+// count of v's first-part entries (into the zeroed rev), where u's run of
+// E_2 starts, and the key (v << 32) | p for the stable sort of the first
+// parts by v (p < 2^31).
+__global__ void k_pair_counts(const uint64_t* __restrict__ e2, int64_t m,
+                              unsigned long long* __restrict__ deg,
+                              unsigned long long* __restrict__ rev, int64_t* __restrict__ first,
+                              uint64_t* __restrict__ keys) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t uv = e2[p], u = uv >> 32, v = uv & 0xFFFFFFFFull;
+    atomicAdd(&deg[u], 1ull);
+    atomicAdd(&deg[v], 1ull);
+    atomicAdd(&rev[v], 1ull);
+    if (p == 0 || (e2[p - 1] >> 32) != u) first[u] = p;
+    keys[p] = (v << 32) | (uint64_t)p;
+  }
+}
+
+// Step 2: v at u's position rev(u) + (p - first[u]); that position is where
+// v lies in N2(u).
+__global__ void k_place_second(const uint64_t* __restrict__ e2, int64_t m,
+                               const int64_t* __restrict__ off2, const uint64_t* __restrict__ rs,
+                               const int64_t* __restrict__ first, int32_t* __restrict__ adj2,
+                               int2* __restrict__ pos) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t uv = e2[p];
+    const int64_t u = (int64_t)(uv >> 32);
+    const int32_t at = (int32_t)(rs[u + 1] - rs[u] + (uint64_t)(p - first[u]));
+    adj2[off2[u] + at] = (int32_t)(uv & 0xFFFFFFFFull);
+    pos[p].x = at;
+  }
+}
+
+// Step 3: the keys sorted stably by v; v's run starts at rs[v] (exclusive
+// prefix of rev) and holds its pairs in E_2 order, i.e. its first-part
+// entries u ascending, so the entry at sorted index i lies at i - rs[v] in
+// N2(v).
+__global__ void k_place_first(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ e2,
+                              int64_t m, const int64_t* __restrict__ off2,
+                              const uint64_t* __restrict__ rs, int32_t* __restrict__ adj2,
+                              int2* __restrict__ pos) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t u = e2[i] >> 32, v = e2[i] & 0xFFFFFFFFull;
-    keys[2 * i] = (u << b) | v;
-    keys[2 * i + 1] = (v << b) | u;
+    const uint64_t k = keys[i];
+    const int64_t v = (int64_t)(k >> 32), p = (int64_t)(k & 0xFFFFFFFFull);
+    const int32_t at = (int32_t)((uint64_t)i - rs[v]);
+    adj2[off2[v] + at] = (int32_t)(e2[p] >> 32);
+    pos[p].y = at;
   }
-}
-
-__global__ void k_low_bits(const uint64_t* __restrict__ keys, int64_t m, int b,
-                           int32_t* __restrict__ out) {
-  const uint64_t mask = (1ull << b) - 1;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-       i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = (int32_t)(keys[i] & mask);
-}
-
-__device__ int32_t find_pos(const int32_t* __restrict__ a, int64_t lo, int64_t hi, int32_t x) {
-  int64_t l = lo, h = hi;
-  while (l < h) {
-    int64_t mid = (l + h) >> 1;
-    if (a[mid] < x)
-      l = mid + 1;
-    else
-      h = mid;
-  }
-  return (int32_t)(l - lo);
 }
 
 // Pair positions read off the bitmap rows: the position of v in u's row is
@@ -378,18 +404,6 @@ __global__ void k_pairpos_bits(const uint32_t* __restrict__ bits, int32_t bw, in
     pos[p] = make_int2(r[0], r[1]);
   }
 }
-
-__global__ void k_pairpos(const uint64_t* __restrict__ e2, int64_t m, const int64_t* __restrict__ off2,
-                          const int32_t* __restrict__ adj2, int2* __restrict__ pos) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    int32_t u = (int32_t)(e2[p] >> 32), v = (int32_t)(e2[p] & 0xFFFFFFFFull);
-    pos[p] = make_int2(find_pos(adj2, off2[u], off2[u + 1], v),
-                       find_pos(adj2, off2[v], off2[v + 1], u));
-  }
-}
-
-
 
 // Pair degrees from the bitmap rows, one warp per node, and the largest
 // (one atomic per warp into the zeroed *mx).
@@ -499,13 +513,23 @@ __global__ void k_upper_emit(const uint32_t* __restrict__ bits, int32_t n, int32
 
 // Largest pair degree: a thread's maximum over its nodes, then one atomic per
 // warp.
-__global__ void k_max_degree(const int64_t* __restrict__ off, int32_t n, int* out) {
+// The largest pair degree: one atomic per block (same-address atomics
+// serialise in L2).
+__global__ void __launch_bounds__(256) k_max_degree(const int64_t* __restrict__ off, int32_t n,
+                                                    int* out) {
+  __shared__ int wmax[8];
   int mx = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x)
     mx = max(mx, (int)(off[v + 1] - off[v]));
   mx = __reduce_max_sync(0xffffffffu, mx);
-  if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(out, mx);
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0;
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (threadIdx.x == 0 && mx > 0) atomicMax(out, mx);
+  }
 }
 
 __global__ void k_edges_out(const uint64_t* __restrict__ e2, const int4* __restrict__ e34,
@@ -773,9 +797,9 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     o += al(((size_t)n + 1) * 4);
     const size_t o_sig = o;
     if (!bitmaps) o += al((size_t)3 * n * 8);
-    const size_t zero_end = o;
-    const size_t o_off2 = o;
+    const size_t o_off2 = o;  // pair degrees are counted into it (no bitmaps)
     o += al(((size_t)n + 1) * 8);
+    const size_t zero_end = o;
     const size_t o_adj2 = o;
     o += al((size_t)2 * m2 * 4);
     const size_t o_pp = o;
@@ -799,10 +823,17 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     HM_CUDA(cudaMemsetAsync(arena, 0xFF, ff_end, s));
     HM_CUDA(cudaMemsetAsync(arena + ff_end, 0, zero_end - ff_end, s));
   }
-  // temporaries of the chains: directed pair keys (without bitmaps); the
-  // maximum pair degree goes to the zeroed counter word beside the error word
-  DBuf<uint64_t> pkeys_buf(bitmaps ? 0 : 2 * m2, s);
-  uint64_t* pkeys = pkeys_buf.p;
+  // temporaries of the chains (without bitmaps): per node the count of its
+  // pairs to lower ids, scanned (zeroed, n + 1) and where its run of E_2
+  // starts (n); per pair a sort key. The maximum pair degree goes to the
+  // zeroed counter word beside the error word.
+  HM_CHECK(m2 < (1ll << 31), HM_EUNSUPPORTED, "2^31 or more distinct pairs");
+  const size_t csr_words = bitmaps ? 0 : ((size_t)n + 1) + (size_t)n + (size_t)m2;
+  DBuf<uint64_t> csr_buf(csr_words, s);
+  uint64_t* rs = csr_buf.p;
+  int64_t* first = bitmaps ? nullptr : reinterpret_cast<int64_t*>(csr_buf.p + n + 1);
+  uint64_t* pkeys = bitmaps ? nullptr : csr_buf.p + 2 * (size_t)n + 1;
+  if (!bitmaps) HM_CUDA(cudaMemsetAsync(rs, 0, ((size_t)n + 1) * 8, s));
   int* mx_p = reinterpret_cast<int*>(counters.p + 15);
 
   {
@@ -831,24 +862,28 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
           g->bits2, n, g->bwords, gv.block, gv.block_inv, g->off2, g->adj2);
       HM_KCHECK();
     } else if (m2) {
-      k_directed_pairs<<<grid1d(m2), T256, 0, f[0]>>>(g->e2, m2, b, pkeys);
+      // degrees and counts, offsets (both scans in one launch), the rows'
+      // second parts straight from E_2, the first parts after a stable sort
+      // of one key per pair by its larger node; pair positions fall out of
+      // the placement
+      k_pair_counts<<<grid1d(m2), T256, 0, f[0]>>>(
+          g->e2, m2, reinterpret_cast<unsigned long long*>(g->off2),
+          reinterpret_cast<unsigned long long*>(rs), first, pkeys);
       HM_KCHECK();
-      // Stable by the first node only: for node x the keys (x, u) of pairs
-      // {u < x} precede the keys (x, v) of pairs {x < v} in E_2 order, and
-      // each group is ascending, so every row comes out sorted.
-      radix_sort_u64(pkeys, nullptr, 2 * m2, b, f[0], b);
-      k_low_bits<<<grid1d(2 * m2), T256, 0, f[0]>>>(pkeys, 2 * m2, b, g->adj2);
+      ScanJob sj[2] = {{reinterpret_cast<uint64_t*>(g->off2), n, nullptr}, {rs, n, nullptr}};
+      scan_batch_inplace(sj, 2, f[0]);
+      k_place_second<<<grid1d(m2), T256, 0, f[0]>>>(g->e2, m2, g->off2, rs, first, g->adj2,
+                                                    g->pairpos);
+      HM_KCHECK();
+      radix_sort_u64(pkeys, nullptr, m2, b, f[0], 32);
+      k_place_first<<<grid1d(m2), T256, 0, f[0]>>>(pkeys, g->e2, m2, g->off2, rs, g->adj2,
+                                                   g->pairpos);
       HM_KCHECK();
     }
-    if (!bitmaps) csr_offsets(pkeys, 2 * m2, b, n, g->off2, f[0]);
-    if (m2) {
-      if (bitmaps) {  // positions from the rows, beside the hash inserts
-        const hm::DevGraph gv = g->view();
-        k_pairpos_bits<<<grid1d(m2), T256, 0, s>>>(g->bits2, g->bwords, gv.block, gv.block_inv,
-                                                    g->e2, m2, g->pairpos);
-      } else {
-        k_pairpos<<<grid1d(m2), T256, 0, f[0]>>>(g->e2, m2, g->off2, g->adj2, g->pairpos);
-      }
+    if (m2 && bitmaps) {  // positions from the rows, beside the hash inserts
+      const hm::DevGraph gv = g->view();
+      k_pairpos_bits<<<grid1d(m2), T256, 0, s>>>(g->bits2, g->bwords, gv.block, gv.block_inv,
+                                                  g->e2, m2, g->pairpos);
       HM_KCHECK();
     }
     if (!bitmaps) {  // with bitmaps k_bits_degree took the maximum

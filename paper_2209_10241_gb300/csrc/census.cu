@@ -895,10 +895,12 @@ __global__ void k_txs_split(const DevGraph g, const unsigned long long* __restri
                             const int64_t* __restrict__ re, uint8_t* __restrict__ share,
                             int32_t* __restrict__ small, int32_t* __restrict__ large,
                             unsigned int* __restrict__ counts) {
-  const int lane = threadIdx.x & 31;
-  const int64_t n = (g.m3 + 31) / 32 * 32;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x) {
+  __shared__ unsigned int wcnt[2][32], bbase[2];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // whole blocks per round (the appends take one atomic per list per block)
+  for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x; t0 < g.m3;
+       t0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = t0 + threadIdx.x;
     bool valid = t < g.m3, is_small = false;
     if (valid) {
       const int4 e = g.e3[t];
@@ -932,16 +934,27 @@ __global__ void k_txs_split(const DevGraph g, const unsigned long long* __restri
       if (quad) mx = max(mx, max(d2[0], max(d2[1], d2[2])));
       is_small = mx <= TXS_SMALL;
     }
-    // warp-aggregated appends
+    // block-aggregated appends: warp counts, one atomic per list, warp offsets
     const unsigned bs = __ballot_sync(0xffffffffu, valid && is_small);
     const unsigned bl = __ballot_sync(0xffffffffu, valid && !is_small);
-    unsigned int base_s = 0, base_l = 0;
     if (lane == 0) {
-      if (bs) base_s = atomicAdd(&counts[0], (unsigned)__popc(bs));
-      if (bl) base_l = atomicAdd(&counts[1], (unsigned)__popc(bl));
+      wcnt[0][wid] = (unsigned)__popc(bs);
+      wcnt[1][wid] = (unsigned)__popc(bl);
     }
-    base_s = __shfl_sync(0xffffffffu, base_s, 0);
-    base_l = __shfl_sync(0xffffffffu, base_l, 0);
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      const int k = threadIdx.x;
+      unsigned run = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        const unsigned c = wcnt[k][w];
+        wcnt[k][w] = run;
+        run += c;
+      }
+      bbase[k] = run ? atomicAdd(&counts[k], run) : 0u;
+    }
+    __syncthreads();
+    const unsigned base_s = bbase[0] + wcnt[0][wid], base_l = bbase[1] + wcnt[1][wid];
+    __syncthreads();  // wcnt and bbase are rewritten next round
     const unsigned below = (1u << lane) - 1u;
     if (valid && is_small) small[base_s + __popc(bs & below)] = (int32_t)t;
     if (valid && !is_small) large[base_l + __popc(bl & below)] = (int32_t)t;

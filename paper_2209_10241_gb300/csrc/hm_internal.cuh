@@ -196,10 +196,6 @@ void radix_sort_u64(uint64_t* keys, uint64_t* vals, int64_t n, int bits, cudaStr
 // lo_bits of lo and the low hi_bits of hi.
 void radix_sort_u128(uint64_t* hi, uint64_t* lo, int64_t n, int hi_bits, int lo_bits,
                      cudaStream_t s);
-// off[v] = first index i with (key[i] >> shift) >= v, for v in [0, num_nodes];
-// keys sorted ascending.
-void csr_offsets(const uint64_t* keys, int64_t n, int shift, int32_t num_nodes, int64_t* off,
-                 cudaStream_t s);
 
 // ------------------------------------------------------------------ hashing
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {

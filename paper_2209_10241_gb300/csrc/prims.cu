@@ -135,16 +135,6 @@ void scan_exclusive_in(const T* in, T* out, int64_t n, cudaStream_t s, T* scratc
   HM_KCHECK();
 }
 
-__global__ void k_csr_offsets(const uint64_t* keys, int64_t n, int shift, int32_t nn,
-                              int64_t* off) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t cur = i < n ? (int64_t)(keys[i] >> shift) : (int64_t)nn;
-    int64_t prev = i > 0 ? (int64_t)(keys[i - 1] >> shift) : -1;
-    for (int64_t v = prev + 1; v <= cur && v <= nn; ++v) off[v] = i;
-  }
-}
-
 unsigned grid_for(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -246,12 +236,6 @@ size_t scan_scratch_elems(int64_t n) {
     tiles = (tiles + SCAN_TILE - 1) / SCAN_TILE;
   }
   return need;
-}
-
-void csr_offsets(const uint64_t* keys, int64_t n, int shift, int32_t num_nodes, int64_t* off,
-                 cudaStream_t s) {
-  k_csr_offsets<<<grid_for(n + 1, 256), 256, 0, s>>>(keys, n, shift, num_nodes, off);
-  HM_KCHECK();
 }
 
 }  // namespace hm

@@ -518,11 +518,25 @@ __device__ __forceinline__ void bins_vote(unsigned long long* blo, unsigned long
     bins_add(blo, bhi, cls, kWeighted ? wt[draw] : 1ull, (uint64_t)__popc(peers), neg);
 }
 
+// Membership tests that read the node signatures first (graphs without
+// bitmaps): a clear signature bit proves the pair / 3-hyperedge absent
+// without a probe.
+__device__ __forceinline__ bool pair_s(const DevGraph& g, int32_t a, int32_t x) {
+  return (!g.sig || (g.sig[a] & sig_bit(x))) && has_pair(g, a, x);
+}
+__device__ __forceinline__ bool triple_s(const DevGraph& g, int32_t a, int32_t b, int32_t x) {
+  if (g.sig) {
+    const uint64_t s = g.sig[(int64_t)g.n + a];
+    if (!(s & sig_bit(b)) || !(s & sig_bit(x))) return false;
+  }
+  return has_triple(g, a, b, x);
+}
+
 // Pair mask of {a, b, x, y} (ab present) and whether its pairs connect it.
 __device__ __forceinline__ bool pair_pattern(const DevGraph& g, int32_t a, int32_t b, int32_t x,
                                              int32_t y, uint32_t& mask) {
-  const bool ax = has_pair(g, a, x), ay = has_pair(g, a, y), bx = has_pair(g, b, x),
-             by = has_pair(g, b, y), xy = has_pair(g, x, y);
+  const bool ax = pair_s(g, a, x), ay = pair_s(g, a, y), bx = pair_s(g, b, x),
+             by = pair_s(g, b, y), xy = pair_s(g, x, y);
   mask = 1u | (ax ? 2u : 0u) | (ay ? 4u : 0u) | (bx ? 8u : 0u) | (by ? 16u : 0u) | (xy ? 32u : 0u);
   const bool xa = ax || bx, ya = ay || by;  // x / y adjacent to {a, b}
   return (xa || (xy && ya)) && (ya || (xy && xa));
@@ -556,11 +570,11 @@ __global__ void k_pair_elems(const DevGraph g, const int64_t* __restrict__ sidx,
       uint32_t ty;
       bool valid = true;
       if (r < L.la) {
-        ty = has_pair(g, L.b, c) ? TY_T : TY_A;
+        ty = pair_s(g, L.b, c) ? TY_T : TY_A;
         tr += ty == TY_T ? 1u : 0u;
       } else {
         ty = TY_B;
-        valid = !has_pair(g, L.a, c);  // listed from a already (in T)
+        valid = !pair_s(g, L.a, c);  // listed from a already (in T)
       }
       elems[j] = make_int2((int32_t)((uint32_t)i | (ty << 30)), valid ? c : -1);
       ework[j] = valid ? (uint64_t)deg2(g, c) : 0ull;
@@ -662,7 +676,7 @@ __global__ void __launch_bounds__(SAMPLE_THREADS)
         const int32_t x = g.adj2[co + r];
         ++r;
         if (x != a && x != b) {
-          const bool inA = has_pair(g, a, x), inB = has_pair(g, b, x);
+          const bool inA = pair_s(g, a, x), inB = pair_s(g, b, x);
           if (!inA && !inB) {
             pp = ty == TY_T ? PP_PAW : PP_PATH;
           } else {
@@ -755,14 +769,14 @@ __global__ void __launch_bounds__(SAMPLE_THREADS)
             const unsigned long long slot = atomicAdd(g1n, 1ull);
             if (slot < cap1) g1[slot] = make_int2((int32_t)i, x == b ? y : x);
           } else {
-            emit = !has_triple(g, a, b, x) && !has_triple(g, a, b, y);
+            emit = !triple_s(g, a, b, x) && !triple_s(g, a, b, y);
           }
         } else if (r < t3a + t3b) {
           const int4 e = g.e3[g.inc3[g.off3[b] + (int64_t)(r - t3a)]];
           x = e.x == b ? e.y : e.x;
           y = e.z == b ? e.y : e.z;
-          emit = x != a && y != a && !has_triple(g, a, b, x) && !has_triple(g, a, b, y) &&
-                 !has_triple(g, a, x, y);
+          emit = x != a && y != a && !triple_s(g, a, b, x) && !triple_s(g, a, b, y) &&
+                 !triple_s(g, a, x, y);
         } else {
           const int4 q = g.e4[inc4[off4[a] + (int64_t)(r - t3a - t3b)]];
           const int32_t m[4] = {q.x, q.y, q.z, q.w};
@@ -777,8 +791,8 @@ __global__ void __launch_bounds__(SAMPLE_THREADS)
               ++k;
             }
           }
-          emit = hb && !has_triple(g, a, b, x) && !has_triple(g, a, b, y) &&
-                 !has_triple(g, a, x, y) && !has_triple(g, b, x, y);
+          emit = hb && !triple_s(g, a, b, x) && !triple_s(g, a, b, y) &&
+                 !triple_s(g, a, x, y) && !triple_s(g, b, x, y);
         }
         ++r;
         uint32_t mask = 0;
@@ -865,10 +879,10 @@ __global__ void __launch_bounds__(SAMPLE_THREADS)
           ok = d >= 0 && d != c;
         } else {
           d = g.adj2[co + (int64_t)(r - l)];
-          ok = d != a && d != b && !has_pair(g, a, d) && !has_pair(g, b, d);
+          ok = d != a && d != b && !pair_s(g, a, d) && !pair_s(g, b, d);
         }
         ++r;
-        if (ok && !(d < c && has_triple(g, a, b, d))) {
+        if (ok && !(d < c && triple_s(g, a, b, d))) {
           uint32_t mask = 0;
           if (pair_pattern(g, a, b, c, d, mask)) cls = lut[mask];
         }
