@@ -1002,6 +1002,14 @@ def main():
 
     peaks, src = _peaks()
     roofline = hbm_roofline(r["dominant"], r["totals"], r["dom_avg_s"], peaks["hbm_gbs"], src)
+    if r["dominant"] in ROOFLINE_NCU and r["dom_avg_s"]:
+        # L2 sectors of the ncu capture over the live launch time, against the
+        # L2 read bandwidth measured by the library's own probe
+        l2_peak = hm.l2_read_bandwidth(64 << 20, 20, stream)
+        l2 = ROOFLINE_NCU[r["dominant"]]["lts_t_sectors"] * 32 / r["dom_avg_s"] / 1e9
+        roofline["l2"] = {"achieved": l2, "peak": l2_peak, "unit": "GB/s", "frac": l2 / l2_peak,
+                          "peak_source": "hm_l2_read_bandwidth: 64 MiB buffer read 20 times "
+                                         "with 16-byte L2-only loads (measured in this run)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,

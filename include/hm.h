@@ -258,6 +258,18 @@ hm_status hm_serialize_launches(int on);
 
 /* Number of kernels the library has launched in this process (instrumentation). */
 uint64_t hm_launch_count(void);
+
+/*
+ * L2 read bandwidth of this GPU (no counterpart in the paper; instrumentation
+ * for the roofline of kernels whose working set stays in L2). Allocates a
+ * device buffer of `bytes` (a multiple of 16, at most 64 MiB so that it stays
+ * resident in L2), fills it, reads it once untimed and then `reps` times with
+ * 16-byte loads that bypass L1 (every SM's resident blocks, each block its
+ * slice), and writes the bytes read per second / 1e9 to *gbs (host). The
+ * time comes from CUDA events on `stream`. Synchronous; HM_EINVAL for a size
+ * outside (0, 64 MiB], not a multiple of 16, or reps < 1.
+ */
+hm_status hm_l2_read_bandwidth(size_t bytes, int reps, double* gbs, void* stream);
 hm_status hm_trace_read(int max_entries, char* names, int name_len, float* ms, int* count);
 
 /* ---------------------------------------------------------------- learned proposal

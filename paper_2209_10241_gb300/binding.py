@@ -81,6 +81,7 @@ _SIGS = {
     "hm_trace_enable": (ctypes.c_int, [ctypes.c_int]),
     "hm_trace_only": (ctypes.c_int, [ctypes.c_char_p]),
     "hm_launch_count": (ctypes.c_uint64, []),
+    "hm_l2_read_bandwidth": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, _vp, _vp]),
     "hm_selftest_wait": (ctypes.c_int, [_vp]),
     "hm_debug_canonical_check": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "hm_serialize_launches": (ctypes.c_int, [ctypes.c_int]),
@@ -355,6 +356,13 @@ def serialize_launches(on: bool = True):
 def launch_count() -> int:
     """Kernels launched by libhm.so so far in this process."""
     return int(load().hm_launch_count())
+
+
+def l2_read_bandwidth(nbytes: int = 64 << 20, reps: int = 20, stream=None) -> float:
+    """hm_l2_read_bandwidth: GB/s of reads from an L2-resident buffer."""
+    out = ctypes.c_double(0.0)
+    _check(load().hm_l2_read_bandwidth(nbytes, reps, ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def _rows(g: Graph, order: int) -> int:

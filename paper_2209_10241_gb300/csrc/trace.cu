@@ -60,11 +60,69 @@ void trace_end(const char* name, cudaStream_t s, cudaEvent_t a) {
   g_entries.push_back(Entry{name, a, b});
 }
 
+namespace {
+
+// Each thread reads its 16-byte words of the buffer `reps` times with loads
+// cached in L2 only; the XOR of the words keeps the loads alive.
+__global__ void __launch_bounds__(256)
+    k_l2_read(const uint4* __restrict__ buf, size_t n16, int reps,
+              unsigned long long* __restrict__ sink) {
+  uint32_t acc = 0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (int r = 0; r < reps; ++r)
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {
+      const uint4 v = __ldcg(buf + i);
+      acc ^= v.x ^ v.y ^ v.z ^ v.w;
+    }
+  if (acc == 0x9E3779B9u) atomicAdd(sink, 1ull);
+}
+
+}  // namespace
+
 }  // namespace hm
 
 extern "C" {
 
 uint64_t hm_launch_count(void) { return hm::launch_count_add(0); }
+
+hm_status hm_l2_read_bandwidth(size_t bytes, int reps, double* gbs, void* stream) {
+  return hm::guarded([&] {
+    HM_CHECK(gbs != nullptr, HM_EINVAL, "NULL result");
+    HM_CHECK(bytes > 0 && bytes <= ((size_t)64 << 20) && bytes % 16 == 0, HM_EINVAL,
+             "bytes must be a positive multiple of 16, at most 64 MiB");
+    HM_CHECK(reps >= 1, HM_EINVAL, "reps must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0, per = 0;
+    HM_CUDA(cudaGetDevice(&dev));
+    HM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    HM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)hm::k_l2_read, 256, 0));
+    const unsigned blocks = (unsigned)(sms * (per > 0 ? per : 1));
+    const size_t n16 = bytes / 16;
+    hm::DBuf<unsigned char> buf(bytes + 256, s);
+    unsigned long long* sink = reinterpret_cast<unsigned long long*>(buf.p + bytes);
+    HM_CUDA(cudaMemsetAsync(buf.p, 0x5A, bytes + 256, s));
+    const uint4* b = reinterpret_cast<const uint4*>(buf.p);
+    hm::k_l2_read<<<blocks, 256, 0, s>>>(b, n16, 1, sink);
+    HM_KCHECK();
+    struct Events {  // destroyed on every exit
+      cudaEvent_t a = nullptr, b = nullptr;
+      ~Events() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+      }
+    } ev;
+    HM_CUDA(cudaEventCreate(&ev.a));
+    HM_CUDA(cudaEventCreate(&ev.b));
+    HM_CUDA(cudaEventRecord(ev.a, s));
+    hm::k_l2_read<<<blocks, 256, 0, s>>>(b, n16, reps, sink);
+    HM_KCHECK();
+    HM_CUDA(cudaEventRecord(ev.b, s));
+    HM_CUDA(cudaEventSynchronize(ev.b));
+    float ms = 0.f;
+    HM_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b));
+    *gbs = (double)bytes * reps / (ms * 1e-3) / 1e9;
+  });
+}
 
 hm_status hm_trace_enable(int on) {
   return hm::guarded([&] {

@@ -283,6 +283,17 @@ def test_abi_errors(hm):
     assert hm.num_classes(3) == 6 and hm.num_classes(4) == 171 and hm.num_classes(5) == -1
 
 
+def test_l2_read_bandwidth_probe(hm):
+    # instrumentation for the L2 roofline: a finite positive rate, and
+    # sizes outside (0, 64 MiB] or not a multiple of 16 rejected
+    bw = hm.l2_read_bandwidth(16 << 20, 4)
+    assert np.isfinite(bw) and bw > 0
+    for bad in (0, 100, (64 << 20) + 16):
+        with pytest.raises(hm.HMError) as e:
+            hm.l2_read_bandwidth(bad, 1)
+        assert e.value.status == 1
+
+
 @pytest.mark.parametrize("k", [3, 4])
 def test_class_table_matches_oracle(hm, k):
     canon, mc, cm = oracle.class_info(k)
