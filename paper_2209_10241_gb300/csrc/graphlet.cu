@@ -927,7 +927,9 @@ __global__ void __launch_bounds__(C4E_THREADS)
 // ws[x]) slots at [2 ws[x], 2 ws[x+1]) (slot = (z << 32) | count, empty = all
 // ones; a match adds 1 to the count word, which never carries into z). A
 // table holds at most ws[x+1] - ws[x] keys in twice as many slots, so every
-// probe ends. k_c4_sum then adds C(count, 2) over all tables.
+// probe ends. The 4-cycle sum Σ_z C(count_z, 2) is taken on the way: a match
+// adds the count it found (the pairs its path closes with the earlier paths
+// to z), so no pass over the tables follows.
 constexpr uint32_t C4T_PIECE = 4096;
 
 // The node x with ws[x] <= pos < ws[x + 1] (ws is nondecreasing, ws[0] = 0 <=
@@ -950,7 +952,9 @@ __device__ __forceinline__ int64_t c4_owner(const uint64_t* __restrict__ ws, int
 
 __global__ void __launch_bounds__(C4E_THREADS)
     k_c4_table(const DevGraph g, const uint64_t* __restrict__ ws, uint64_t total,
-               unsigned long long* __restrict__ table) {
+               unsigned long long* __restrict__ table, int32_t nodes_per_graph,
+               unsigned long long* __restrict__ agg) {
+  C4Sum acc;  // each repeat of an endpoint z adds its count so far: Σ_z C(count_z, 2)
   __shared__ int64_t s_off[C4E_CAP];
   __shared__ uint32_t s_pre[C4E_CAP];
   __shared__ uint32_t s_wsum[C4E_THREADS / 32];
@@ -1046,7 +1050,8 @@ __global__ void __launch_bounds__(C4E_THREADS)
             const unsigned long long prev = atomicCAS(p, ~0ull, key | 1ull);
             if (prev == ~0ull) break;
             if ((prev >> 32) == (uint32_t)z) {
-              atomicAdd(p, 1ull);
+              const unsigned long long old = atomicAdd(p, 1ull);
+              acc.add(agg, (int64_t)z / nodes_per_graph, old & 0xFFFFFFFFull);
               break;
             }
             if (++slot == tcap) slot = 0;
@@ -1058,22 +1063,9 @@ __global__ void __launch_bounds__(C4E_THREADS)
       pos = wx + e;
     }
   }
+  c4_flush_block<C4E_THREADS / 32>(acc, agg);
 }
 
-// C(count, 2) over every table slot; a slot's graph is that of its z.
-__global__ void __launch_bounds__(256)
-    k_c4_sum(const unsigned long long* __restrict__ table, uint64_t nslots,
-             int32_t nodes_per_graph, unsigned long long* __restrict__ agg) {
-  C4Sum acc;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nslots;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    const unsigned long long v = table[i];
-    if (v == ~0ull) continue;
-    const uint64_t c = v & 0xFFFFFFFFull;
-    if (c > 1) acc.add(agg, (int64_t)(v >> 32) / nodes_per_graph, c * (c - 1) / 2);
-  }
-  c4_flush_block<8>(acc, agg);
-}
 
 // Sort tier, counting: each run of c equal keys (c paths from x to one z)
 // closes C(c, 2) 4-cycles at x.
@@ -1295,9 +1287,7 @@ void graphlet_pairs(const hm_graph* g, GraphletScratch& G, cudaStream_t s) {
       HM_CUDA(cudaMemsetAsync(tab, 0xFF, 2 * nk * sizeof(uint64_t), s));
       const uint64_t pieces = (nk + C4T_PIECE - 1) / C4T_PIECE;
       k_c4_table<<<(unsigned)std::min<uint64_t>(pieces, 1u << 30), C4E_THREADS, 0, s>>>(
-          g->view(), g->C4.ws, nk, tab);
-      HM_KCHECK();
-      k_c4_sum<<<std::min<unsigned>(grid_n(2 * nk), 152 * 8), 256, 0, s>>>(tab, 2 * nk, G.per, G.agg);
+          g->view(), g->C4.ws, nk, tab, G.per, G.agg);
       HM_KCHECK();
       st.end();
     } else if (nk) {
