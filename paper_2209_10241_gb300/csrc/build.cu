@@ -56,11 +56,12 @@ __device__ __forceinline__ void set_bit(const BitsOut& o, uint32_t* bm, int32_t 
 
 // Normalisation: hyperedge j's members (sorted, repeats collapsed) as long as
 // it has at most kmax distinct members; hyperedges with more are only counted
-// (size kmax + 1). MODE 0 only counts per size; MODE 1 emits the packed sort
-// key of each kept hyperedge of size >= 2 (members concatenated with b bits
-// each, most significant first); MODE 2 sets the bitmap bits of each kept
-// hyperedge instead (pairs, co-occurrence, exact triple rows) and emits sort
-// keys only for 3- and 4-hyperedges.
+// (size kmax + 1). Every mode counts the hyperedges per size into cnt; MODE 1
+// emits the packed sort key of each kept hyperedge of size >= 2 (members
+// concatenated with b bits each, most significant first) into arrays sized
+// for the worst case; MODE 2 sets the bitmap bits of each kept hyperedge
+// instead (pairs, co-occurrence, exact triple rows) and emits sort keys only
+// for 3- and 4-hyperedges.
 //
 // A block takes NORM_ITEMS * 256 consecutive hyperedges, each warp 32 *
 // NORM_ITEMS of them, whose members are one contiguous range of the input:
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(NORM_THREADS)
       continue;
     }
     if (big) {
-      if (MODE == 0) sz[it] = kmax + 1;
+      sz[it] = kmax + 1;
       continue;
     }
     if (cntd < 2) continue;
@@ -169,7 +170,6 @@ __global__ void __launch_bounds__(NORM_THREADS)
                      1u << (c & 31));
           }
       }
-      if (cntd == 2) continue;
     }
     sz[it] = cntd;
   }
@@ -189,12 +189,11 @@ __global__ void __launch_bounds__(NORM_THREADS)
   __syncthreads();
   if (threadIdx.x < 8 && scnt[threadIdx.x])
     sbase[threadIdx.x] = atomicAdd(&cnt[threadIdx.x], (unsigned long long)scnt[threadIdx.x]);
-  if (MODE == 0) return;
   __syncthreads();
 #pragma unroll
   for (int it = 0; it < NORM_ITEMS; ++it) {
     const int cntd = sz[it];
-    if (!cntd) continue;
+    if (cntd < (MODE == 2 ? 3 : 2) || cntd > kmax) continue;  // counted only
     const unsigned long long slot = sbase[cntd] + loc[it];
     unsigned __int128 key = 0;
 #pragma unroll
@@ -607,16 +606,56 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   g->bits = b;
 
   TraceSpan span_norm("ingest_normalize", s);
-  // counters of the two normalisation passes and the error word, zeroed at once
+  // counters of the normalisation pass, the error word and two more words
+  // (maximum degree, error word of the structures), zeroed at once
   DBuf<unsigned long long> counters(17, s);
   HM_CUDA(cudaMemsetAsync(counters.p, 0, 17 * sizeof(unsigned long long), s));
   unsigned long long* cnt = counters.p;
-  unsigned long long* cnt2 = counters.p + 8;
   int* err_p = reinterpret_cast<int*>(counters.p + 16);
+  const bool bitmaps = use_bitmap(n, block ? block : n, block != 0);
+  const bool tri_rows = bitmaps && kmax >= 3 && use_tri3(n, block);
+  size_t words = 0, tw = 0;
+  auto al = [](size_t bytes) { return (bytes + 255) & ~(size_t)255; };
+  size_t bb = 0;
+  if (bitmaps) {
+    // rows padded to a multiple of four words: 16-byte aligned row loads
+    g->bwords = (((block ? block : n) + 127) / 128) * 4;
+    words = (size_t)n * g->bwords;
+    if (tri_rows) tw = (size_t)n * n * g->bwords;
+    bb = al(words * 4);
+  }
+  const size_t bits_bytes = bitmaps ? 3 * bb + al(tw * 4) : 0;
+  // One pass normalises and counts: the bitmaps (kept by the graph) and the
+  // sort keys of every hyperedge that could be kept (m per size, temporary)
+  // exist before it, so no counting pass has to size them first.
+  BitsOut bo{};
+  if (bitmaps) {
+    unsigned char* bits = keep(g, dalloc<unsigned char>(bits_bytes, s));
+    HM_CUDA(cudaMemsetAsync(bits, 0, bits_bytes, s));
+    g->bits2 = reinterpret_cast<uint32_t*>(bits);
+    g->bits3 = reinterpret_cast<uint32_t*>(bits + bb);
+    g->bits4 = reinterpret_cast<uint32_t*>(bits + 2 * bb);
+    if (tw) g->tri3 = reinterpret_cast<uint32_t*>(bits + 3 * bb);
+    const hm::DevGraph gv = g->view();
+    bo = BitsOut{g->bits2, g->bits3, g->bits4, g->tri3, g->bwords, gv.block, n, gv.block_inv};
+  }
+  const size_t u2 = bitmaps ? 0 : (size_t)m, u3 = kmax >= 3 ? (size_t)m : 0,
+               u4 = kmax >= 4 ? (size_t)m : 0;
+  DBuf<uint64_t> keybuf(u2 + 2 * u3 + 2 * u4, s);
+  uint64_t* c2 = keybuf.p;
+  uint64_t* c3hi = c2 + u2;
+  uint64_t* c3lo = c3hi + u3;
+  uint64_t* c4hi = c3lo + u3;
+  uint64_t* c4lo = c4hi + u4;
   if (m > 0) {
-    k_normalize<0><<<norm_grid(m), NORM_THREADS, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt, err_p,
-                                              nullptr, nullptr, nullptr, nullptr, nullptr,
-                                              BitsOut{});
+    if (bitmaps)
+      k_normalize<2><<<norm_grid(m), NORM_THREADS, 0, s>>>(d_members, d_offsets, m, n, kmax, b,
+                                                          cnt, err_p, c2, c3hi, c3lo, c4hi, c4lo,
+                                                          bo);
+    else
+      k_normalize<1><<<norm_grid(m), NORM_THREADS, 0, s>>>(d_members, d_offsets, m, n, kmax, b,
+                                                          cnt, err_p, c2, c3hi, c3lo, c4hi, c4lo,
+                                                          bo);
     HM_KCHECK();
   }
   span_norm.end();
@@ -633,65 +672,32 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   g->counts[kmax + 1] = (int64_t)hc[kmax + 1];
 
   TraceSpan span_sort("ingest_sort_unique", s);
-  const bool bitmaps = use_bitmap(n, block ? block : n, block != 0);
-  const bool tri_rows = bitmaps && kmax >= 3 && use_tri3(n, block);
-  size_t words = 0, tw = 0;
-  auto al = [](size_t bytes) { return (bytes + 255) & ~(size_t)255; };
-  // Two allocations for this phase, each with its zeroed part first: one the
-  // graph keeps (bitmaps, then E_2 / E_3 / E_4, sized for the hyperedges
-  // before dedup) and one of temporaries (kept counts, sort scratch, sort
-  // keys, pair-row counts).
+  // Two allocations for this phase: one the graph keeps (E_2 / E_3 / E_4,
+  // sized for the hyperedges before dedup) and one of temporaries with its
+  // zeroed part first (kept counts, sort scratch, pair-row counts).
   const size_t h2n = hc[2], h3n = kmax >= 3 ? hc[3] : 0, h4n = kmax >= 4 ? hc[4] : 0;
-  size_t bb = 0;
-  if (bitmaps) {
-    // rows padded to a multiple of four words: 16-byte aligned row loads
-    g->bwords = (((block ? block : n) + 127) / 128) * 4;
-    words = (size_t)n * g->bwords;
-    if (tri_rows) tw = (size_t)n * n * g->bwords;
-    bb = al(words * 4);
-  }
-  const size_t bits_bytes = bitmaps ? 3 * bb + al(tw * 4) : 0;
   const size_t b2 = al(h2n * 8), b3 = al(h3n * 16);
-  unsigned char* owned = keep(g, dalloc<unsigned char>(bits_bytes + b2 + b3 + h4n * 16 + 256, s));
-  BitsOut bo{};
-  if (bitmaps) {
-    g->bits2 = reinterpret_cast<uint32_t*>(owned);
-    g->bits3 = reinterpret_cast<uint32_t*>(owned + bb);
-    g->bits4 = reinterpret_cast<uint32_t*>(owned + 2 * bb);
-    if (tw) g->tri3 = reinterpret_cast<uint32_t*>(owned + 3 * bb);
-    const hm::DevGraph gv = g->view();
-    bo = BitsOut{g->bits2, g->bits3, g->bits4, g->tri3, g->bwords, gv.block, n, gv.block_inv};
-  }
-  {
-    unsigned char* eb = owned + bits_bytes;
-    g->e2 = reinterpret_cast<uint64_t*>(eb);
-    if (h3n) g->e3 = reinterpret_cast<int4*>(eb + b2);
-    if (h4n) g->e4 = reinterpret_cast<int4*>(eb + b2 + b3);
-  }
+  unsigned char* owned = keep(g, dalloc<unsigned char>(b2 + b3 + h4n * 16 + 256, s));
+  g->e2 = reinterpret_cast<uint64_t*>(owned);
+  if (h3n) g->e3 = reinterpret_cast<int4*>(owned + b2);
+  if (h4n) g->e4 = reinterpret_cast<int4*>(owned + b2 + b3);
   // Sort keys: every size without bitmaps; with bitmaps only the 3- and
   // 4-hyperedges (pairs are read off the pair rows, sorted and without repeats
   // by construction). E_2, E_3, E_4 come out in ascending order in their final
   // layout; their sizes land in kept[] (one synchronisation).
-  const size_t k2 = bitmaps ? 0 : h2n, k3 = h3n;
-  const size_t key_words = k2 + 2 * k3 + 2 * h4n;
   SortJob jobs[3];
   int nj = 0;
-  // key_base / kept_base: where the keys and counts will live (the sizing
-  // pass only needs which words exist)
-  auto make_jobs = [&](uint64_t* key_base, uint64_t* kept_base) {
-    uint64_t* c2 = key_base;
-    uint64_t* c3hi = c2 + k2;
-    uint64_t* c3lo = c3hi + k3;
-    uint64_t* c4hi = c3lo + k3;
-    uint64_t* c4lo = c4hi + h4n;
+  // kept_base: where the counts will live (the sizing pass only needs which
+  // words exist)
+  auto make_jobs = [&](uint64_t* kept_base) {
     nj = 0;
-    auto add = [&](uint64_t* lo, uint64_t* hi, int64_t cnt, int size, int unpack, void* out) {
+    auto add = [&](uint64_t* lo, uint64_t* hi, int64_t count, int size, int unpack, void* out) {
       SortJob& J = jobs[nj];
       J = SortJob{};
       J.a = lo;
       J.b = hi;
       J.b_is_key = hi != nullptr;
-      J.n = cnt;
+      J.n = count;
       const int bits = size * b, lo_bits = bits > 64 ? 64 : bits, hi_bits = bits - lo_bits;
       for (int sh = 0; sh < lo_bits; sh += 8) {
         J.arr[J.passes] = 0;
@@ -712,32 +718,19 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
     if (!bitmaps) add(c2, nullptr, (int64_t)h2n, 2, SortJob::PAIR, g->e2);
     if (kmax >= 3) add(c3lo, c3hi, (int64_t)h3n, 3, SortJob::TRIPLE, g->e3);
     if (kmax >= 4) add(c4lo, c4hi, (int64_t)h4n, 4, SortJob::QUAD, g->e4);
-    return std::make_tuple(c2, c3hi, c3lo, c4hi, c4lo);
   };
   size_t sort_zero = 0, sort_bytes = 0;
   {
     uint64_t sizing[1];  // never dereferenced: only non-null matters
-    make_jobs(sizing, sizing);
+    make_jobs(sizing);
     if (nj) sort_bytes = sort_batch_scratch(jobs, nj, &sort_zero);
   }
-  const size_t o_sort = 256, o_keys = o_sort + al(sort_bytes), o_rc = o_keys + al(key_words * 8);
+  const size_t o_sort = 256, o_rc = o_sort + al(sort_bytes);
   DBuf<unsigned char> tmp(o_rc + ((size_t)n + 1) * 8, s);
   uint64_t* kept = reinterpret_cast<uint64_t*>(tmp.p);
   uint64_t* rc2 = reinterpret_cast<uint64_t*>(tmp.p + o_rc);
-  if (bitmaps) HM_CUDA(cudaMemsetAsync(owned, 0, bits_bytes, s));
   HM_CUDA(cudaMemsetAsync(tmp.p, 0, o_sort + sort_zero, s));
-  const auto keyp = make_jobs(reinterpret_cast<uint64_t*>(tmp.p + o_keys), kept);
-  if (m > 0) {
-    uint64_t *c2, *c3hi, *c3lo, *c4hi, *c4lo;
-    std::tie(c2, c3hi, c3lo, c4hi, c4lo) = keyp;
-    if (bitmaps)
-      k_normalize<2><<<norm_grid(m), NORM_THREADS, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt2, err_p,
-                                                c2, c3hi, c3lo, c4hi, c4lo, bo);
-    else
-      k_normalize<1><<<norm_grid(m), NORM_THREADS, 0, s>>>(d_members, d_offsets, m, n, kmax, b, cnt2, err_p,
-                                                c2, c3hi, c3lo, c4hi, c4lo, bo);
-    HM_KCHECK();
-  }
+  make_jobs(kept);
   if (bitmaps) {
     // pair rows -> E_2 (f[0]), sorts (s)
     Fork f(s, 1);
@@ -765,6 +758,7 @@ void build_graph(hm_graph* g, const int32_t* d_members, const int64_t* d_offsets
   if (kmax >= 3) g->counts[3] = m3;
   if (kmax >= 4) g->counts[4] = m4;
   tmp.release();
+  keybuf.release();
 
   TraceSpan span_tables("ingest_structures", s);
   // Outputs and temporaries on `s`; then three independent chains run
