@@ -886,22 +886,31 @@ struct ScanBatch {
 
 // In place: a[i] = sum of the input a[0..i), a[n] = total (and *total). Each
 // tile reads its 2048 inputs before anything of it is written, and no tile
-// reads another's inputs, so in-place is safe.
-__global__ void __launch_bounds__(TPB) k_scan_batch(const ScanBatch B) {
+// reads another's inputs, so in-place is safe. The tile moves through shared
+// memory both ways, so that global loads and stores are coalesced while each
+// thread scans IPT consecutive values.
+__global__ void __launch_bounds__(TPB) k_scan_batch(const __grid_constant__ ScanBatch B) {
   __shared__ uint64_t wtot[TPB / 32];
   __shared__ uint64_t tile_excl;
   __shared__ uint32_t tile_s;
+  __shared__ uint64_t stage[TILE];
   int e = 0;
   while (e + 1 < B.nj && (int64_t)blockIdx.x >= B.first[e + 1]) ++e;
   const ScanDev& J = B.j[e];
   if (threadIdx.x == 0) tile_s = B.single ? 0u : atomicAdd(J.ctr, 1u);
   __syncthreads();
   const int64_t tile = tile_s;
-  const int64_t i0 = tile * TILE + (int64_t)threadIdx.x * IPT;
+  const int64_t t0 = tile * TILE;
+#pragma unroll
+  for (int it = 0; it < IPT; ++it) {
+    const int64_t i = t0 + it * TPB + threadIdx.x;
+    stage[it * TPB + threadIdx.x] = i < J.n ? J.a[i] : 0;
+  }
+  __syncthreads();
   uint64_t v[IPT], sum = 0;
 #pragma unroll
   for (int it = 0; it < IPT; ++it) {
-    v[it] = i0 + it < J.n ? J.a[i0 + it] : 0;
+    v[it] = stage[threadIdx.x * IPT + it];
     sum += v[it];
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -940,8 +949,14 @@ __global__ void __launch_bounds__(TPB) k_scan_batch(const ScanBatch B) {
   uint64_t run = tile_excl + before + incl - sum;
 #pragma unroll
   for (int it = 0; it < IPT; ++it) {
-    if (i0 + it < J.n) J.a[i0 + it] = run;
+    stage[threadIdx.x * IPT + it] = run;
     run += v[it];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < IPT; ++it) {
+    const int64_t i = t0 + it * TPB + threadIdx.x;
+    if (i < J.n) J.a[i] = stage[it * TPB + threadIdx.x];
   }
 }
 
