@@ -863,18 +863,31 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// After the records are sorted by t: 3-hyperedge t's records are [rs[t], re[t]).
-__global__ void k_txs_runs(const uint64_t* __restrict__ rec, uint64_t nrec,
-                           int64_t* __restrict__ rs, int64_t* __restrict__ re) {
+// Records grouped by 3-hyperedge without a sort (their order within a
+// 3-hyperedge does not matter): counts per t into the zeroed rs, an exclusive
+// scan of rs (so t's records are [rs[t], rs[t + 1])), then each record placed
+// at rs[t] plus a per-t cursor.
+__global__ void k_txs_rec_count(const uint64_t* __restrict__ rec, uint64_t nrec,
+                                unsigned long long* __restrict__ cnt) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nrec;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t r = rec[i];
+    if (r != REC_NONE) atomicAdd(&cnt[r & REC_T], 1ull);
+  }
+}
+
+__global__ void k_txs_rec_place(const uint64_t* __restrict__ rec, uint64_t nrec,
+                                const int64_t* __restrict__ rs, unsigned int* __restrict__ cur,
+                                uint64_t* __restrict__ out) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nrec;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t r = rec[i];
     if (r == REC_NONE) continue;
     const uint64_t t = r & REC_T;
-    if (i == 0 || (rec[i - 1] & REC_T) != t) rs[t] = (int64_t)i;
-    if (i + 1 == nrec || (rec[i + 1] & REC_T) != t) re[t] = (int64_t)(i + 1);
+    out[rs[t] + atomicAdd(&cur[t], 1u)] = r;
   }
 }
+
 
 // Splits E_3 for k_census_txs: a 3-hyperedge whose every scanned list (per
 // member pair, the out-list of its lower-ranked member or, for a pair inside
@@ -1379,8 +1392,9 @@ void launch_txs(const hm_graph* g, unsigned long long* hist, cudaStream_t s, boo
   };
   const size_t o_lists = take((size_t)2 * m3 * 4), o_counts = take(16), o_share = take((size_t)m3),
                o_tab = take((size_t)tcap * 8), o_val = take((size_t)tcap * 4),
-               o_bloom = take((size_t)nbits / 8), o_runs = take((size_t)2 * m3 * 8),
-               o_rec = take((size_t)std::max<uint64_t>(1, nrec) * 8);
+               o_bloom = take((size_t)nbits / 8), o_runs = take(((size_t)m3 + 1) * 8),
+               o_cur = take((size_t)m3 * 4), o_rec = take((size_t)std::max<uint64_t>(1, nrec) * 8),
+               o_grp = take((size_t)std::max<uint64_t>(1, nrec) * 8);
   DBuf<unsigned char> buf(at, s);
   int32_t* small = reinterpret_cast<int32_t*>(buf.p + o_lists);
   int32_t* large = small + m3;
@@ -1389,18 +1403,22 @@ void launch_txs(const hm_graph* g, unsigned long long* hist, cudaStream_t s, boo
   unsigned long long* tab = reinterpret_cast<unsigned long long*>(buf.p + o_tab);
   int32_t* tval = reinterpret_cast<int32_t*>(buf.p + o_val);
   uint32_t* bloom = reinterpret_cast<uint32_t*>(buf.p + o_bloom);
+  // t's records are [rs[t], re[t]) = [rs[t], rs[t + 1]) of grp
   int64_t* rs = reinterpret_cast<int64_t*>(buf.p + o_runs);
-  int64_t* re = rs + m3;
+  int64_t* re = rs + 1;
+  unsigned int* cur = reinterpret_cast<unsigned int*>(buf.p + o_cur);
   uint64_t* rec = reinterpret_cast<uint64_t*>(buf.p + o_rec);
+  uint64_t* grp = reinterpret_cast<uint64_t*>(buf.p + o_grp);
   // two trace spans: the preparation (member-pair set, quad filter, wedge
-  // records and their sort, the split) and the TX kernel itself
+  // records grouped by 3-hyperedge, the split) and the TX kernel itself
   cudaEvent_t ev = nullptr;
   const bool trp = traced && trace_on("census_TX_prep");
   if (trp) trace_begin(s, &ev);
   HM_CUDA(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned int), s));
   HM_CUDA(cudaMemsetAsync(tab, 0xFF, (size_t)tcap * 8, s));
   HM_CUDA(cudaMemsetAsync(bloom, 0, (size_t)nbits / 8, s));
-  HM_CUDA(cudaMemsetAsync(rs, 0, (size_t)2 * m3 * 8, s));
+  HM_CUDA(cudaMemsetAsync(rs, 0, ((size_t)m3 + 1) * 8, s));
+  HM_CUDA(cudaMemsetAsync(cur, 0, (size_t)m3 * 4, s));
   k_tp_insert<<<grid1d(m3), 256, 0, s>>>(g->view(), tab, tval, tcap - 1);
   HM_KCHECK();
   if (g->counts[4]) {
@@ -1408,16 +1426,17 @@ void launch_txs(const hm_graph* g, unsigned long long* hist, cudaStream_t s, boo
     HM_KCHECK();
   }
   if (nrec) {
-    // records by 3-hyperedge: a stable sort on the low bits that hold t
-    // (2^ebits > m3, so the sentinels sort last)
-    int ebits = 1;
-    while ((1ll << ebits) <= m3) ++ebits;
+    // records grouped by 3-hyperedge: counts, offsets, placement
     const uint64_t want = ((uint64_t)g->n + 255) / 256;
     k_txs_wedges<<<(unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, 152 * 8)), 256, 0, s>>>(
         g->view(), g->out_deg, g->out_adj, g->TXO.ws, tab, tval, tcap - 1, rec);
     HM_KCHECK();
-    radix_sort_u64(rec, nullptr, (int64_t)nrec, ebits, s);
-    k_txs_runs<<<grid1d((int64_t)nrec), 256, 0, s>>>(rec, nrec, rs, re);
+    k_txs_rec_count<<<grid1d((int64_t)nrec), 256, 0, s>>>(
+        rec, nrec, reinterpret_cast<unsigned long long*>(rs));
+    HM_KCHECK();
+    ScanJob sj{reinterpret_cast<uint64_t*>(rs), m3, nullptr};
+    scan_batch_inplace(&sj, 1, s);
+    k_txs_rec_place<<<grid1d((int64_t)nrec), 256, 0, s>>>(rec, nrec, rs, cur, grp);
     HM_KCHECK();
   }
   k_txs_split<<<grid1d(m3), 256, 0, s>>>(g->view(), tab, tcap - 1, bloom, nbits, g->out_deg, rs,
@@ -1431,7 +1450,7 @@ void launch_txs(const hm_graph* g, unsigned long long* hist, cudaStream_t s, boo
   const int64_t want = (m3 + CENSUS_THREADS / 8 - 1) / (CENSUS_THREADS / 8);
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * per));
   k_census_txs<<<blocks, CENSUS_THREADS, 0, s>>>(g->view(), large, small, counts, share,
-                                                 g->out_deg, g->out_adj, rec, rs, re, lut,
+                                                 g->out_deg, g->out_adj, grp, rs, re, lut,
                                                  (int)T.lut.size(), T.ncls, sub ? 1 : 0, hist);
   HM_KCHECK();
   if (tr) trace_end("census_TX", s, ev);
