@@ -149,9 +149,12 @@ hm_status hm_count_exact(hm_graph* g, int order, uint64_t* d_hist, void* stream)
  *   d_raw             uint64[2 * ncls] (device) or NULL: (raw[2c], raw[2c+1]) =
  *                     low and high words of the integer accumulator of class c
  *                     (the plain count n_c for uniform draws).
- * Enqueued on `stream`. HM_EINVAL on a bad order, or when a stratum with
- * |E_s| > 0 gets S_s == 0 (its classes could not be estimated); an empty
- * stratum contributes an exact 0. HM_EUNSUPPORTED if order > max_order.
+ * Runs on `stream`, which it synchronises between stages to size them. At
+ * order 4 the first call with S_2 > 0 builds the graph's node -> 4-hyperedge
+ * lists (kept with the graph, 4 bytes per incidence). HM_EINVAL on a bad
+ * order, or when a stratum with |E_s| > 0 gets S_s == 0 (its classes could
+ * not be estimated); an empty stratum contributes an exact 0.
+ * HM_EUNSUPPORTED if order > max_order.
  */
 hm_status hm_count_sampled(hm_graph* g, int order, const uint64_t* samples_per_size,
                            uint64_t total_samples, uint64_t seed, const uint32_t* d_q,
