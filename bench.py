@@ -85,6 +85,8 @@ ROOFLINE_NCU = {
 ALU_LANES_PER_SM_CLK = 64
 # kernel -> (unit, algorithmic ops per unit or None when counted from the
 # graph, DRAM bytes per launch from ncu on the face-to-face workload)
+# L2 sectors per launch of the dense kernels (ncu, the face-to-face workload)
+L2_SECTORS_ALU = {"census_gl_edges": 103_600}
 ROOFLINE_ALU = {
     "census_gl_edges": ("pair", None, 145_000),
     "census_gl_pairs": ("node pair", None, 26_000),
@@ -560,6 +562,13 @@ def small_exact_row(hm, stream, flush, order=4, steps=20, warmup=5):
     peak = sms * ALU_LANES_PER_SM_CLK * mhz * 1e6 / 1e12
     ach = (ops / r["dom_avg_s"] / 1e12) if ops and r["dom_avg_s"] else None
     ms = r["total_ms"] / steps
+    l2 = None
+    if dom in L2_SECTORS_ALU and r["dom_avg_s"]:
+        # the kernel's L2 sectors (ncu) over its live launch time, against the
+        # L2 read bandwidth of the library's probe
+        l2_peak = hm.l2_read_bandwidth(64 << 20, 20, stream)
+        a2 = L2_SECTORS_ALU[dom] * 32 / r["dom_avg_s"] / 1e9
+        l2 = {"achieved": a2, "peak": l2_peak, "unit": "GB/s", "frac": a2 / l2_peak}
     return {"workload": "f2f-330", "nodes": h.num_nodes, "hyperedges": h.num_hyperedges,
             "ms_per_step": ms, "sets_per_step": r["sets_per_step"],
             "sets_per_s": r["sets_per_step"] / (ms / 1e3), "kernels": r["kernels"],
@@ -570,7 +579,8 @@ def small_exact_row(hm, stream, flush, order=4, steps=20, warmup=5):
                          "units_per_launch": units, "unit_kind": unit, "ops_per_unit": per_unit,
                          "launch_ms": (r["dom_avg_s"] or 0) * 1e3,
                          "peak_source": f"{sms} SMs x {ALU_LANES_PER_SM_CLK} lanes x {mhz:.0f} "
-                                        f"MHz (maximum SM clock, {src})"}}
+                                        f"MHz (maximum SM clock, {src})",
+                         **({"l2": l2} if l2 else {})}}
 
 
 def mre(est, T, mask):
