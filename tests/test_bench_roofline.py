@@ -33,3 +33,24 @@ def test_random_graphs_match_direct_count():
         pairs = {tuple(sorted(rng.choice(n, 2, replace=False))) for _ in range(3 * n)}
         e2 = np.array(sorted(pairs))
         assert bench.graphlet_pair_ops(e2, n, bw) == _brute(e2, n, bw)
+
+
+def test_hbm_roofline_fields():
+    # 288 B per TX candidate over the launch time, against the copy bandwidth;
+    # the DRAM bytes of the capture over the same time beside it
+    r = bench.hbm_roofline("census_TX", {"census_TX": 1_000_000}, 1e-4, 5000.0, "measured")
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - 1_000_000 * 288 / 1e-4 / 1e9) < 1e-6
+    assert abs(r["frac"] - r["achieved"] / 5000.0) < 1e-12
+    traffic = bench.ROOFLINE_HBM["census_TX"][3]
+    assert r["traffic"] == traffic
+    assert abs(r["dram_gbs_from_traffic"] - traffic / 1e-4 / 1e9) < 1e-6
+    assert r["ncu"]["kernel"] == "k_census_txs"
+    # a kernel without a byte model reports nulls, not a made-up fraction
+    n = bench.hbm_roofline("census_c4_table", {}, 1e-4, 5000.0, "measured")
+    assert n["achieved"] is None and n["frac"] is None and n["traffic"] is None
+
+
+def test_whole_job_rate():
+    # replicas: every rank does the units of a step, the slowest rank's time counts
+    assert bench.whole_job_rate(1000, 10, 4, 20.0) == 1000 * 10 * 4 / 0.02
