@@ -89,8 +89,11 @@ hm_status hm_class_of_mask(int order, uint32_t mask, int32_t* cls);
  * than two distinct members are dropped, duplicate hyperedges collapse (E is a
  * set). Hyperedges with more than max_order distinct members cannot lie in a
  * max_order-node set (Def. 2), so they are only counted (hm_graph_info).
- * Synchronous on `stream`. Errors: HM_EINVAL (bad sizes, a member outside
- * [0, num_nodes), offsets not monotone), HM_ENOMEM, HM_ECUDA, HM_ETABLEFULL (a
+ * Synchronous on `stream`. Besides what the graph keeps, the build takes
+ * temporaries of about 40 bytes per input hyperedge (sort keys sized for every
+ * hyperedge, so that one pass normalises). Errors: HM_EINVAL (bad sizes, a
+ * member outside [0, num_nodes), offsets not monotone), HM_ENOMEM, HM_ECUDA,
+ * HM_EUNSUPPORTED (2^31 or more distinct pairs), HM_ETABLEFULL (a
  * hash set could not hold its keys: only when the HM_TABLE_CAP test hook
  * forces tables smaller than their key sets), HM_ETIMEOUT (a bounded wait of
  * the sort gave up). On success *out owns device memory until hm_free.
